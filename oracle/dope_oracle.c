@@ -1,0 +1,717 @@
+/*
+ * DOPE oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, CPU implementation of what the DOPE ADMM hot path computes
+ * (Dolz, Ben Ayed, Desrosiers, "DOPE: Distributed Optimization for Pairwise
+ * Energies", arXiv 1704.03116).  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load it.  The CUDA library
+ * never links, includes or calls anything here, and nothing here comes from
+ * the CUDA library.
+ *
+ * Floating point: every double operation is a single IEEE round-to-nearest
+ * operation in the order written (the build passes -ffp-contract=off and no
+ * fast-math), because several of these doubles decide integers (Eq. 8's
+ * capacities are rounded to int64).
+ *
+ * Contents
+ *   orc_quantise        instance canonicalisation of Eq. 1 (fixed point x1024)
+ *   orc_energy          Eq. 1 / Eq. 3 on the quantised instance, int64
+ *   orc_bk_mincut       Boykov-Kolmogorov max-flow (the serial solver the paper
+ *                       uses for Eq. 8 and for sGC), written from the published
+ *                       algorithm: two search trees, growth / augmentation /
+ *                       adoption, with the distance + timestamp heuristic; the
+ *                       canonical (pointwise-minimal) sink side is taken by a
+ *                       backward residual BFS from t
+ *   orc_bruteforce      enumeration of all 2^n labelings (n <= 24), any sign
+ *   orc_shifted_caps    Eq. 8 unary of every block (Q = I), x1024, rounded
+ *   orc_block_cuts      Eq. 8 solved exactly per block ("in parallel", Alg. 1)
+ *   orc_update          Eq. 10 (y) and Eq. 11 (a) for Q = I, per-block ||yhat_k - S_k y||^2
+ *   orc_admm            Algorithm 1 end to end
+ *   orc_global_mincut   the whole-image serial graph cut (sGC) of Section 3
+ *
+ * Notation follows the paper: u (unary), w (pairwise), lambda, y (relaxed
+ * global labels), yhat (block labels), a (scaled multipliers), mu.
+ * For the non-overlapping partition (Q = I) Theorem 1 gives, for pixel i in
+ * block b(i) with cross-block neighbours X(i) = { j in N(i) : b(j) != b(i) }:
+ *   (C_k + R_k S_k) y  at i  =  sum_{j in X(i)} w_ij (y_i - y_j)
+ * which is what orc_shifted_caps and orc_update evaluate (the literal matrix
+ * form of Theorem 1 lives in oracle/theorem1.py and pins this).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Grid geometry                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Forward neighbour offsets (dz, dy, dx) in weight-layout order.
+ * 2-D grids are stored with D = 1.  Direction k < d/2 is forward offset k,
+ * direction k >= d/2 is the backward offset k - d/2. */
+static const int OFF4[2][3] = {{0, 0, 1}, {0, 1, 0}};
+static const int OFF8[4][3] = {{0, 0, 1}, {0, 1, 0}, {0, 1, 1}, {0, 1, -1}};
+static const int OFF6[3][3] = {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}};
+
+typedef struct {
+    int64_t D, H, W;      /* grid extent, D = 1 for 2-D */
+    int conn;             /* 4, 8 (2-D) or 6 (3-D) */
+    int bd, bh, bw;       /* block shape, bd = 1 for 2-D */
+    int nh;               /* number of forward offsets = conn / 2 */
+    const int (*off)[3];
+} grid_t;
+
+static int grid_init(grid_t *g, const int64_t *dims, int conn, const int *block)
+{
+    g->D = dims[0]; g->H = dims[1]; g->W = dims[2];
+    g->conn = conn;
+    g->bd = block[0]; g->bh = block[1]; g->bw = block[2];
+    if (conn == 4) { g->off = OFF4; g->nh = 2; }
+    else if (conn == 8) { g->off = OFF8; g->nh = 4; }
+    else if (conn == 6) { g->off = OFF6; g->nh = 3; }
+    else return -1;
+    if (g->D <= 0 || g->H <= 0 || g->W <= 0) return -1;
+    if (g->bd <= 0 || g->bh <= 0 || g->bw <= 0) return -1;
+    if (g->D % g->bd || g->H % g->bh || g->W % g->bw) return -1;
+    return 0;
+}
+
+static inline int64_t g_n(const grid_t *g) { return g->D * g->H * g->W; }
+
+/* Neighbour of pixel (z,y,x) along direction k, or -1 outside the grid. */
+static inline int64_t g_nbr(const grid_t *g, int64_t z, int64_t y, int64_t x, int k,
+                            int64_t *nz, int64_t *ny, int64_t *nx)
+{
+    int s = (k < g->nh) ? 1 : -1;
+    int o = (k < g->nh) ? k : k - g->nh;
+    int64_t zz = z + s * g->off[o][0], yy = y + s * g->off[o][1], xx = x + s * g->off[o][2];
+    if (zz < 0 || zz >= g->D || yy < 0 || yy >= g->H || xx < 0 || xx >= g->W) return -1;
+    *nz = zz; *ny = yy; *nx = xx;
+    return (zz * g->H + yy) * g->W + xx;
+}
+
+/* Weight of the undirected edge between pixel i and its neighbour j along
+ * direction k: forward edges are stored at i, backward ones at j. */
+static inline int64_t g_wt(const grid_t *g, const int64_t *Wl, int64_t i, int64_t j, int k)
+{
+    int64_t n = g_n(g);
+    if (k < g->nh) return Wl[(int64_t)k * n + i];
+    return Wl[(int64_t)(k - g->nh) * n + j];
+}
+
+static inline int64_t g_block_of(const grid_t *g, int64_t z, int64_t y, int64_t x)
+{
+    int64_t nby = g->H / g->bh, nbx = g->W / g->bw;
+    return ((z / g->bd) * nby + (y / g->bh)) * nbx + (x / g->bw);
+}
+
+static inline int64_t g_nblocks(const grid_t *g)
+{
+    return (g->D / g->bd) * (g->H / g->bh) * (g->W / g->bw);
+}
+
+/* Global pixel index of local node l of block k (block-local order is
+ * row-major over (z, y, x) inside the block). */
+static inline int64_t g_block_pixel(const grid_t *g, int64_t k, int l,
+                                    int64_t *pz, int64_t *py, int64_t *px)
+{
+    int64_t nby = g->H / g->bh, nbx = g->W / g->bw;
+    int64_t kz = k / (nby * nbx), ky = (k / nbx) % nby, kx = k % nbx;
+    int lz = l / (g->bh * g->bw), ly = (l / g->bw) % g->bh, lx = l % g->bw;
+    int64_t z = kz * g->bd + lz, y = ky * g->bh + ly, x = kx * g->bw + lx;
+    *pz = z; *py = y; *px = x;
+    return (z * g->H + y) * g->W + x;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Instance canonicalisation (Eq. 1, Eq. 2)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* U_i = rne(1024 u_i), Wl_ij = rne(lambda * wq_ij); wq is already x1024.
+ * Returns 0, or -2 if a weight is negative (not submodular, footnote on
+ * submodularity in Section 1), -3 if a weight toward a pixel outside the
+ * grid is non-zero. */
+int orc_quantise(const int64_t *dims, int conn, const int *block,
+                 const float *u, const int32_t *wq, double lambda,
+                 int64_t *U, int64_t *Wl)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    int64_t n = g_n(&g);
+    for (int64_t i = 0; i < n; i++) U[i] = llrint(1024.0 * (double)u[i]);
+    for (int k = 0; k < g.nh; k++) {
+        for (int64_t z = 0; z < g.D; z++)
+            for (int64_t y = 0; y < g.H; y++)
+                for (int64_t x = 0; x < g.W; x++) {
+                    int64_t i = (z * g.H + y) * g.W + x, nz, ny, nx;
+                    int32_t w = wq[(int64_t)k * n + i];
+                    if (w < 0) return -2;
+                    if (g_nbr(&g, z, y, x, k, &nz, &ny, &nx) < 0 && w != 0) return -3;
+                    Wl[(int64_t)k * n + i] = llrint(lambda * (double)w);
+                }
+    }
+    return 0;
+}
+
+/* E_int(y) = sum_i U_i y_i + sum_{undirected edges} Wl_ij |y_i - y_j|  (Eq. 1,
+ * each undirected edge counted once, as in y^T L y of Eq. 3).  E = E_int/1024. */
+int64_t orc_energy(const int64_t *dims, int conn, const int *block,
+                   const int64_t *U, const int64_t *Wl, const uint8_t *lab)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return INT64_MIN;
+    int64_t n = g_n(&g), e = 0;
+    for (int64_t i = 0; i < n; i++) e += U[i] * (int64_t)lab[i];
+    for (int k = 0; k < g.nh; k++)
+        for (int64_t z = 0; z < g.D; z++)
+            for (int64_t y = 0; y < g.H; y++)
+                for (int64_t x = 0; x < g.W; x++) {
+                    int64_t i = (z * g.H + y) * g.W + x, nz, ny, nx;
+                    int64_t j = g_nbr(&g, z, y, x, k, &nz, &ny, &nx);
+                    if (j < 0) continue;
+                    if (lab[i] != lab[j]) e += Wl[(int64_t)k * n + i];
+                }
+    return e;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Boykov-Kolmogorov max-flow                                               */
+/* ------------------------------------------------------------------------ */
+
+#define BK_TERMINAL (-1)
+#define BK_ORPHAN (-2)
+#define BK_FREE (-3)
+#define TREE_NONE 0
+#define TREE_S 1
+#define TREE_T 2
+
+typedef struct {
+    int n, m;           /* nodes, arcs (arcs come in sister pairs a, a^1) */
+    int *first, *next, *head;
+    int64_t *rcap;      /* residual capacity of each arc */
+    int64_t *tr;        /* >0: residual s->i, <0: residual i->t */
+    int *parent;        /* arc from node to its tree parent, or BK_* */
+    unsigned char *tree;
+    int *ts, *dist;
+    int *q; unsigned char *inq; int qh, qt;   /* FIFO of active nodes, size n+1 */
+    int *orph; int norph;                       /* orphan stack */
+    long time;
+} bk_t;
+
+static int bk_alloc(bk_t *b, int n, int medges)
+{
+    memset(b, 0, sizeof(*b));
+    b->n = n; b->m = 0;
+    b->first = malloc(sizeof(int) * (size_t)n);
+    b->next = malloc(sizeof(int) * (size_t)(2 * medges + 2));
+    b->head = malloc(sizeof(int) * (size_t)(2 * medges + 2));
+    b->rcap = malloc(sizeof(int64_t) * (size_t)(2 * medges + 2));
+    b->tr = calloc((size_t)n, sizeof(int64_t));
+    b->parent = malloc(sizeof(int) * (size_t)n);
+    b->tree = calloc((size_t)n, 1);
+    b->ts = calloc((size_t)n, sizeof(int));
+    b->dist = calloc((size_t)n, sizeof(int));
+    b->q = malloc(sizeof(int) * (size_t)(n + 1));
+    b->inq = calloc((size_t)n, 1);
+    b->orph = malloc(sizeof(int) * (size_t)(n + 1));
+    if (!b->first || !b->next || !b->head || !b->rcap || !b->tr || !b->parent ||
+        !b->tree || !b->ts || !b->dist || !b->q || !b->inq || !b->orph) return -1;
+    for (int i = 0; i < n; i++) b->first[i] = -1;
+    return 0;
+}
+
+static void bk_free(bk_t *b)
+{
+    free(b->first); free(b->next); free(b->head); free(b->rcap); free(b->tr);
+    free(b->parent); free(b->tree); free(b->ts); free(b->dist); free(b->q);
+    free(b->inq); free(b->orph);
+}
+
+/* Undirected-with-two-capacities edge: cap(i->j) = cij, cap(j->i) = cji. */
+static void bk_edge(bk_t *b, int i, int j, int64_t cij, int64_t cji)
+{
+    int a = b->m, s = b->m + 1;
+    b->head[a] = j; b->rcap[a] = cij; b->next[a] = b->first[i]; b->first[i] = a;
+    b->head[s] = i; b->rcap[s] = cji; b->next[s] = b->first[j]; b->first[j] = s;
+    b->m += 2;
+}
+
+static void bk_activate(bk_t *b, int i)
+{
+    if (b->inq[i]) return;
+    b->inq[i] = 1;
+    b->q[b->qt] = i;
+    b->qt = (b->qt + 1) % (b->n + 1);
+}
+
+static int bk_pop(bk_t *b)
+{
+    while (b->qh != b->qt) {
+        int i = b->q[b->qh];
+        b->qh = (b->qh + 1) % (b->n + 1);
+        b->inq[i] = 0;
+        if (b->tree[i] != TREE_NONE) return i;
+    }
+    return -1;
+}
+
+static void bk_orphan(bk_t *b, int i)
+{
+    b->parent[i] = BK_ORPHAN;
+    b->orph[b->norph++] = i;
+}
+
+/* Augment along s ~> tail(a) -a-> head(a) ~> t. */
+static void bk_augment(bk_t *b, int a)
+{
+    int x, pa;
+    int64_t bn = b->rcap[a];
+    /* bottleneck on the source side */
+    for (x = b->head[a ^ 1];; x = b->head[pa]) {
+        pa = b->parent[x];
+        if (pa == BK_TERMINAL) { if (b->tr[x] < bn) bn = b->tr[x]; break; }
+        if (b->rcap[pa ^ 1] < bn) bn = b->rcap[pa ^ 1];
+    }
+    /* bottleneck on the sink side */
+    for (x = b->head[a];; x = b->head[pa]) {
+        pa = b->parent[x];
+        if (pa == BK_TERMINAL) { if (-b->tr[x] < bn) bn = -b->tr[x]; break; }
+        if (b->rcap[pa] < bn) bn = b->rcap[pa];
+    }
+    b->rcap[a] -= bn; b->rcap[a ^ 1] += bn;
+    for (x = b->head[a ^ 1];;) {
+        pa = b->parent[x];
+        if (pa == BK_TERMINAL) {
+            b->tr[x] -= bn;
+            if (b->tr[x] == 0) bk_orphan(b, x);
+            break;
+        }
+        int nx = b->head[pa];
+        b->rcap[pa] += bn; b->rcap[pa ^ 1] -= bn;
+        if (b->rcap[pa ^ 1] == 0) bk_orphan(b, x);
+        x = nx;
+    }
+    for (x = b->head[a];;) {
+        pa = b->parent[x];
+        if (pa == BK_TERMINAL) {
+            b->tr[x] += bn;
+            if (b->tr[x] == 0) bk_orphan(b, x);
+            break;
+        }
+        int nx = b->head[pa];
+        b->rcap[pa ^ 1] += bn; b->rcap[pa] -= bn;
+        if (b->rcap[pa] == 0) bk_orphan(b, x);
+        x = nx;
+    }
+}
+
+/* Adoption stage: find each orphan a new parent in its own tree whose path
+ * reaches the terminal, preferring the shortest; otherwise free it. */
+static void bk_adopt(bk_t *b)
+{
+    while (b->norph > 0) {
+        int p = b->orph[--b->norph];
+        int tp = b->tree[p];
+        int best = -1, dmin = 1 << 30;
+        b->time++;
+        for (int a = b->first[p]; a >= 0; a = b->next[a]) {
+            int q = b->head[a];
+            if (b->tree[q] != tp) continue;
+            int64_t r = (tp == TREE_S) ? b->rcap[a ^ 1] : b->rcap[a];
+            if (r <= 0) continue;
+            /* walk to the root of q */
+            int d = 0, j = q, ok = 0;
+            for (;;) {
+                if (b->ts[j] == b->time) { d += b->dist[j]; ok = 1; break; }
+                int pj = b->parent[j];
+                d++;
+                if (pj == BK_TERMINAL) { b->ts[j] = (int)b->time; b->dist[j] = 1; ok = 1; break; }
+                if (pj == BK_ORPHAN || pj == BK_FREE) break;
+                j = b->head[pj];
+            }
+            if (!ok) continue;
+            if (d < dmin) { dmin = d; best = a; }
+            for (j = q; b->ts[j] != b->time; j = b->head[b->parent[j]]) {
+                b->ts[j] = (int)b->time; b->dist[j] = d; d--;
+            }
+        }
+        if (best >= 0) {
+            b->parent[p] = best;
+            b->ts[p] = (int)b->time;
+            b->dist[p] = dmin + 1;
+            continue;
+        }
+        /* no parent: p becomes free */
+        for (int a = b->first[p]; a >= 0; a = b->next[a]) {
+            int q = b->head[a];
+            if (b->tree[q] != tp) continue;
+            int64_t r = (tp == TREE_S) ? b->rcap[a ^ 1] : b->rcap[a];
+            if (r > 0) bk_activate(b, q);
+            int pq = b->parent[q];
+            if (pq >= 0 && b->head[pq] == p) bk_orphan(b, q);
+        }
+        b->tree[p] = TREE_NONE;
+        b->parent[p] = BK_FREE;
+    }
+}
+
+/* Max-flow; afterwards lab[i] = 1 iff i reaches t in the residual graph,
+ * which is the minimal sink side of all minimum cuts (the pointwise-minimal
+ * minimiser of the energy, with y_i = 1 <=> sink side). */
+static void bk_run(bk_t *b, uint8_t *lab)
+{
+    b->qh = b->qt = 0; b->norph = 0; b->time = 0;
+    for (int i = 0; i < b->n; i++) {
+        if (b->tr[i] > 0) { b->tree[i] = TREE_S; b->parent[i] = BK_TERMINAL; b->dist[i] = 1; bk_activate(b, i); }
+        else if (b->tr[i] < 0) { b->tree[i] = TREE_T; b->parent[i] = BK_TERMINAL; b->dist[i] = 1; bk_activate(b, i); }
+        else { b->tree[i] = TREE_NONE; b->parent[i] = BK_FREE; }
+        b->ts[i] = 0;
+    }
+    for (;;) {
+        int p = bk_pop(b);
+        if (p < 0) break;
+        int found = -1;
+        if (b->tree[p] == TREE_S) {
+            for (int a = b->first[p]; a >= 0; a = b->next[a]) {
+                if (b->rcap[a] <= 0) continue;
+                int q = b->head[a];
+                if (b->tree[q] == TREE_NONE) {
+                    b->tree[q] = TREE_S; b->parent[q] = a ^ 1;
+                    b->ts[q] = b->ts[p]; b->dist[q] = b->dist[p] + 1;
+                    bk_activate(b, q);
+                } else if (b->tree[q] == TREE_T) { found = a; break; }
+                else if (b->ts[q] <= b->ts[p] && b->dist[q] > b->dist[p]) {
+                    b->parent[q] = a ^ 1; b->ts[q] = b->ts[p]; b->dist[q] = b->dist[p] + 1;
+                }
+            }
+        } else {
+            for (int a = b->first[p]; a >= 0; a = b->next[a]) {
+                if (b->rcap[a ^ 1] <= 0) continue;
+                int q = b->head[a];
+                if (b->tree[q] == TREE_NONE) {
+                    b->tree[q] = TREE_T; b->parent[q] = a ^ 1;
+                    b->ts[q] = b->ts[p]; b->dist[q] = b->dist[p] + 1;
+                    bk_activate(b, q);
+                } else if (b->tree[q] == TREE_S) { found = a ^ 1; break; }
+                else if (b->ts[q] <= b->ts[p] && b->dist[q] > b->dist[p]) {
+                    b->parent[q] = a ^ 1; b->ts[q] = b->ts[p]; b->dist[q] = b->dist[p] + 1;
+                }
+            }
+        }
+        b->time++;
+        if (found >= 0) {
+            bk_activate(b, p);   /* p may have unexplored neighbours left */
+            bk_augment(b, found);
+            bk_adopt(b);
+        }
+    }
+    /* canonical cut: backward BFS from t over residual arcs */
+    int *queue = malloc(sizeof(int) * (size_t)(b->n + 1));
+    int qh = 0, qt = 0;
+    for (int i = 0; i < b->n; i++) {
+        lab[i] = 0;
+        if (b->tr[i] < 0) { lab[i] = 1; queue[qt++] = i; }
+    }
+    while (qh < qt) {
+        int x = queue[qh++];
+        for (int a = b->first[x]; a >= 0; a = b->next[a]) {
+            int j = b->head[a];
+            if (!lab[j] && b->rcap[a ^ 1] > 0) { lab[j] = 1; queue[qt++] = j; }
+        }
+    }
+    free(queue);
+}
+
+/* Generic min-cut of  sum_i c_i y_i + sum_e [ cuv_e * (1-y_u) y_v + cvu_e * y_u (1-y_v) ]
+ * with y_i = 1 <=> sink side: terminal capacity c_i > 0 is s->i, c_i < 0 is
+ * i->t; cap(u->v) = cuv_e, cap(v->u) = cvu_e (both >= 0).
+ * Writes the canonical (pointwise-minimal) minimiser to lab; returns 0. */
+int orc_bk_mincut(int n, const int64_t *c, int m, const int32_t *eu, const int32_t *ev,
+                  const int64_t *cuv, const int64_t *cvu, uint8_t *lab)
+{
+    bk_t b;
+    if (bk_alloc(&b, n, m)) { bk_free(&b); return -1; }
+    for (int i = 0; i < n; i++) b.tr[i] = c[i];
+    for (int e = 0; e < m; e++) {
+        if (cuv[e] < 0 || cvu[e] < 0) { bk_free(&b); return -2; }
+        bk_edge(&b, eu[e], ev[e], cuv[e], cvu[e]);
+    }
+    bk_run(&b, lab);
+    bk_free(&b);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brute force (any sign of w): pins the cut on tiny instances              */
+/* ------------------------------------------------------------------------ */
+
+/* E(y) = sum_i c_i y_i + sum_e w_e |y_u - y_v| over all 2^n labelings.
+ * Outputs the minimum, the AND and OR of all minimisers and their count. */
+int orc_bruteforce(int n, const int64_t *c, int m, const int32_t *eu, const int32_t *ev,
+                   const int64_t *w, int64_t *emin, uint8_t *and_lab, uint8_t *or_lab,
+                   int64_t *count)
+{
+    if (n > 24 || n < 0) return -1;
+    int64_t best = INT64_MAX, cnt = 0;
+    uint32_t andm = 0, orm = 0;
+    for (uint32_t s = 0; s < (1u << n); s++) {
+        int64_t e = 0;
+        for (int i = 0; i < n; i++) if (s >> i & 1u) e += c[i];
+        for (int k = 0; k < m; k++)
+            if (((s >> eu[k]) ^ (s >> ev[k])) & 1u) e += w[k];
+        if (e < best) { best = e; cnt = 1; andm = s; orm = s; }
+        else if (e == best) { cnt++; andm &= s; orm |= s; }
+    }
+    *emin = best; *count = cnt;
+    for (int i = 0; i < n; i++) { and_lab[i] = (andm >> i) & 1u; or_lab[i] = (orm >> i) & 1u; }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* DOPE, Q = I (non-overlapping blocks)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 8 unary of every pixel, scaled by 1024 and rounded half-to-even:
+ *   1024 c_i = U_i + sum_{j in X(i)} Wl_ij (y_i - y_j) + (1024 mu) ((a_i - y_i) + 1/2)
+ * i.e. 1024 * ( u_i + lambda [(C_k + R_k S_k) y]_i + mu (a_i - y_i + 1/2) ).
+ * Order of operations: start from U_i, add the cross terms in direction
+ * order k = 0..d-1, then add the multiplier term.  s_out (may be NULL)
+ * receives the unrounded double, C_out the rounded int64. */
+int orc_shifted_caps(const int64_t *dims, int conn, const int *block,
+                     const int64_t *U, const int64_t *Wl,
+                     const double *y, const double *a, double mu,
+                     double *s_out, int64_t *C_out)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    double m1024 = 1024.0 * mu;
+    for (int64_t z = 0; z < g.D; z++)
+        for (int64_t yy = 0; yy < g.H; yy++)
+            for (int64_t x = 0; x < g.W; x++) {
+                int64_t i = (z * g.H + yy) * g.W + x, nz, ny, nx;
+                int64_t bi = g_block_of(&g, z, yy, x);
+                double s = (double)U[i];
+                for (int k = 0; k < g.conn; k++) {
+                    int64_t j = g_nbr(&g, z, yy, x, k, &nz, &ny, &nx);
+                    if (j < 0 || g_block_of(&g, nz, ny, nx) == bi) continue;
+                    double w = (double)g_wt(&g, Wl, i, j, k);
+                    double dy = y[i] - y[j];
+                    double t = w * dy;
+                    s = s + t;
+                }
+                double v = a[i] - y[i];
+                v = v + 0.5;
+                double t = m1024 * v;
+                s = s + t;
+                if (s_out) s_out[i] = s;
+                C_out[i] = llrint(s);
+            }
+    return 0;
+}
+
+/* Eq. 8 for every block, solved exactly by BK on the block graph: terminal
+ * capacity C_i, n-links Wl_ij for edges with both ends in the block (edges
+ * leaving the block are represented by the C_k, R_k terms already inside C).
+ * Blocks are independent ("in parallel", Algorithm 1). */
+int orc_block_cuts(const int64_t *dims, int conn, const int *block,
+                   const int64_t *Wl, const int64_t *C, uint8_t *yhat)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    int64_t K = g_nblocks(&g);
+    int B = g.bd * g.bh * g.bw;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t k = 0; k < K; k++) {
+        bk_t b;
+        uint8_t *lab = malloc((size_t)B);
+        int64_t *gidx = malloc(sizeof(int64_t) * (size_t)B);
+        if (!lab || !gidx || bk_alloc(&b, B, B * g.nh)) { err |= 1; free(lab); free(gidx); continue; }
+        for (int l = 0; l < B; l++) {
+            int64_t z, y, x;
+            gidx[l] = g_block_pixel(&g, k, l, &z, &y, &x);
+            b.tr[l] = C[gidx[l]];
+        }
+        for (int l = 0; l < B; l++) {
+            int64_t z, y, x, nz, ny, nx;
+            int64_t i = g_block_pixel(&g, k, l, &z, &y, &x);
+            for (int o = 0; o < g.nh; o++) {
+                int64_t j = g_nbr(&g, z, y, x, o, &nz, &ny, &nx);
+                if (j < 0 || g_block_of(&g, nz, ny, nx) != k) continue;
+                int lj = (int)(((nz % g.bd) * g.bh + (ny % g.bh)) * g.bw + (nx % g.bw));
+                int64_t w = Wl[(int64_t)o * g_n(&g) + i];
+                if (w > 0) bk_edge(&b, l, lj, w, w);
+            }
+        }
+        bk_run(&b, lab);
+        for (int l = 0; l < B; l++) yhat[gidx[l]] = lab[l];
+        bk_free(&b);
+        free(lab); free(gidx);
+    }
+    return err ? -1 : 0;
+}
+
+/* Eq. 10 and Eq. 11 for Q = I, then the per-block quantity of the stop test:
+ *   g_i   = sum_{j in X(i)} Wl_ij (yhat_i - yhat_j) / 1024   (= lambda [(C+RS)^T yhat]_i)
+ *   y_i   = (yhat_i + a_i) - g_i / mu                        (Eq. 10)
+ *   a_i   = a_i + (yhat_i - y_i)                             (Eq. 11)
+ *   r2_k  = sum_{i in block k} (yhat_i - y_i)^2  (block-local order)
+ * y and a are updated in place. */
+int orc_update(const int64_t *dims, int conn, const int *block,
+               const int64_t *Wl, const uint8_t *yhat, double mu,
+               double *y, double *a, double *r2)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    int64_t n = g_n(&g);
+    for (int64_t z = 0; z < g.D; z++)
+        for (int64_t yy = 0; yy < g.H; yy++)
+            for (int64_t x = 0; x < g.W; x++) {
+                int64_t i = (z * g.H + yy) * g.W + x, nz, ny, nx;
+                int64_t bi = g_block_of(&g, z, yy, x);
+                int64_t G = 0;
+                for (int k = 0; k < g.conn; k++) {
+                    int64_t j = g_nbr(&g, z, yy, x, k, &nz, &ny, &nx);
+                    if (j < 0 || g_block_of(&g, nz, ny, nx) == bi) continue;
+                    G += g_wt(&g, Wl, i, j, k) * ((int64_t)yhat[i] - (int64_t)yhat[j]);
+                }
+                double gi = (double)G / 1024.0;
+                double yi = ((double)yhat[i] + a[i]) - gi / mu;
+                y[i] = yi;
+                a[i] = a[i] + ((double)yhat[i] - yi);
+            }
+    int64_t K = g_nblocks(&g);
+    int B = g.bd * g.bh * g.bw;
+    for (int64_t k = 0; k < K; k++) {
+        double s = 0.0;
+        for (int l = 0; l < B; l++) {
+            int64_t z, yy, x;
+            int64_t i = g_block_pixel(&g, k, l, &z, &yy, &x);
+            double d = (double)yhat[i] - y[i];
+            s = s + d * d;
+        }
+        r2[k] = s;
+    }
+    (void)n;
+    return 0;
+}
+
+/* Algorithm 1.  y := 1/2, a := 0, mu := mu0; then repeat
+ *   yhat_k <- argmin Eq. 8 (all blocks), y <- Eq. 10, a <- Eq. 11, mu <- mu * mu_fact
+ * while some block has ||yhat_k - S_k y||_2 > eps (tested after the updates,
+ * so at least one iteration runs), for at most max_iter iterations.
+ * Outputs: labels = yhat of the last iteration, *iters, and per iteration t
+ * (0-based, if the arrays are non-NULL): rmax[t] = max_k ||yhat_k - S_k y||,
+ * flips[t] = number of labels that changed vs the previous iteration.
+ * Returns 0 converged, 1 max_iter reached, <0 error. */
+int orc_admm(const int64_t *dims, int conn, const int *block,
+             const int64_t *U, const int64_t *Wl,
+             double mu0, double mu_fact, double eps, int max_iter,
+             uint8_t *labels, int *iters, double *rmax_trace, int64_t *flips_trace,
+             double *y_out, double *a_out, double *mu_out)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    int64_t n = g_n(&g), K = g_nblocks(&g);
+    double *y = malloc(sizeof(double) * (size_t)n);
+    double *a = malloc(sizeof(double) * (size_t)n);
+    double *r2 = malloc(sizeof(double) * (size_t)K);
+    int64_t *C = malloc(sizeof(int64_t) * (size_t)n);
+    uint8_t *prev = malloc((size_t)n);
+    if (!y || !a || !r2 || !C || !prev) { free(y); free(a); free(r2); free(C); free(prev); return -4; }
+    for (int64_t i = 0; i < n; i++) { y[i] = 0.5; a[i] = 0.0; prev[i] = 0; }
+    double mu = mu0;
+    int t = 0, rc = 1;
+    while (t < max_iter) {
+        orc_shifted_caps(dims, conn, block, U, Wl, y, a, mu, NULL, C);
+        orc_block_cuts(dims, conn, block, Wl, C, labels);
+        orc_update(dims, conn, block, Wl, labels, mu, y, a, r2);
+        double m2 = 0.0;
+        for (int64_t k = 0; k < K; k++) if (r2[k] > m2) m2 = r2[k];
+        double rmax = sqrt(m2);
+        if (rmax_trace) rmax_trace[t] = rmax;
+        if (flips_trace) {
+            int64_t f = 0;
+            for (int64_t i = 0; i < n; i++) f += (labels[i] != prev[i]);
+            flips_trace[t] = f;
+        }
+        memcpy(prev, labels, (size_t)n);
+        mu = mu * mu_fact;
+        t++;
+        if (!(rmax > eps)) { rc = 0; break; }
+    }
+    *iters = t;
+    if (y_out) memcpy(y_out, y, sizeof(double) * (size_t)n);
+    if (a_out) memcpy(a_out, a, sizeof(double) * (size_t)n);
+    if (mu_out) *mu_out = mu;
+    free(y); free(a); free(r2); free(C); free(prev);
+    return rc;
+}
+
+/* One ADMM iteration from a given state (the same step orc_admm takes):
+ * solve Eq. 8 with (y, a, mu), then Eq. 10 / Eq. 11 in place.  r2 per block. */
+int orc_admm_step(const int64_t *dims, int conn, const int *block,
+                  const int64_t *U, const int64_t *Wl, double mu,
+                  double *y, double *a, uint8_t *yhat, double *r2)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    int64_t n = g_n(&g);
+    int64_t *C = malloc(sizeof(int64_t) * (size_t)n);
+    if (!C) return -4;
+    orc_shifted_caps(dims, conn, block, U, Wl, y, a, mu, NULL, C);
+    orc_block_cuts(dims, conn, block, Wl, C, yhat);
+    orc_update(dims, conn, block, Wl, yhat, mu, y, a, r2);
+    free(C);
+    return 0;
+}
+
+/* The serial graph cut (sGC) on the whole grid: exact global minimiser of
+ * Eq. 1 (canonical, pointwise minimal).  Returns E_int of it. */
+int64_t orc_global_mincut(const int64_t *dims, int conn, const int *block,
+                          const int64_t *U, const int64_t *Wl, uint8_t *labels)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return INT64_MIN;
+    int64_t n = g_n(&g);
+    if (n > 0x7fffffff / (g.nh + 1)) return INT64_MIN;
+    bk_t b;
+    if (bk_alloc(&b, (int)n, (int)(n * g.nh))) { bk_free(&b); return INT64_MIN; }
+    for (int64_t i = 0; i < n; i++) b.tr[i] = U[i];
+    for (int64_t z = 0; z < g.D; z++)
+        for (int64_t y = 0; y < g.H; y++)
+            for (int64_t x = 0; x < g.W; x++) {
+                int64_t i = (z * g.H + y) * g.W + x, nz, ny, nx;
+                for (int o = 0; o < g.nh; o++) {
+                    int64_t j = g_nbr(&g, z, y, x, o, &nz, &ny, &nx);
+                    if (j < 0) continue;
+                    int64_t w = Wl[(int64_t)o * n + i];
+                    if (w > 0) bk_edge(&b, (int)i, (int)j, w, w);
+                }
+            }
+    bk_run(&b, labels);
+    bk_free(&b);
+    return orc_energy(dims, conn, block, U, Wl, labels);
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -1,0 +1,308 @@
+"""Seeded synthetic DOPE instances.
+
+This module only draws images / volumes and turns them into the potentials of
+Eq. 1 - 2 (unaries as log-posterior ratios, contrast-sensitive Potts weights).
+It holds none of the ADMM arithmetic and imports neither the CUDA library nor
+the oracle, so both sides can be fed from it.
+
+Every instance is a dict:
+    grid   (H, W) or (D, H, W)
+    conn   4 or 8 (2-D), 6 (3-D)
+    block  sub-region shape, same rank as grid
+    lam    lambda of Eq. 1
+    mu0    initial ADMM penalty (100 in 2-D, 500 in 3-D: Section 3 settings)
+    u      float32 [N]  unary  u_i = log p(y_i=0|x_i) - log p(y_i=1|x_i)   (Eq. 2)
+    wq     int32 [conn/2, N]  rne(1024 w_ij) of the edge from pixel i to its
+           forward neighbour along offset k (0 where the neighbour is outside)
+
+Forward offsets (same order everywhere in this project): 2-D (dy, dx):
+4-conn (0,+1), (+1,0); 8-conn adds (+1,+1), (+1,-1).  3-D (dz, dy, dx):
+(0,0,+1), (0,+1,0), (+1,0,0).
+
+The paper's own images, MRI volume and CNN unaries are not available; these
+generators are synthetic stand-ins with the same kinds of structure.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+FWD_OFFSETS = {
+    4: [(0, 0, 1), (0, 1, 0)],
+    8: [(0, 0, 1), (0, 1, 0), (0, 1, 1), (0, 1, -1)],
+    6: [(0, 0, 1), (0, 1, 0), (1, 0, 0)],
+}
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _shifted(vol, dz, dy, dx):
+    """(valid mask, neighbour values) for the forward offset on a (D,H,W[,C]) array."""
+    D, H, W = vol.shape[:3]
+    nb = np.zeros_like(vol)
+    valid = np.zeros((D, H, W), bool)
+    zs = slice(0, D - dz) if dz >= 0 else slice(-dz, D)
+    ys = slice(0, H - dy) if dy >= 0 else slice(-dy, H)
+    xs = slice(0, W - dx) if dx >= 0 else slice(-dx, W)
+    zt = slice(dz, D) if dz >= 0 else slice(0, D + dz)
+    yt = slice(dy, H) if dy >= 0 else slice(0, H + dy)
+    xt = slice(dx, W) if dx >= 0 else slice(0, W + dx)
+    nb[zs, ys, xs] = vol[zt, yt, xt]
+    valid[zs, ys, xs] = True
+    return valid, nb
+
+
+def contrast_weights(vol, conn, sigma=None, fixed_sigma=None, inv_dist=False):
+    """Contrast-sensitive Potts weights w_ij = exp(-|x_i - x_j|^2 / (2 sigma^2)) [/ |p_i - p_j|]
+    for every forward offset.  vol is (D, H, W) or (D, H, W, C).  sigma defaults
+    to the mean feature difference over all neighbour pairs.  Returns float64
+    [conn/2, N] and the sigma used."""
+    offs = FWD_OFFSETS[conn]
+    diffs, valids = [], []
+    for (dz, dy, dx) in offs:
+        valid, nb = _shifted(vol, dz, dy, dx)
+        d = vol - nb
+        d2 = (d * d).sum(axis=-1) if vol.ndim == 4 else d * d
+        diffs.append(d2)
+        valids.append(valid)
+    if fixed_sigma is not None:
+        sig = float(fixed_sigma)
+    elif sigma is None:
+        tot = sum(np.sqrt(d2[v]).sum() for d2, v in zip(diffs, valids))
+        cnt = sum(int(v.sum()) for v in valids)
+        sig = float(tot / max(cnt, 1))
+        sig = max(sig, 1e-6)
+    else:
+        sig = float(sigma)
+    out = np.zeros((len(offs),) + vol.shape[:3], np.float64)
+    for k, ((dz, dy, dx), d2, v) in enumerate(zip(offs, diffs, valids)):
+        w = np.exp(-d2 / (2.0 * sig * sig))
+        if inv_dist:
+            w = w / np.sqrt(dz * dz + dy * dy + dx * dx)
+        out[k] = np.where(v, w, 0.0)
+    return out.reshape(len(offs), -1), sig
+
+
+def quantise_weights(w):
+    """wq = rne(1024 w) as int32 (numpy rint rounds half to even)."""
+    return np.rint(1024.0 * np.asarray(w, np.float64)).astype(np.int32)
+
+
+def _gauss_logpdf(x, m, s):
+    return -0.5 * ((x - m) / s) ** 2 - np.log(s) - 0.5 * np.log(2 * np.pi)
+
+
+# --------------------------------------------------------------------------
+# 64x64 single-channel disk (4-conn Potts, lambda = 2, 16x16 sub-regions)
+# --------------------------------------------------------------------------
+
+def disk64(seed=0, size=64, radius=20.0, lam=2.0, block=(16, 16), sigma=0.1):
+    """Two-region disk on background: intensities N(0.7, 0.1) inside, N(0.3, 0.1)
+    outside (fp32); u = log N(x; 0.3, 0.1) - log N(x; 0.7, 0.1); 4-connected
+    w = exp(-(x_i - x_j)^2 / (2 * 0.1^2))."""
+    rng = _rng(seed)
+    yy, xx = np.mgrid[0:size, 0:size]
+    c = size / 2.0
+    inside = (yy - c) ** 2 + (xx - c) ** 2 <= radius * radius
+    img = np.where(inside, rng.normal(0.7, 0.1, (size, size)),
+                   rng.normal(0.3, 0.1, (size, size))).astype(np.float32)
+    x = img.astype(np.float64)
+    u = (_gauss_logpdf(x, 0.3, 0.1) - _gauss_logpdf(x, 0.7, 0.1)).astype(np.float32)
+    w, _ = contrast_weights(x[None], 4, fixed_sigma=sigma)
+    return {"name": f"disk{size}", "grid": (size, size), "conn": 4, "block": tuple(block),
+            "lam": float(lam), "mu0": 100.0, "u": u.reshape(-1), "wq": quantise_weights(w),
+            "truth": inside.reshape(-1).astype(np.uint8), "image": img}
+
+
+# --------------------------------------------------------------------------
+# 512x512 RGB ellipses, GMM unaries (8-conn contrast Potts, 32x32 sub-regions)
+# --------------------------------------------------------------------------
+
+def _kmeanspp(X, k, rng):
+    cent = [X[rng.integers(len(X))]]
+    for _ in range(1, k):
+        d2 = np.min(((X[:, None, :] - np.array(cent)[None]) ** 2).sum(-1), axis=1)
+        p = d2 / d2.sum() if d2.sum() > 0 else np.full(len(X), 1.0 / len(X))
+        cent.append(X[rng.choice(len(X), p=p)])
+    return np.array(cent)
+
+
+def fit_gmm(X, k, rng, iters=50, reg=1e-4):
+    """Full-covariance EM from a k-means++ start; returns (weights, means, covs)."""
+    X = np.asarray(X, np.float64)
+    n, dim = X.shape
+    mu = _kmeanspp(X, k, rng)
+    lab = np.argmin(((X[:, None, :] - mu[None]) ** 2).sum(-1), axis=1)
+    pi = np.array([max((lab == j).mean(), 1e-3) for j in range(k)])
+    pi /= pi.sum()
+    cov = np.array([np.cov(X[lab == j].T) + reg * np.eye(dim) if (lab == j).sum() > dim
+                    else np.cov(X.T) + reg * np.eye(dim) for j in range(k)])
+    for _ in range(iters):
+        logr = np.stack([np.log(pi[j]) + _mvn_logpdf(X, mu[j], cov[j]) for j in range(k)], 1)
+        m = logr.max(1, keepdims=True)
+        r = np.exp(logr - m)
+        r /= r.sum(1, keepdims=True)
+        nk = r.sum(0) + 1e-12
+        pi = nk / n
+        mu = (r.T @ X) / nk[:, None]
+        for j in range(k):
+            d = X - mu[j]
+            cov[j] = (r[:, j, None] * d).T @ d / nk[j] + reg * np.eye(dim)
+    return pi, mu, cov
+
+
+def _mvn_logpdf(X, m, C):
+    dim = X.shape[1]
+    L = np.linalg.cholesky(C)
+    z = np.linalg.solve(L, (X - m).T)
+    return -0.5 * (z * z).sum(0) - np.log(np.diag(L)).sum() - 0.5 * dim * np.log(2 * np.pi)
+
+
+def gmm_loglik(X, gmm):
+    pi, mu, cov = gmm
+    logs = np.stack([np.log(pi[j]) + _mvn_logpdf(X, mu[j], cov[j]) for j in range(len(pi))], 1)
+    m = logs.max(1, keepdims=True)
+    return (m[:, 0] + np.log(np.exp(logs - m).sum(1)))
+
+
+def ellipses_rgb(seed=0, size=512, lam=4.0, block=(32, 32), conn=8, n_ellipses=12,
+                 noise=0.08, box=24):
+    """12 random ellipses (centres U[0,size)^2, semi-axes U[16,128], angle U[0,pi),
+    colours U[0,1]^3) painted in order over a U[0,1]^3 background, plus N(0, 0.08^2)
+    noise; two 3-component GMMs fit on a 24x24 foreground box (centre of the largest
+    ellipse) and a 24x24 background box (a corner away from the ellipses);
+    u = log p_bg(x) - log p_fg(x); contrast weights with sigma = mean colour
+    difference over neighbour pairs, divided by the pixel distance."""
+    rng = _rng(seed)
+    H = W = size
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    img = np.empty((H, W, 3), np.float64)
+    img[:] = rng.uniform(0, 1, 3)
+    masks, areas, centres = [], [], []
+    scale = size / 512.0
+    for _ in range(n_ellipses):
+        cy, cx = rng.uniform(0, H), rng.uniform(0, W)
+        a, b = rng.uniform(16, 128) * scale, rng.uniform(16, 128) * scale
+        th = rng.uniform(0, np.pi)
+        col = rng.uniform(0, 1, 3)
+        dy, dx = yy - cy, xx - cx
+        xr = dx * np.cos(th) + dy * np.sin(th)
+        yr = -dx * np.sin(th) + dy * np.cos(th)
+        m = (xr / a) ** 2 + (yr / b) ** 2 <= 1.0
+        img[m] = col
+        masks.append(m); areas.append(np.pi * a * b); centres.append((cy, cx))
+    img = img + rng.normal(0, noise, img.shape)
+    img32 = img.astype(np.float32)
+    X = img32.reshape(-1, 3).astype(np.float64)
+    anym = np.zeros((H, W), bool)
+    for m in masks:
+        anym |= m
+    big = int(np.argmax(areas))
+    cy, cx = centres[big]
+    fy = int(np.clip(round(cy) - box // 2, 0, H - box))
+    fx = int(np.clip(round(cx) - box // 2, 0, W - box))
+    corners = [(0, 0), (0, W - box), (H - box, 0), (H - box, W - box)]
+    cover = [anym[y:y + box, x:x + box].sum() for (y, x) in corners]
+    by, bx = corners[int(np.argmin(cover))]
+    fg = img32[fy:fy + box, fx:fx + box].reshape(-1, 3).astype(np.float64)
+    bg = img32[by:by + box, bx:bx + box].reshape(-1, 3).astype(np.float64)
+    g_fg = fit_gmm(fg, 3, rng)
+    g_bg = fit_gmm(bg, 3, rng)
+    u = (gmm_loglik(X, g_bg) - gmm_loglik(X, g_fg))
+    u = np.clip(u, -1.0e5, 1.0e5).astype(np.float32)
+    w, sig = contrast_weights(img32.astype(np.float64)[None], conn, inv_dist=True)
+    return {"name": f"ellipses{size}", "grid": (H, W), "conn": conn, "block": tuple(block),
+            "lam": float(lam), "mu0": 100.0, "u": u, "wq": quantise_weights(w),
+            "sigma": sig, "image": img32}
+
+
+# --------------------------------------------------------------------------
+# 256x256x128 volume, nested ellipsoids (6-conn, 16x16x8 sub-regions)
+# --------------------------------------------------------------------------
+
+def ellipsoids3d(seed=0, shape=(128, 256, 256), lam=3.0, block=(8, 16, 16), noise=0.05):
+    """3 nested random ellipsoids (levels 0.2 background, 0.45, 0.7, 0.9), smooth
+    multiplicative bias 1 + 0.2 * (random 2nd-order polynomial), Rician-like noise
+    sqrt((v + n1)^2 + n2^2) with n ~ N(0, 0.05^2).  Foreground = inside the middle
+    ellipsoid; u = log-ratio of Gaussians fit to the two classes; 6-connected
+    contrast weights, sigma = mean |dx| over neighbour pairs."""
+    rng = _rng(seed)
+    D, H, W = shape
+    z, y, x = np.meshgrid(np.linspace(-1, 1, D), np.linspace(-1, 1, H), np.linspace(-1, 1, W),
+                          indexing="ij")
+    vol = np.full(shape, 0.2)
+    c0 = rng.uniform(-0.15, 0.15, 3)
+    ax0 = rng.uniform(0.6, 0.85, 3)
+    levels = [0.45, 0.7, 0.9]
+    fg = None
+    for lvl, f in zip(levels, [1.0, 0.7, 0.4]):
+        c = c0 + rng.uniform(-0.05, 0.05, 3) * f
+        ax = ax0 * f * rng.uniform(0.9, 1.0, 3)
+        m = ((z - c[0]) / ax[0]) ** 2 + ((y - c[1]) / ax[1]) ** 2 + ((x - c[2]) / ax[2]) ** 2 <= 1
+        vol[m] = lvl
+        if lvl == 0.7:
+            fg = m
+    coef = rng.normal(0, 1, 10)
+    terms = [np.ones_like(z), z, y, x, z * z, y * y, x * x, z * y, z * x, y * x]
+    poly = sum(cf * t for cf, t in zip(coef, terms))
+    poly = poly / max(np.abs(poly).max(), 1e-9)
+    vol = vol * (1.0 + 0.2 * poly)
+    n1 = rng.normal(0, noise, shape)
+    n2 = rng.normal(0, noise, shape)
+    vol = np.sqrt((vol + n1) ** 2 + n2 ** 2).astype(np.float32)
+    v64 = vol.astype(np.float64)
+    m1, s1 = v64[fg].mean(), v64[fg].std() + 1e-6
+    m0, s0 = v64[~fg].mean(), v64[~fg].std() + 1e-6
+    u = (_gauss_logpdf(v64, m0, s0) - _gauss_logpdf(v64, m1, s1)).astype(np.float32)
+    w, sig = contrast_weights(v64, 6)
+    return {"name": "ellipsoids%dx%dx%d" % (W, H, D), "grid": tuple(shape), "conn": 6,
+            "block": tuple(block), "lam": float(lam), "mu0": 500.0, "u": u.reshape(-1),
+            "wq": quantise_weights(w), "sigma": sig, "truth": fg.reshape(-1).astype(np.uint8)}
+
+
+# --------------------------------------------------------------------------
+# Small random instances for tests
+# --------------------------------------------------------------------------
+
+def random_instance(grid, conn, block, lam=1.0, seed=0, u_scale=4.0, w_max=1.0, mu0=None,
+                    smooth=True, w_int_max=None):
+    """A random instance: a smooth random field plus noise for u (so that
+    labels form regions and blocks have boundaries), uniform random weights.
+    If w_int_max is given, weights are integers in [0, w_int_max] (x1024 not
+    applied) -- useful for exact hand checks."""
+    rng = _rng(seed)
+    grid = tuple(int(g) for g in grid)
+    dims = grid if len(grid) == 3 else (1,) + grid
+    n = int(np.prod(dims))
+    if smooth:
+        f = rng.normal(0, 1, dims)
+        for ax in range(3):
+            if dims[ax] > 2:
+                f = (f + np.roll(f, 1, ax) + np.roll(f, -1, ax)) / 3.0
+        f = f / (f.std() + 1e-9)
+        u = u_scale * f + rng.normal(0, u_scale * 0.5, dims)
+    else:
+        u = rng.normal(0, u_scale, dims)
+    vol = np.zeros(dims)
+    offs = FWD_OFFSETS[conn]
+    wq = np.zeros((len(offs), n), np.int32)
+    for k, (dz, dy, dx) in enumerate(offs):
+        valid, _ = _shifted(vol, dz, dy, dx)
+        if w_int_max is not None:
+            w = rng.integers(0, w_int_max + 1, dims)
+            wq[k] = np.where(valid, w, 0).reshape(-1).astype(np.int32)
+        else:
+            w = rng.uniform(0, w_max, dims)
+            wq[k] = np.where(valid, np.rint(1024.0 * w), 0).reshape(-1).astype(np.int32)
+    if mu0 is None:
+        mu0 = 500.0 if len(grid) == 3 else 100.0
+    return {"name": "random", "grid": grid, "conn": conn, "block": tuple(block), "lam": float(lam),
+            "mu0": float(mu0), "u": u.reshape(-1).astype(np.float32), "wq": wq}
+
+
+CONFIGS = {
+    "disk64": disk64,
+    "ellipses512": ellipses_rgb,
+    "ellipsoids256": ellipsoids3d,
+}
