@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: pixels/s of DOPE ADMM to convergence on one GB300 (per rank).
+
+Workload (default "ellipses512"): the 512x512 RGB ellipse image, 8-connected
+contrast-sensitive Potts, 32x32 sub-regions (K = 256), solved for the three
+lambdas 1, 4 and 16; one step = the three solves to convergence
+(Algorithm 1, mu0 = 100, mu_fact = 1.05, eps = 1e-3).  Inputs are synthetic
+(seeded), resident in HBM for `value`; `e2e` goes through the C-ABI with
+pinned host buffers, host<->device copies inside the timed region.  The L2
+is flushed (a 256 MiB write) before every timed step, outside the step's
+events.
+
+--impl reference times the oracle (the plain CPU implementation of the
+method: BK per block + FP64 ADMM, OpenMP over blocks) on the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LAMBDAS = (1.0, 4.0, 16.0)
+METRIC = "pixels/sec to ADMM convergence"
+PROFILES = os.path.join(ROOT, "profiles")
+KERNEL_SRC = os.path.join(ROOT, "paper_1704_03116_gb300", "csrc", "dope_kernels.cuh")
+
+
+def workload(name):
+    from paper_1704_03116_gb300 import inputs
+    if name == "ellipses512":
+        d = inputs.ellipses_rgb(lam=1.0)
+        return [dict(d, lam=lam) for lam in LAMBDAS], {
+            "workload": "ellipses512x512_rgb_8conn_blocks32x32_lambda1,4,16", "grid": [512, 512],
+            "connectivity": 8, "block": [32, 32], "lambdas": list(LAMBDAS), "mu0": 100.0,
+            "mu_fact": 1.05, "eps": 1e-3}
+    if name == "disk64":
+        d = inputs.disk64()
+        return [d], {"workload": "disk64x64_4conn_blocks16x16_lambda2", "grid": [64, 64],
+                     "connectivity": 4, "block": [16, 16], "lambdas": [2.0], "mu0": 100.0,
+                     "mu_fact": 1.05, "eps": 1e-3}
+    if name == "ellipsoids256":
+        d = inputs.ellipsoids3d()
+        return [d], {"workload": "ellipsoids256x256x128_6conn_blocks16x16x8_lambda3",
+                     "grid": [128, 256, 256], "connectivity": 6, "block": [8, 16, 16],
+                     "lambdas": [3.0], "mu0": 500.0, "mu_fact": 1.05, "eps": 1e-3}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def face_geometry(grid, block, conn):
+    """(F, cross pairs per block): face pixels and (face pixel, cross edge)
+    pairs of an interior block (used for the algorithmic byte counts)."""
+    offs = {4: [(0, 0, 1), (0, 1, 0)], 8: [(0, 0, 1), (0, 1, 0), (0, 1, 1), (0, 1, -1)],
+            6: [(0, 0, 1), (0, 1, 0), (1, 0, 0)]}[conn]
+    b = tuple(block) if len(block) == 3 else (1,) + tuple(block)
+    F = X = 0
+    for z in range(b[0]):
+        for y in range(b[1]):
+            for x in range(b[2]):
+                c = 0
+                for (dz, dy, dx) in offs:
+                    for s in (1, -1):
+                        zz, yy, xx = z + s * dz, y + s * dy, x + s * dx
+                        if not (0 <= zz < b[0] and 0 <= yy < b[1] and 0 <= xx < b[2]):
+                            c += 1
+                F += c > 0
+                X += c
+    return F, X
+
+
+def algorithmic_bytes(n, k, F, X, nh):
+    """Algorithmic HBM bytes of one launch of each hot kernel.
+    Block solver, iteration >= 2: U 4 + Wl 4*nh + yhat read 1 + yhat write 1 per
+    pixel, face y and a 16 per face pixel, neighbour face y 8 per cross pair.
+    Block solver, iteration 1 (y = 1/2, a = 0): U, Wl, yhat write only.
+    Face update: per face pixel own yhat 1, a 8, y and a written 16; per cross
+    pair the neighbour's yhat 1 and the edge weight 4."""
+    solve_first = n * (4 + 4 * nh + 1)
+    solve_later = n * (4 + 4 * nh + 2) + k * F * 16 + k * X * 8
+    update = k * F * (1 + 8 + 16) + k * X * (1 + 4)
+    return solve_first, solve_later, update
+
+
+def kernel_traffic():
+    """Per-launch DRAM bytes of the block solver from the committed ncu summary,
+    or None when there is none or the kernel source changed since."""
+    path = os.path.join(PROFILES, "k_block_solve_ellipses512.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    return float(m.group(1)) if h.group(1) == cur else None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(insts, cfg):
+    """The oracle (as it stands) on one full step of the workload: every lambda's
+    Algorithm 1 run, OpenMP over blocks on all host cores."""
+    import oracle
+    qs = [oracle.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"]) for d in insts]
+    t0 = time.perf_counter()
+    res = [oracle.admm(q, d["mu0"]) for q, d in zip(qs, insts)]
+    dt = time.perf_counter() - t0
+    px = sum(q.n for q in qs)
+    gaps = []
+    for q, r in zip(qs, res):
+        _, egc = oracle.global_mincut(q)
+        gaps.append((r["energy"] - egc) / abs(egc))
+    return {"value": px / dt, "unit": "pixels/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one full step ({len(qs)} solves, {px} pixels) in {dt:.2f} s",
+            "oracle_iterations": [r["iterations"] for r in res]}, gaps, res
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    insts, cfg = workload(args.workload)
+    qs = [oracle.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"]) for d in insts]
+    times, px = [], []
+    for s in range(args.warmup + args.steps):
+        j = s % len(qs)           # each step: one of the workload's solves (bounded sample)
+        t0 = time.perf_counter()
+        oracle.admm(qs[j], insts[j]["mu0"])
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            px.append(qs[j].n)
+    val = sum(px) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pixels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": val, "unit": "pixels/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "each step one solve of the workload, cycling over its lambdas"},
+            "e2e": {"value": val, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dope", choices=["dope", "reference"])
+    ap.add_argument("--workload", default="ellipses512")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1704_03116_gb300 import _build
+    if int(os.environ.get("LOCAL_RANK", "0")) == 0:
+        _build.build()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+    from paper_1704_03116_gb300 import dope
+
+    insts, cfg = workload(args.workload)
+    ctxs = []
+    for d in insts:
+        g = dope.Dope(d["grid"], d["conn"], d["block"], d["lam"], mu0=d["mu0"])
+        g.set_unaries(torch.from_numpy(d["u"]).cuda())
+        g.set_weights(torch.from_numpy(d["wq"]).cuda())
+        ctxs.append(g)
+    n_px = sum(g.n for g in ctxs)
+    labels = [torch.empty(g.n, dtype=torch.uint8, device="cuda") for g in ctxs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        for g, lab in zip(ctxs, labels):
+            g.solve(lab)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region -----------------------------------
+    for g in ctxs:
+        g.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps * len(ctxs))]
+    clocks = Clocks(local)
+    launches, iters, energies = 0, [], []
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        for j, (g, lab) in enumerate(zip(ctxs, labels)):
+            a, b = ev[s * len(ctxs) + j]
+            a.record(stream)
+            _, E, it = g.solve(lab)
+            b.record(stream)
+            st = g.stats()
+            launches += st["kernel_launches"]
+            iters.append(it)
+            energies.append(E)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    lat = [a.elapsed_time(b) for a, b in ev]
+    step_ms = [sum(lat[s * len(ctxs):(s + 1) * len(ctxs)]) for s in range(args.steps)]
+    t_local = sum(step_ms) / 1e3
+    t_max = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n_px * args.steps / t_max
+    profs = [g.profile() for g in ctxs]
+    for g in ctxs:
+        g.set_profiling(False)
+
+    # ---- roofline of the dominant kernel --------------------------------
+    hbm, peak_kind = peaks()
+    nh = insts[0]["conn"] // 2
+    F, X = face_geometry(insts[0]["grid"], insts[0]["block"], insts[0]["conn"])
+    n1, k1 = ctxs[0].n, ctxs[0].nblocks
+    sf, sl, up = algorithmic_bytes(n1, k1, F, X, nh)
+    solve_ms = sum(p["ms"][0] for p in profs)
+    solve_n = sum(p["launches"][0] for p in profs)
+    first_n = sum(p["first_iteration_launches"] for p in profs)
+    upd_ms = sum(p["ms"][1] for p in profs)
+    upd_n = sum(p["launches"][1] for p in profs)
+    if solve_ms >= upd_ms:
+        kname, kms, kn = "k_block_solve", solve_ms, solve_n
+        kbytes = first_n * sf + (solve_n - first_n) * sl
+    else:
+        kname, kms, kn = "k_face_update", upd_ms, upd_n
+        kbytes = upd_n * up
+    achieved = kbytes / (kms / 1e3) / 1e9
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
+            "traffic": kernel_traffic() if kname == "k_block_solve" else None,
+            "algorithmic_bytes_per_launch": kbytes / max(kn, 1),
+            "avg_launch_us": 1e3 * kms / max(kn, 1), "launches": kn,
+            "time_share": {"k_block_solve": solve_ms / (solve_ms + upd_ms),
+                           "k_face_update": upd_ms / (solve_ms + upd_ms)},
+            "first_iteration_avg_us": 1e3 * sum(p["first_iteration_ms"] for p in profs) / max(first_n, 1)}
+
+    # ---- end to end through the C-ABI with pinned host buffers ---------
+    hu = [torch.from_numpy(d["u"]).pin_memory() for d in insts]
+    hw = [torch.from_numpy(np.ascontiguousarray(d["wq"])).pin_memory() for d in insts]
+    hl = [torch.empty(g.n, dtype=torch.uint8).pin_memory() for g in ctxs]
+    e2e_ms = []
+    barrier()
+    for s in range(args.steps):
+        flush.fill_((s + 1) & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g, u, w, lab in zip(ctxs, hu, hw, hl):
+            g.set_unaries(u.numpy())
+            g.set_weights(w.numpy())
+            g.solve(lab.numpy())
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    barrier()
+    e2e_t = sum(e2e_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([e2e_t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    h2d = sum(d["u"].nbytes + d["wq"].nbytes for d in insts)
+    d2h = sum(g.n for g in ctxs) + 8 * len(ctxs)
+
+    line = {"metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64", "data": "synthetic",
+            "config": dict(cfg, l2="flushed before every step (256 MiB write)",
+                           parallelism="replicas" if world > 1 else "single"),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "solves": len(lat)},
+            "iterations": sorted(set(iters)), "energies": sorted(set(energies)),
+            "wall_s": wall, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "e2e": {"value": world * n_px * args.steps / e2e_t, "unit": "pixels/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.mean(e2e_ms)}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, gaps, res = cpu_baseline(insts, cfg)
+        line["cpu_baseline"] = cb
+        line["energy_gap_vs_global_mincut"] = gaps
+        line["oracle_match"] = all(abs(E * 1024 - r["energy"]) <= 1e-4 * abs(r["energy"])
+                                   for E, r in zip(energies[-len(insts):], res))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

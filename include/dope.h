@@ -1,0 +1,212 @@
+/*
+ * dope.h -- C-ABI of the GB300 DOPE ADMM hot path.
+ *
+ * DOPE (Dolz, Ben Ayed, Desrosiers, "DOPE: Distributed Optimization for
+ * Pairwise Energies", arXiv 1704.03116) minimises the binary pairwise energy
+ *
+ *     E(y) = sum_i u_i y_i + lambda sum_{edges ij} w_ij |y_i - y_j|       (Eq. 1)
+ *
+ * by splitting the grid into sub-regions (blocks) and running the ADMM of
+ * Algorithm 1: every block solves its own graph-cut sub-problem with unaries
+ * shifted by the consistency variable y and the multipliers a (Eq. 8), then y
+ * (Eq. 10) and a (Eq. 11) are updated, mu grows by mu_fact, until every block
+ * satisfies ||yhat_k - S_k y||_2 <= eps.  This library runs that loop on one
+ * GPU: one CTA per block with the block's residual graph in shared memory
+ * (push-relabel + BFS, canonical minimal cut), and a fused elementwise kernel
+ * for the y / a updates.  Partitions are non-overlapping (Q = I).
+ *
+ * Conventions
+ *  - Grids: 2-D (H, W) or 3-D (D, H, W), row-major, pixel index
+ *    i = (z*H + y)*W + x.  N = number of pixels.  N < 2^31.
+ *  - Connectivity 4 or 8 (2-D), 6 (3-D).  Forward offsets, in this order:
+ *      4-conn (dy,dx): (0,+1) (+1,0);  8-conn adds (+1,+1) (+1,-1);
+ *      6-conn (dz,dy,dx): (0,0,+1) (0,+1,0) (+1,0,0).
+ *  - Weights: int32 wq[conn/2][N]; wq[k][i] is the pairwise weight of the
+ *    edge from pixel i to its forward neighbour along offset k, already in
+ *    fixed point x1024 (wq = rne(1024 w)).  Entries whose neighbour lies
+ *    outside the grid must be 0.  All entries must be >= 0 (submodular, the
+ *    condition in the footnote of Section 1 for |y_i - y_j| terms).
+ *  - Quantised instance: U_i = rne(1024 u_i) (int32, |U_i| < 2^30),
+ *    Wl_ij = rne(lambda * wq_ij) (int32, < 2^24); E_int(y) = sum U_i y_i +
+ *    sum over undirected edges Wl_ij |y_i - y_j| (each edge once, Eq. 3);
+ *    E = E_int / 1024 exactly.
+ *  - Labels: uint8, 1 = foreground (y_i = 1).  Among minimisers of a block
+ *    sub-problem the pointwise-minimal one is returned (unique), so labels
+ *    are deterministic and bit-exact.
+ *  - Memory: `where` = DOPE_HOST (0) for host pointers or DOPE_DEVICE (1) for
+ *    device pointers of the current device.  The caller owns every buffer it
+ *    passes; the library only reads / writes it during the call, ordered on
+ *    `stream` (a cudaStream_t, NULL = legacy default stream).  Calls that
+ *    return results to the host synchronise `stream`.  Device state is owned
+ *    by the context.
+ *  - Every function returns a DOPE_* status; no exception crosses the ABI.
+ *    A context is not thread-safe; use one context per stream.
+ */
+#ifndef DOPE_H
+#define DOPE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DOPE_OK            0
+#define DOPE_EINVAL        1   /* bad shape / connectivity / block / pointer / order of calls */
+#define DOPE_EUNSUPPORTED  2   /* negative weight (non-submodular) on the submodular path */
+#define DOPE_ENOMEM        3   /* device or host allocation failed */
+#define DOPE_EOVERFLOW     4   /* |U_i| >= 2^30 or Wl_ij >= 2^24, non-finite u */
+#define DOPE_ENOTCONV      5   /* max_iter reached before the stop test held; outputs valid */
+#define DOPE_ETIMEOUT      6   /* a block solver hit its pulse bound; outputs not valid */
+#define DOPE_ECUDA         7   /* a CUDA runtime call failed */
+
+#define DOPE_HOST   0
+#define DOPE_DEVICE 1
+
+typedef struct dope_ctx dope_ctx;
+
+/* Algorithm 1 inputs (lambda, eps, mu0, mu_fact) plus solver knobs.
+ * Defaults (dope_default_params): mu0 = 0 -> 100 for 2-D grids and 500 for
+ * 3-D grids (the paper's settings, Section 3), mu_fact = 1.05, eps = 1e-3,
+ * max_iter = 1000, relabel_period = 0 (automatic), threads = 0 (automatic),
+ * max_pulses = 0 (automatic: 64 * block volume + 4096). */
+typedef struct {
+    double mu0;
+    double mu_fact;
+    double eps;
+    int max_iter;
+    int relabel_period;  /* push-relabel pulses between global relabels */
+    int threads;         /* threads per block-solver CTA (multiple of 32) */
+    int max_pulses;      /* bound on push-relabel pulses per block and iteration */
+} dope_params;
+
+/* Statistics of the last dope_solve / dope_iterate call. */
+typedef struct {
+    int iterations;             /* ADMM iterations run (Algorithm 1 loop count) */
+    int converged;              /* 1 if the stop test held */
+    int64_t pulses_total;       /* push-relabel pulses summed over blocks and iterations */
+    int pulses_max;             /* most pulses one block took in one iteration */
+    int64_t free_nodes_total;   /* nodes left for push-relabel after exact folding */
+    double rmax_last;           /* max_k ||yhat_k - S_k y||_2 after the last iteration */
+    int64_t kernel_launches;    /* kernels this library launched during the call */
+} dope_stats;
+
+/* Device time of the hot-path kernels, measured with CUDA events on the
+ * caller's stream while profiling is on (dope_set_profiling).  Only launches
+ * that did work are counted (launches issued past convergence return at
+ * once and are excluded).  Index 0 = block solver (steps a4-a6), index 1 =
+ * face update (steps a2-a3). */
+typedef struct {
+    int64_t launches[2];
+    double ms[2];
+    int64_t first_iteration_launches;   /* block-solver launches that were iteration 1 */
+    double first_iteration_ms;          /* their device time */
+} dope_profile;
+
+/* Fill *p with the defaults above. */
+void dope_default_params(dope_params *p);
+
+/* Create a context for one grid / partition / lambda (Algorithm 1 inputs,
+ * Section 2 "Block partition scheme").
+ *   grid[ndim]        ndim = 2: (H, W); ndim = 3: (D, H, W)
+ *   connectivity      4 or 8 for ndim = 2, 6 for ndim = 3
+ *   block_shape[ndim] sub-region shape in pixels; must divide grid exactly;
+ *                     block volume in [1, 4096]
+ *   lambda            >= 0 (Eq. 1)
+ *   p                 NULL for defaults
+ * Allocates the device state on the current device.  *out receives the
+ * context (NULL on error). */
+int dope_create(const int64_t *grid, int ndim, int connectivity, const int32_t *block_shape,
+                double lambda, const dope_params *p, dope_ctx **out);
+
+/* Unaries u[N] (float32, image order), Eq. 2: u_i = log p(y_i=0|x_i) -
+ * log p(y_i=1|x_i), so u_i < 0 favours foreground.  Quantised on the device
+ * to U_i = rne(1024 u_i).  Returns DOPE_EOVERFLOW if some |U_i| >= 2^30 or
+ * u_i is not finite.  Synchronises `stream`. */
+int dope_set_unaries(dope_ctx *ctx, const float *u, int64_t n, int where, void *stream);
+
+/* Pairwise weights wq[conn/2][N] (int32, image order, x1024), Eq. 1.
+ * Quantised on the device to Wl = rne(lambda * wq).  DOPE_EUNSUPPORTED if
+ * some wq < 0, DOPE_EINVAL if a weight toward a pixel outside the grid is
+ * non-zero, DOPE_EOVERFLOW if some Wl >= 2^24.  Synchronises `stream`. */
+int dope_set_weights(dope_ctx *ctx, const int32_t *wq, int64_t n, int where, void *stream);
+
+/* Algorithm 1 from its initial state (y = 1/2, a = 0, mu = mu0) until every
+ * block has ||yhat_k - S_k y||_2 <= eps (tested after each iteration, so at
+ * least one runs) or max_iter iterations.  Writes labels[N] (image order;
+ * the yhat of the last iteration), *energy_int = E_int(labels) (may be NULL)
+ * and *iterations (may be NULL).  Returns DOPE_OK, or DOPE_ENOTCONV with
+ * valid outputs when max_iter was reached.  Synchronises `stream`. */
+int dope_solve(dope_ctx *ctx, uint8_t *labels, int where, int64_t *energy_int,
+               int *iterations, void *stream);
+
+/* Reset the ADMM state to y = 1/2, a = 0, mu = mu0, t = 0 (Algorithm 1,
+ * Initialization). */
+int dope_reset(dope_ctx *ctx);
+
+/* Run up to n_iter further iterations of Algorithm 1 from the current state,
+ * stopping early when the stop test holds.  *iterations_done = total
+ * iterations since the last reset, *converged = 1 if the stop test held
+ * after the last iteration run.  Synchronises `stream`. */
+int dope_iterate(dope_ctx *ctx, int n_iter, int *iterations_done, int *converged, void *stream);
+
+/* Copy the ADMM state out (host buffers of N entries, image order):
+ * y (Eq. 10), a (Eq. 11, one multiplier per pixel since Q = I), yhat (block
+ * labels of the last iteration; 0 before the first), mu (value the next
+ * iteration will use), t (iterations done).  Any pointer may be NULL. */
+int dope_get_state(dope_ctx *ctx, double *y, double *a, uint8_t *yhat, double *mu, int *t,
+                   void *stream);
+
+/* Load an ADMM state (host buffers, image order; checkpoint / resume and
+ * parity tests).  t = 0 requires y = 1/2 and a = 0 everywhere.  For t >= 1
+ * the state must be one Algorithm 1 can reach with Q = I: every pixel with no
+ * neighbour in another block must have y_i = yhat_i and a_i = 0 exactly
+ * (Eq. 10 / 11 keep them so), else DOPE_EINVAL. */
+int dope_set_state(dope_ctx *ctx, const double *y, const double *a, const uint8_t *yhat,
+                   double mu, int t, void *stream);
+
+/* Step a4 alone (test hook): the Eq. 8 unaries of the next iteration for the
+ * current state, 1024 c_i rounded half-to-even, as int64 C[N] (host, image
+ * order).  Values whose magnitude exceeds 2^62 are clamped to +-2^62. */
+int dope_shifted_caps(dope_ctx *ctx, int64_t *C, void *stream);
+
+/* Step a5 alone (test hook): solve every block's Eq. 8 min-cut for the given
+ * int64 unaries C[N] (host, image order) with the block's n-links Wl, and
+ * write the canonical block labels yhat[N] (host, image order).  Leaves the
+ * ADMM state unchanged. */
+int dope_block_cuts(dope_ctx *ctx, const int64_t *C, uint8_t *yhat, void *stream);
+
+/* E_int of arbitrary labels[N] (image order) on the context's instance,
+ * Eq. 1 in int64 (x1024). */
+int dope_energy(dope_ctx *ctx, const uint8_t *labels, int where, int64_t *energy_int,
+                void *stream);
+
+/* Per-iteration max_k ||yhat_k - S_k y||_2 of the last solve / iterate
+ * calls since the reset (host, up to cap entries); *count = entries written. */
+int dope_trace(dope_ctx *ctx, double *rmax, int cap, int *count);
+
+/* Statistics of the last dope_solve / dope_iterate call. */
+int dope_get_stats(dope_ctx *ctx, dope_stats *st);
+
+/* Turn per-kernel CUDA-event timing on (1) or off (0); turning it on clears
+ * the accumulated profile. */
+int dope_set_profiling(dope_ctx *ctx, int enable);
+
+/* Accumulated per-kernel device times since profiling was turned on. */
+int dope_get_profile(dope_ctx *ctx, dope_profile *out);
+
+/* Number of blocks K and block volume of the context. */
+int dope_get_geometry(dope_ctx *ctx, int64_t *n_pixels, int64_t *n_blocks, int *block_volume,
+                      int *face_size);
+
+/* Free the context and its device memory (NULL is ignored). */
+void dope_destroy(dope_ctx *ctx);
+
+/* Static description of a status code. */
+const char *dope_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOPE_H */

@@ -508,6 +508,13 @@ int orc_shifted_caps(const int64_t *dims, int conn, const int *block,
                 double t = m1024 * v;
                 s = s + t;
                 if (s_out) s_out[i] = s;
+                /* |1024 c_i| is clamped to 2^62 before rounding: n-link
+                 * capacities are below 2^28 per node, so a node whose unary
+                 * is that large takes the same label in every minimiser and
+                 * the clamp changes no minimiser (it only keeps llrint in
+                 * range when mu has grown for many iterations). */
+                if (s > 4611686018427387904.0) s = 4611686018427387904.0;
+                if (s < -4611686018427387904.0) s = -4611686018427387904.0;
                 C_out[i] = llrint(s);
             }
     return 0;

@@ -1,0 +1,716 @@
+// dope.cu -- C-ABI of the GB300 DOPE ADMM hot path (declared in include/dope.h).
+//
+// Algorithm 1 of Dolz, Ben Ayed, Desrosiers (arXiv 1704.03116) on one GPU:
+// per iteration one launch of k_block_solve (all blocks' Eq. 8 min-cuts,
+// "in parallel") followed by one launch of k_face_update (Eq. 10, Eq. 11 and
+// the per-block stop quantity).  Iterations are issued in batches; every
+// kernel checks the device-side stop flag first, so launches past
+// convergence return at once and the host synchronises once per batch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dope.h"
+#include "dope_kernels.cuh"
+
+using namespace dope;
+
+struct dope_ctx {
+    Geo g;
+    int ndim, conn;
+    double lambda;
+    dope_params p;
+    int threads, smem;
+    // device state
+    int32_t* U = nullptr;
+    int32_t* Wl = nullptr;
+    uint8_t* yhat = nullptr;
+    double* yF = nullptr;
+    double* aF = nullptr;
+    double* r2blk = nullptr;
+    int16_t* faceIndex = nullptr;
+    int16_t* faceLocal = nullptr;
+    Ctrl* ctrl = nullptr;
+    size_t ctrl_bytes = 0;
+    // staging (lazily allocated)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    void* stage2 = nullptr;
+    size_t stage2_bytes = 0;
+    // host state
+    int have_u = 0, have_w = 0;
+    int t = 0;          // iterations done since reset
+    double mu = 0.0;    // mu the next iteration uses
+    dope_stats stats{};
+    long long launches = 0;   // kernels launched since the last stats reset
+    // profiling
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev;   // 3 per iteration: before solve, between, after update
+    dope_profile prof{};
+};
+
+namespace {
+
+#define CK(x)                                  \
+    do {                                       \
+        cudaError_t _e = (x);                  \
+        if (_e != cudaSuccess) return DOPE_ECUDA; \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152LL * 32) b = 152LL * 32;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+int ensure_stage(dope_ctx* c, size_t bytes, int which) {
+    void** p = which ? &c->stage2 : &c->stage;
+    size_t* sz = which ? &c->stage2_bytes : &c->stage_bytes;
+    if (*sz >= bytes) return DOPE_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *sz = 0;
+    if (cudaMalloc(p, bytes) != cudaSuccess) return DOPE_ENOMEM;
+    *sz = bytes;
+    return DOPE_OK;
+}
+
+// Read the control header (conv_t, status, stats) after synchronising.
+int read_ctrl(dope_ctx* c, Ctrl* h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(h, c->ctrl, sizeof(Ctrl) - sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return DOPE_OK;
+}
+
+int clear_status(dope_ctx* c, cudaStream_t st) {
+    CK(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl) - sizeof(unsigned long long), st));
+    return DOPE_OK;
+}
+
+template <int CONN>
+void launch_solve(dope_ctx* c, const SolveArgs& a, cudaStream_t st) {
+    k_block_solve<CONN><<<c->g.K, c->threads, c->smem, st>>>(a);
+}
+
+void solve_launch(dope_ctx* c, const SolveArgs& a, cudaStream_t st) {
+    c->launches++;
+    if (c->conn == 4) launch_solve<4>(c, a, st);
+    else if (c->conn == 8) launch_solve<8>(c, a, st);
+    else launch_solve<6>(c, a, st);
+}
+
+void update_launch(dope_ctx* c, const UpdArgs& a, cudaStream_t st) {
+    c->launches++;
+    const int threads = 256;
+    const int blocks = (int)(((long long)c->g.K * 32 + threads - 1) / threads);
+    if (c->conn == 4) k_face_update<4><<<blocks, threads, 0, st>>>(a);
+    else if (c->conn == 8) k_face_update<8><<<blocks, threads, 0, st>>>(a);
+    else k_face_update<6><<<blocks, threads, 0, st>>>(a);
+}
+
+SolveArgs solve_args(dope_ctx* c) {
+    SolveArgs a;
+    a.g = c->g;
+    a.U = c->U;
+    a.Wl = c->Wl;
+    a.yhat = c->yhat;
+    a.yF = c->yF;
+    a.aF = c->aF;
+    a.faceIndex = c->faceIndex;
+    a.Cgiven = nullptr;
+    a.ctrl = c->ctrl;
+    a.mu = c->mu;
+    a.eps = c->p.eps;
+    a.t = c->t + 1;
+    a.first = (c->t == 0);
+    a.check_prev = 0;
+    a.relabel_period = c->p.relabel_period;
+    a.max_pulses = c->p.max_pulses;
+    return a;
+}
+
+UpdArgs update_args(dope_ctx* c) {
+    UpdArgs a;
+    a.g = c->g;
+    a.Wl = c->Wl;
+    a.yhat = c->yhat;
+    a.yF = c->yF;
+    a.aF = c->aF;
+    a.r2blk = c->r2blk;
+    a.faceLocal = c->faceLocal;
+    a.faceIndex = c->faceIndex;
+    a.ctrl = c->ctrl;
+    a.mu = c->mu;
+    a.t = c->t + 1;
+    return a;
+}
+
+// Up to n iterations of Algorithm 1 from the current state.
+int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
+    if (!c->have_u || !c->have_w) return DOPE_EINVAL;
+    const int t0 = c->t;
+    if (n > c->p.max_iter - t0) n = c->p.max_iter - t0;
+    memset(&c->stats, 0, sizeof(c->stats));
+    if (n <= 0) {
+        c->stats.iterations = c->t;
+        return DOPE_OK;
+    }
+    int rc = clear_status(c, st);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(&c->ctrl->r2max[t0 + 1], 0, sizeof(unsigned long long) * (size_t)n, st));
+    if (c->profiling && c->ev.size() < 3 * (size_t)n) {
+        size_t have = c->ev.size();
+        c->ev.resize(3 * (size_t)n);
+        for (size_t i = have; i < c->ev.size(); ++i) CK(cudaEventCreate(&c->ev[i]));
+    }
+    std::vector<double> mus((size_t)n + 1);
+    mus[0] = c->mu;
+    for (int j = 1; j <= n; ++j) mus[j] = mus[j - 1] * c->p.mu_fact;
+    Ctrl h{};
+    int launched = 0, batch = 4;
+    while (launched < n) {
+        const int nb = (n - launched < batch) ? n - launched : batch;
+        for (int j = 0; j < nb; ++j) {
+            const int idx = launched + j;
+            SolveArgs sa = solve_args(c);
+            sa.t = t0 + idx + 1;
+            sa.mu = mus[idx];
+            sa.first = (t0 + idx == 0);
+            sa.check_prev = (idx > 0);
+            if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx], st));
+            solve_launch(c, sa, st);
+            if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx + 1], st));
+            UpdArgs ua = update_args(c);
+            ua.t = t0 + idx + 1;
+            ua.mu = mus[idx];
+            update_launch(c, ua, st);
+            if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx + 2], st));
+        }
+        CK(cudaGetLastError());
+        launched += nb;
+        rc = read_ctrl(c, &h, st);
+        if (rc) return rc;
+        if (h.status) return h.status;
+        if (h.conv_t) break;
+        if (batch < 32) batch *= 2;
+    }
+    int done, converged;
+    if (h.conv_t) {
+        done = h.conv_t - t0;
+        converged = 1;
+    } else {
+        done = launched;
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, &c->ctrl->r2max[t0 + done], sizeof(bits), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double r2;
+        memcpy(&r2, &bits, sizeof(r2));
+        converged = !(std::sqrt(r2) > c->p.eps);
+    }
+    if (c->profiling) {
+        for (int idx = 0; idx < done; ++idx) {
+            float a = 0.f, b = 0.f;
+            CK(cudaEventElapsedTime(&a, c->ev[3 * idx], c->ev[3 * idx + 1]));
+            CK(cudaEventElapsedTime(&b, c->ev[3 * idx + 1], c->ev[3 * idx + 2]));
+            c->prof.launches[0]++;
+            c->prof.ms[0] += a;
+            c->prof.launches[1]++;
+            c->prof.ms[1] += b;
+            if (t0 + idx == 0) {
+                c->prof.first_iteration_launches++;
+                c->prof.first_iteration_ms += a;
+            }
+        }
+    }
+    c->t = t0 + done;
+    c->mu = mus[done];
+    c->stats.iterations = c->t;
+    c->stats.converged = converged;
+    c->stats.pulses_total = (int64_t)h.pulses_total;
+    c->stats.pulses_max = h.pulses_max;
+    c->stats.free_nodes_total = (int64_t)h.free_total;
+    {
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, &c->ctrl->r2max[c->t], sizeof(bits), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double r2;
+        memcpy(&r2, &bits, sizeof(r2));
+        c->stats.rmax_last = std::sqrt(r2);
+    }
+    c->stats.kernel_launches = c->launches;
+    return DOPE_OK;
+}
+
+int energy_of(dope_ctx* c, const uint8_t* lab_bm, int64_t* out, cudaStream_t st) {
+    CK(cudaMemsetAsync(&c->ctrl->energy, 0, sizeof(unsigned long long), st));
+    c->launches++;
+    const int threads = 256;
+    const int blocks = grid_for(c->g.N, threads);
+    if (c->conn == 4) k_energy<4><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, lab_bm, c->ctrl);
+    else if (c->conn == 8) k_energy<8><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, lab_bm, c->ctrl);
+    else k_energy<6><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, lab_bm, c->ctrl);
+    CK(cudaGetLastError());
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, &c->ctrl->energy, sizeof(v), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (out) *out = (int64_t)v;
+    return DOPE_OK;
+}
+
+int reset_state(dope_ctx* c) {
+    c->t = 0;
+    c->mu = c->p.mu0;
+    const int threads = 256;
+    k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads>>>(c->g, c->yF, c->aF);
+    CK(cudaGetLastError());
+    CK(cudaMemset(c->yhat, 0, (size_t)c->g.N));
+    CK(cudaDeviceSynchronize());
+    return DOPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dope_default_params(dope_params* p) {
+    if (!p) return;
+    p->mu0 = 0.0;
+    p->mu_fact = 1.05;
+    p->eps = 1e-3;
+    p->max_iter = 1000;
+    p->relabel_period = 0;
+    p->threads = 0;
+    p->max_pulses = 0;
+}
+
+const char* dope_strerror(int s) {
+    switch (s) {
+        case DOPE_OK: return "ok";
+        case DOPE_EINVAL: return "invalid argument";
+        case DOPE_EUNSUPPORTED: return "unsupported input (negative pairwise weight)";
+        case DOPE_ENOMEM: return "out of memory";
+        case DOPE_EOVERFLOW: return "capacity out of range";
+        case DOPE_ENOTCONV: return "max_iter reached before convergence";
+        case DOPE_ETIMEOUT: return "block solver hit its pulse bound";
+        case DOPE_ECUDA: return "CUDA runtime error";
+        default: return "unknown status";
+    }
+}
+
+void dope_destroy(dope_ctx* c) {
+    if (!c) return;
+    cudaFree(c->U);
+    cudaFree(c->Wl);
+    cudaFree(c->yhat);
+    cudaFree(c->yF);
+    cudaFree(c->aF);
+    cudaFree(c->r2blk);
+    cudaFree(c->faceIndex);
+    cudaFree(c->faceLocal);
+    cudaFree(c->ctrl);
+    cudaFree(c->stage);
+    cudaFree(c->stage2);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    delete c;
+}
+
+int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* block_shape,
+                double lambda, const dope_params* p, dope_ctx** out) {
+    if (!out) return DOPE_EINVAL;
+    *out = nullptr;
+    if (!grid || !block_shape || (ndim != 2 && ndim != 3)) return DOPE_EINVAL;
+    if (ndim == 2 && connectivity != 4 && connectivity != 8) return DOPE_EINVAL;
+    if (ndim == 3 && connectivity != 6) return DOPE_EINVAL;
+    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return DOPE_EINVAL;
+    int64_t dims[3] = {1, 1, 1};
+    int32_t blk[3] = {1, 1, 1};
+    for (int i = 0; i < ndim; ++i) {
+        dims[3 - ndim + i] = grid[i];
+        blk[3 - ndim + i] = block_shape[i];
+    }
+    for (int i = 0; i < 3; ++i) {
+        if (dims[i] <= 0 || blk[i] <= 0 || dims[i] % blk[i]) return DOPE_EINVAL;
+        if (dims[i] > (1LL << 30)) return DOPE_EINVAL;
+    }
+    const long long N = dims[0] * dims[1] * dims[2];
+    const long long B = (long long)blk[0] * blk[1] * blk[2];
+    if (N >= (1LL << 31) || B > 4096) return DOPE_EINVAL;
+    if (p && (p->threads < 0 || p->threads > 512 || p->threads % 32 ||
+              (p->threads > 0 && (long long)p->threads * NPTMAX < B)))
+        return DOPE_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return DOPE_ECUDA;
+    }
+
+    dope_ctx* c = new (std::nothrow) dope_ctx();
+    if (!c) return DOPE_ENOMEM;
+    c->ndim = ndim;
+    c->conn = connectivity;
+    c->lambda = lambda;
+    dope_default_params(&c->p);
+    if (p) c->p = *p;
+    if (!(c->p.mu0 > 0.0)) c->p.mu0 = (ndim == 3) ? 500.0 : 100.0;
+    if (!(c->p.mu_fact > 0.0)) c->p.mu_fact = 1.05;
+    if (!(c->p.eps >= 0.0)) c->p.eps = 1e-3;
+    if (c->p.max_iter <= 0) c->p.max_iter = 1000;
+    if (c->p.relabel_period <= 0) c->p.relabel_period = 16;
+    if (c->p.max_pulses <= 0) c->p.max_pulses = (int)(64 * B + 4096);
+
+    Geo& g = c->g;
+    g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
+    g.bd = blk[0]; g.bh = blk[1]; g.bw = blk[2];
+    g.B = (int)B;
+    g.nbz = g.D / g.bd; g.nby = g.H / g.bh; g.nbx = g.W / g.bw;
+    g.K = g.nbz * g.nby * g.nbx;
+    g.N = N;
+
+    // face slots: pixels with a neighbour outside their block (any direction)
+    static const int OFF[3][4][3] = {
+        {{0, 0, 1}, {0, 1, 0}, {0, 0, 0}, {0, 0, 0}},
+        {{0, 0, 1}, {0, 1, 0}, {0, 1, 1}, {0, 1, -1}},
+        {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}, {0, 0, 0}}};
+    const int ci = connectivity == 4 ? 0 : (connectivity == 8 ? 1 : 2);
+    const int nh = connectivity / 2;
+    std::vector<int16_t> fidx((size_t)B, -1), floc;
+    for (int l = 0; l < (int)B; ++l) {
+        int lx = l % g.bw, ly = (l / g.bw) % g.bh, lz = l / (g.bw * g.bh);
+        bool face = false;
+        for (int o = 0; o < nh && !face; ++o)
+            for (int s = -1; s <= 1; s += 2) {
+                int z = lz + s * OFF[ci][o][0], y = ly + s * OFF[ci][o][1], x = lx + s * OFF[ci][o][2];
+                if (z < 0 || z >= g.bd || y < 0 || y >= g.bh || x < 0 || x >= g.bw) face = true;
+            }
+        if (face) {
+            fidx[(size_t)l] = (int16_t)floc.size();
+            floc.push_back((int16_t)l);
+        }
+    }
+    g.F = (int)floc.size();
+
+    int threads = c->p.threads;
+    if (threads <= 0) {
+        threads = (int)((B + 31) / 32 * 32);
+        if (threads > 512) threads = 512;
+        if (threads < 32) threads = 32;
+    }
+    if (threads % 32 || threads > 512 || (long long)threads * NPTMAX < B) {
+        delete c;
+        return DOPE_EINVAL;
+    }
+    c->threads = threads;
+    c->smem = (int)((connectivity + 3) * 4 * B + B);
+
+    int rc = DOPE_OK;
+    auto A = [&](void** ptr, size_t bytes) {
+        if (rc == DOPE_OK && cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) rc = DOPE_ENOMEM;
+    };
+    A((void**)&c->U, sizeof(int32_t) * (size_t)N);
+    A((void**)&c->Wl, sizeof(int32_t) * (size_t)N * nh);
+    A((void**)&c->yhat, (size_t)N);
+    A((void**)&c->yF, sizeof(double) * (size_t)g.K * g.F);
+    A((void**)&c->aF, sizeof(double) * (size_t)g.K * g.F);
+    A((void**)&c->r2blk, sizeof(double) * (size_t)g.K);
+    A((void**)&c->faceIndex, sizeof(int16_t) * (size_t)B);
+    A((void**)&c->faceLocal, sizeof(int16_t) * (size_t)(g.F ? g.F : 1));
+    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
+    A((void**)&c->ctrl, c->ctrl_bytes);
+    if (rc) { cudaGetLastError(); dope_destroy(c); return rc; }
+    if (cudaMemcpy(c->faceIndex, fidx.data(), sizeof(int16_t) * (size_t)B, cudaMemcpyHostToDevice) ||
+        (g.F && cudaMemcpy(c->faceLocal, floc.data(), sizeof(int16_t) * (size_t)g.F, cudaMemcpyHostToDevice)) ||
+        cudaMemset(c->ctrl, 0, c->ctrl_bytes)) {
+        dope_destroy(c);
+        return DOPE_ECUDA;
+    }
+    cudaError_t e1 = cudaSuccess;
+    if (connectivity == 4) e1 = cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
+    else if (connectivity == 8) e1 = cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
+    else e1 = cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
+    if (e1 != cudaSuccess) { dope_destroy(c); return DOPE_EINVAL; }
+    rc = reset_state(c);
+    if (rc) { dope_destroy(c); return rc; }
+    *out = c;
+    return DOPE_OK;
+}
+
+int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* stream) {
+    if (!c || !u || n != c->g.N || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const float* src = u;
+    if (where == DOPE_HOST) {
+        int rc = ensure_stage(c, sizeof(float) * (size_t)n, 0);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(c->stage, u, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, st));
+        src = (const float*)c->stage;
+    }
+    int rc = clear_status(c, st);
+    if (rc) return rc;
+    const int threads = 256;
+    k_set_unaries<<<grid_for(n, threads), threads, 0, st>>>(c->g, src, c->U, c->ctrl);
+    CK(cudaGetLastError());
+    Ctrl h{};
+    rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    c->have_u = (h.status == 0);
+    return h.status;
+}
+
+int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void* stream) {
+    if (!c || !wq || n != c->g.N || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const int nh = c->conn / 2;
+    const int32_t* src = wq;
+    if (where == DOPE_HOST) {
+        int rc = ensure_stage(c, sizeof(int32_t) * (size_t)n * nh, 0);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(c->stage, wq, sizeof(int32_t) * (size_t)n * nh, cudaMemcpyHostToDevice, st));
+        src = (const int32_t*)c->stage;
+    }
+    int rc = clear_status(c, st);
+    if (rc) return rc;
+    const int threads = 256;
+    const int blocks = grid_for(n, threads);
+    if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
+    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
+    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
+    CK(cudaGetLastError());
+    Ctrl h{};
+    rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    c->have_w = (h.status == 0);
+    return h.status;
+}
+
+int dope_reset(dope_ctx* c) {
+    if (!c) return DOPE_EINVAL;
+    return reset_state(c);
+}
+
+int dope_iterate(dope_ctx* c, int n_iter, int* iterations_done, int* converged, void* stream) {
+    if (!c || n_iter < 0) return DOPE_EINVAL;
+    c->launches = 0;
+    int rc = run_iterations(c, n_iter, S(stream));
+    if (rc) return rc;
+    if (iterations_done) *iterations_done = c->t;
+    if (converged) *converged = c->stats.converged;
+    return DOPE_OK;
+}
+
+int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int* iterations,
+               void* stream) {
+    if (!c || !labels || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    if (!c->have_u || !c->have_w) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    // Algorithm 1 initialisation: y = 1/2, a = 0, mu = mu0 (stream-ordered)
+    c->t = 0;
+    c->mu = c->p.mu0;
+    c->launches = 1;
+    const int threads = 256;
+    k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads, 0, st>>>(c->g, c->yF, c->aF);
+    CK(cudaGetLastError());
+    int rc = run_iterations(c, c->p.max_iter, st);
+    if (rc) return rc;
+    if (energy_int) {
+        rc = energy_of(c, c->yhat, energy_int, st);
+        if (rc) return rc;
+    }
+    uint8_t* dst = labels;
+    if (where == DOPE_HOST) {
+        rc = ensure_stage(c, (size_t)c->g.N, 1);
+        if (rc) return rc;
+        dst = (uint8_t*)c->stage2;
+    }
+    k_unpermute_u8<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, c->yhat, dst);
+    c->launches++;
+    CK(cudaGetLastError());
+    if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    c->stats.kernel_launches = c->launches;
+    if (iterations) *iterations = c->t;
+    return c->stats.converged ? DOPE_OK : DOPE_ENOTCONV;
+}
+
+int dope_get_state(dope_ctx* c, double* y, double* a, uint8_t* yhat, double* mu, int* t, void* stream) {
+    if (!c) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const size_t N = (size_t)c->g.N;
+    int rc = ensure_stage(c, N * 17, 1);
+    if (rc) return rc;
+    double* dy = (double*)c->stage2;
+    double* da = dy + N;
+    uint8_t* dh = (uint8_t*)(da + N);
+    const int threads = 256;
+    k_get_state<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, c->yF, c->aF, c->yhat, c->faceIndex,
+                                                               c->t, dy, da, dh);
+    CK(cudaGetLastError());
+    if (y) CK(cudaMemcpyAsync(y, dy, N * 8, cudaMemcpyDeviceToHost, st));
+    if (a) CK(cudaMemcpyAsync(a, da, N * 8, cudaMemcpyDeviceToHost, st));
+    if (yhat) CK(cudaMemcpyAsync(yhat, dh, N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (mu) *mu = c->mu;
+    if (t) *t = c->t;
+    return DOPE_OK;
+}
+
+int dope_set_state(dope_ctx* c, const double* y, const double* a, const uint8_t* yhat, double mu,
+                   int t, void* stream) {
+    if (!c || !y || !a || !yhat || t < 0 || t > c->p.max_iter || !(mu > 0.0)) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const size_t N = (size_t)c->g.N;
+    int rc = ensure_stage(c, N * 17, 1);
+    if (rc) return rc;
+    double* dy = (double*)c->stage2;
+    double* da = dy + N;
+    uint8_t* dh = (uint8_t*)(da + N);
+    CK(cudaMemcpyAsync(dy, y, N * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(da, a, N * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dh, yhat, N, cudaMemcpyHostToDevice, st));
+    rc = clear_status(c, st);
+    if (rc) return rc;
+    const int threads = 256;
+    k_set_state<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, dy, da, dh, c->faceIndex, t, c->yF,
+                                                               c->aF, c->yhat, c->ctrl);
+    CK(cudaGetLastError());
+    Ctrl h{};
+    rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    if (h.status) {
+        reset_state(c);
+        return h.status;
+    }
+    c->t = t;
+    c->mu = mu;
+    return DOPE_OK;
+}
+
+int dope_shifted_caps(dope_ctx* c, int64_t* C, void* stream) {
+    if (!c || !C || !c->have_u || !c->have_w) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const size_t N = (size_t)c->g.N;
+    int rc = ensure_stage(c, N * 8, 1);
+    if (rc) return rc;
+    long long* d = (long long*)c->stage2;
+    const int threads = 256;
+    const int blocks = grid_for(c->g.N, threads);
+    const int first = c->t == 0;
+    if (c->conn == 4)
+        k_shifted_caps<4><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->yF, c->aF, c->faceIndex, first, c->mu, d);
+    else if (c->conn == 8)
+        k_shifted_caps<8><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->yF, c->aF, c->faceIndex, first, c->mu, d);
+    else
+        k_shifted_caps<6><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->yF, c->aF, c->faceIndex, first, c->mu, d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(C, d, N * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return DOPE_OK;
+}
+
+int dope_block_cuts(dope_ctx* c, const int64_t* C, uint8_t* yhat, void* stream) {
+    if (!c || !C || !yhat || !c->have_w) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const size_t N = (size_t)c->g.N;
+    int rc = ensure_stage(c, N * 17, 1);
+    if (rc) return rc;
+    long long* cimg = (long long*)c->stage2;
+    long long* cbm = cimg + N;
+    uint8_t* lab = (uint8_t*)(cbm + N);
+    // labels land in a scratch slab; the ADMM state is left untouched
+    rc = ensure_stage(c, N, 0);
+    if (rc) return rc;
+    uint8_t* ybm = (uint8_t*)c->stage;
+    CK(cudaMemcpyAsync(cimg, C, N * 8, cudaMemcpyHostToDevice, st));
+    const int threads = 256;
+    k_permute_i64<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, cimg, cbm);
+    rc = clear_status(c, st);
+    if (rc) return rc;
+    SolveArgs a = solve_args(c);
+    a.Cgiven = cbm;
+    a.yhat = ybm;
+    a.check_prev = 0;
+    solve_launch(c, a, st);
+    k_unpermute_u8<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, ybm, lab);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(yhat, lab, N, cudaMemcpyDeviceToHost, st));
+    Ctrl h{};
+    rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    c->stats.pulses_total = (int64_t)h.pulses_total;
+    c->stats.pulses_max = h.pulses_max;
+    c->stats.free_nodes_total = (int64_t)h.free_total;
+    return h.status;
+}
+
+int dope_energy(dope_ctx* c, const uint8_t* labels, int where, int64_t* energy_int, void* stream) {
+    if (!c || !labels || !energy_int || !c->have_u || !c->have_w) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const size_t N = (size_t)c->g.N;
+    int rc = ensure_stage(c, 2 * N, 1);
+    if (rc) return rc;
+    uint8_t* img = (uint8_t*)c->stage2;
+    uint8_t* bm = img + N;
+    const uint8_t* src = labels;
+    if (where == DOPE_HOST) {
+        CK(cudaMemcpyAsync(img, labels, N, cudaMemcpyHostToDevice, st));
+        src = img;
+    }
+    const int threads = 256;
+    k_permute_u8<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, src, bm);
+    CK(cudaGetLastError());
+    return energy_of(c, bm, energy_int, st);
+}
+
+int dope_trace(dope_ctx* c, double* rmax, int cap, int* count) {
+    if (!c || (!rmax && cap > 0)) return DOPE_EINVAL;
+    int n = c->t < cap ? c->t : cap;
+    std::vector<unsigned long long> bits((size_t)n + 1);
+    if (n > 0) {
+        CK(cudaMemcpy(bits.data(), &c->ctrl->r2max[1], sizeof(unsigned long long) * (size_t)n,
+                      cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) {
+            double r2;
+            memcpy(&r2, &bits[(size_t)i], sizeof(r2));
+            rmax[i] = std::sqrt(r2);
+        }
+    }
+    if (count) *count = n;
+    return DOPE_OK;
+}
+
+int dope_get_stats(dope_ctx* c, dope_stats* st) {
+    if (!c || !st) return DOPE_EINVAL;
+    *st = c->stats;
+    return DOPE_OK;
+}
+
+int dope_set_profiling(dope_ctx* c, int enable) {
+    if (!c) return DOPE_EINVAL;
+    c->profiling = enable ? 1 : 0;
+    memset(&c->prof, 0, sizeof(c->prof));
+    return DOPE_OK;
+}
+
+int dope_get_profile(dope_ctx* c, dope_profile* out) {
+    if (!c || !out) return DOPE_EINVAL;
+    *out = c->prof;
+    return DOPE_OK;
+}
+
+int dope_get_geometry(dope_ctx* c, int64_t* n_pixels, int64_t* n_blocks, int* block_volume, int* face_size) {
+    if (!c) return DOPE_EINVAL;
+    if (n_pixels) *n_pixels = c->g.N;
+    if (n_blocks) *n_blocks = c->g.K;
+    if (block_volume) *block_volume = c->g.B;
+    if (face_size) *face_size = c->g.F;
+    return DOPE_OK;
+}
+
+}  // extern "C"

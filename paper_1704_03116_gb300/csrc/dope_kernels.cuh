@@ -1,0 +1,702 @@
+// dope_kernels.cuh -- device code of the DOPE ADMM hot path (sm_103a).
+//
+// Layout in HBM (all "block-major": pixel (z,y,x) of block k = (kz,ky,kx) at
+// local index l = (lz*bh + ly)*bw + lx lives at k*B + l, so one CTA reads one
+// contiguous slab):
+//   U    int32 [N]            quantised unaries, rne(1024 u)
+//   Wl   int32 [conn/2][N]    quantised forward-edge weights, rne(lambda wq)
+//   yhat uint8 [N]            block labels of the last iteration
+//   yF   f64   [K][F]         y of the F face pixels of every block (Eq. 10)
+//   aF   f64   [K][F]         a of the face pixels (Eq. 11)
+// Pixels with no neighbour in another block ("interior") always have
+// y = yhat and a = 0 once an iteration has run (Eq. 10 / 11 with Q = I give
+// y = yhat + a - 0 and a = a + 0 starting from a = 0), so only the face is
+// stored; this is exact, not an approximation.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dope {
+
+constexpr int NPTMAX = 8;          // nodes per thread in the block solver
+constexpr int FREE = 0, FIX0 = 1, FIX1 = 2;
+constexpr int MAX_FOLD_ROUNDS = 64;
+constexpr double CLAMP62 = 4611686018427387904.0;   // 2^62
+
+struct Geo {
+    int D, H, W;            // grid (D = 1 for 2-D)
+    int bd, bh, bw, B;      // block shape and volume
+    int nbz, nby, nbx, K;   // block grid
+    int F;                  // face pixels per block
+    long long N;
+};
+
+struct Ctrl {
+    int conv_t;             // iteration whose stop test held (0 = not yet)
+    int status;             // first DOPE_* error raised by a kernel
+    int pulses_max;
+    int pad;
+    unsigned long long pulses_total;
+    unsigned long long free_total;
+    unsigned long long energy;      // k_energy accumulator (two's complement)
+    unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
+};
+
+struct SolveArgs {
+    Geo g;
+    const int32_t* U;
+    const int32_t* Wl;
+    uint8_t* yhat;
+    const double* yF;
+    const double* aF;
+    const int16_t* faceIndex;       // [B] face slot of local pixel, -1 if interior
+    const long long* Cgiven;        // block-major int64 unaries (test hook) or null
+    Ctrl* ctrl;
+    double mu, eps;
+    int t, first, check_prev;
+    int relabel_period, max_pulses;
+};
+
+struct UpdArgs {
+    Geo g;
+    const int32_t* Wl;
+    const uint8_t* yhat;
+    double* yF;
+    double* aF;
+    double* r2blk;
+    const int16_t* faceLocal;       // [F] local pixel of face slot
+    const int16_t* faceIndex;
+    Ctrl* ctrl;
+    double mu;
+    int t;
+};
+
+// Direction k of connectivity CONN: k < CONN/2 is forward offset k, k >= CONN/2
+// the backward offset k - CONN/2.  Forward offsets (dz,dy,dx):
+// 4: (0,0,1) (0,1,0); 8: + (0,1,1) (0,1,-1); 6: (0,0,1) (0,1,0) (1,0,0).
+template <int CONN>
+__device__ __forceinline__ void dir_off(int k, int& dz, int& dy, int& dx) {
+    constexpr int nh = CONN / 2;
+    const int o = k < nh ? k : k - nh;
+    const int s = k < nh ? 1 : -1;
+    if (CONN == 6) {
+        dz = (o == 2); dy = (o == 1); dx = (o == 0);
+    } else {
+        dz = 0; dy = (o >= 1); dx = (o == 0) ? 1 : (o == 1 ? 0 : (o == 2 ? 1 : -1));
+    }
+    dz *= s; dy *= s; dx *= s;
+}
+
+template <int CONN>
+__device__ __forceinline__ int opp_dir(int k) {
+    constexpr int nh = CONN / 2;
+    return k < nh ? k + nh : k - nh;
+}
+
+__device__ __forceinline__ void set_status(Ctrl* c, int code) {
+    atomicCAS(&c->status, 0, code);
+}
+
+// Cross-block neighbour of local pixel (lz,ly,lx) of block (kz,ky,kx) along
+// direction d.  Returns false if the neighbour is inside the same block or
+// outside the grid; else the neighbour's block kn and local index ln.
+template <int CONN>
+__device__ __forceinline__ bool cross_nbr(const Geo& g, int kz, int ky, int kx, int lz, int ly,
+                                          int lx, int d, int& kn, int& ln) {
+    int dz, dy, dx;
+    dir_off<CONN>(d, dz, dy, dx);
+    int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+    if (nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw) return false;
+    int gz = kz * g.bd + nlz, gy = ky * g.bh + nly, gx = kx * g.bw + nlx;
+    if (gz < 0 || gz >= g.D || gy < 0 || gy >= g.H || gx < 0 || gx >= g.W) return false;
+    int nkz = kz + (nlz < 0 ? -1 : (nlz >= g.bd ? 1 : 0));
+    int nky = ky + (nly < 0 ? -1 : (nly >= g.bh ? 1 : 0));
+    int nkx = kx + (nlx < 0 ? -1 : (nlx >= g.bw ? 1 : 0));
+    nlz -= (nkz - kz) * g.bd; nly -= (nky - ky) * g.bh; nlx -= (nkx - kx) * g.bw;
+    kn = (nkz * g.nby + nky) * g.nbx + nkx;
+    ln = (nlz * g.bh + nly) * g.bw + nlx;
+    return true;
+}
+
+// Eq. 8 unary of pixel v of block k, x1024, rounded half-to-even (step a4):
+//   s = U_i; s += Wl_ij * (y_i - y_j) for cross-block j in direction order;
+//   s += (1024 mu) * ((a_i - y_i) + 1/2)
+// Every double operation is one IEEE round-to-nearest op (explicit
+// intrinsics, so nothing is contracted into an FMA).  At the first iteration
+// y = 1/2 and a = 0 make every shift vanish and s = U_i exactly.
+template <int CONN>
+__device__ __forceinline__ long long shifted_cap(const Geo& g, const int32_t* __restrict__ U,
+                                                 const int32_t* __restrict__ Wl,
+                                                 const uint8_t* __restrict__ yhat,
+                                                 const double* __restrict__ yF,
+                                                 const double* __restrict__ aF,
+                                                 const int16_t* __restrict__ faceIndex, int k,
+                                                 int kz, int ky, int kx, int v, int lz, int ly,
+                                                 int lx, int first, double m1024) {
+    constexpr int nh = CONN / 2;
+    const long long gi = (long long)k * g.B + v;
+    const int Ui = U[gi];
+    if (first) return (long long)Ui;
+    const int f = faceIndex[v];
+    double s = (double)Ui;
+    double yv, av;
+    if (f < 0) {
+        yv = (double)yhat[gi];
+        av = 0.0;
+    } else {
+        yv = yF[(long long)k * g.F + f];
+        av = aF[(long long)k * g.F + f];
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int kn, ln;
+            if (!cross_nbr<CONN>(g, kz, ky, kx, lz, ly, lx, d, kn, ln)) continue;
+            const int fn = faceIndex[ln];
+            const double yj = yF[(long long)kn * g.F + fn];
+            const int w = (d < nh) ? Wl[(long long)d * g.N + gi]
+                                   : Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
+            s = __dadd_rn(s, __dmul_rn((double)w, __dsub_rn(yv, yj)));
+        }
+    }
+    s = __dadd_rn(s, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
+    s = fmin(fmax(s, -CLAMP62), CLAMP62);
+    return __double2ll_rn(s);
+}
+
+// ---------------------------------------------------------------------------
+// Block solver: one CTA per block (steps a4, a5, a6).
+//
+// Shared memory (B = block volume):
+//   res   int32 [CONN][B]   residual capacity of edge v -> v + off(d)
+//   R1    8 B  [B]          int64 unary during folding; then e[B], ein[B]
+//   R2    4 B  [B]          int32 n-link sum during folding; then h0[B], h1[B] (int16)
+//   st    uint8 [B]         FREE / FIX0 / FIX1
+//
+// 1. Capacity build: res = Wl on intra-block edges, C64 = Eq. 8 unary.
+// 2. Exact folding: a free node with C >= sum of its remaining n-links takes
+//    label 0 in the pointwise-minimal minimiser, one with C < -sum takes 1;
+//    it is fixed and its n-links are folded into the neighbours' unaries
+//    (+w if fixed to 0, -w if fixed to 1).  Repeated until nothing changes.
+//    After this every free node has |C| < 2^28, so int32 is exact.
+// 3. Push-relabel on the free nodes (implicit terminals: e > 0 excess,
+//    e < 0 remaining capacity to t), synchronous pulses: push along admissible
+//    edges with heights fixed for the pulse, then relabel with double-buffered
+//    heights; global relabel (BFS from t) every relabel_period pulses.
+// 4. Canonical cut: after the max-preflow, the nodes that reach t in the
+//    residual graph (backward BFS from the nodes with e < 0) form the minimal
+//    sink side, i.e. the pointwise-minimal minimiser; label 1 = sink side.
+// ---------------------------------------------------------------------------
+
+// Backward BFS from t over residual edges into h (1 = has residual to t,
+// HMAX = cannot reach t).  Returns whether any free node with excess can
+// still reach t.
+template <int CONN>
+__device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const int* __restrict__ e,
+                                             int16_t* h, const uint8_t* st, const int* doff,
+                                             const uint8_t* imask, int B, int HMAX, int tid,
+                                             int NT) {
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v < B) h[v] = (st[v] == FREE && e[v] < 0) ? (int16_t)1 : (int16_t)HMAX;
+    }
+    __syncthreads();
+    for (int level = 1; level < HMAX; ++level) {
+        int ch = 0;
+#pragma unroll
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v < B && h[v] == HMAX && st[v] == FREE) {
+#pragma unroll
+                for (int d = 0; d < CONN; ++d) {
+                    if (!((imask[q] >> d) & 1)) continue;
+                    if (res[d * B + v] > 0 && h[v + doff[d]] == level) {
+                        h[v] = (int16_t)(level + 1);
+                        ch = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        if (!__syncthreads_or(ch)) break;
+    }
+    int act = 0;
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v < B && st[v] == FREE && e[v] > 0 && h[v] < HMAX) act = 1;
+    }
+    return __syncthreads_or(act);
+}
+
+template <int CONN>
+__global__ void __launch_bounds__(512) k_block_solve(SolveArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Geo& g = A.g;
+    const int B = g.B;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int k = blockIdx.x;
+    int* res = reinterpret_cast<int*>(smem);
+    long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
+    int* e = reinterpret_cast<int*>(C64);
+    int* ein = e + B;
+    int* capsum = reinterpret_cast<int*>(C64 + B);
+    int16_t* hA = reinterpret_cast<int16_t*>(capsum);
+    int16_t* hB = hA + B;
+    uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
+    __shared__ int s_skip;
+
+    // stop test of the previous iteration (Algorithm 1 loop condition)
+    if (tid == 0) {
+        int skip = 0;
+        if (A.check_prev) {
+            if (*(volatile int*)&A.ctrl->conv_t) {
+                skip = 1;
+            } else {
+                double r2 = __longlong_as_double((long long)A.ctrl->r2max[A.t - 1]);
+                if (!(__dsqrt_rn(r2) > A.eps)) {
+                    skip = 1;
+                    if (blockIdx.x == 0) atomicCAS(&A.ctrl->conv_t, 0, A.t - 1);
+                }
+            }
+        }
+        s_skip = skip;
+    }
+    __syncthreads();
+    if (s_skip) return;
+
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    int doff[CONN];
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        int dz, dy, dx;
+        dir_off<CONN>(d, dz, dy, dx);
+        doff[d] = (dz * g.bh + dy) * g.bw + dx;
+    }
+    constexpr int nh = CONN / 2;
+    const double m1024 = __dmul_rn(1024.0, A.mu);
+    uint8_t imask[NPTMAX];
+    long long creg[NPTMAX];
+
+    // 1. capacity build
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        imask[q] = 0;
+        if (v >= B) continue;
+        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+        const long long gi = (long long)k * B + v;
+        int cs = 0;
+        uint8_t m = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int dz, dy, dx;
+            dir_off<CONN>(d, dz, dy, dx);
+            const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+            int w = 0;
+            if (nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw) {
+                m |= (uint8_t)(1u << d);
+                w = (d < nh) ? A.Wl[(long long)d * g.N + gi]
+                             : A.Wl[(long long)(d - nh) * g.N + gi + doff[d]];
+            }
+            res[d * B + v] = w;
+            cs += w;
+        }
+        imask[q] = m;
+        capsum[v] = cs;
+        st[v] = FREE;
+        long long c;
+        if (A.Cgiven) c = A.Cgiven[gi];
+        else c = shifted_cap<CONN>(g, A.U, A.Wl, A.yhat, A.yF, A.aF, A.faceIndex, k, kz, ky, kx, v,
+                                   lz, ly, lx, A.first, m1024);
+        C64[v] = c;
+    }
+    __syncthreads();
+
+    // 2. exact folding of forced nodes
+    for (int round = 0; round < MAX_FOLD_ROUNDS; ++round) {
+        int changed = 0;
+#pragma unroll
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v < B && st[v] == FREE) {
+                const long long c = C64[v];
+                const long long cs = capsum[v];
+                int ns = (c >= cs) ? FIX0 : (c < -cs ? FIX1 : FREE);
+                if (ns != FREE) {
+                    st[v] = (uint8_t)ns;
+#pragma unroll
+                    for (int d = 0; d < CONN; ++d) res[d * B + v] = 0;
+                    changed = 1;
+                }
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+#pragma unroll
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v < B && st[v] == FREE) {
+                long long c = C64[v];
+                int cs = capsum[v];
+#pragma unroll
+                for (int d = 0; d < CONN; ++d) {
+                    const int r = res[d * B + v];
+                    if (r > 0) {
+                        const int su = st[v + doff[d]];
+                        if (su != FREE) {
+                            c += (su == FIX0) ? r : -r;
+                            cs -= r;
+                            res[d * B + v] = 0;
+                        }
+                    }
+                }
+                C64[v] = c;
+                capsum[v] = cs;
+            }
+        }
+        __syncthreads();
+    }
+
+    // registers <- unaries, then R1 becomes e / ein and R2 the heights
+    int nfree = 0;
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        creg[q] = 0;
+        if (v < B && st[v] == FREE) { creg[q] = C64[v]; nfree++; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v < B) { e[v] = (int)creg[q]; ein[v] = 0; }
+    }
+    const int HMAX = B + 1;
+    int pulses = 0;
+    int16_t* hc = hA;
+    int16_t* hn = hB;
+    if (__syncthreads_or(nfree)) {
+        // 3. push-relabel (phase 1: maximum preflow)
+        int active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT);
+        const int period = A.relabel_period;
+        while (active) {
+            if (pulses >= A.max_pulses) {
+                if (tid == 0) set_status(A.ctrl, 6 /* DOPE_ETIMEOUT */);
+                break;
+            }
+            // push: heights hc fixed for the whole phase
+#pragma unroll
+            for (int q = 0; q < NPTMAX; ++q) {
+                int v = tid + q * NT;
+                if (v < B && st[v] == FREE) {
+                    int ev = e[v];
+                    const int hv = hc[v];
+                    if (ev > 0 && hv < HMAX) {
+#pragma unroll
+                        for (int d = 0; d < CONN; ++d) {
+                            if (ev == 0) break;
+                            const int r = res[d * B + v];
+                            if (r > 0) {
+                                const int u = v + doff[d];
+                                if (hc[u] == hv - 1) {
+                                    const int dl = min(ev, r);
+                                    res[d * B + v] = r - dl;
+                                    res[opp_dir<CONN>(d) * B + u] += dl;
+                                    atomicAdd(&ein[u], dl);
+                                    ev -= dl;
+                                }
+                            }
+                        }
+                        e[v] = ev;
+                    }
+                }
+            }
+            __syncthreads();
+            // merge incoming flow, relabel into hn
+            int act = 0;
+#pragma unroll
+            for (int q = 0; q < NPTMAX; ++q) {
+                int v = tid + q * NT;
+                if (v >= B) continue;
+                int hv = hc[v];
+                if (st[v] == FREE) {
+                    const int ev = e[v] + ein[v];
+                    ein[v] = 0;
+                    e[v] = ev;
+                    if (ev > 0 && hv < HMAX) {
+                        int mn = HMAX;
+                        bool adm = false;
+#pragma unroll
+                        for (int d = 0; d < CONN; ++d) {
+                            if (res[d * B + v] > 0) {
+                                const int hu = hc[v + doff[d]];
+                                adm |= (hu == hv - 1);
+                                mn = min(mn, hu);
+                            }
+                        }
+                        if (!adm) hv = min(mn + 1, HMAX);
+                        if (hv < HMAX) act = 1;
+                    }
+                }
+                hn[v] = (int16_t)hv;
+            }
+            active = __syncthreads_or(act);
+            int16_t* tmp = hc; hc = hn; hn = tmp;
+            ++pulses;
+            if (active && period > 0 && (pulses % period) == 0)
+                active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT);
+        }
+        // 4. canonical cut
+        bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT);
+    }
+
+    // 6. labels
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v >= B) continue;
+        uint8_t lab;
+        if (st[v] == FIX0) lab = 0;
+        else if (st[v] == FIX1) lab = 1;
+        else lab = (hc[v] < HMAX) ? 1 : 0;
+        A.yhat[(long long)k * B + v] = lab;
+    }
+    int nf = 0;
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v < B && st[v] == FREE) nf++;
+    }
+    // statistics
+    for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    if ((tid & 31) == 0 && nf) atomicAdd(&A.ctrl->free_total, (unsigned long long)nf);
+    if (tid == 0 && pulses) {
+        atomicAdd(&A.ctrl->pulses_total, (unsigned long long)pulses);
+        atomicMax(&A.ctrl->pulses_max, pulses);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Steps a2 + a3: Eq. 10 / Eq. 11 on the face pixels and the per-block stop
+// quantity r2_k = sum_{i in block k} (yhat_i - y_i)^2 (interior pixels add
+// exactly 0).  One warp per block; face slots strided over the lanes.
+//   G_i = sum_{j in X(i)} Wl_ij (yhat_i - yhat_j)        (exact, integer)
+//   y_i = (yhat_i + a_i) - (G_i / 1024) / mu               (Eq. 10)
+//   a_i = a_i + (yhat_i - y_i)                             (Eq. 11)
+// ---------------------------------------------------------------------------
+template <int CONN>
+__global__ void __launch_bounds__(256) k_face_update(UpdArgs A) {
+    if (*(volatile int*)&A.ctrl->conv_t) return;
+    const Geo& g = A.g;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= g.K) return;
+    constexpr int nh = CONN / 2;
+    const int k = warp;
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    double r2 = 0.0;
+    for (int f = lane; f < g.F; f += 32) {
+        const int v = A.faceLocal[f];
+        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+        const long long gi = (long long)k * g.B + v;
+        const int yh = A.yhat[gi];
+        int G = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int kn, ln;
+            if (!cross_nbr<CONN>(g, kz, ky, kx, lz, ly, lx, d, kn, ln)) continue;
+            const long long gj = (long long)kn * g.B + ln;
+            const int w = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
+            G += w * (yh - (int)A.yhat[gj]);
+        }
+        const long long s = (long long)k * g.F + f;
+        const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
+        const double aa = A.aF[s];
+        const double yn = __dsub_rn(__dadd_rn((double)yh, aa), __ddiv_rn(gq, A.mu));
+        const double an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
+        A.yF[s] = yn;
+        A.aF[s] = an;
+        const double dd = __dsub_rn((double)yh, yn);
+        r2 = __dadd_rn(r2, __dmul_rn(dd, dd));
+    }
+    for (int o = 16; o > 0; o >>= 1) r2 = __dadd_rn(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    if (lane == 0) {
+        A.r2blk[k] = r2;
+        atomicMax(&A.ctrl->r2max[A.t], (unsigned long long)__double_as_longlong(r2));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up, finish and test-hook kernels (image order <-> block-major)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long bm_index(const Geo& g, long long i) {
+    const int x = (int)(i % g.W);
+    const long long r = i / g.W;
+    const int y = (int)(r % g.H);
+    const int z = (int)(r / g.H);
+    const int k = ((z / g.bd) * g.nby + (y / g.bh)) * g.nbx + (x / g.bw);
+    const int l = ((z % g.bd) * g.bh + (y % g.bh)) * g.bw + (x % g.bw);
+    return (long long)k * g.B + l;
+}
+
+// U = rne(1024 u); |U| < 2^30 and u finite, else DOPE_EOVERFLOW.
+__global__ void k_set_unaries(Geo g, const float* __restrict__ u, int32_t* __restrict__ U, Ctrl* c) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = __dmul_rn(1024.0, (double)u[i]);
+        int q = 0;
+        if (!(fabs(v) < 1073741823.5)) set_status(c, 4);
+        else q = (int)__double2ll_rn(v);
+        U[bm_index(g, i)] = q;
+    }
+}
+
+// Wl = rne(lambda wq); wq >= 0 (else DOPE_EUNSUPPORTED), zero toward the
+// outside of the grid (else DOPE_EINVAL), Wl < 2^24 (else DOPE_EOVERFLOW).
+template <int CONN>
+__global__ void k_set_weights(Geo g, const int32_t* __restrict__ wq, int32_t* __restrict__ Wl,
+                              double lambda, Ctrl* c) {
+    constexpr int nh = CONN / 2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.W);
+        const long long r = i / g.W;
+        const int y = (int)(r % g.H);
+        const int z = (int)(r / g.H);
+        const long long b = bm_index(g, i);
+#pragma unroll
+        for (int d = 0; d < nh; ++d) {
+            int dz, dy, dx;
+            dir_off<CONN>(d, dz, dy, dx);
+            const int w = wq[(long long)d * g.N + i];
+            int q = 0;
+            const bool inside = (z + dz < g.D) && (y + dy < g.H) && (x + dx >= 0) && (x + dx < g.W);
+            if (w < 0) set_status(c, 2);
+            else if (!inside && w != 0) set_status(c, 1);
+            else {
+                const double v = __dmul_rn(lambda, (double)w);
+                if (!(v < 16777215.5)) set_status(c, 4);
+                else q = (int)__double2ll_rn(v);
+            }
+            Wl[(long long)d * g.N + b] = q;
+        }
+    }
+}
+
+__global__ void k_init_state(Geo g, double* yF, double* aF) {
+    const long long n = (long long)g.K * g.F;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        yF[i] = 0.5;
+        aF[i] = 0.0;
+    }
+}
+
+// labels (image order) <- yhat (block-major)
+__global__ void k_unpermute_u8(Geo g, const uint8_t* __restrict__ src, uint8_t* __restrict__ dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[bm_index(g, i)];
+}
+
+__global__ void k_permute_u8(Geo g, const uint8_t* __restrict__ src, uint8_t* __restrict__ dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[bm_index(g, i)] = src[i];
+}
+
+__global__ void k_permute_i64(Geo g, const long long* __restrict__ src, long long* __restrict__ dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[bm_index(g, i)] = src[i];
+}
+
+// E_int of block-major labels (Eq. 1, each undirected edge once), int64.
+template <int CONN>
+__global__ void k_energy(Geo g, const int32_t* __restrict__ U, const int32_t* __restrict__ Wl,
+                         const uint8_t* __restrict__ lab, Ctrl* c) {
+    constexpr int nh = CONN / 2;
+    long long acc = 0;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < g.N;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(gi / g.B), v = (int)(gi % g.B);
+        const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+        const int yi = lab[gi];
+        acc += (long long)U[gi] * yi;
+#pragma unroll
+        for (int d = 0; d < nh; ++d) {
+            int dz, dy, dx;
+            dir_off<CONN>(d, dz, dy, dx);
+            const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+            long long gj;
+            if (nlz < g.bd && nly < g.bh && nlx >= 0 && nlx < g.bw) {
+                gj = gi + (dz * g.bh + dy) * g.bw + dx;
+            } else {
+                int kn, ln;
+                if (!cross_nbr<CONN>(g, kz, ky, kx, lz, ly, lx, d, kn, ln)) continue;
+                gj = (long long)kn * g.B + ln;
+            }
+            if (yi != lab[gj]) acc += Wl[(long long)d * g.N + gi];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&c->energy, (unsigned long long)acc);
+}
+
+// Dense state (image order) from the face state.
+__global__ void k_get_state(Geo g, const double* yF, const double* aF, const uint8_t* yhat,
+                            const int16_t* faceIndex, int t, double* y, double* a, uint8_t* yh) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = bm_index(g, i);
+        const int k = (int)(b / g.B), v = (int)(b % g.B);
+        const int f = faceIndex[v];
+        const uint8_t lab = yhat[b];
+        double yv, av;
+        if (f >= 0) { yv = yF[(long long)k * g.F + f]; av = aF[(long long)k * g.F + f]; }
+        else { yv = t == 0 ? 0.5 : (double)lab; av = 0.0; }
+        if (y) y[i] = yv;
+        if (a) a[i] = av;
+        if (yh) yh[i] = t == 0 ? 0 : lab;
+    }
+}
+
+// Face state from a dense state; checks the interior invariant.
+__global__ void k_set_state(Geo g, const double* y, const double* a, const uint8_t* yh,
+                            const int16_t* faceIndex, int t, double* yF, double* aF,
+                            uint8_t* yhat, Ctrl* c) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = bm_index(g, i);
+        const int k = (int)(b / g.B), v = (int)(b % g.B);
+        const int f = faceIndex[v];
+        const uint8_t lab = yh[i];
+        if (lab > 1) set_status(c, 1);
+        yhat[b] = lab;
+        if (t == 0) {
+            if (y[i] != 0.5 || a[i] != 0.0) set_status(c, 1);
+        } else if (f < 0) {
+            if (y[i] != (double)lab || a[i] != 0.0) set_status(c, 1);
+        }
+        if (f >= 0) { yF[(long long)k * g.F + f] = y[i]; aF[(long long)k * g.F + f] = a[i]; }
+    }
+}
+
+// Step a4 alone: Eq. 8 unaries of every pixel (image order) for the state.
+template <int CONN>
+__global__ void k_shifted_caps(Geo g, const int32_t* U, const int32_t* Wl, const uint8_t* yhat,
+                               const double* yF, const double* aF, const int16_t* faceIndex,
+                               int first, double mu, long long* out) {
+    const double m1024 = __dmul_rn(1024.0, mu);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = bm_index(g, i);
+        const int k = (int)(b / g.B), v = (int)(b % g.B);
+        const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+        out[i] = shifted_cap<CONN>(g, U, Wl, yhat, yF, aF, faceIndex, k, kz, ky, kx, v, lz, ly, lx,
+                                   first, m1024);
+    }
+}
+
+}  // namespace dope

@@ -1,0 +1,366 @@
+"""Thin Python binding of the DOPE C-ABI (include/dope.h).
+
+Argument marshalling only: every step of the ADMM path runs in libdope.so's
+CUDA kernels.  Each ``dope_*`` function here has the C function's name and
+meaning; arrays may be torch CUDA tensors (passed as device pointers, on the
+current torch stream unless ``stream`` is given), or numpy arrays / CPU
+tensors (passed as host pointers).  There is no CPU fallback: if the library
+is missing or fails to load, importing this module raises ImportError.
+
+DOPE: Dolz, Ben Ayed, Desrosiers, "DOPE: Distributed Optimization for
+Pairwise Energies" (arXiv 1704.03116), Algorithm 1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdope.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "dope.h")
+
+DOPE_OK, DOPE_EINVAL, DOPE_EUNSUPPORTED, DOPE_ENOMEM = 0, 1, 2, 3
+DOPE_EOVERFLOW, DOPE_ENOTCONV, DOPE_ETIMEOUT, DOPE_ECUDA = 4, 5, 6, 7
+DOPE_HOST, DOPE_DEVICE = 0, 1
+
+
+class DopeError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {status} ({_lib.dope_strerror(status).decode()})")
+
+
+class dope_params(ctypes.Structure):
+    _fields_ = [("mu0", ctypes.c_double), ("mu_fact", ctypes.c_double), ("eps", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("relabel_period", ctypes.c_int),
+                ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int)]
+
+
+class dope_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("pulses_total", ctypes.c_int64), ("pulses_max", ctypes.c_int),
+                ("free_nodes_total", ctypes.c_int64), ("rmax_last", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+class dope_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 2), ("ms", ctypes.c_double * 2),
+                ("first_iteration_launches", ctypes.c_int64), ("first_iteration_ms", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                          "(nvcc, sm_103a). There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "dope_default_params": (None, [P(dope_params)]),
+        "dope_create": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params), P(vp)]),
+        "dope_set_unaries": (i32, [vp, vp, i64, i32, vp]),
+        "dope_set_weights": (i32, [vp, vp, i64, i32, vp]),
+        "dope_solve": (i32, [vp, vp, i32, P(ctypes.c_int64), P(ctypes.c_int), vp]),
+        "dope_reset": (i32, [vp]),
+        "dope_iterate": (i32, [vp, i32, P(ctypes.c_int), P(ctypes.c_int), vp]),
+        "dope_get_state": (i32, [vp, vp, vp, vp, P(ctypes.c_double), P(ctypes.c_int), vp]),
+        "dope_set_state": (i32, [vp, vp, vp, vp, dbl, i32, vp]),
+        "dope_shifted_caps": (i32, [vp, vp, vp]),
+        "dope_block_cuts": (i32, [vp, vp, vp, vp]),
+        "dope_energy": (i32, [vp, vp, i32, P(ctypes.c_int64), vp]),
+        "dope_trace": (i32, [vp, vp, i32, P(ctypes.c_int)]),
+        "dope_get_stats": (i32, [vp, P(dope_stats)]),
+        "dope_get_geometry": (i32, [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int), P(ctypes.c_int)]),
+        "dope_set_profiling": (i32, [vp, i32]),
+        "dope_get_profile": (i32, [vp, P(dope_profile)]),
+        "dope_destroy": (None, [vp]),
+        "dope_strerror": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+try:
+    _lib = _load()
+except OSError as e:  # pragma: no cover - a broken build must fail loudly
+    raise ImportError(f"cannot load {LIB_PATH}: {e}") from e
+
+
+def declared_symbols(header=HEADER):
+    """Function names declared in include/dope.h."""
+    txt = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dope_[a-z_0-9]+)\s*\(", txt, re.M)))
+
+
+def _check(rc, where):
+    if rc not in (DOPE_OK,):
+        raise DopeError(rc, where)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _ptr(x, dtype):
+    """(pointer, where, keepalive) of a torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.dtype != dtype[1] or not x.is_contiguous():
+                raise TypeError(f"expected contiguous {dtype[1]} tensor")
+            return ctypes.c_void_p(x.data_ptr()), (DOPE_DEVICE if x.is_cuda else DOPE_HOST), x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype[0])
+    return ctypes.c_void_p(a.ctypes.data), DOPE_HOST, a
+
+
+def _t(np_dtype):
+    import torch
+    return (np_dtype, {np.float32: torch.float32, np.int32: torch.int32, np.uint8: torch.uint8,
+                       np.int64: torch.int64, np.float64: torch.float64}[np_dtype])
+
+
+# --------------------------------------------------------------------------
+# C-ABI functions (same names)
+# --------------------------------------------------------------------------
+
+def dope_default_params():
+    p = dope_params()
+    _lib.dope_default_params(ctypes.byref(p))
+    return p
+
+
+def dope_create(grid, connectivity, block_shape, lam, params=None):
+    grid = [int(g) for g in grid]
+    block = [int(b) for b in block_shape]
+    if len(grid) != len(block):
+        raise ValueError("grid and block_shape must have the same rank")
+    g = (ctypes.c_int64 * len(grid))(*grid)
+    b = (ctypes.c_int32 * len(block))(*block)
+    ctx = ctypes.c_void_p()
+    rc = _lib.dope_create(g, len(grid), int(connectivity), b, float(lam),
+                          ctypes.byref(params) if params is not None else None, ctypes.byref(ctx))
+    _check(rc, "dope_create")
+    return ctx
+
+
+def dope_set_unaries(ctx, u, stream=None):
+    p, where, keep = _ptr(u, _t(np.float32))
+    _check(_lib.dope_set_unaries(ctx, p, int(np.prod(keep.shape)), where, _stream(stream)), "dope_set_unaries")
+
+
+def dope_set_weights(ctx, wq, stream=None):
+    p, where, keep = _ptr(wq, _t(np.int32))
+    n = int(np.prod(keep.shape)) // max(1, int(keep.shape[0])) if len(keep.shape) == 2 else None
+    if n is None:
+        raise ValueError("wq must be [conn/2, N]")
+    _check(_lib.dope_set_weights(ctx, p, n, where, _stream(stream)), "dope_set_weights")
+
+
+def dope_solve(ctx, labels, stream=None, allow_notconv=False):
+    """Runs Algorithm 1; writes labels; returns (E_int, iterations, status)."""
+    p, where, keep = _ptr(labels, _t(np.uint8))
+    e = ctypes.c_int64(0)
+    it = ctypes.c_int(0)
+    rc = _lib.dope_solve(ctx, p, where, ctypes.byref(e), ctypes.byref(it), _stream(stream))
+    if rc == DOPE_ENOTCONV and allow_notconv:
+        return e.value, it.value, rc
+    _check(rc, "dope_solve")
+    if where == DOPE_HOST and keep is not labels and isinstance(labels, np.ndarray):
+        labels[...] = keep.reshape(labels.shape)
+    return e.value, it.value, rc
+
+
+def dope_reset(ctx):
+    _check(_lib.dope_reset(ctx), "dope_reset")
+
+
+def dope_iterate(ctx, n_iter, stream=None):
+    done = ctypes.c_int(0)
+    conv = ctypes.c_int(0)
+    _check(_lib.dope_iterate(ctx, int(n_iter), ctypes.byref(done), ctypes.byref(conv), _stream(stream)),
+           "dope_iterate")
+    return done.value, bool(conv.value)
+
+
+def _geom(ctx):
+    n, k = ctypes.c_int64(0), ctypes.c_int64(0)
+    b, f = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.dope_get_geometry(ctx, ctypes.byref(n), ctypes.byref(k), ctypes.byref(b), ctypes.byref(f)),
+           "dope_get_geometry")
+    return n.value, k.value, b.value, f.value
+
+
+def dope_get_geometry(ctx):
+    return _geom(ctx)
+
+
+def dope_get_state(ctx, stream=None):
+    n = _geom(ctx)[0]
+    y = np.empty(n, np.float64)
+    a = np.empty(n, np.float64)
+    yh = np.empty(n, np.uint8)
+    mu = ctypes.c_double(0)
+    t = ctypes.c_int(0)
+    _check(_lib.dope_get_state(ctx, y.ctypes.data, a.ctypes.data, yh.ctypes.data, ctypes.byref(mu),
+                               ctypes.byref(t), _stream(stream)), "dope_get_state")
+    return {"y": y, "a": a, "yhat": yh, "mu": mu.value, "t": t.value}
+
+
+def dope_set_state(ctx, y, a, yhat, mu, t, stream=None):
+    y = np.ascontiguousarray(y, np.float64)
+    a = np.ascontiguousarray(a, np.float64)
+    yh = np.ascontiguousarray(yhat, np.uint8)
+    _check(_lib.dope_set_state(ctx, y.ctypes.data, a.ctypes.data, yh.ctypes.data, float(mu), int(t),
+                               _stream(stream)), "dope_set_state")
+
+
+def dope_shifted_caps(ctx, stream=None):
+    n = _geom(ctx)[0]
+    C = np.empty(n, np.int64)
+    _check(_lib.dope_shifted_caps(ctx, C.ctypes.data, _stream(stream)), "dope_shifted_caps")
+    return C
+
+
+def dope_block_cuts(ctx, C, stream=None):
+    C = np.ascontiguousarray(C, np.int64)
+    yh = np.empty(C.shape[0], np.uint8)
+    _check(_lib.dope_block_cuts(ctx, C.ctypes.data, yh.ctypes.data, _stream(stream)), "dope_block_cuts")
+    return yh
+
+
+def dope_energy(ctx, labels, stream=None):
+    p, where, keep = _ptr(labels, _t(np.uint8))
+    e = ctypes.c_int64(0)
+    _check(_lib.dope_energy(ctx, p, where, ctypes.byref(e), _stream(stream)), "dope_energy")
+    return e.value
+
+
+def dope_trace(ctx, cap=4096):
+    r = np.zeros(cap, np.float64)
+    cnt = ctypes.c_int(0)
+    _check(_lib.dope_trace(ctx, r.ctypes.data, cap, ctypes.byref(cnt)), "dope_trace")
+    return r[:cnt.value].copy()
+
+
+def dope_get_stats(ctx):
+    s = dope_stats()
+    _check(_lib.dope_get_stats(ctx, ctypes.byref(s)), "dope_get_stats")
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def dope_set_profiling(ctx, enable):
+    _check(_lib.dope_set_profiling(ctx, int(bool(enable))), "dope_set_profiling")
+
+
+def dope_get_profile(ctx):
+    p = dope_profile()
+    _check(_lib.dope_get_profile(ctx, ctypes.byref(p)), "dope_get_profile")
+    return {"launches": list(p.launches), "ms": list(p.ms),
+            "first_iteration_launches": p.first_iteration_launches,
+            "first_iteration_ms": p.first_iteration_ms}
+
+
+def dope_destroy(ctx):
+    _lib.dope_destroy(ctx)
+
+
+def dope_strerror(status):
+    return _lib.dope_strerror(int(status)).decode()
+
+
+# --------------------------------------------------------------------------
+# Convenience object over the same calls
+# --------------------------------------------------------------------------
+
+class Dope:
+    """One DOPE context: grid, connectivity, block shape, lambda (Algorithm 1 inputs)."""
+
+    def __init__(self, grid, connectivity, block_shape, lam, mu0=None, mu_fact=None, eps=None,
+                 max_iter=None, relabel_period=None, threads=None, max_pulses=None):
+        p = dope_default_params()
+        for k, v in dict(mu0=mu0, mu_fact=mu_fact, eps=eps, max_iter=max_iter,
+                         relabel_period=relabel_period, threads=threads, max_pulses=max_pulses).items():
+            if v is not None:
+                setattr(p, k, v)
+        self.grid = tuple(int(g) for g in grid)
+        self.ctx = dope_create(grid, connectivity, block_shape, lam, p)
+        self.n, self.nblocks, self.block_volume, self.face_size = _geom(self.ctx)
+
+    @classmethod
+    def from_instance(cls, inst, **kw):
+        d = cls(inst["grid"], inst["conn"], inst["block"], inst["lam"], mu0=inst.get("mu0"), **kw)
+        d.set_unaries(inst["u"])
+        d.set_weights(inst["wq"])
+        return d
+
+    def set_unaries(self, u, stream=None):
+        dope_set_unaries(self.ctx, u, stream)
+
+    def set_weights(self, wq, stream=None):
+        dope_set_weights(self.ctx, wq, stream)
+
+    def solve(self, labels=None, stream=None, allow_notconv=False):
+        """(labels, E = E_int / 1024, iterations)."""
+        if labels is None:
+            labels = np.empty(self.n, np.uint8)
+        e, it, _ = dope_solve(self.ctx, labels, stream, allow_notconv)
+        return labels, e / 1024.0, it
+
+    def iterate(self, n, stream=None):
+        return dope_iterate(self.ctx, n, stream)
+
+    def reset(self):
+        dope_reset(self.ctx)
+
+    def get_state(self):
+        return dope_get_state(self.ctx)
+
+    def set_state(self, y, a, yhat, mu, t):
+        dope_set_state(self.ctx, y, a, yhat, mu, t)
+
+    def shifted_caps(self):
+        return dope_shifted_caps(self.ctx)
+
+    def block_cuts(self, C):
+        return dope_block_cuts(self.ctx, C)
+
+    def energy_int(self, labels):
+        return dope_energy(self.ctx, labels)
+
+    def trace(self):
+        return dope_trace(self.ctx)
+
+    def stats(self):
+        return dope_get_stats(self.ctx)
+
+    def set_profiling(self, on=True):
+        dope_set_profiling(self.ctx, on)
+
+    def profile(self):
+        return dope_get_profile(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            dope_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

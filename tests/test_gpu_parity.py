@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the oracle.
+
+Bars (the method's own): block cuts and labels bit-exact (integer min-cut with
+a unique canonical minimiser); y / a within 1e-5 relative with floor
+max(|x_ref|, 1) (they are computed with the same IEEE operations, so in
+practice they are bit-identical); energy within 1e-4 relative (exact when the
+labels match); iteration count equal unless the deciding residual is within
+1e-9 relative of eps (the per-block sums of squares are added in a different
+order on the two sides).
+"""
+import numpy as np
+import pytest
+
+from paper_1704_03116_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+Y_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dp():
+    from paper_1704_03116_gb300 import _build
+    _build.build()
+    from paper_1704_03116_gb300 import dope
+    return dope
+
+
+def _inst(orc, d):
+    return orc.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"])
+
+
+def _close(x, ref, tol=Y_TOL):
+    x, ref = np.asarray(x), np.asarray(ref)
+    return np.all(np.abs(x - ref) <= tol * np.maximum(np.abs(ref), 1.0))
+
+
+SMALL = [
+    ((64, 64), 4, (16, 16), 2.0),
+    ((48, 40), 8, (8, 8), 3.0),
+    ((30, 35), 4, (5, 7), 1.5),        # block of 35 nodes: partial warp
+    ((50, 80), 8, (25, 40), 2.0),      # block of 1000 nodes: 2 nodes per thread, ragged
+    ((16, 16, 16), 6, (8, 8, 4), 2.5),
+    ((12, 18, 20), 6, (4, 6, 5), 1.0),
+    ((64, 128), 4, (64, 64), 4.0),     # block volume 4096 (the maximum)
+    ((8, 40), 8, (1, 8), 2.0),         # one-row blocks
+    ((24, 24), 4, (1, 1), 1.0),        # every pixel its own block
+]
+
+
+@pytest.mark.parametrize("grid,conn,block,lam", SMALL)
+@pytest.mark.parametrize("mode", ["first", "random"])
+def test_block_cuts_bitexact(orc, dp, grid, conn, block, lam, mode):
+    """Step a5 alone: same int64 unaries in, same canonical block labels out."""
+    d = inputs.random_instance(grid, conn, block, lam=lam, seed=sum(grid) + len(mode))
+    inst = _inst(orc, d)
+    rng = np.random.default_rng(1)
+    if mode == "first":
+        C = inst.U.copy()
+    else:
+        wsum = np.abs(inst.Wl).sum(axis=0).max() * 2 + 1
+        C = rng.integers(-2 * wsum, 2 * wsum, inst.n)
+    ref = orc.block_cuts(inst, C)
+    g = dp.Dope.from_instance(d)
+    got = g.block_cuts(C)
+    assert np.array_equal(got, ref)
+
+
+def _oracle_states(orc, inst, mu0, t_max):
+    """States (y, a, yhat, mu, t) of Algorithm 1 after t = 0..t_max iterations."""
+    y, a, mu = np.full(inst.n, 0.5), np.zeros(inst.n), mu0
+    states = [(y.copy(), a.copy(), np.zeros(inst.n, np.uint8), mu, 0)]
+    for t in range(1, t_max + 1):
+        yhat, y, a, r2 = orc.admm_step(inst, mu, y, a)
+        mu = mu * 1.05
+        states.append((y.copy(), a.copy(), yhat.copy(), mu, t))
+    return states
+
+
+@pytest.mark.parametrize("grid,conn,block,lam", SMALL[:6])
+def test_shifted_caps_and_step_parity(orc, dp, grid, conn, block, lam):
+    """For the same dual state: Eq. 8 unaries equal as int64, one iteration gives
+    bit-exact yhat and y / a within tolerance (steps a2-a6)."""
+    d = inputs.random_instance(grid, conn, block, lam=lam, seed=7)
+    inst = _inst(orc, d)
+    g = dp.Dope.from_instance(d)
+    for (y, a, yhat, mu, t) in _oracle_states(orc, inst, d["mu0"], 4):
+        g.set_state(y, a, yhat, mu, t)
+        s_ref, C_ref = orc.shifted_caps(inst, y, a, mu)
+        assert np.array_equal(g.shifted_caps(), C_ref), f"t={t}"
+        yh_ref, y_ref, a_ref, r2 = orc.admm_step(inst, mu, y, a)
+        done, conv = g.iterate(1)
+        assert done == t + 1
+        st = g.get_state()
+        assert np.array_equal(st["yhat"], yh_ref), f"t={t}"
+        assert _close(st["y"], y_ref) and _close(st["a"], a_ref), f"t={t}"
+        assert st["mu"] == mu * 1.05
+        assert conv == (not (np.sqrt(r2.max()) > 1e-3))
+
+
+def _solve_both(orc, dp, d, **kw):
+    inst = _inst(orc, d)
+    ref = orc.admm(inst, d["mu0"], 1.05, 1e-3, kw.get("max_iter", 1000))
+    g = dp.Dope.from_instance(d, **kw)
+    lab, E, it = g.solve(allow_notconv=True)
+    return inst, ref, g, lab, E, it
+
+
+def _assert_solve_parity(ref, lab, E, it, trace):
+    if it != ref["iterations"]:
+        t = min(it, ref["iterations"])
+        # only allowed when the deciding residual sits on eps within rounding
+        assert abs(ref["rmax"][t - 1] - 1e-3) <= 1e-9 * 1e-3, (it, ref["iterations"])
+        return
+    assert np.array_equal(lab, ref["labels"])
+    assert E * 1024 == ref["energy"]
+    assert abs(E * 1024 - ref["energy"]) <= 1e-4 * abs(ref["energy"])
+    np.testing.assert_allclose(trace, ref["rmax"], rtol=1e-9, atol=1e-15)
+
+
+@pytest.mark.parametrize("grid,conn,block,lam", SMALL[:7])
+def test_solve_parity_small(orc, dp, grid, conn, block, lam):
+    d = inputs.random_instance(grid, conn, block, lam=lam, seed=11)
+    inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
+    _assert_solve_parity(ref, lab, E, it, g.trace())
+
+
+def test_solve_parity_disk64(orc, dp):
+    """64x64 disk, 4-conn, lambda 2, 16x16 sub-regions; gap to sGC reported."""
+    d = inputs.disk64()
+    inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
+    _assert_solve_parity(ref, lab, E, it, g.trace())
+    _, egc = orc.global_mincut(inst)
+    gap = (E * 1024 - egc) / abs(egc)
+    print(f"disk64: iterations {it}, E {E}, E_gc {egc / 1024}, gap {gap:.3e}")
+    assert gap >= 0
+
+
+@pytest.mark.parametrize("lam", [1.0, 4.0, 16.0])
+def test_solve_parity_ellipses512(orc, dp, lam):
+    """512x512 RGB ellipses, 8-conn contrast Potts, 32x32 sub-regions (full size)."""
+    d = inputs.ellipses_rgb(lam=lam)
+    inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
+    _assert_solve_parity(ref, lab, E, it, g.trace())
+    _, egc = orc.global_mincut(inst)
+    print(f"ellipses512 lam={lam}: iterations {it}, gap {(E * 1024 - egc) / abs(egc):.3e}, "
+          f"stats {g.stats()}")
+
+
+def test_solve_parity_ellipsoids_full(orc, dp):
+    """256x256x128 volume, 6-conn, 16x16x8 sub-regions, lambda 3 (full size)."""
+    d = inputs.ellipsoids3d()
+    inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
+    _assert_solve_parity(ref, lab, E, it, g.trace())
+    print(f"ellipsoids: iterations {it}, E {E}, stats {g.stats()}")
+
+
+def test_lambda_zero_thresholds(orc, dp):
+    d = inputs.random_instance((64, 64), 8, (16, 16), lam=0.0, seed=3)
+    d["u"][:7] = 0.0
+    g = dp.Dope.from_instance(d)
+    lab, E, it = g.solve()
+    inst = _inst(orc, d)
+    assert it == 1
+    assert np.array_equal(lab, (inst.U < 0).astype(np.uint8))
+
+
+def test_single_block_is_global_mincut(orc, dp):
+    d = inputs.random_instance((48, 48), 4, (48, 48), lam=2.0, seed=5)
+    g = dp.Dope.from_instance(d)
+    lab, E, it = g.solve()
+    inst = _inst(orc, d)
+    ref, egc = orc.global_mincut(inst)
+    assert it == 1 and np.array_equal(lab, ref) and E * 1024 == egc
+
+
+def test_not_converged_outputs_valid(orc, dp):
+    d = inputs.ellipses_rgb(size=128, lam=8.0)
+    inst, ref, g, lab, E, it = _solve_both(orc, dp, d, max_iter=3)
+    assert it == 3 and not ref["converged"]
+    assert np.array_equal(lab, ref["labels"]) and E * 1024 == ref["energy"]
+    with pytest.raises(dp.DopeError) as ei:
+        g.solve()
+    assert ei.value.status == dp.DOPE_ENOTCONV
+
+
+def test_energy_kernel(orc, dp):
+    d = inputs.random_instance((40, 56), 8, (8, 8), lam=1.7, seed=2)
+    inst = _inst(orc, d)
+    g = dp.Dope.from_instance(d)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        lab = (rng.random(inst.n) < 0.5).astype(np.uint8)
+        assert g.energy_int(lab) == orc.energy(inst, lab)
+
+
+def test_device_buffers_match_host(orc, dp):
+    import torch
+    d = inputs.random_instance((96, 64), 4, (16, 16), lam=2.0, seed=9)
+    g = dp.Dope.from_instance(d)
+    lab_h, E_h, it_h = g.solve()
+    g2 = dp.Dope(d["grid"], d["conn"], d["block"], d["lam"], mu0=d["mu0"])
+    g2.set_unaries(torch.from_numpy(d["u"]).cuda())
+    g2.set_weights(torch.from_numpy(d["wq"]).cuda())
+    lab_d = torch.empty(g2.n, dtype=torch.uint8, device="cuda")
+    _, E_d, it_d = g2.solve(lab_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(lab_d.cpu().numpy(), lab_h) and E_d == E_h and it_d == it_h
+
+
+def test_repeat_solves_identical(dp):
+    d = inputs.random_instance((128, 128), 8, (32, 32), lam=4.0, seed=4)
+    g = dp.Dope.from_instance(d)
+    a = g.solve()
+    b = g.solve()
+    assert np.array_equal(a[0], b[0]) and a[1:] == b[1:]
+
+
+def test_input_errors(dp):
+    d = inputs.random_instance((32, 32), 4, (8, 8), lam=1.0, seed=1)
+    g = dp.Dope(d["grid"], 4, (8, 8), 1.0)
+    bad = d["wq"].copy()
+    bad[0, 5] = -3
+    with pytest.raises(dp.DopeError) as ei:
+        g.set_weights(bad)
+    assert ei.value.status == dp.DOPE_EUNSUPPORTED
+    bad = d["wq"].copy()
+    bad[0, 31] = 7                       # right neighbour of the last column does not exist
+    with pytest.raises(dp.DopeError) as ei:
+        g.set_weights(bad)
+    assert ei.value.status == dp.DOPE_EINVAL
+    bad = d["wq"].copy()
+    bad[1, 0] = 1 << 25
+    with pytest.raises(dp.DopeError) as ei:
+        g.set_weights(bad)
+    assert ei.value.status == dp.DOPE_EOVERFLOW
+    u = d["u"].copy()
+    u[3] = np.inf
+    with pytest.raises(dp.DopeError) as ei:
+        g.set_unaries(u)
+    assert ei.value.status == dp.DOPE_EOVERFLOW
+    with pytest.raises(dp.DopeError) as ei:     # no valid inputs yet
+        g.solve()
+    assert ei.value.status == dp.DOPE_EINVAL
+    g.set_unaries(d["u"])
+    g.set_weights(d["wq"])
+    lab, E, it = g.solve()
+    st = g.get_state()
+    y = st["y"].copy()
+    inner = 10 * 32 + 11                      # local (2, 3) of block (1, 1): interior
+    y[inner] = 0.25
+    with pytest.raises(dp.DopeError) as ei:
+        g.set_state(y, st["a"], st["yhat"], st["mu"], st["t"])
+    assert ei.value.status == dp.DOPE_EINVAL
