@@ -175,7 +175,7 @@ def test_single_block_is_global_mincut(orc, dp):
 
 
 def test_not_converged_outputs_valid(orc, dp):
-    d = inputs.ellipses_rgb(size=128, lam=8.0)
+    d = inputs.ellipses_rgb(lam=4.0)          # needs 45 iterations
     inst, ref, g, lab, E, it = _solve_both(orc, dp, d, max_iter=3)
     assert it == 3 and not ref["converged"]
     assert np.array_equal(lab, ref["labels"]) and E * 1024 == ref["energy"]
