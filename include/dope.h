@@ -199,6 +199,38 @@ int dope_get_profile(dope_ctx *ctx, dope_profile *out);
 int dope_get_geometry(dope_ctx *ctx, int64_t *n_pixels, int64_t *n_blocks, int *block_volume,
                       int *face_size);
 
+/* Size of the device scratch array behind dope_solve_noalloc. */
+#define DOPE_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Allocation-free variant of dope_solve, for callers that cannot allocate
+ * device memory: code running while a framework's caching allocator holds
+ * the GPU's memory, plugins whose host forbids cudaMalloc after start-up,
+ * and latency-critical loops that cannot afford an allocation or the
+ * synchronisation of cudaFree.  The paper has no counterpart; this is a
+ * deployment entry point.
+ *
+ * It runs the same Algorithm 1 solve as dope_create + dope_set_unaries +
+ * dope_set_weights + dope_solve (same kernels, same results), without a
+ * context.  Arguments are those of dope_create plus: u[N] (float32, image
+ * order) and wq[conn/2][N] (int32, image order) as DEVICE pointers, labels[N]
+ * a DEVICE pointer receiving the labels (image order), *energy_int and
+ * *iterations (host, may be NULL).  Calls no cudaMalloc / cudaFree and no
+ * allocating library routine: all device state lives in one static device
+ * array of DOPE_NOALLOC_SCRATCH_BYTES that every GPU loading this library
+ * holds until the process exits.  Problems whose state does not fit
+ * (roughly N <= 262144 pixels for 8-connected 32x32 blocks) are rejected with
+ * DOPE_EINVAL before any GPU work.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array and it keeps the last call's contents (each call clears
+ * what must start at zero itself): calls that overlap on the GPU -- on two
+ * streams, or from two host threads -- race and corrupt each other; issue
+ * them one after another.  Synchronises `stream`.  Returns what dope_solve
+ * returns (DOPE_ENOTCONV with valid outputs at max_iter). */
+int dope_solve_noalloc(const int64_t *grid, int ndim, int connectivity, const int32_t *block_shape,
+                       double lambda, const dope_params *p, const float *u, const int32_t *wq,
+                       uint8_t *labels, int64_t *energy_int, int *iterations, void *stream);
+
 /* Free the context and its device memory (NULL is ignored). */
 void dope_destroy(dope_ctx *ctx);
 

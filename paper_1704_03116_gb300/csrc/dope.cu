@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -714,3 +715,264 @@ int dope_get_geometry(dope_ctx* c, int64_t* n_pixels, int64_t* n_blocks, int* bl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve (dope_solve_noalloc).
+//
+// For callers that must not allocate device memory: code that runs while a
+// framework's caching allocator has reserved the GPU's memory, plugins whose
+// host application forbids cudaMalloc after start-up, or latency-critical
+// loops where an allocation (and the implicit synchronisation of cudaFree)
+// is not acceptable.  All device state of one solve lives in the file-scope
+// array below; every GPU that loads this library holds it until the process
+// exits.  In host code `dope_noalloc_scratch` is only a host-side stand-in
+// for the symbol: its device address is taken once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char dope_noalloc_scratch[DOPE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+int g_noalloc_rc[NOALLOC_MAX_DEVICES];
+
+// Face slots of a block: pixels with a neighbour outside the block, numbered
+// in increasing local index (same tables as dope_create builds on the host).
+template <int CONN>
+__global__ void k_face_tables(int bd, int bh, int bw, int16_t* faceIndex, int16_t* faceLocal) {
+    __shared__ int warp_tot[32];
+    __shared__ int running;
+    const int B = bd * bh * bw;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) running = 0;
+    __syncthreads();
+    for (int base = 0; base < B; base += blockDim.x) {
+        const int l = base + tid;
+        bool face = false;
+        if (l < B) {
+            const int lx = l % bw, ly = (l / bw) % bh, lz = l / (bw * bh);
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int dz, dy, dx;
+                dir_off<CONN>(d, dz, dy, dx);
+                const int z = lz + dz, y = ly + dy, x = lx + dx;
+                if (z < 0 || z >= bd || y < 0 || y >= bh || x < 0 || x >= bw) face = true;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, face);
+        if (lane == 0) warp_tot[wid] = __popc(m);
+        __syncthreads();
+        int off = running;
+        for (int w = 0; w < wid; ++w) off += warp_tot[w];
+        if (l < B) {
+            if (face) {
+                const int slot = off + __popc(m & ((1u << lane) - 1u));
+                faceIndex[l] = (int16_t)slot;
+                faceLocal[slot] = (int16_t)l;
+            } else {
+                faceIndex[l] = -1;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_tot[w];
+            running += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// Per-device set-up: device address of the scratch array.
+int noalloc_setup(int* dev_out, void** ptr_out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DOPE_ECUDA;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return DOPE_EINVAL;
+    std::call_once(g_noalloc_once[dev], [dev]() {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, dope_noalloc_scratch);
+        g_noalloc_ptr[dev] = ptr;
+        g_noalloc_rc[dev] = (e == cudaSuccess && ptr) ? DOPE_OK : DOPE_ECUDA;
+    });
+    *dev_out = dev;
+    *ptr_out = g_noalloc_ptr[dev];
+    return g_noalloc_rc[dev];
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivity,
+                                  const int32_t* block_shape, double lambda, const dope_params* p,
+                                  const float* u, const int32_t* wq, uint8_t* labels,
+                                  int64_t* energy_int, int* iterations, void* stream) {
+    if (!grid || !block_shape || !u || !wq || !labels) return DOPE_EINVAL;
+    if (ndim != 2 && ndim != 3) return DOPE_EINVAL;
+    if (ndim == 2 && connectivity != 4 && connectivity != 8) return DOPE_EINVAL;
+    if (ndim == 3 && connectivity != 6) return DOPE_EINVAL;
+    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return DOPE_EINVAL;
+    int64_t dims[3] = {1, 1, 1};
+    int32_t blk[3] = {1, 1, 1};
+    for (int i = 0; i < ndim; ++i) {
+        dims[3 - ndim + i] = grid[i];
+        blk[3 - ndim + i] = block_shape[i];
+    }
+    for (int i = 0; i < 3; ++i) {
+        if (dims[i] <= 0 || blk[i] <= 0 || dims[i] % blk[i] || dims[i] > (1LL << 30)) return DOPE_EINVAL;
+    }
+    const long long N = dims[0] * dims[1] * dims[2];
+    const long long B = (long long)blk[0] * blk[1] * blk[2];
+    if (N >= (1LL << 31) || B > 4096) return DOPE_EINVAL;
+    dope_params prm;
+    dope_default_params(&prm);
+    if (p) prm = *p;
+    if (!(prm.mu0 > 0.0)) prm.mu0 = (ndim == 3) ? 500.0 : 100.0;
+    if (!(prm.mu_fact > 0.0)) prm.mu_fact = 1.05;
+    if (!(prm.eps >= 0.0)) prm.eps = 1e-3;
+    if (prm.max_iter <= 0) prm.max_iter = 1000;
+    if (prm.relabel_period <= 0) prm.relabel_period = 16;
+    if (prm.max_pulses <= 0) prm.max_pulses = (int)(64 * B + 4096);
+    int threads = prm.threads;
+    if (threads <= 0) {
+        threads = (int)((B + 31) / 32 * 32);
+        if (threads > 512) threads = 512;
+        if (threads < 32) threads = 32;
+    }
+    if (threads % 32 || threads > 512 || (long long)threads * NPTMAX < B) return DOPE_EINVAL;
+
+    Geo g;
+    g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
+    g.bd = blk[0]; g.bh = blk[1]; g.bw = blk[2];
+    g.B = (int)B;
+    g.nbz = g.D / g.bd; g.nby = g.H / g.bh; g.nbx = g.W / g.bw;
+    g.K = g.nbz * g.nby * g.nbx;
+    g.N = N;
+    {   // face count (interior = (bd-2)(bh-2)(bw-2)-style box of the connectivity)
+        const int iz = (connectivity == 6) ? (g.bd > 2 ? g.bd - 2 : 0) : g.bd;
+        const int iy = g.bh > 2 ? g.bh - 2 : 0, ix = g.bw > 2 ? g.bw - 2 : 0;
+        g.F = (int)(B - (long long)iz * iy * ix);
+    }
+    const int nh = connectivity / 2;
+
+    // scratch layout
+    const size_t ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(prm.max_iter + 2);
+    size_t off = 0;
+    const size_t o_ctrl = off;  off += align256(ctrl_bytes);
+    const size_t o_U = off;     off += align256(sizeof(int32_t) * (size_t)N);
+    const size_t o_Wl = off;    off += align256(sizeof(int32_t) * (size_t)N * nh);
+    const size_t o_yhat = off;  off += align256((size_t)N);
+    const size_t o_yF = off;    off += align256(sizeof(double) * (size_t)g.K * g.F);
+    const size_t o_aF = off;    off += align256(sizeof(double) * (size_t)g.K * g.F);
+    const size_t o_r2 = off;    off += align256(sizeof(double) * (size_t)g.K);
+    const size_t o_fi = off;    off += align256(sizeof(int16_t) * (size_t)B);
+    const size_t o_fl = off;    off += align256(sizeof(int16_t) * (size_t)(g.F ? g.F : 1));
+    if (off > (size_t)DOPE_NOALLOC_SCRATCH_BYTES) return DOPE_EINVAL;
+
+    int dev = 0;
+    void* base = nullptr;
+    int rc = noalloc_setup(&dev, &base);
+    if (rc) return rc;
+    unsigned char* sb = static_cast<unsigned char*>(base);
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(sb + o_ctrl);
+    int32_t* U = reinterpret_cast<int32_t*>(sb + o_U);
+    int32_t* Wl = reinterpret_cast<int32_t*>(sb + o_Wl);
+    uint8_t* yhat = sb + o_yhat;
+    double* yF = reinterpret_cast<double*>(sb + o_yF);
+    double* aF = reinterpret_cast<double*>(sb + o_aF);
+    double* r2blk = reinterpret_cast<double*>(sb + o_r2);
+    int16_t* faceIndex = reinterpret_cast<int16_t*>(sb + o_fi);
+    int16_t* faceLocal = reinterpret_cast<int16_t*>(sb + o_fl);
+    cudaStream_t st = S(stream);
+    const int smem = (int)((connectivity + 3) * 4 * B + B);
+
+    // everything that must start at zero: the control word and the trace
+    CK(cudaMemsetAsync(ctrl, 0, ctrl_bytes, st));
+    if (connectivity == 4) {
+        CK(cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_face_tables<4><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal);
+    } else if (connectivity == 8) {
+        CK(cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_face_tables<8><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal);
+    } else {
+        CK(cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_face_tables<6><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal);
+    }
+    const int tpb = 256;
+    k_set_unaries<<<grid_for(N, tpb), tpb, 0, st>>>(g, u, U, ctrl);
+    if (connectivity == 4) k_set_weights<4><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl);
+    else if (connectivity == 8) k_set_weights<8><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl);
+    else k_set_weights<6><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl);
+    k_init_state<<<grid_for((long long)g.K * g.F, tpb), tpb, 0, st>>>(g, yF, aF);
+    CK(cudaGetLastError());
+    Ctrl h{};
+    CK(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl) - sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h.status) return h.status;
+
+    // Algorithm 1, batches of iterations with the device-side stop test
+    SolveArgs sa;
+    sa.g = g; sa.U = U; sa.Wl = Wl; sa.yhat = yhat; sa.yF = yF; sa.aF = aF;
+    sa.faceIndex = faceIndex; sa.Cgiven = nullptr; sa.ctrl = ctrl; sa.eps = prm.eps;
+    sa.relabel_period = prm.relabel_period; sa.max_pulses = prm.max_pulses;
+    UpdArgs ua;
+    ua.g = g; ua.Wl = Wl; ua.yhat = yhat; ua.yF = yF; ua.aF = aF; ua.r2blk = r2blk;
+    ua.faceLocal = faceLocal; ua.faceIndex = faceIndex; ua.ctrl = ctrl;
+    const int ublocks = (int)(((long long)g.K * 32 + tpb - 1) / tpb);
+    double mu = prm.mu0;
+    int launched = 0, batch = 4;
+    while (launched < prm.max_iter) {
+        const int nb = (prm.max_iter - launched < batch) ? prm.max_iter - launched : batch;
+        for (int j = 0; j < nb; ++j) {
+            const int t = launched + j + 1;
+            sa.t = t; sa.mu = mu; sa.first = (t == 1); sa.check_prev = (t > 1);
+            ua.t = t; ua.mu = mu;
+            if (connectivity == 4) {
+                k_block_solve<4><<<g.K, threads, smem, st>>>(sa);
+                k_face_update<4><<<ublocks, tpb, 0, st>>>(ua);
+            } else if (connectivity == 8) {
+                k_block_solve<8><<<g.K, threads, smem, st>>>(sa);
+                k_face_update<8><<<ublocks, tpb, 0, st>>>(ua);
+            } else {
+                k_block_solve<6><<<g.K, threads, smem, st>>>(sa);
+                k_face_update<6><<<ublocks, tpb, 0, st>>>(ua);
+            }
+            mu = mu * prm.mu_fact;
+        }
+        CK(cudaGetLastError());
+        launched += nb;
+        CK(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl) - sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (h.status) return h.status;
+        if (h.conv_t) break;
+        if (batch < 32) batch *= 2;
+    }
+    int done = launched, converged = 0;
+    if (h.conv_t) {
+        done = h.conv_t;
+        converged = 1;
+    } else {
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, &ctrl->r2max[done], sizeof(bits), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double r2;
+        memcpy(&r2, &bits, sizeof(r2));
+        converged = !(std::sqrt(r2) > prm.eps);
+    }
+    if (energy_int) {
+        CK(cudaMemsetAsync(&ctrl->energy, 0, sizeof(unsigned long long), st));
+        if (connectivity == 4) k_energy<4><<<grid_for(N, tpb), tpb, 0, st>>>(g, U, Wl, yhat, ctrl);
+        else if (connectivity == 8) k_energy<8><<<grid_for(N, tpb), tpb, 0, st>>>(g, U, Wl, yhat, ctrl);
+        else k_energy<6><<<grid_for(N, tpb), tpb, 0, st>>>(g, U, Wl, yhat, ctrl);
+    }
+    k_unpermute_u8<<<grid_for(N, tpb), tpb, 0, st>>>(g, yhat, labels);
+    CK(cudaGetLastError());
+    unsigned long long e = 0;
+    if (energy_int) CK(cudaMemcpyAsync(&e, &ctrl->energy, sizeof(e), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (energy_int) *energy_int = (int64_t)e;
+    if (iterations) *iterations = done;
+    return converged ? DOPE_OK : DOPE_ENOTCONV;
+}

@@ -76,6 +76,8 @@ def _load():
         "dope_get_geometry": (i32, [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int), P(ctypes.c_int)]),
         "dope_set_profiling": (i32, [vp, i32]),
         "dope_get_profile": (i32, [vp, P(dope_profile)]),
+        "dope_solve_noalloc": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params),
+                                     vp, vp, vp, P(ctypes.c_int64), P(ctypes.c_int), vp]),
         "dope_destroy": (None, [vp]),
         "dope_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -273,6 +275,29 @@ def dope_get_profile(ctx):
     return {"launches": list(p.launches), "ms": list(p.ms),
             "first_iteration_launches": p.first_iteration_launches,
             "first_iteration_ms": p.first_iteration_ms}
+
+
+def dope_solve_noalloc(grid, connectivity, block_shape, lam, u, wq, labels, params=None, stream=None,
+                       allow_notconv=False):
+    """Allocation-free solve (no context, no device allocation): u, wq and
+    labels must be CUDA tensors.  Returns (E_int, iterations, status)."""
+    grid = [int(x) for x in grid]
+    block = [int(x) for x in block_shape]
+    pu, wu, ku = _ptr(u, _t(np.float32))
+    pw, ww, kw = _ptr(wq, _t(np.int32))
+    pl, wl, kl = _ptr(labels, _t(np.uint8))
+    if not (wu == ww == wl == DOPE_DEVICE):
+        raise TypeError("dope_solve_noalloc takes device tensors")
+    g = (ctypes.c_int64 * len(grid))(*grid)
+    b = (ctypes.c_int32 * len(block))(*block)
+    e = ctypes.c_int64(0)
+    it = ctypes.c_int(0)
+    rc = _lib.dope_solve_noalloc(g, len(grid), int(connectivity), b, float(lam),
+                                 ctypes.byref(params) if params is not None else None,
+                                 pu, pw, pl, ctypes.byref(e), ctypes.byref(it), _stream(stream))
+    if not (rc == DOPE_ENOTCONV and allow_notconv):
+        _check(rc, "dope_solve_noalloc")
+    return e.value, it.value, rc
 
 
 def dope_destroy(ctx):
