@@ -69,7 +69,8 @@ typedef struct dope_ctx dope_ctx;
  * Defaults (dope_default_params): mu0 = 0 -> 100 for 2-D grids and 500 for
  * 3-D grids (the paper's settings, Section 3), mu_fact = 1.05, eps = 1e-3,
  * max_iter = 1000, relabel_period = 0 (automatic), threads = 0 (automatic),
- * max_pulses = 0 (automatic: 64 * block volume + 4096). */
+ * max_pulses = 0 (automatic: 64 * block volume + 4096), fold_rounds = 0
+ * (automatic: 64). */
 typedef struct {
     double mu0;
     double mu_fact;
@@ -78,6 +79,7 @@ typedef struct {
     int relabel_period;  /* push-relabel pulses between global relabels */
     int threads;         /* threads per block-solver CTA (multiple of 32) */
     int max_pulses;      /* bound on push-relabel pulses per block and iteration */
+    int fold_rounds;     /* bound on exact-folding rounds per block and iteration */
 } dope_params;
 
 /* Statistics of the last dope_solve / dope_iterate call. */
@@ -89,6 +91,11 @@ typedef struct {
     int64_t free_nodes_total;   /* nodes left for push-relabel after exact folding */
     double rmax_last;           /* max_k ||yhat_k - S_k y||_2 after the last iteration */
     int64_t kernel_launches;    /* kernels this library launched during the call */
+    int64_t bfs_levels_total;   /* BFS levels (barrier rounds) summed over blocks */
+    int bfs_levels_max;         /* longest single BFS of one block */
+    int fold_rounds_max;        /* most folding rounds one block took */
+    double phase_cycles[4];     /* SM cycles of the block solver, summed over CTAs:
+                                   capacity build, folding, push-relabel pulses, BFS */
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the

@@ -36,6 +36,7 @@ struct dope_ctx {
     double* r2blk = nullptr;
     int16_t* faceIndex = nullptr;
     int16_t* faceLocal = nullptr;
+    int* halo = nullptr;
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
     // staging (lazily allocated)
@@ -110,11 +111,18 @@ void solve_launch(dope_ctx* c, const SolveArgs& a, cudaStream_t st) {
 
 void update_launch(dope_ctx* c, const UpdArgs& a, cudaStream_t st) {
     c->launches++;
-    const int threads = 256;
-    const int blocks = (int)(((long long)c->g.K * 32 + threads - 1) / threads);
-    if (c->conn == 4) k_face_update<4><<<blocks, threads, 0, st>>>(a);
-    else if (c->conn == 8) k_face_update<8><<<blocks, threads, 0, st>>>(a);
-    else k_face_update<6><<<blocks, threads, 0, st>>>(a);
+    const int threads = face_update_threads(c->g.F);
+    if (c->conn == 4) k_face_update<4><<<c->g.K, threads, 0, st>>>(a);
+    else if (c->conn == 8) k_face_update<8><<<c->g.K, threads, 0, st>>>(a);
+    else k_face_update<6><<<c->g.K, threads, 0, st>>>(a);
+}
+
+// Iteration-dependent solver arguments: mu and the integer forced-test bound.
+void set_mu(SolveArgs& a, double mu) {
+    a.mu = mu;
+    const double h = (1024.0 * mu) * 0.5;
+    a.int_test = (h < 4503599627370496.0) ? 1 : 0;   // 2^52
+    a.H = a.int_test ? (long long)std::floor(h) : 0;
 }
 
 SolveArgs solve_args(dope_ctx* c) {
@@ -126,6 +134,8 @@ SolveArgs solve_args(dope_ctx* c) {
     a.yF = c->yF;
     a.aF = c->aF;
     a.faceIndex = c->faceIndex;
+    a.halo = c->halo;
+    a.faceLocal = c->faceLocal;
     a.Cgiven = nullptr;
     a.ctrl = c->ctrl;
     a.mu = c->mu;
@@ -135,6 +145,8 @@ SolveArgs solve_args(dope_ctx* c) {
     a.check_prev = 0;
     a.relabel_period = c->p.relabel_period;
     a.max_pulses = c->p.max_pulses;
+    a.fold_rounds = c->p.fold_rounds;
+    set_mu(a, c->mu);
     return a;
 }
 
@@ -148,6 +160,7 @@ UpdArgs update_args(dope_ctx* c) {
     a.r2blk = c->r2blk;
     a.faceLocal = c->faceLocal;
     a.faceIndex = c->faceIndex;
+    a.halo = c->halo;
     a.ctrl = c->ctrl;
     a.mu = c->mu;
     a.t = c->t + 1;
@@ -183,7 +196,7 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
             const int idx = launched + j;
             SolveArgs sa = solve_args(c);
             sa.t = t0 + idx + 1;
-            sa.mu = mus[idx];
+            set_mu(sa, mus[idx]);
             sa.first = (t0 + idx == 0);
             sa.check_prev = (idx > 0);
             if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx], st));
@@ -238,6 +251,10 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
     c->stats.pulses_total = (int64_t)h.pulses_total;
     c->stats.pulses_max = h.pulses_max;
     c->stats.free_nodes_total = (int64_t)h.free_total;
+    c->stats.bfs_levels_total = (int64_t)h.bfs_levels;
+    c->stats.bfs_levels_max = h.bfs_levels_max;
+    c->stats.fold_rounds_max = h.fold_rounds_max;
+    for (int i = 0; i < 4; ++i) c->stats.phase_cycles[i] = (double)h.cyc[i];
     {
         unsigned long long bits = 0;
         CK(cudaMemcpyAsync(&bits, &c->ctrl->r2max[c->t], sizeof(bits), cudaMemcpyDeviceToHost, st));
@@ -290,6 +307,7 @@ void dope_default_params(dope_params* p) {
     p->relabel_period = 0;
     p->threads = 0;
     p->max_pulses = 0;
+    p->fold_rounds = 0;
 }
 
 const char* dope_strerror(int s) {
@@ -316,6 +334,7 @@ void dope_destroy(dope_ctx* c) {
     cudaFree(c->r2blk);
     cudaFree(c->faceIndex);
     cudaFree(c->faceLocal);
+    cudaFree(c->halo);
     cudaFree(c->ctrl);
     cudaFree(c->stage);
     cudaFree(c->stage2);
@@ -366,6 +385,7 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
     if (c->p.max_iter <= 0) c->p.max_iter = 1000;
     if (c->p.relabel_period <= 0) c->p.relabel_period = 16;
     if (c->p.max_pulses <= 0) c->p.max_pulses = (int)(64 * B + 4096);
+    if (c->p.fold_rounds <= 0) c->p.fold_rounds = MAX_FOLD_ROUNDS;
 
     Geo& g = c->g;
     g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
@@ -397,6 +417,24 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
         }
     }
     g.F = (int)floc.size();
+    // halo table [conn][F]: the cross-block neighbour of every face slot
+    std::vector<int> halo((size_t)connectivity * (g.F ? g.F : 1), -1);
+    for (int f = 0; f < g.F; ++f) {
+        const int l = floc[(size_t)f];
+        const int lx = l % g.bw, ly = (l / g.bw) % g.bh, lz = l / (g.bw * g.bh);
+        for (int d = 0; d < connectivity; ++d) {
+            const int o = d < nh ? d : d - nh, sg = d < nh ? 1 : -1;
+            int z = lz + sg * OFF[ci][o][0], y = ly + sg * OFF[ci][o][1], x = lx + sg * OFF[ci][o][2];
+            if (z >= 0 && z < g.bd && y >= 0 && y < g.bh && x >= 0 && x < g.bw) continue;
+            const int dkz = z < 0 ? -1 : (z >= g.bd ? 1 : 0);
+            const int dky = y < 0 ? -1 : (y >= g.bh ? 1 : 0);
+            const int dkx = x < 0 ? -1 : (x >= g.bw ? 1 : 0);
+            z -= dkz * g.bd; y -= dky * g.bh; x -= dkx * g.bw;
+            const int ln = (z * g.bh + y) * g.bw + x;
+            halo[(size_t)d * g.F + f] = halo_entry((dkz + 1) * 9 + (dky + 1) * 3 + (dkx + 1), ln,
+                                                   fidx[(size_t)ln]);
+        }
+    }
 
     int threads = c->p.threads;
     if (threads <= 0) {
@@ -423,11 +461,13 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
     A((void**)&c->r2blk, sizeof(double) * (size_t)g.K);
     A((void**)&c->faceIndex, sizeof(int16_t) * (size_t)B);
     A((void**)&c->faceLocal, sizeof(int16_t) * (size_t)(g.F ? g.F : 1));
+    A((void**)&c->halo, sizeof(int) * halo.size());
     c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
     A((void**)&c->ctrl, c->ctrl_bytes);
     if (rc) { cudaGetLastError(); dope_destroy(c); return rc; }
     if (cudaMemcpy(c->faceIndex, fidx.data(), sizeof(int16_t) * (size_t)B, cudaMemcpyHostToDevice) ||
         (g.F && cudaMemcpy(c->faceLocal, floc.data(), sizeof(int16_t) * (size_t)g.F, cudaMemcpyHostToDevice)) ||
+        cudaMemcpy(c->halo, halo.data(), sizeof(int) * halo.size(), cudaMemcpyHostToDevice) ||
         cudaMemset(c->ctrl, 0, c->ctrl_bytes)) {
         dope_destroy(c);
         return DOPE_ECUDA;
@@ -437,6 +477,10 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
     else if (connectivity == 8) e1 = cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
     else e1 = cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
     if (e1 != cudaSuccess) { dope_destroy(c); return DOPE_EINVAL; }
+    if (connectivity == 4) cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    else if (connectivity == 8) cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    else cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaGetLastError();
     rc = reset_state(c);
     if (rc) { dope_destroy(c); return rc; }
     *out = c;
@@ -741,7 +785,8 @@ int g_noalloc_rc[NOALLOC_MAX_DEVICES];
 // Face slots of a block: pixels with a neighbour outside the block, numbered
 // in increasing local index (same tables as dope_create builds on the host).
 template <int CONN>
-__global__ void k_face_tables(int bd, int bh, int bw, int16_t* faceIndex, int16_t* faceLocal) {
+__global__ void k_face_tables(int bd, int bh, int bw, int16_t* faceIndex, int16_t* faceLocal,
+                              int* halo) {
     __shared__ int warp_tot[32];
     __shared__ int running;
     const int B = bd * bh * bw;
@@ -782,6 +827,26 @@ __global__ void k_face_tables(int bd, int bh, int bw, int16_t* faceIndex, int16_
             running += tot;
         }
         __syncthreads();
+    }
+    // halo table [CONN][F]
+    const int F = running;
+    for (int i = tid; i < CONN * F; i += blockDim.x) {
+        const int d = i / F, f = i % F;
+        const int l = faceLocal[f];
+        const int lx = l % bw, ly = (l / bw) % bh, lz = l / (bw * bh);
+        int dz, dy, dx;
+        dir_off<CONN>(d, dz, dy, dx);
+        int z = lz + dz, y = ly + dy, x = lx + dx;
+        int e = -1;
+        if (!(z >= 0 && z < bd && y >= 0 && y < bh && x >= 0 && x < bw)) {
+            const int dkz = z < 0 ? -1 : (z >= bd ? 1 : 0);
+            const int dky = y < 0 ? -1 : (y >= bh ? 1 : 0);
+            const int dkx = x < 0 ? -1 : (x >= bw ? 1 : 0);
+            z -= dkz * bd; y -= dky * bh; x -= dkx * bw;
+            const int ln = (z * bh + y) * bw + x;
+            e = halo_entry((dkz + 1) * 9 + (dky + 1) * 3 + (dkx + 1), ln, faceIndex[ln]);
+        }
+        halo[i] = e;
     }
 }
 
@@ -835,6 +900,7 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     if (prm.max_iter <= 0) prm.max_iter = 1000;
     if (prm.relabel_period <= 0) prm.relabel_period = 16;
     if (prm.max_pulses <= 0) prm.max_pulses = (int)(64 * B + 4096);
+    if (prm.fold_rounds <= 0) prm.fold_rounds = MAX_FOLD_ROUNDS;
     int threads = prm.threads;
     if (threads <= 0) {
         threads = (int)((B + 31) / 32 * 32);
@@ -869,6 +935,7 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     const size_t o_r2 = off;    off += align256(sizeof(double) * (size_t)g.K);
     const size_t o_fi = off;    off += align256(sizeof(int16_t) * (size_t)B);
     const size_t o_fl = off;    off += align256(sizeof(int16_t) * (size_t)(g.F ? g.F : 1));
+    const size_t o_halo = off;  off += align256(sizeof(int) * (size_t)connectivity * (g.F ? g.F : 1));
     if (off > (size_t)DOPE_NOALLOC_SCRATCH_BYTES) return DOPE_EINVAL;
 
     int dev = 0;
@@ -885,6 +952,7 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     double* r2blk = reinterpret_cast<double*>(sb + o_r2);
     int16_t* faceIndex = reinterpret_cast<int16_t*>(sb + o_fi);
     int16_t* faceLocal = reinterpret_cast<int16_t*>(sb + o_fl);
+    int* halo = reinterpret_cast<int*>(sb + o_halo);
     cudaStream_t st = S(stream);
     const int smem = (int)((connectivity + 3) * 4 * B + B);
 
@@ -892,13 +960,13 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     CK(cudaMemsetAsync(ctrl, 0, ctrl_bytes, st));
     if (connectivity == 4) {
         CK(cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_face_tables<4><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal);
+        k_face_tables<4><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal, halo);
     } else if (connectivity == 8) {
         CK(cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_face_tables<8><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal);
+        k_face_tables<8><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal, halo);
     } else {
         CK(cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_face_tables<6><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal);
+        k_face_tables<6><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal, halo);
     }
     const int tpb = 256;
     k_set_unaries<<<grid_for(N, tpb), tpb, 0, st>>>(g, u, U, ctrl);
@@ -915,29 +983,30 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     // Algorithm 1, batches of iterations with the device-side stop test
     SolveArgs sa;
     sa.g = g; sa.U = U; sa.Wl = Wl; sa.yhat = yhat; sa.yF = yF; sa.aF = aF;
-    sa.faceIndex = faceIndex; sa.Cgiven = nullptr; sa.ctrl = ctrl; sa.eps = prm.eps;
+    sa.faceIndex = faceIndex; sa.halo = halo; sa.faceLocal = faceLocal; sa.Cgiven = nullptr; sa.ctrl = ctrl; sa.eps = prm.eps;
     sa.relabel_period = prm.relabel_period; sa.max_pulses = prm.max_pulses;
+    sa.fold_rounds = prm.fold_rounds;
     UpdArgs ua;
     ua.g = g; ua.Wl = Wl; ua.yhat = yhat; ua.yF = yF; ua.aF = aF; ua.r2blk = r2blk;
-    ua.faceLocal = faceLocal; ua.faceIndex = faceIndex; ua.ctrl = ctrl;
-    const int ublocks = (int)(((long long)g.K * 32 + tpb - 1) / tpb);
+    ua.faceLocal = faceLocal; ua.faceIndex = faceIndex; ua.halo = halo; ua.ctrl = ctrl;
+    const int uthreads = face_update_threads(g.F);
     double mu = prm.mu0;
     int launched = 0, batch = 4;
     while (launched < prm.max_iter) {
         const int nb = (prm.max_iter - launched < batch) ? prm.max_iter - launched : batch;
         for (int j = 0; j < nb; ++j) {
             const int t = launched + j + 1;
-            sa.t = t; sa.mu = mu; sa.first = (t == 1); sa.check_prev = (t > 1);
+            sa.t = t; set_mu(sa, mu); sa.first = (t == 1); sa.check_prev = (t > 1);
             ua.t = t; ua.mu = mu;
             if (connectivity == 4) {
                 k_block_solve<4><<<g.K, threads, smem, st>>>(sa);
-                k_face_update<4><<<ublocks, tpb, 0, st>>>(ua);
+                k_face_update<4><<<g.K, uthreads, 0, st>>>(ua);
             } else if (connectivity == 8) {
                 k_block_solve<8><<<g.K, threads, smem, st>>>(sa);
-                k_face_update<8><<<ublocks, tpb, 0, st>>>(ua);
+                k_face_update<8><<<g.K, uthreads, 0, st>>>(ua);
             } else {
                 k_block_solve<6><<<g.K, threads, smem, st>>>(sa);
-                k_face_update<6><<<ublocks, tpb, 0, st>>>(ua);
+                k_face_update<6><<<g.K, uthreads, 0, st>>>(ua);
             }
             mu = mu * prm.mu_fact;
         }

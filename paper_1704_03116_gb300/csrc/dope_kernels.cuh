@@ -39,6 +39,10 @@ struct Ctrl {
     unsigned long long pulses_total;
     unsigned long long free_total;
     unsigned long long energy;      // k_energy accumulator (two's complement)
+    unsigned long long cyc[4];      // SM cycles of CTA thread 0: build, fold, pulses, BFS
+    unsigned long long bfs_levels;  // BFS levels summed over all BFS runs
+    int bfs_levels_max;
+    int fold_rounds_max;
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
 };
 
@@ -50,11 +54,16 @@ struct SolveArgs {
     const double* yF;
     const double* aF;
     const int16_t* faceIndex;       // [B] face slot of local pixel, -1 if interior
+    const int* halo;                // [CONN][F] cross-block neighbour of face slot (halo_entry)
+    const int16_t* faceLocal;       // [F] local pixel of face slot
     const long long* Cgiven;        // block-major int64 unaries (test hook) or null
     Ctrl* ctrl;
     double mu, eps;
     int t, first, check_prev;
     int relabel_period, max_pulses;
+    int fold_rounds;                // bound on exact-folding rounds
+    int int_test;                   // interior forced test in integers (needs 512 mu < 2^52)
+    long long H;                    // floor(512 mu)
 };
 
 struct UpdArgs {
@@ -66,10 +75,33 @@ struct UpdArgs {
     double* r2blk;
     const int16_t* faceLocal;       // [F] local pixel of face slot
     const int16_t* faceIndex;
+    const int* halo;
     Ctrl* ctrl;
     double mu;
     int t;
 };
+
+// Halo table entry of (face slot f, direction d): -1 if the neighbour is in
+// the same block, else (block-offset code << 24) | (ln << 12) | fn with the
+// neighbour's local index ln, its face slot fn and code = (dkz+1)*9 +
+// (dky+1)*3 + (dkx+1) for the block offset (dkz, dky, dkx) in {-1,0,1}^3.
+__host__ __device__ inline int halo_entry(int code, int ln, int fn) {
+    return (code << 24) | (ln << 12) | fn;
+}
+
+// Decode a halo entry for block (kz,ky,kx); false if the neighbour block is
+// outside the block grid (the pixel lies on the grid border).
+__device__ __forceinline__ bool halo_decode(const Geo& g, int e, int kz, int ky, int kx, int& kn,
+                                            int& ln, int& fn) {
+    if (e < 0) return false;
+    const int code = e >> 24;
+    const int nkz = kz + code / 9 - 1, nky = ky + (code / 3) % 3 - 1, nkx = kx + code % 3 - 1;
+    if (nkz < 0 || nkz >= g.nbz || nky < 0 || nky >= g.nby || nkx < 0 || nkx >= g.nbx) return false;
+    kn = (nkz * g.nby + nky) * g.nbx + nkx;
+    ln = (e >> 12) & 0xfff;
+    fn = e & 0xfff;
+    return true;
+}
 
 // Direction k of connectivity CONN: k < CONN/2 is forward offset k, k >= CONN/2
 // the backward offset k - CONN/2.  Forward offsets (dz,dy,dx):
@@ -162,6 +194,54 @@ __device__ __forceinline__ long long shifted_cap(const Geo& g, const int32_t* __
     return __double2ll_rn(s);
 }
 
+// The unaries the block solver works with.  For a pixel with no cross-block
+// neighbour at iteration t >= 2, y = yhat and a = 0, so s = U + h with
+// h = +-512 mu exactly (sign + for yhat = 0).  With H = floor(512 mu) and
+// U + H, U - H exact integers below 2^53, round-to-nearest is monotone and
+// C = rne(s) lies in {U + H, U + H + 1} (yhat = 0) or {U - H - 1, U - H}
+// (yhat = 1).  If U + H >= cs (resp. U - H < -cs), where cs is the node's
+// n-link sum, the node is forced to keep its label whatever C is exactly,
+// and U +- H (forced the same way) stands in for C; the pointwise-minimal
+// minimiser does not change.  Every other pixel gets the exact FP64 value.
+//
+// face_cap: the exact value for face slot f (pixel v) -- the operations of
+// shifted_cap in the same order, with the neighbours found through the halo
+// table and every load issued before the FP64 chain.
+template <int CONN>
+__device__ __forceinline__ long long face_cap(const Geo& g, const int32_t* __restrict__ U,
+                                              const int32_t* __restrict__ Wl,
+                                              const double* __restrict__ yF,
+                                              const double* __restrict__ aF,
+                                              const int* __restrict__ halo, int k, int kz, int ky,
+                                              int kx, int v, int f, double m1024) {
+    constexpr int nh = CONN / 2;
+    const long long gi = (long long)k * g.B + v;
+    double yj[CONN];
+    int wj[CONN];
+    unsigned ok = 0;
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        int kn, ln, fn;
+        yj[d] = 0.0;
+        wj[d] = 0;
+        if (halo_decode(g, halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+            ok |= 1u << d;
+            yj[d] = yF[(long long)kn * g.F + fn];
+            wj[d] = (d < nh) ? Wl[(long long)d * g.N + gi]
+                             : Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
+        }
+    }
+    const double yv = yF[(long long)k * g.F + f];
+    const double av = aF[(long long)k * g.F + f];
+    double s = (double)U[gi];
+#pragma unroll
+    for (int d = 0; d < CONN; ++d)
+        if ((ok >> d) & 1) s = __dadd_rn(s, __dmul_rn((double)wj[d], __dsub_rn(yv, yj[d])));
+    s = __dadd_rn(s, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
+    s = fmin(fmax(s, -CLAMP62), CLAMP62);
+    return __double2ll_rn(s);
+}
+
 // ---------------------------------------------------------------------------
 // Block solver: one CTA per block (steps a4, a5, a6).
 //
@@ -192,23 +272,25 @@ __device__ __forceinline__ long long shifted_cap(const Geo& g, const int32_t* __
 template <int CONN>
 __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const int* __restrict__ e,
                                              int16_t* h, const uint8_t* st, const int* doff,
-                                             const uint8_t* imask, int B, int HMAX, int tid,
-                                             int NT) {
+                                             unsigned long long imask, int B, int HMAX, int tid,
+                                             int NT, int& levels) {
 #pragma unroll
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v < B) h[v] = (st[v] == FREE && e[v] < 0) ? (int16_t)1 : (int16_t)HMAX;
     }
     __syncthreads();
-    for (int level = 1; level < HMAX; ++level) {
+    int level = 1;
+    for (; level < HMAX; ++level) {
         int ch = 0;
 #pragma unroll
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
             if (v < B && h[v] == HMAX && st[v] == FREE) {
+                const unsigned m = (unsigned)(imask >> (8 * q)) & 0xffu;
 #pragma unroll
                 for (int d = 0; d < CONN; ++d) {
-                    if (!((imask[q] >> d) & 1)) continue;
+                    if (!((m >> d) & 1)) continue;
                     if (res[d * B + v] > 0 && h[v + doff[d]] == level) {
                         h[v] = (int16_t)(level + 1);
                         ch = 1;
@@ -219,6 +301,7 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
         }
         if (!__syncthreads_or(ch)) break;
     }
+    levels += level;
     int act = 0;
 #pragma unroll
     for (int q = 0; q < NPTMAX; ++q) {
@@ -229,7 +312,7 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
 }
 
 template <int CONN>
-__global__ void __launch_bounds__(512) k_block_solve(SolveArgs A) {
+__global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Geo& g = A.g;
     const int B = g.B;
@@ -274,46 +357,80 @@ __global__ void __launch_bounds__(512) k_block_solve(SolveArgs A) {
     }
     constexpr int nh = CONN / 2;
     const double m1024 = __dmul_rn(1024.0, A.mu);
-    uint8_t imask[NPTMAX];
-    long long creg[NPTMAX];
+    unsigned long long imask = 0;        // 8 bits per own node: intra-block directions
+    long long c_start = clock64();
+    long long c_bfs = 0;
+    int levels = 0, bfs_max = 0;
 
-    // 1. capacity build
+    // 1a. capacity build: forward intra-block n-links from HBM, U and yhat
 #pragma unroll
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
-        imask[q] = 0;
         if (v >= B) continue;
         const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
         const long long gi = (long long)k * B + v;
-        int cs = 0;
         uint8_t m = 0;
 #pragma unroll
         for (int d = 0; d < CONN; ++d) {
             int dz, dy, dx;
             dir_off<CONN>(d, dz, dy, dx);
             const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
-            int w = 0;
-            if (nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw) {
-                m |= (uint8_t)(1u << d);
-                w = (d < nh) ? A.Wl[(long long)d * g.N + gi]
-                             : A.Wl[(long long)(d - nh) * g.N + gi + doff[d]];
-            }
-            res[d * B + v] = w;
-            cs += w;
+            const bool in = nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw;
+            if (in) m |= (uint8_t)(1u << d);
+            if (d < nh) res[d * B + v] = in ? A.Wl[(long long)d * g.N + gi] : 0;
         }
-        imask[q] = m;
-        capsum[v] = cs;
-        st[v] = FREE;
-        long long c;
-        if (A.Cgiven) c = A.Cgiven[gi];
-        else c = shifted_cap<CONN>(g, A.U, A.Wl, A.yhat, A.yF, A.aF, A.faceIndex, k, kz, ky, kx, v,
-                                   lz, ly, lx, A.first, m1024);
-        C64[v] = c;
+        imask |= (unsigned long long)m << (8 * q);
+        C64[v] = A.Cgiven ? A.Cgiven[gi] : (long long)A.U[gi];
+        st[v] = A.first ? 0 : A.yhat[gi];
     }
     __syncthreads();
+    // 1b. backward n-links from shared memory, n-link sums, interior unaries
+    const bool need_caps = !A.Cgiven && !A.first;
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v >= B) continue;
+        const unsigned m = (unsigned)(imask >> (8 * q)) & 0xffu;
+        int cs = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            if (d < nh) {
+                cs += res[d * B + v];
+            } else {
+                const int w = ((m >> d) & 1) ? res[(d - nh) * B + v + doff[d]] : 0;
+                res[d * B + v] = w;
+                cs += w;
+            }
+        }
+        capsum[v] = cs;
+        const int yh = st[v];
+        st[v] = FREE;
+        if (need_caps && A.faceIndex[v] < 0) {
+            // interior pixel: y = yhat, a = 0 (see the note above face_cap)
+            const long long Ui = C64[v];
+            const long long T = yh ? Ui - A.H : Ui + A.H;
+            if (A.int_test && (yh ? (T < -(long long)cs) : (T >= (long long)cs))) {
+                C64[v] = T;
+            } else {
+                const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+                C64[v] = shifted_cap<CONN>(g, A.U, A.Wl, A.yhat, A.yF, A.aF, A.faceIndex, k, kz, ky,
+                                           kx, v, lz, ly, lx, 0, m1024);
+            }
+        }
+    }
+    // 1c. face pixels, one face slot per thread: exact FP64 Eq. 8 unary
+    if (need_caps) {
+        for (int f = tid; f < g.F; f += NT) {
+            const int v = A.faceLocal[f];
+            C64[v] = face_cap<CONN>(g, A.U, A.Wl, A.yF, A.aF, A.halo, k, kz, ky, kx, v, f, m1024);
+        }
+    }
+    __syncthreads();
+    const long long c_built = clock64();
 
     // 2. exact folding of forced nodes
-    for (int round = 0; round < MAX_FOLD_ROUNDS; ++round) {
+    int round = 0;
+    for (; round < A.fold_rounds; ++round) {
         int changed = 0;
 #pragma unroll
         for (int q = 0; q < NPTMAX; ++q) {
@@ -356,27 +473,36 @@ __global__ void __launch_bounds__(512) k_block_solve(SolveArgs A) {
         __syncthreads();
     }
 
-    // registers <- unaries, then R1 becomes e / ein and R2 the heights
+    // unaries of free nodes (|C| < 2^28) -> R2 as int32, then R1 becomes e / ein
+    // and R2 the heights
     int nfree = 0;
 #pragma unroll
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
-        creg[q] = 0;
-        if (v < B && st[v] == FREE) { creg[q] = C64[v]; nfree++; }
+        if (v < B) {
+            const bool fr = st[v] == FREE;
+            capsum[v] = fr ? (int)C64[v] : 0;
+            nfree += fr;
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
-        if (v < B) { e[v] = (int)creg[q]; ein[v] = 0; }
+        if (v < B) { e[v] = capsum[v]; ein[v] = 0; }
     }
+    const long long c_folded = clock64();
     const int HMAX = B + 1;
     int pulses = 0;
     int16_t* hc = hA;
     int16_t* hn = hB;
     if (__syncthreads_or(nfree)) {
         // 3. push-relabel (phase 1: maximum preflow)
-        int active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT);
+        long long cb = clock64();
+        int lv0 = levels;
+        int active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT, levels);
+        bfs_max = max(bfs_max, levels - lv0);
+        c_bfs += clock64() - cb;
         const int period = A.relabel_period;
         while (active) {
             if (pulses >= A.max_pulses) {
@@ -442,12 +568,22 @@ __global__ void __launch_bounds__(512) k_block_solve(SolveArgs A) {
             active = __syncthreads_or(act);
             int16_t* tmp = hc; hc = hn; hn = tmp;
             ++pulses;
-            if (active && period > 0 && (pulses % period) == 0)
-                active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT);
+            if (active && period > 0 && (pulses % period) == 0) {
+                cb = clock64();
+                lv0 = levels;
+                active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT, levels);
+                bfs_max = max(bfs_max, levels - lv0);
+                c_bfs += clock64() - cb;
+            }
         }
         // 4. canonical cut
-        bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT);
+        cb = clock64();
+        lv0 = levels;
+        bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT, levels);
+        bfs_max = max(bfs_max, levels - lv0);
+        c_bfs += clock64() - cb;
     }
+    const long long c_end = clock64();
 
     // 6. labels
 #pragma unroll
@@ -469,16 +605,25 @@ __global__ void __launch_bounds__(512) k_block_solve(SolveArgs A) {
     // statistics
     for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
     if ((tid & 31) == 0 && nf) atomicAdd(&A.ctrl->free_total, (unsigned long long)nf);
-    if (tid == 0 && pulses) {
-        atomicAdd(&A.ctrl->pulses_total, (unsigned long long)pulses);
-        atomicMax(&A.ctrl->pulses_max, pulses);
+    if (tid == 0) {
+        if (pulses) {
+            atomicAdd(&A.ctrl->pulses_total, (unsigned long long)pulses);
+            atomicMax(&A.ctrl->pulses_max, pulses);
+        }
+        atomicAdd(&A.ctrl->cyc[0], (unsigned long long)(c_built - c_start));
+        atomicAdd(&A.ctrl->cyc[1], (unsigned long long)(c_folded - c_built));
+        atomicAdd(&A.ctrl->cyc[2], (unsigned long long)(c_end - c_folded - c_bfs));
+        atomicAdd(&A.ctrl->cyc[3], (unsigned long long)c_bfs);
+        if (levels) atomicAdd(&A.ctrl->bfs_levels, (unsigned long long)levels);
+        atomicMax(&A.ctrl->bfs_levels_max, bfs_max);
+        atomicMax(&A.ctrl->fold_rounds_max, round);
     }
 }
 
 // ---------------------------------------------------------------------------
 // Steps a2 + a3: Eq. 10 / Eq. 11 on the face pixels and the per-block stop
 // quantity r2_k = sum_{i in block k} (yhat_i - y_i)^2 (interior pixels add
-// exactly 0).  One warp per block; face slots strided over the lanes.
+// exactly 0).  One CTA per block; face slots strided over its threads.
 //   G_i = sum_{j in X(i)} Wl_ij (yhat_i - yhat_j)        (exact, integer)
 //   y_i = (yhat_i + a_i) - (G_i / 1024) / mu               (Eq. 10)
 //   a_i = a_i + (yhat_i - y_i)                             (Eq. 11)
@@ -487,27 +632,30 @@ template <int CONN>
 __global__ void __launch_bounds__(256) k_face_update(UpdArgs A) {
     if (*(volatile int*)&A.ctrl->conv_t) return;
     const Geo& g = A.g;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= g.K) return;
+    const int k = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int nh = CONN / 2;
-    const int k = warp;
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
     double r2 = 0.0;
-    for (int f = lane; f < g.F; f += 32) {
+    for (int f = tid; f < g.F; f += blockDim.x) {
         const int v = A.faceLocal[f];
-        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
         const long long gi = (long long)k * g.B + v;
+        int wj[CONN], yj[CONN];
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int kn, ln, fn;
+            wj[d] = 0;
+            yj[d] = 0;
+            if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+                const long long gj = (long long)kn * g.B + ln;
+                wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
+                yj[d] = A.yhat[gj];
+            }
+        }
         const int yh = A.yhat[gi];
         int G = 0;
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            int kn, ln;
-            if (!cross_nbr<CONN>(g, kz, ky, kx, lz, ly, lx, d, kn, ln)) continue;
-            const long long gj = (long long)kn * g.B + ln;
-            const int w = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
-            G += w * (yh - (int)A.yhat[gj]);
-        }
+        for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
         const long long s = (long long)k * g.F + f;
         const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
         const double aa = A.aF[s];
@@ -519,10 +667,21 @@ __global__ void __launch_bounds__(256) k_face_update(UpdArgs A) {
         r2 = __dadd_rn(r2, __dmul_rn(dd, dd));
     }
     for (int o = 16; o > 0; o >>= 1) r2 = __dadd_rn(r2, __shfl_xor_sync(0xffffffffu, r2, o));
-    if (lane == 0) {
-        A.r2blk[k] = r2;
-        atomicMax(&A.ctrl->r2max[A.t], (unsigned long long)__double_as_longlong(r2));
+    __shared__ double wsum[8];
+    if (lane == 0) wsum[wid] = r2;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = __dadd_rn(t, wsum[w]);
+        A.r2blk[k] = t;
+        atomicMax(&A.ctrl->r2max[A.t], (unsigned long long)__double_as_longlong(t));
     }
+}
+
+// Threads of a k_face_update CTA (one CTA per block) for F face slots.
+inline int face_update_threads(int F) {
+    int t = (F + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > 256 ? 256 : t);
 }
 
 // ---------------------------------------------------------------------------

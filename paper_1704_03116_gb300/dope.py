@@ -36,14 +36,16 @@ class DopeError(RuntimeError):
 class dope_params(ctypes.Structure):
     _fields_ = [("mu0", ctypes.c_double), ("mu_fact", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("relabel_period", ctypes.c_int),
-                ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int), ("fold_rounds", ctypes.c_int)]
 
 
 class dope_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("pulses_total", ctypes.c_int64), ("pulses_max", ctypes.c_int),
                 ("free_nodes_total", ctypes.c_int64), ("rmax_last", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("bfs_levels_total", ctypes.c_int64),
+                ("bfs_levels_max", ctypes.c_int), ("fold_rounds_max", ctypes.c_int),
+                ("phase_cycles", ctypes.c_double * 4)]
 
 
 class dope_profile(ctypes.Structure):
@@ -262,7 +264,9 @@ def dope_trace(ctx, cap=4096):
 def dope_get_stats(ctx):
     s = dope_stats()
     _check(_lib.dope_get_stats(ctx, ctypes.byref(s)), "dope_get_stats")
-    return {f: getattr(s, f) for f, _ in s._fields_}
+    out = {f: getattr(s, f) for f, _ in s._fields_}
+    out["phase_cycles"] = list(s.phase_cycles)
+    return out
 
 
 def dope_set_profiling(ctx, enable):
@@ -316,10 +320,11 @@ class Dope:
     """One DOPE context: grid, connectivity, block shape, lambda (Algorithm 1 inputs)."""
 
     def __init__(self, grid, connectivity, block_shape, lam, mu0=None, mu_fact=None, eps=None,
-                 max_iter=None, relabel_period=None, threads=None, max_pulses=None):
+                 max_iter=None, relabel_period=None, threads=None, max_pulses=None, fold_rounds=None):
         p = dope_default_params()
         for k, v in dict(mu0=mu0, mu_fact=mu_fact, eps=eps, max_iter=max_iter,
-                         relabel_period=relabel_period, threads=threads, max_pulses=max_pulses).items():
+                         relabel_period=relabel_period, threads=threads, max_pulses=max_pulses,
+                         fold_rounds=fold_rounds).items():
             if v is not None:
                 setattr(p, k, v)
         self.grid = tuple(int(g) for g in grid)
