@@ -99,10 +99,10 @@ def algorithmic_bytes(n, k, F, X, nh):
     return solve_first, solve_later, update
 
 
-def kernel_traffic():
-    """Per-launch DRAM bytes of the block solver from the committed ncu summary,
-    or None when there is none or the kernel source changed since."""
-    path = os.path.join(PROFILES, "k_block_solve_ellipses512.md")
+def kernel_traffic(kname):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, or None when there is none or the kernel source changed since."""
+    path = os.path.join(PROFILES, f"{kname}_ellipses512.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -305,21 +305,27 @@ def main():
     first_n = sum(p["first_iteration_launches"] for p in profs)
     upd_ms = sum(p["ms"][1] for p in profs)
     upd_n = sum(p["launches"][1] for p in profs)
-    if solve_ms >= upd_ms:
+    iters_n = sum(p["iterations"] for p in profs)
+    if upd_n == 0:
+        # persistent mode: one launch runs every iteration of a solve
+        kname, kms, kn = "k_admm_persistent", solve_ms, solve_n
+        kbytes = first_n * sf + (iters_n - first_n) * sl + iters_n * up
+        share = {"k_admm_persistent": 1.0}
+    elif solve_ms >= upd_ms:
         kname, kms, kn = "k_block_solve", solve_ms, solve_n
         kbytes = first_n * sf + (solve_n - first_n) * sl
+        share = {"k_block_solve": solve_ms / (solve_ms + upd_ms), "k_face_update": upd_ms / (solve_ms + upd_ms)}
     else:
         kname, kms, kn = "k_face_update", upd_ms, upd_n
         kbytes = upd_n * up
+        share = {"k_block_solve": solve_ms / (solve_ms + upd_ms), "k_face_update": upd_ms / (solve_ms + upd_ms)}
     achieved = kbytes / (kms / 1e3) / 1e9
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
-            "traffic": kernel_traffic() if kname == "k_block_solve" else None,
+            "traffic": kernel_traffic(kname),
             "algorithmic_bytes_per_launch": kbytes / max(kn, 1),
-            "avg_launch_us": 1e3 * kms / max(kn, 1), "launches": kn,
-            "time_share": {"k_block_solve": solve_ms / (solve_ms + upd_ms),
-                           "k_face_update": upd_ms / (solve_ms + upd_ms)},
-            "first_iteration_avg_us": 1e3 * sum(p["first_iteration_ms"] for p in profs) / max(first_n, 1)}
+            "avg_launch_us": 1e3 * kms / max(kn, 1), "launches": kn, "iterations_covered": iters_n,
+            "time_share": share}
 
     # ---- end to end through the C-ABI with pinned host buffers ---------
     hu = [torch.from_numpy(d["u"]).pin_memory() for d in insts]

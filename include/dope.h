@@ -70,7 +70,7 @@ typedef struct dope_ctx dope_ctx;
  * 3-D grids (the paper's settings, Section 3), mu_fact = 1.05, eps = 1e-3,
  * max_iter = 1000, relabel_period = 0 (automatic), threads = 0 (automatic),
  * max_pulses = 0 (automatic: 64 * block volume + 4096), fold_rounds = 0
- * (automatic: 64). */
+ * (automatic: 64), launch_mode = 0 (persistent, when the device can run it). */
 typedef struct {
     double mu0;
     double mu_fact;
@@ -80,6 +80,8 @@ typedef struct {
     int threads;         /* threads per block-solver CTA (multiple of 32) */
     int max_pulses;      /* bound on push-relabel pulses per block and iteration */
     int fold_rounds;     /* bound on exact-folding rounds per block and iteration */
+    int launch_mode;     /* 0: one persistent cooperative launch per solve / iterate call;
+                            1: two launches per iteration (solve, update) */
 } dope_params;
 
 /* Statistics of the last dope_solve / dope_iterate call. */
@@ -96,18 +98,23 @@ typedef struct {
     int fold_rounds_max;        /* most folding rounds one block took */
     double phase_cycles[4];     /* SM cycles of the block solver, summed over CTAs:
                                    capacity build, folding, push-relabel pulses, BFS */
+    double loop_cycles[4];      /* persistent launch, summed over CTAs and iterations:
+                                   solve phase, first barrier wait, update phase,
+                                   second barrier wait */
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the
  * caller's stream while profiling is on (dope_set_profiling).  Only launches
  * that did work are counted (launches issued past convergence return at
- * once and are excluded).  Index 0 = block solver (steps a4-a6), index 1 =
- * face update (steps a2-a3). */
+ * once and are excluded).  launch_mode 1: index 0 = block solver (steps
+ * a4-a6), index 1 = face update (steps a2-a3).  launch_mode 0: index 0 = the
+ * persistent kernel (all steps, one launch per call), index 1 unused. */
 typedef struct {
     int64_t launches[2];
     double ms[2];
     int64_t first_iteration_launches;   /* block-solver launches that were iteration 1 */
     double first_iteration_ms;          /* their device time */
+    int64_t iterations;                 /* ADMM iterations the timed launches covered */
 } dope_profile;
 
 /* Fill *p with the defaults above. */

@@ -27,6 +27,10 @@ struct dope_ctx {
     double lambda;
     dope_params p;
     int threads, smem;
+    int persist_grid = 0;     // CTAs of the persistent launch (0: not possible)
+    int resident = 0;         // 1: the resident persistent kernel (K CTAs, one block each)
+    int resident_smem = 0;
+    int resident_threads = 0;
     // device state
     int32_t* U = nullptr;
     int32_t* Wl = nullptr;
@@ -167,6 +171,87 @@ UpdArgs update_args(dope_ctx* c) {
     return a;
 }
 
+void fill_stats(dope_ctx* c, const Ctrl& h) {
+    c->stats.pulses_total = (int64_t)h.pulses_total;
+    c->stats.pulses_max = h.pulses_max;
+    c->stats.free_nodes_total = (int64_t)h.free_total;
+    c->stats.bfs_levels_total = (int64_t)h.bfs_levels;
+    c->stats.bfs_levels_max = h.bfs_levels_max;
+    c->stats.fold_rounds_max = h.fold_rounds_max;
+    for (int i = 0; i < 4; ++i) c->stats.phase_cycles[i] = (double)h.cyc[i];
+    for (int i = 0; i < 4; ++i) c->stats.loop_cycles[i] = (double)h.pcyc[i];
+}
+
+int read_r2max(dope_ctx* c, int t, double* r2, cudaStream_t st) {
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, &c->ctrl->r2max[t], sizeof(bits), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memcpy(r2, &bits, sizeof(*r2));
+    return DOPE_OK;
+}
+
+// Up to n iterations in one cooperative launch of k_admm_persistent.
+int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
+    const int t0 = c->t;
+    PersistArgs P;
+    P.s = solve_args(c);
+    P.u = update_args(c);
+    P.t0 = t0;
+    P.n = n;
+    P.mu_start = c->mu;
+    P.mu_fact = c->p.mu_fact;
+    P.spin_limit = 4000000000LL;   // about 2 s at the GB300 clock
+    P.dynamic = c->persist_grid < c->g.K;
+    void* args[] = {&P};
+    if (c->profiling) {
+        if (c->ev.size() < 2) {
+            c->ev.resize(2);
+            for (auto& e : c->ev) CK(cudaEventCreate(&e));
+        }
+        CK(cudaEventRecord(c->ev[0], st));
+    }
+    cudaError_t e;
+    if (c->resident) {
+        const void* fn = c->conn == 4 ? (const void*)k_admm_resident<4>
+                       : c->conn == 8 ? (const void*)k_admm_resident<8> : (const void*)k_admm_resident<6>;
+        e = cudaLaunchCooperativeKernel(fn, c->g.K, c->resident_threads, args, c->resident_smem, st);
+    } else {
+        const void* fn = c->conn == 4 ? (const void*)k_admm_persistent<4>
+                       : c->conn == 8 ? (const void*)k_admm_persistent<8> : (const void*)k_admm_persistent<6>;
+        e = cudaLaunchCooperativeKernel(fn, c->persist_grid, c->threads, args, c->smem, st);
+    }
+    if (e != cudaSuccess) return DOPE_ECUDA;
+    c->launches++;
+    if (c->profiling) CK(cudaEventRecord(c->ev[1], st));
+    Ctrl h{};
+    int rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    if (h.status) return h.status;
+    const int done = h.iters_done - t0;
+    int converged = h.conv_t != 0;
+    if (c->profiling) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->prof.launches[0]++;
+        c->prof.ms[0] += ms;
+        c->prof.iterations += done;
+        if (t0 == 0) c->prof.first_iteration_launches++;
+    }
+    double mu = c->mu;
+    for (int j = 0; j < done; ++j) mu = mu * c->p.mu_fact;
+    c->t = t0 + done;
+    c->mu = mu;
+    c->stats.iterations = c->t;
+    c->stats.converged = converged;
+    fill_stats(c, h);
+    double r2 = 0.0;
+    rc = read_r2max(c, c->t, &r2, st);
+    if (rc) return rc;
+    c->stats.rmax_last = std::sqrt(r2);
+    c->stats.kernel_launches = c->launches;
+    return DOPE_OK;
+}
+
 // Up to n iterations of Algorithm 1 from the current state.
 int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
     if (!c->have_u || !c->have_w) return DOPE_EINVAL;
@@ -180,6 +265,7 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
     int rc = clear_status(c, st);
     if (rc) return rc;
     CK(cudaMemsetAsync(&c->ctrl->r2max[t0 + 1], 0, sizeof(unsigned long long) * (size_t)n, st));
+    if (c->p.launch_mode == 0 && c->persist_grid > 0) return run_persistent(c, n, st);
     if (c->profiling && c->ev.size() < 3 * (size_t)n) {
         size_t have = c->ev.size();
         c->ev.resize(3 * (size_t)n);
@@ -238,6 +324,7 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
             c->prof.ms[0] += a;
             c->prof.launches[1]++;
             c->prof.ms[1] += b;
+            c->prof.iterations++;
             if (t0 + idx == 0) {
                 c->prof.first_iteration_launches++;
                 c->prof.first_iteration_ms += a;
@@ -248,13 +335,7 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
     c->mu = mus[done];
     c->stats.iterations = c->t;
     c->stats.converged = converged;
-    c->stats.pulses_total = (int64_t)h.pulses_total;
-    c->stats.pulses_max = h.pulses_max;
-    c->stats.free_nodes_total = (int64_t)h.free_total;
-    c->stats.bfs_levels_total = (int64_t)h.bfs_levels;
-    c->stats.bfs_levels_max = h.bfs_levels_max;
-    c->stats.fold_rounds_max = h.fold_rounds_max;
-    for (int i = 0; i < 4; ++i) c->stats.phase_cycles[i] = (double)h.cyc[i];
+    fill_stats(c, h);
     {
         unsigned long long bits = 0;
         CK(cudaMemcpyAsync(&bits, &c->ctrl->r2max[c->t], sizeof(bits), cudaMemcpyDeviceToHost, st));
@@ -308,6 +389,7 @@ void dope_default_params(dope_params* p) {
     p->threads = 0;
     p->max_pulses = 0;
     p->fold_rounds = 0;
+    p->launch_mode = 0;
 }
 
 const char* dope_strerror(int s) {
@@ -481,6 +563,43 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
     else if (connectivity == 8) cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     else cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaGetLastError();
+    {   // persistent launch: as many CTAs as can be co-resident, at most K
+        const void* fn = connectivity == 4 ? (const void*)k_admm_persistent<4>
+                       : connectivity == 8 ? (const void*)k_admm_persistent<8>
+                                           : (const void*)k_admm_persistent<6>;
+        int dev = 0, sms = 0, coop = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem) == cudaSuccess) {
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c->threads, c->smem) != cudaSuccess)
+                per_sm = 0;
+        }
+        cudaGetLastError();
+        long long cap = (long long)per_sm * sms;
+        c->persist_grid = (coop && cap > 0) ? (int)(cap < g.K ? cap : g.K) : 0;
+        // resident variant: every block's CTA co-resident with its extra shared memory
+        const void* fr = connectivity == 4 ? (const void*)k_admm_resident<4>
+                       : connectivity == 8 ? (const void*)k_admm_resident<8>
+                                           : (const void*)k_admm_resident<6>;
+        const size_t rs = resident_smem_bytes(connectivity, (int)B, g.F);
+        int rt = (int)((B + 31) / 32 * 32);
+        if (rt > 256) rt = 256;
+        int per_sm_r = 0;
+        if (coop && rs <= 227 * 1024 && (long long)rt * NPTMAX >= B && c->p.threads == 0 &&
+            cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs) == cudaSuccess) {
+            cudaFuncSetAttribute(fr, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, fr, rt, rs) != cudaSuccess)
+                per_sm_r = 0;
+        }
+        cudaGetLastError();
+        if (per_sm_r > 0 && (long long)per_sm_r * sms >= g.K) {
+            c->resident = 1;
+            c->resident_smem = (int)rs;
+            c->resident_threads = rt;
+        }
+    }
     rc = reset_state(c);
     if (rc) { dope_destroy(c); return rc; }
     *out = c;

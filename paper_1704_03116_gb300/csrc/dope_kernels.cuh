@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda/atomic>
+
 namespace dope {
 
 constexpr int NPTMAX = 8;          // nodes per thread in the block solver
@@ -43,6 +45,13 @@ struct Ctrl {
     unsigned long long bfs_levels;  // BFS levels summed over all BFS runs
     int bfs_levels_max;
     int fold_rounds_max;
+    unsigned bar_count;             // grid barrier of the persistent kernel: arrivals
+    unsigned bar_gen;               // (unused)
+    int abort;                      // set when a barrier wait gave up
+    int iters_done;                 // last iteration the persistent kernel ran
+    unsigned work[2];               // block counters of the persistent kernel (solve, update)
+    unsigned long long pcyc[4];     // persistent kernel, thread 0 of each CTA: solve phase,
+                                    // first barrier wait, update phase, second barrier wait
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
 };
 
@@ -119,6 +128,16 @@ __device__ __forceinline__ void dir_off(int k, int& dz, int& dy, int& dx) {
     dz *= s; dy *= s; dx *= s;
 }
 
+// Local-index offset of direction d inside a block with row pitch bw and
+// plane size pl (= bh * bw); the direction is a compile-time constant in the
+// unrolled loops, so this folds to one or two integer operations.
+template <int CONN>
+__device__ __forceinline__ int dir_lofs(int d, int bw, int pl) {
+    int dz, dy, dx;
+    dir_off<CONN>(d, dz, dy, dx);
+    return dz * pl + dy * bw + dx;
+}
+
 template <int CONN>
 __device__ __forceinline__ int opp_dir(int k) {
     constexpr int nh = CONN / 2;
@@ -173,17 +192,17 @@ __device__ __forceinline__ long long shifted_cap(const Geo& g, const int32_t* __
     double s = (double)Ui;
     double yv, av;
     if (f < 0) {
-        yv = (double)yhat[gi];
+        yv = (double)__ldcg(&yhat[gi]);
         av = 0.0;
     } else {
-        yv = yF[(long long)k * g.F + f];
-        av = aF[(long long)k * g.F + f];
+        yv = __ldcg(&yF[(long long)k * g.F + f]);
+        av = __ldcg(&aF[(long long)k * g.F + f]);
 #pragma unroll
         for (int d = 0; d < CONN; ++d) {
             int kn, ln;
             if (!cross_nbr<CONN>(g, kz, ky, kx, lz, ly, lx, d, kn, ln)) continue;
             const int fn = faceIndex[ln];
-            const double yj = yF[(long long)kn * g.F + fn];
+            const double yj = __ldcg(&yF[(long long)kn * g.F + fn]);
             const int w = (d < nh) ? Wl[(long long)d * g.N + gi]
                                    : Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
             s = __dadd_rn(s, __dmul_rn((double)w, __dsub_rn(yv, yj)));
@@ -208,12 +227,11 @@ __device__ __forceinline__ long long shifted_cap(const Geo& g, const int32_t* __
 // shifted_cap in the same order, with the neighbours found through the halo
 // table and every load issued before the FP64 chain.
 template <int CONN>
-__device__ __forceinline__ long long face_cap(const Geo& g, const int32_t* __restrict__ U,
-                                              const int32_t* __restrict__ Wl,
-                                              const double* __restrict__ yF,
-                                              const double* __restrict__ aF,
-                                              const int* __restrict__ halo, int k, int kz, int ky,
-                                              int kx, int v, int f, double m1024) {
+__device__ __forceinline__ long long face_cap_core(const Geo& g, long long Ui, double yv, double av,
+                                                   const int32_t* __restrict__ Wl,
+                                                   const double* __restrict__ yF,
+                                                   const int* __restrict__ halo, int k, int kz,
+                                                   int ky, int kx, int v, int f, double m1024) {
     constexpr int nh = CONN / 2;
     const long long gi = (long long)k * g.B + v;
     double yj[CONN];
@@ -226,18 +244,38 @@ __device__ __forceinline__ long long face_cap(const Geo& g, const int32_t* __res
         wj[d] = 0;
         if (halo_decode(g, halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
             ok |= 1u << d;
-            yj[d] = yF[(long long)kn * g.F + fn];
+            yj[d] = __ldcg(&yF[(long long)kn * g.F + fn]);
             wj[d] = (d < nh) ? Wl[(long long)d * g.N + gi]
                              : Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
         }
     }
-    const double yv = yF[(long long)k * g.F + f];
-    const double av = aF[(long long)k * g.F + f];
-    double s = (double)U[gi];
+    double s = (double)Ui;
 #pragma unroll
     for (int d = 0; d < CONN; ++d)
         if ((ok >> d) & 1) s = __dadd_rn(s, __dmul_rn((double)wj[d], __dsub_rn(yv, yj[d])));
     s = __dadd_rn(s, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
+    s = fmin(fmax(s, -CLAMP62), CLAMP62);
+    return __double2ll_rn(s);
+}
+
+template <int CONN>
+__device__ __forceinline__ long long face_cap(const Geo& g, const int32_t* __restrict__ U,
+                                              const int32_t* __restrict__ Wl,
+                                              const double* __restrict__ yF,
+                                              const double* __restrict__ aF,
+                                              const int* __restrict__ halo, int k, int kz, int ky,
+                                              int kx, int v, int f, double m1024) {
+    const double yv = __ldcg(&yF[(long long)k * g.F + f]);
+    const double av = __ldcg(&aF[(long long)k * g.F + f]);
+    return face_cap_core<CONN>(g, (long long)U[(long long)k * g.B + v], yv, av, Wl, yF, halo, k, kz,
+                               ky, kx, v, f, m1024);
+}
+
+// Eq. 8 unary of an interior pixel (y = yhat, a = 0), the operations of
+// shifted_cap's interior branch.
+__device__ __forceinline__ long long interior_cap(long long Ui, int yh, double m1024) {
+    double s = (double)Ui;
+    s = __dadd_rn(s, __dmul_rn(m1024, __dadd_rn(__dsub_rn(0.0, (double)yh), 0.5)));
     s = fmin(fmax(s, -CLAMP62), CLAMP62);
     return __double2ll_rn(s);
 }
@@ -271,7 +309,7 @@ __device__ __forceinline__ long long face_cap(const Geo& g, const int32_t* __res
 // still reach t.
 template <int CONN>
 __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const int* __restrict__ e,
-                                             int16_t* h, const uint8_t* st, const int* doff,
+                                             int16_t* h, const uint8_t* st, int bw, int pl,
                                              unsigned long long imask, int B, int HMAX, int tid,
                                              int NT, int& levels) {
 #pragma unroll
@@ -291,7 +329,7 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
 #pragma unroll
                 for (int d = 0; d < CONN; ++d) {
                     if (!((m >> d) & 1)) continue;
-                    if (res[d * B + v] > 0 && h[v + doff[d]] == level) {
+                    if (res[d * B + v] > 0 && h[v + dir_lofs<CONN>(d, bw, pl)] == level) {
                         h[v] = (int16_t)(level + 1);
                         ch = 1;
                         break;
@@ -312,12 +350,14 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
 }
 
 template <int CONN>
-__global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned char* smem, int bw, int pl,
+                                       unsigned long long imask, long long c_start, uint8_t* lab_smem);
+
+template <int CONN>
+__device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
     const Geo& g = A.g;
     const int B = g.B;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int k = blockIdx.x;
     int* res = reinterpret_cast<int*>(smem);
     long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
     int* e = reinterpret_cast<int*>(C64);
@@ -326,41 +366,12 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
     int16_t* hA = reinterpret_cast<int16_t*>(capsum);
     int16_t* hB = hA + B;
     uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
-    __shared__ int s_skip;
-
-    // stop test of the previous iteration (Algorithm 1 loop condition)
-    if (tid == 0) {
-        int skip = 0;
-        if (A.check_prev) {
-            if (*(volatile int*)&A.ctrl->conv_t) {
-                skip = 1;
-            } else {
-                double r2 = __longlong_as_double((long long)A.ctrl->r2max[A.t - 1]);
-                if (!(__dsqrt_rn(r2) > A.eps)) {
-                    skip = 1;
-                    if (blockIdx.x == 0) atomicCAS(&A.ctrl->conv_t, 0, A.t - 1);
-                }
-            }
-        }
-        s_skip = skip;
-    }
-    __syncthreads();
-    if (s_skip) return;
-
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
-    int doff[CONN];
-#pragma unroll
-    for (int d = 0; d < CONN; ++d) {
-        int dz, dy, dx;
-        dir_off<CONN>(d, dz, dy, dx);
-        doff[d] = (dz * g.bh + dy) * g.bw + dx;
-    }
+    const int bw = g.bw, pl = g.bh * g.bw;
     constexpr int nh = CONN / 2;
     const double m1024 = __dmul_rn(1024.0, A.mu);
     unsigned long long imask = 0;        // 8 bits per own node: intra-block directions
-    long long c_start = clock64();
-    long long c_bfs = 0;
-    int levels = 0, bfs_max = 0;
+    const long long c_start = clock64();
 
     // 1a. capacity build: forward intra-block n-links from HBM, U and yhat
 #pragma unroll
@@ -381,7 +392,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
         }
         imask |= (unsigned long long)m << (8 * q);
         C64[v] = A.Cgiven ? A.Cgiven[gi] : (long long)A.U[gi];
-        st[v] = A.first ? 0 : A.yhat[gi];
+        st[v] = A.first ? 0 : __ldcg(&A.yhat[gi]);
     }
     __syncthreads();
     // 1b. backward n-links from shared memory, n-link sums, interior unaries
@@ -397,7 +408,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
             if (d < nh) {
                 cs += res[d * B + v];
             } else {
-                const int w = ((m >> d) & 1) ? res[(d - nh) * B + v + doff[d]] : 0;
+                const int w = ((m >> d) & 1) ? res[(d - nh) * B + v + dir_lofs<CONN>(d, bw, pl)] : 0;
                 res[d * B + v] = w;
                 cs += w;
             }
@@ -426,7 +437,29 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
         }
     }
     __syncthreads();
+    cut_block<CONN>(A, k, smem, bw, pl, imask, c_start, nullptr);
+}
+
+// Steps a5-a6 on the graph the build left in shared memory (res, C64, capsum,
+// st): exact folding, push-relabel, canonical cut, labels to A.yhat (and to
+// lab_smem when given), statistics.
+template <int CONN>
+__device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned char* smem, int bw, int pl,
+                                       unsigned long long imask, long long c_start, uint8_t* lab_smem) {
+    const Geo& g = A.g;
+    const int B = g.B;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    int* res = reinterpret_cast<int*>(smem);
+    long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
+    int* e = reinterpret_cast<int*>(C64);
+    int* ein = e + B;
+    int* capsum = reinterpret_cast<int*>(C64 + B);
+    int16_t* hA = reinterpret_cast<int16_t*>(capsum);
+    int16_t* hB = hA + B;
+    uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
     const long long c_built = clock64();
+    long long c_bfs = 0;
+    int levels = 0, bfs_max = 0;
 
     // 2. exact folding of forced nodes
     int round = 0;
@@ -447,7 +480,15 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
                 }
             }
         }
-        if (!__syncthreads_or(changed)) break;
+        // stop when nothing changed, or when no node is left free
+        int left = 0;
+#pragma unroll
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            left |= (v < B && st[v] == FREE);
+        }
+        const int any_changed = __syncthreads_or(changed);
+        if (!any_changed || !__syncthreads_or(left)) { round += any_changed; break; }
 #pragma unroll
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
@@ -458,7 +499,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
                 for (int d = 0; d < CONN; ++d) {
                     const int r = res[d * B + v];
                     if (r > 0) {
-                        const int su = st[v + doff[d]];
+                        const int su = st[v + dir_lofs<CONN>(d, bw, pl)];
                         if (su != FREE) {
                             c += (su == FIX0) ? r : -r;
                             cs -= r;
@@ -500,7 +541,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
         // 3. push-relabel (phase 1: maximum preflow)
         long long cb = clock64();
         int lv0 = levels;
-        int active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT, levels);
+        int active = bfs_from_sink<CONN>(res, e, hc, st, bw, pl, imask, B, HMAX, tid, NT, levels);
         bfs_max = max(bfs_max, levels - lv0);
         c_bfs += clock64() - cb;
         const int period = A.relabel_period;
@@ -522,7 +563,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
                             if (ev == 0) break;
                             const int r = res[d * B + v];
                             if (r > 0) {
-                                const int u = v + doff[d];
+                                const int u = v + dir_lofs<CONN>(d, bw, pl);
                                 if (hc[u] == hv - 1) {
                                     const int dl = min(ev, r);
                                     res[d * B + v] = r - dl;
@@ -554,7 +595,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
 #pragma unroll
                         for (int d = 0; d < CONN; ++d) {
                             if (res[d * B + v] > 0) {
-                                const int hu = hc[v + doff[d]];
+                                const int hu = hc[v + dir_lofs<CONN>(d, bw, pl)];
                                 adm |= (hu == hv - 1);
                                 mn = min(mn, hu);
                             }
@@ -571,7 +612,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
             if (active && period > 0 && (pulses % period) == 0) {
                 cb = clock64();
                 lv0 = levels;
-                active = bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT, levels);
+                active = bfs_from_sink<CONN>(res, e, hc, st, bw, pl, imask, B, HMAX, tid, NT, levels);
                 bfs_max = max(bfs_max, levels - lv0);
                 c_bfs += clock64() - cb;
             }
@@ -579,7 +620,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
         // 4. canonical cut
         cb = clock64();
         lv0 = levels;
-        bfs_from_sink<CONN>(res, e, hc, st, doff, imask, B, HMAX, tid, NT, levels);
+        bfs_from_sink<CONN>(res, e, hc, st, bw, pl, imask, B, HMAX, tid, NT, levels);
         bfs_max = max(bfs_max, levels - lv0);
         c_bfs += clock64() - cb;
     }
@@ -595,6 +636,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
         else if (st[v] == FIX1) lab = 1;
         else lab = (hc[v] < HMAX) ? 1 : 0;
         A.yhat[(long long)k * B + v] = lab;
+        if (lab_smem) lab_smem[v] = lab;
     }
     int nf = 0;
 #pragma unroll
@@ -618,6 +660,34 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
         atomicMax(&A.ctrl->bfs_levels_max, bfs_max);
         atomicMax(&A.ctrl->fold_rounds_max, round);
     }
+    __syncthreads();   // shared memory is reused by the next block / phase
+}
+
+// One launch = one iteration's block solves (steps a4-a6), one CTA per block.
+// With check_prev, the CTA first evaluates the stop test of the previous
+// iteration (Algorithm 1's loop condition) and returns if it holds.
+template <int CONN>
+__global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) {
+        int skip = 0;
+        if (A.check_prev) {
+            if (*(volatile int*)&A.ctrl->conv_t) {
+                skip = 1;
+            } else {
+                double r2 = __longlong_as_double((long long)__ldcg(&A.ctrl->r2max[A.t - 1]));
+                if (!(__dsqrt_rn(r2) > A.eps)) {
+                    skip = 1;
+                    if (blockIdx.x == 0) atomicCAS(&A.ctrl->conv_t, 0, A.t - 1);
+                }
+            }
+        }
+        s_skip = skip;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    solve_block<CONN>(A, blockIdx.x, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -629,53 +699,67 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
 //   a_i = a_i + (yhat_i - y_i)                             (Eq. 11)
 // ---------------------------------------------------------------------------
 template <int CONN>
-__global__ void __launch_bounds__(256) k_face_update(UpdArgs A) {
-    if (*(volatile int*)&A.ctrl->conv_t) return;
+__device__ void update_block(const UpdArgs& A, int k) {
     const Geo& g = A.g;
-    const int k = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     constexpr int nh = CONN / 2;
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
-    double r2 = 0.0;
-    for (int f = tid; f < g.F; f += blockDim.x) {
-        const int v = A.faceLocal[f];
-        const long long gi = (long long)k * g.B + v;
-        int wj[CONN], yj[CONN];
+    // r_k^2 is summed in a fixed order, whatever the CTA shape: face slots in
+    // chunks of 32, each chunk by the same butterfly, chunks in increasing order
+    __shared__ double part[128];
+    const int nchunks = (g.F + 31) >> 5;
+    for (int ch = wid; ch < nchunks; ch += nw) {
+        const int f = ch * 32 + lane;
+        double d2 = 0.0;
+        if (f < g.F) {
+            const int v = A.faceLocal[f];
+            const long long gi = (long long)k * g.B + v;
+            int wj[CONN], yj[CONN];
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            int kn, ln, fn;
-            wj[d] = 0;
-            yj[d] = 0;
-            if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
-                const long long gj = (long long)kn * g.B + ln;
-                wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
-                yj[d] = A.yhat[gj];
+            for (int d = 0; d < CONN; ++d) {
+                int kn, ln, fn;
+                wj[d] = 0;
+                yj[d] = 0;
+                if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+                    const long long gj = (long long)kn * g.B + ln;
+                    wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
+                    yj[d] = __ldcg(&A.yhat[gj]);
+                }
             }
-        }
-        const int yh = A.yhat[gi];
-        int G = 0;
+            const int yh = __ldcg(&A.yhat[gi]);
+            int G = 0;
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
-        const long long s = (long long)k * g.F + f;
-        const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
-        const double aa = A.aF[s];
-        const double yn = __dsub_rn(__dadd_rn((double)yh, aa), __ddiv_rn(gq, A.mu));
-        const double an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
-        A.yF[s] = yn;
-        A.aF[s] = an;
-        const double dd = __dsub_rn((double)yh, yn);
-        r2 = __dadd_rn(r2, __dmul_rn(dd, dd));
+            for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
+            const long long s = (long long)k * g.F + f;
+            const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
+            const double aa = __ldcg(&A.aF[s]);
+            // G = 0: (G/1024)/mu = +0 and x - (+0) = x exactly, so the division is skipped
+            const double ya = __dadd_rn((double)yh, aa);
+            const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, A.mu)) : ya;
+            const double an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
+            A.yF[s] = yn;
+            A.aF[s] = an;
+            const double dd = __dsub_rn((double)yh, yn);
+            d2 = __dmul_rn(dd, dd);
+        }
+        for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        if (lane == 0) part[ch] = d2;
     }
-    for (int o = 16; o > 0; o >>= 1) r2 = __dadd_rn(r2, __shfl_xor_sync(0xffffffffu, r2, o));
-    __shared__ double wsum[8];
-    if (lane == 0) wsum[wid] = r2;
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = __dadd_rn(t, wsum[w]);
+        for (int ch = 0; ch < nchunks; ++ch) t = __dadd_rn(t, part[ch]);
         A.r2blk[k] = t;
         atomicMax(&A.ctrl->r2max[A.t], (unsigned long long)__double_as_longlong(t));
     }
+    __syncthreads();   // part is reused by the next block
+}
+
+// One launch = one iteration's Eq. 10 / Eq. 11 update, one CTA per block.
+template <int CONN>
+__global__ void __launch_bounds__(256) k_face_update(UpdArgs A) {
+    if (*(volatile int*)&A.ctrl->conv_t) return;
+    update_block<CONN>(A, blockIdx.x);
 }
 
 // Threads of a k_face_update CTA (one CTA per block) for F face slots.
@@ -855,6 +939,383 @@ __global__ void k_shifted_caps(Geo g, const int32_t* U, const int32_t* Wl, const
         const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
         out[i] = shifted_cap<CONN>(g, U, Wl, yhat, yF, aF, faceIndex, k, kz, ky, kx, v, lz, ly, lx,
                                    first, m1024);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Persistent path: all of Algorithm 1 in one cooperative launch.
+//
+// Every CTA owns blocks k = blockIdx.x, blockIdx.x + gridDim.x, ...  Each
+// iteration: solve the owned blocks (a4-a6), grid barrier, update their face
+// state (a2-a3), grid barrier, then every CTA reads the same max_k r_k^2 and
+// takes the same decision (a3); mu <- mu * mu_fact (a7) on the device, the
+// same double multiplication as the host sequence.  Mutable state is read
+// with L2 loads (__ldcg) since it is written by other CTAs within the launch.
+// ---------------------------------------------------------------------------
+struct PersistArgs {
+    SolveArgs s;
+    UpdArgs u;
+    int t0, n;              // run iterations t0+1 .. t0+n
+    double mu_start, mu_fact;
+    long long spin_limit;   // SM cycles a barrier wait may take before giving up
+    int dynamic;            // blocks handed out by an atomic counter (K > grid)
+};
+
+// Next block for this CTA: static stride, or the phase's atomic counter.
+__device__ __forceinline__ int next_block(int dynamic, unsigned* counter, int k_prev, int* s_k) {
+    if (!dynamic) return k_prev < 0 ? (int)blockIdx.x : k_prev + (int)gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) *s_k = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    return *s_k;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// arrival counter only grows: barrier number b of the launch completes when
+// it reaches b * nblocks.  Thread 0 arrives with a release RMW (the CTA's
+// earlier writes are ordered before it through __syncthreads) and waits with
+// acquire loads, so writes made before the barrier by any CTA are visible
+// after it.  A wait that exceeds spin_limit sets DOPE_ETIMEOUT and the abort
+// flag; every CTA then returns false from this and from later barriers.
+// Split form of the barrier: arrive (release) now, wait (acquire) later;
+// work placed between the two must not read other CTAs' writes.
+__device__ __forceinline__ void grid_arrive(Ctrl* c, unsigned& nbar) {
+    __syncthreads();
+    ++nbar;
+    if (threadIdx.x == 0) {
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(c->bar_count);
+        cnt.fetch_add(1u, cuda::memory_order_release);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(Ctrl* c, unsigned nblocks, unsigned nbar, long long spin_limit) {
+    __shared__ int s_okw;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(c->bar_count);
+        const unsigned target = nbar * nblocks;
+        const long long t0 = clock64();
+        while (cnt.load(cuda::memory_order_acquire) < target) {
+            if (*(volatile int*)&c->abort) { ok = 0; break; }
+            if (clock64() - t0 > spin_limit) {
+                set_status(c, 6 /* DOPE_ETIMEOUT */);
+                atomicExch(&c->abort, 1);
+                ok = 0;
+                break;
+            }
+        }
+        s_okw = ok;
+    }
+    __syncthreads();
+    return s_okw != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned nblocks, unsigned& nbar,
+                                          long long spin_limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    ++nbar;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(c->bar_count);
+        const unsigned target = nbar * nblocks;
+        if (cnt.fetch_add(1u, cuda::memory_order_release) + 1u != target) {
+            const long long t0 = clock64();
+            while (cnt.load(cuda::memory_order_acquire) < target) {
+                if (*(volatile int*)&c->abort) { ok = 0; break; }
+                if (clock64() - t0 > spin_limit) {
+                    set_status(c, 6 /* DOPE_ETIMEOUT */);
+                    atomicExch(&c->abort, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        } else {
+            cuda::atomic_thread_fence(cuda::memory_order_acquire, cuda::thread_scope_device);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int CONN>
+__global__ void __launch_bounds__(512, 2) k_admm_persistent(PersistArgs P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_k;
+    Ctrl* c = P.s.ctrl;
+    const int K = P.s.g.K;
+    double mu = P.mu_start;
+    int t = P.t0, conv = 0;
+    unsigned nbar = 0;
+    for (int j = 0; j < P.n; ++j) {
+        t = P.t0 + j + 1;
+        SolveArgs A = P.s;
+        A.t = t;
+        A.first = (t == 1);
+        A.check_prev = 0;
+        A.mu = mu;
+        const double h = __dmul_rn(__dmul_rn(1024.0, mu), 0.5);
+        A.int_test = h < 4503599627370496.0 ? 1 : 0;   // 2^52
+        A.H = A.int_test ? (long long)floor(h) : 0;
+        // the update counter is idle during the solve phase and vice versa,
+        // so each is reset in the other phase
+        const long long c0 = clock64();
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->work[1] = 0u;
+        for (int k = next_block(P.dynamic, &c->work[0], -1, &s_k); k < K;
+             k = next_block(P.dynamic, &c->work[0], k, &s_k))
+            solve_block<CONN>(A, k, smem);
+        const long long c1 = clock64();
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
+        const long long c2 = clock64();
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->work[0] = 0u;
+        UpdArgs U = P.u;
+        U.t = t;
+        U.mu = mu;
+        for (int k = next_block(P.dynamic, &c->work[1], -1, &s_k); k < K;
+             k = next_block(P.dynamic, &c->work[1], k, &s_k))
+            update_block<CONN>(U, k);
+        const long long c3 = clock64();
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
+        if (threadIdx.x == 0) {
+            const long long c4 = clock64();
+            atomicAdd(&c->pcyc[0], (unsigned long long)(c1 - c0));
+            atomicAdd(&c->pcyc[1], (unsigned long long)(c2 - c1));
+            atomicAdd(&c->pcyc[2], (unsigned long long)(c3 - c2));
+            atomicAdd(&c->pcyc[3], (unsigned long long)(c4 - c3));
+        }
+        mu = __dmul_rn(mu, P.mu_fact);
+        const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[t]));
+        if (!(__dsqrt_rn(r2) > P.s.eps)) { conv = 1; break; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->iters_done = t;
+        c->conv_t = conv ? t : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Resident persistent path (K <= co-resident CTAs): CTA k owns block k for
+// the whole launch and keeps its intra-block n-links, n-link sums, unaries,
+// labels and face state in shared memory, so a light iteration reads only the
+// neighbours' halo (face y, labels) from L2.  Arithmetic is the same as in
+// solve_block / update_block, operation for operation.
+//
+// Extra shared memory after the solver's (aligned to 16 B):
+//   yS, aS  f64 [F]          face y and a of the owned block
+//   resW    int32 [CONN][B]  intra-block n-link capacities
+//   cs0     int32 [B]        their sums
+//   Us      int32 [B]        unaries
+//   lab     uint8 [B]        labels
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t solver_smem_bytes(int conn, int B) {
+    return (size_t)(conn + 3) * 4 * B + B;
+}
+__host__ __device__ inline size_t resident_smem_bytes(int conn, int B, int F) {
+    return ((solver_smem_bytes(conn, B) + 15) & ~(size_t)15) + 16 * (size_t)F + (size_t)4 * conn * B +
+           (size_t)8 * B + B;
+}
+
+template <int CONN>
+__device__ __forceinline__ void update_block_resident(const UpdArgs& A, int k, int t, double mu,
+                                                      const uint8_t* lab, double* yS, double* aS) {
+    const Geo& g = A.g;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    constexpr int nh = CONN / 2;
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    __shared__ double part[128];
+    const int nchunks = (g.F + 31) >> 5;
+    for (int ch = wid; ch < nchunks; ch += nw) {
+        const int f = ch * 32 + lane;
+        double d2 = 0.0;
+        if (f < g.F) {
+            const int v = A.faceLocal[f];
+            const long long gi = (long long)k * g.B + v;
+            int wj[CONN], yj[CONN];
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int kn, ln, fn;
+                wj[d] = 0;
+                yj[d] = 0;
+                if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+                    const long long gj = (long long)kn * g.B + ln;
+                    wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
+                    yj[d] = __ldcg(&A.yhat[gj]);
+                }
+            }
+            const int yh = lab[v];
+            int G = 0;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
+            const long long sidx = (long long)k * g.F + f;
+            const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
+            const double aa = aS[f];
+            const double ya = __dadd_rn((double)yh, aa);
+            const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
+            const double an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
+            yS[f] = yn;
+            aS[f] = an;
+            A.yF[sidx] = yn;
+            A.aF[sidx] = an;
+            const double dd = __dsub_rn((double)yh, yn);
+            d2 = __dmul_rn(dd, dd);
+        }
+        for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        if (lane == 0) part[ch] = d2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int ch = 0; ch < nchunks; ++ch) sum = __dadd_rn(sum, part[ch]);
+        A.r2blk[k] = sum;
+        atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(sum));
+    }
+    __syncthreads();
+}
+
+template <int CONN>
+__global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Geo& g = P.s.g;
+    const int B = g.B, F = g.F;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int k = blockIdx.x;                  // gridDim.x == K
+    constexpr int nh = CONN / 2;
+    Ctrl* c = P.s.ctrl;
+    int* res = reinterpret_cast<int*>(smem);
+    long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
+    int* capsum = reinterpret_cast<int*>(C64 + B);
+    uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
+    double* yS = reinterpret_cast<double*>(smem + ((solver_smem_bytes(CONN, B) + 15) & ~(size_t)15));
+    double* aS = yS + F;
+    int* resW = reinterpret_cast<int*>(aS + F);
+    int* cs0 = resW + CONN * B;
+    int* Us = cs0 + B;
+    uint8_t* lab = reinterpret_cast<uint8_t*>(Us + B);
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    const int bw = g.bw, pl = g.bh * g.bw;
+    unsigned long long imask = 0;
+    // one-time load of the owned block
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v >= B) continue;
+        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+        const long long gi = (long long)k * B + v;
+        uint8_t m = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int dz, dy, dx;
+            dir_off<CONN>(d, dz, dy, dx);
+            const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+            const bool in = nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw;
+            if (in) m |= (uint8_t)(1u << d);
+            if (d < nh) resW[d * B + v] = in ? P.s.Wl[(long long)d * g.N + gi] : 0;
+        }
+        imask |= (unsigned long long)m << (8 * q);
+        Us[v] = P.s.U[gi];
+        lab[v] = P.t0 == 0 ? 0 : __ldcg(&P.s.yhat[gi]);
+    }
+    for (int f = tid; f < F; f += NT) {
+        yS[f] = __ldcg(&P.s.yF[(long long)k * F + f]);
+        aS[f] = __ldcg(&P.s.aF[(long long)k * F + f]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NPTMAX; ++q) {
+        int v = tid + q * NT;
+        if (v >= B) continue;
+        const unsigned m = (unsigned)(imask >> (8 * q)) & 0xffu;
+        int cs = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            if (d < nh) {
+                cs += resW[d * B + v];
+            } else {
+                const int w = ((m >> d) & 1) ? resW[(d - nh) * B + v + dir_lofs<CONN>(d, bw, pl)] : 0;
+                resW[d * B + v] = w;
+                cs += w;
+            }
+        }
+        cs0[v] = cs;
+    }
+    __syncthreads();
+
+    double mu = P.mu_start;
+    int t = P.t0, conv = 0;
+    unsigned nbar = 0;
+    bool pending = false;   // the previous iteration's closing barrier: arrived, wait still due
+    for (int j = 0; j < P.n; ++j) {
+        const int tn = P.t0 + j + 1;
+        const bool first = (tn == 1);
+        const double m1024 = __dmul_rn(1024.0, mu);
+        const double h = __dmul_rn(m1024, 0.5);
+        const int int_test = h < 4503599627370496.0 ? 1 : 0;   // 2^52
+        const long long H = int_test ? (long long)floor(h) : 0;
+        const long long c0 = clock64();
+        // Build, part 1: n-links and interior unaries from this CTA's shared
+        // memory only.  It overlaps the previous iteration's closing barrier
+        // and is thrown away if that iteration's stop test holds.
+#pragma unroll
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v >= B) continue;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) res[d * B + v] = resW[d * B + v];
+            const int cs = cs0[v];
+            capsum[v] = cs;
+            st[v] = FREE;
+            const long long Ui = Us[v];
+            long long cv = Ui;
+            if (!first && P.s.faceIndex[v] < 0) {
+                const int yh = lab[v];
+                const long long T = yh ? Ui - H : Ui + H;
+                if (int_test && (yh ? (T < -(long long)cs) : (T >= (long long)cs))) cv = T;
+                else cv = interior_cap(Ui, yh, m1024);
+            }
+            C64[v] = cv;
+        }
+        if (pending) {
+            if (!grid_wait(c, gridDim.x, nbar, P.spin_limit)) break;
+            pending = false;
+            const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[t]));
+            if (!(__dsqrt_rn(r2) > P.s.eps)) { conv = 1; break; }
+        }
+        t = tn;
+        // Build, part 2: face pixels, with the neighbours' face y from L2
+        if (!first) {
+            for (int f = tid; f < F; f += NT) {
+                const int v = P.s.faceLocal[f];
+                C64[v] = face_cap_core<CONN>(g, (long long)Us[v], yS[f], aS[f], P.s.Wl, P.s.yF, P.s.halo, k,
+                                             kz, ky, kx, v, f, m1024);
+            }
+        }
+        __syncthreads();
+        cut_block<CONN>(P.s, k, smem, bw, pl, imask, c0, lab);
+        const long long c1 = clock64();
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
+        const long long c2 = clock64();
+        update_block_resident<CONN>(P.u, k, t, mu, lab, yS, aS);
+        const long long c3 = clock64();
+        if (threadIdx.x == 0) {
+            atomicAdd(&c->pcyc[0], (unsigned long long)(c1 - c0));
+            atomicAdd(&c->pcyc[1], (unsigned long long)(c2 - c1));
+            atomicAdd(&c->pcyc[2], (unsigned long long)(c3 - c2));
+        }
+        mu = __dmul_rn(mu, P.mu_fact);
+        if (j == P.n - 1) {
+            if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
+            const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[t]));
+            conv = !(__dsqrt_rn(r2) > P.s.eps);
+        } else {
+            grid_arrive(c, nbar);
+            pending = true;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->iters_done = t;
+        c->conv_t = conv ? t : 0;
     }
 }
 

@@ -36,7 +36,8 @@ class DopeError(RuntimeError):
 class dope_params(ctypes.Structure):
     _fields_ = [("mu0", ctypes.c_double), ("mu_fact", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("relabel_period", ctypes.c_int),
-                ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int), ("fold_rounds", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int), ("fold_rounds", ctypes.c_int),
+                ("launch_mode", ctypes.c_int)]
 
 
 class dope_stats(ctypes.Structure):
@@ -45,12 +46,13 @@ class dope_stats(ctypes.Structure):
                 ("free_nodes_total", ctypes.c_int64), ("rmax_last", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("bfs_levels_total", ctypes.c_int64),
                 ("bfs_levels_max", ctypes.c_int), ("fold_rounds_max", ctypes.c_int),
-                ("phase_cycles", ctypes.c_double * 4)]
+                ("phase_cycles", ctypes.c_double * 4), ("loop_cycles", ctypes.c_double * 4)]
 
 
 class dope_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 2), ("ms", ctypes.c_double * 2),
-                ("first_iteration_launches", ctypes.c_int64), ("first_iteration_ms", ctypes.c_double)]
+                ("first_iteration_launches", ctypes.c_int64), ("first_iteration_ms", ctypes.c_double),
+                ("iterations", ctypes.c_int64)]
 
 
 def _load():
@@ -266,6 +268,7 @@ def dope_get_stats(ctx):
     _check(_lib.dope_get_stats(ctx, ctypes.byref(s)), "dope_get_stats")
     out = {f: getattr(s, f) for f, _ in s._fields_}
     out["phase_cycles"] = list(s.phase_cycles)
+    out["loop_cycles"] = list(s.loop_cycles)
     return out
 
 
@@ -278,7 +281,7 @@ def dope_get_profile(ctx):
     _check(_lib.dope_get_profile(ctx, ctypes.byref(p)), "dope_get_profile")
     return {"launches": list(p.launches), "ms": list(p.ms),
             "first_iteration_launches": p.first_iteration_launches,
-            "first_iteration_ms": p.first_iteration_ms}
+            "first_iteration_ms": p.first_iteration_ms, "iterations": p.iterations}
 
 
 def dope_solve_noalloc(grid, connectivity, block_shape, lam, u, wq, labels, params=None, stream=None,
@@ -320,11 +323,12 @@ class Dope:
     """One DOPE context: grid, connectivity, block shape, lambda (Algorithm 1 inputs)."""
 
     def __init__(self, grid, connectivity, block_shape, lam, mu0=None, mu_fact=None, eps=None,
-                 max_iter=None, relabel_period=None, threads=None, max_pulses=None, fold_rounds=None):
+                 max_iter=None, relabel_period=None, threads=None, max_pulses=None, fold_rounds=None,
+                 launch_mode=None):
         p = dope_default_params()
         for k, v in dict(mu0=mu0, mu_fact=mu_fact, eps=eps, max_iter=max_iter,
                          relabel_period=relabel_period, threads=threads, max_pulses=max_pulses,
-                         fold_rounds=fold_rounds).items():
+                         fold_rounds=fold_rounds, launch_mode=launch_mode).items():
             if v is not None:
                 setattr(p, k, v)
         self.grid = tuple(int(g) for g in grid)
