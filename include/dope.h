@@ -80,8 +80,10 @@ typedef struct {
     int threads;         /* threads per block-solver CTA (multiple of 32) */
     int max_pulses;      /* bound on push-relabel pulses per block and iteration */
     int fold_rounds;     /* bound on exact-folding rounds per block and iteration */
-    int launch_mode;     /* 0: one persistent cooperative launch per solve / iterate call;
-                            1: two launches per iteration (solve, update) */
+    int launch_mode;     /* 0: one persistent cooperative launch per solve / iterate call,
+                               with run-ahead windows once labels stop moving;
+                            1: two launches per iteration (solve, update);
+                            2: persistent launch without run-ahead windows */
 } dope_params;
 
 /* Statistics of the last dope_solve / dope_iterate call. */
@@ -100,7 +102,11 @@ typedef struct {
                                    capacity build, folding, push-relabel pulses, BFS */
     double loop_cycles[4];      /* persistent launch, summed over CTAs and iterations:
                                    solve phase, first barrier wait, update phase,
-                                   second barrier wait */
+                                   run-ahead windows */
+    int windows;                /* run-ahead windows run (launch_mode 0) */
+    int window_iterations;      /* iterations committed from run-ahead windows */
+    double window_cycles[6];    /* run-ahead windows, summed over CTAs: build, block solve,
+                                   label check, own update, halo update, window set-up */
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the

@@ -41,6 +41,10 @@ struct dope_ctx {
     int16_t* faceIndex = nullptr;
     int16_t* faceLocal = nullptr;
     int* halo = nullptr;
+    int16_t* hslot = nullptr;   // [conn][F] halo pixel index of (direction, face slot)
+    int* hinfo = nullptr;       // [NH] halo_entry of each distinct halo pixel
+    int NH = 0;
+    int window_ok = 0;          // the resident kernel fits with its run-ahead window arrays
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
     // staging (lazily allocated)
@@ -180,6 +184,7 @@ void fill_stats(dope_ctx* c, const Ctrl& h) {
     c->stats.fold_rounds_max = h.fold_rounds_max;
     for (int i = 0; i < 4; ++i) c->stats.phase_cycles[i] = (double)h.cyc[i];
     for (int i = 0; i < 4; ++i) c->stats.loop_cycles[i] = (double)h.pcyc[i];
+    for (int i = 0; i < 6; ++i) c->stats.window_cycles[i] = (double)h.wcyc[i];
 }
 
 int read_r2max(dope_ctx* c, int t, double* r2, cudaStream_t st) {
@@ -202,6 +207,10 @@ int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
     P.mu_fact = c->p.mu_fact;
     P.spin_limit = 4000000000LL;   // about 2 s at the GB300 clock
     P.dynamic = c->persist_grid < c->g.K;
+    P.window = c->window_ok && c->p.launch_mode == 0;
+    P.NH = c->NH;
+    P.hslot = c->hslot;
+    P.hinfo = c->hinfo;
     void* args[] = {&P};
     if (c->profiling) {
         if (c->ev.size() < 2) {
@@ -244,6 +253,8 @@ int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
     c->stats.iterations = c->t;
     c->stats.converged = converged;
     fill_stats(c, h);
+    c->stats.windows = h.windows;
+    c->stats.window_iterations = h.window_iters;
     double r2 = 0.0;
     rc = read_r2max(c, c->t, &r2, st);
     if (rc) return rc;
@@ -265,7 +276,7 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
     int rc = clear_status(c, st);
     if (rc) return rc;
     CK(cudaMemsetAsync(&c->ctrl->r2max[t0 + 1], 0, sizeof(unsigned long long) * (size_t)n, st));
-    if (c->p.launch_mode == 0 && c->persist_grid > 0) return run_persistent(c, n, st);
+    if (c->p.launch_mode != 1 && c->persist_grid > 0) return run_persistent(c, n, st);
     if (c->profiling && c->ev.size() < 3 * (size_t)n) {
         size_t have = c->ev.size();
         c->ev.resize(3 * (size_t)n);
@@ -364,6 +375,27 @@ int energy_of(dope_ctx* c, const uint8_t* lab_bm, int64_t* out, cudaStream_t st)
     return DOPE_OK;
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum.
+// The limit is a per-function, process-wide setting: setting it to one
+// context's own size would lower it under another context's launches.
+void raise_smem_limit(const void* fn) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && optin > (int)fa.sharedSizeBytes)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaGetLastError();
+}
+
+template <int CONN>
+void raise_smem_limits() {
+    raise_smem_limit((const void*)k_block_solve<CONN>);
+    raise_smem_limit((const void*)k_admm_persistent<CONN>);
+    raise_smem_limit((const void*)k_admm_resident<CONN>);
+}
+
 int reset_state(dope_ctx* c) {
     c->t = 0;
     c->mu = c->p.mu0;
@@ -417,6 +449,8 @@ void dope_destroy(dope_ctx* c) {
     cudaFree(c->faceIndex);
     cudaFree(c->faceLocal);
     cudaFree(c->halo);
+    cudaFree(c->hslot);
+    cudaFree(c->hinfo);
     cudaFree(c->ctrl);
     cudaFree(c->stage);
     cudaFree(c->stage2);
@@ -517,6 +551,21 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
                                                    fidx[(size_t)ln]);
         }
     }
+    // distinct halo pixels (first-seen order over face slots, then directions)
+    std::vector<int16_t> hslot((size_t)connectivity * (g.F ? g.F : 1), -1);
+    std::vector<int> hinfo;
+    for (int f = 0; f < g.F; ++f)
+        for (int d = 0; d < connectivity; ++d) {
+            const int e = halo[(size_t)d * g.F + f];
+            if (e < 0) continue;
+            int slot = -1;
+            for (size_t h = 0; h < hinfo.size(); ++h)
+                if (hinfo[h] == e) { slot = (int)h; break; }
+            if (slot < 0) { slot = (int)hinfo.size(); hinfo.push_back(e); }
+            hslot[(size_t)d * g.F + f] = (int16_t)slot;
+        }
+    c->NH = (int)hinfo.size();
+    if (hinfo.empty()) hinfo.push_back(-1);
 
     int threads = c->p.threads;
     if (threads <= 0) {
@@ -544,25 +593,29 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
     A((void**)&c->faceIndex, sizeof(int16_t) * (size_t)B);
     A((void**)&c->faceLocal, sizeof(int16_t) * (size_t)(g.F ? g.F : 1));
     A((void**)&c->halo, sizeof(int) * halo.size());
+    A((void**)&c->hslot, sizeof(int16_t) * hslot.size());
+    A((void**)&c->hinfo, sizeof(int) * hinfo.size());
     c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
     A((void**)&c->ctrl, c->ctrl_bytes);
     if (rc) { cudaGetLastError(); dope_destroy(c); return rc; }
     if (cudaMemcpy(c->faceIndex, fidx.data(), sizeof(int16_t) * (size_t)B, cudaMemcpyHostToDevice) ||
         (g.F && cudaMemcpy(c->faceLocal, floc.data(), sizeof(int16_t) * (size_t)g.F, cudaMemcpyHostToDevice)) ||
         cudaMemcpy(c->halo, halo.data(), sizeof(int) * halo.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->hslot, hslot.data(), sizeof(int16_t) * hslot.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(c->hinfo, hinfo.data(), sizeof(int) * hinfo.size(), cudaMemcpyHostToDevice) ||
         cudaMemset(c->ctrl, 0, c->ctrl_bytes)) {
         dope_destroy(c);
         return DOPE_ECUDA;
     }
-    cudaError_t e1 = cudaSuccess;
-    if (connectivity == 4) e1 = cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
-    else if (connectivity == 8) e1 = cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
-    else e1 = cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
-    if (e1 != cudaSuccess) { dope_destroy(c); return DOPE_EINVAL; }
-    if (connectivity == 4) cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    else if (connectivity == 8) cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    else cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaGetLastError();
+    if (connectivity == 4) raise_smem_limits<4>();
+    else if (connectivity == 8) raise_smem_limits<8>();
+    else raise_smem_limits<6>();
+    {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (c->smem > optin) { dope_destroy(c); return DOPE_EINVAL; }
+    }
     {   // persistent launch: as many CTAs as can be co-resident, at most K
         const void* fn = connectivity == 4 ? (const void*)k_admm_persistent<4>
                        : connectivity == 8 ? (const void*)k_admm_persistent<8>
@@ -571,9 +624,13 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem) == cudaSuccess) {
-            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c->threads, c->smem) != cudaSuccess)
+        {
+            int optin0 = 0;
+            cudaDeviceGetAttribute(&optin0, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaFuncAttributes fa0;
+            if (cudaFuncGetAttributes(&fa0, fn) != cudaSuccess ||
+                (size_t)c->smem + fa0.sharedSizeBytes > (size_t)optin0 ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c->threads, c->smem) != cudaSuccess)
                 per_sm = 0;
         }
         cudaGetLastError();
@@ -583,21 +640,30 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
         const void* fr = connectivity == 4 ? (const void*)k_admm_resident<4>
                        : connectivity == 8 ? (const void*)k_admm_resident<8>
                                            : (const void*)k_admm_resident<6>;
-        const size_t rs = resident_smem_bytes(connectivity, (int)B, g.F);
         int rt = (int)((B + 31) / 32 * 32);
         if (rt > 256) rt = 256;
-        int per_sm_r = 0;
-        if (coop && rs <= 227 * 1024 && (long long)rt * NPTMAX >= B && c->p.threads == 0 &&
-            cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs) == cudaSuccess) {
-            cudaFuncSetAttribute(fr, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, fr, rt, rs) != cudaSuccess)
-                per_sm_r = 0;
-        }
-        cudaGetLastError();
-        if (per_sm_r > 0 && (long long)per_sm_r * sms >= g.K) {
-            c->resident = 1;
-            c->resident_smem = (int)rs;
-            c->resident_threads = rt;
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        size_t static_smem = 0;
+        if (cudaFuncGetAttributes(&fa, fr) == cudaSuccess) static_smem = fa.sharedSizeBytes;
+        else optin = 0;
+        for (int with_window = 1; with_window >= 0 && !c->resident; --with_window) {
+            const size_t rs = with_window ? window_smem_bytes(connectivity, (int)B, g.F, c->NH)
+                                          : resident_smem_bytes(connectivity, (int)B, g.F);
+            int per_sm_r = 0;
+            if (coop && rs + static_smem <= (size_t)optin && (long long)rt * NPTMAX >= B &&
+                c->p.threads == 0 && g.F <= 128 * 32) {
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, fr, rt, rs) != cudaSuccess)
+                    per_sm_r = 0;
+            }
+            cudaGetLastError();
+            if (per_sm_r > 0 && (long long)per_sm_r * sms >= g.K) {
+                c->resident = 1;
+                c->resident_smem = (int)rs;
+                c->resident_threads = rt;
+                c->window_ok = with_window;
+            }
         }
     }
     rc = reset_state(c);
@@ -1078,13 +1144,13 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     // everything that must start at zero: the control word and the trace
     CK(cudaMemsetAsync(ctrl, 0, ctrl_bytes, st));
     if (connectivity == 4) {
-        CK(cudaFuncSetAttribute(k_block_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        raise_smem_limits<4>();
         k_face_tables<4><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal, halo);
     } else if (connectivity == 8) {
-        CK(cudaFuncSetAttribute(k_block_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        raise_smem_limits<8>();
         k_face_tables<8><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal, halo);
     } else {
-        CK(cudaFuncSetAttribute(k_block_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        raise_smem_limits<6>();
         k_face_tables<6><<<1, 1024, 0, st>>>(g.bd, g.bh, g.bw, faceIndex, faceLocal, halo);
     }
     const int tpb = 256;

@@ -49,7 +49,12 @@ struct Ctrl {
     unsigned bar_gen;               // (unused)
     int abort;                      // set when a barrier wait gave up
     int iters_done;                 // last iteration the persistent kernel ran
+    int thaw;                       // earliest iteration of a window whose labels moved
+    int windows;                    // run-ahead windows run (statistics)
+    int window_iters;               // iterations done inside windows (statistics)
     unsigned work[2];               // block counters of the persistent kernel (solve, update)
+    unsigned long long wcyc[6];     // run-ahead windows, thread 0 of each CTA: build, cut,
+                                    // label check, own update, halo update, set-up + resolution
     unsigned long long pcyc[4];     // persistent kernel, thread 0 of each CTA: solve phase,
                                     // first barrier wait, update phase, second barrier wait
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
@@ -312,7 +317,7 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
                                              int16_t* h, const uint8_t* st, int bw, int pl,
                                              unsigned long long imask, int B, int HMAX, int tid,
                                              int NT, int& levels) {
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v < B) h[v] = (st[v] == FREE && e[v] < 0) ? (int16_t)1 : (int16_t)HMAX;
@@ -321,7 +326,7 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
     int level = 1;
     for (; level < HMAX; ++level) {
         int ch = 0;
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
             if (v < B && h[v] == HMAX && st[v] == FREE) {
@@ -341,7 +346,7 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
     }
     levels += level;
     int act = 0;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v < B && st[v] == FREE && e[v] > 0 && h[v] < HMAX) act = 1;
@@ -351,7 +356,8 @@ __device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const 
 
 template <int CONN>
 __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned char* smem, int bw, int pl,
-                                       unsigned long long imask, long long c_start, uint8_t* lab_smem);
+                                       unsigned long long imask, long long c_start, uint8_t* lab_smem,
+                                       bool to_global = true);
 
 template <int CONN>
 __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
@@ -374,7 +380,7 @@ __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
     const long long c_start = clock64();
 
     // 1a. capacity build: forward intra-block n-links from HBM, U and yhat
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v >= B) continue;
@@ -397,7 +403,7 @@ __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
     __syncthreads();
     // 1b. backward n-links from shared memory, n-link sums, interior unaries
     const bool need_caps = !A.Cgiven && !A.first;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v >= B) continue;
@@ -445,7 +451,8 @@ __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
 // lab_smem when given), statistics.
 template <int CONN>
 __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned char* smem, int bw, int pl,
-                                       unsigned long long imask, long long c_start, uint8_t* lab_smem) {
+                                       unsigned long long imask, long long c_start, uint8_t* lab_smem,
+                                       bool to_global) {
     const Geo& g = A.g;
     const int B = g.B;
     const int tid = threadIdx.x, NT = blockDim.x;
@@ -465,7 +472,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
     int round = 0;
     for (; round < A.fold_rounds; ++round) {
         int changed = 0;
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
             if (v < B && st[v] == FREE) {
@@ -482,14 +489,14 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
         }
         // stop when nothing changed, or when no node is left free
         int left = 0;
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
             left |= (v < B && st[v] == FREE);
         }
         const int any_changed = __syncthreads_or(changed);
         if (!any_changed || !__syncthreads_or(left)) { round += any_changed; break; }
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
             if (v < B && st[v] == FREE) {
@@ -517,7 +524,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
     // unaries of free nodes (|C| < 2^28) -> R2 as int32, then R1 becomes e / ein
     // and R2 the heights
     int nfree = 0;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v < B) {
@@ -527,7 +534,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
         }
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v < B) { e[v] = capsum[v]; ein[v] = 0; }
@@ -551,7 +558,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
                 break;
             }
             // push: heights hc fixed for the whole phase
-#pragma unroll
+#pragma unroll 1
             for (int q = 0; q < NPTMAX; ++q) {
                 int v = tid + q * NT;
                 if (v < B && st[v] == FREE) {
@@ -580,7 +587,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
             __syncthreads();
             // merge incoming flow, relabel into hn
             int act = 0;
-#pragma unroll
+#pragma unroll 1
             for (int q = 0; q < NPTMAX; ++q) {
                 int v = tid + q * NT;
                 if (v >= B) continue;
@@ -627,7 +634,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
     const long long c_end = clock64();
 
     // 6. labels
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v >= B) continue;
@@ -635,11 +642,11 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
         if (st[v] == FIX0) lab = 0;
         else if (st[v] == FIX1) lab = 1;
         else lab = (hc[v] < HMAX) ? 1 : 0;
-        A.yhat[(long long)k * B + v] = lab;
+        if (to_global) A.yhat[(long long)k * B + v] = lab;
         if (lab_smem) lab_smem[v] = lab;
     }
     int nf = 0;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v < B && st[v] == FREE) nf++;
@@ -960,6 +967,10 @@ struct PersistArgs {
     double mu_start, mu_fact;
     long long spin_limit;   // SM cycles a barrier wait may take before giving up
     int dynamic;            // blocks handed out by an atomic counter (K > grid)
+    int window;             // resident kernel: run-ahead windows of frozen iterations
+    int NH;                 // halo pixels of a block (distinct cross-block neighbours)
+    const int16_t* hslot;   // [CONN][F] halo pixel of (direction, face slot), -1 if none
+    const int* hinfo;       // [NH] halo_entry of each halo pixel
 };
 
 // Next block for this CTA: static stride, or the phase's atomic counter.
@@ -1112,9 +1123,45 @@ __global__ void __launch_bounds__(512, 2) k_admm_persistent(PersistArgs P) {
 __host__ __device__ inline size_t solver_smem_bytes(int conn, int B) {
     return (size_t)(conn + 3) * 4 * B + B;
 }
+
+// Byte offsets of the resident kernel's shared-memory arrays.  The host sizes
+// the launch with `.resident_end` / `.window_end` and the kernel takes every
+// pointer from here, so the two cannot disagree.
+struct ResidentLayout {
+    size_t yS, aS, resW, cs0, Us, fl, lab, resident_end;                 // always present
+    size_t yS0, aS0, hy, ha, rloc, Gf, hG, hw, hs, hl, labw, window_end;  // run-ahead windows
+};
+
+constexpr int WMAX = 64;   // most iterations per run-ahead window
+
+__host__ __device__ inline ResidentLayout resident_layout(int conn, int B, int F, int NH) {
+    ResidentLayout L;
+    size_t o = (solver_smem_bytes(conn, B) + 15) & ~(size_t)15;
+    L.yS = o;   o += 8 * (size_t)F;
+    L.aS = o;   o += 8 * (size_t)F;
+    L.resW = o; o += 4 * (size_t)conn * B;
+    L.cs0 = o;  o += 4 * (size_t)B;
+    L.Us = o;   o += 4 * (size_t)B;
+    L.fl = o;   o += 2 * (size_t)F;
+    L.lab = o;  o += (size_t)B;
+    L.resident_end = o;
+    o = (o + 15) & ~(size_t)15;
+    L.yS0 = o;  o += 8 * (size_t)F;
+    L.aS0 = o;  o += 8 * (size_t)F;
+    L.hy = o;   o += 8 * (size_t)NH;
+    L.ha = o;   o += 8 * (size_t)NH;
+    L.rloc = o; o += 8 * (size_t)WMAX;
+    L.Gf = o;   o += 4 * (size_t)F;
+    L.hG = o;   o += 4 * (size_t)NH;
+    L.hw = o;   o += 4 * (size_t)conn * F;
+    L.hs = o;   o += 2 * (size_t)conn * F;
+    L.hl = o;   o += (size_t)NH;
+    L.labw = o; o += (size_t)B;
+    L.window_end = o;
+    return L;
+}
 __host__ __device__ inline size_t resident_smem_bytes(int conn, int B, int F) {
-    return ((solver_smem_bytes(conn, B) + 15) & ~(size_t)15) + 16 * (size_t)F + (size_t)4 * conn * B +
-           (size_t)8 * B + B;
+    return resident_layout(conn, B, F, 0).resident_end;
 }
 
 template <int CONN>
@@ -1174,12 +1221,41 @@ __device__ __forceinline__ void update_block_resident(const UpdArgs& A, int k, i
     __syncthreads();
 }
 
+// One Eq. 10 / Eq. 11 step of a face pixel with fixed label yh and cross sum G
+// (the operations of update_block, in the same order).
+__device__ __forceinline__ double face_step(int yh, int G, double mu, double& y, double& a) {
+    const double gq = __dmul_rn((double)G, 0.0009765625);
+    const double ya = __dadd_rn((double)yh, a);
+    const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
+    a = __dadd_rn(a, __dsub_rn((double)yh, yn));
+    y = yn;
+    const double dd = __dsub_rn((double)yh, yn);
+    return __dmul_rn(dd, dd);
+}
+
+__host__ __device__ inline size_t window_smem_bytes(int conn, int B, int F, int NH) {
+    return resident_layout(conn, B, F, NH).window_end;
+}
+
+// ---------------------------------------------------------------------------
+// Run-ahead windows (resident kernel).  Once labels stop moving, a face
+// pixel's y and a follow Eq. 10 / 11 with a constant cross sum G, and the Eq. 8
+// unaries of the next iteration depend only on the block's own state and on
+// its halo pixels' y.  A CTA can therefore run iterations ahead on its own:
+// it keeps its halo pixels' y, a, label and G in shared memory, advances them
+// with the same operations their owner uses, solves its block exactly each
+// iteration and checks that the labels did not move.  The first iteration in
+// which any block's labels moved (or the window end) bounds the valid run;
+// iterations are only committed up to it, and the stop test is evaluated on
+// the committed ones in order.  Every committed state is the one the ordinary
+// iteration computes, bit for bit.
+// ---------------------------------------------------------------------------
 template <int CONN>
 __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Geo& g = P.s.g;
-    const int B = g.B, F = g.F;
-    const int tid = threadIdx.x, NT = blockDim.x;
+    const int B = g.B, F = g.F, NH = P.NH;
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
     const int k = blockIdx.x;                  // gridDim.x == K
     constexpr int nh = CONN / 2;
     Ctrl* c = P.s.ctrl;
@@ -1187,17 +1263,34 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
     int* capsum = reinterpret_cast<int*>(C64 + B);
     uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
-    double* yS = reinterpret_cast<double*>(smem + ((solver_smem_bytes(CONN, B) + 15) & ~(size_t)15));
-    double* aS = yS + F;
-    int* resW = reinterpret_cast<int*>(aS + F);
-    int* cs0 = resW + CONN * B;
-    int* Us = cs0 + B;
-    uint8_t* lab = reinterpret_cast<uint8_t*>(Us + B);
+    const ResidentLayout L = resident_layout(CONN, B, F, NH);
+    double* yS = reinterpret_cast<double*>(smem + L.yS);
+    double* aS = reinterpret_cast<double*>(smem + L.aS);
+    int* resW = reinterpret_cast<int*>(smem + L.resW);
+    int* cs0 = reinterpret_cast<int*>(smem + L.cs0);
+    int* Us = reinterpret_cast<int*>(smem + L.Us);
+    int16_t* fl = reinterpret_cast<int16_t*>(smem + L.fl);   // face slot -> local pixel
+    uint8_t* lab = smem + L.lab;
+    // run-ahead window arrays: allocated (and touched) only when P.window
+    double* yS0 = reinterpret_cast<double*>(smem + L.yS0);
+    double* aS0 = reinterpret_cast<double*>(smem + L.aS0);
+    double* hy = reinterpret_cast<double*>(smem + L.hy);
+    double* ha = reinterpret_cast<double*>(smem + L.ha);
+    double* rloc = reinterpret_cast<double*>(smem + L.rloc);
+    int* Gf = reinterpret_cast<int*>(smem + L.Gf);
+    int* hG = reinterpret_cast<int*>(smem + L.hG);
+    int* hw = reinterpret_cast<int*>(smem + L.hw);
+    int16_t* hs = reinterpret_cast<int16_t*>(smem + L.hs);
+    uint8_t* hl = smem + L.hl;
+    uint8_t* labw = smem + L.labw;
+    __shared__ double part[128];
+
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
     const int bw = g.bw, pl = g.bh * g.bw;
     unsigned long long imask = 0;
+    unsigned fmask = 0;                          // bit q: own node q is a face pixel
     // one-time load of the owned block
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v >= B) continue;
@@ -1214,15 +1307,35 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
             if (d < nh) resW[d * B + v] = in ? P.s.Wl[(long long)d * g.N + gi] : 0;
         }
         imask |= (unsigned long long)m << (8 * q);
+        if (P.s.faceIndex[v] >= 0) fmask |= 1u << q;
         Us[v] = P.s.U[gi];
         lab[v] = P.t0 == 0 ? 0 : __ldcg(&P.s.yhat[gi]);
     }
     for (int f = tid; f < F; f += NT) {
         yS[f] = __ldcg(&P.s.yF[(long long)k * F + f]);
         aS[f] = __ldcg(&P.s.aF[(long long)k * F + f]);
+        fl[f] = P.s.faceLocal[f];
     }
+    if (P.window) {
+        // cross-edge weights and halo slots of the face slots, -1 where the
+        // neighbour lies outside the grid
+        for (int i = tid; i < CONN * F; i += NT) {
+            const int d = i / F, f = i % F;
+            int kn, ln, fn;
+            int w = 0, slot = -1;
+            if (halo_decode(g, P.s.halo[i], kz, ky, kx, kn, ln, fn)) {
+                const long long gi = (long long)k * B + P.s.faceLocal[f];
+                w = (d < nh) ? P.s.Wl[(long long)d * g.N + gi]
+                             : P.s.Wl[(long long)(d - nh) * g.N + (long long)kn * B + ln];
+                slot = P.hslot[i];
+            }
+            hw[i] = w;
+            hs[i] = (int16_t)slot;
+        }
+    }
+    if (blockIdx.x == 0 && tid == 0) c->thaw = 0x7fffffff;
     __syncthreads();
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
         if (v >= B) continue;
@@ -1242,33 +1355,20 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     }
     __syncthreads();
 
-    double mu = P.mu_start;
-    int t = P.t0, conv = 0;
-    unsigned nbar = 0;
-    bool pending = false;   // the previous iteration's closing barrier: arrived, wait still due
-    for (int j = 0; j < P.n; ++j) {
-        const int tn = P.t0 + j + 1;
-        const bool first = (tn == 1);
-        const double m1024 = __dmul_rn(1024.0, mu);
-        const double h = __dmul_rn(m1024, 0.5);
-        const int int_test = h < 4503599627370496.0 ? 1 : 0;   // 2^52
-        const long long H = int_test ? (long long)floor(h) : 0;
-        const long long c0 = clock64();
-        // Build, part 1: n-links and interior unaries from this CTA's shared
-        // memory only.  It overlaps the previous iteration's closing barrier
-        // and is thrown away if that iteration's stop test holds.
-#pragma unroll
+    // Build of iteration t (first = t is 1): n-links and interior unaries from
+    // shared memory; face unaries with the halo y from L2 (hy == nullptr) or
+    // from the window's halo copy.
+    auto build = [&](bool first, double m1024, int int_test, long long H, bool local) {
+#pragma unroll 1
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
             if (v >= B) continue;
-#pragma unroll
-            for (int d = 0; d < CONN; ++d) res[d * B + v] = resW[d * B + v];
             const int cs = cs0[v];
             capsum[v] = cs;
             st[v] = FREE;
             const long long Ui = Us[v];
             long long cv = Ui;
-            if (!first && P.s.faceIndex[v] < 0) {
+            if (!first && !((fmask >> q) & 1u)) {
                 const int yh = lab[v];
                 const long long T = yh ? Ui - H : Ui + H;
                 if (int_test && (yh ? (T < -(long long)cs) : (T >= (long long)cs))) cv = T;
@@ -1276,42 +1376,263 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
             }
             C64[v] = cv;
         }
-        if (pending) {
-            if (!grid_wait(c, gridDim.x, nbar, P.spin_limit)) break;
-            pending = false;
-            const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[t]));
-            if (!(__dsqrt_rn(r2) > P.s.eps)) { conv = 1; break; }
-        }
-        t = tn;
-        // Build, part 2: face pixels, with the neighbours' face y from L2
         if (!first) {
             for (int f = tid; f < F; f += NT) {
-                const int v = P.s.faceLocal[f];
-                C64[v] = face_cap_core<CONN>(g, (long long)Us[v], yS[f], aS[f], P.s.Wl, P.s.yF, P.s.halo, k,
+                const int v = fl[f];
+                long long cv;
+                if (!local) {
+                    cv = face_cap_core<CONN>(g, (long long)Us[v], yS[f], aS[f], P.s.Wl, P.s.yF, P.s.halo, k,
                                              kz, ky, kx, v, f, m1024);
+                } else {
+                    const double yv = yS[f], av = aS[f];
+                    double sv = (double)Us[v];
+#pragma unroll
+                    for (int d = 0; d < CONN; ++d) {
+                        const int hsl = hs[d * F + f];
+                        if (hsl >= 0)
+                            sv = __dadd_rn(sv, __dmul_rn((double)hw[d * F + f], __dsub_rn(yv, hy[hsl])));
+                    }
+                    sv = __dadd_rn(sv, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
+                    sv = fmin(fmax(sv, -CLAMP62), CLAMP62);
+                    cv = __double2ll_rn(sv);
+                }
+                C64[v] = cv;
             }
         }
         __syncthreads();
-        cut_block<CONN>(P.s, k, smem, bw, pl, imask, c0, lab);
-        const long long c1 = clock64();
-        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
-        const long long c2 = clock64();
-        update_block_resident<CONN>(P.u, k, t, mu, lab, yS, aS);
-        const long long c3 = clock64();
-        if (threadIdx.x == 0) {
-            atomicAdd(&c->pcyc[0], (unsigned long long)(c1 - c0));
-            atomicAdd(&c->pcyc[1], (unsigned long long)(c2 - c1));
-            atomicAdd(&c->pcyc[2], (unsigned long long)(c3 - c2));
+    };
+    // Intra-block n-links into the solver's residual array (needed only when
+    // some node is not forced).
+    auto copy_res = [&]() {
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v >= B) continue;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) res[d * B + v] = resW[d * B + v];
         }
-        mu = __dmul_rn(mu, P.mu_fact);
-        if (j == P.n - 1) {
-            if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
+        __syncthreads();
+    };
+    // When every node is forced in the first folding round (C >= its n-link
+    // sum: label 0; C < minus it: label 1) the labels are those cut_block
+    // returns, without the max-flow; out receives them.  false: some node is
+    // free and cut_block must run.
+    auto fast_forced = [&](uint8_t* out) -> bool {
+        int fr = 0;
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v >= B) continue;
+            const long long cv = C64[v], cs = cs0[v];
+            if (!(cv >= cs) && !(cv < -cs)) fr = 1;
+        }
+        if (__syncthreads_or(fr)) return false;
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v >= B) continue;
+            out[v] = C64[v] >= (long long)cs0[v] ? 0 : 1;
+        }
+        return true;
+    };
+    // Fixed-order block sum of per-face-slot values computed by fn(f) (the
+    // order update_block uses for r_k^2).
+    auto face_sum = [&](auto fn) -> double {
+        const int nchunks = (F + 31) >> 5;
+        for (int ch = wid; ch < nchunks; ch += nw) {
+            const int f = ch * 32 + lane;
+            double d2 = f < F ? fn(f) : 0.0;
+            for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+            if (lane == 0) part[ch] = d2;
+        }
+        __syncthreads();
+        double t2 = 0.0;
+        for (int ch = 0; ch < nchunks; ++ch) t2 = __dadd_rn(t2, part[ch]);
+        __syncthreads();
+        return t2;
+    };
+    auto iter_consts = [&](double mu, double& m1024, int& int_test, long long& H) {
+        m1024 = __dmul_rn(1024.0, mu);
+        const double h = __dmul_rn(m1024, 0.5);
+        int_test = h < 4503599627370496.0 ? 1 : 0;   // 2^52
+        H = int_test ? (long long)floor(h) : 0;
+    };
+
+    const int tlimit = P.t0 + P.n;
+    double mu = P.mu_start;
+    int t = P.t0, conv = 0;
+    unsigned nbar = 0;
+    bool need_normal = true, failed = false;
+    while (t < tlimit && !failed) {
+        if (need_normal || !P.window) {
+            // ordinary iteration t+1
+            ++t;
+            double m1024; int int_test; long long H;
+            iter_consts(mu, m1024, int_test, H);
+            const long long c0 = clock64();
+            build(t == 1, m1024, int_test, H, false);
+            if (t > 1 && fast_forced(lab)) {
+#pragma unroll 1
+                for (int q = 0; q < NPTMAX; ++q) {
+                    int v = tid + q * NT;
+                    if (v < B) P.s.yhat[(long long)k * B + v] = lab[v];
+                }
+            } else {
+                copy_res();
+                cut_block<CONN>(P.s, k, smem, bw, pl, imask, c0, lab);
+            }
+            const long long c1 = clock64();
+            if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
+            const long long c2 = clock64();
+            update_block_resident<CONN>(P.u, k, t, mu, lab, yS, aS);
+            const long long c3 = clock64();
+            mu = __dmul_rn(mu, P.mu_fact);
+            if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
+            if (tid == 0) {
+                atomicAdd(&c->pcyc[0], (unsigned long long)(c1 - c0));
+                atomicAdd(&c->pcyc[1], (unsigned long long)(c2 - c1));
+                atomicAdd(&c->pcyc[2], (unsigned long long)(c3 - c2));
+            }
             const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[t]));
-            conv = !(__dsqrt_rn(r2) > P.s.eps);
-        } else {
-            grid_arrive(c, nbar);
-            pending = true;
+            if (!(__dsqrt_rn(r2) > P.s.eps)) { conv = 1; break; }
+            need_normal = (t == 1);
+            continue;
         }
+        // ---- run-ahead window from iteration tw = t ----
+        const int tw = t;
+        // Once labels are frozen every block residual shrinks by 1/mu_fact per
+        // iteration, so the stop test is expected about ln(r/eps)/ln(mu_fact)
+        // iterations on; the window is cut there (plus one) instead of running
+        // WMAX iterations past the stop.  This only sizes the window; what is
+        // committed is decided by the exact stop test below.
+        int Wn = min(WMAX, tlimit - tw);
+        {
+            const double r_tw = __dsqrt_rn(__longlong_as_double((long long)__ldcg(&c->r2max[tw])));
+            if (r_tw > P.s.eps && P.mu_fact > 1.0) {
+                const double n_pred = ceil(log(r_tw / P.s.eps) / log(P.mu_fact));
+                if (n_pred + 1.0 < (double)Wn) Wn = max(1, (int)n_pred + 1);
+            }
+        }
+        const long long c0 = clock64();
+        for (int f = tid; f < F; f += NT) { yS0[f] = yS[f]; aS0[f] = aS[f]; }
+        // own cross sums G (constant while labels do not move)
+        for (int f = tid; f < F; f += NT) {
+            const int v = fl[f];
+            int G = 0;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int kn, ln, fn;
+                if (hs[d * F + f] >= 0 && halo_decode(g, P.s.halo[d * F + f], kz, ky, kx, kn, ln, fn))
+                    G += hw[d * F + f] * ((int)lab[v] - (int)__ldcg(&P.s.yhat[(long long)kn * B + ln]));
+            }
+            Gf[f] = G;
+        }
+        // halo pixels: state, label and their own cross sums
+        for (int h = tid; h < NH; h += NT) {
+            int kn, ln, fn;
+            if (!halo_decode(g, P.hinfo[h], kz, ky, kx, kn, ln, fn)) continue;
+            const int knz = kn / (g.nby * g.nbx), kny = (kn / g.nbx) % g.nby, knx = kn % g.nbx;
+            hy[h] = __ldcg(&P.s.yF[(long long)kn * F + fn]);
+            ha[h] = __ldcg(&P.s.aF[(long long)kn * F + fn]);
+            const int yh = __ldcg(&P.s.yhat[(long long)kn * B + ln]);
+            hl[h] = (uint8_t)yh;
+            int G = 0;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int km, lm, fm;
+                if (halo_decode(g, P.s.halo[d * F + fn], knz, kny, knx, km, lm, fm)) {
+                    const long long gj = (long long)kn * B + ln;
+                    const int w = (d < nh) ? P.s.Wl[(long long)d * g.N + gj]
+                                           : P.s.Wl[(long long)(d - nh) * g.N + (long long)km * B + lm];
+                    G += w * (yh - (int)__ldcg(&P.s.yhat[(long long)km * B + lm]));
+                }
+            }
+            hG[h] = G;
+        }
+        __syncthreads();
+        double muw = mu;
+        int thaw_s = Wn + 1;
+        long long wc[5] = {0, 0, 0, 0, 0};
+        const long long cs_start = clock64();
+        for (int sidx = 1; sidx <= Wn; ++sidx) {
+            double m1024; int int_test; long long H;
+            iter_consts(muw, m1024, int_test, H);
+            long long ta = clock64();
+            build(false, m1024, int_test, H, true);
+            long long tb = clock64();
+            if (!fast_forced(labw)) {
+                copy_res();
+                cut_block<CONN>(P.s, k, smem, bw, pl, imask, clock64(), labw, false);
+            }
+            long long tc = clock64();
+            int moved = 0;
+#pragma unroll 1
+            for (int q = 0; q < NPTMAX; ++q) {
+                int v = tid + q * NT;
+                if (v < B && labw[v] != lab[v]) moved = 1;
+            }
+            if (__syncthreads_or(moved)) { thaw_s = sidx; break; }
+            long long td = clock64();
+            const double r2 = face_sum([&](int f) {
+                return face_step(lab[fl[f]], Gf[f], muw, yS[f], aS[f]);
+            });
+            if (tid == 0) rloc[sidx - 1] = r2;
+            long long te = clock64();
+            for (int h = tid; h < NH; h += NT) {
+                double yv = hy[h], av = ha[h];
+                face_step(hl[h], hG[h], muw, yv, av);
+                hy[h] = yv;
+                ha[h] = av;
+            }
+            muw = __dmul_rn(muw, P.mu_fact);
+            __syncthreads();
+            long long tf = clock64();
+            wc[0] += tb - ta; wc[1] += tc - tb; wc[2] += td - tc; wc[3] += te - td; wc[4] += tf - te;
+        }
+        if (tid == 0) {
+            for (int i = 0; i < 5; ++i) atomicAdd(&c->wcyc[i], (unsigned long long)wc[i]);
+            atomicAdd(&c->wcyc[5], (unsigned long long)(cs_start - c0));
+        }
+        // resolution: earliest moved iteration over all blocks, committed residuals
+        if (tid == 0) atomicMin(&c->thaw, tw + thaw_s);
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
+        const int tstar = __ldcg(&c->thaw);
+        const int tvalid = min(tstar - 1, tw + Wn);
+        if (tid == 0)
+            for (int tt = tw + 1; tt <= tvalid; ++tt)
+                atomicMax(&c->r2max[tt], (unsigned long long)__double_as_longlong(rloc[tt - tw - 1]));
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
+        if (blockIdx.x == 0 && tid == 0) {
+            c->thaw = 0x7fffffff;
+            c->windows += 1;
+            c->window_iters += tvalid - tw;
+        }
+        int tend = tvalid;
+        for (int tt = tw + 1; tt <= tvalid; ++tt) {
+            const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[tt]));
+            if (!(__dsqrt_rn(r2) > P.s.eps)) { tend = tt; conv = 1; break; }
+        }
+        // own face state at tend: replay the committed iterations from the window start
+        for (int f = tid; f < F; f += NT) {
+            double yv = yS0[f], av = aS0[f];
+            double m = mu;
+            const int yh = lab[fl[f]];
+            for (int tt = tw + 1; tt <= tend; ++tt) {
+                face_step(yh, Gf[f], m, yv, av);
+                m = __dmul_rn(m, P.mu_fact);
+            }
+            yS[f] = yv;
+            aS[f] = av;
+            P.u.yF[(long long)k * F + f] = yv;
+            P.u.aF[(long long)k * F + f] = av;
+        }
+        for (int tt = tw + 1; tt <= tend; ++tt) mu = __dmul_rn(mu, P.mu_fact);
+        t = tend;
+        const long long c1 = clock64();
+        if (tid == 0) atomicAdd(&c->pcyc[3], (unsigned long long)(c1 - c0));
+        if (conv) break;
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
+        need_normal = (tstar <= tw + Wn);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->iters_done = t;

@@ -46,7 +46,9 @@ class dope_stats(ctypes.Structure):
                 ("free_nodes_total", ctypes.c_int64), ("rmax_last", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("bfs_levels_total", ctypes.c_int64),
                 ("bfs_levels_max", ctypes.c_int), ("fold_rounds_max", ctypes.c_int),
-                ("phase_cycles", ctypes.c_double * 4), ("loop_cycles", ctypes.c_double * 4)]
+                ("phase_cycles", ctypes.c_double * 4), ("loop_cycles", ctypes.c_double * 4),
+                ("windows", ctypes.c_int), ("window_iterations", ctypes.c_int),
+                ("window_cycles", ctypes.c_double * 6)]
 
 
 class dope_profile(ctypes.Structure):
@@ -269,6 +271,7 @@ def dope_get_stats(ctx):
     out = {f: getattr(s, f) for f, _ in s._fields_}
     out["phase_cycles"] = list(s.phase_cycles)
     out["loop_cycles"] = list(s.loop_cycles)
+    out["window_cycles"] = list(s.window_cycles)
     return out
 
 

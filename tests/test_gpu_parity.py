@@ -255,15 +255,40 @@ def test_input_errors(dp):
 
 
 @pytest.mark.parametrize("grid,conn,block,lam", [((128, 128), 8, (32, 32), 8.0), ((32, 48, 48), 6, (8, 16, 16), 3.0),
-                                                 ((96, 96), 4, (16, 16), 2.0)])
-def test_launch_modes_identical(dp, grid, conn, block, lam):
-    """The persistent single-launch path and the per-iteration launches give
-    bit-identical labels, energies, iteration counts and residual traces."""
+                                                 ((96, 96), 4, (16, 16), 2.0), ((256, 256), 8, (32, 32), 16.0)])
+@pytest.mark.parametrize("mode", [0, 2])
+def test_launch_modes_identical(dp, grid, conn, block, lam, mode):
+    """The persistent single-launch paths (mode 0 with run-ahead windows, mode 2
+    without) and the per-iteration launches (mode 1) give bit-identical labels,
+    energies, iteration counts, residual traces and final states."""
     d = inputs.random_instance(grid, conn, block, lam=lam, seed=21)
-    a = dp.Dope.from_instance(d, launch_mode=0)
+    a = dp.Dope.from_instance(d, launch_mode=mode)
     b = dp.Dope.from_instance(d, launch_mode=1)
     ra, rb = a.solve(), b.solve()
     assert np.array_equal(ra[0], rb[0]) and ra[1:] == rb[1:]
     assert np.array_equal(a.trace(), b.trace())
     sa, sb = a.get_state(), b.get_state()
     assert np.array_equal(sa["y"], sb["y"]) and np.array_equal(sa["a"], sb["a"])
+    assert sa["mu"] == sb["mu"] and sa["t"] == sb["t"]
+
+
+@pytest.mark.parametrize("lam", [1.0, 16.0])
+def test_windows_resume_and_iterate(dp, lam):
+    """Iterating in pieces (checkpoint / resume through get_state / set_state)
+    reaches the same state as one solve, with run-ahead windows on."""
+    d = inputs.ellipses_rgb(size=256, lam=lam)
+    a = dp.Dope.from_instance(d)
+    lab, E, it = a.solve()
+    sa = a.get_state()
+    assert it >= 2
+    b = dp.Dope.from_instance(d)
+    b.reset()
+    done, conv = b.iterate(1)
+    st = b.get_state()
+    c2 = dp.Dope.from_instance(d)
+    c2.set_state(st["y"], st["a"], st["yhat"], st["mu"], st["t"])
+    done, conv = c2.iterate(1000)
+    sc = c2.get_state()
+    assert conv and done == it
+    assert np.array_equal(sc["yhat"], lab)
+    assert np.array_equal(sc["y"], sa["y"]) and np.array_equal(sc["a"], sa["a"])
