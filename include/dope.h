@@ -70,7 +70,9 @@ typedef struct dope_ctx dope_ctx;
  * 3-D grids (the paper's settings, Section 3), mu_fact = 1.05, eps = 1e-3,
  * max_iter = 1000, relabel_period = 0 (automatic), threads = 0 (automatic),
  * max_pulses = 0 (automatic: 64 * block volume + 4096), fold_rounds = 0
- * (automatic: 64), launch_mode = 0 (persistent, when the device can run it). */
+ * (automatic: 3), launch_mode = 0 (persistent, when the device can run it).
+ * relabel_period 0 means 8.  The knobs change speed only, never results: the
+ * block cut is exact for any of them. */
 typedef struct {
     double mu0;
     double mu_fact;

@@ -499,7 +499,7 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
     if (!(c->p.mu_fact > 0.0)) c->p.mu_fact = 1.05;
     if (!(c->p.eps >= 0.0)) c->p.eps = 1e-3;
     if (c->p.max_iter <= 0) c->p.max_iter = 1000;
-    if (c->p.relabel_period <= 0) c->p.relabel_period = 16;
+    if (c->p.relabel_period <= 0) c->p.relabel_period = 8;
     if (c->p.max_pulses <= 0) c->p.max_pulses = (int)(64 * B + 4096);
     if (c->p.fold_rounds <= 0) c->p.fold_rounds = MAX_FOLD_ROUNDS;
 
@@ -578,7 +578,7 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
         return DOPE_EINVAL;
     }
     c->threads = threads;
-    c->smem = (int)((connectivity + 3) * 4 * B + B);
+    c->smem = (int)solver_smem_bytes(connectivity, (int)B);
 
     int rc = DOPE_OK;
     auto A = [&](void** ptr, size_t bytes) {
@@ -1083,7 +1083,7 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     if (!(prm.mu_fact > 0.0)) prm.mu_fact = 1.05;
     if (!(prm.eps >= 0.0)) prm.eps = 1e-3;
     if (prm.max_iter <= 0) prm.max_iter = 1000;
-    if (prm.relabel_period <= 0) prm.relabel_period = 16;
+    if (prm.relabel_period <= 0) prm.relabel_period = 8;
     if (prm.max_pulses <= 0) prm.max_pulses = (int)(64 * B + 4096);
     if (prm.fold_rounds <= 0) prm.fold_rounds = MAX_FOLD_ROUNDS;
     int threads = prm.threads;
@@ -1139,7 +1139,7 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     int16_t* faceLocal = reinterpret_cast<int16_t*>(sb + o_fl);
     int* halo = reinterpret_cast<int*>(sb + o_halo);
     cudaStream_t st = S(stream);
-    const int smem = (int)((connectivity + 3) * 4 * B + B);
+    const int smem = (int)solver_smem_bytes(connectivity, (int)B);
 
     // everything that must start at zero: the control word and the trace
     CK(cudaMemsetAsync(ctrl, 0, ctrl_bytes, st));

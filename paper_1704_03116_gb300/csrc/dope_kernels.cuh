@@ -22,8 +22,18 @@ namespace dope {
 
 constexpr int NPTMAX = 8;          // nodes per thread in the block solver
 constexpr int FREE = 0, FIX0 = 1, FIX1 = 2;
-constexpr int MAX_FOLD_ROUNDS = 64;
+constexpr int MAX_FOLD_ROUNDS = 3;    // default bound on exact-folding rounds
 constexpr double CLAMP62 = 4611686018427387904.0;   // 2^62
+
+// Block-solver shared memory: res int32 [conn][B], R1 8 B [B], R2 4 B [B],
+// st uint8 [B], then (aligned to 4 B) the bit-parallel BFS words: per-direction
+// residual masks [conn][W], seeds / frontier buffers [3][W], W = ceil(B / 32).
+__host__ __device__ inline size_t solver_bits_offset(int conn, int B) {
+    return ((size_t)(conn + 3) * 4 * B + B + 3) & ~(size_t)3;
+}
+__host__ __device__ inline size_t solver_smem_bytes(int conn, int B) {
+    return solver_bits_offset(conn, B) + 4 * (size_t)(conn + 3) * ((B + 31) / 32);
+}
 
 struct Geo {
     int D, H, W;            // grid (D = 1 for 2-D)
@@ -309,42 +319,86 @@ __device__ __forceinline__ long long interior_cap(long long Ui, int yh, double m
 //    sink side, i.e. the pointwise-minimal minimiser; label 1 = sink side.
 // ---------------------------------------------------------------------------
 
-// Backward BFS from t over residual edges into h (1 = has residual to t,
-// HMAX = cannot reach t).  Returns whether any free node with excess can
+// Backward BFS from t, bit-parallel.  Every node is a bit of W = ceil(B/32)
+// words; each direction's residual edges (res > 0) become a mask built with
+// warp ballots, and one warp expands the frontier level by level: the nodes
+// that can step into the frontier along direction d are E_d & (F shifted by
+// the direction's local offset).  The distances are the exact BFS distances
+// (1 = residual capacity to t, HMAX = cannot reach t), the same heights the
+// level-synchronous search gives, at one warp-synchronisation per level
+// instead of a block barrier.  Returns whether a free node with excess can
 // still reach t.
 template <int CONN>
-__device__ __forceinline__ int bfs_from_sink(const int* __restrict__ res, const int* __restrict__ e,
-                                             int16_t* h, const uint8_t* st, int bw, int pl,
-                                             unsigned long long imask, int B, int HMAX, int tid,
-                                             int NT, int& levels) {
-#pragma unroll 1
-    for (int q = 0; q < NPTMAX; ++q) {
-        int v = tid + q * NT;
-        if (v < B) h[v] = (st[v] == FREE && e[v] < 0) ? (int16_t)1 : (int16_t)HMAX;
+__device__ __forceinline__ int bfs_bits(const int* __restrict__ res, const int* __restrict__ e, int16_t* h,
+                                        const uint8_t* st, uint32_t* bits, int bw, int pl, int B,
+                                        int HMAX, int tid, int NT, int& levels) {
+    const int W = (B + 31) >> 5;
+    uint32_t* E = bits;                  // [CONN][W]
+    uint32_t* Fa = bits + CONN * W;      // frontier, two buffers
+    uint32_t* Fb = Fa + W;
+    const int lane = tid & 31;
+    for (int base = 0; base < B; base += NT) {
+        const int v = base + tid;
+        const bool in = v < B;
+        const int wi = v >> 5;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const unsigned m = __ballot_sync(0xffffffffu, in && res[d * B + v] > 0);
+            if (lane == 0 && wi < W) E[d * W + wi] = m;
+        }
+        const bool seed = in && st[v] == FREE && e[v] < 0;
+        const unsigned ms = __ballot_sync(0xffffffffu, seed);
+        if (lane == 0 && wi < W) Fa[wi] = ms;
+        if (in) h[v] = seed ? (int16_t)1 : (int16_t)HMAX;
     }
     __syncthreads();
-    int level = 1;
-    for (; level < HMAX; ++level) {
-        int ch = 0;
-#pragma unroll 1
-        for (int q = 0; q < NPTMAX; ++q) {
-            int v = tid + q * NT;
-            if (v < B && h[v] == HMAX && st[v] == FREE) {
-                const unsigned m = (unsigned)(imask >> (8 * q)) & 0xffu;
+    int lv = 1;
+    if (tid < 32) {
+        constexpr int MAXW = 4;          // W <= 128 (B <= 4096)
+        uint32_t vis[MAXW];
+#pragma unroll
+        for (int s2 = 0; s2 < MAXW; ++s2) {
+            const int i = lane + 32 * s2;
+            vis[s2] = i < W ? Fa[i] : 0u;
+        }
+        uint32_t* F = Fa;
+        uint32_t* Nf = Fb;
+        while (lv < HMAX - 1) {
+            unsigned any = 0;
+#pragma unroll
+            for (int s2 = 0; s2 < MAXW; ++s2) {
+                const int i = lane + 32 * s2;
+                if (i >= W) continue;
+                uint32_t nw = 0;
 #pragma unroll
                 for (int d = 0; d < CONN; ++d) {
-                    if (!((m >> d) & 1)) continue;
-                    if (res[d * B + v] > 0 && h[v + dir_lofs<CONN>(d, bw, pl)] == level) {
-                        h[v] = (int16_t)(level + 1);
-                        ch = 1;
-                        break;
-                    }
+                    const int o = dir_lofs<CONN>(d, bw, pl);   // G[v] = F[v + o]
+                    const int a = o >> 5, b = o & 31;
+                    const int i0 = i + a, i1 = i + a + 1;
+                    const uint32_t lo = (i0 >= 0 && i0 < W) ? F[i0] : 0u;
+                    const uint32_t hi = (b != 0 && i1 >= 0 && i1 < W) ? F[i1] : 0u;
+                    const uint32_t G = b ? ((lo >> b) | (hi << (32 - b))) : lo;
+                    nw |= E[d * W + i] & G;
+                }
+                nw &= ~vis[s2];
+                Nf[i] = nw;
+                vis[s2] |= nw;
+                any |= nw;
+                uint32_t m = nw;
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    h[32 * i + j] = (int16_t)(lv + 1);
+                    m &= m - 1;
                 }
             }
+            if (!__any_sync(0xffffffffu, any != 0)) break;
+            ++lv;
+            __syncwarp();
+            uint32_t* tmp = F; F = Nf; Nf = tmp;
         }
-        if (!__syncthreads_or(ch)) break;
     }
-    levels += level;
+    levels += lv;
+    __syncthreads();
     int act = 0;
 #pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
@@ -464,6 +518,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
     int16_t* hA = reinterpret_cast<int16_t*>(capsum);
     int16_t* hB = hA + B;
     uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + solver_bits_offset(CONN, B));
     const long long c_built = clock64();
     long long c_bfs = 0;
     int levels = 0, bfs_max = 0;
@@ -548,7 +603,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
         // 3. push-relabel (phase 1: maximum preflow)
         long long cb = clock64();
         int lv0 = levels;
-        int active = bfs_from_sink<CONN>(res, e, hc, st, bw, pl, imask, B, HMAX, tid, NT, levels);
+        int active = bfs_bits<CONN>(res, e, hc, st, bits, bw, pl, B, HMAX, tid, NT, levels);
         bfs_max = max(bfs_max, levels - lv0);
         c_bfs += clock64() - cb;
         const int period = A.relabel_period;
@@ -619,7 +674,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
             if (active && period > 0 && (pulses % period) == 0) {
                 cb = clock64();
                 lv0 = levels;
-                active = bfs_from_sink<CONN>(res, e, hc, st, bw, pl, imask, B, HMAX, tid, NT, levels);
+                active = bfs_bits<CONN>(res, e, hc, st, bits, bw, pl, B, HMAX, tid, NT, levels);
                 bfs_max = max(bfs_max, levels - lv0);
                 c_bfs += clock64() - cb;
             }
@@ -627,7 +682,7 @@ __device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned ch
         // 4. canonical cut
         cb = clock64();
         lv0 = levels;
-        bfs_from_sink<CONN>(res, e, hc, st, bw, pl, imask, B, HMAX, tid, NT, levels);
+        bfs_bits<CONN>(res, e, hc, st, bits, bw, pl, B, HMAX, tid, NT, levels);
         bfs_max = max(bfs_max, levels - lv0);
         c_bfs += clock64() - cb;
     }
@@ -1120,10 +1175,6 @@ __global__ void __launch_bounds__(512, 2) k_admm_persistent(PersistArgs P) {
 //   Us      int32 [B]        unaries
 //   lab     uint8 [B]        labels
 // ---------------------------------------------------------------------------
-__host__ __device__ inline size_t solver_smem_bytes(int conn, int B) {
-    return (size_t)(conn + 3) * 4 * B + B;
-}
-
 // Byte offsets of the resident kernel's shared-memory arrays.  The host sizes
 // the launch with `.resident_end` / `.window_end` and the kernel takes every
 // pointer from here, so the two cannot disagree.
