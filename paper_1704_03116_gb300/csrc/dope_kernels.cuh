@@ -1170,7 +1170,7 @@ __global__ void __launch_bounds__(512, 2) k_admm_persistent(PersistArgs P) {
 //
 // Extra shared memory after the solver's (aligned to 16 B):
 //   yS, aS  f64 [F]          face y and a of the owned block
-//   resW    int32 [CONN][B]  intra-block n-link capacities
+//   resW    int32 [CONN/2][B] intra-block n-link capacities, forward directions
 //   cs0     int32 [B]        their sums
 //   Us      int32 [B]        unaries
 //   lab     uint8 [B]        labels
@@ -1180,8 +1180,12 @@ __global__ void __launch_bounds__(512, 2) k_admm_persistent(PersistArgs P) {
 // pointer from here, so the two cannot disagree.
 struct ResidentLayout {
     size_t yS, aS, resW, cs0, Us, fl, lab, resident_end;                 // always present
-    size_t yS0, aS0, hy, ha, rloc, Gf, hG, hw, hs, hl, labw, window_end;  // run-ahead windows
+    size_t yS0, aS0, hy, ha, rloc, Gf, hG, hw, hs, hl, labw;              // run-ahead windows
+    size_t cI, cB, cW, cE, hB;                                             // window certificates
+    size_t ring, window_end;                                               // last RING own states
 };
+
+constexpr int RING = 4;    // own face states kept for short rollbacks
 
 constexpr int WMAX = 64;   // most iterations per run-ahead window
 
@@ -1190,7 +1194,7 @@ __host__ __device__ inline ResidentLayout resident_layout(int conn, int B, int F
     size_t o = (solver_smem_bytes(conn, B) + 15) & ~(size_t)15;
     L.yS = o;   o += 8 * (size_t)F;
     L.aS = o;   o += 8 * (size_t)F;
-    L.resW = o; o += 4 * (size_t)conn * B;
+    L.resW = o; o += 4 * (size_t)(conn / 2) * B;     // forward planes only
     L.cs0 = o;  o += 4 * (size_t)B;
     L.Us = o;   o += 4 * (size_t)B;
     L.fl = o;   o += 2 * (size_t)F;
@@ -1208,6 +1212,14 @@ __host__ __device__ inline ResidentLayout resident_layout(int conn, int B, int F
     L.hs = o;   o += 2 * (size_t)conn * F;
     L.hl = o;   o += (size_t)NH;
     L.labw = o; o += (size_t)B;
+    o = (o + 7) & ~(size_t)7;
+    L.cI = o;   o += 8 * (size_t)F;
+    L.cB = o;   o += 4 * (size_t)F;
+    L.cW = o;   o += 4 * (size_t)F;
+    L.cE = o;   o += 4 * (size_t)F;
+    L.hB = o;   o += 4 * (size_t)NH;
+    o = (o + 7) & ~(size_t)7;
+    L.ring = o; o += 16 * (size_t)RING * F;
     L.window_end = o;
     return L;
 }
@@ -1334,6 +1346,13 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     int16_t* hs = reinterpret_cast<int16_t*>(smem + L.hs);
     uint8_t* hl = smem + L.hl;
     uint8_t* labw = smem + L.labw;
+    long long* cI = reinterpret_cast<long long*>(smem + L.cI);   // certificate: exact integer part
+    float* cB = reinterpret_cast<float*>(smem + L.cB);            // bound on |a|, |y - yhat|
+    float* cW = reinterpret_cast<float*>(smem + L.cW);            // sum_j w_j (B_i + B_j)
+    float* cE = reinterpret_cast<float*>(smem + L.cE);            // rounding allowance
+    float* hB = reinterpret_cast<float*>(smem + L.hB);            // bound for halo pixels
+    double* ring = reinterpret_cast<double*>(smem + L.ring);      // [RING][2][F] own y, a
+    __shared__ long long s_tau;                                   // max interior |U| + n-link sum
     __shared__ double part[128];
 
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
@@ -1394,17 +1413,28 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         int cs = 0;
 #pragma unroll
         for (int d = 0; d < CONN; ++d) {
-            if (d < nh) {
-                cs += resW[d * B + v];
-            } else {
-                const int w = ((m >> d) & 1) ? resW[(d - nh) * B + v + dir_lofs<CONN>(d, bw, pl)] : 0;
-                resW[d * B + v] = w;
-                cs += w;
-            }
+            if (d < nh) cs += resW[d * B + v];
+            else if ((m >> d) & 1) cs += resW[(d - nh) * B + v + dir_lofs<CONN>(d, bw, pl)];
         }
         cs0[v] = cs;
     }
+    if (tid == 0) s_tau = 0;
     __syncthreads();
+    {   // interior pixels are forced to keep their label once 512 mu exceeds this
+        long long tmax = 0;
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v < B && !((fmask >> q) & 1u)) {
+                const long long u = Us[v];
+                const long long x = (u < 0 ? -u : u) + cs0[v] + 2;
+                tmax = x > tmax ? x : tmax;
+            }
+        }
+        if (tmax) atomicMax(&s_tau, tmax);
+    }
+    __syncthreads();
+    const long long tau_int = s_tau;
 
     // Build of iteration t (first = t is 1): n-links and interior unaries from
     // shared memory; face unaries with the halo y from L2 (hy == nullptr) or
@@ -1459,8 +1489,11 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         for (int q = 0; q < NPTMAX; ++q) {
             int v = tid + q * NT;
             if (v >= B) continue;
+            const unsigned m = (unsigned)(imask >> (8 * q)) & 0xffu;
 #pragma unroll
-            for (int d = 0; d < CONN; ++d) res[d * B + v] = resW[d * B + v];
+            for (int d = 0; d < CONN; ++d)
+                res[d * B + v] = d < nh ? resW[d * B + v]
+                               : (((m >> d) & 1) ? resW[(d - nh) * B + v + dir_lofs<CONN>(d, bw, pl)] : 0);
         }
         __syncthreads();
     };
@@ -1498,9 +1531,10 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         }
         __syncthreads();
         double t2 = 0.0;
-        for (int ch = 0; ch < nchunks; ++ch) t2 = __dadd_rn(t2, part[ch]);
+        if (tid == 0)
+            for (int ch = 0; ch < nchunks; ++ch) t2 = __dadd_rn(t2, part[ch]);
         __syncthreads();
-        return t2;
+        return t2;   // valid in thread 0
     };
     auto iter_consts = [&](double mu, double& m1024, int& int_test, long long& H) {
         m1024 = __dmul_rn(1024.0, mu);
@@ -1559,10 +1593,15 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         int Wn = min(WMAX, tlimit - tw);
         {
             const double r_tw = __dsqrt_rn(__longlong_as_double((long long)__ldcg(&c->r2max[tw])));
+            const double r_pr = tw >= 2 ? __dsqrt_rn(__longlong_as_double((long long)__ldcg(&c->r2max[tw - 1])))
+                                        : 0.0;
+            // the geometric regime shows as r_tw / r_{tw-1} = 1 / mu_fact
+            const bool geometric = r_pr > 0.0 && fabs(r_tw * P.mu_fact / r_pr - 1.0) < 1e-3;
             if (r_tw > P.s.eps && P.mu_fact > 1.0) {
                 const double n_pred = ceil(log(r_tw / P.s.eps) / log(P.mu_fact));
                 if (n_pred + 1.0 < (double)Wn) Wn = max(1, (int)n_pred + 1);
             }
+            if (!geometric) Wn = min(Wn, 16);
         }
         const long long c0 = clock64();
         for (int f = tid; f < F; f += NT) { yS0[f] = yS[f]; aS0[f] = aS[f]; }
@@ -1601,6 +1640,46 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
             hG[h] = G;
         }
         __syncthreads();
+        // Certificates (see the note on the frozen regime above the loop): with
+        // labels frozen, a_t = g / mu_t and y_t - yhat = a_{t-1} - g / mu_t in
+        // exact arithmetic (g = G / 1024), each computed step adding at most a
+        // few ulps (no accumulation, since a is reset to g / mu every step), so
+        //   B = |a_tw| + |y_tw - yhat| + 2 |g| / mu_tw + 2^-40
+        // bounds |a| and |y - yhat| for every state of the window.
+        const double inv_mu_tw = 1.0 / mu;   // 1 / mu of the window's first iteration (bounds only)
+        for (int h = tid; h < NH; h += NT) {
+            const double b = fabs(ha[h]) + fabs(hy[h] - (double)hl[h]) +
+                             2.0 * fabs((double)hG[h]) * 0.0009765625 * inv_mu_tw * (1.0 + 1e-12) +
+                             9.094947017729282e-13;   // 2^-40
+            hB[h] = __double2float_ru(b);
+        }
+        __syncthreads();
+        for (int f = tid; f < F; f += NT) {
+            const int v = fl[f];
+            const double b = fabs(aS[f]) + fabs(yS[f] - (double)lab[v]) +
+                             2.0 * fabs((double)Gf[f]) * 0.0009765625 * inv_mu_tw * (1.0 + 1e-12) +
+                             9.094947017729282e-13;
+            const float bf = __double2float_ru(b);
+            long long I = Us[v], wtot = 0;
+            float wsum = 0.f;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                const int hsl = hs[d * F + f];
+                if (hsl < 0) continue;
+                const int w = hw[d * F + f];
+                I += (long long)w * ((int)lab[v] - (int)hl[hsl]);
+                wsum = __fadd_ru(wsum, __fmul_ru((float)w, __fadd_ru(bf, hB[hsl])));
+                wtot += w;
+            }
+            cI[f] = I;
+            cB[f] = bf;
+            cW[f] = wsum;
+            // allowance for the computed value vs the exact one: 2^-40 (|I| + 3 sum w)
+            // here, plus 2^-40 * 2h per iteration below
+            cE[f] = __double2float_ru(9.094947017729282e-13 * ((double)llabs(I) + 3.0 * (double)wtot) *
+                                      (1.0 + 1e-12));
+        }
+        __syncthreads();
         double muw = mu;
         int thaw_s = Wn + 1;
         long long wc[5] = {0, 0, 0, 0, 0};
@@ -1609,25 +1688,52 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
             double m1024; int int_test; long long H;
             iter_consts(muw, m1024, int_test, H);
             long long ta = clock64();
-            build(false, m1024, int_test, H, true);
-            long long tb = clock64();
-            if (!fast_forced(labw)) {
-                copy_res();
-                cut_block<CONN>(P.s, k, smem, bw, pl, imask, clock64(), labw, false);
+            // Certified frozen iteration: every interior pixel forced by the
+            // integer bound, every face pixel forced (to its own label) by
+            // its certificate -> the labels do not move; no unaries needed.
+            bool cert = int_test && H >= tau_int && P.mu_fact >= 1.0;
+            if (cert) {
+                const float mf = __double2float_ru(m1024);
+                const float e2h = __fmul_ru(1.8189894035458565e-12f, __double2float_ru(__dmul_rn(m1024, 0.5)));  // 2^-40 * 2h
+                int okc = 1;
+                for (int f = tid; f < F; f += NT) {
+                    const int v = fl[f];
+                    const float dl = __fadd_ru(__fadd_ru(cW[f], __fmul_ru(__fmul_ru(2.f, mf), cB[f])),
+                                               __fadd_ru(cE[f], e2h));
+                    if (!(dl < 4.0e18f)) { okc = 0; continue; }
+                    const long long D = (long long)ceilf(dl) + 1;
+                    const long long cs = cs0[v];
+                    const bool ok = lab[v] ? (cI[f] - H + D + 1 <= -cs) : (cI[f] + H - D - 1 >= cs);
+                    okc &= ok ? 1 : 0;
+                }
+                cert = __syncthreads_and(okc) != 0;
             }
-            long long tc = clock64();
-            int moved = 0;
+            long long tb = ta, tc = ta;
+            if (!cert) {
+                build(false, m1024, int_test, H, true);
+                tb = clock64();
+                if (!fast_forced(labw)) {
+                    copy_res();
+                    cut_block<CONN>(P.s, k, smem, bw, pl, imask, clock64(), labw, false);
+                }
+                tc = clock64();
+                int moved = 0;
 #pragma unroll 1
-            for (int q = 0; q < NPTMAX; ++q) {
-                int v = tid + q * NT;
-                if (v < B && labw[v] != lab[v]) moved = 1;
+                for (int q = 0; q < NPTMAX; ++q) {
+                    int v = tid + q * NT;
+                    if (v < B && labw[v] != lab[v]) moved = 1;
+                }
+                if (__syncthreads_or(moved)) { thaw_s = sidx; break; }
             }
-            if (__syncthreads_or(moved)) { thaw_s = sidx; break; }
             long long td = clock64();
             const double r2 = face_sum([&](int f) {
                 return face_step(lab[fl[f]], Gf[f], muw, yS[f], aS[f]);
             });
             if (tid == 0) rloc[sidx - 1] = r2;
+            {
+                double* rs = ring + (size_t)(sidx % RING) * 2 * F;
+                for (int f = tid; f < F; f += NT) { rs[f] = yS[f]; rs[F + f] = aS[f]; }
+            }
             long long te = clock64();
             for (int h = tid; h < NH; h += NT) {
                 double yv = hy[h], av = ha[h];
@@ -1658,24 +1764,41 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
             c->windows += 1;
             c->window_iters += tvalid - tw;
         }
-        int tend = tvalid;
-        for (int tt = tw + 1; tt <= tvalid; ++tt) {
+        // first committed iteration whose stop test holds (all candidates read at once)
+        __shared__ int s_stop;
+        if (tid == 0) s_stop = 0x7fffffff;
+        __syncthreads();
+        for (int tt = tw + 1 + tid; tt <= tvalid; tt += NT) {
             const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[tt]));
-            if (!(__dsqrt_rn(r2) > P.s.eps)) { tend = tt; conv = 1; break; }
+            if (!(__dsqrt_rn(r2) > P.s.eps)) atomicMin(&s_stop, tt);
         }
-        // own face state at tend: replay the committed iterations from the window start
-        for (int f = tid; f < F; f += NT) {
-            double yv = yS0[f], av = aS0[f];
-            double m = mu;
-            const int yh = lab[fl[f]];
-            for (int tt = tw + 1; tt <= tend; ++tt) {
-                face_step(yh, Gf[f], m, yv, av);
-                m = __dmul_rn(m, P.mu_fact);
+        __syncthreads();
+        int tend = tvalid;
+        if (s_stop <= tvalid) { tend = s_stop; conv = 1; }
+        // own face state at tend: the current one, one kept in the ring, or a
+        // replay of the committed iterations from the window start
+        const int sdone = thaw_s - 1;                  // iterations this CTA advanced
+        const int back = (tw + sdone) - tend;          // iterations to undo
+        if (back > 0 && back < RING && tend > tw) {
+            const double* rs = ring + (size_t)((tend - tw) % RING) * 2 * F;
+            for (int f = tid; f < F; f += NT) { yS[f] = rs[f]; aS[f] = rs[F + f]; }
+        } else if (back > 0) {
+            for (int f = tid; f < F; f += NT) {
+                double yv = yS0[f], av = aS0[f];
+                double m = mu;
+                const int yh = lab[fl[f]];
+                for (int tt = tw + 1; tt <= tend; ++tt) {
+                    face_step(yh, Gf[f], m, yv, av);
+                    m = __dmul_rn(m, P.mu_fact);
+                }
+                yS[f] = yv;
+                aS[f] = av;
             }
-            yS[f] = yv;
-            aS[f] = av;
-            P.u.yF[(long long)k * F + f] = yv;
-            P.u.aF[(long long)k * F + f] = av;
+        }
+        __syncthreads();
+        for (int f = tid; f < F; f += NT) {
+            P.u.yF[(long long)k * F + f] = yS[f];
+            P.u.aF[(long long)k * F + f] = aS[f];
         }
         for (int tt = tw + 1; tt <= tend; ++tt) mu = __dmul_rn(mu, P.mu_fact);
         t = tend;
