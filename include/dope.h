@@ -107,8 +107,9 @@ typedef struct {
                                    run-ahead windows */
     int windows;                /* run-ahead windows run (launch_mode 0) */
     int window_iterations;      /* iterations committed from run-ahead windows */
-    double window_cycles[6];    /* run-ahead windows, summed over CTAs: build, block solve,
-                                   label check, own update, halo update, window set-up */
+    double window_cycles[8];    /* run-ahead windows, summed over CTAs: build, block solve,
+                                   label check, own update, halo update, window set-up,
+                                   wait at the closing barrier, rest of the resolution */
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the

@@ -184,7 +184,7 @@ void fill_stats(dope_ctx* c, const Ctrl& h) {
     c->stats.fold_rounds_max = h.fold_rounds_max;
     for (int i = 0; i < 4; ++i) c->stats.phase_cycles[i] = (double)h.cyc[i];
     for (int i = 0; i < 4; ++i) c->stats.loop_cycles[i] = (double)h.pcyc[i];
-    for (int i = 0; i < 6; ++i) c->stats.window_cycles[i] = (double)h.wcyc[i];
+    for (int i = 0; i < 8; ++i) c->stats.window_cycles[i] = (double)h.wcyc[i];
 }
 
 int read_r2max(dope_ctx* c, int t, double* r2, cudaStream_t st) {

@@ -63,8 +63,9 @@ struct Ctrl {
     int windows;                    // run-ahead windows run (statistics)
     int window_iters;               // iterations done inside windows (statistics)
     unsigned work[2];               // block counters of the persistent kernel (solve, update)
-    unsigned long long wcyc[6];     // run-ahead windows, thread 0 of each CTA: build, cut,
-                                    // label check, own update, halo update, set-up + resolution
+    unsigned long long wcyc[8];     // run-ahead windows, thread 0 of each CTA: build, cut,
+                                    // label check, own update, halo update, set-up,
+                                    // wait at the closing barrier, rest of the resolution
     unsigned long long pcyc[4];     // persistent kernel, thread 0 of each CTA: solve phase,
                                     // first barrier wait, update phase, second barrier wait
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
@@ -1436,6 +1437,20 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     __syncthreads();
     const long long tau_int = s_tau;
 
+    // Eq. 8 unary of face slot f with the halo y from the window's halo copy
+    // (the operations of face_cap_core, in the same order).
+    auto local_face_cap = [&](int f, int v, double m1024) -> long long {
+        const double yv = yS[f], av = aS[f];
+        double sv = (double)Us[v];
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int hsl = hs[d * F + f];
+            if (hsl >= 0) sv = __dadd_rn(sv, __dmul_rn((double)hw[d * F + f], __dsub_rn(yv, hy[hsl])));
+        }
+        sv = __dadd_rn(sv, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
+        sv = fmin(fmax(sv, -CLAMP62), CLAMP62);
+        return __double2ll_rn(sv);
+    };
     // Build of iteration t (first = t is 1): n-links and interior unaries from
     // shared memory; face unaries with the halo y from L2 (hy == nullptr) or
     // from the window's halo copy.
@@ -1465,17 +1480,7 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
                     cv = face_cap_core<CONN>(g, (long long)Us[v], yS[f], aS[f], P.s.Wl, P.s.yF, P.s.halo, k,
                                              kz, ky, kx, v, f, m1024);
                 } else {
-                    const double yv = yS[f], av = aS[f];
-                    double sv = (double)Us[v];
-#pragma unroll
-                    for (int d = 0; d < CONN; ++d) {
-                        const int hsl = hs[d * F + f];
-                        if (hsl >= 0)
-                            sv = __dadd_rn(sv, __dmul_rn((double)hw[d * F + f], __dsub_rn(yv, hy[hsl])));
-                    }
-                    sv = __dadd_rn(sv, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
-                    sv = fmin(fmax(sv, -CLAMP62), CLAMP62);
-                    cv = __double2ll_rn(sv);
+                    cv = local_face_cap(f, v, m1024);
                 }
                 C64[v] = cv;
             }
@@ -1691,11 +1696,28 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
             // Certified frozen iteration: every interior pixel forced by the
             // integer bound, every face pixel forced (to its own label) by
             // its certificate -> the labels do not move; no unaries needed.
-            bool cert = int_test && H >= tau_int && P.mu_fact >= 1.0;
+            bool cert = int_test && P.mu_fact >= 1.0;
             if (cert) {
                 const float mf = __double2float_ru(m1024);
                 const float e2h = __fmul_ru(1.8189894035458565e-12f, __double2float_ru(__dmul_rn(m1024, 0.5)));  // 2^-40 * 2h
                 int okc = 1;
+                if (H < tau_int) {
+                    // interior pixels one by one: the integer bound, else the exact unary
+#pragma unroll 1
+                    for (int q = 0; q < NPTMAX; ++q) {
+                        int v = tid + q * NT;
+                        if (v >= B || ((fmask >> q) & 1u)) continue;
+                        const int yh = lab[v];
+                        const long long Ui = Us[v], cs = cs0[v];
+                        const long long T = yh ? Ui - H : Ui + H;
+                        bool ok = yh ? (T < -cs) : (T >= cs);
+                        if (!ok) {
+                            const long long C = interior_cap(Ui, yh, m1024);
+                            ok = yh ? (C < -cs) : (C >= cs);
+                        }
+                        okc &= ok ? 1 : 0;
+                    }
+                }
                 for (int f = tid; f < F; f += NT) {
                     const int v = fl[f];
                     const float dl = __fadd_ru(__fadd_ru(cW[f], __fmul_ru(__fmul_ru(2.f, mf), cB[f])),
@@ -1703,7 +1725,12 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
                     if (!(dl < 4.0e18f)) { okc = 0; continue; }
                     const long long D = (long long)ceilf(dl) + 1;
                     const long long cs = cs0[v];
-                    const bool ok = lab[v] ? (cI[f] - H + D + 1 <= -cs) : (cI[f] + H - D - 1 >= cs);
+                    bool ok = lab[v] ? (cI[f] - H + D + 1 <= -cs) : (cI[f] + H - D - 1 >= cs);
+                    if (!ok) {
+                        // no certificate: the exact unary decides for this pixel
+                        const long long C = local_face_cap(f, v, m1024);
+                        ok = lab[v] ? (C < -cs) : (C >= cs);
+                    }
                     okc &= ok ? 1 : 0;
                 }
                 cert = __syncthreads_and(okc) != 0;
@@ -1752,7 +1779,9 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         }
         // resolution: earliest moved iteration over all blocks, committed residuals
         if (tid == 0) atomicMin(&c->thaw, tw + thaw_s);
+        const long long cr0 = clock64();
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
+        const long long cr1 = clock64();
         const int tstar = __ldcg(&c->thaw);
         const int tvalid = min(tstar - 1, tw + Wn);
         if (tid == 0)
@@ -1803,7 +1832,11 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         for (int tt = tw + 1; tt <= tend; ++tt) mu = __dmul_rn(mu, P.mu_fact);
         t = tend;
         const long long c1 = clock64();
-        if (tid == 0) atomicAdd(&c->pcyc[3], (unsigned long long)(c1 - c0));
+        if (tid == 0) {
+            atomicAdd(&c->pcyc[3], (unsigned long long)(c1 - c0));
+            atomicAdd(&c->wcyc[6], (unsigned long long)(cr1 - cr0));
+            atomicAdd(&c->wcyc[7], (unsigned long long)(c1 - cr1));
+        }
         if (conv) break;
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
         need_normal = (tstar <= tw + Wn);

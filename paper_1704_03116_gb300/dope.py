@@ -48,7 +48,7 @@ class dope_stats(ctypes.Structure):
                 ("bfs_levels_max", ctypes.c_int), ("fold_rounds_max", ctypes.c_int),
                 ("phase_cycles", ctypes.c_double * 4), ("loop_cycles", ctypes.c_double * 4),
                 ("windows", ctypes.c_int), ("window_iterations", ctypes.c_int),
-                ("window_cycles", ctypes.c_double * 6)]
+                ("window_cycles", ctypes.c_double * 8)]
 
 
 class dope_profile(ctypes.Structure):
