@@ -254,6 +254,119 @@ int dope_solve_noalloc(const int64_t *grid, int ndim, int connectivity, const in
                        double lambda, const dope_params *p, const float *u, const int32_t *wq,
                        uint8_t *labels, int64_t *energy_int, int *iterations, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves.  The paper runs the blocks of one problem in parallel
+ * (Algorithm 1, "in parallel" over k); these calls run the blocks of many
+ * problems in one persistent launch.  Each problem still runs its own
+ * Algorithm 1 (own iteration count, mu and stop test) with the per-block
+ * arithmetic of the single-problem path, so its iterates, labels and energy
+ * are bit-identical to running it alone.
+ * ------------------------------------------------------------------------- */
+#define DOPE_BATCH_MAX 256
+
+/* Advance n (1 .. DOPE_BATCH_MAX) distinct contexts together in one
+ * cooperative launch: each runs up to n_iter more iterations of Algorithm 1
+ * from its current state (never beyond its max_iter), stopping when its own
+ * stop test holds.  The contexts may differ in grid, connectivity, block
+ * shape, lambda and parameters; each must have its unaries and weights set.
+ * Per context (arrays of n, any may be NULL): iterations[i] = iterations done
+ * since its reset, converged[i] = its stop test held after its last
+ * iteration, status[i] = its status.  Read labels with dope_labels.
+ * Synchronises `stream`.  Returns DOPE_OK, the first nonzero per-context
+ * status, DOPE_ETIMEOUT if a bounded grid-barrier wait gave up, or
+ * DOPE_EUNSUPPORTED if the device cannot run cooperative launches. */
+int dope_iterate_batch(dope_ctx *const *ctxs, int n, int n_iter, int *iterations, int *converged,
+                       int *status, void *stream);
+
+/* Labels of the last iteration run (Algorithm 1 output for Q = I: yhat;
+ * image order, N bytes at `labels` in `where` memory) and *energy_int =
+ * E_int of them (may be NULL), without running further iterations.
+ * Synchronises `stream`. */
+int dope_labels(dope_ctx *ctx, uint8_t *labels, int where, int64_t *energy_int, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Request server (continuous batching on one GPU).  The paper has no
+ * counterpart; this is the serving layer around the batched launch.
+ *
+ * A worker thread owns one device memory arena.  A submitted request is
+ * admitted (first come, first served) when its device state fits in the
+ * arena's free memory and fewer than max_batch requests are admitted; its
+ * inputs are uploaded on a side stream while the GPU works on the others;
+ * the running persistent launch is asked to end at its next iteration
+ * boundary, and the next launch takes the new request in.  A launch also
+ * ends when one of its requests finishes, whose labels and energy are then
+ * written out and whose memory returns to the arena.  Grids need not be
+ * whole numbers of blocks: the server pads them with isolated zero-cost
+ * pixels, which changes no label or energy of the caller's pixels.
+ * mode 1 solves admitted requests one at a time through the single-problem
+ * path (dope_solve's kernels), for comparison.
+ * ------------------------------------------------------------------------- */
+typedef struct dope_server dope_server;
+
+typedef struct {
+    uint64_t hbm_bytes;   /* arena size (0: 3/4 of the device's free memory at creation) */
+    int max_batch;        /* most admitted requests (0: DOPE_BATCH_MAX) */
+    int mode;             /* 0: continuous batching, 1: one request at a time */
+    int launch_iters;     /* most iterations of one batched launch (0: no bound) */
+    int reserved;
+} dope_server_params;
+
+typedef struct {
+    int ndim;                 /* 2 or 3 */
+    int connectivity;         /* 4 / 8 (2-D), 6 (3-D) */
+    int64_t grid[3];          /* first ndim entries used; need not be a multiple of the block */
+    int32_t block_shape[3];   /* first ndim entries used */
+    double lambda;
+    dope_params params;       /* as for dope_create (used when use_params != 0) */
+    int use_params;
+    int where_inputs;         /* DOPE_HOST or DOPE_DEVICE, for unaries and weights */
+    const float *unaries;     /* [N] image order */
+    const int32_t *weights;   /* [conn/2][N] image order */
+    uint8_t *labels;          /* [N] image order, receives the labels */
+    int where_labels;         /* DOPE_HOST or DOPE_DEVICE */
+    int reserved;
+    uint64_t tag;             /* returned in the result */
+} dope_request;
+
+typedef struct {
+    uint64_t id, tag;
+    int status;               /* DOPE_OK, DOPE_ENOTCONV (labels valid), or an error */
+    int iterations;
+    int converged;
+    int reserved;
+    int64_t energy_int;       /* E_int of the labels */
+    double t_submit, t_admit, t_done;   /* seconds on dope_server_clock */
+} dope_result;
+
+typedef struct {
+    int64_t submitted, admitted, completed, launches, yields;
+    int64_t queued, in_flight;          /* now */
+    int64_t max_in_flight;
+    uint64_t bytes_limit, bytes_in_use, bytes_peak;
+    double gpu_launch_s;                /* summed device time of the solve launches */
+} dope_server_stats;
+
+/* Start a server on the current device (p may be NULL for defaults). */
+int dope_server_create(const dope_server_params *p, dope_server **out);
+
+/* Queue a request; *id (may be NULL) receives its id.  The request struct is
+ * copied; the buffers it points to must stay valid, and unchanged, until its
+ * result has been polled.  Returns DOPE_EINVAL for a malformed request. */
+int dope_server_submit(dope_server *srv, const dope_request *req, uint64_t *id);
+
+/* Completed results, oldest first: waits up to timeout_s seconds for at
+ * least one, then returns up to cap of them (*count may be 0 on timeout). */
+int dope_server_poll(dope_server *srv, dope_result *out, int cap, int *count, double timeout_s);
+
+/* Seconds since the server was created (the clock of dope_result). */
+double dope_server_clock(const dope_server *srv);
+
+int dope_server_get_stats(dope_server *srv, dope_server_stats *st);
+
+/* Stop the worker (requests not yet completed are dropped) and free
+ * everything (NULL is ignored). */
+void dope_server_destroy(dope_server *srv);
+
 /* Free the context and its device memory (NULL is ignored). */
 void dope_destroy(dope_ctx *ctx);
 

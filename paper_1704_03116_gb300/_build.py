@@ -1,8 +1,10 @@
 """Build of the CUDA library libdope.so (sm_103a), in-tree.
 
-The library is one translation unit (csrc/dope.cu + csrc/dope_kernels.cuh)
-compiled by nvcc for sm_103a only; it links the CUDA runtime statically and
-has no PyTorch dependency (the C-ABI takes plain pointers).
+Two translation units, compiled in parallel by nvcc for sm_103a only and
+linked into one shared library: csrc/dope.cu (kernels in
+csrc/dope_kernels.cuh, the solver C-ABI) and csrc/dope_server.cu (the request
+server, host code).  It links the CUDA runtime statically and has no PyTorch
+dependency (the C-ABI takes plain pointers).
 """
 import os
 import subprocess
@@ -10,8 +12,10 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "dope.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "dope_kernels.cuh"), os.path.join(ROOT, "include", "dope.h")]
+SRC = [os.path.join(HERE, "csrc", "dope.cu"), os.path.join(HERE, "csrc", "dope_server.cu")]
+DEPS = SRC + [os.path.join(HERE, "csrc", "dope_kernels.cuh"), os.path.join(HERE, "csrc", "dope_internal.h"),
+              os.path.join(ROOT, "include", "dope.h")]
+OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdope.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -28,16 +32,31 @@ def build(force=False, verbose=False):
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in DEPS)):
         return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I" + os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *SRC]
+    os.makedirs(OBJDIR, exist_ok=True)
+    common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-I" + os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+        common.insert(1, "-Xptxas=-v")
+    objs, procs = [], []
+    for src in SRC:
+        obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+        objs.append(obj)
+        procs.append(subprocess.Popen([*common, "-c", "-o", obj, src], stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    failed = False
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            sys.stderr.write(out + err)
+            failed = True
+        elif verbose:
+            sys.stderr.write(err)
+    if failed:
+        raise RuntimeError("nvcc failed building libdope.so")
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs], capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed building libdope.so")
-    if verbose:
-        sys.stderr.write(r.stderr)
+        raise RuntimeError("nvcc failed linking libdope.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

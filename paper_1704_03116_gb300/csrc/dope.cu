@@ -11,12 +11,14 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "dope.h"
+#include "dope_internal.h"
 #include "dope_kernels.cuh"
 
 using namespace dope;
@@ -25,9 +27,12 @@ struct dope_ctx {
     Geo g;
     int ndim, conn;
     double lambda;
+    dope_allocator al{};          // device memory source (null alloc: cudaMalloc)
+    dope_tables* own_tab = nullptr;   // tables built for this context (else shared)
     dope_params p;
     int threads, smem;
     int persist_grid = 0;     // CTAs of the persistent launch (0: not possible)
+    int pthreads = 0;         // threads per CTA of the persistent launch (256-wide or 512-wide kernel)
     int resident = 0;         // 1: the resident persistent kernel (K CTAs, one block each)
     int resident_smem = 0;
     int resident_threads = 0;
@@ -81,14 +86,52 @@ int grid_for(long long n, int threads) {
     return (int)b;
 }
 
+void* dalloc(const dope_allocator& al, size_t bytes) {
+    if (!bytes) bytes = 16;
+    if (al.alloc) return al.alloc(al.self, bytes);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(const dope_allocator& al, void* p) {
+    if (!p) return;
+    if (al.alloc) al.release(al.self, p);
+    else cudaFree(p);
+}
+
+// Width of the persistent / batched solver CTA for a block of B nodes
+// (threads: the context's solver width): the 256-wide kernel (3 CTAs per SM)
+// up to 1024 nodes, else the 512-wide one (2 CTAs per SM).
+int solver_width(int B, int threads) {
+    if (threads <= 256) return threads;
+    return B <= 1024 ? 256 : threads;
+}
+
+const void* persistent_fn(int conn, int nt) {
+    if (nt <= 256)
+        return conn == 4 ? (const void*)k_admm_persistent<4, 256>
+             : conn == 8 ? (const void*)k_admm_persistent<8, 256> : (const void*)k_admm_persistent<6, 256>;
+    return conn == 4 ? (const void*)k_admm_persistent<4, 512>
+         : conn == 8 ? (const void*)k_admm_persistent<8, 512> : (const void*)k_admm_persistent<6, 512>;
+}
+
+const void* batch_fn(int nt) {
+    return nt <= 256 ? (const void*)k_admm_batch<256> : (const void*)k_admm_batch<512>;
+}
+
 int ensure_stage(dope_ctx* c, size_t bytes, int which) {
     void** p = which ? &c->stage2 : &c->stage;
     size_t* sz = which ? &c->stage2_bytes : &c->stage_bytes;
     if (*sz >= bytes) return DOPE_OK;
-    if (*p) cudaFree(*p);
+    dfree(c->al, *p);
     *p = nullptr;
     *sz = 0;
-    if (cudaMalloc(p, bytes) != cudaSuccess) return DOPE_ENOMEM;
+    *p = dalloc(c->al, bytes);
+    if (!*p) return DOPE_ENOMEM;
     *sz = bytes;
     return DOPE_OK;
 }
@@ -225,9 +268,8 @@ int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
                        : c->conn == 8 ? (const void*)k_admm_resident<8> : (const void*)k_admm_resident<6>;
         e = cudaLaunchCooperativeKernel(fn, c->g.K, c->resident_threads, args, c->resident_smem, st);
     } else {
-        const void* fn = c->conn == 4 ? (const void*)k_admm_persistent<4>
-                       : c->conn == 8 ? (const void*)k_admm_persistent<8> : (const void*)k_admm_persistent<6>;
-        e = cudaLaunchCooperativeKernel(fn, c->persist_grid, c->threads, args, c->smem, st);
+        e = cudaLaunchCooperativeKernel(persistent_fn(c->conn, c->pthreads), c->persist_grid, c->pthreads, args,
+                                        c->smem, st);
     }
     if (e != cudaSuccess) return DOPE_ECUDA;
     c->launches++;
@@ -392,21 +434,333 @@ void raise_smem_limit(const void* fn) {
 template <int CONN>
 void raise_smem_limits() {
     raise_smem_limit((const void*)k_block_solve<CONN>);
-    raise_smem_limit((const void*)k_admm_persistent<CONN>);
+    raise_smem_limit((const void*)k_admm_persistent<CONN, 256>);
+    raise_smem_limit((const void*)k_admm_persistent<CONN, 512>);
     raise_smem_limit((const void*)k_admm_resident<CONN>);
 }
 
-int reset_state(dope_ctx* c) {
+// Algorithm 1 initialisation (y = 1/2, a = 0, mu = mu0), stream-ordered.
+int reset_state_async(dope_ctx* c, cudaStream_t st) {
     c->t = 0;
     c->mu = c->p.mu0;
     const int threads = 256;
-    k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads>>>(c->g, c->yF, c->aF);
+    k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads, 0, st>>>(c->g, c->yF, c->aF);
     CK(cudaGetLastError());
-    CK(cudaMemset(c->yhat, 0, (size_t)c->g.N));
+    CK(cudaMemsetAsync(c->yhat, 0, (size_t)c->g.N, st));
+    return DOPE_OK;
+}
+
+int reset_state(dope_ctx* c) {
+    int rc = reset_state_async(c, 0);
+    if (rc) return rc;
     CK(cudaDeviceSynchronize());
     return DOPE_OK;
 }
 
+
+// Persistent-launch choices of a context: CTAs of k_admm_persistent, and
+// whether the resident kernel (one CTA per block, with or without its
+// run-ahead window arrays) fits co-resident.
+void choose_launch(dope_ctx* c) {
+    const Geo& g = c->g;
+    const int connectivity = c->conn;
+    const long long B = g.B;
+    c->pthreads = solver_width(g.B, c->p.threads > 0 ? c->p.threads : c->threads);
+    if (c->p.threads > 0) c->pthreads = c->threads;
+    const void* fn = persistent_fn(connectivity, c->pthreads);
+    int dev = 0, sms = 0, coop = 0, per_sm = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    {
+        cudaFuncAttributes fa0;
+        if (cudaFuncGetAttributes(&fa0, fn) != cudaSuccess ||
+            (size_t)c->smem + fa0.sharedSizeBytes > (size_t)optin ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c->pthreads, c->smem) != cudaSuccess)
+            per_sm = 0;
+    }
+    cudaGetLastError();
+    long long cap = (long long)per_sm * sms;
+    c->persist_grid = (coop && cap > 0) ? (int)(cap < g.K ? cap : g.K) : 0;
+    const void* fr = connectivity == 4 ? (const void*)k_admm_resident<4>
+                   : connectivity == 8 ? (const void*)k_admm_resident<8>
+                                       : (const void*)k_admm_resident<6>;
+    int rt = (int)((B + 31) / 32 * 32);
+    if (rt > 256) rt = 256;
+    cudaFuncAttributes fa;
+    size_t static_smem = 0;
+    if (cudaFuncGetAttributes(&fa, fr) == cudaSuccess) static_smem = fa.sharedSizeBytes;
+    else optin = 0;
+    for (int with_window = 1; with_window >= 0 && !c->resident; --with_window) {
+        const size_t rs = with_window ? window_smem_bytes(connectivity, (int)B, g.F, c->NH)
+                                      : resident_smem_bytes(connectivity, (int)B, g.F);
+        int per_sm_r = 0;
+        if (coop && rs + static_smem <= (size_t)optin && (long long)rt * NPTMAX >= B &&
+            c->p.threads == 0 && g.F <= 128 * 32) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, fr, rt, rs) != cudaSuccess)
+                per_sm_r = 0;
+        }
+        cudaGetLastError();
+        if (per_sm_r > 0 && (long long)per_sm_r * sms >= g.K) {
+            c->resident = 1;
+            c->resident_smem = (int)rs;
+            c->resident_threads = rt;
+            c->window_ok = with_window;
+        }
+    }
+}
+
+std::once_flag g_smem_once[3];
+
+void raise_all_smem_limits(int conn) {
+    const int ci = conn == 4 ? 0 : (conn == 8 ? 1 : 2);
+    std::call_once(g_smem_once[ci], [conn]() {
+        if (conn == 4) raise_smem_limits<4>();
+        else if (conn == 8) raise_smem_limits<8>();
+        else raise_smem_limits<6>();
+        raise_smem_limit((const void*)k_admm_batch<256>);
+        raise_smem_limit((const void*)k_admm_batch<512>);
+    });
+}
+
+}  // namespace
+
+int dope_tables_create(int connectivity, const int32_t blk3[3], const dope_allocator* alp,
+                       cudaStream_t st, dope_tables** out) {
+    if (!out || !blk3) return DOPE_EINVAL;
+    *out = nullptr;
+    if (connectivity != 4 && connectivity != 8 && connectivity != 6) return DOPE_EINVAL;
+    const int bd = blk3[0], bh = blk3[1], bw = blk3[2];
+    if (bd <= 0 || bh <= 0 || bw <= 0 || (long long)bd * bh * bw > 4096) return DOPE_EINVAL;
+    const int B = bd * bh * bw;
+    // face slots: pixels with a neighbour outside their block (any direction)
+    static const int OFF[3][4][3] = {
+        {{0, 0, 1}, {0, 1, 0}, {0, 0, 0}, {0, 0, 0}},
+        {{0, 0, 1}, {0, 1, 0}, {0, 1, 1}, {0, 1, -1}},
+        {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}, {0, 0, 0}}};
+    const int ci = connectivity == 4 ? 0 : (connectivity == 8 ? 1 : 2);
+    const int nh = connectivity / 2;
+    std::vector<int16_t> fidx((size_t)B, -1), floc;
+    for (int l = 0; l < B; ++l) {
+        int lx = l % bw, ly = (l / bw) % bh, lz = l / (bw * bh);
+        bool face = false;
+        for (int o = 0; o < nh && !face; ++o)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                int z = lz + sg * OFF[ci][o][0], y = ly + sg * OFF[ci][o][1], x = lx + sg * OFF[ci][o][2];
+                if (z < 0 || z >= bd || y < 0 || y >= bh || x < 0 || x >= bw) face = true;
+            }
+        if (face) {
+            fidx[(size_t)l] = (int16_t)floc.size();
+            floc.push_back((int16_t)l);
+        }
+    }
+    const int F = (int)floc.size();
+    // halo table [conn][F]: the cross-block neighbour of every face slot
+    std::vector<int> halo((size_t)connectivity * (F ? F : 1), -1);
+    for (int f = 0; f < F; ++f) {
+        const int l = floc[(size_t)f];
+        const int lx = l % bw, ly = (l / bw) % bh, lz = l / (bw * bh);
+        for (int d = 0; d < connectivity; ++d) {
+            const int o = d < nh ? d : d - nh, sg = d < nh ? 1 : -1;
+            int z = lz + sg * OFF[ci][o][0], y = ly + sg * OFF[ci][o][1], x = lx + sg * OFF[ci][o][2];
+            if (z >= 0 && z < bd && y >= 0 && y < bh && x >= 0 && x < bw) continue;
+            const int dkz = z < 0 ? -1 : (z >= bd ? 1 : 0);
+            const int dky = y < 0 ? -1 : (y >= bh ? 1 : 0);
+            const int dkx = x < 0 ? -1 : (x >= bw ? 1 : 0);
+            z -= dkz * bd; y -= dky * bh; x -= dkx * bw;
+            const int ln = (z * bh + y) * bw + x;
+            halo[(size_t)d * F + f] = halo_entry((dkz + 1) * 9 + (dky + 1) * 3 + (dkx + 1), ln,
+                                                 fidx[(size_t)ln]);
+        }
+    }
+    // distinct halo pixels (first-seen order over face slots, then directions)
+    std::vector<int16_t> hslot((size_t)connectivity * (F ? F : 1), -1);
+    std::vector<int> hinfo;
+    for (int f = 0; f < F; ++f)
+        for (int d = 0; d < connectivity; ++d) {
+            const int e = halo[(size_t)d * F + f];
+            if (e < 0) continue;
+            int slot = -1;
+            for (size_t h = 0; h < hinfo.size(); ++h)
+                if (hinfo[h] == e) { slot = (int)h; break; }
+            if (slot < 0) { slot = (int)hinfo.size(); hinfo.push_back(e); }
+            hslot[(size_t)d * F + f] = (int16_t)slot;
+        }
+    const int NH = (int)hinfo.size();
+    if (hinfo.empty()) hinfo.push_back(-1);
+
+    dope_tables* t = new (std::nothrow) dope_tables();
+    if (!t) return DOPE_ENOMEM;
+    t->conn = connectivity;
+    t->blk[0] = bd; t->blk[1] = bh; t->blk[2] = bw;
+    t->F = F;
+    t->NH = NH;
+    t->al = alp ? *alp : dope_allocator{nullptr, nullptr, nullptr};
+    const size_t b_fi = sizeof(int16_t) * (size_t)B, b_fl = sizeof(int16_t) * (size_t)(F ? F : 1);
+    const size_t b_ha = sizeof(int) * halo.size(), b_hs = sizeof(int16_t) * hslot.size();
+    const size_t b_hi = sizeof(int) * hinfo.size();
+    t->faceIndex = (int16_t*)dalloc(t->al, b_fi);
+    t->faceLocal = (int16_t*)dalloc(t->al, b_fl);
+    t->halo = (int*)dalloc(t->al, b_ha);
+    t->hslot = (int16_t*)dalloc(t->al, b_hs);
+    t->hinfo = (int*)dalloc(t->al, b_hi);
+    t->bytes = b_fi + b_fl + b_ha + b_hs + b_hi;
+    if (!t->faceIndex || !t->faceLocal || !t->halo || !t->hslot || !t->hinfo) {
+        dope_tables_destroy(t);
+        return DOPE_ENOMEM;
+    }
+    if (cudaMemcpyAsync(t->faceIndex, fidx.data(), b_fi, cudaMemcpyHostToDevice, st) ||
+        (F && cudaMemcpyAsync(t->faceLocal, floc.data(), sizeof(int16_t) * (size_t)F, cudaMemcpyHostToDevice, st)) ||
+        cudaMemcpyAsync(t->halo, halo.data(), b_ha, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(t->hslot, hslot.data(), b_hs, cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(t->hinfo, hinfo.data(), b_hi, cudaMemcpyHostToDevice, st)) {
+        cudaGetLastError();
+        dope_tables_destroy(t);
+        return DOPE_ECUDA;
+    }
+    // pageable sources: the copies above are staged before they return
+    *out = t;
+    return DOPE_OK;
+}
+
+void dope_tables_destroy(dope_tables* t) {
+    if (!t) return;
+    dfree(t->al, t->faceIndex);
+    dfree(t->al, t->faceLocal);
+    dfree(t->al, t->halo);
+    dfree(t->al, t->hslot);
+    dfree(t->al, t->hinfo);
+    delete t;
+}
+
+int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_t* block_shape,
+                   double lambda, const dope_params* p, int pad, const dope_allocator* alp,
+                   dope_tables* tab, cudaStream_t st, dope_ctx** out) {
+    if (!out) return DOPE_EINVAL;
+    *out = nullptr;
+    if (!grid || !block_shape || (ndim != 2 && ndim != 3)) return DOPE_EINVAL;
+    if (ndim == 2 && connectivity != 4 && connectivity != 8) return DOPE_EINVAL;
+    if (ndim == 3 && connectivity != 6) return DOPE_EINVAL;
+    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return DOPE_EINVAL;
+    int64_t dims[3] = {1, 1, 1}, udims[3] = {1, 1, 1};
+    int32_t blk[3] = {1, 1, 1};
+    for (int i = 0; i < ndim; ++i) {
+        dims[3 - ndim + i] = grid[i];
+        blk[3 - ndim + i] = block_shape[i];
+    }
+    for (int i = 0; i < 3; ++i) {
+        if (dims[i] <= 0 || blk[i] <= 0 || dims[i] > (1LL << 30)) return DOPE_EINVAL;
+        udims[i] = dims[i];
+        if (dims[i] % blk[i]) {
+            if (!pad) return DOPE_EINVAL;
+            dims[i] = (dims[i] + blk[i] - 1) / blk[i] * blk[i];
+        }
+    }
+    const long long N = dims[0] * dims[1] * dims[2];
+    const long long B = (long long)blk[0] * blk[1] * blk[2];
+    if (N >= (1LL << 31) || B > 4096) return DOPE_EINVAL;
+    if (p && (p->threads < 0 || p->threads > 512 || p->threads % 32 ||
+              (p->threads > 0 && (long long)p->threads * NPTMAX < B)))
+        return DOPE_EINVAL;
+    if (tab && (tab->conn != connectivity || tab->blk[0] != blk[0] || tab->blk[1] != blk[1] ||
+                tab->blk[2] != blk[2]))
+        return DOPE_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return DOPE_ECUDA;
+    }
+
+    dope_ctx* c = new (std::nothrow) dope_ctx();
+    if (!c) return DOPE_ENOMEM;
+    c->al = alp ? *alp : dope_allocator{nullptr, nullptr, nullptr};
+    c->ndim = ndim;
+    c->conn = connectivity;
+    c->lambda = lambda;
+    dope_default_params(&c->p);
+    if (p) c->p = *p;
+    if (!(c->p.mu0 > 0.0)) c->p.mu0 = (ndim == 3) ? 500.0 : 100.0;
+    if (!(c->p.mu_fact > 0.0)) c->p.mu_fact = 1.05;
+    if (!(c->p.eps >= 0.0)) c->p.eps = 1e-3;
+    if (c->p.max_iter <= 0) c->p.max_iter = 1000;
+    if (c->p.relabel_period <= 0) c->p.relabel_period = 8;
+    if (c->p.max_pulses <= 0) c->p.max_pulses = (int)(64 * B + 4096);
+    if (c->p.fold_rounds <= 0) c->p.fold_rounds = MAX_FOLD_ROUNDS;
+
+    Geo& g = c->g;
+    g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
+    g.bd = blk[0]; g.bh = blk[1]; g.bw = blk[2];
+    g.B = (int)B;
+    g.nbz = g.D / g.bd; g.nby = g.H / g.bh; g.nbx = g.W / g.bw;
+    g.K = g.nbz * g.nby * g.nbx;
+    g.N = N;
+    g.Du = (int)udims[0]; g.Hu = (int)udims[1]; g.Wu = (int)udims[2];
+    g.Nu = udims[0] * udims[1] * udims[2];
+
+    int rc = DOPE_OK;
+    if (!tab) {
+        rc = dope_tables_create(connectivity, blk, alp, st, &c->own_tab);
+        if (rc) { delete c; return rc; }
+        tab = c->own_tab;
+    }
+    g.F = tab->F;
+    c->NH = tab->NH;
+    c->faceIndex = tab->faceIndex;
+    c->faceLocal = tab->faceLocal;
+    c->halo = tab->halo;
+    c->hslot = tab->hslot;
+    c->hinfo = tab->hinfo;
+
+    int threads = c->p.threads;
+    if (threads <= 0) {
+        threads = (int)((B + 31) / 32 * 32);
+        if (threads > 512) threads = 512;
+        if (threads < 32) threads = 32;
+    }
+    if (threads % 32 || threads > 512 || (long long)threads * NPTMAX < B) {
+        dope_destroy(c);
+        return DOPE_EINVAL;
+    }
+    c->threads = threads;
+    c->smem = (int)solver_smem_bytes(connectivity, (int)B);
+    const int nh = connectivity / 2;
+
+    auto A = [&](void** ptr, size_t bytes) {
+        if (rc == DOPE_OK) {
+            *ptr = dalloc(c->al, bytes);
+            if (!*ptr) rc = DOPE_ENOMEM;
+        }
+    };
+    A((void**)&c->U, sizeof(int32_t) * (size_t)N);
+    A((void**)&c->Wl, sizeof(int32_t) * (size_t)N * nh);
+    A((void**)&c->yhat, (size_t)N);
+    A((void**)&c->yF, sizeof(double) * (size_t)g.K * g.F);
+    A((void**)&c->aF, sizeof(double) * (size_t)g.K * g.F);
+    A((void**)&c->r2blk, sizeof(double) * (size_t)g.K);
+    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
+    A((void**)&c->ctrl, c->ctrl_bytes);
+    if (rc) { dope_destroy(c); return rc; }
+    if (cudaMemsetAsync(c->ctrl, 0, c->ctrl_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        dope_destroy(c);
+        return DOPE_ECUDA;
+    }
+    raise_all_smem_limits(connectivity);
+    {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (c->smem > optin) { dope_destroy(c); return DOPE_EINVAL; }
+    }
+    choose_launch(c);
+    rc = reset_state_async(c, st);
+    if (rc) { dope_destroy(c); return rc; }
+    *out = c;
+    return DOPE_OK;
+}
+
+namespace {
 }  // namespace
 
 extern "C" {
@@ -440,240 +794,35 @@ const char* dope_strerror(int s) {
 
 void dope_destroy(dope_ctx* c) {
     if (!c) return;
-    cudaFree(c->U);
-    cudaFree(c->Wl);
-    cudaFree(c->yhat);
-    cudaFree(c->yF);
-    cudaFree(c->aF);
-    cudaFree(c->r2blk);
-    cudaFree(c->faceIndex);
-    cudaFree(c->faceLocal);
-    cudaFree(c->halo);
-    cudaFree(c->hslot);
-    cudaFree(c->hinfo);
-    cudaFree(c->ctrl);
-    cudaFree(c->stage);
-    cudaFree(c->stage2);
+    const dope_allocator al = c->al;
+    dfree(al, c->U);
+    dfree(al, c->Wl);
+    dfree(al, c->yhat);
+    dfree(al, c->yF);
+    dfree(al, c->aF);
+    dfree(al, c->r2blk);
+    dfree(al, c->ctrl);
+    dfree(al, c->stage);
+    dfree(al, c->stage2);
+    if (c->own_tab) dope_tables_destroy(c->own_tab);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
 }
 
 int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* block_shape,
                 double lambda, const dope_params* p, dope_ctx** out) {
-    if (!out) return DOPE_EINVAL;
-    *out = nullptr;
-    if (!grid || !block_shape || (ndim != 2 && ndim != 3)) return DOPE_EINVAL;
-    if (ndim == 2 && connectivity != 4 && connectivity != 8) return DOPE_EINVAL;
-    if (ndim == 3 && connectivity != 6) return DOPE_EINVAL;
-    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return DOPE_EINVAL;
-    int64_t dims[3] = {1, 1, 1};
-    int32_t blk[3] = {1, 1, 1};
-    for (int i = 0; i < ndim; ++i) {
-        dims[3 - ndim + i] = grid[i];
-        blk[3 - ndim + i] = block_shape[i];
-    }
-    for (int i = 0; i < 3; ++i) {
-        if (dims[i] <= 0 || blk[i] <= 0 || dims[i] % blk[i]) return DOPE_EINVAL;
-        if (dims[i] > (1LL << 30)) return DOPE_EINVAL;
-    }
-    const long long N = dims[0] * dims[1] * dims[2];
-    const long long B = (long long)blk[0] * blk[1] * blk[2];
-    if (N >= (1LL << 31) || B > 4096) return DOPE_EINVAL;
-    if (p && (p->threads < 0 || p->threads > 512 || p->threads % 32 ||
-              (p->threads > 0 && (long long)p->threads * NPTMAX < B)))
-        return DOPE_EINVAL;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
+    int rc = dope_create_ex(grid, ndim, connectivity, block_shape, lambda, p, 0, nullptr, nullptr, 0, out);
+    if (rc) return rc;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        dope_destroy(*out);
+        *out = nullptr;
         return DOPE_ECUDA;
     }
-
-    dope_ctx* c = new (std::nothrow) dope_ctx();
-    if (!c) return DOPE_ENOMEM;
-    c->ndim = ndim;
-    c->conn = connectivity;
-    c->lambda = lambda;
-    dope_default_params(&c->p);
-    if (p) c->p = *p;
-    if (!(c->p.mu0 > 0.0)) c->p.mu0 = (ndim == 3) ? 500.0 : 100.0;
-    if (!(c->p.mu_fact > 0.0)) c->p.mu_fact = 1.05;
-    if (!(c->p.eps >= 0.0)) c->p.eps = 1e-3;
-    if (c->p.max_iter <= 0) c->p.max_iter = 1000;
-    if (c->p.relabel_period <= 0) c->p.relabel_period = 8;
-    if (c->p.max_pulses <= 0) c->p.max_pulses = (int)(64 * B + 4096);
-    if (c->p.fold_rounds <= 0) c->p.fold_rounds = MAX_FOLD_ROUNDS;
-
-    Geo& g = c->g;
-    g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
-    g.bd = blk[0]; g.bh = blk[1]; g.bw = blk[2];
-    g.B = (int)B;
-    g.nbz = g.D / g.bd; g.nby = g.H / g.bh; g.nbx = g.W / g.bw;
-    g.K = g.nbz * g.nby * g.nbx;
-    g.N = N;
-
-    // face slots: pixels with a neighbour outside their block (any direction)
-    static const int OFF[3][4][3] = {
-        {{0, 0, 1}, {0, 1, 0}, {0, 0, 0}, {0, 0, 0}},
-        {{0, 0, 1}, {0, 1, 0}, {0, 1, 1}, {0, 1, -1}},
-        {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}, {0, 0, 0}}};
-    const int ci = connectivity == 4 ? 0 : (connectivity == 8 ? 1 : 2);
-    const int nh = connectivity / 2;
-    std::vector<int16_t> fidx((size_t)B, -1), floc;
-    for (int l = 0; l < (int)B; ++l) {
-        int lx = l % g.bw, ly = (l / g.bw) % g.bh, lz = l / (g.bw * g.bh);
-        bool face = false;
-        for (int o = 0; o < nh && !face; ++o)
-            for (int s = -1; s <= 1; s += 2) {
-                int z = lz + s * OFF[ci][o][0], y = ly + s * OFF[ci][o][1], x = lx + s * OFF[ci][o][2];
-                if (z < 0 || z >= g.bd || y < 0 || y >= g.bh || x < 0 || x >= g.bw) face = true;
-            }
-        if (face) {
-            fidx[(size_t)l] = (int16_t)floc.size();
-            floc.push_back((int16_t)l);
-        }
-    }
-    g.F = (int)floc.size();
-    // halo table [conn][F]: the cross-block neighbour of every face slot
-    std::vector<int> halo((size_t)connectivity * (g.F ? g.F : 1), -1);
-    for (int f = 0; f < g.F; ++f) {
-        const int l = floc[(size_t)f];
-        const int lx = l % g.bw, ly = (l / g.bw) % g.bh, lz = l / (g.bw * g.bh);
-        for (int d = 0; d < connectivity; ++d) {
-            const int o = d < nh ? d : d - nh, sg = d < nh ? 1 : -1;
-            int z = lz + sg * OFF[ci][o][0], y = ly + sg * OFF[ci][o][1], x = lx + sg * OFF[ci][o][2];
-            if (z >= 0 && z < g.bd && y >= 0 && y < g.bh && x >= 0 && x < g.bw) continue;
-            const int dkz = z < 0 ? -1 : (z >= g.bd ? 1 : 0);
-            const int dky = y < 0 ? -1 : (y >= g.bh ? 1 : 0);
-            const int dkx = x < 0 ? -1 : (x >= g.bw ? 1 : 0);
-            z -= dkz * g.bd; y -= dky * g.bh; x -= dkx * g.bw;
-            const int ln = (z * g.bh + y) * g.bw + x;
-            halo[(size_t)d * g.F + f] = halo_entry((dkz + 1) * 9 + (dky + 1) * 3 + (dkx + 1), ln,
-                                                   fidx[(size_t)ln]);
-        }
-    }
-    // distinct halo pixels (first-seen order over face slots, then directions)
-    std::vector<int16_t> hslot((size_t)connectivity * (g.F ? g.F : 1), -1);
-    std::vector<int> hinfo;
-    for (int f = 0; f < g.F; ++f)
-        for (int d = 0; d < connectivity; ++d) {
-            const int e = halo[(size_t)d * g.F + f];
-            if (e < 0) continue;
-            int slot = -1;
-            for (size_t h = 0; h < hinfo.size(); ++h)
-                if (hinfo[h] == e) { slot = (int)h; break; }
-            if (slot < 0) { slot = (int)hinfo.size(); hinfo.push_back(e); }
-            hslot[(size_t)d * g.F + f] = (int16_t)slot;
-        }
-    c->NH = (int)hinfo.size();
-    if (hinfo.empty()) hinfo.push_back(-1);
-
-    int threads = c->p.threads;
-    if (threads <= 0) {
-        threads = (int)((B + 31) / 32 * 32);
-        if (threads > 512) threads = 512;
-        if (threads < 32) threads = 32;
-    }
-    if (threads % 32 || threads > 512 || (long long)threads * NPTMAX < B) {
-        delete c;
-        return DOPE_EINVAL;
-    }
-    c->threads = threads;
-    c->smem = (int)solver_smem_bytes(connectivity, (int)B);
-
-    int rc = DOPE_OK;
-    auto A = [&](void** ptr, size_t bytes) {
-        if (rc == DOPE_OK && cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) rc = DOPE_ENOMEM;
-    };
-    A((void**)&c->U, sizeof(int32_t) * (size_t)N);
-    A((void**)&c->Wl, sizeof(int32_t) * (size_t)N * nh);
-    A((void**)&c->yhat, (size_t)N);
-    A((void**)&c->yF, sizeof(double) * (size_t)g.K * g.F);
-    A((void**)&c->aF, sizeof(double) * (size_t)g.K * g.F);
-    A((void**)&c->r2blk, sizeof(double) * (size_t)g.K);
-    A((void**)&c->faceIndex, sizeof(int16_t) * (size_t)B);
-    A((void**)&c->faceLocal, sizeof(int16_t) * (size_t)(g.F ? g.F : 1));
-    A((void**)&c->halo, sizeof(int) * halo.size());
-    A((void**)&c->hslot, sizeof(int16_t) * hslot.size());
-    A((void**)&c->hinfo, sizeof(int) * hinfo.size());
-    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
-    A((void**)&c->ctrl, c->ctrl_bytes);
-    if (rc) { cudaGetLastError(); dope_destroy(c); return rc; }
-    if (cudaMemcpy(c->faceIndex, fidx.data(), sizeof(int16_t) * (size_t)B, cudaMemcpyHostToDevice) ||
-        (g.F && cudaMemcpy(c->faceLocal, floc.data(), sizeof(int16_t) * (size_t)g.F, cudaMemcpyHostToDevice)) ||
-        cudaMemcpy(c->halo, halo.data(), sizeof(int) * halo.size(), cudaMemcpyHostToDevice) ||
-        cudaMemcpy(c->hslot, hslot.data(), sizeof(int16_t) * hslot.size(), cudaMemcpyHostToDevice) ||
-        cudaMemcpy(c->hinfo, hinfo.data(), sizeof(int) * hinfo.size(), cudaMemcpyHostToDevice) ||
-        cudaMemset(c->ctrl, 0, c->ctrl_bytes)) {
-        dope_destroy(c);
-        return DOPE_ECUDA;
-    }
-    if (connectivity == 4) raise_smem_limits<4>();
-    else if (connectivity == 8) raise_smem_limits<8>();
-    else raise_smem_limits<6>();
-    {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (c->smem > optin) { dope_destroy(c); return DOPE_EINVAL; }
-    }
-    {   // persistent launch: as many CTAs as can be co-resident, at most K
-        const void* fn = connectivity == 4 ? (const void*)k_admm_persistent<4>
-                       : connectivity == 8 ? (const void*)k_admm_persistent<8>
-                                           : (const void*)k_admm_persistent<6>;
-        int dev = 0, sms = 0, coop = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        {
-            int optin0 = 0;
-            cudaDeviceGetAttribute(&optin0, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-            cudaFuncAttributes fa0;
-            if (cudaFuncGetAttributes(&fa0, fn) != cudaSuccess ||
-                (size_t)c->smem + fa0.sharedSizeBytes > (size_t)optin0 ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c->threads, c->smem) != cudaSuccess)
-                per_sm = 0;
-        }
-        cudaGetLastError();
-        long long cap = (long long)per_sm * sms;
-        c->persist_grid = (coop && cap > 0) ? (int)(cap < g.K ? cap : g.K) : 0;
-        // resident variant: every block's CTA co-resident with its extra shared memory
-        const void* fr = connectivity == 4 ? (const void*)k_admm_resident<4>
-                       : connectivity == 8 ? (const void*)k_admm_resident<8>
-                                           : (const void*)k_admm_resident<6>;
-        int rt = (int)((B + 31) / 32 * 32);
-        if (rt > 256) rt = 256;
-        int optin = 0;
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncAttributes fa;
-        size_t static_smem = 0;
-        if (cudaFuncGetAttributes(&fa, fr) == cudaSuccess) static_smem = fa.sharedSizeBytes;
-        else optin = 0;
-        for (int with_window = 1; with_window >= 0 && !c->resident; --with_window) {
-            const size_t rs = with_window ? window_smem_bytes(connectivity, (int)B, g.F, c->NH)
-                                          : resident_smem_bytes(connectivity, (int)B, g.F);
-            int per_sm_r = 0;
-            if (coop && rs + static_smem <= (size_t)optin && (long long)rt * NPTMAX >= B &&
-                c->p.threads == 0 && g.F <= 128 * 32) {
-                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, fr, rt, rs) != cudaSuccess)
-                    per_sm_r = 0;
-            }
-            cudaGetLastError();
-            if (per_sm_r > 0 && (long long)per_sm_r * sms >= g.K) {
-                c->resident = 1;
-                c->resident_smem = (int)rs;
-                c->resident_threads = rt;
-                c->window_ok = with_window;
-            }
-        }
-    }
-    rc = reset_state(c);
-    if (rc) { dope_destroy(c); return rc; }
-    *out = c;
     return DOPE_OK;
 }
 
 int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* stream) {
-    if (!c || !u || n != c->g.N || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    if (!c || !u || n != c->g.Nu || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     const float* src = u;
     if (where == DOPE_HOST) {
@@ -685,7 +834,7 @@ int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* st
     int rc = clear_status(c, st);
     if (rc) return rc;
     const int threads = 256;
-    k_set_unaries<<<grid_for(n, threads), threads, 0, st>>>(c->g, src, c->U, c->ctrl);
+    k_set_unaries<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, src, c->U, c->ctrl);
     CK(cudaGetLastError());
     Ctrl h{};
     rc = read_ctrl(c, &h, st);
@@ -695,7 +844,7 @@ int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* st
 }
 
 int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void* stream) {
-    if (!c || !wq || n != c->g.N || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    if (!c || !wq || n != c->g.Nu || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     const int nh = c->conn / 2;
     const int32_t* src = wq;
@@ -708,7 +857,7 @@ int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void*
     int rc = clear_status(c, st);
     if (rc) return rc;
     const int threads = 256;
-    const int blocks = grid_for(n, threads);
+    const int blocks = grid_for(c->g.N, threads);
     if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
     else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
     else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
@@ -755,14 +904,14 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
     }
     uint8_t* dst = labels;
     if (where == DOPE_HOST) {
-        rc = ensure_stage(c, (size_t)c->g.N, 1);
+        rc = ensure_stage(c, (size_t)c->g.Nu, 1);
         if (rc) return rc;
         dst = (uint8_t*)c->stage2;
     }
-    k_unpermute_u8<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, c->yhat, dst);
+    k_unpermute_u8<<<grid_for(c->g.Nu, threads), threads, 0, st>>>(c->g, c->yhat, dst);
     c->launches++;
     CK(cudaGetLastError());
-    if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.N, cudaMemcpyDeviceToHost, st));
+    if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     c->stats.kernel_launches = c->launches;
     if (iterations) *iterations = c->t;
@@ -1101,6 +1250,8 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     g.nbz = g.D / g.bd; g.nby = g.H / g.bh; g.nbx = g.W / g.bw;
     g.K = g.nbz * g.nby * g.nbx;
     g.N = N;
+    g.Du = g.D; g.Hu = g.H; g.Wu = g.W;
+    g.Nu = N;
     {   // face count (interior = (bd-2)(bh-2)(bw-2)-style box of the connectivity)
         const int iz = (connectivity == 6) ? (g.bd > 2 ? g.bd - 2 : 0) : g.bd;
         const int iy = g.bh > 2 ? g.bh - 2 : 0, ix = g.bw > 2 ? g.bw - 2 : 0;
@@ -1229,4 +1380,374 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     if (energy_int) *energy_int = (int64_t)e;
     if (iterations) *iterations = done;
     return converged ? DOPE_OK : DOPE_ENOTCONV;
+}
+
+// ---------------------------------------------------------------------------
+// Stream-ordered pieces used by the request server, and the batched launch.
+// ---------------------------------------------------------------------------
+int dope_upload_async(dope_ctx* c, const float* u, const int32_t* wq, int where, cudaStream_t st,
+                      cudaEvent_t after_copies) {
+    if (!c || !u || !wq || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    const size_t n = (size_t)c->g.Nu;
+    const int nh = c->conn / 2;
+    const float* su = u;
+    const int32_t* sw = wq;
+    if (where == DOPE_HOST) {
+        int rc = ensure_stage(c, sizeof(float) * n + sizeof(int32_t) * n * nh, 0);
+        if (rc) return rc;
+        float* du = (float*)c->stage;
+        int32_t* dw = (int32_t*)(du + n);
+        CK(cudaMemcpyAsync(du, u, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dw, wq, sizeof(int32_t) * n * nh, cudaMemcpyHostToDevice, st));
+        su = du;
+        sw = dw;
+    }
+    if (after_copies) CK(cudaEventRecord(after_copies, st));
+    int rc = clear_status(c, st);
+    if (rc) return rc;
+    const int threads = 256;
+    const int blocks = grid_for(c->g.N, threads);
+    k_set_unaries<<<blocks, threads, 0, st>>>(c->g, su, c->U, c->ctrl);
+    if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl);
+    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl);
+    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl);
+    CK(cudaGetLastError());
+    c->have_u = c->have_w = 1;   // provisional until dope_ctx_status has read the status word
+    return DOPE_OK;
+}
+
+int dope_ctx_status(dope_ctx* c, int* status, cudaStream_t st) {
+    if (!c || !status) return DOPE_EINVAL;
+    Ctrl h{};
+    int rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    *status = h.status;
+    if (h.status) c->have_u = c->have_w = 0;
+    return DOPE_OK;
+}
+
+int dope_status_async(dope_ctx* c, int* status_pinned, cudaStream_t st) {
+    if (!c || !status_pinned) return DOPE_EINVAL;
+    CK(cudaMemcpyAsync(status_pinned, &c->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return DOPE_OK;
+}
+
+int dope_ctx_max_iter(const dope_ctx* c) { return c ? c->p.max_iter : 0; }
+
+void dope_release_staging(dope_ctx* c) {
+    if (!c) return;
+    dfree(c->al, c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+}
+
+size_t dope_ctx_device_bytes(const dope_ctx* c) {
+    if (!c) return 0;
+    const size_t N = (size_t)c->g.N, KF = (size_t)c->g.K * c->g.F;
+    return N * 4 + N * 4 * (size_t)(c->conn / 2) + N + 16 * KF + 8 * (size_t)c->g.K + c->ctrl_bytes +
+           c->stage_bytes + c->stage2_bytes;
+}
+
+int64_t dope_ctx_pixels(const dope_ctx* c) { return c ? (int64_t)c->g.Nu : 0; }
+
+int dope_iterations(const dope_ctx* c, int* t, int* converged) {
+    if (!c) return DOPE_EINVAL;
+    if (t) *t = c->t;
+    if (converged) *converged = c->stats.converged;
+    return DOPE_OK;
+}
+
+int dope_finish_async(dope_ctx* c, uint8_t* labels_dev, int64_t* energy_pinned, cudaStream_t st) {
+    if (!c || !labels_dev) return DOPE_EINVAL;
+    const int threads = 256;
+    if (energy_pinned) {
+        CK(cudaMemsetAsync(&c->ctrl->energy, 0, sizeof(unsigned long long), st));
+        const int blocks = grid_for(c->g.N, threads);
+        if (c->conn == 4) k_energy<4><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
+        else if (c->conn == 8) k_energy<8><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
+        else k_energy<6><<<blocks, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
+        CK(cudaMemcpyAsync(energy_pinned, &c->ctrl->energy, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    }
+    k_unpermute_u8<<<grid_for(c->g.Nu, threads), threads, 0, st>>>(c->g, c->yhat, labels_dev);
+    CK(cudaGetLastError());
+    return DOPE_OK;
+}
+
+struct dope_batch_ws {
+    BatchDesc* hdesc = nullptr;   // pinned; copied to the constant table c_batch
+    BatchProb* hprob = nullptr;   // pinned
+    BatchProb* dprob = nullptr;
+    BatchOut* hout = nullptr;     // pinned
+    BatchOut* dout = nullptr;
+    Ctrl* bc = nullptr;
+    int* hstatus = nullptr;       // pinned copy of the launch's status word
+    int n = 0;                    // problems of the launch in flight
+    int threads = 0, smem = 0, grid = 0;
+    bool holds_table = false;     // this workspace's launch owns c_batch until collected
+};
+
+namespace {
+// c_batch is one table per process: one batched launch in flight at a time.
+// Taken by dope_batch_launch, given back by dope_batch_collect (or when the
+// workspace is destroyed), possibly from another thread: a binary semaphore.
+std::mutex g_table_m;
+std::condition_variable g_table_cv;
+bool g_table_busy = false;
+
+void table_acquire() {
+    std::unique_lock<std::mutex> lk(g_table_m);
+    g_table_cv.wait(lk, [] { return !g_table_busy; });
+    g_table_busy = true;
+}
+
+void table_release() {
+    {
+        std::lock_guard<std::mutex> lk(g_table_m);
+        g_table_busy = false;
+    }
+    g_table_cv.notify_one();
+}
+}  // namespace
+
+int dope_batch_ws_create(dope_batch_ws** out) {
+    if (!out) return DOPE_EINVAL;
+    *out = nullptr;
+    dope_batch_ws* w = new (std::nothrow) dope_batch_ws();
+    if (!w) return DOPE_ENOMEM;
+    if (cudaMallocHost(&w->hdesc, sizeof(BatchDesc) * BATCH_MAX) != cudaSuccess ||
+        cudaMallocHost(&w->hprob, sizeof(BatchProb) * BATCH_MAX) != cudaSuccess ||
+        cudaMalloc(&w->dprob, sizeof(BatchProb) * BATCH_MAX) != cudaSuccess ||
+        cudaMallocHost(&w->hout, sizeof(BatchOut) * BATCH_MAX) != cudaSuccess ||
+        cudaMalloc(&w->dout, sizeof(BatchOut) * BATCH_MAX) != cudaSuccess ||
+        cudaMalloc(&w->bc, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMallocHost(&w->hstatus, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        dope_batch_ws_destroy(w);
+        return DOPE_ENOMEM;
+    }
+    *out = w;
+    return DOPE_OK;
+}
+
+void dope_batch_ws_destroy(dope_batch_ws* w) {
+    if (!w) return;
+    if (w->holds_table) {
+        w->holds_table = false;
+        table_release();
+    }
+    cudaFreeHost(w->hdesc);
+    cudaFreeHost(w->hprob);
+    cudaFree(w->dprob);
+    cudaFreeHost(w->hout);
+    cudaFree(w->dout);
+    cudaFree(w->bc);
+    cudaFreeHost(w->hstatus);
+    delete w;
+}
+
+namespace {
+
+// Co-resident CTAs per SM of k_admm_batch for (threads, dynamic smem), cached.
+int batch_per_sm(int threads, int smem) {
+    static std::mutex mu;
+    static std::vector<int> keys, vals;
+    std::lock_guard<std::mutex> lk(mu);
+    const int key = threads * (1 << 20) + smem;
+    for (size_t i = 0; i < keys.size(); ++i)
+        if (keys[i] == key) return vals[i];
+    int dev = 0, optin = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, batch_fn(threads)) != cudaSuccess ||
+        (size_t)smem + fa.sharedSizeBytes > (size_t)optin ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fn(threads), threads, smem) !=
+            cudaSuccess)
+        per_sm = 0;
+    cudaGetLastError();
+    keys.push_back(key);
+    vals.push_back(per_sm);
+    return per_sm;
+}
+
+}  // namespace
+
+int dope_batch_launch(dope_ctx* const* cs, int n, int n_iter, int exit_on_done, int clear_status,
+                      const int* yield_flag, dope_batch_ws* w, cudaStream_t st) {
+    if (!cs || n < 1 || n > BATCH_MAX || !w || n_iter < 0) return DOPE_EINVAL;
+    int threads = 32, smem = 0;
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        dope_ctx* c = cs[i];
+        if (!c || !c->have_u || !c->have_w) return DOPE_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (cs[j] == c) return DOPE_EINVAL;
+        const int width = solver_width(c->g.B, c->threads);
+        if (width > threads) threads = width;
+        if (c->smem > smem) smem = c->smem;
+        total += c->g.K;
+        BatchDesc& d = w->hdesc[i];
+        d.g = c->g;
+        d.U = c->U;
+        d.Wl = c->Wl;
+        d.yhat = c->yhat;
+        d.yF = c->yF;
+        d.aF = c->aF;
+        d.r2blk = c->r2blk;
+        d.faceIndex = c->faceIndex;
+        d.halo = c->halo;
+        d.faceLocal = c->faceLocal;
+        d.Cgiven = nullptr;
+        d.ctrl = c->ctrl;
+        d.eps = c->p.eps;
+        d.relabel_period = c->p.relabel_period;
+        d.max_pulses = c->p.max_pulses;
+        d.fold_rounds = c->p.fold_rounds;
+        d.conn = c->conn;
+        BatchProb& b = w->hprob[i];
+        b.t0 = c->t;
+        const int left = c->p.max_iter - c->t;
+        b.n = n_iter < left ? n_iter : left;
+        if (b.n < 0) b.n = 0;
+        b.K = c->g.K;
+        b.pad = 0;
+        b.mu = c->mu;
+        b.mu_fact = c->p.mu_fact;
+    }
+    raise_all_smem_limits(cs[0]->conn);
+    int dev = 0, sms = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const int per_sm = batch_per_sm(threads, smem);
+    if (!coop || per_sm <= 0) return DOPE_EUNSUPPORTED;
+    long long grid = (long long)per_sm * sms;
+    if (grid > total) grid = total;
+    if (grid < 1) grid = 1;
+    BatchArgs P;
+    P.probs = w->dprob;
+    P.out = w->dout;
+    P.nprob = n;
+    P.exit_on_done = exit_on_done ? 1 : 0;
+    P.yield_flag = yield_flag;
+    P.bc = w->bc;
+    P.spin_limit = 4000000000LL;   // about 2 s at the GB300 clock
+    if (w->holds_table) return DOPE_EINVAL;   // previous launch not collected
+    table_acquire();
+    w->holds_table = true;
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_batch, w->hdesc, sizeof(BatchDesc) * (size_t)n, 0,
+                                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->dprob, w->hprob, sizeof(BatchProb) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_batch_prep<<<n, 128, 0, st>>>(P, clear_status ? 1 : 0);
+        e = cudaGetLastError();
+    }
+    void* args[] = {&P};
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(batch_fn(threads), (int)grid, threads, args, smem, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->hout, w->dout, sizeof(BatchOut) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->hstatus, &w->bc->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(st);   // nothing may still read the table
+        w->holds_table = false;
+        table_release();
+        return DOPE_ECUDA;
+    }
+    for (int i = 0; i < n; ++i) cs[i]->launches += 2;
+    w->n = n;
+    w->threads = threads;
+    w->smem = smem;
+    w->grid = (int)grid;
+    return DOPE_OK;
+}
+
+int dope_batch_collect(dope_ctx* const* cs, int n, dope_batch_ws* w, int* t, int* conv, int* status) {
+    if (!cs || !w || n != w->n) return DOPE_EINVAL;
+    if (w->holds_table) {
+        w->holds_table = false;
+        table_release();
+    }
+    for (int i = 0; i < n; ++i) {
+        dope_ctx* c = cs[i];
+        const BatchOut& o = w->hout[i];
+        c->t = o.t;
+        c->mu = o.mu;
+        memset(&c->stats, 0, sizeof(c->stats));
+        c->stats.iterations = o.t;
+        c->stats.converged = o.conv;
+        c->stats.rmax_last = std::sqrt(o.r2);
+        c->stats.kernel_launches = c->launches;
+        if (t) t[i] = o.t;
+        if (conv) conv[i] = o.conv;
+        if (status) status[i] = o.status;
+    }
+    w->n = 0;
+    return *w->hstatus;
+}
+
+namespace {
+std::mutex g_batch_mu;
+dope_batch_ws* g_batch_ws[NOALLOC_MAX_DEVICES];
+}  // namespace
+
+extern "C" int dope_iterate_batch(dope_ctx* const* ctxs, int n, int n_iter, int* iterations,
+                                  int* converged, int* status, void* stream) {
+    if (!ctxs || n < 1 || n > DOPE_BATCH_MAX || n_iter < 0) return DOPE_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return DOPE_ECUDA;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (!g_batch_ws[dev]) {
+        int rc = dope_batch_ws_create(&g_batch_ws[dev]);
+        if (rc) return rc;
+    }
+    dope_batch_ws* w = g_batch_ws[dev];
+    cudaStream_t st = S(stream);
+    for (int i = 0; i < n; ++i)
+        if (ctxs[i]) ctxs[i]->launches = 0;
+    int rc = dope_batch_launch(ctxs, n, n_iter, 0, 1, nullptr, w, st);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(st));
+    std::vector<int> sts((size_t)n, 0);
+    rc = dope_batch_collect(ctxs, n, w, iterations, converged, sts.data());
+    if (status)
+        for (int i = 0; i < n; ++i) status[i] = sts[(size_t)i];
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+        if (sts[(size_t)i]) return sts[(size_t)i];
+    return DOPE_OK;
+}
+
+extern "C" int dope_labels(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, void* stream) {
+    if (!c || !labels || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    if (!c->have_u || !c->have_w) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    int rc;
+    if (energy_int) {
+        rc = energy_of(c, c->yhat, energy_int, st);
+        if (rc) return rc;
+    }
+    uint8_t* dst = labels;
+    if (where == DOPE_HOST) {
+        rc = ensure_stage(c, (size_t)c->g.Nu, 1);
+        if (rc) return rc;
+        dst = (uint8_t*)c->stage2;
+    }
+    const int threads = 256;
+    k_unpermute_u8<<<grid_for(c->g.Nu, threads), threads, 0, st>>>(c->g, c->yhat, dst);
+    CK(cudaGetLastError());
+    if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return DOPE_OK;
+}
+
+int dope_run_single(dope_ctx* c, cudaStream_t st, int* t, int* conv) {
+    if (!c) return DOPE_EINVAL;
+    c->launches = 0;
+    int rc = run_iterations(c, c->p.max_iter - c->t, st);
+    if (t) *t = c->t;
+    if (conv) *conv = c->stats.converged;
+    return rc;
 }

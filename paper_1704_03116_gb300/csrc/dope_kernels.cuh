@@ -36,11 +36,16 @@ __host__ __device__ inline size_t solver_smem_bytes(int conn, int B) {
 }
 
 struct Geo {
-    int D, H, W;            // grid (D = 1 for 2-D)
+    int D, H, W;            // grid (D = 1 for 2-D), a whole number of blocks
     int bd, bh, bw, B;      // block shape and volume
     int nbz, nby, nbx, K;   // block grid
     int F;                  // face pixels per block
     long long N;
+    // caller's grid, <= (D, H, W); pixels beyond it are padding with zero
+    // unary and zero n-links (isolated, so they change no other pixel's
+    // iterates and add nothing to the energy)
+    int Du, Hu, Wu;
+    long long Nu;
 };
 
 struct Ctrl {
@@ -56,7 +61,7 @@ struct Ctrl {
     int bfs_levels_max;
     int fold_rounds_max;
     unsigned bar_count;             // grid barrier of the persistent kernel: arrivals
-    unsigned bar_gen;               // (unused)
+    unsigned yield;                 // batched launch: the host's request to end it, as read by CTA 0
     int abort;                      // set when a barrier wait gave up
     int iters_done;                 // last iteration the persistent kernel ran
     int thaw;                       // earliest iteration of a window whose labels moved
@@ -105,6 +110,37 @@ struct UpdArgs {
     double mu;
     int t;
 };
+
+// Values of one iteration t that the block solver and the face update need:
+// mu, and the integer forced-node test bound H = floor(512 mu) when
+// 512 mu < 2^52 (int_test).
+struct IterArgs {
+    double mu;
+    long long H;
+    int t, first, int_test;
+};
+
+__device__ __forceinline__ IterArgs iter_args(int t, double mu) {
+    IterArgs it;
+    it.mu = mu;
+    it.t = t;
+    it.first = (t == 1);
+    const double h = __dmul_rn(__dmul_rn(1024.0, mu), 0.5);
+    it.int_test = h < 4503599627370496.0 ? 1 : 0;   // 2^52
+    it.H = it.int_test ? (long long)floor(h) : 0;
+    return it;
+}
+
+// The iteration values a SolveArgs carries (k_block_solve, test hooks).
+__device__ __forceinline__ IterArgs iter_of(const SolveArgs& A) {
+    IterArgs it;
+    it.mu = A.mu;
+    it.H = A.H;
+    it.t = A.t;
+    it.first = A.first;
+    it.int_test = A.int_test;
+    return it;
+}
 
 // Halo table entry of (face slot f, direction d): -1 if the neighbour is in
 // the same block, else (block-offset code << 24) | (ln << 12) | fn with the
@@ -409,13 +445,16 @@ __device__ __forceinline__ int bfs_bits(const int* __restrict__ res, const int* 
     return __syncthreads_or(act);
 }
 
-template <int CONN>
-__device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned char* smem, int bw, int pl,
+// The block solver and the face update are templates over the argument
+// block (SolveArgs / UpdArgs, or a batched launch's per-problem descriptor):
+// any type with the fields they read.
+template <int CONN, class SA>
+__device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsigned char* smem, int bw, int pl,
                                        unsigned long long imask, long long c_start, uint8_t* lab_smem,
                                        bool to_global = true);
 
-template <int CONN>
-__device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
+template <int CONN, class SA>
+__device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, unsigned char* smem) {
     const Geo& g = A.g;
     const int B = g.B;
     const int tid = threadIdx.x, NT = blockDim.x;
@@ -430,7 +469,7 @@ __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
     const int bw = g.bw, pl = g.bh * g.bw;
     constexpr int nh = CONN / 2;
-    const double m1024 = __dmul_rn(1024.0, A.mu);
+    const double m1024 = __dmul_rn(1024.0, it.mu);
     unsigned long long imask = 0;        // 8 bits per own node: intra-block directions
     const long long c_start = clock64();
 
@@ -453,11 +492,11 @@ __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
         }
         imask |= (unsigned long long)m << (8 * q);
         C64[v] = A.Cgiven ? A.Cgiven[gi] : (long long)A.U[gi];
-        st[v] = A.first ? 0 : __ldcg(&A.yhat[gi]);
+        st[v] = it.first ? 0 : __ldcg(&A.yhat[gi]);
     }
     __syncthreads();
     // 1b. backward n-links from shared memory, n-link sums, interior unaries
-    const bool need_caps = !A.Cgiven && !A.first;
+    const bool need_caps = !A.Cgiven && !it.first;
 #pragma unroll 1
     for (int q = 0; q < NPTMAX; ++q) {
         int v = tid + q * NT;
@@ -480,8 +519,8 @@ __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
         if (need_caps && A.faceIndex[v] < 0) {
             // interior pixel: y = yhat, a = 0 (see the note above face_cap)
             const long long Ui = C64[v];
-            const long long T = yh ? Ui - A.H : Ui + A.H;
-            if (A.int_test && (yh ? (T < -(long long)cs) : (T >= (long long)cs))) {
+            const long long T = yh ? Ui - it.H : Ui + it.H;
+            if (it.int_test && (yh ? (T < -(long long)cs) : (T >= (long long)cs))) {
                 C64[v] = T;
             } else {
                 const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
@@ -498,14 +537,14 @@ __device__ void solve_block(const SolveArgs& A, int k, unsigned char* smem) {
         }
     }
     __syncthreads();
-    cut_block<CONN>(A, k, smem, bw, pl, imask, c_start, nullptr);
+    cut_block<CONN, SA>(A, k, smem, bw, pl, imask, c_start, nullptr);
 }
 
 // Steps a5-a6 on the graph the build left in shared memory (res, C64, capsum,
 // st): exact folding, push-relabel, canonical cut, labels to A.yhat (and to
 // lab_smem when given), statistics.
-template <int CONN>
-__device__ __forceinline__ void cut_block(const SolveArgs& A, int k, unsigned char* smem, int bw, int pl,
+template <int CONN, class SA>
+__device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsigned char* smem, int bw, int pl,
                                        unsigned long long imask, long long c_start, uint8_t* lab_smem,
                                        bool to_global) {
     const Geo& g = A.g;
@@ -750,7 +789,7 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
     }
     __syncthreads();
     if (s_skip) return;
-    solve_block<CONN>(A, blockIdx.x, smem);
+    solve_block<CONN>(A, iter_of(A), blockIdx.x, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -761,8 +800,8 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
 //   y_i = (yhat_i + a_i) - (G_i / 1024) / mu               (Eq. 10)
 //   a_i = a_i + (yhat_i - y_i)                             (Eq. 11)
 // ---------------------------------------------------------------------------
-template <int CONN>
-__device__ void update_block(const UpdArgs& A, int k) {
+template <int CONN, class UA>
+__device__ void update_block(const UA& __restrict__ A, double mu, int t, int k) {
     const Geo& g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     constexpr int nh = CONN / 2;
@@ -798,7 +837,7 @@ __device__ void update_block(const UpdArgs& A, int k) {
             const double aa = __ldcg(&A.aF[s]);
             // G = 0: (G/1024)/mu = +0 and x - (+0) = x exactly, so the division is skipped
             const double ya = __dadd_rn((double)yh, aa);
-            const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, A.mu)) : ya;
+            const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
             const double an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
             A.yF[s] = yn;
             A.aF[s] = an;
@@ -810,10 +849,10 @@ __device__ void update_block(const UpdArgs& A, int k) {
     }
     __syncthreads();
     if (tid == 0) {
-        double t = 0.0;
-        for (int ch = 0; ch < nchunks; ++ch) t = __dadd_rn(t, part[ch]);
-        A.r2blk[k] = t;
-        atomicMax(&A.ctrl->r2max[A.t], (unsigned long long)__double_as_longlong(t));
+        double r2 = 0.0;
+        for (int ch = 0; ch < nchunks; ++ch) r2 = __dadd_rn(r2, part[ch]);
+        A.r2blk[k] = r2;
+        atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
     }
     __syncthreads();   // part is reused by the next block
 }
@@ -822,7 +861,7 @@ __device__ void update_block(const UpdArgs& A, int k) {
 template <int CONN>
 __global__ void __launch_bounds__(256) k_face_update(UpdArgs A) {
     if (*(volatile int*)&A.ctrl->conv_t) return;
-    update_block<CONN>(A, blockIdx.x);
+    update_block<CONN>(A, A.mu, A.t, blockIdx.x);
 }
 
 // Threads of a k_face_update CTA (one CTA per block) for F face slots.
@@ -844,14 +883,28 @@ __device__ __forceinline__ long long bm_index(const Geo& g, long long i) {
     return (long long)k * g.B + l;
 }
 
-// U = rne(1024 u); |U| < 2^30 and u finite, else DOPE_EOVERFLOW.
+// Caller-grid index of padded pixel (z, y, x), or -1 for a padding pixel.
+__device__ __forceinline__ long long user_index(const Geo& g, int z, int y, int x) {
+    if (z >= g.Du || y >= g.Hu || x >= g.Wu) return -1;
+    return ((long long)z * g.Hu + y) * g.Wu + x;
+}
+
+// U = rne(1024 u); |U| < 2^30 and u finite, else DOPE_EOVERFLOW.  Padding
+// pixels get 0.
 __global__ void k_set_unaries(Geo g, const float* __restrict__ u, int32_t* __restrict__ U, Ctrl* c) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
          i += (long long)gridDim.x * blockDim.x) {
-        const double v = __dmul_rn(1024.0, (double)u[i]);
+        const int x = (int)(i % g.W);
+        const long long r = i / g.W;
+        const int y = (int)(r % g.H);
+        const int z = (int)(r / g.H);
+        const long long iu = user_index(g, z, y, x);
         int q = 0;
-        if (!(fabs(v) < 1073741823.5)) set_status(c, 4);
-        else q = (int)__double2ll_rn(v);
+        if (iu >= 0) {
+            const double v = __dmul_rn(1024.0, (double)u[iu]);
+            if (!(fabs(v) < 1073741823.5)) set_status(c, 4);
+            else q = (int)__double2ll_rn(v);
+        }
         U[bm_index(g, i)] = q;
     }
 }
@@ -869,13 +922,18 @@ __global__ void k_set_weights(Geo g, const int32_t* __restrict__ wq, int32_t* __
         const int y = (int)(r % g.H);
         const int z = (int)(r / g.H);
         const long long b = bm_index(g, i);
+        const long long iu = user_index(g, z, y, x);
 #pragma unroll
         for (int d = 0; d < nh; ++d) {
             int dz, dy, dx;
             dir_off<CONN>(d, dz, dy, dx);
-            const int w = wq[(long long)d * g.N + i];
+            if (iu < 0) {           // padding pixel: no n-links
+                Wl[(long long)d * g.N + b] = 0;
+                continue;
+            }
+            const int w = wq[(long long)d * g.Nu + iu];
             int q = 0;
-            const bool inside = (z + dz < g.D) && (y + dy < g.H) && (x + dx >= 0) && (x + dx < g.W);
+            const bool inside = (z + dz < g.Du) && (y + dy < g.Hu) && (x + dx >= 0) && (x + dx < g.Wu);
             if (w < 0) set_status(c, 2);
             else if (!inside && w != 0) set_status(c, 1);
             else {
@@ -897,11 +955,16 @@ __global__ void k_init_state(Geo g, double* yF, double* aF) {
     }
 }
 
-// labels (image order) <- yhat (block-major)
+// labels (caller's image order, padding dropped) <- yhat (block-major)
 __global__ void k_unpermute_u8(Geo g, const uint8_t* __restrict__ src, uint8_t* __restrict__ dst) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
-         i += (long long)gridDim.x * blockDim.x)
-        dst[i] = src[bm_index(g, i)];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.Nu;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.Wu);
+        const long long r = i / g.Wu;
+        const int y = (int)(r % g.Hu);
+        const int z = (int)(r / g.Hu);
+        dst[i] = src[bm_index(g, ((long long)z * g.H + y) * g.W + x)];
+    }
 }
 
 __global__ void k_permute_u8(Geo g, const uint8_t* __restrict__ src, uint8_t* __restrict__ dst) {
@@ -1107,8 +1170,14 @@ __device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned nblocks, unsigned& n
     return s_ok != 0;
 }
 
-template <int CONN>
-__global__ void __launch_bounds__(512, 2) k_admm_persistent(PersistArgs P) {
+// Occupancy of the block-solver kernels by CTA width: 256 threads (up to
+// 2048 nodes, 4 per thread for 32x32 blocks) run 3 CTAs per SM with 80
+// registers; 512 threads (blocks up to 4096 nodes) run 2 CTAs per SM with 64.
+template <int NT>
+struct SolverOcc { static constexpr int min_blocks = NT <= 256 ? 3 : 2; };
+
+template <int CONN, int NT>
+__global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persistent(PersistArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_k;
     Ctrl* c = P.s.ctrl;
@@ -1118,31 +1187,21 @@ __global__ void __launch_bounds__(512, 2) k_admm_persistent(PersistArgs P) {
     unsigned nbar = 0;
     for (int j = 0; j < P.n; ++j) {
         t = P.t0 + j + 1;
-        SolveArgs A = P.s;
-        A.t = t;
-        A.first = (t == 1);
-        A.check_prev = 0;
-        A.mu = mu;
-        const double h = __dmul_rn(__dmul_rn(1024.0, mu), 0.5);
-        A.int_test = h < 4503599627370496.0 ? 1 : 0;   // 2^52
-        A.H = A.int_test ? (long long)floor(h) : 0;
+        const IterArgs it = iter_args(t, mu);
         // the update counter is idle during the solve phase and vice versa,
         // so each is reset in the other phase
         const long long c0 = clock64();
         if (blockIdx.x == 0 && threadIdx.x == 0) c->work[1] = 0u;
         for (int k = next_block(P.dynamic, &c->work[0], -1, &s_k); k < K;
              k = next_block(P.dynamic, &c->work[0], k, &s_k))
-            solve_block<CONN>(A, k, smem);
+            solve_block<CONN>(P.s, it, k, smem);
         const long long c1 = clock64();
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
         const long long c2 = clock64();
         if (blockIdx.x == 0 && threadIdx.x == 0) c->work[0] = 0u;
-        UpdArgs U = P.u;
-        U.t = t;
-        U.mu = mu;
         for (int k = next_block(P.dynamic, &c->work[1], -1, &s_k); k < K;
              k = next_block(P.dynamic, &c->work[1], k, &s_k))
-            update_block<CONN>(U, k);
+            update_block<CONN>(P.u, mu, t, k);
         const long long c3 = clock64();
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
         if (threadIdx.x == 0) {
@@ -1845,6 +1904,244 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         c->iters_done = t;
         c->conv_t = conv ? t : 0;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batched path: many problems (contexts) advanced in one cooperative launch.
+// Every iteration the blocks of all live problems form one list (live problem
+// q owns entries base_q .. base_q + K_q - 1) handed out by an atomic counter,
+// in the solve phase and again in the update phase.  Each problem keeps its
+// own iteration count, mu and stop test (Algorithm 1 per problem, unchanged),
+// and the per-block arithmetic is that of the single-problem kernels, so a
+// problem's iterates are bit-identical whatever it is batched with.  A problem
+// leaves the list when its stop test holds or its allowance of iterations is
+// used up.  The launch ends when no problem is left, when the host's yield
+// flag is set (read at an iteration boundary) or, if asked, at the first
+// boundary where a problem finished while others go on.
+// ---------------------------------------------------------------------------
+constexpr int BATCH_MAX = 256;   // problems per launch
+
+// Per-problem arguments of the block solver and the face update, in constant
+// memory: every CTA reads the same problem's fields, which the constant cache
+// broadcasts, as the single-problem kernels read theirs from the kernel
+// parameters.  Written by the host before each batched launch (one batched
+// launch in flight per process at a time).
+struct BatchDesc {
+    Geo g;
+    const int32_t* U;
+    const int32_t* Wl;
+    uint8_t* yhat;
+    double* yF;
+    double* aF;
+    double* r2blk;
+    const int16_t* faceIndex;
+    const int* halo;
+    const int16_t* faceLocal;
+    const long long* Cgiven;        // always null here
+    Ctrl* ctrl;
+    double eps;
+    int relabel_period, max_pulses, fold_rounds, conn;
+};
+
+__constant__ BatchDesc c_batch[BATCH_MAX];
+
+// Per-problem loop state of a batched launch (device memory).
+struct BatchProb {
+    int t0;                 // iterations done before the launch
+    int n;                  // iterations allowed in this launch
+    int K;                  // blocks
+    int pad;
+    double mu;              // mu of iteration t0 + 1
+    double mu_fact;
+};
+
+// Per-problem result of a batched launch (written by CTA 0 at its end).
+struct BatchOut {
+    int t;                  // iterations done
+    int conv;               // the stop test held at iteration t
+    int status;             // the problem's status word
+    int pad;
+    double mu;              // mu of iteration t + 1
+    double r2;              // max_k r2_k of iteration t (0 if t = 0)
+};
+
+struct BatchArgs {
+    const BatchProb* probs; // [nprob], device memory
+    BatchOut* out;          // [nprob]
+    int nprob;              // 1 .. BATCH_MAX
+    int exit_on_done;
+    const int* yield_flag;  // host-mapped or device int; nonzero ends the launch (may be null)
+    Ctrl* bc;               // barrier and block counters of the launch (zeroed by the host)
+    long long spin_limit;
+};
+
+// Live problem owning list entry gk (binary search over the live bases).
+__device__ __forceinline__ int batch_owner(const int* lbase, int nlive, int gk) {
+    int lo = 0, hi = nlive - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (lbase[mid] <= gk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(BatchArgs P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_mu[BATCH_MAX];
+    __shared__ int s_t[BATCH_MAX];
+    __shared__ int s_K[BATCH_MAX];
+    __shared__ int s_list[BATCH_MAX];     // live problems, in problem order
+    __shared__ int s_lbase[BATCH_MAX];    // their first list entries
+    __shared__ unsigned char s_alive[BATCH_MAX];
+    __shared__ unsigned char s_conv[BATCH_MAX];
+    __shared__ int s_nlive, s_total, s_k, s_any, s_done;
+    const int np = P.nprob;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    Ctrl* bc = P.bc;
+    for (int p = tid; p < np; p += blockDim.x) {
+        const BatchProb bp = P.probs[p];
+        s_t[p] = bp.t0;
+        s_mu[p] = bp.mu;
+        s_K[p] = bp.K;
+        s_alive[p] = (bp.n > 0 && __ldcg(&c_batch[p].ctrl->status) == 0) ? 1 : 0;
+        s_conv[p] = 0;
+    }
+    __syncthreads();
+    unsigned nbar = 0;
+    for (;;) {
+        // live list and its block bases (warp 0, ballot + shuffle scan)
+        if (wid == 0) {
+            int run = 0, cnt = 0;
+            for (int c0 = 0; c0 < np; c0 += 32) {
+                const int p = c0 + lane;
+                const bool al = p < np && s_alive[p];
+                const int kp = al ? s_K[p] : 0;
+                int v = kp;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, al);
+                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+                if (al) {
+                    s_list[pos] = p;
+                    s_lbase[pos] = run + v - kp;
+                }
+                run += __shfl_sync(0xffffffffu, v, 31);
+                cnt += __popc(m);
+            }
+            if (lane == 0) {
+                s_nlive = cnt;
+                s_total = run;
+            }
+        }
+        __syncthreads();
+        const int nlive = s_nlive, total = s_total;
+        if (nlive == 0) break;
+        // solve phase (the update counter is idle now and is reset here)
+        if (blockIdx.x == 0 && tid == 0) bc->work[1] = 0u;
+        for (;;) {
+            __syncthreads();
+            if (tid == 0) s_k = (int)atomicAdd(&bc->work[0], 1u);
+            __syncthreads();
+            const int gk = s_k;
+            if (gk >= total) break;
+            const int q = batch_owner(s_lbase, nlive, gk);
+            const int p = s_list[q];
+            const int k = gk - s_lbase[q];
+            const IterArgs it = iter_args(s_t[p] + 1, s_mu[p]);
+            const int conn = c_batch[p].conn;
+            if (conn == 4) solve_block<4>(c_batch[p], it, k, smem);
+            else if (conn == 8) solve_block<8>(c_batch[p], it, k, smem);
+            else solve_block<6>(c_batch[p], it, k, smem);
+        }
+        if (!grid_sync(bc, gridDim.x, nbar, P.spin_limit)) break;
+        // update phase
+        if (blockIdx.x == 0 && tid == 0) bc->work[0] = 0u;
+        for (;;) {
+            __syncthreads();
+            if (tid == 0) s_k = (int)atomicAdd(&bc->work[1], 1u);
+            __syncthreads();
+            const int gk = s_k;
+            if (gk >= total) break;
+            const int q = batch_owner(s_lbase, nlive, gk);
+            const int p = s_list[q];
+            const int k = gk - s_lbase[q];
+            const int conn = c_batch[p].conn;
+            if (conn == 4) update_block<4>(c_batch[p], s_mu[p], s_t[p] + 1, k);
+            else if (conn == 8) update_block<8>(c_batch[p], s_mu[p], s_t[p] + 1, k);
+            else update_block<6>(c_batch[p], s_mu[p], s_t[p] + 1, k);
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            unsigned y = 0;
+            if (P.yield_flag) {
+                cuda::atomic_ref<const int, cuda::thread_scope_system> f(*P.yield_flag);
+                y = f.load(cuda::memory_order_relaxed) != 0 ? 1u : 0u;
+            }
+            bc->yield = y;
+        }
+        if (!grid_sync(bc, gridDim.x, nbar, P.spin_limit)) break;
+        // per-problem stop tests; every CTA takes the same decisions
+        if (tid == 0) { s_any = 0; s_done = 0; }
+        __syncthreads();
+        for (int q = tid; q < nlive; q += blockDim.x) {
+            const int p = s_list[q];
+            const int t = s_t[p] + 1;
+            const double r2 = __longlong_as_double((long long)__ldcg(&c_batch[p].ctrl->r2max[t]));
+            const bool conv = !(__dsqrt_rn(r2) > c_batch[p].eps);
+            s_t[p] = t;
+            s_mu[p] = __dmul_rn(s_mu[p], P.probs[p].mu_fact);
+            if (conv || t - P.probs[p].t0 >= P.probs[p].n) {
+                s_alive[p] = 0;
+                s_conv[p] = conv ? 1 : 0;
+                s_done = 1;
+            } else {
+                s_any = 1;
+            }
+        }
+        __syncthreads();
+        const unsigned yield = __ldcg(&bc->yield);
+        if (!s_any || yield || (P.exit_on_done && s_done)) break;
+    }
+    if (blockIdx.x == 0) {
+        for (int p = tid; p < np; p += blockDim.x) {
+            const Ctrl* c = c_batch[p].ctrl;
+            BatchOut o;
+            o.t = s_t[p];
+            o.conv = s_conv[p];
+            o.status = __ldcg(&c->status);
+            o.pad = 0;
+            o.mu = s_mu[p];
+            o.r2 = o.t > 0 ? __longlong_as_double((long long)__ldcg(&c->r2max[o.t])) : 0.0;
+            P.out[p] = o;
+        }
+    }
+}
+
+// Before a batched launch (one CTA per problem): zero the launch's barrier
+// and block counters, the trace slots the launch will fill and, if asked,
+// each problem's status word.
+__global__ void k_batch_prep(BatchArgs P, int clear_status) {
+    const int p = blockIdx.x;
+    if (p == 0 && threadIdx.x == 0) {
+        Ctrl* bc = P.bc;
+        bc->status = 0;
+        bc->bar_count = 0u;
+        bc->abort = 0;
+        bc->yield = 0u;
+        bc->work[0] = 0u;
+        bc->work[1] = 0u;
+    }
+    if (p >= P.nprob) return;
+    const BatchProb bp = P.probs[p];
+    Ctrl* c = c_batch[p].ctrl;
+    if (threadIdx.x == 0 && clear_status) {
+        c->status = 0;
+        c->conv_t = 0;
+    }
+    for (int j = threadIdx.x; j < bp.n; j += blockDim.x) c->r2max[bp.t0 + 1 + j] = 0ull;
 }
 
 }  // namespace dope

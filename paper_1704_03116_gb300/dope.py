@@ -57,6 +57,36 @@ class dope_profile(ctypes.Structure):
                 ("iterations", ctypes.c_int64)]
 
 
+class dope_server_params(ctypes.Structure):
+    _fields_ = [("hbm_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_int), ("mode", ctypes.c_int),
+                ("launch_iters", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class dope_request(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("connectivity", ctypes.c_int), ("grid", ctypes.c_int64 * 3),
+                ("block_shape", ctypes.c_int32 * 3), ("lambda_", ctypes.c_double), ("params", dope_params),
+                ("use_params", ctypes.c_int), ("where_inputs", ctypes.c_int), ("unaries", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("where_labels", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("tag", ctypes.c_uint64)]
+
+
+class dope_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("energy_int", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class dope_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "admitted", "completed", "launches", "yields",
+                                              "queued", "in_flight", "max_in_flight")] + \
+               [(k, ctypes.c_uint64) for k in ("bytes_limit", "bytes_in_use", "bytes_peak")] + \
+               [("gpu_launch_s", ctypes.c_double)]
+
+
+DOPE_BATCH_MAX = 256
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
@@ -84,6 +114,14 @@ def _load():
         "dope_get_profile": (i32, [vp, P(dope_profile)]),
         "dope_solve_noalloc": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params),
                                      vp, vp, vp, P(ctypes.c_int64), P(ctypes.c_int), vp]),
+        "dope_iterate_batch": (i32, [P(vp), i32, i32, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), vp]),
+        "dope_labels": (i32, [vp, vp, i32, P(ctypes.c_int64), vp]),
+        "dope_server_create": (i32, [P(dope_server_params), P(vp)]),
+        "dope_server_submit": (i32, [vp, P(dope_request), P(ctypes.c_uint64)]),
+        "dope_server_poll": (i32, [vp, P(dope_result), i32, P(ctypes.c_int), dbl]),
+        "dope_server_clock": (dbl, [vp]),
+        "dope_server_get_stats": (i32, [vp, P(dope_server_stats)]),
+        "dope_server_destroy": (None, [vp]),
         "dope_destroy": (None, [vp]),
         "dope_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -310,6 +348,62 @@ def dope_solve_noalloc(grid, connectivity, block_shape, lam, u, wq, labels, para
     return e.value, it.value, rc
 
 
+def dope_iterate_batch(ctxs, n_iter, stream=None):
+    """One batched launch over the contexts; per context (iterations, converged, status)."""
+    n = len(ctxs)
+    arr = (ctypes.c_void_p * n)(*[c if isinstance(c, int) else c.value for c in ctxs])
+    it = (ctypes.c_int * n)()
+    cv = (ctypes.c_int * n)()
+    st = (ctypes.c_int * n)()
+    rc = _lib.dope_iterate_batch(arr, n, int(n_iter), it, cv, st, _stream(stream))
+    _check(rc, "dope_iterate_batch")
+    return [(it[i], bool(cv[i]), st[i]) for i in range(n)]
+
+
+def dope_labels(ctx, labels, stream=None):
+    """Labels of the last iteration into `labels`; returns E_int."""
+    p, where, keep = _ptr(labels, _t(np.uint8))
+    e = ctypes.c_int64(0)
+    _check(_lib.dope_labels(ctx, p, where, ctypes.byref(e), _stream(stream)), "dope_labels")
+    if where == DOPE_HOST and keep is not labels and isinstance(labels, np.ndarray):
+        labels[...] = keep.reshape(labels.shape)
+    return e.value
+
+
+def dope_server_create(hbm_bytes=0, max_batch=0, mode=0, launch_iters=0):
+    p = dope_server_params(int(hbm_bytes), int(max_batch), int(mode), int(launch_iters), 0)
+    out = ctypes.c_void_p()
+    _check(_lib.dope_server_create(ctypes.byref(p), ctypes.byref(out)), "dope_server_create")
+    return out
+
+
+def dope_server_submit(srv, req):
+    rid = ctypes.c_uint64(0)
+    _check(_lib.dope_server_submit(srv, ctypes.byref(req), ctypes.byref(rid)), "dope_server_submit")
+    return rid.value
+
+
+def dope_server_poll(srv, cap=256, timeout=0.0):
+    buf = (dope_result * cap)()
+    n = ctypes.c_int(0)
+    _check(_lib.dope_server_poll(srv, buf, cap, ctypes.byref(n), float(timeout)), "dope_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def dope_server_clock(srv):
+    return _lib.dope_server_clock(srv)
+
+
+def dope_server_get_stats(srv):
+    st = dope_server_stats()
+    _check(_lib.dope_server_get_stats(srv, ctypes.byref(st)), "dope_server_get_stats")
+    return {k: getattr(st, k) for k, _ in dope_server_stats._fields_}
+
+
+def dope_server_destroy(srv):
+    _lib.dope_server_destroy(srv)
+
+
 def dope_destroy(ctx):
     _lib.dope_destroy(ctx)
 
@@ -340,7 +434,8 @@ class Dope:
 
     @classmethod
     def from_instance(cls, inst, **kw):
-        d = cls(inst["grid"], inst["conn"], inst["block"], inst["lam"], mu0=inst.get("mu0"), **kw)
+        kw.setdefault("mu0", inst.get("mu0"))
+        d = cls(inst["grid"], inst["conn"], inst["block"], inst["lam"], **kw)
         d.set_unaries(inst["u"])
         d.set_weights(inst["wq"])
         return d
@@ -391,10 +486,93 @@ class Dope:
     def profile(self):
         return dope_get_profile(self.ctx)
 
+    def labels(self, labels=None, stream=None):
+        """(labels, E_int) of the last iteration run."""
+        if labels is None:
+            labels = np.empty(self.n, np.uint8)
+        e = dope_labels(self.ctx, labels, stream)
+        return labels, e
+
     def close(self):
         if self.ctx:
             dope_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def iterate_batch(solvers, n_iter, stream=None):
+    """dope_iterate_batch over Dope objects."""
+    return dope_iterate_batch([d.ctx for d in solvers], n_iter, stream)
+
+
+class Server:
+    """Request server (continuous batching): submit solves, poll results.
+
+    Buffers handed to ``submit`` are kept referenced here until their result
+    has been polled."""
+
+    def __init__(self, hbm_bytes=0, max_batch=0, mode=0, launch_iters=0):
+        self.srv = dope_server_create(hbm_bytes, max_batch, mode, launch_iters)
+        self._keep = {}
+
+    def submit(self, grid, connectivity, block_shape, lam, u, wq, labels, params=None, tag=0):
+        grid = [int(g) for g in grid]
+        block = [int(b) for b in block_shape]
+        if len(grid) != len(block) or len(grid) not in (2, 3):
+            raise ValueError("grid and block_shape must both have rank 2 or 3")
+        pu, wu, ku = _ptr(u, _t(np.float32))
+        pw, ww, kw = _ptr(wq, _t(np.int32))
+        if wu != ww:
+            raise TypeError("unaries and weights must both be host or both device arrays")
+        if isinstance(labels, np.ndarray):
+            if labels.dtype != np.uint8 or not labels.flags.c_contiguous:
+                raise TypeError("labels must be a contiguous uint8 array")
+            pl, wl, kl = ctypes.c_void_p(labels.ctypes.data), DOPE_HOST, labels
+        else:
+            pl, wl, kl = _ptr(labels, _t(np.uint8))
+        r = dope_request()
+        r.ndim = len(grid)
+        r.connectivity = int(connectivity)
+        for i in range(len(grid)):
+            r.grid[i] = grid[i]
+            r.block_shape[i] = block[i]
+        r.lambda_ = float(lam)
+        if params is not None:
+            r.params = params
+            r.use_params = 1
+        r.where_inputs = wu
+        r.unaries, r.weights, r.labels = pu, pw, pl
+        r.where_labels = wl
+        r.tag = int(tag)
+        rid = dope_server_submit(self.srv, r)
+        self._keep[rid] = (ku, kw, kl)
+        return rid
+
+    def poll(self, timeout=0.0, cap=256):
+        out = []
+        for r in dope_server_poll(self.srv, cap, timeout):
+            self._keep.pop(r.id, None)
+            out.append({"id": r.id, "tag": r.tag, "status": r.status, "iterations": r.iterations,
+                        "converged": bool(r.converged), "energy_int": r.energy_int,
+                        "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done})
+        return out
+
+    def clock(self):
+        return dope_server_clock(self.srv)
+
+    def stats(self):
+        return dope_server_get_stats(self.srv)
+
+    def close(self):
+        if self.srv:
+            dope_server_destroy(self.srv)
+            self.srv = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -306,3 +306,120 @@ CONFIGS = {
     "ellipses512": ellipses_rgb,
     "ellipsoids256": ellipsoids3d,
 }
+
+
+def pad_to_blocks(d):
+    """Copy of instance d with its grid rounded up to whole blocks: the extra
+    pixels get unary 0 and no n-links (isolated zero-cost pixels), which is the
+    padding the request server applies to ragged grids."""
+    grid = tuple(int(g) for g in d["grid"])
+    block = tuple(int(b) for b in d["block"])
+    pg = tuple(-(-g // b) * b for g, b in zip(grid, block))
+    if pg == grid:
+        return dict(d)
+    nh = len(FWD_OFFSETS[d["conn"]])
+    u = np.zeros(pg, np.float32)
+    u[tuple(slice(0, g) for g in grid)] = np.asarray(d["u"], np.float32).reshape(grid)
+    wq = np.zeros((nh,) + pg, np.int32)
+    wq[(slice(None),) + tuple(slice(0, g) for g in grid)] = np.asarray(d["wq"], np.int32).reshape((nh,) + grid)
+    out = dict(d)
+    out.update(grid=pg, u=u.reshape(-1), wq=wq.reshape(nh, -1), unpadded_grid=grid)
+    return out
+
+
+def crop_padded(labels, d_padded):
+    """The caller's pixels of labels computed on pad_to_blocks(d)."""
+    grid = d_padded.get("unpadded_grid", d_padded["grid"])
+    full = np.asarray(labels).reshape(d_padded["grid"])
+    return full[tuple(slice(0, g) for g in grid)].reshape(-1)
+
+
+# --------------------------------------------------------------------------
+# Serving stream: Poisson arrivals of RGB contrast-Potts segmentations of
+# random side in [128, 2048], 4- or 8-connected, lambda in [1, 16]
+# --------------------------------------------------------------------------
+
+def serving_base(seed=0, size=2048, noise=0.08, box=24):
+    """A size x size RGB image with the statistics of ellipses_rgb: 12 ellipses
+    per 512x512 of area (centres uniform, semi-axes U[16,128], angle U[0,pi),
+    colours U[0,1]^3) over a U[0,1]^3 background, N(0, 0.08^2) noise; 3-component
+    GMMs fit on a 24x24 box inside the largest ellipse and on the 24x24 box (of
+    64 seeded candidates) least covered by ellipses; unaries and 8-connected
+    contrast weights (sigma = mean colour difference, divided by the pixel
+    distance) over the whole image.  Requests are crops of it."""
+    rng = _rng(1000 + seed)
+    H = W = size
+    n_ell = 12 * max(1, (size * size) // (512 * 512))
+    img = np.empty((H, W, 3), np.float32)
+    img[:] = rng.uniform(0, 1, 3)
+    anym = np.zeros((H, W), bool)
+    areas, centres = [], []
+    for _ in range(n_ell):
+        cy, cx = rng.uniform(0, H), rng.uniform(0, W)
+        a, b = rng.uniform(16, 128), rng.uniform(16, 128)
+        th = rng.uniform(0, np.pi)
+        col = rng.uniform(0, 1, 3).astype(np.float32)
+        r = max(a, b)
+        y0, y1 = max(0, int(cy - r) - 1), min(H, int(cy + r) + 2)
+        x0, x1 = max(0, int(cx - r) - 1), min(W, int(cx + r) + 2)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1].astype(np.float64)
+        dy, dx = yy - cy, xx - cx
+        xr = dx * np.cos(th) + dy * np.sin(th)
+        yr = -dx * np.sin(th) + dy * np.cos(th)
+        m = (xr / a) ** 2 + (yr / b) ** 2 <= 1.0
+        img[y0:y1, x0:x1][m] = col
+        anym[y0:y1, x0:x1] |= m
+        areas.append(np.pi * a * b)
+        centres.append((cy, cx))
+    img += rng.normal(0, noise, img.shape).astype(np.float32)
+    cy, cx = centres[int(np.argmax(areas))]
+    fy = int(np.clip(round(cy) - box // 2, 0, H - box))
+    fx = int(np.clip(round(cx) - box // 2, 0, W - box))
+    cand = rng.integers(0, H - box, (64, 2))
+    cover = [anym[y:y + box, x:x + box].sum() for (y, x) in cand]
+    by, bx = (int(v) for v in cand[int(np.argmin(cover))])
+    g_fg = fit_gmm(img[fy:fy + box, fx:fx + box].reshape(-1, 3).astype(np.float64), 3, rng)
+    g_bg = fit_gmm(img[by:by + box, bx:bx + box].reshape(-1, 3).astype(np.float64), 3, rng)
+    X = img.reshape(-1, 3).astype(np.float64)
+    u = np.clip(gmm_loglik(X, g_bg) - gmm_loglik(X, g_fg), -1.0e5, 1.0e5).astype(np.float32)
+    del X
+    w, sig = contrast_weights(img.astype(np.float64)[None], 8, inv_dist=True)
+    return {"size": size, "u": u.reshape(H, W), "wq": quantise_weights(w).reshape(4, H, W), "sigma": sig}
+
+
+def serving_requests(n=1000, rate=200.0, seed=0, side=(128, 2048), n_bases=2, base_size=2048,
+                     block=(32, 32), lam=(1.0, 16.0)):
+    """The request stream: Poisson arrivals (exponential gaps of mean 1/rate),
+    side uniform in [side0, side1], 4- or 8-connectivity 50/50, lambda uniform
+    in [lam0, lam1], a base image and a uniform crop position."""
+    rng = _rng(2000 + seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    t -= t[0]
+    out = []
+    for i in range(n):
+        s = int(rng.integers(side[0], side[1] + 1))
+        conn = 4 if rng.random() < 0.5 else 8
+        out.append({"arrival": float(t[i]), "base": int(rng.integers(n_bases)), "side": s,
+                    "y0": int(rng.integers(0, base_size - s + 1)), "x0": int(rng.integers(0, base_size - s + 1)),
+                    "conn": conn, "lam": float(rng.uniform(lam[0], lam[1])), "block": tuple(block),
+                    "grid": (s, s), "mu0": 100.0})
+    return out
+
+
+def crop_request(base, req):
+    """(u [s*s] float32, wq [conn/2, s*s] int32) of a request: the crop of the
+    base image's potentials, with the n-links that leave the crop set to 0."""
+    s, y0, x0 = req["side"], req["y0"], req["x0"]
+    nh = req["conn"] // 2
+    u = np.ascontiguousarray(base["u"][y0:y0 + s, x0:x0 + s]).reshape(-1)
+    w = np.array(base["wq"][:nh, y0:y0 + s, x0:x0 + s])
+    w[0, :, -1] = 0
+    w[1, -1, :] = 0
+    if nh == 4:
+        w[2, -1, :] = 0
+        w[2, :, -1] = 0
+        w[3, -1, :] = 0
+        w[3, :, 0] = 0
+    return u, w.reshape(nh, -1)

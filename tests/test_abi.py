@@ -59,3 +59,44 @@ def test_no_gpu_fails_loudly(lib):
     with pytest.raises(lib.DopeError) as ei:
         lib.dope_create((64, 64), 4, (16, 16), 1.0)
     assert ei.value.status == lib.DOPE_ECUDA
+
+
+def test_no_gpu_server_and_batch(lib):
+    """The server and the batched call also fail loudly without a device, and
+    reject malformed arguments before touching it."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lib.DopeError) as ei:
+        lib.dope_server_create()
+    assert ei.value.status == lib.DOPE_ECUDA
+    p = lib.dope_server_params(0, 0, 7, 0, 0)            # unknown mode
+    out = ctypes.c_void_p()
+    assert lib._lib.dope_server_create(ctypes.byref(p), ctypes.byref(out)) == lib.DOPE_EINVAL
+    assert lib._lib.dope_server_submit(None, None, None) == lib.DOPE_EINVAL
+    with pytest.raises(lib.DopeError) as ei:
+        lib.dope_iterate_batch([], 10)
+    assert ei.value.status == lib.DOPE_EINVAL
+    arr = (ctypes.c_void_p * 1)(None)
+    rc = lib._lib.dope_iterate_batch(arr, lib.DOPE_BATCH_MAX + 1, 10, None, None, None, None)
+    assert rc == lib.DOPE_EINVAL
+
+
+def test_struct_layouts_match_header(lib):
+    """ctypes mirrors of the C structs have the C sizes (compiled probe)."""
+    import os
+    import subprocess
+    import tempfile
+    src = ('#include <stdio.h>\n#include "dope.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
+           'sizeof(dope_params),sizeof(dope_stats),sizeof(dope_profile),sizeof(dope_server_params),'
+           'sizeof(dope_request),sizeof(dope_result),sizeof(dope_server_stats));return 0;}\n')
+    inc = os.path.dirname(lib.HEADER)
+    with tempfile.TemporaryDirectory() as td:
+        c = os.path.join(td, "sz.c")
+        exe = os.path.join(td, "sz")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I" + inc, c, "-o", exe], check=True)
+        got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(t) for t in (lib.dope_params, lib.dope_stats, lib.dope_profile, lib.dope_server_params,
+                                       lib.dope_request, lib.dope_result, lib.dope_server_stats)]
+    assert got == want

@@ -1,0 +1,161 @@
+"""GPU: the request server (continuous batching) -- each result is the same
+alone and in the mix.
+
+"Alone" is the same request solved by itself: through the single-problem path
+(a server in one-at-a-time mode, which runs dope_solve's kernels), and for
+small requests also by the oracle on the padded instance.  Labels, energies
+and iteration counts must be identical.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1704_03116_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    from paper_1704_03116_gb300 import _build
+    _build.build()
+    from paper_1704_03116_gb300 import dope
+    return dope
+
+
+def _requests(n, seed, max_side=200):
+    """Mixed requests: ragged 2-D grids (not multiples of the block), 4- or
+    8-connectivity, lambda in [1, 16], 16x16 or 32x32 blocks, a few 3-D."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        if i % 7 == 6:
+            g = tuple(int(x) for x in rng.integers(9, 20, 3))
+            d = inputs.random_instance(g, 6, (4, 8, 8), lam=float(rng.uniform(1, 4)), seed=seed * 100 + i)
+        else:
+            g = (int(rng.integers(20, max_side)), int(rng.integers(20, max_side)))
+            conn = 4 if rng.random() < 0.5 else 8
+            blk = (16, 16) if rng.random() < 0.5 else (32, 32)
+            d = inputs.random_instance(g, conn, blk, lam=float(rng.uniform(1, 16)), seed=seed * 100 + i)
+        out.append(d)
+    return out
+
+
+def _run(dp, reqs, delays=None, **kw):
+    srv = dp.Server(**kw)
+    labels = [np.zeros(int(np.prod(d["grid"])), np.uint8) for d in reqs]
+    ids = []
+    for i, d in enumerate(reqs):
+        if delays is not None:
+            time.sleep(delays[i])
+        ids.append(srv.submit(d["grid"], d["conn"], d["block"], d["lam"], d["u"], d["wq"], labels[i], tag=i))
+    res = {}
+    t0 = time.time()
+    while len(res) < len(reqs):
+        for r in srv.poll(timeout=1.0):
+            res[r["tag"]] = r
+        assert time.time() - t0 < 300, "server did not finish"
+    st = srv.stats()
+    srv.close()
+    return labels, res, st
+
+
+@pytest.fixture(scope="module")
+def mix():
+    return _requests(24, 1)
+
+
+@pytest.fixture(scope="module")
+def alone(dp, mix):
+    labels, res, st = _run(dp, mix, mode=1)
+    return labels, res
+
+
+def test_server_mix_equals_alone(dp, mix, alone):
+    lab1, res1 = alone
+    labels, res, st = _run(dp, mix, mode=0)
+    for i in range(len(mix)):
+        assert res[i]["status"] == 0 and res1[i]["status"] == 0
+        assert res[i]["iterations"] == res1[i]["iterations"], i
+        assert res[i]["energy_int"] == res1[i]["energy_int"], i
+        assert np.array_equal(labels[i], lab1[i]), i
+    assert st["completed"] == len(mix)
+    assert st["max_in_flight"] > 1          # requests did run together
+
+
+def test_server_matches_oracle(orc, dp, mix, alone):
+    lab1, res1 = alone
+    for i in (0, 1, 2, 6, 13):
+        d = inputs.pad_to_blocks(mix[i])
+        inst = orc.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"])
+        ref = orc.admm(inst, d["mu0"])
+        assert res1[i]["iterations"] == ref["iterations"]
+        assert np.array_equal(lab1[i], inputs.crop_padded(ref["labels"], d))
+        assert res1[i]["energy_int"] == ref["energy"]
+
+
+def test_server_staggered_arrivals(dp, mix, alone):
+    """Requests arriving while others run are admitted between iterations."""
+    lab1, res1 = alone
+    rng = np.random.default_rng(5)
+    labels, res, st = _run(dp, mix, delays=rng.exponential(0.002, len(mix)), mode=0)
+    for i in range(len(mix)):
+        assert res[i]["status"] == 0
+        assert res[i]["iterations"] == res1[i]["iterations"]
+        assert np.array_equal(labels[i], lab1[i])
+        assert res[i]["t_submit"] <= res[i]["t_admit"] <= res[i]["t_done"]
+
+
+def test_server_admission_by_memory(dp, mix, alone):
+    """A small arena admits a few requests at a time; all still finish, same results."""
+    lab1, res1 = alone
+    sub = mix[:16]
+    labels, res, st = _run(dp, sub, mode=0, hbm_bytes=4 << 20)
+    for i in range(len(sub)):
+        assert res[i]["status"] == 0
+        assert np.array_equal(labels[i], lab1[i])
+    assert st["bytes_peak"] <= st["bytes_limit"] == 4 << 20
+    assert st["max_in_flight"] < len(sub)
+
+
+def test_server_request_too_large(dp):
+    d = inputs.random_instance((512, 512), 8, (32, 32), lam=2.0, seed=9)
+    small = inputs.random_instance((40, 40), 4, (16, 16), lam=2.0, seed=10)
+    labels, res, st = _run(dp, [d, small], mode=0, hbm_bytes=4 << 20)
+    assert res[0]["status"] == dp.DOPE_ENOMEM
+    assert res[1]["status"] == 0
+
+
+def test_server_device_buffers(dp, mix, alone):
+    torch = pytest.importorskip("torch")
+    lab1, res1 = alone
+    srv = dp.Server(mode=0)
+    outs = []
+    for i, d in enumerate(mix[:6]):
+        u = torch.from_numpy(d["u"]).cuda()
+        w = torch.from_numpy(d["wq"]).cuda()
+        lab = torch.zeros(int(np.prod(d["grid"])), dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        srv.submit(d["grid"], d["conn"], d["block"], d["lam"], u, w, lab, tag=i)
+        outs.append(lab)
+    got = {}
+    t0 = time.time()
+    while len(got) < 6:
+        for r in srv.poll(timeout=1.0):
+            got[r["tag"]] = r
+        assert time.time() - t0 < 120
+    srv.close()
+    for i in range(6):
+        assert got[i]["status"] == 0
+        assert np.array_equal(outs[i].cpu().numpy(), lab1[i])
+
+
+def test_server_rejects_bad_requests(dp):
+    srv = dp.Server()
+    d = inputs.disk64()
+    with pytest.raises(dp.DopeError):
+        srv.submit(d["grid"], 6, d["block"], d["lam"], d["u"], d["wq"], np.zeros(4096, np.uint8))
+    with pytest.raises(dp.DopeError):
+        srv.submit(d["grid"], 4, d["block"], -1.0, d["u"], d["wq"], np.zeros(4096, np.uint8))
+    srv.close()

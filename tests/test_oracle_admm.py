@@ -244,3 +244,41 @@ def test_admm_step_matches_admm_loop(orc):
         mu = mu * 1.05
     assert yhat.tolist() == res["labels"].tolist()
     assert np.array_equal(y, res["y"]) and np.array_equal(a, res["a"])
+
+
+@pytest.mark.parametrize("grid,conn,block", [((37, 50), 4, (16, 16)), ((45, 29), 8, (8, 8)),
+                                             ((9, 13, 11), 6, (4, 4, 4))])
+def test_padding_pixels_change_nothing(orc, grid, conn, block):
+    """Isolated zero-cost pixels (the request server's padding of ragged grids)
+    leave Algorithm 1 unchanged on the caller's pixels: same labels, same
+    iteration count, same energy, and the global minimum is unchanged.  Pinned
+    against the unpadded instance on a grid that the blocks tile, padded by
+    one more row of blocks."""
+    from paper_1704_03116_gb300 import inputs
+    tiled = tuple(g // b * b for g, b in zip(grid, block))
+    d = inputs.random_instance(tiled, conn, block, lam=2.0, seed=sum(grid))
+    base = orc.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"])
+    ref = orc.admm(base, d["mu0"])
+    # pad: one more block along the first axis, and the padded instance of a
+    # ragged crop that pad_to_blocks rounds back up to `tiled`
+    big = dict(d)
+    big["grid"] = (tiled[0] + block[0],) + tiled[1:]
+    big["unpadded_grid"] = tiled
+    nh = d["wq"].shape[0]
+    u = np.zeros(big["grid"], np.float32)
+    u[:tiled[0]] = d["u"].reshape(tiled)
+    w = np.zeros((nh,) + big["grid"], np.int32)
+    w[:, :tiled[0]] = d["wq"].reshape((nh,) + tiled)
+    big["u"], big["wq"] = u.reshape(-1), w.reshape(nh, -1)
+    inst = orc.quantise(big["grid"], conn, block, big["u"], big["wq"], 2.0)
+    got = orc.admm(inst, d["mu0"])
+    assert got["iterations"] == ref["iterations"]
+    assert np.array_equal(inputs.crop_padded(got["labels"], big), ref["labels"])
+    assert got["energy"] == ref["energy"]
+    assert orc.global_mincut(inst)[1] == orc.global_mincut(base)[1]
+    # pad_to_blocks itself: a ragged grid is rounded up with zero pixels
+    r = inputs.random_instance(grid, conn, block, lam=1.0, seed=1)
+    p = inputs.pad_to_blocks(r)
+    assert all(g % b == 0 for g, b in zip(p["grid"], block))
+    assert np.array_equal(inputs.crop_padded(p["u"], p), r["u"])
+    assert p["u"].size - r["u"].size == np.count_nonzero(p["u"] == 0) - np.count_nonzero(r["u"] == 0)
