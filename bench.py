@@ -429,10 +429,12 @@ def main():
     upd_n = sum(p["launches"][1] for p in profs)
     iters_n = sum(p["iterations"] for p in profs)
     if upd_n == 0:
-        # persistent mode: one launch runs every iteration of a solve
-        kname, kms, kn = "k_admm_persistent", solve_ms, solve_n
+        # persistent mode: one launch runs every iteration of a solve (the
+        # resident kernel when every block fits on the GPU at once)
+        kname = "k_admm_resident" if ctxs[0].stats()["solver_kernel"] == 2 else "k_admm_persistent"
+        kms, kn = solve_ms, solve_n
         kbytes = first_n * sf + (iters_n - first_n) * sl + iters_n * up
-        share = {"k_admm_persistent": 1.0}
+        share = {kname: 1.0}
     elif solve_ms >= upd_ms:
         kname, kms, kn = "k_block_solve", solve_ms, solve_n
         kbytes = first_n * sf + (solve_n - first_n) * sl

@@ -110,6 +110,10 @@ typedef struct {
     double window_cycles[8];    /* run-ahead windows, summed over CTAs: build, block solve,
                                    label check, own update, halo update, window set-up,
                                    wait at the closing barrier, rest of the resolution */
+    int solver_kernel;          /* kernel that ran the iterations: 0 k_block_solve + k_face_update
+                                   (two launches per iteration), 1 k_admm_persistent, 2 k_admm_resident,
+                                   3 k_admm_batch (dope_iterate_batch) */
+    int reserved;
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the
@@ -283,6 +287,41 @@ int dope_iterate_batch(dope_ctx *const *ctxs, int n, int n_iter, int *iterations
  * E_int of them (may be NULL), without running further iterations.
  * Synchronises `stream`. */
 int dope_labels(dope_ctx *ctx, uint8_t *labels, int where, int64_t *energy_int, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Autotuner.  Picks, for one instance, the solver settings with the shortest
+ * device time to convergence: block shape (optional), relabel frequency,
+ * CTA width (256 threads: 3 CTAs per SM; 512 threads: 2 per SM), folding
+ * rounds and launch mode.  Only the block shape changes the decomposition
+ * (Section 2) and so the iterates and the final energy; the other settings
+ * change speed only (the block cut is exact and canonical), so their labels
+ * are bit-identical.  The paper fixes its block sizes by hand; this is a
+ * deployment tool.
+ * ------------------------------------------------------------------------- */
+#define DOPE_TUNE_BLOCK 1     /* also try block shapes that tile the grid */
+
+typedef struct {
+    int32_t block_shape[3];   /* first ndim entries used */
+    dope_params params;
+    double ms;                /* best device time of one solve (CUDA events) */
+    int iterations;
+    int converged;
+    int64_t energy_int;
+    int status;
+    int reserved;
+} dope_tune_result;
+
+/* Stage-wise search from (block_shape, base): block shapes when flags has
+ * DOPE_TUNE_BLOCK, then relabel_period in {2,4,8,16,32}, threads in {auto,
+ * 256, 512}, fold_rounds in {1,2,3,4}, launch_mode in {0,2}; each candidate
+ * is created, given u[N] / wq[conn/2][N] (`where` memory), solved once to
+ * warm up and `reps` (>= 1) times timed.  Every candidate tried goes to
+ * out[] (up to cap entries; *count = entries written); *best = the fastest
+ * converged one.  Synchronises `stream`. */
+int dope_autotune(const int64_t *grid, int ndim, int connectivity, const int32_t *block_shape,
+                  double lambda, const dope_params *base, const float *u, const int32_t *wq,
+                  int where, int flags, int reps, dope_tune_result *out, int cap, int *count,
+                  dope_tune_result *best, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Request server (continuous batching on one GPU).  The paper has no

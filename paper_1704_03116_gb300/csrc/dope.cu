@@ -297,6 +297,7 @@ int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
     fill_stats(c, h);
     c->stats.windows = h.windows;
     c->stats.window_iterations = h.window_iters;
+    c->stats.solver_kernel = c->resident ? 2 : 1;
     double r2 = 0.0;
     rc = read_r2max(c, c->t, &r2, st);
     if (rc) return rc;
@@ -1680,6 +1681,7 @@ int dope_batch_collect(dope_ctx* const* cs, int n, dope_batch_ws* w, int* t, int
         c->stats.converged = o.conv;
         c->stats.rmax_last = std::sqrt(o.r2);
         c->stats.kernel_launches = c->launches;
+        c->stats.solver_kernel = 3;
         if (t) t[i] = o.t;
         if (conv) conv[i] = o.conv;
         if (status) status[i] = o.status;
@@ -1750,4 +1752,189 @@ int dope_run_single(dope_ctx* c, cudaStream_t st, int* t, int* conv) {
     if (t) *t = c->t;
     if (conv) *conv = c->stats.converged;
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner (dope_autotune): stage-wise search over solver settings.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneRun {
+    const int64_t* grid;
+    int ndim, conn;
+    double lambda;
+    const float* u;          // device
+    const int32_t* wq;       // device
+    int reps;
+    cudaStream_t st;
+    uint8_t* lab;            // device, N
+    cudaEvent_t e0, e1;
+};
+
+// One candidate: create, load, warm up, time `reps` solves.
+void tune_one(const TuneRun& R, const int32_t* blk, const dope_params& prm, dope_tune_result* r) {
+    memset(r, 0, sizeof(*r));
+    for (int i = 0; i < R.ndim; ++i) r->block_shape[i] = blk[i];
+    r->params = prm;
+    r->ms = -1.0;
+    dope_ctx* c = nullptr;
+    int rc = dope_create(R.grid, R.ndim, R.conn, blk, R.lambda, &prm, &c);
+    if (!rc) rc = dope_set_unaries(c, R.u, c->g.Nu, DOPE_DEVICE, R.st);
+    if (!rc) rc = dope_set_weights(c, R.wq, c->g.Nu, DOPE_DEVICE, R.st);
+    int64_t e = 0;
+    int it = 0;
+    if (!rc) {
+        rc = dope_solve(c, R.lab, DOPE_DEVICE, &e, &it, R.st);
+        if (rc == DOPE_ENOTCONV) rc = DOPE_OK;
+    }
+    double best = -1.0;
+    for (int k = 0; !rc && k < R.reps; ++k) {
+        cudaEventRecord(R.e0, R.st);
+        rc = dope_solve(c, R.lab, DOPE_DEVICE, &e, &it, R.st);
+        cudaEventRecord(R.e1, R.st);
+        cudaEventSynchronize(R.e1);
+        if (rc == DOPE_ENOTCONV) rc = DOPE_OK;
+        float ms = 0.f;
+        if (!rc && cudaEventElapsedTime(&ms, R.e0, R.e1) == cudaSuccess && (best < 0 || ms < best)) best = ms;
+    }
+    cudaGetLastError();
+    if (c) {
+        r->converged = c->stats.converged;
+        dope_destroy(c);
+    }
+    r->status = rc;
+    r->ms = best;
+    r->iterations = it;
+    r->energy_int = e;
+}
+
+bool tune_better(const dope_tune_result& a, const dope_tune_result& b) {
+    if (a.status || !a.converged || a.ms < 0) return false;
+    if (b.status || !b.converged || b.ms < 0) return true;
+    return a.ms < b.ms;
+}
+
+}  // namespace
+
+extern "C" int dope_autotune(const int64_t* grid, int ndim, int connectivity, const int32_t* block_shape,
+                             double lambda, const dope_params* base, const float* u, const int32_t* wq,
+                             int where, int flags, int reps, dope_tune_result* out, int cap, int* count,
+                             dope_tune_result* best, void* stream) {
+    if (!grid || !block_shape || !u || !wq || !best || (where != DOPE_HOST && where != DOPE_DEVICE) ||
+        (ndim != 2 && ndim != 3) || reps < 1 || cap < 0 || (cap > 0 && !out))
+        return DOPE_EINVAL;
+    long long n = 1;
+    for (int i = 0; i < ndim; ++i) {
+        if (grid[i] <= 0) return DOPE_EINVAL;
+        n *= grid[i];
+    }
+    const int nh = connectivity / 2;
+    if (nh < 2 || nh > 4) return DOPE_EINVAL;
+    dope_params prm0;
+    dope_default_params(&prm0);
+    if (base) prm0 = *base;
+    cudaStream_t st = S(stream);
+    TuneRun R;
+    R.grid = grid;
+    R.ndim = ndim;
+    R.conn = connectivity;
+    R.lambda = lambda;
+    R.reps = reps;
+    R.st = st;
+    void* du = nullptr;
+    void* dw = nullptr;
+    void* dl = nullptr;
+    if (cudaMalloc(&dl, (size_t)n) != cudaSuccess) { cudaGetLastError(); return DOPE_ENOMEM; }
+    R.lab = (uint8_t*)dl;
+    if (where == DOPE_HOST) {
+        if (cudaMalloc(&du, sizeof(float) * (size_t)n) != cudaSuccess ||
+            cudaMalloc(&dw, sizeof(int32_t) * (size_t)n * nh) != cudaSuccess ||
+            cudaMemcpyAsync(du, u, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(dw, wq, sizeof(int32_t) * (size_t)n * nh, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(du); cudaFree(dw); cudaFree(dl);
+            return DOPE_ENOMEM;
+        }
+        R.u = (const float*)du;
+        R.wq = (const int32_t*)dw;
+    } else {
+        R.u = u;
+        R.wq = wq;
+    }
+    cudaEventCreate(&R.e0);
+    cudaEventCreate(&R.e1);
+    int nout = 0;
+    auto record = [&](const dope_tune_result& r) {
+        if (nout < cap) out[nout] = r;
+        ++nout;
+    };
+    int32_t blk[3] = {1, 1, 1};
+    for (int i = 0; i < ndim; ++i) blk[i] = block_shape[i];
+    dope_tune_result cur;
+    tune_one(R, blk, prm0, &cur);
+    record(cur);
+    // stage 1: block shapes tiling the grid
+    if (flags & DOPE_TUNE_BLOCK) {
+        static const int S2[] = {8, 16, 32, 64};
+        static const int S3[] = {4, 8, 16, 32};
+        std::vector<std::vector<int32_t>> cands;
+        if (ndim == 2) {
+            for (int by : S2)
+                for (int bx : S2)
+                    if (by * bx >= 64 && by * bx <= 4096 && grid[0] % by == 0 && grid[1] % bx == 0)
+                        cands.push_back({by, bx, 1});
+        } else {
+            for (int bz : S3)
+                for (int by : S3)
+                    for (int bx : S3)
+                        if (bz * by * bx >= 256 && bz * by * bx <= 4096 && grid[0] % bz == 0 &&
+                            grid[1] % by == 0 && grid[2] % bx == 0)
+                            cands.push_back({bz, by, bx});
+        }
+        for (auto& b : cands) {
+            bool same = true;
+            for (int i = 0; i < ndim; ++i) same = same && b[(size_t)i] == blk[i];
+            if (same) continue;
+            dope_tune_result r;
+            tune_one(R, b.data(), prm0, &r);
+            record(r);
+            if (tune_better(r, cur)) cur = r;
+        }
+        for (int i = 0; i < ndim; ++i) blk[i] = cur.block_shape[i];
+    }
+    // stages 2-5: settings that leave the labels unchanged
+    const int relabels[] = {2, 4, 8, 16, 32};
+    const int widths[] = {0, 256, 512};
+    const int folds[] = {1, 2, 3, 4};
+    const int modes[] = {0, 2};
+    for (int stage = 0; stage < 4; ++stage) {
+        const int* vals = stage == 0 ? relabels : stage == 1 ? widths : stage == 2 ? folds : modes;
+        const int nv = stage == 0 ? 5 : stage == 1 ? 3 : stage == 2 ? 4 : 2;
+        const dope_params start = cur.params;
+        for (int v = 0; v < nv; ++v) {
+            dope_params q = start;
+            if (stage == 0) { if (q.relabel_period == vals[v] || (q.relabel_period == 0 && vals[v] == 8)) continue; q.relabel_period = vals[v]; }
+            if (stage == 1) { if (q.threads == vals[v]) continue; q.threads = vals[v]; }
+            if (stage == 2) { if (q.fold_rounds == vals[v] || (q.fold_rounds == 0 && vals[v] == 3)) continue; q.fold_rounds = vals[v]; }
+            if (stage == 3) { if (q.launch_mode == vals[v]) continue; q.launch_mode = vals[v]; }
+            if (stage == 1 && vals[v] > 0) {
+                long long B = 1;
+                for (int i = 0; i < ndim; ++i) B *= blk[i];
+                if ((long long)vals[v] * NPTMAX < B) continue;
+            }
+            dope_tune_result r;
+            tune_one(R, blk, q, &r);
+            record(r);
+            if (tune_better(r, cur)) cur = r;
+        }
+    }
+    *best = cur;
+    if (count) *count = nout < cap ? nout : cap;
+    cudaEventDestroy(R.e0);
+    cudaEventDestroy(R.e1);
+    cudaFree(du);
+    cudaFree(dw);
+    cudaFree(dl);
+    cudaGetLastError();
+    return cur.status;
 }

@@ -48,7 +48,8 @@ class dope_stats(ctypes.Structure):
                 ("bfs_levels_max", ctypes.c_int), ("fold_rounds_max", ctypes.c_int),
                 ("phase_cycles", ctypes.c_double * 4), ("loop_cycles", ctypes.c_double * 4),
                 ("windows", ctypes.c_int), ("window_iterations", ctypes.c_int),
-                ("window_cycles", ctypes.c_double * 8)]
+                ("window_cycles", ctypes.c_double * 8), ("solver_kernel", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class dope_profile(ctypes.Structure):
@@ -84,7 +85,14 @@ class dope_server_stats(ctypes.Structure):
                [("gpu_launch_s", ctypes.c_double)]
 
 
+class dope_tune_result(ctypes.Structure):
+    _fields_ = [("block_shape", ctypes.c_int32 * 3), ("params", dope_params), ("ms", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("energy_int", ctypes.c_int64),
+                ("status", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
 DOPE_BATCH_MAX = 256
+DOPE_TUNE_BLOCK = 1
 
 
 def _load():
@@ -122,6 +130,8 @@ def _load():
         "dope_server_clock": (dbl, [vp]),
         "dope_server_get_stats": (i32, [vp, P(dope_server_stats)]),
         "dope_server_destroy": (None, [vp]),
+        "dope_autotune": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params), vp, vp, i32,
+                                i32, i32, P(dope_tune_result), i32, P(ctypes.c_int), P(dope_tune_result), vp]),
         "dope_destroy": (None, [vp]),
         "dope_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -402,6 +412,34 @@ def dope_server_get_stats(srv):
 
 def dope_server_destroy(srv):
     _lib.dope_server_destroy(srv)
+
+
+def _tune_dict(r, ndim):
+    p = r.params
+    return {"block": tuple(r.block_shape[:ndim]), "relabel_period": p.relabel_period, "threads": p.threads,
+            "fold_rounds": p.fold_rounds, "launch_mode": p.launch_mode, "ms": r.ms, "iterations": r.iterations,
+            "converged": bool(r.converged), "energy_int": r.energy_int, "status": r.status, "params": p}
+
+
+def dope_autotune(grid, connectivity, block_shape, lam, u, wq, params=None, flags=0, reps=2, cap=256,
+                  stream=None):
+    """Stage-wise search of solver settings; returns (best, all_tried) as dicts."""
+    grid = [int(g) for g in grid]
+    block = [int(b) for b in block_shape]
+    pu, wu, ku = _ptr(u, _t(np.float32))
+    pw, ww, kw = _ptr(wq, _t(np.int32))
+    if wu != ww:
+        raise TypeError("unaries and weights must both be host or both device arrays")
+    g = (ctypes.c_int64 * len(grid))(*grid)
+    b = (ctypes.c_int32 * len(block))(*block)
+    out = (dope_tune_result * cap)()
+    best = dope_tune_result()
+    n = ctypes.c_int(0)
+    rc = _lib.dope_autotune(g, len(grid), int(connectivity), b, float(lam),
+                            ctypes.byref(params) if params is not None else None, pu, pw, wu, int(flags),
+                            int(reps), out, cap, ctypes.byref(n), ctypes.byref(best), _stream(stream))
+    _check(rc, "dope_autotune")
+    return _tune_dict(best, len(grid)), [_tune_dict(out[i], len(grid)) for i in range(n.value)]
 
 
 def dope_destroy(ctx):

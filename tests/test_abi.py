@@ -87,9 +87,10 @@ def test_struct_layouts_match_header(lib):
     import os
     import subprocess
     import tempfile
-    src = ('#include <stdio.h>\n#include "dope.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
+    src = ('#include <stdio.h>\n#include "dope.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n",'
            'sizeof(dope_params),sizeof(dope_stats),sizeof(dope_profile),sizeof(dope_server_params),'
-           'sizeof(dope_request),sizeof(dope_result),sizeof(dope_server_stats));return 0;}\n')
+           'sizeof(dope_request),sizeof(dope_result),sizeof(dope_server_stats),sizeof(dope_tune_result));'
+           'return 0;}\n')
     inc = os.path.dirname(lib.HEADER)
     with tempfile.TemporaryDirectory() as td:
         c = os.path.join(td, "sz.c")
@@ -98,5 +99,6 @@ def test_struct_layouts_match_header(lib):
         subprocess.run(["gcc", "-I" + inc, c, "-o", exe], check=True)
         got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(t) for t in (lib.dope_params, lib.dope_stats, lib.dope_profile, lib.dope_server_params,
-                                       lib.dope_request, lib.dope_result, lib.dope_server_stats)]
+                                       lib.dope_request, lib.dope_result, lib.dope_server_stats,
+                                       lib.dope_tune_result)]
     assert got == want
