@@ -86,6 +86,21 @@ def _load():
     lib.orc_admm_step.restype = ctypes.c_int
     lib.orc_global_mincut.argtypes = geo + [_I64P, _I64P, _U8P]
     lib.orc_global_mincut.restype = ctypes.c_int64
+    ov = geo + [_I32P]
+    lib.orc_ov_geometry.argtypes = ov + [_I32P, _I32P, ctypes.POINTER(ctypes.c_int), _I64P]
+    lib.orc_ov_geometry.restype = ctypes.c_int
+    lib.orc_ov_caps.argtypes = ov + [_I64P, _I64P, _F64P, _F64P, ctypes.c_double, _F64P, _I64P]
+    lib.orc_ov_caps.restype = ctypes.c_int
+    lib.orc_ov_block_cuts.argtypes = ov + [_I64P, _I64P, _U8P]
+    lib.orc_ov_block_cuts.restype = ctypes.c_int
+    lib.orc_ov_update.argtypes = ov + [_I64P, _U8P, ctypes.c_double, _F64P, _F64P, _F64P]
+    lib.orc_ov_update.restype = ctypes.c_int
+    lib.orc_ov_labels.argtypes = ov + [_U8P, _U8P]
+    lib.orc_ov_labels.restype = ctypes.c_int
+    lib.orc_ov_admm.argtypes = ov + [_I64P, _I64P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int), _F64P, _F64P, _F64P,
+                                     _U8P, _F64P]
+    lib.orc_ov_admm.restype = ctypes.c_int
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -290,3 +305,113 @@ def num_threads() -> int:
 
 def set_threads(n: int) -> None:
     _load().orc_set_threads(int(n))
+
+
+# --------------------------------------------------------------------------
+# Overlapping blocks (Q != I): every tile of `block` grown by `grow` pixels per
+# side (clipped to the grid).  Block state (a, yhat, Eq. 8 unaries) is stored
+# per block as the full box of (block + 2 grow) pixels, box-major; box nodes
+# outside the grid are phantoms (0).
+# --------------------------------------------------------------------------
+
+class Overlap:
+    """Geometry of an overlapping partition: q (Proposition 1's q_ii per pixel,
+    image order), box extent, M = qmax^2 (integer scale of every block's Eq. 8
+    objective), K."""
+
+    def __init__(self, inst: Instance, grow):
+        self.inst = inst
+        self.grow = _dims3(grow) if len(tuple(grow)) < 3 else tuple(int(g) for g in grow)
+        self._g = _c(self.grow, np.int32)
+        q = np.empty(inst.n, np.int32)
+        box = np.empty(3, np.int32)
+        M = ctypes.c_int(0)
+        K = np.zeros(1, np.int64)
+        rc = _load().orc_ov_geometry(*inst._geo(), _p(self._g, _I32P), _p(q, _I32P), _p(box, _I32P),
+                                     ctypes.byref(M), _p(K, _I64P))
+        if rc != 0:
+            raise ValueError("invalid overlap (needs 2 grow <= block on every axis)")
+        self.q, self.box, self.M, self.K = q, tuple(int(b) for b in box), int(M.value), int(K[0])
+        self.eb = int(np.prod(self.box))
+
+    def _args(self):
+        return self.inst._geo() + [_p(self._g, _I32P)]
+
+    def caps(self, y, a, mu):
+        """Eq. 8 unaries of every box node: (s = x1024 double, C = rne(M s))."""
+        y = _c(y, np.float64).reshape(-1)
+        a = _c(a, np.float64).reshape(-1)
+        s = np.empty(self.K * self.eb, np.float64)
+        C = np.empty(self.K * self.eb, np.int64)
+        rc = _load().orc_ov_caps(*self._args(), _p(self.inst.U, _I64P), _p(self.inst.Wl, _I64P),
+                                 _p(y, _F64P), _p(a, _F64P), float(mu), _p(s, _F64P), _p(C, _I64P))
+        assert rc == 0
+        return s, C
+
+    def block_cuts(self, C):
+        C = _c(C, np.int64).reshape(-1)
+        yh = np.empty(self.K * self.eb, np.uint8)
+        rc = _load().orc_ov_block_cuts(*self._args(), _p(self.inst.Wl, _I64P), _p(C, _I64P), _p(yh, _U8P))
+        assert rc == 0
+        return yh
+
+    def update(self, yhat, mu, y, a):
+        """Eq. 10 / Eq. 11: (y, a, r2) from block labels (box-major)."""
+        y = np.array(y, dtype=np.float64).reshape(-1)
+        a = np.array(a, dtype=np.float64).reshape(-1)
+        yh = _c(yhat, np.uint8).reshape(-1)
+        r2 = np.empty(self.K, np.float64)
+        rc = _load().orc_ov_update(*self._args(), _p(self.inst.Wl, _I64P), _p(yh, _U8P), float(mu),
+                                   _p(y, _F64P), _p(a, _F64P), _p(r2, _F64P))
+        assert rc == 0
+        return y, a, r2
+
+    def labels(self, yhat):
+        """Proposition 1 output: strict majority of the block copies."""
+        yh = _c(yhat, np.uint8).reshape(-1)
+        lab = np.empty(self.inst.n, np.uint8)
+        assert _load().orc_ov_labels(*self._args(), _p(yh, _U8P), _p(lab, _U8P)) == 0
+        return lab
+
+    def step(self, mu, y, a):
+        """One Algorithm 1 iteration: (yhat, y', a', r2)."""
+        s, C = self.caps(y, a, mu)
+        yh = self.block_cuts(C)
+        y2, a2, r2 = self.update(yh, mu, y, a)
+        return yh, y2, a2, r2
+
+    def admm(self, mu0, mu_fact=1.05, eps=1e-3, max_iter=1000):
+        n = self.inst.n
+        labels = np.empty(n, np.uint8)
+        iters = ctypes.c_int(0)
+        rmax = np.zeros(max_iter, np.float64)
+        y = np.empty(n, np.float64)
+        a = np.empty(self.K * self.eb, np.float64)
+        yh = np.empty(self.K * self.eb, np.uint8)
+        mu = np.zeros(1, np.float64)
+        rc = _load().orc_ov_admm(*self._args(), _p(self.inst.U, _I64P), _p(self.inst.Wl, _I64P),
+                                 float(mu0), float(mu_fact), float(eps), int(max_iter), _p(labels, _U8P),
+                                 ctypes.byref(iters), _p(rmax, _F64P), _p(y, _F64P), _p(a, _F64P),
+                                 _p(yh, _U8P), _p(mu, _F64P))
+        if rc < 0:
+            raise RuntimeError(f"orc_ov_admm failed: {rc}")
+        t = iters.value
+        return {"labels": labels, "iterations": t, "converged": rc == 0, "rmax": rmax[:t].copy(),
+                "y": y, "a": a, "yhat": yh, "mu": float(mu[0]), "energy": energy(self.inst, labels)}
+
+    def box_pixels(self):
+        """Pixel index of every box node (box-major, -1 for phantoms), plain numpy."""
+        D, H, W = self.inst.dims
+        bd, bh, bw = self.inst.block
+        gd, gh, gw = self.grow
+        ed, eh, ew = self.box
+        out = np.full(self.K * self.eb, -1, np.int64)
+        nbz, nby, nbx = D // bd, H // bh, W // bw
+        lz, ly, lx = np.meshgrid(np.arange(ed), np.arange(eh), np.arange(ew), indexing="ij")
+        for k in range(self.K):
+            kz, ky, kx = k // (nby * nbx), (k // nbx) % nby, k % nbx
+            z, y, x = kz * bd - gd + lz, ky * bh - gh + ly, kx * bw - gw + lx
+            ok = (z >= 0) & (z < D) & (y >= 0) & (y < H) & (x >= 0) & (x < W)
+            idx = np.where(ok, (z * H + y) * W + x, -1).reshape(-1)
+            out[k * self.eb:(k + 1) * self.eb] = idx
+        return out

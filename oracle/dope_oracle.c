@@ -722,3 +722,341 @@ void orc_set_threads(int n)
     (void)n;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* DOPE, overlapping blocks (Q != I; the paper's Size10 / Size25 partitions) */
+/* ------------------------------------------------------------------------ */
+/*
+ * Partition: the regular tiling by `block` (the Q = I partition) with every
+ * tile grown by grow[a] pixels on both sides along axis a, clipped to the
+ * grid (Section 3: blocks "increased" in size).  2 grow[a] <= block[a], so a
+ * pixel lies in at most two tiles per axis and q_i (Proposition 1: the number
+ * of blocks holding i) is a power of two, at most qmax = 2^(axes with grow > 0).
+ * Block k is stored as the full box of (block + 2 grow) pixels per axis around
+ * tile k; box nodes outside the grid do not belong to Omega_k ("phantoms":
+ * label 0, multiplier 0, no terms).
+ *
+ * Theorem 1 in stencil form (derived from the matrix definitions; the literal
+ * matrices of oracle/theorem1.py pin it), for i in Omega_k, with
+ * phi_kj = 1 - [j in Omega_k] / q_j:
+ *   u_hat_k[i]                 = u_i / q_i
+ *   W_hat_k[i,j]               = w_ij / (q_i q_j)           (i, j in Omega_k)
+ *   [(C_k + R_k S_k) y]_i      = (1/q_i) sum_{j in N(i)} w_ij phi_kj (y_i - y_j)
+ *   [(C_k + R_k S_k)^T yh_k]_j = [j in Omega_k] (1/q_j) sum_{i in N(j)} w_ij phi_ki yh_k[j]
+ *                                - phi_kj sum_{i in N(j), i in Omega_k} (w_ij / q_i) yh_k[i]
+ * Integers: every block objective of Eq. 8 is multiplied by M = qmax^2 (a
+ * positive constant: same minimisers), so the n-links M Wl_ij / (q_i q_j) are
+ * integers, and the unary is rne(M * 1024 c_i).  Eq. 10's cross term is an
+ * integer in units of 1 / (1024 M): the "G" below.  With grow = 0 every
+ * formula here reduces, operation for operation, to the Q = I functions above.
+ */
+
+typedef struct {
+    grid_t g;
+    int gd, gh, gw;           /* grow per side */
+    int ed, eh, ew, eb;       /* box extent, box volume */
+    int64_t nbz, nby, nbx, K; /* tiles */
+    int qmax, M;
+} ov_t;
+
+static int ov_init(ov_t *o, const int64_t *dims, int conn, const int *block, const int *grow)
+{
+    if (grid_init(&o->g, dims, conn, block)) return -1;
+    o->gd = grow[0]; o->gh = grow[1]; o->gw = grow[2];
+    if (o->gd < 0 || o->gh < 0 || o->gw < 0) return -1;
+    if (2 * o->gd > o->g.bd || 2 * o->gh > o->g.bh || 2 * o->gw > o->g.bw) return -1;
+    o->ed = o->g.bd + 2 * o->gd; o->eh = o->g.bh + 2 * o->gh; o->ew = o->g.bw + 2 * o->gw;
+    o->eb = o->ed * o->eh * o->ew;
+    o->nbz = o->g.D / o->g.bd; o->nby = o->g.H / o->g.bh; o->nbx = o->g.W / o->g.bw;
+    o->K = o->nbz * o->nby * o->nbx;
+    o->qmax = (o->gd > 0 ? 2 : 1) * (o->gh > 0 ? 2 : 1) * (o->gw > 0 ? 2 : 1);
+    o->M = o->qmax * o->qmax;
+    return 0;
+}
+
+/* Tiles along one axis whose grown range holds coordinate c. */
+static int ov_axis_count(int64_t c, int64_t nb, int b, int gr)
+{
+    int n = 0;
+    int64_t lo = (c - gr) / b - 1, hi = (c + gr) / b + 1;
+    for (int64_t t = lo; t <= hi; t++) {
+        if (t < 0 || t >= nb) continue;
+        if (c >= t * b - gr && c < (t + 1) * b + gr) n++;
+    }
+    return n;
+}
+
+static int ov_q(const ov_t *o, int64_t z, int64_t y, int64_t x)
+{
+    return ov_axis_count(z, o->nbz, o->g.bd, o->gd) * ov_axis_count(y, o->nby, o->g.bh, o->gh) *
+           ov_axis_count(x, o->nbx, o->g.bw, o->gw);
+}
+
+/* Tile coordinates of block k. */
+static void ov_tile(const ov_t *o, int64_t k, int64_t *kz, int64_t *ky, int64_t *kx)
+{
+    *kz = k / (o->nby * o->nbx); *ky = (k / o->nbx) % o->nby; *kx = k % o->nbx;
+}
+
+/* Box node l of block k -> grid coordinates; returns the pixel index or -1 for
+ * a phantom (outside the grid). */
+static int64_t ov_node(const ov_t *o, int64_t k, int l, int64_t *pz, int64_t *py, int64_t *px)
+{
+    int64_t kz, ky, kx;
+    ov_tile(o, k, &kz, &ky, &kx);
+    int lz = l / (o->eh * o->ew), ly = (l / o->ew) % o->eh, lx = l % o->ew;
+    int64_t z = kz * o->g.bd - o->gd + lz, y = ky * o->g.bh - o->gh + ly, x = kx * o->g.bw - o->gw + lx;
+    *pz = z; *py = y; *px = x;
+    if (z < 0 || z >= o->g.D || y < 0 || y >= o->g.H || x < 0 || x >= o->g.W) return -1;
+    return (z * o->g.H + y) * o->g.W + x;
+}
+
+/* Box-local index of grid pixel (z, y, x) in block k, or -1 if not in Omega_k. */
+static int ov_local(const ov_t *o, int64_t k, int64_t z, int64_t y, int64_t x)
+{
+    int64_t kz, ky, kx;
+    ov_tile(o, k, &kz, &ky, &kx);
+    int64_t lz = z - (kz * o->g.bd - o->gd), ly = y - (ky * o->g.bh - o->gh), lx = x - (kx * o->g.bw - o->gw);
+    if (lz < 0 || lz >= o->ed || ly < 0 || ly >= o->eh || lx < 0 || lx >= o->ew) return -1;
+    return (int)((lz * o->eh + ly) * o->ew + lx);
+}
+
+/* Geometry query: q per pixel (image order), box extent, M. */
+int orc_ov_geometry(const int64_t *dims, int conn, const int *block, const int *grow,
+                    int32_t *q, int *box, int *M, int64_t *K)
+{
+    ov_t o;
+    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    if (q)
+        for (int64_t z = 0; z < o.g.D; z++)
+            for (int64_t y = 0; y < o.g.H; y++)
+                for (int64_t x = 0; x < o.g.W; x++) q[(z * o.g.H + y) * o.g.W + x] = ov_q(&o, z, y, x);
+    if (box) { box[0] = o.ed; box[1] = o.eh; box[2] = o.ew; }
+    if (M) *M = o.M;
+    if (K) *K = o.K;
+    return 0;
+}
+
+/* Eq. 8 unary of every box node (K x eb, box-major), general Q:
+ *   s  = U_i + sum_d (Wl_ij phi_kj)(y_i - y_j)     directions d = 0..conn-1, phi = 0 skipped
+ *   s  = s / q_i + (1024 mu)((a_ki - y_i) + 1/2)
+ *   C  = rne(M s), |M s| clamped to 2^62.
+ * s_out (may be NULL) gets s, C_out gets C; phantoms get 0. */
+int orc_ov_caps(const int64_t *dims, int conn, const int *block, const int *grow,
+                const int64_t *U, const int64_t *Wl, const double *y, const double *a,
+                double mu, double *s_out, int64_t *C_out)
+{
+    ov_t o;
+    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    const grid_t *g = &o.g;
+    double m1024 = 1024.0 * mu;
+    for (int64_t k = 0; k < o.K; k++)
+        for (int l = 0; l < o.eb; l++) {
+            int64_t z, yy, x, nz, ny, nx;
+            int64_t i = ov_node(&o, k, l, &z, &yy, &x);
+            int64_t kl = k * o.eb + l;
+            if (i < 0) { if (s_out) s_out[kl] = 0.0; C_out[kl] = 0; continue; }
+            double s = (double)U[i];
+            for (int d = 0; d < g->conn; d++) {
+                int64_t j = g_nbr(g, z, yy, x, d, &nz, &ny, &nx);
+                if (j < 0) continue;
+                double phi = 1.0;
+                if (ov_local(&o, k, nz, ny, nx) >= 0) {
+                    int qj = ov_q(&o, nz, ny, nx);
+                    if (qj == 1) continue;
+                    phi = 1.0 - 1.0 / (double)qj;
+                }
+                double w = (double)g_wt(g, Wl, i, j, d);
+                double wf = w * phi;
+                double dy = y[i] - y[j];
+                double t = wf * dy;
+                s = s + t;
+            }
+            s = s / (double)ov_q(&o, z, yy, x);
+            double v = a[kl] - y[i];
+            v = v + 0.5;
+            double t = m1024 * v;
+            s = s + t;
+            if (s_out) s_out[kl] = s;
+            double ms = (double)o.M * s;
+            if (ms > 4611686018427387904.0) ms = 4611686018427387904.0;
+            if (ms < -4611686018427387904.0) ms = -4611686018427387904.0;
+            C_out[kl] = llrint(ms);
+        }
+    return 0;
+}
+
+/* Eq. 8 of every block by BK on its box graph: terminal C (box-major), n-link
+ * M Wl_ij / (q_i q_j) between box nodes in the grid; phantoms get label 0. */
+int orc_ov_block_cuts(const int64_t *dims, int conn, const int *block, const int *grow,
+                      const int64_t *Wl, const int64_t *C, uint8_t *yhat)
+{
+    ov_t o;
+    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    const grid_t *g = &o.g;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t k = 0; k < o.K; k++) {
+        bk_t b;
+        uint8_t *lab = malloc((size_t)o.eb);
+        if (!lab || bk_alloc(&b, o.eb, o.eb * g->nh)) { err |= 1; free(lab); continue; }
+        for (int l = 0; l < o.eb; l++) b.tr[l] = C[k * o.eb + l];
+        for (int l = 0; l < o.eb; l++) {
+            int64_t z, y, x, nz, ny, nx;
+            int64_t i = ov_node(&o, k, l, &z, &y, &x);
+            if (i < 0) continue;
+            int qi = ov_q(&o, z, y, x);
+            for (int d = 0; d < g->nh; d++) {
+                int64_t j = g_nbr(g, z, y, x, d, &nz, &ny, &nx);
+                if (j < 0) continue;
+                int lj = ov_local(&o, k, nz, ny, nx);
+                if (lj < 0) continue;
+                int qj = ov_q(&o, nz, ny, nx);
+                int64_t w = Wl[(int64_t)d * g_n(g) + i] * (int64_t)(o.M / (qi * qj));
+                if (w > 0) bk_edge(&b, l, lj, w, w);
+            }
+        }
+        bk_run(&b, lab);
+        for (int l = 0; l < o.eb; l++) {
+            int64_t z, y, x;
+            yhat[k * o.eb + l] = ov_node(&o, k, l, &z, &y, &x) < 0 ? 0 : lab[l];
+        }
+        bk_free(&b);
+        free(lab);
+    }
+    return err ? -1 : 0;
+}
+
+/* Eq. 10 (y, image order) and Eq. 11 (a, box-major), general Q, then the
+ * per-block stop quantity r2_k = sum_{l in Omega_k} (yhat_kl - y_i)^2 (box order):
+ *   A_j  = sum_{k holding j, increasing k} (yhat_kj + a_kj)
+ *   G_j  = 1024 M sum_k [(C_k + R_k S_k)^T yh_k]_j / lambda   (exact integer)
+ *   y_j  = A_j / q_j - ((G_j / (1024 M)) / mu) / q_j
+ *   a_kl = a_kl + (yhat_kl - y_i). */
+int orc_ov_update(const int64_t *dims, int conn, const int *block, const int *grow,
+                  const int64_t *Wl, const uint8_t *yhat, double mu, double *y, double *a, double *r2)
+{
+    ov_t o;
+    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    const grid_t *g = &o.g;
+    for (int64_t z = 0; z < g->D; z++)
+        for (int64_t yy = 0; yy < g->H; yy++)
+            for (int64_t x = 0; x < g->W; x++) {
+                int64_t j = (z * g->H + yy) * g->W + x, iz, iy, ix;
+                int qj = ov_q(&o, z, yy, x);
+                /* tiles whose box can hold j or a neighbour of j */
+                int64_t k0z = (z - 1 - o.gd) / g->bd - 1, k1z = (z + 1 + o.gd) / g->bd + 1;
+                int64_t k0y = (yy - 1 - o.gh) / g->bh - 1, k1y = (yy + 1 + o.gh) / g->bh + 1;
+                int64_t k0x = (x - 1 - o.gw) / g->bw - 1, k1x = (x + 1 + o.gw) / g->bw + 1;
+                double A = 0.0;
+                int64_t G = 0;
+                for (int64_t kz = k0z; kz <= k1z; kz++)
+                    for (int64_t ky = k0y; ky <= k1y; ky++)
+                        for (int64_t kx = k0x; kx <= k1x; kx++) {
+                            if (kz < 0 || kz >= o.nbz || ky < 0 || ky >= o.nby || kx < 0 || kx >= o.nbx) continue;
+                            int64_t k = (kz * o.nby + ky) * o.nbx + kx;
+                            int lj = ov_local(&o, k, z, yy, x);
+                            int64_t yj = lj >= 0 ? yhat[k * o.eb + lj] : 0;
+                            if (lj >= 0) {
+                                double t = (double)yhat[k * o.eb + lj] + a[k * o.eb + lj];
+                                A = A + t;
+                            }
+                            for (int d = 0; d < g->conn; d++) {
+                                int64_t i = g_nbr(g, z, yy, x, d, &iz, &iy, &ix);
+                                if (i < 0) continue;
+                                int li = ov_local(&o, k, iz, iy, ix);
+                                int qi = ov_q(&o, iz, iy, ix);
+                                int64_t w = g_wt(g, Wl, j, i, d);
+                                if (lj >= 0 && yj) {   /* M (q_i - [i in Omega_k]) / (q_i q_j) */
+                                    G += w * ((int64_t)o.M * (qi - (li >= 0)) / (qi * qj));
+                                }
+                                if (li >= 0 && yhat[k * o.eb + li]) {   /* M (q_j - [j in Omega_k]) / (q_j q_i) */
+                                    G -= w * ((int64_t)o.M * (qj - (lj >= 0)) / (qj * qi));
+                                }
+                            }
+                        }
+                double yv = A / (double)qj;
+                double gq = (double)G / (1024.0 * (double)o.M);
+                double t = gq / mu;
+                t = t / (double)qj;
+                y[j] = yv - t;
+            }
+    for (int64_t k = 0; k < o.K; k++) {
+        double s = 0.0;
+        for (int l = 0; l < o.eb; l++) {
+            int64_t z, yy, x;
+            int64_t i = ov_node(&o, k, l, &z, &yy, &x);
+            if (i < 0) continue;
+            double yh = (double)yhat[k * o.eb + l];
+            a[k * o.eb + l] = a[k * o.eb + l] + (yh - y[i]);
+            double d = yh - y[i];
+            s = s + d * d;
+        }
+        r2[k] = s;
+    }
+    return 0;
+}
+
+/* Proposition 1 for the output: label_i = 1 iff the block copies vote 1 by a
+ * strict majority (2 sum_k yhat_ki > q_i); with consistent blocks this is the
+ * common label, Q^-1 sum_k S_k^T yhat_k. */
+int orc_ov_labels(const int64_t *dims, int conn, const int *block, const int *grow,
+                  const uint8_t *yhat, uint8_t *labels)
+{
+    ov_t o;
+    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    const grid_t *g = &o.g;
+    for (int64_t z = 0; z < g->D; z++)
+        for (int64_t yy = 0; yy < g->H; yy++)
+            for (int64_t x = 0; x < g->W; x++) {
+                int votes = 0;
+                for (int64_t k = 0; k < o.K; k++) {
+                    int l = ov_local(&o, k, z, yy, x);
+                    if (l >= 0) votes += yhat[k * o.eb + l];
+                }
+                labels[(z * g->H + yy) * g->W + x] = (uint8_t)(2 * votes > ov_q(&o, z, yy, x));
+            }
+    return 0;
+}
+
+/* Algorithm 1 with overlapping blocks; same loop as orc_admm.  Outputs the
+ * Proposition 1 labels, iterations, rmax trace, final y (image order), a and
+ * yhat (box-major) and mu. */
+int orc_ov_admm(const int64_t *dims, int conn, const int *block, const int *grow,
+                const int64_t *U, const int64_t *Wl, double mu0, double mu_fact, double eps,
+                int max_iter, uint8_t *labels, int *iters, double *rmax_trace,
+                double *y_out, double *a_out, uint8_t *yhat_out, double *mu_out)
+{
+    ov_t o;
+    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    int64_t n = g_n(&o.g), KB = o.K * o.eb;
+    double *y = malloc(sizeof(double) * (size_t)n);
+    double *a = calloc((size_t)KB, sizeof(double));
+    double *r2 = malloc(sizeof(double) * (size_t)o.K);
+    int64_t *C = malloc(sizeof(int64_t) * (size_t)KB);
+    uint8_t *yh = calloc((size_t)KB, 1);
+    if (!y || !a || !r2 || !C || !yh) { free(y); free(a); free(r2); free(C); free(yh); return -4; }
+    for (int64_t i = 0; i < n; i++) y[i] = 0.5;
+    double mu = mu0;
+    int t = 0, rc = 1;
+    while (t < max_iter) {
+        orc_ov_caps(dims, conn, block, grow, U, Wl, y, a, mu, NULL, C);
+        orc_ov_block_cuts(dims, conn, block, grow, Wl, C, yh);
+        orc_ov_update(dims, conn, block, grow, Wl, yh, mu, y, a, r2);
+        double m2 = 0.0;
+        for (int64_t k = 0; k < o.K; k++) if (r2[k] > m2) m2 = r2[k];
+        double rmax = sqrt(m2);
+        if (rmax_trace) rmax_trace[t] = rmax;
+        mu = mu * mu_fact;
+        t++;
+        if (!(rmax > eps)) { rc = 0; break; }
+    }
+    orc_ov_labels(dims, conn, block, grow, yh, labels);
+    *iters = t;
+    if (y_out) memcpy(y_out, y, sizeof(double) * (size_t)n);
+    if (a_out) memcpy(a_out, a, sizeof(double) * (size_t)KB);
+    if (yhat_out) memcpy(yhat_out, yh, (size_t)KB);
+    if (mu_out) *mu_out = mu;
+    free(y); free(a); free(r2); free(C); free(yh);
+    return rc;
+}
