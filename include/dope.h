@@ -86,6 +86,13 @@ typedef struct {
                                with run-ahead windows once labels stop moving;
                             1: two launches per iteration (solve, update);
                             2: persistent launch without run-ahead windows */
+    int grow[3];         /* overlapping partition (Section 2: blocks "can overlap"; Section 3's
+                            Size10 / Size25): every block grown by grow[a] pixels on both sides
+                            along axis a (first ndim entries, same order as the grid), clipped to
+                            the grid; 2 grow[a] <= block_shape[a].  All 0 (default): the
+                            non-overlapping partition, Q = I.  Overlapping contexts run three
+                            launches per iteration; the batched calls and the server take only
+                            Q = I contexts. */
 } dope_params;
 
 /* Statistics of the last dope_solve / dope_iterate call. */
@@ -177,10 +184,21 @@ int dope_reset(dope_ctx *ctx);
  * after the last iteration run.  Synchronises `stream`. */
 int dope_iterate(dope_ctx *ctx, int n_iter, int *iterations_done, int *converged, void *stream);
 
+/* Overlapping contexts (grow != 0): the per-block state, box-major -- block k
+ * is the box of (block_shape + 2 grow) pixels around its tile, node l at
+ * k * V + l (V = box volume; nodes outside the grid are 0): a (Eq. 11, one
+ * multiplier per block copy of a pixel) and yhat (the block labels of the last
+ * iteration).  cap = entries available in each array (K * V needed); *count =
+ * K * V.  DOPE_EINVAL for non-overlapping contexts. */
+int dope_get_block_state(dope_ctx *ctx, double *a, uint8_t *yhat, int64_t cap, int64_t *count,
+                         void *stream);
+
 /* Copy the ADMM state out (host buffers of N entries, image order):
  * y (Eq. 10), a (Eq. 11, one multiplier per pixel since Q = I), yhat (block
  * labels of the last iteration; 0 before the first), mu (value the next
- * iteration will use), t (iterations done).  Any pointer may be NULL. */
+ * iteration will use), t (iterations done).  Any pointer may be NULL.
+ * Overlapping contexts give y, mu and t here (a and yhat must be NULL; they
+ * are per block copy: dope_get_block_state). */
 int dope_get_state(dope_ctx *ctx, double *y, double *a, uint8_t *yhat, double *mu, int *t,
                    void *stream);
 

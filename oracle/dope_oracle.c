@@ -757,6 +757,7 @@ typedef struct {
     int ed, eh, ew, eb;       /* box extent, box volume */
     int64_t nbz, nby, nbx, K; /* tiles */
     int qmax, M;
+    uint8_t *q;               /* q per pixel, computed once by ov_init (ov_free releases it) */
 } ov_t;
 
 static int ov_init(ov_t *o, const int64_t *dims, int conn, const int *block, const int *grow)
@@ -771,8 +772,11 @@ static int ov_init(ov_t *o, const int64_t *dims, int conn, const int *block, con
     o->K = o->nbz * o->nby * o->nbx;
     o->qmax = (o->gd > 0 ? 2 : 1) * (o->gh > 0 ? 2 : 1) * (o->gw > 0 ? 2 : 1);
     o->M = o->qmax * o->qmax;
+    o->q = NULL;
     return 0;
 }
+
+static void ov_free(ov_t *o) { free(o->q); o->q = NULL; }
 
 /* Tiles along one axis whose grown range holds coordinate c. */
 static int ov_axis_count(int64_t c, int64_t nb, int b, int gr)
@@ -786,10 +790,27 @@ static int ov_axis_count(int64_t c, int64_t nb, int b, int gr)
     return n;
 }
 
-static int ov_q(const ov_t *o, int64_t z, int64_t y, int64_t x)
+static int ov_q_count(const ov_t *o, int64_t z, int64_t y, int64_t x)
 {
     return ov_axis_count(z, o->nbz, o->g.bd, o->gd) * ov_axis_count(y, o->nby, o->g.bh, o->gh) *
            ov_axis_count(x, o->nbx, o->g.bw, o->gw);
+}
+
+/* Fill the per-pixel table; -4 if out of memory. */
+static int ov_make_q(ov_t *o)
+{
+    o->q = malloc((size_t)g_n(&o->g));
+    if (!o->q) return -4;
+    for (int64_t z = 0; z < o->g.D; z++)
+        for (int64_t y = 0; y < o->g.H; y++)
+            for (int64_t x = 0; x < o->g.W; x++)
+                o->q[(z * o->g.H + y) * o->g.W + x] = (uint8_t)ov_q_count(o, z, y, x);
+    return 0;
+}
+
+static inline int ov_q(const ov_t *o, int64_t z, int64_t y, int64_t x)
+{
+    return o->q[(z * o->g.H + y) * o->g.W + x];
 }
 
 /* Tile coordinates of block k. */
@@ -826,7 +847,7 @@ int orc_ov_geometry(const int64_t *dims, int conn, const int *block, const int *
                     int32_t *q, int *box, int *M, int64_t *K)
 {
     ov_t o;
-    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    if (ov_init(&o, dims, conn, block, grow) || ov_make_q(&o)) return -1;
     if (q)
         for (int64_t z = 0; z < o.g.D; z++)
             for (int64_t y = 0; y < o.g.H; y++)
@@ -834,6 +855,7 @@ int orc_ov_geometry(const int64_t *dims, int conn, const int *block, const int *
     if (box) { box[0] = o.ed; box[1] = o.eh; box[2] = o.ew; }
     if (M) *M = o.M;
     if (K) *K = o.K;
+    ov_free(&o);
     return 0;
 }
 
@@ -847,7 +869,7 @@ int orc_ov_caps(const int64_t *dims, int conn, const int *block, const int *grow
                 double mu, double *s_out, int64_t *C_out)
 {
     ov_t o;
-    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    if (ov_init(&o, dims, conn, block, grow) || ov_make_q(&o)) return -1;
     const grid_t *g = &o.g;
     double m1024 = 1024.0 * mu;
     for (int64_t k = 0; k < o.K; k++)
@@ -883,6 +905,7 @@ int orc_ov_caps(const int64_t *dims, int conn, const int *block, const int *grow
             if (ms < -4611686018427387904.0) ms = -4611686018427387904.0;
             C_out[kl] = llrint(ms);
         }
+    ov_free(&o);
     return 0;
 }
 
@@ -892,7 +915,7 @@ int orc_ov_block_cuts(const int64_t *dims, int conn, const int *block, const int
                       const int64_t *Wl, const int64_t *C, uint8_t *yhat)
 {
     ov_t o;
-    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    if (ov_init(&o, dims, conn, block, grow) || ov_make_q(&o)) return -1;
     const grid_t *g = &o.g;
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
@@ -924,6 +947,7 @@ int orc_ov_block_cuts(const int64_t *dims, int conn, const int *block, const int
         bk_free(&b);
         free(lab);
     }
+    ov_free(&o);
     return err ? -1 : 0;
 }
 
@@ -937,7 +961,7 @@ int orc_ov_update(const int64_t *dims, int conn, const int *block, const int *gr
                   const int64_t *Wl, const uint8_t *yhat, double mu, double *y, double *a, double *r2)
 {
     ov_t o;
-    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    if (ov_init(&o, dims, conn, block, grow) || ov_make_q(&o)) return -1;
     const grid_t *g = &o.g;
     for (int64_t z = 0; z < g->D; z++)
         for (int64_t yy = 0; yy < g->H; yy++)
@@ -994,6 +1018,7 @@ int orc_ov_update(const int64_t *dims, int conn, const int *block, const int *gr
         }
         r2[k] = s;
     }
+    ov_free(&o);
     return 0;
 }
 
@@ -1004,18 +1029,23 @@ int orc_ov_labels(const int64_t *dims, int conn, const int *block, const int *gr
                   const uint8_t *yhat, uint8_t *labels)
 {
     ov_t o;
-    if (ov_init(&o, dims, conn, block, grow)) return -1;
+    if (ov_init(&o, dims, conn, block, grow) || ov_make_q(&o)) return -1;
     const grid_t *g = &o.g;
     for (int64_t z = 0; z < g->D; z++)
         for (int64_t yy = 0; yy < g->H; yy++)
             for (int64_t x = 0; x < g->W; x++) {
                 int votes = 0;
-                for (int64_t k = 0; k < o.K; k++) {
-                    int l = ov_local(&o, k, z, yy, x);
-                    if (l >= 0) votes += yhat[k * o.eb + l];
-                }
+                for (int64_t kz = (z - o.gd) / g->bd - 1; kz <= (z + o.gd) / g->bd + 1; kz++)
+                    for (int64_t ky = (yy - o.gh) / g->bh - 1; ky <= (yy + o.gh) / g->bh + 1; ky++)
+                        for (int64_t kx = (x - o.gw) / g->bw - 1; kx <= (x + o.gw) / g->bw + 1; kx++) {
+                            if (kz < 0 || kz >= o.nbz || ky < 0 || ky >= o.nby || kx < 0 || kx >= o.nbx) continue;
+                            int64_t k = (kz * o.nby + ky) * o.nbx + kx;
+                            int l = ov_local(&o, k, z, yy, x);
+                            if (l >= 0) votes += yhat[k * o.eb + l];
+                        }
                 labels[(z * g->H + yy) * g->W + x] = (uint8_t)(2 * votes > ov_q(&o, z, yy, x));
             }
+    ov_free(&o);
     return 0;
 }
 

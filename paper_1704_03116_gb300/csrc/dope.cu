@@ -20,6 +20,7 @@
 #include "dope.h"
 #include "dope_internal.h"
 #include "dope_kernels.cuh"
+#include "dope_overlap.cuh"
 
 using namespace dope;
 
@@ -50,6 +51,10 @@ struct dope_ctx {
     int* hinfo = nullptr;       // [NH] halo_entry of each distinct halo pixel
     int NH = 0;
     int window_ok = 0;          // the resident kernel fits with its run-ahead window arrays
+    // overlapping partition (grow != 0): image-order U / Wl / q / y, box-major a / yhat
+    int ov = 0;
+    OvArgs oa{};
+    int ov_threads = 0, ov_smem = 0;
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
     // staging (lazily allocated)
@@ -238,6 +243,10 @@ int read_r2max(dope_ctx* c, int t, double* r2, cudaStream_t st) {
     return DOPE_OK;
 }
 
+int ov_run(dope_ctx* c, int n, cudaStream_t st);
+int ov_reset_async(dope_ctx* c, cudaStream_t st);
+int ov_finish(dope_ctx* c, uint8_t* labels_dev, int64_t* energy, cudaStream_t st);
+
 // Up to n iterations in one cooperative launch of k_admm_persistent.
 int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
     const int t0 = c->t;
@@ -319,6 +328,7 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
     int rc = clear_status(c, st);
     if (rc) return rc;
     CK(cudaMemsetAsync(&c->ctrl->r2max[t0 + 1], 0, sizeof(unsigned long long) * (size_t)n, st));
+    if (c->ov) return ov_run(c, n, st);
     if (c->p.launch_mode != 1 && c->persist_grid > 0) return run_persistent(c, n, st);
     if (c->profiling && c->ev.size() < 3 * (size_t)n) {
         size_t have = c->ev.size();
@@ -452,7 +462,7 @@ int reset_state_async(dope_ctx* c, cudaStream_t st) {
 }
 
 int reset_state(dope_ctx* c) {
-    int rc = reset_state_async(c, 0);
+    int rc = c->ov ? ov_reset_async(c, 0) : reset_state_async(c, 0);
     if (rc) return rc;
     CK(cudaDeviceSynchronize());
     return DOPE_OK;
@@ -510,6 +520,238 @@ void choose_launch(dope_ctx* c) {
             c->window_ok = with_window;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Overlapping partition (grow != 0): set-up, iterations, finish.
+// ---------------------------------------------------------------------------
+// Tiles along one axis whose grown range [t b - g, (t+1) b + g) holds c.
+int ov_axis_q(long long c, int b, int gr, int nb) {
+    long long lo = c - gr >= 0 ? (c - gr) / b : -((gr - c + b - 1) / b);
+    long long hi = (c + gr) / b;
+    if (lo < 0) lo = 0;
+    if (hi > nb - 1) hi = nb - 1;
+    return (int)(hi - lo + 1);
+}
+
+template <int CONN>
+void ov_raise_smem() {
+    static std::once_flag once;
+    std::call_once(once, []() { raise_smem_limit((const void*)k_ov_solve<CONN>); });
+}
+
+int ov_reset_async(dope_ctx* c, cudaStream_t st) {
+    c->t = 0;
+    c->mu = c->p.mu0;
+    const OvArgs& A = c->oa;
+    const int threads = 256;
+    // y = 1/2 (Algorithm 1 initialisation), a = 0, yhat = 0
+    k_init_state<<<grid_for(A.N, threads), threads, 0, st>>>(Geo{1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
+                                                                   (int)A.N, A.N, 1, 1, 1, A.N}, A.y, A.a);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(A.a, 0, sizeof(double) * (size_t)A.g.K * A.g.B, st));
+    CK(cudaMemsetAsync(A.yhat, 0, (size_t)A.g.K * A.g.B, st));
+    return DOPE_OK;
+}
+
+int create_overlap(dope_ctx* c, const int64_t dims[3], const int32_t blk[3], const int grow3[3],
+                   cudaStream_t st) {
+    for (int i = 0; i < 3; ++i)
+        if (grow3[i] < 0 || 2 * grow3[i] > blk[i]) return DOPE_EINVAL;
+    const long long box = (long long)(blk[0] + 2 * grow3[0]) * (blk[1] + 2 * grow3[1]) * (blk[2] + 2 * grow3[2]);
+    if (box > 4096) return DOPE_EINVAL;
+    const long long N = dims[0] * dims[1] * dims[2];
+    c->ov = 1;
+    // flat geometry: the whole grid as one "block", so the set-up kernels keep image order
+    Geo& g = c->g;
+    g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
+    g.bd = g.D; g.bh = g.H; g.bw = g.W;
+    g.B = (int)(N < (1LL << 30) ? N : (1LL << 30));
+    g.nbz = g.nby = g.nbx = 1;
+    g.K = 1;
+    g.F = 0;
+    g.N = N;
+    g.Du = g.D; g.Hu = g.H; g.Wu = g.W;
+    g.Nu = N;
+    OvArgs& A = c->oa;
+    A.D = g.D; A.H = g.H; A.W = g.W;
+    A.tbd = blk[0]; A.tbh = blk[1]; A.tbw = blk[2];
+    A.gd = grow3[0]; A.gh = grow3[1]; A.gw = grow3[2];
+    A.nbz = (int)(dims[0] / blk[0]); A.nby = (int)(dims[1] / blk[1]); A.nbx = (int)(dims[2] / blk[2]);
+    const int qmax = (A.gd ? 2 : 1) * (A.gh ? 2 : 1) * (A.gw ? 2 : 1);
+    A.M = qmax * qmax;
+    A.N = N;
+    Geo& b = A.g;
+    memset(&b, 0, sizeof(b));
+    b.bd = blk[0] + 2 * A.gd; b.bh = blk[1] + 2 * A.gh; b.bw = blk[2] + 2 * A.gw;
+    b.B = (int)box;
+    b.D = b.bd; b.H = b.bh; b.W = b.bw;
+    b.nbz = A.nbz; b.nby = A.nby; b.nbx = A.nbx;
+    b.K = A.nbz * A.nby * A.nbx;
+    b.N = (long long)b.K * b.B;
+    A.eps = c->p.eps;
+    A.relabel_period = c->p.relabel_period;
+    A.max_pulses = c->p.max_pulses;
+    A.fold_rounds = c->p.fold_rounds;
+    int t = (int)((box + 31) / 32 * 32);
+    if (t > 512) t = 512;
+    if (t < 32) t = 32;
+    c->ov_threads = t;
+    c->ov_smem = (int)solver_smem_bytes(c->conn, (int)box);
+    c->threads = t;
+    c->smem = c->ov_smem;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (c->ov_smem > optin) return DOPE_EINVAL;
+    if (c->conn == 4) ov_raise_smem<4>();
+    else if (c->conn == 8) ov_raise_smem<8>();
+    else ov_raise_smem<6>();
+    const int nh = c->conn / 2;
+    const size_t KB = (size_t)b.K * b.B;
+    int rc = DOPE_OK;
+    auto Al = [&](void** ptr, size_t bytes) {
+        if (rc == DOPE_OK) {
+            *ptr = dalloc(c->al, bytes);
+            if (!*ptr) rc = DOPE_ENOMEM;
+        }
+    };
+    Al((void**)&c->U, sizeof(int32_t) * (size_t)N);
+    Al((void**)&c->Wl, sizeof(int32_t) * (size_t)N * nh);
+    Al((void**)&A.q, (size_t)N);
+    Al((void**)&A.y, sizeof(double) * (size_t)N);
+    Al((void**)&A.a, sizeof(double) * KB);
+    Al((void**)&A.yhat, KB);
+    Al((void**)&c->r2blk, sizeof(double) * (size_t)b.K);
+    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
+    Al((void**)&c->ctrl, c->ctrl_bytes);
+    if (rc) return rc;
+    A.U = c->U;
+    A.Wl = c->Wl;
+    A.r2blk = c->r2blk;
+    A.ctrl = c->ctrl;
+    // q: blocks holding each pixel (Proposition 1's q_ii), per-axis counts multiplied
+    std::vector<uint8_t> q((size_t)N);
+    for (long long z = 0; z < dims[0]; ++z) {
+        const int qz = ov_axis_q(z, blk[0], A.gd, A.nbz);
+        for (long long y = 0; y < dims[1]; ++y) {
+            const int qy = ov_axis_q(y, blk[1], A.gh, A.nby);
+            for (long long x = 0; x < dims[2]; ++x)
+                q[(size_t)((z * dims[1] + y) * dims[2] + x)] = (uint8_t)(qz * qy * ov_axis_q(x, blk[2], A.gw, A.nbx));
+        }
+    }
+    if (cudaMemcpy(const_cast<uint8_t*>(A.q), q.data(), (size_t)N, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemsetAsync(c->ctrl, 0, c->ctrl_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return DOPE_ECUDA;
+    }
+    return ov_reset_async(c, st);
+}
+
+template <int CONN>
+void ov_launch_iteration(dope_ctx* c, int t, double mu, int check_prev, cudaStream_t st, cudaEvent_t mid) {
+    const OvArgs& A = c->oa;
+    k_ov_solve<CONN><<<A.g.K, c->ov_threads, c->ov_smem, st>>>(A, mu, t, check_prev);
+    if (mid) cudaEventRecord(mid, st);
+    k_ov_y<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
+    k_ov_a<CONN><<<A.g.K, 256, 0, st>>>(A, t);
+    c->launches += 3;
+}
+
+// Up to n iterations of Algorithm 1 on the overlapping partition (three
+// launches per iteration, issued in batches; the stop test of iteration t is
+// read by iteration t + 1's solve launch, as in launch mode 1).
+int ov_run(dope_ctx* c, int n, cudaStream_t st) {
+    const int t0 = c->t;
+    std::vector<double> mus((size_t)n + 1);
+    mus[0] = c->mu;
+    for (int j = 1; j <= n; ++j) mus[j] = mus[j - 1] * c->p.mu_fact;
+    if (c->profiling && c->ev.size() < 3 * (size_t)n) {
+        const size_t have = c->ev.size();
+        c->ev.resize(3 * (size_t)n);
+        for (size_t i = have; i < c->ev.size(); ++i) CK(cudaEventCreate(&c->ev[i]));
+    }
+    Ctrl h{};
+    int launched = 0, batch = 4;
+    while (launched < n) {
+        const int nb = (n - launched < batch) ? n - launched : batch;
+        for (int j = 0; j < nb; ++j) {
+            const int idx = launched + j;
+            if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx], st));
+            if (c->conn == 4) ov_launch_iteration<4>(c, t0 + idx + 1, mus[idx], idx > 0, st, c->profiling ? c->ev[3 * idx + 1] : nullptr);
+            else if (c->conn == 8) ov_launch_iteration<8>(c, t0 + idx + 1, mus[idx], idx > 0, st, c->profiling ? c->ev[3 * idx + 1] : nullptr);
+            else ov_launch_iteration<6>(c, t0 + idx + 1, mus[idx], idx > 0, st, c->profiling ? c->ev[3 * idx + 1] : nullptr);
+            if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx + 2], st));
+        }
+        CK(cudaGetLastError());
+        launched += nb;
+        int rc = read_ctrl(c, &h, st);
+        if (rc) return rc;
+        if (h.status) return h.status;
+        if (h.conv_t) break;
+        if (batch < 32) batch *= 2;
+    }
+    int done, converged;
+    if (h.conv_t) {
+        done = h.conv_t - t0;
+        converged = 1;
+    } else {
+        done = launched;
+        double r2 = 0.0;
+        int rc = read_r2max(c, t0 + done, &r2, st);
+        if (rc) return rc;
+        converged = !(std::sqrt(r2) > c->p.eps);
+    }
+    if (c->profiling) {
+        for (int idx = 0; idx < done; ++idx) {
+            float ms_a = 0.f, ms_b = 0.f;
+            CK(cudaEventElapsedTime(&ms_a, c->ev[3 * idx], c->ev[3 * idx + 1]));
+            CK(cudaEventElapsedTime(&ms_b, c->ev[3 * idx + 1], c->ev[3 * idx + 2]));
+            c->prof.launches[0]++;
+            c->prof.ms[0] += ms_a;
+            c->prof.launches[1]++;
+            c->prof.ms[1] += ms_b;
+            c->prof.iterations++;
+            if (t0 + idx == 0) {
+                c->prof.first_iteration_launches++;
+                c->prof.first_iteration_ms += ms_a;
+            }
+        }
+    }
+    c->t = t0 + done;
+    c->mu = mus[done];
+    c->stats.iterations = c->t;
+    c->stats.converged = converged;
+    fill_stats(c, h);
+    double r2 = 0.0;
+    int rc = read_r2max(c, c->t, &r2, st);
+    if (rc) return rc;
+    c->stats.rmax_last = std::sqrt(r2);
+    c->stats.kernel_launches = c->launches;
+    c->stats.solver_kernel = 0;
+    return DOPE_OK;
+}
+
+// Proposition 1 labels (image order, device) and, if asked, their E_int.
+int ov_finish(dope_ctx* c, uint8_t* labels_dev, int64_t* energy, cudaStream_t st) {
+    const OvArgs& A = c->oa;
+    k_ov_labels<<<grid_for(A.N, 256), 256, 0, st>>>(A, labels_dev);
+    c->launches++;
+    CK(cudaGetLastError());
+    if (energy) {
+        CK(cudaMemsetAsync(&c->ctrl->energy, 0, sizeof(unsigned long long), st));
+        const int blocks = grid_for(A.N, 256);
+        if (c->conn == 4) k_energy_img<4><<<blocks, 256, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl);
+        else if (c->conn == 8) k_energy_img<8><<<blocks, 256, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl);
+        else k_energy_img<6><<<blocks, 256, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl);
+        c->launches++;
+        CK(cudaGetLastError());
+        unsigned long long v = 0;
+        CK(cudaMemcpyAsync(&v, &c->ctrl->energy, sizeof(v), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *energy = (int64_t)v;
+    }
+    return DOPE_OK;
 }
 
 std::once_flag g_smem_once[3];
@@ -688,6 +930,20 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
     if (c->p.relabel_period <= 0) c->p.relabel_period = 8;
     if (c->p.max_pulses <= 0) c->p.max_pulses = (int)(64 * B + 4096);
     if (c->p.fold_rounds <= 0) c->p.fold_rounds = MAX_FOLD_ROUNDS;
+    {
+        int grow3[3] = {0, 0, 0};
+        bool any = false;
+        for (int i = 0; i < ndim; ++i) {
+            grow3[3 - ndim + i] = c->p.grow[i];
+            any = any || c->p.grow[i] != 0;
+        }
+        if (any) {
+            int rc = pad ? DOPE_EINVAL : create_overlap(c, dims, blk, grow3, st);
+            if (rc) { dope_destroy(c); return rc; }
+            *out = c;
+            return DOPE_OK;
+        }
+    }
 
     Geo& g = c->g;
     g.D = (int)dims[0]; g.H = (int)dims[1]; g.W = (int)dims[2];
@@ -777,6 +1033,7 @@ void dope_default_params(dope_params* p) {
     p->max_pulses = 0;
     p->fold_rounds = 0;
     p->launch_mode = 0;
+    p->grow[0] = p->grow[1] = p->grow[2] = 0;
 }
 
 const char* dope_strerror(int s) {
@@ -805,6 +1062,10 @@ void dope_destroy(dope_ctx* c) {
     dfree(al, c->ctrl);
     dfree(al, c->stage);
     dfree(al, c->stage2);
+    dfree(al, const_cast<uint8_t*>(c->oa.q));
+    dfree(al, c->oa.y);
+    dfree(al, c->oa.a);
+    dfree(al, c->oa.yhat);
     if (c->own_tab) dope_tables_destroy(c->own_tab);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
@@ -862,6 +1123,7 @@ int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void*
     if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
     else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
     else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
+    if (c->ov) k_ov_wcheck<<<grid_for(c->g.N * nh, threads), threads, 0, st>>>(c->Wl, c->g.N * nh, c->oa.M, c->ctrl);
     CK(cudaGetLastError());
     Ctrl h{};
     rc = read_ctrl(c, &h, st);
@@ -890,6 +1152,23 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
     if (!c || !labels || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
     if (!c->have_u || !c->have_w) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    if (c->ov) {
+        c->launches = 0;
+        int rc = ov_reset_async(c, st);
+        if (!rc) rc = run_iterations(c, c->p.max_iter, st);
+        uint8_t* dst = labels;
+        if (!rc && where == DOPE_HOST) {
+            rc = ensure_stage(c, (size_t)c->g.Nu, 1);
+            dst = (uint8_t*)c->stage2;
+        }
+        if (!rc) rc = ov_finish(c, dst, energy_int, st);
+        if (rc) return rc;
+        if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        c->stats.kernel_launches = c->launches;
+        if (iterations) *iterations = c->t;
+        return c->stats.converged ? DOPE_OK : DOPE_ENOTCONV;
+    }
     // Algorithm 1 initialisation: y = 1/2, a = 0, mu = mu0 (stream-ordered)
     c->t = 0;
     c->mu = c->p.mu0;
@@ -922,6 +1201,14 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
 int dope_get_state(dope_ctx* c, double* y, double* a, uint8_t* yhat, double* mu, int* t, void* stream) {
     if (!c) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    if (c->ov) {
+        if (a || yhat) return DOPE_EINVAL;
+        if (y) CK(cudaMemcpyAsync(y, c->oa.y, sizeof(double) * (size_t)c->oa.N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (mu) *mu = c->mu;
+        if (t) *t = c->t;
+        return DOPE_OK;
+    }
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 17, 1);
     if (rc) return rc;
@@ -944,6 +1231,7 @@ int dope_get_state(dope_ctx* c, double* y, double* a, uint8_t* yhat, double* mu,
 int dope_set_state(dope_ctx* c, const double* y, const double* a, const uint8_t* yhat, double mu,
                    int t, void* stream) {
     if (!c || !y || !a || !yhat || t < 0 || t > c->p.max_iter || !(mu > 0.0)) return DOPE_EINVAL;
+    if (c->ov) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 17, 1);
@@ -974,6 +1262,7 @@ int dope_set_state(dope_ctx* c, const double* y, const double* a, const uint8_t*
 
 int dope_shifted_caps(dope_ctx* c, int64_t* C, void* stream) {
     if (!c || !C || !c->have_u || !c->have_w) return DOPE_EINVAL;
+    if (c->ov) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 8, 1);
@@ -996,6 +1285,7 @@ int dope_shifted_caps(dope_ctx* c, int64_t* C, void* stream) {
 
 int dope_block_cuts(dope_ctx* c, const int64_t* C, uint8_t* yhat, void* stream) {
     if (!c || !C || !yhat || !c->have_w) return DOPE_EINVAL;
+    if (c->ov) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 17, 1);
@@ -1043,6 +1333,20 @@ int dope_energy(dope_ctx* c, const uint8_t* labels, int where, int64_t* energy_i
         src = img;
     }
     const int threads = 256;
+    if (c->ov) {
+        CK(cudaMemsetAsync(&c->ctrl->energy, 0, sizeof(unsigned long long), st));
+        const int blocks = grid_for(c->g.N, threads);
+        const OvArgs& A = c->oa;
+        if (c->conn == 4) k_energy_img<4><<<blocks, threads, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl);
+        else if (c->conn == 8) k_energy_img<8><<<blocks, threads, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl);
+        else k_energy_img<6><<<blocks, threads, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl);
+        CK(cudaGetLastError());
+        unsigned long long v = 0;
+        CK(cudaMemcpyAsync(&v, &c->ctrl->energy, sizeof(v), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *energy_int = (int64_t)v;
+        return DOPE_OK;
+    }
     k_permute_u8<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, src, bm);
     CK(cudaGetLastError());
     return energy_of(c, bm, energy_int, st);
@@ -1086,10 +1390,11 @@ int dope_get_profile(dope_ctx* c, dope_profile* out) {
 
 int dope_get_geometry(dope_ctx* c, int64_t* n_pixels, int64_t* n_blocks, int* block_volume, int* face_size) {
     if (!c) return DOPE_EINVAL;
+    const Geo& g = c->ov ? c->oa.g : c->g;
     if (n_pixels) *n_pixels = c->g.N;
-    if (n_blocks) *n_blocks = c->g.K;
-    if (block_volume) *block_volume = c->g.B;
-    if (face_size) *face_size = c->g.F;
+    if (n_blocks) *n_blocks = g.K;
+    if (block_volume) *block_volume = g.B;
+    if (face_size) *face_size = c->ov ? 0 : g.F;
     return DOPE_OK;
 }
 
@@ -1580,7 +1885,7 @@ int dope_batch_launch(dope_ctx* const* cs, int n, int n_iter, int exit_on_done, 
     long long total = 0;
     for (int i = 0; i < n; ++i) {
         dope_ctx* c = cs[i];
-        if (!c || !c->have_u || !c->have_w) return DOPE_EINVAL;
+        if (!c || !c->have_u || !c->have_w || c->ov) return DOPE_EINVAL;
         for (int j = 0; j < i; ++j)
             if (cs[j] == c) return DOPE_EINVAL;
         const int width = solver_width(c->g.B, c->threads);
@@ -1727,6 +2032,19 @@ extern "C" int dope_labels(dope_ctx* c, uint8_t* labels, int where, int64_t* ene
     if (!c->have_u || !c->have_w) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     int rc;
+    if (c->ov) {
+        uint8_t* dst = labels;
+        if (where == DOPE_HOST) {
+            rc = ensure_stage(c, (size_t)c->g.Nu, 1);
+            if (rc) return rc;
+            dst = (uint8_t*)c->stage2;
+        }
+        rc = ov_finish(c, dst, energy_int, st);
+        if (rc) return rc;
+        if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return DOPE_OK;
+    }
     if (energy_int) {
         rc = energy_of(c, c->yhat, energy_int, st);
         if (rc) return rc;
@@ -1937,4 +2255,17 @@ extern "C" int dope_autotune(const int64_t* grid, int ndim, int connectivity, co
     cudaFree(dl);
     cudaGetLastError();
     return cur.status;
+}
+
+extern "C" int dope_get_block_state(dope_ctx* c, double* a, uint8_t* yhat, int64_t cap, int64_t* count,
+                                    void* stream) {
+    if (!c || !c->ov) return DOPE_EINVAL;
+    const int64_t n = (int64_t)c->oa.g.K * c->oa.g.B;
+    if (count) *count = n;
+    if ((a || yhat) && cap < n) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    if (a) CK(cudaMemcpyAsync(a, c->oa.a, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    if (yhat) CK(cudaMemcpyAsync(yhat, c->oa.yhat, (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return DOPE_OK;
 }

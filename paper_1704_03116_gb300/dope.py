@@ -37,7 +37,7 @@ class dope_params(ctypes.Structure):
     _fields_ = [("mu0", ctypes.c_double), ("mu_fact", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("relabel_period", ctypes.c_int),
                 ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int), ("fold_rounds", ctypes.c_int),
-                ("launch_mode", ctypes.c_int)]
+                ("launch_mode", ctypes.c_int), ("grow", ctypes.c_int * 3)]
 
 
 class dope_stats(ctypes.Structure):
@@ -132,6 +132,7 @@ def _load():
         "dope_server_destroy": (None, [vp]),
         "dope_autotune": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params), vp, vp, i32,
                                 i32, i32, P(dope_tune_result), i32, P(ctypes.c_int), P(dope_tune_result), vp]),
+        "dope_get_block_state": (i32, [vp, vp, vp, i64, P(ctypes.c_int64), vp]),
         "dope_destroy": (None, [vp]),
         "dope_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -265,15 +266,19 @@ def dope_get_geometry(ctx):
     return _geom(ctx)
 
 
-def dope_get_state(ctx, stream=None):
+def dope_get_state(ctx, stream=None, y_only=False):
+    """State after the last iteration: y, a, yhat (image order), mu, t.  With
+    y_only (required for overlapping partitions, whose a / yhat are per block
+    copy: dope_get_block_state) a and yhat are None."""
     n = _geom(ctx)[0]
     y = np.empty(n, np.float64)
-    a = np.empty(n, np.float64)
-    yh = np.empty(n, np.uint8)
+    a = None if y_only else np.empty(n, np.float64)
+    yh = None if y_only else np.empty(n, np.uint8)
     mu = ctypes.c_double(0)
     t = ctypes.c_int(0)
-    _check(_lib.dope_get_state(ctx, y.ctypes.data, a.ctypes.data, yh.ctypes.data, ctypes.byref(mu),
-                               ctypes.byref(t), _stream(stream)), "dope_get_state")
+    _check(_lib.dope_get_state(ctx, y.ctypes.data, None if y_only else a.ctypes.data,
+                               None if y_only else yh.ctypes.data, ctypes.byref(mu), ctypes.byref(t),
+                               _stream(stream)), "dope_get_state")
     return {"y": y, "a": a, "yhat": yh, "mu": mu.value, "t": t.value}
 
 
@@ -442,6 +447,18 @@ def dope_autotune(grid, connectivity, block_shape, lam, u, wq, params=None, flag
     return _tune_dict(best, len(grid)), [_tune_dict(out[i], len(grid)) for i in range(n.value)]
 
 
+def dope_get_block_state(ctx, stream=None):
+    """Overlapping contexts: per-block multipliers a and labels yhat, box-major."""
+    n = ctypes.c_int64(0)
+    _check(_lib.dope_get_block_state(ctx, None, None, 0, ctypes.byref(n), _stream(stream)),
+           "dope_get_block_state")
+    a = np.empty(n.value, np.float64)
+    yh = np.empty(n.value, np.uint8)
+    _check(_lib.dope_get_block_state(ctx, a.ctypes.data, yh.ctypes.data, n.value, ctypes.byref(n),
+                                     _stream(stream)), "dope_get_block_state")
+    return a, yh
+
+
 def dope_destroy(ctx):
     _lib.dope_destroy(ctx)
 
@@ -459,14 +476,18 @@ class Dope:
 
     def __init__(self, grid, connectivity, block_shape, lam, mu0=None, mu_fact=None, eps=None,
                  max_iter=None, relabel_period=None, threads=None, max_pulses=None, fold_rounds=None,
-                 launch_mode=None):
+                 launch_mode=None, grow=None):
         p = dope_default_params()
         for k, v in dict(mu0=mu0, mu_fact=mu_fact, eps=eps, max_iter=max_iter,
                          relabel_period=relabel_period, threads=threads, max_pulses=max_pulses,
                          fold_rounds=fold_rounds, launch_mode=launch_mode).items():
             if v is not None:
                 setattr(p, k, v)
+        if grow is not None:
+            for i, g in enumerate(grow):
+                p.grow[i] = int(g)
         self.grid = tuple(int(g) for g in grid)
+        self.overlap = grow is not None and any(int(g) for g in grow)
         self.ctx = dope_create(grid, connectivity, block_shape, lam, p)
         self.n, self.nblocks, self.block_volume, self.face_size = _geom(self.ctx)
 
@@ -498,7 +519,7 @@ class Dope:
         dope_reset(self.ctx)
 
     def get_state(self):
-        return dope_get_state(self.ctx)
+        return dope_get_state(self.ctx, y_only=self.overlap)
 
     def set_state(self, y, a, yhat, mu, t):
         dope_set_state(self.ctx, y, a, yhat, mu, t)
@@ -523,6 +544,10 @@ class Dope:
 
     def profile(self):
         return dope_get_profile(self.ctx)
+
+    def block_state(self):
+        """(a, yhat) per block copy, box-major (overlapping partitions)."""
+        return dope_get_block_state(self.ctx)
 
     def labels(self, labels=None, stream=None):
         """(labels, E_int) of the last iteration run."""
