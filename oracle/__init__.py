@@ -101,6 +101,16 @@ def _load():
                                      ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int), _F64P, _F64P, _F64P,
                                      _U8P, _F64P]
     lib.orc_ov_admm.restype = ctypes.c_int
+    lib.orc_quantise_signed.argtypes = geo + [_F32P, _I32P, ctypes.c_double, _I64P, _I64P]
+    lib.orc_quantise_signed.restype = ctypes.c_int
+    lib.orc_nsm_block_solve.argtypes = geo + [_I64P, _I64P, _U8P, ctypes.c_int]
+    lib.orc_nsm_block_solve.restype = ctypes.c_int
+    lib.orc_nsm_admm.argtypes = geo + [_I64P, _I64P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int), _F64P,
+                                       _F64P, _F64P, _F64P]
+    lib.orc_nsm_admm.restype = ctypes.c_int
+    lib.orc_lsa_tr_global.argtypes = [_I64P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, _U8P]
+    lib.orc_lsa_tr_global.restype = ctypes.c_int64
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -148,8 +158,9 @@ def _dims3(grid):
     return grid if len(grid) == 3 else (1,) + grid
 
 
-def quantise(grid, conn, block, u, wq, lam) -> Instance:
-    """Instance canonicalisation: U = rne(1024 u), Wl = rne(lambda wq) (FP64)."""
+def quantise(grid, conn, block, u, wq, lam, signed=False) -> Instance:
+    """Instance canonicalisation: U = rne(1024 u), Wl = rne(lambda wq) (FP64).
+    signed=True accepts negative weights (non-submodular instances)."""
     lib = _load()
     dims, blk = _dims3(grid), _dims3(block)
     n = int(np.prod(dims))
@@ -158,7 +169,8 @@ def quantise(grid, conn, block, u, wq, lam) -> Instance:
     U = np.empty(n, np.int64)
     Wl = np.empty((conn // 2, n), np.int64)
     inst = Instance(dims, conn, blk, U, Wl)
-    rc = lib.orc_quantise(*inst._geo(), _p(u, _F32P), _p(wq, _I32P), float(lam), _p(U, _I64P), _p(Wl, _I64P))
+    fn = lib.orc_quantise_signed if signed else lib.orc_quantise
+    rc = fn(*inst._geo(), _p(u, _F32P), _p(wq, _I32P), float(lam), _p(U, _I64P), _p(Wl, _I64P))
     if rc != 0:
         raise ValueError(f"orc_quantise failed: {rc}")
     return inst
@@ -415,3 +427,56 @@ class Overlap:
             idx = np.where(ok, (z * H + y) * W + x, -1).reshape(-1)
             out[k * self.eb:(k + 1) * self.eb] = idx
         return out
+
+
+# --------------------------------------------------------------------------
+# Non-submodular blocks: LSA-TR (trust-region local submodular approximation)
+# --------------------------------------------------------------------------
+
+LSA_STEPS = 16
+
+
+def nsm_block_solve(inst: Instance, C, yhat, steps=LSA_STEPS):
+    """Every block's Eq. 8 by LSA-TR from the labels yhat (image order)."""
+    C = _c(C, np.int64).reshape(-1)
+    yh = np.array(yhat, dtype=np.uint8).reshape(-1)
+    assert _load().orc_nsm_block_solve(*inst._geo(), _p(inst.Wl, _I64P), _p(C, _I64P), _p(yh, _U8P),
+                                       int(steps)) == 0
+    return yh
+
+
+def nsm_step(inst: Instance, mu, y, a, yhat, steps=LSA_STEPS):
+    """One Algorithm 1 iteration with LSA-TR blocks: (yhat', y', a', r2)."""
+    s, C = shifted_caps(inst, y, a, mu)
+    yh = nsm_block_solve(inst, C, yhat, steps)
+    y2, a2, r2 = update(inst, yh, mu, y, a)
+    return yh, y2, a2, r2
+
+
+def nsm_admm(inst: Instance, mu0, mu_fact=1.05, eps=1e-3, max_iter=1000, steps=LSA_STEPS):
+    n = inst.n
+    labels = np.empty(n, np.uint8)
+    iters = ctypes.c_int(0)
+    rmax = np.zeros(max_iter, np.float64)
+    y = np.empty(n, np.float64)
+    a = np.empty(n, np.float64)
+    mu = np.zeros(1, np.float64)
+    rc = _load().orc_nsm_admm(*inst._geo(), _p(inst.U, _I64P), _p(inst.Wl, _I64P), float(mu0), float(mu_fact),
+                              float(eps), int(max_iter), int(steps), _p(labels, _U8P), ctypes.byref(iters),
+                              _p(rmax, _F64P), _p(y, _F64P), _p(a, _F64P), _p(mu, _F64P))
+    if rc < 0:
+        raise RuntimeError(f"orc_nsm_admm failed: {rc}")
+    t = iters.value
+    return {"labels": labels, "iterations": t, "converged": rc == 0, "rmax": rmax[:t].copy(), "y": y,
+            "a": a, "mu": float(mu[0]), "energy": energy(inst, labels)}
+
+
+def lsa_tr_global(inst: Instance, steps=200):
+    """Serial LSA-TR on the whole grid from 0: (labels, E_int)."""
+    d = _c(inst.dims, np.int64)
+    labels = np.empty(inst.n, np.uint8)
+    e = _load().orc_lsa_tr_global(_p(d, _I64P), int(inst.conn), _p(inst.U, _I64P), _p(inst.Wl, _I64P),
+                                  int(steps), _p(labels, _U8P))
+    if e == np.iinfo(np.int64).min:
+        raise RuntimeError("orc_lsa_tr_global failed")
+    return labels, int(e)

@@ -135,9 +135,26 @@ static inline int64_t g_block_pixel(const grid_t *g, int64_t k, int l,
  * Returns 0, or -2 if a weight is negative (not submodular, footnote on
  * submodularity in Section 1), -3 if a weight toward a pixel outside the
  * grid is non-zero. */
+static int quantise_impl(const int64_t *dims, int conn, const int *block, const float *u,
+                         const int32_t *wq, double lambda, int64_t *U, int64_t *Wl, int allow_negative);
+
 int orc_quantise(const int64_t *dims, int conn, const int *block,
                  const float *u, const int32_t *wq, double lambda,
                  int64_t *U, int64_t *Wl)
+{
+    return quantise_impl(dims, conn, block, u, wq, lambda, U, Wl, 0);
+}
+
+/* The same with weights of any sign (non-submodular instances, Section 3.4). */
+int orc_quantise_signed(const int64_t *dims, int conn, const int *block,
+                        const float *u, const int32_t *wq, double lambda,
+                        int64_t *U, int64_t *Wl)
+{
+    return quantise_impl(dims, conn, block, u, wq, lambda, U, Wl, 1);
+}
+
+static int quantise_impl(const int64_t *dims, int conn, const int *block, const float *u,
+                         const int32_t *wq, double lambda, int64_t *U, int64_t *Wl, int allow_negative)
 {
     grid_t g;
     if (grid_init(&g, dims, conn, block)) return -1;
@@ -149,7 +166,7 @@ int orc_quantise(const int64_t *dims, int conn, const int *block,
                 for (int64_t x = 0; x < g.W; x++) {
                     int64_t i = (z * g.H + y) * g.W + x, nz, ny, nx;
                     int32_t w = wq[(int64_t)k * n + i];
-                    if (w < 0) return -2;
+                    if (w < 0 && !allow_negative) return -2;
                     if (g_nbr(&g, z, y, x, k, &nz, &ny, &nx) < 0 && w != 0) return -3;
                     Wl[(int64_t)k * n + i] = llrint(lambda * (double)w);
                 }
@@ -1089,4 +1106,202 @@ int orc_ov_admm(const int64_t *dims, int conn, const int *block, const int *grow
     if (mu_out) *mu_out = mu;
     free(y); free(a); free(r2); free(C); free(yh);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Non-submodular blocks: LSA-TR per block (Section 3.4 of the paper uses     */
+/* the trust-region local submodular approximation of Gorelick et al. 2014)  */
+/* ------------------------------------------------------------------------ */
+/*
+ * Block objective (Eq. 8, Q = I) with weights of any sign:
+ *   E(x) = sum_i C_i x_i + sum_{edges ij in the block} Wl_ij |x_i - x_j|.
+ * An edge with Wl_ij = -w < 0 equals -w x_i - w x_j + 2 w x_i x_j; its product
+ * is replaced by the tangent of x_i x_j at the current labelling x^s,
+ * x_i^s x_j + x_j^s x_i - x_i^s x_j^s, which makes the approximation
+ * submodular and exact at x^s.  One trust-region step minimises
+ *   approx(x) + lam * sum_i |x_i - x_i^s|
+ * exactly (canonical minimal cut) and keeps the minimiser x* if E(x*) < E(x^s).
+ * Trust region (integers): lam starts at LSA_LAM0; if x* = x^s the region
+ * grows (lam /= 4; stop once lam = 0); an accepted step with actual decrease
+ * R >= 3/4 of the predicted decrease P grows it too; a rejected step shrinks
+ * it (lam = max(4 lam, 1)).  At most `steps` steps.  Everything is int64, so
+ * the result is a deterministic function of (C, Wl, x^0).
+ */
+#define LSA_LAM0 1024
+
+/* Exact block energy of labels x over the block's own edges. */
+static int64_t lsa_energy(const grid_t *g, int64_t k, int B, const int64_t *Cb, const int64_t *Wl,
+                          const uint8_t *x)
+{
+    int64_t e = 0;
+    for (int l = 0; l < B; l++) {
+        int64_t z, y, xx, nz, ny, nx;
+        int64_t i = g_block_pixel(g, k, l, &z, &y, &xx);
+        if (x[l]) e += Cb[l];
+        for (int o = 0; o < g->nh; o++) {
+            int64_t j = g_nbr(g, z, y, xx, o, &nz, &ny, &nx);
+            if (j < 0 || g_block_of(g, nz, ny, nx) != k) continue;
+            int lj = (int)(((nz % g->bd) * g->bh + (ny % g->bh)) * g->bw + (nx % g->bw));
+            if (x[l] != x[lj]) e += Wl[(int64_t)o * g_n(g) + i];
+        }
+    }
+    return e;
+}
+
+/* LSA-TR on block k from x (in place); Cb = block unaries (local order). */
+static int lsa_tr_block(const grid_t *g, int64_t k, const int64_t *Cb, const int64_t *Wl, uint8_t *x,
+                        int steps, int *steps_done)
+{
+    int B = g->bd * g->bh * g->bw;
+    int64_t *un = malloc(sizeof(int64_t) * (size_t)B);
+    uint8_t *xs = malloc((size_t)B);
+    bk_t b;
+    int rc = 0, s = 0;
+    if (!un || !xs) { free(un); free(xs); return -4; }
+    int64_t lam = LSA_LAM0;
+    int64_t e_cur = lsa_energy(g, k, B, Cb, Wl, x);
+    for (s = 0; s < steps; s++) {
+        /* approximation around x: unaries, submodular n-links, constant */
+        int64_t cst = 0;
+        for (int l = 0; l < B; l++) un[l] = Cb[l];
+        if (bk_alloc(&b, B, B * g->nh)) { rc = -4; break; }
+        for (int l = 0; l < B; l++) {
+            int64_t z, y, xx, nz, ny, nx;
+            int64_t i = g_block_pixel(g, k, l, &z, &y, &xx);
+            for (int o = 0; o < g->nh; o++) {
+                int64_t j = g_nbr(g, z, y, xx, o, &nz, &ny, &nx);
+                if (j < 0 || g_block_of(g, nz, ny, nx) != k) continue;
+                int lj = (int)(((nz % g->bd) * g->bh + (ny % g->bh)) * g->bw + (nx % g->bw));
+                int64_t w = Wl[(int64_t)o * g_n(g) + i];
+                if (w > 0) {
+                    bk_edge(&b, l, lj, w, w);
+                } else if (w < 0) {
+                    int64_t m = -w;
+                    un[l] += -m + 2 * m * x[lj];
+                    un[lj] += -m + 2 * m * x[l];
+                    cst -= 2 * m * x[l] * x[lj];
+                }
+            }
+        }
+        for (int l = 0; l < B; l++) b.tr[l] = un[l] + lam * (1 - 2 * (int64_t)x[l]);
+        bk_run(&b, xs);
+        bk_free(&b);
+        int same = 1;
+        for (int l = 0; l < B; l++) same &= (xs[l] == x[l]);
+        if (same) {
+            if (lam == 0) { s++; break; }
+            lam /= 4;
+            continue;
+        }
+        /* predicted value of the approximation at x* (at x it equals e_cur) */
+        int64_t ap = cst;
+        for (int l = 0; l < B; l++) if (xs[l]) ap += un[l];
+        for (int l = 0; l < B; l++) {
+            int64_t z, y, xx, nz, ny, nx;
+            int64_t i = g_block_pixel(g, k, l, &z, &y, &xx);
+            for (int o = 0; o < g->nh; o++) {
+                int64_t j = g_nbr(g, z, y, xx, o, &nz, &ny, &nx);
+                if (j < 0 || g_block_of(g, nz, ny, nx) != k) continue;
+                int lj = (int)(((nz % g->bd) * g->bh + (ny % g->bh)) * g->bw + (nx % g->bw));
+                int64_t w = Wl[(int64_t)o * g_n(g) + i];
+                if (w > 0 && xs[l] != xs[lj]) ap += w;
+            }
+        }
+        int64_t e_new = lsa_energy(g, k, B, Cb, Wl, xs);
+        int64_t R = e_cur - e_new, P = e_cur - ap;
+        if (R > 0) {
+            memcpy(x, xs, (size_t)B);
+            e_cur = e_new;
+            if (4 * R >= 3 * P) lam /= 4;
+        } else {
+            lam = lam * 4 > 0 ? lam * 4 : 1;
+            if (lam > ((int64_t)1 << 50)) lam = (int64_t)1 << 50;
+        }
+    }
+    if (steps_done) *steps_done = s;
+    free(un); free(xs);
+    return rc;
+}
+
+/* Eq. 8 for every block by LSA-TR from the block's labels in yhat (image
+ * order, updated in place); C = Eq. 8 unaries (image order). */
+int orc_nsm_block_solve(const int64_t *dims, int conn, const int *block, const int64_t *Wl,
+                        const int64_t *C, uint8_t *yhat, int steps)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    int64_t K = g_nblocks(&g);
+    int B = g.bd * g.bh * g.bw;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t k = 0; k < K; k++) {
+        int64_t *Cb = malloc(sizeof(int64_t) * (size_t)B);
+        uint8_t *x = malloc((size_t)B);
+        int64_t *gi = malloc(sizeof(int64_t) * (size_t)B);
+        if (!Cb || !x || !gi) { err |= 1; free(Cb); free(x); free(gi); continue; }
+        for (int l = 0; l < B; l++) {
+            int64_t z, y, xx;
+            gi[l] = g_block_pixel(&g, k, l, &z, &y, &xx);
+            Cb[l] = C[gi[l]];
+            x[l] = yhat[gi[l]];
+        }
+        if (lsa_tr_block(&g, k, Cb, Wl, x, steps, NULL)) err |= 1;
+        for (int l = 0; l < B; l++) yhat[gi[l]] = x[l];
+        free(Cb); free(x); free(gi);
+    }
+    return err ? -1 : 0;
+}
+
+/* Algorithm 1 with LSA-TR block solves (Q = I); yhat^0 = 0 and each
+ * iteration's LSA-TR starts from the block's previous labels.  Same loop and
+ * outputs as orc_admm. */
+int orc_nsm_admm(const int64_t *dims, int conn, const int *block, const int64_t *U, const int64_t *Wl,
+                 double mu0, double mu_fact, double eps, int max_iter, int steps, uint8_t *labels,
+                 int *iters, double *rmax_trace, double *y_out, double *a_out, double *mu_out)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    int64_t n = g_n(&g), K = g_nblocks(&g);
+    double *y = malloc(sizeof(double) * (size_t)n);
+    double *a = malloc(sizeof(double) * (size_t)n);
+    double *r2 = malloc(sizeof(double) * (size_t)K);
+    int64_t *C = malloc(sizeof(int64_t) * (size_t)n);
+    if (!y || !a || !r2 || !C) { free(y); free(a); free(r2); free(C); return -4; }
+    for (int64_t i = 0; i < n; i++) { y[i] = 0.5; a[i] = 0.0; labels[i] = 0; }
+    double mu = mu0;
+    int t = 0, rc = 1;
+    while (t < max_iter) {
+        orc_shifted_caps(dims, conn, block, U, Wl, y, a, mu, NULL, C);
+        orc_nsm_block_solve(dims, conn, block, Wl, C, labels, steps);
+        orc_update(dims, conn, block, Wl, labels, mu, y, a, r2);
+        double m2 = 0.0;
+        for (int64_t k = 0; k < K; k++) if (r2[k] > m2) m2 = r2[k];
+        double rmax = sqrt(m2);
+        if (rmax_trace) rmax_trace[t] = rmax;
+        mu = mu * mu_fact;
+        t++;
+        if (!(rmax > eps)) { rc = 0; break; }
+    }
+    *iters = t;
+    if (y_out) memcpy(y_out, y, sizeof(double) * (size_t)n);
+    if (a_out) memcpy(a_out, a, sizeof(double) * (size_t)n);
+    if (mu_out) *mu_out = mu;
+    free(y); free(a); free(r2); free(C);
+    return rc;
+}
+
+/* Serial LSA-TR on the whole grid (one block = the grid) from x = 0: the
+ * non-submodular counterpart of sGC the paper compares against (Table 3).
+ * Returns E_int of the result. */
+int64_t orc_lsa_tr_global(const int64_t *dims, int conn, const int64_t *U, const int64_t *Wl,
+                          int steps, uint8_t *labels)
+{
+    int whole[3] = {(int)dims[0], (int)dims[1], (int)dims[2]};
+    grid_t g;
+    if (grid_init(&g, dims, conn, whole)) return INT64_MIN;
+    int64_t n = g_n(&g);
+    if (n > 0x7fffffff / (g.nh + 1)) return INT64_MIN;
+    memset(labels, 0, (size_t)n);
+    if (lsa_tr_block(&g, 0, U, Wl, labels, steps, NULL)) return INT64_MIN;
+    return orc_energy(dims, conn, whole, U, Wl, labels);
 }

@@ -423,3 +423,22 @@ def crop_request(base, req):
         w[3, -1, :] = 0
         w[3, :, 0] = 0
     return u, w.reshape(nh, -1)
+
+
+def nonsubmodular_instance(seed=0, size=1024, block=(16, 16), lam=1.0, neg_frac=0.2, u_sd=2.0):
+    """A 4-connected grid with non-submodular pairwise terms: unaries N(0, 2^2);
+    |w_ij| ~ |N(0, 1)|, and a random neg_frac of the edges negative (for
+    w |y_i - y_j| that is f(1,0) + f(0,1) < f(0,0) + f(1,1), the footnote's
+    non-submodular case); wq = rne(1024 w), 0 toward the outside."""
+    rng = _rng(3000 + seed)
+    H = W = size
+    u = rng.normal(0.0, u_sd, (H, W)).astype(np.float32)
+    wq = np.zeros((2, H * W), np.int32)
+    vol = np.zeros((1, H, W))
+    for k, (dz, dy, dx) in enumerate(FWD_OFFSETS[4]):
+        valid, _ = _shifted(vol, dz, dy, dx)
+        mag = np.abs(rng.normal(0.0, 1.0, (1, H, W)))
+        sign = np.where(rng.random((1, H, W)) < neg_frac, -1.0, 1.0)
+        wq[k] = np.where(valid, np.rint(1024.0 * mag * sign), 0).reshape(-1).astype(np.int32)
+    return {"name": f"nonsubmodular{size}", "grid": (H, W), "conn": 4, "block": tuple(block),
+            "lam": float(lam), "mu0": 100.0, "u": u.reshape(-1), "wq": wq}
