@@ -93,6 +93,12 @@ typedef struct {
                             non-overlapping partition, Q = I.  Overlapping contexts run three
                             launches per iteration; the batched calls and the server take only
                             Q = I contexts. */
+    int lsa_steps;       /* 0 (default): submodular weights only (negative weights are
+                            DOPE_EUNSUPPORTED).  > 0: weights of any sign (non-submodular pairwise
+                            terms, Section 3.4); every block's Eq. 8 is solved by LSA-TR (trust-region
+                            local submodular approximation, each step an exact block cut) with at
+                            most lsa_steps steps per block and iteration.  Such contexts run two
+                            launches per iteration, Q = I only. */
 } dope_params;
 
 /* Statistics of the last dope_solve / dope_iterate call. */

@@ -21,6 +21,7 @@
 #include "dope_internal.h"
 #include "dope_kernels.cuh"
 #include "dope_overlap.cuh"
+#include "dope_nsm.cuh"
 
 using namespace dope;
 
@@ -54,6 +55,8 @@ struct dope_ctx {
     // overlapping partition (grow != 0): image-order U / Wl / q / y, box-major a / yhat
     int ov = 0;
     OvArgs oa{};
+    int nsm = 0;                // non-submodular: LSA-TR block solves (k_nsm_solve)
+    int nsm_smem = 0;
     int ov_threads = 0, ov_smem = 0;
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
@@ -160,6 +163,12 @@ void launch_solve(dope_ctx* c, const SolveArgs& a, cudaStream_t st) {
 
 void solve_launch(dope_ctx* c, const SolveArgs& a, cudaStream_t st) {
     c->launches++;
+    if (c->nsm) {
+        if (c->conn == 4) k_nsm_solve<4><<<c->g.K, c->threads, c->nsm_smem, st>>>(a, c->p.lsa_steps);
+        else if (c->conn == 8) k_nsm_solve<8><<<c->g.K, c->threads, c->nsm_smem, st>>>(a, c->p.lsa_steps);
+        else k_nsm_solve<6><<<c->g.K, c->threads, c->nsm_smem, st>>>(a, c->p.lsa_steps);
+        return;
+    }
     if (c->conn == 4) launch_solve<4>(c, a, st);
     else if (c->conn == 8) launch_solve<8>(c, a, st);
     else launch_solve<6>(c, a, st);
@@ -448,6 +457,7 @@ void raise_smem_limits() {
     raise_smem_limit((const void*)k_admm_persistent<CONN, 256>);
     raise_smem_limit((const void*)k_admm_persistent<CONN, 512>);
     raise_smem_limit((const void*)k_admm_resident<CONN>);
+    raise_smem_limit((const void*)k_nsm_solve<CONN>);
 }
 
 // Algorithm 1 initialisation (y = 1/2, a = 0, mu = mu0), stream-ordered.
@@ -938,7 +948,7 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
             any = any || c->p.grow[i] != 0;
         }
         if (any) {
-            int rc = pad ? DOPE_EINVAL : create_overlap(c, dims, blk, grow3, st);
+            int rc = (pad || c->p.lsa_steps > 0) ? DOPE_EINVAL : create_overlap(c, dims, blk, grow3, st);
             if (rc) { dope_destroy(c); return rc; }
             *out = c;
             return DOPE_OK;
@@ -1011,6 +1021,17 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
         if (c->smem > optin) { dope_destroy(c); return DOPE_EINVAL; }
     }
     choose_launch(c);
+    if (c->p.lsa_steps > 0) {
+        // non-submodular: LSA-TR block solves, two launches per iteration
+        c->nsm = 1;
+        c->persist_grid = 0;
+        c->resident = 0;
+        c->nsm_smem = (int)(((solver_smem_bytes(connectivity, (int)B) + 15) & ~(size_t)15) + nsm_extra_bytes((int)B));
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (c->nsm_smem > optin || pad) { dope_destroy(c); return DOPE_EINVAL; }
+    }
     rc = reset_state_async(c, st);
     if (rc) { dope_destroy(c); return rc; }
     *out = c;
@@ -1034,6 +1055,7 @@ void dope_default_params(dope_params* p) {
     p->fold_rounds = 0;
     p->launch_mode = 0;
     p->grow[0] = p->grow[1] = p->grow[2] = 0;
+    p->lsa_steps = 0;
 }
 
 const char* dope_strerror(int s) {
@@ -1120,9 +1142,9 @@ int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void*
     if (rc) return rc;
     const int threads = 256;
     const int blocks = grid_for(c->g.N, threads);
-    if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
-    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
-    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl);
+    if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
+    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
+    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
     if (c->ov) k_ov_wcheck<<<grid_for(c->g.N * nh, threads), threads, 0, st>>>(c->Wl, c->g.N * nh, c->oa.M, c->ctrl);
     CK(cudaGetLastError());
     Ctrl h{};
@@ -1285,7 +1307,7 @@ int dope_shifted_caps(dope_ctx* c, int64_t* C, void* stream) {
 
 int dope_block_cuts(dope_ctx* c, const int64_t* C, uint8_t* yhat, void* stream) {
     if (!c || !C || !yhat || !c->have_w) return DOPE_EINVAL;
-    if (c->ov) return DOPE_EINVAL;
+    if (c->ov || c->nsm) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 17, 1);
@@ -1612,9 +1634,9 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     }
     const int tpb = 256;
     k_set_unaries<<<grid_for(N, tpb), tpb, 0, st>>>(g, u, U, ctrl);
-    if (connectivity == 4) k_set_weights<4><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl);
-    else if (connectivity == 8) k_set_weights<8><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl);
-    else k_set_weights<6><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl);
+    if (connectivity == 4) k_set_weights<4><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl, 0);
+    else if (connectivity == 8) k_set_weights<8><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl, 0);
+    else k_set_weights<6><<<grid_for(N, tpb), tpb, 0, st>>>(g, wq, Wl, lambda, ctrl, 0);
     k_init_state<<<grid_for((long long)g.K * g.F, tpb), tpb, 0, st>>>(g, yF, aF);
     CK(cudaGetLastError());
     Ctrl h{};
@@ -1714,9 +1736,9 @@ int dope_upload_async(dope_ctx* c, const float* u, const int32_t* wq, int where,
     const int threads = 256;
     const int blocks = grid_for(c->g.N, threads);
     k_set_unaries<<<blocks, threads, 0, st>>>(c->g, su, c->U, c->ctrl);
-    if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl);
-    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl);
-    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl);
+    if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl, c->nsm);
+    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl, c->nsm);
+    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, sw, c->Wl, c->lambda, c->ctrl, c->nsm);
     CK(cudaGetLastError());
     c->have_u = c->have_w = 1;   // provisional until dope_ctx_status has read the status word
     return DOPE_OK;
@@ -1885,7 +1907,7 @@ int dope_batch_launch(dope_ctx* const* cs, int n, int n_iter, int exit_on_done, 
     long long total = 0;
     for (int i = 0; i < n; ++i) {
         dope_ctx* c = cs[i];
-        if (!c || !c->have_u || !c->have_w || c->ov) return DOPE_EINVAL;
+        if (!c || !c->have_u || !c->have_w || c->ov || c->nsm) return DOPE_EINVAL;
         for (int j = 0; j < i; ++j)
             if (cs[j] == c) return DOPE_EINVAL;
         const int width = solver_width(c->g.B, c->threads);

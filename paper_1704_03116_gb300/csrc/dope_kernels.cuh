@@ -913,7 +913,7 @@ __global__ void k_set_unaries(Geo g, const float* __restrict__ u, int32_t* __res
 // outside of the grid (else DOPE_EINVAL), Wl < 2^24 (else DOPE_EOVERFLOW).
 template <int CONN>
 __global__ void k_set_weights(Geo g, const int32_t* __restrict__ wq, int32_t* __restrict__ Wl,
-                              double lambda, Ctrl* c) {
+                              double lambda, Ctrl* c, int allow_negative) {
     constexpr int nh = CONN / 2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -934,11 +934,11 @@ __global__ void k_set_weights(Geo g, const int32_t* __restrict__ wq, int32_t* __
             const int w = wq[(long long)d * g.Nu + iu];
             int q = 0;
             const bool inside = (z + dz < g.Du) && (y + dy < g.Hu) && (x + dx >= 0) && (x + dx < g.Wu);
-            if (w < 0) set_status(c, 2);
+            if (w < 0 && !allow_negative) set_status(c, 2);
             else if (!inside && w != 0) set_status(c, 1);
             else {
                 const double v = __dmul_rn(lambda, (double)w);
-                if (!(v < 16777215.5)) set_status(c, 4);
+                if (!(fabs(v) < 16777215.5)) set_status(c, 4);
                 else q = (int)__double2ll_rn(v);
             }
             Wl[(long long)d * g.N + b] = q;

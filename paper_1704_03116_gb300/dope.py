@@ -37,7 +37,7 @@ class dope_params(ctypes.Structure):
     _fields_ = [("mu0", ctypes.c_double), ("mu_fact", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("relabel_period", ctypes.c_int),
                 ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int), ("fold_rounds", ctypes.c_int),
-                ("launch_mode", ctypes.c_int), ("grow", ctypes.c_int * 3)]
+                ("launch_mode", ctypes.c_int), ("grow", ctypes.c_int * 3), ("lsa_steps", ctypes.c_int)]
 
 
 class dope_stats(ctypes.Structure):
@@ -476,11 +476,11 @@ class Dope:
 
     def __init__(self, grid, connectivity, block_shape, lam, mu0=None, mu_fact=None, eps=None,
                  max_iter=None, relabel_period=None, threads=None, max_pulses=None, fold_rounds=None,
-                 launch_mode=None, grow=None):
+                 launch_mode=None, grow=None, lsa_steps=None):
         p = dope_default_params()
         for k, v in dict(mu0=mu0, mu_fact=mu_fact, eps=eps, max_iter=max_iter,
                          relabel_period=relabel_period, threads=threads, max_pulses=max_pulses,
-                         fold_rounds=fold_rounds, launch_mode=launch_mode).items():
+                         fold_rounds=fold_rounds, launch_mode=launch_mode, lsa_steps=lsa_steps).items():
             if v is not None:
                 setattr(p, k, v)
         if grow is not None:

@@ -442,3 +442,15 @@ def nonsubmodular_instance(seed=0, size=1024, block=(16, 16), lam=1.0, neg_frac=
         wq[k] = np.where(valid, np.rint(1024.0 * mag * sign), 0).reshape(-1).astype(np.int32)
     return {"name": f"nonsubmodular{size}", "grid": (H, W), "conn": 4, "block": tuple(block),
             "lam": float(lam), "mu0": 100.0, "u": u.reshape(-1), "wq": wq}
+
+
+def signed_instance(d, neg_frac=0.2, seed=0):
+    """Copy of instance d with a random neg_frac of its edges made negative
+    (non-submodular pairwise terms)."""
+    rng = _rng(4000 + seed)
+    wq = np.array(d["wq"], np.int32)
+    flip = rng.random(wq.shape) < neg_frac
+    out = dict(d)
+    out["wq"] = np.where(flip, -wq, wq).astype(np.int32)
+    out["name"] = d.get("name", "instance") + "_signed"
+    return out
