@@ -304,28 +304,26 @@ def _summ(res, st, t0, reqs, arrivals):
             "failed": sum(1 for i in res if res[i]["status"] != 0), "completed": len(res)}
 
 
-def run_serving(args):
+def serving_summary(requests, rate, saturated=True):
     """Serving stream: requests (RGB contrast-Potts crops, side U[128,2048],
     4/8-conn 50/50, lambda U[1,16]) arrive as a Poisson process at `rate`;
     the batched server (continuous batching) against the same server solving
-    one request at a time through the single-problem path.  Also both with
-    every request queued at once (capacity)."""
+    one request at a time through the single-problem path, and both again with
+    every request queued at once (capacity).  Returns (summary, launches)."""
     import torch
-    from paper_1704_03116_gb300 import _build, inputs
-    _build.build()
-    torch.cuda.set_device(0)
+    from paper_1704_03116_gb300 import inputs
     from paper_1704_03116_gb300 import dope
-    n = args.requests
-    reqs = inputs.serving_requests(n, rate=args.rate)
+    n = requests
+    reqs = inputs.serving_requests(n, rate=rate)
     arrivals = [r["arrival"] for r in reqs]
     bases = [inputs.serving_base(b) for b in range(2)]
     dbase = [(torch.from_numpy(b["u"]).cuda(), torch.from_numpy(b["wq"]).cuda()) for b in bases]
     dev_in = []
     for r in reqs:
         U, WQ = dbase[r["base"]]
-        s, y0, x0, nh = r["side"], r["y0"], r["x0"], r["conn"] // 2
-        u = U[y0:y0 + s, x0:x0 + s].contiguous().reshape(-1)
-        w = WQ[:nh, y0:y0 + s, x0:x0 + s].clone()
+        s_, y0, x0, nh = r["side"], r["y0"], r["x0"], r["conn"] // 2
+        u = U[y0:y0 + s_, x0:x0 + s_].contiguous().reshape(-1)
+        w = WQ[:nh, y0:y0 + s_, x0:x0 + s_].clone()
         w[0, :, -1] = 0
         w[1, -1, :] = 0
         if nh == 4:
@@ -341,8 +339,6 @@ def run_serving(args):
         r = dict(reqs[k], lam=2.0)
         warm.append((dev_in[k][0], dev_in[k][1], torch.zeros_like(labels[k]), r))
     torch.cuda.synchronize()
-    clk = Clocks(0)
-    clk.start()
     out = {}
     res_b, st_b, t0b = _serve(dope, torch, reqs, dev_in, labels, 0, arrivals, warm)
     out["batched"] = _summ(res_b, st_b, t0b, reqs, arrivals)
@@ -353,25 +349,36 @@ def run_serving(args):
     same = all(res_b[i]["energy_int"] == res_1[i]["energy_int"] and
                res_b[i]["iterations"] == res_1[i]["iterations"] for i in range(n))
     same = same and all(torch.equal(a, b) for a, b in zip(keep, labels))
-    if not args.no_saturated:
+    if saturated:
         res_bs, st_bs, t0bs = _serve(dope, torch, reqs, dev_in, labels, 0, None, warm)
         out["batched_saturated"] = _summ(res_bs, st_bs, t0bs, reqs, None)
         res_1s, st_1s, t01s = _serve(dope, torch, reqs, dev_in, labels, 1, None, warm)
         out["one_at_a_time_saturated"] = _summ(res_1s, st_1s, t01s, reqs, None)
+    out["results_identical_batched_vs_one_at_a_time"] = bool(same)
+    out["iterations_mean"] = round(sum(res_b[i]["iterations"] for i in range(n)) / n, 1)
+    out["config"] = {"workload": "serving stream: RGB contrast-Potts crops of two seeded 2048x2048 ellipse "
+                                 "images, side U[128,2048], 4/8-conn 50/50, lambda U[1,16], blocks 32x32",
+                     "requests": n, "rate_per_s": rate, "inputs": "device-resident"}
+    return out, int(2 * st_b["launches"] + 5 * n)
+
+
+def run_serving(args):
+    """bench.py --workload serving: the serving comparison as its own line."""
+    import torch
+    from paper_1704_03116_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    clk = Clocks(0)
+    clk.start()
+    out, launches = serving_summary(args.requests, args.rate, not args.no_saturated)
     clocks = clk.stop()
-    iters = [res_b[i]["iterations"] for i in range(n)]
     line = {"metric": "solves/sec of a Poisson request stream to ADMM convergence (p50/p99 latency)",
             "value": out["batched"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1,
             "warmup": 1, "ms_per_step": round(out["batched"]["makespan_s"] * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {
-                "workload": "serving stream: RGB contrast-Potts crops of two seeded 2048x2048 ellipse images, "
-                            "side U[128,2048], 4/8-conn 50/50, lambda U[1,16], blocks 32x32",
-                "requests": n, "rate_per_s": args.rate, "inputs": "device-resident",
-                "l2": "inputs larger than L2 (1.5 Mpx mean per request)"},
-            "serving": out, "results_identical_batched_vs_one_at_a_time": bool(same),
-            "iterations_mean": round(sum(iters) / n, 1), "clocks": clocks,
-            "gpu_launches": int(2 * st_b["launches"] + 5 * n)}
+            "data": "synthetic", "config": dict(out.pop("config"),
+                                                l2="inputs larger than L2 (1.5 Mpx mean per request)"),
+            "serving": out, "clocks": clocks, "gpu_launches": launches}
     print(json.dumps(line))
 
 
@@ -386,6 +393,8 @@ def main():
     ap.add_argument("--requests", type=int, default=1000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per second")
     ap.add_argument("--no-saturated", action="store_true", help="serving workload: skip the capacity runs")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default workload: skip the serving comparison added to its line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -556,6 +565,13 @@ def main():
         line["energy_gap_vs_serial_lsa_tr" if insts[0].get("lsa_steps") else "energy_gap_vs_global_mincut"] = gaps
         line["oracle_match"] = all(abs(E * 1024 - r["energy"]) <= 1e-4 * abs(r["energy"])
                                    for E, r in zip(energies[-len(insts):], res))
+    if rank == 0 and world == 1 and args.workload == "ellipses512" and not args.no_serving:
+        # the serving target: batched vs one-at-a-time on the request stream
+        try:
+            srv, _ = serving_summary(args.requests, args.rate, not args.no_saturated)
+            line["serving"] = srv
+        except Exception as e:  # the main line stands on its own
+            line["serving"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
