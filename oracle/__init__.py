@@ -292,8 +292,8 @@ def grid_edges(inst: Instance, within_blocks: bool = False):
     """Edge list (u, v, Wl) of the grid (each undirected edge once), optionally
     only the edges whose two ends share a block.  Plain numpy, for tests."""
     D, H, W = inst.dims
-    offs = {4: [(0, 0, 1), (0, 1, 0)], 8: [(0, 0, 1), (0, 1, 0), (0, 1, 1), (0, 1, -1)],
-            6: [(0, 0, 1), (0, 1, 0), (1, 0, 0)]}[inst.conn]
+    from .theorem1 import _OFFS
+    offs = _OFFS[inst.conn]
     bd, bh, bw = inst.block
     eu, ev, ww = [], [], []
     for k, (dz, dy, dx) in enumerate(offs):

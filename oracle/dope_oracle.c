@@ -57,6 +57,44 @@ static const int OFF4[2][3] = {{0, 0, 1}, {0, 1, 0}};
 static const int OFF8[4][3] = {{0, 0, 1}, {0, 1, 0}, {0, 1, 1}, {0, 1, -1}};
 static const int OFF6[3][3] = {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}};
 
+/* Larger kernels (Section 3: kernel sizes 5, 7, 9; square in 2-D, spherical in
+ * 3-D).  Forward offsets of radius r, in this order: dz = 0..r, dy = -r..r,
+ * dx = -r..r, keeping the offsets that are lexicographically positive
+ * (dz > 0, or dz = 0 and dy > 0, or dz = dy = 0 and dx > 0) and inside the
+ * kernel (2-D: |dy|, |dx| <= r with dz = 0; 3-D: dz^2 + dy^2 + dx^2 <= r^2).
+ * conn = number of neighbours: 2-D 24 / 48 / 80 (r = 2, 3, 4), 3-D 32 (r = 2). */
+static int OFFK[128][3];
+static int offk_conn = 0;
+
+static int big_kernel(int conn, int *r, int *is3d)
+{
+    switch (conn) {
+        case 24: *r = 2; *is3d = 0; return 1;
+        case 48: *r = 3; *is3d = 0; return 1;
+        case 80: *r = 4; *is3d = 0; return 1;
+        case 32: *r = 2; *is3d = 1; return 1;
+        default: return 0;
+    }
+}
+
+static const int (*big_offsets(int conn))[3]
+{
+    int r, is3d, n = 0;
+    if (!big_kernel(conn, &r, &is3d)) return NULL;
+    if (offk_conn == conn) return (const int (*)[3])OFFK;
+    for (int dz = 0; dz <= (is3d ? r : 0); dz++)
+        for (int dy = -r; dy <= r; dy++)
+            for (int dx = -r; dx <= r; dx++) {
+                int pos = dz > 0 || (dz == 0 && dy > 0) || (dz == 0 && dy == 0 && dx > 0);
+                int in = is3d ? (dz * dz + dy * dy + dx * dx <= r * r) : 1;
+                if (!pos || !in) continue;
+                OFFK[n][0] = dz; OFFK[n][1] = dy; OFFK[n][2] = dx;
+                n++;
+            }
+    offk_conn = conn;
+    return (const int (*)[3])OFFK;
+}
+
 typedef struct {
     int64_t D, H, W;      /* grid extent, D = 1 for 2-D */
     int conn;             /* 4, 8 (2-D) or 6 (3-D) */
@@ -73,6 +111,7 @@ static int grid_init(grid_t *g, const int64_t *dims, int conn, const int *block)
     if (conn == 4) { g->off = OFF4; g->nh = 2; }
     else if (conn == 8) { g->off = OFF8; g->nh = 4; }
     else if (conn == 6) { g->off = OFF6; g->nh = 3; }
+    else if (big_offsets(conn)) { g->off = big_offsets(conn); g->nh = conn / 2; }
     else return -1;
     if (g->D <= 0 || g->H <= 0 || g->W <= 0) return -1;
     if (g->bd <= 0 || g->bh <= 0 || g->bw <= 0) return -1;
@@ -795,6 +834,18 @@ static int ov_init(ov_t *o, const int64_t *dims, int conn, const int *block, con
 
 static void ov_free(ov_t *o) { free(o->q); o->q = NULL; }
 
+/* Largest coordinate offset of the neighbourhood. */
+static int64_t ov_radius(const grid_t *g)
+{
+    int r = 0;
+    for (int o = 0; o < g->nh; o++)
+        for (int a = 0; a < 3; a++) {
+            int v = g->off[o][a] < 0 ? -g->off[o][a] : g->off[o][a];
+            if (v > r) r = v;
+        }
+    return r;
+}
+
 /* Tiles along one axis whose grown range holds coordinate c. */
 static int ov_axis_count(int64_t c, int64_t nb, int b, int gr)
 {
@@ -985,10 +1036,11 @@ int orc_ov_update(const int64_t *dims, int conn, const int *block, const int *gr
             for (int64_t x = 0; x < g->W; x++) {
                 int64_t j = (z * g->H + yy) * g->W + x, iz, iy, ix;
                 int qj = ov_q(&o, z, yy, x);
-                /* tiles whose box can hold j or a neighbour of j */
-                int64_t k0z = (z - 1 - o.gd) / g->bd - 1, k1z = (z + 1 + o.gd) / g->bd + 1;
-                int64_t k0y = (yy - 1 - o.gh) / g->bh - 1, k1y = (yy + 1 + o.gh) / g->bh + 1;
-                int64_t k0x = (x - 1 - o.gw) / g->bw - 1, k1x = (x + 1 + o.gw) / g->bw + 1;
+                /* tiles whose box can hold j or a neighbour of j (up to R away) */
+                int64_t R = ov_radius(g);
+                int64_t k0z = (z - R - o.gd) / g->bd - 1, k1z = (z + R + o.gd) / g->bd + 1;
+                int64_t k0y = (yy - R - o.gh) / g->bh - 1, k1y = (yy + R + o.gh) / g->bh + 1;
+                int64_t k0x = (x - R - o.gw) / g->bw - 1, k1x = (x + R + o.gw) / g->bw + 1;
                 double A = 0.0;
                 int64_t G = 0;
                 for (int64_t kz = k0z; kz <= k1z; kz++)

@@ -26,6 +26,13 @@ import numpy as np
 _OFFS = {4: [(0, 0, 1), (0, 1, 0)],
          8: [(0, 0, 1), (0, 1, 0), (0, 1, 1), (0, 1, -1)],
          6: [(0, 0, 1), (0, 1, 0), (1, 0, 0)]}
+# larger kernels: every nonzero offset of the square (2-D) or ball (3-D) of
+# radius r with a positive first nonzero coordinate, ordered by (dz, dy, dx)
+for _r, _c3 in ((2, False), (3, False), (4, False), (2, True)):
+    _l = sorted((dz, dy, dx) for dz in range(0, (_r if _c3 else 0) + 1)
+                for dy in range(-_r, _r + 1) for dx in range(-_r, _r + 1)
+                if (dz, dy, dx) > (0, 0, 0) and (not _c3 or dz * dz + dy * dy + dx * dx <= _r * _r))
+    _OFFS[len(_l) * 2] = _l
 
 
 def grid_pairwise(dims, conn, w_fwd):

@@ -33,6 +33,30 @@ FWD_OFFSETS = {
 }
 
 
+def _kernel_offsets(r, is3d):
+    """Forward offsets of a square (2-D) or spherical (3-D) kernel of radius r:
+    dz = 0..r, dy = -r..r, dx = -r..r, lexicographically positive ones inside
+    the kernel, in that order."""
+    out = []
+    for dz in range(0, (r if is3d else 0) + 1):
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                if not (dz > 0 or (dz == 0 and dy > 0) or (dz == 0 and dy == 0 and dx > 0)):
+                    continue
+                if is3d and dz * dz + dy * dy + dx * dx > r * r:
+                    continue
+                out.append((dz, dy, dx))
+    return out
+
+
+# Section 3's larger kernels: 5x5, 7x7, 9x9 squares (24, 48, 80 neighbours) and
+# the radius-2 sphere in 3-D (32 neighbours)
+for _r in (2, 3, 4):
+    FWD_OFFSETS[(2 * _r + 1) ** 2 - 1] = _kernel_offsets(_r, False)
+FWD_OFFSETS[32] = _kernel_offsets(2, True)
+KERNEL_CONN = {(2, 3): 8, (2, 5): 24, (2, 7): 48, (2, 9): 80, (3, 3): 6, (3, 5): 32}
+
+
 def _rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 
