@@ -1,9 +1,9 @@
 """Build of the CUDA library libdope.so (sm_103a), in-tree.
 
-Two translation units, compiled in parallel by nvcc for sm_103a only and
-linked into one shared library: csrc/dope.cu (kernels in
-csrc/dope_kernels.cuh, the solver C-ABI) and csrc/dope_server.cu (the request
-server, host code).  It links the CUDA runtime statically and has no PyTorch
+Three translation units, compiled in parallel by nvcc for sm_103a only and
+linked into one shared library: csrc/dope.cu (kernels in csrc/*.cuh, the
+solver C-ABI), csrc/dope_big.cu (the larger-kernel instantiations) and
+csrc/dope_server.cu (the request server, host code).  It links the CUDA runtime statically and has no PyTorch
 dependency (the C-ABI takes plain pointers).
 """
 import os
@@ -12,9 +12,10 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "dope.cu"), os.path.join(HERE, "csrc", "dope_server.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "dope_kernels.cuh"), os.path.join(HERE, "csrc", "dope_internal.h"),
-              os.path.join(ROOT, "include", "dope.h")]
+SRC = [os.path.join(HERE, "csrc", "dope.cu"), os.path.join(HERE, "csrc", "dope_big.cu"),
+       os.path.join(HERE, "csrc", "dope_server.cu")]
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("dope_kernels.cuh", "dope_internal.h", "dope_overlap.cuh",
+                                                       "dope_nsm.cuh", "dope_big.h")] + [os.path.join(ROOT, "include", "dope.h")]
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdope.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -15,6 +15,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "dope.h"
@@ -22,6 +23,7 @@
 #include "dope_kernels.cuh"
 #include "dope_overlap.cuh"
 #include "dope_nsm.cuh"
+#include "dope_big.h"
 
 using namespace dope;
 
@@ -544,6 +546,19 @@ int ov_axis_q(long long c, int b, int gr, int nb) {
     return (int)(hi - lo + 1);
 }
 
+// Calls f(std::integral_constant<int, CONN>) for the connectivities the
+// overlapping-partition kernels are built for (the 3x3 ones and the larger
+// kernels of Section 3); false for any other.
+template <class F>
+bool ov_dispatch(int conn, F&& f) {
+    switch (conn) {
+        case 4: f(std::integral_constant<int, 4>{}); return true;
+        case 8: f(std::integral_constant<int, 8>{}); return true;
+        case 6: f(std::integral_constant<int, 6>{}); return true;
+        default: return false;   // the larger kernels: dope_big.cu's launchers
+    }
+}
+
 template <int CONN>
 void ov_raise_smem() {
     static std::once_flag once;
@@ -614,9 +629,7 @@ int create_overlap(dope_ctx* c, const int64_t dims[3], const int32_t blk[3], con
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (c->ov_smem > optin) return DOPE_EINVAL;
-    if (c->conn == 4) ov_raise_smem<4>();
-    else if (c->conn == 8) ov_raise_smem<8>();
-    else ov_raise_smem<6>();
+    if (!ov_dispatch(c->conn, [](auto cc) { ov_raise_smem<decltype(cc)::value>(); })) big_raise_smem(c->conn);
     const int nh = c->conn / 2;
     const size_t KB = (size_t)b.K * b.B;
     int rc = DOPE_OK;
@@ -688,9 +701,13 @@ int ov_run(dope_ctx* c, int n, cudaStream_t st) {
         for (int j = 0; j < nb; ++j) {
             const int idx = launched + j;
             if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx], st));
-            if (c->conn == 4) ov_launch_iteration<4>(c, t0 + idx + 1, mus[idx], idx > 0, st, c->profiling ? c->ev[3 * idx + 1] : nullptr);
-            else if (c->conn == 8) ov_launch_iteration<8>(c, t0 + idx + 1, mus[idx], idx > 0, st, c->profiling ? c->ev[3 * idx + 1] : nullptr);
-            else ov_launch_iteration<6>(c, t0 + idx + 1, mus[idx], idx > 0, st, c->profiling ? c->ev[3 * idx + 1] : nullptr);
+            cudaEvent_t mid = c->profiling ? c->ev[3 * idx + 1] : nullptr;
+            if (!ov_dispatch(c->conn, [&](auto cc) {
+                    ov_launch_iteration<decltype(cc)::value>(c, t0 + idx + 1, mus[idx], idx > 0, st, mid);
+                })) {
+                big_ov_iteration(c->conn, c->oa, c->ov_threads, c->ov_smem, mus[idx], t0 + idx + 1, idx > 0, st, mid);
+                c->launches += 3;
+            }
             if (c->profiling) CK(cudaEventRecord(c->ev[3 * idx + 2], st));
         }
         CK(cudaGetLastError());
@@ -751,9 +768,10 @@ int ov_finish(dope_ctx* c, uint8_t* labels_dev, int64_t* energy, cudaStream_t st
     if (energy) {
         CK(cudaMemsetAsync(&c->ctrl->energy, 0, sizeof(unsigned long long), st));
         const int blocks = grid_for(A.N, 256);
-        if (c->conn == 4) k_energy_img<4><<<blocks, 256, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl);
-        else if (c->conn == 8) k_energy_img<8><<<blocks, 256, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl);
-        else k_energy_img<6><<<blocks, 256, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl);
+        if (!ov_dispatch(c->conn, [&](auto cc) {
+                k_energy_img<decltype(cc)::value><<<blocks, 256, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl);
+            }))
+            big_energy_img(c->conn, A.D, A.H, A.W, c->U, c->Wl, labels_dev, c->ctrl, blocks, 256, st);
         c->launches++;
         CK(cudaGetLastError());
         unsigned long long v = 0;
@@ -893,8 +911,10 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
     if (!out) return DOPE_EINVAL;
     *out = nullptr;
     if (!grid || !block_shape || (ndim != 2 && ndim != 3)) return DOPE_EINVAL;
-    if (ndim == 2 && connectivity != 4 && connectivity != 8) return DOPE_EINVAL;
-    if (ndim == 3 && connectivity != 6) return DOPE_EINVAL;
+    const bool big_kernel = (ndim == 2 && (connectivity == 24 || connectivity == 48 || connectivity == 80)) ||
+                            (ndim == 3 && connectivity == 32);
+    if (ndim == 2 && connectivity != 4 && connectivity != 8 && !big_kernel) return DOPE_EINVAL;
+    if (ndim == 3 && connectivity != 6 && !big_kernel) return DOPE_EINVAL;
     if (!(lambda >= 0.0) || !std::isfinite(lambda)) return DOPE_EINVAL;
     int64_t dims[3] = {1, 1, 1}, udims[3] = {1, 1, 1};
     int32_t blk[3] = {1, 1, 1};
@@ -947,7 +967,9 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
             grow3[3 - ndim + i] = c->p.grow[i];
             any = any || c->p.grow[i] != 0;
         }
-        if (any) {
+        if (any || big_kernel) {
+            // overlapping partitions, and the larger kernels (at zero growth the
+            // overlap kernels compute exactly the Q = I iteration)
             int rc = (pad || c->p.lsa_steps > 0) ? DOPE_EINVAL : create_overlap(c, dims, blk, grow3, st);
             if (rc) { dope_destroy(c); return rc; }
             *out = c;
@@ -1142,10 +1164,16 @@ int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void*
     if (rc) return rc;
     const int threads = 256;
     const int blocks = grid_for(c->g.N, threads);
-    if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
+    if (c->ov) {
+        if (!ov_dispatch(c->conn, [&](auto cc) {
+                k_set_weights<decltype(cc)::value><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, 0);
+            }))
+            big_set_weights(c->conn, c->g, src, c->Wl, c->lambda, c->ctrl, blocks, threads, st);
+        const long long scale = (long long)c->oa.M * (c->conn > 8 ? c->conn / 8 : 1);
+        k_ov_wcheck<<<grid_for(c->g.N * nh, threads), threads, 0, st>>>(c->Wl, c->g.N * nh, scale, c->ctrl);
+    } else if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
     else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
     else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
-    if (c->ov) k_ov_wcheck<<<grid_for(c->g.N * nh, threads), threads, 0, st>>>(c->Wl, c->g.N * nh, c->oa.M, c->ctrl);
     CK(cudaGetLastError());
     Ctrl h{};
     rc = read_ctrl(c, &h, st);
@@ -1359,9 +1387,10 @@ int dope_energy(dope_ctx* c, const uint8_t* labels, int where, int64_t* energy_i
         CK(cudaMemsetAsync(&c->ctrl->energy, 0, sizeof(unsigned long long), st));
         const int blocks = grid_for(c->g.N, threads);
         const OvArgs& A = c->oa;
-        if (c->conn == 4) k_energy_img<4><<<blocks, threads, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl);
-        else if (c->conn == 8) k_energy_img<8><<<blocks, threads, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl);
-        else k_energy_img<6><<<blocks, threads, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl);
+        if (!ov_dispatch(c->conn, [&](auto cc) {
+                k_energy_img<decltype(cc)::value><<<blocks, threads, 0, st>>>(A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl);
+            }))
+            big_energy_img(c->conn, A.D, A.H, A.W, c->U, c->Wl, src, c->ctrl, blocks, threads, st);
         CK(cudaGetLastError());
         unsigned long long v = 0;
         CK(cudaMemcpyAsync(&v, &c->ctrl->energy, sizeof(v), cudaMemcpyDeviceToHost, st));

@@ -174,10 +174,41 @@ __device__ __forceinline__ void dir_off(int k, int& dz, int& dy, int& dx) {
     const int s = k < nh ? 1 : -1;
     if (CONN == 6) {
         dz = (o == 2); dy = (o == 1); dx = (o == 0);
-    } else {
+    } else if (CONN == 4 || CONN == 8) {
         dz = 0; dy = (o >= 1); dx = (o == 0) ? 1 : (o == 1 ? 0 : (o == 2 ? 1 : -1));
+    } else if (CONN == 32) {
+        // radius-2 ball, forward offsets ordered by (dz, dy, dx)
+        dz = o < 6 ? 0 : (o < 15 ? 1 : 2);
+        if (o < 6) {
+            dy = o < 2 ? 0 : (o < 5 ? 1 : 2);
+            dx = o < 2 ? o + 1 : (o < 5 ? o - 3 : 0);
+        } else if (o < 15) {
+            dy = (o - 6) / 3 - 1;
+            dx = (o - 6) % 3 - 1;
+        } else {
+            dy = 0;
+            dx = 0;
+        }
+    } else {
+        // (2r+1)^2 - 1 square kernel: row dy = 0 with dx = 1..r, then rows
+        // dy = 1..r with dx = -r..r
+        constexpr int r = CONN == 24 ? 2 : (CONN == 48 ? 3 : 4);
+        dz = 0;
+        if (o < r) {
+            dy = 0;
+            dx = o + 1;
+        } else {
+            dy = 1 + (o - r) / (2 * r + 1);
+            dx = (o - r) % (2 * r + 1) - r;
+        }
     }
     dz *= s; dy *= s; dx *= s;
+}
+
+// Largest coordinate offset of the neighbourhood of connectivity CONN.
+template <int CONN>
+__host__ __device__ constexpr int kernel_radius() {
+    return CONN == 24 || CONN == 32 ? 2 : (CONN == 48 ? 3 : (CONN == 80 ? 4 : 1));
 }
 
 // Local-index offset of direction d inside a block with row pitch bw and
@@ -891,6 +922,7 @@ __device__ __forceinline__ long long user_index(const Geo& g, int z, int y, int 
 
 // U = rne(1024 u); |U| < 2^30 and u finite, else DOPE_EOVERFLOW.  Padding
 // pixels get 0.
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 __global__ void k_set_unaries(Geo g, const float* __restrict__ u, int32_t* __restrict__ U, Ctrl* c) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
          i += (long long)gridDim.x * blockDim.x) {
@@ -908,6 +940,7 @@ __global__ void k_set_unaries(Geo g, const float* __restrict__ u, int32_t* __res
         U[bm_index(g, i)] = q;
     }
 }
+#endif
 
 // Wl = rne(lambda wq); wq >= 0 (else DOPE_EUNSUPPORTED), zero toward the
 // outside of the grid (else DOPE_EINVAL), Wl < 2^24 (else DOPE_EOVERFLOW).
@@ -933,7 +966,8 @@ __global__ void k_set_weights(Geo g, const int32_t* __restrict__ wq, int32_t* __
             }
             const int w = wq[(long long)d * g.Nu + iu];
             int q = 0;
-            const bool inside = (z + dz < g.Du) && (y + dy < g.Hu) && (x + dx >= 0) && (x + dx < g.Wu);
+            const bool inside = (z + dz >= 0) && (z + dz < g.Du) && (y + dy >= 0) && (y + dy < g.Hu) &&
+                                (x + dx >= 0) && (x + dx < g.Wu);
             if (w < 0 && !allow_negative) set_status(c, 2);
             else if (!inside && w != 0) set_status(c, 1);
             else {
@@ -946,6 +980,7 @@ __global__ void k_set_weights(Geo g, const int32_t* __restrict__ wq, int32_t* __
     }
 }
 
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 __global__ void k_init_state(Geo g, double* yF, double* aF) {
     const long long n = (long long)g.K * g.F;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -954,8 +989,10 @@ __global__ void k_init_state(Geo g, double* yF, double* aF) {
         aF[i] = 0.0;
     }
 }
+#endif
 
 // labels (caller's image order, padding dropped) <- yhat (block-major)
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 __global__ void k_unpermute_u8(Geo g, const uint8_t* __restrict__ src, uint8_t* __restrict__ dst) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.Nu;
          i += (long long)gridDim.x * blockDim.x) {
@@ -966,18 +1003,23 @@ __global__ void k_unpermute_u8(Geo g, const uint8_t* __restrict__ src, uint8_t* 
         dst[i] = src[bm_index(g, ((long long)z * g.H + y) * g.W + x)];
     }
 }
+#endif
 
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 __global__ void k_permute_u8(Geo g, const uint8_t* __restrict__ src, uint8_t* __restrict__ dst) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
          i += (long long)gridDim.x * blockDim.x)
         dst[bm_index(g, i)] = src[i];
 }
+#endif
 
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 __global__ void k_permute_i64(Geo g, const long long* __restrict__ src, long long* __restrict__ dst) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
          i += (long long)gridDim.x * blockDim.x)
         dst[bm_index(g, i)] = src[i];
 }
+#endif
 
 // E_int of block-major labels (Eq. 1, each undirected edge once), int64.
 template <int CONN>
@@ -1013,6 +1055,7 @@ __global__ void k_energy(Geo g, const int32_t* __restrict__ U, const int32_t* __
 }
 
 // Dense state (image order) from the face state.
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 __global__ void k_get_state(Geo g, const double* yF, const double* aF, const uint8_t* yhat,
                             const int16_t* faceIndex, int t, double* y, double* a, uint8_t* yh) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
@@ -1029,8 +1072,10 @@ __global__ void k_get_state(Geo g, const double* yF, const double* aF, const uin
         if (yh) yh[i] = t == 0 ? 0 : lab;
     }
 }
+#endif
 
 // Face state from a dense state; checks the interior invariant.
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 __global__ void k_set_state(Geo g, const double* y, const double* a, const uint8_t* yh,
                             const int16_t* faceIndex, int t, double* yF, double* aF,
                             uint8_t* yhat, Ctrl* c) {
@@ -1050,6 +1095,7 @@ __global__ void k_set_state(Geo g, const double* y, const double* a, const uint8
         if (f >= 0) { yF[(long long)k * g.F + f] = y[i]; aF[(long long)k * g.F + f] = a[i]; }
     }
 }
+#endif
 
 // Step a4 alone: Eq. 8 unaries of every pixel (image order) for the state.
 template <int CONN>
@@ -1906,6 +1952,7 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     }
 }
 
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY   // the batched launch and its constant table live in one translation unit
 // ---------------------------------------------------------------------------
 // Batched path: many problems (contexts) advanced in one cooperative launch.
 // Every iteration the blocks of all live problems form one list (live problem
@@ -2143,5 +2190,6 @@ __global__ void k_batch_prep(BatchArgs P, int clear_status) {
     }
     for (int j = threadIdx.x; j < bp.n; j += blockDim.x) c->r2max[bp.t0 + 1 + j] = 0ull;
 }
+#endif  // DOPE_KERNEL_TEMPLATES_ONLY
 
 }  // namespace dope

@@ -165,7 +165,15 @@ __global__ void __launch_bounds__(512) k_ov_solve(OvArgs A, double mu, int t, in
     cut_block<CONN, OvArgs>(A, k, smem, bw, pl, 0ull, c_start, nullptr);
 }
 
-// Eq. 10 for every pixel (one thread per pixel).
+// Tiles whose box holds coordinate c along one axis: [lo, hi] (at most two).
+__device__ __forceinline__ void ov_tiles(int c, int gr, int tb, int nb, int& lo, int& hi) {
+    lo = max(0, floordiv(c - gr, tb));
+    hi = min(nb - 1, floordiv(c + gr, tb));
+}
+
+// Eq. 10 for every pixel (one thread per pixel).  A_j runs over the blocks
+// holding j in increasing block order; the integer G_j over the blocks holding
+// j (first term) and, per neighbour i, over the blocks holding i (second term).
 template <int CONN>
 __global__ void k_ov_y(OvArgs A, double mu) {
     if (*(volatile int*)&A.ctrl->conv_t) return;
@@ -177,34 +185,59 @@ __global__ void k_ov_y(OvArgs A, double mu) {
         const int y = (int)((j / A.W) % A.H);
         const int z = (int)(j / ((long long)A.W * A.H));
         const int qj = A.q[j];
-        const int kz0 = max(0, floordiv(z - 1 - A.gd, A.tbd)), kz1 = min(A.nbz - 1, floordiv(z + 1 + A.gd, A.tbd));
-        const int ky0 = max(0, floordiv(y - 1 - A.gh, A.tbh)), ky1 = min(A.nby - 1, floordiv(y + 1 + A.gh, A.tbh));
-        const int kx0 = max(0, floordiv(x - 1 - A.gw, A.tbw)), kx1 = min(A.nbx - 1, floordiv(x + 1 + A.gw, A.tbw));
+        int kz0, kz1, ky0, ky1, kx0, kx1;
+        ov_tiles(z, A.gd, A.tbd, A.nbz, kz0, kz1);
+        ov_tiles(y, A.gh, A.tbh, A.nby, ky0, ky1);
+        ov_tiles(x, A.gw, A.tbw, A.nbx, kx0, kx1);
         double Asum = 0.0;
         long long G = 0;
+        // blocks holding j: A_j and the first term
         for (int kz = kz0; kz <= kz1; ++kz)
             for (int ky = ky0; ky <= ky1; ++ky)
                 for (int kx = kx0; kx <= kx1; ++kx) {
                     const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
                     const int lj = ov_local(A, kz, ky, kx, z, y, x);
-                    const int yj = lj >= 0 ? A.yhat[kb + lj] : 0;
-                    if (lj >= 0) Asum = __dadd_rn(Asum, __dadd_rn((double)yj, A.a[kb + lj]));
-#pragma unroll
+                    const int yj = A.yhat[kb + lj];
+                    Asum = __dadd_rn(Asum, __dadd_rn((double)yj, A.a[kb + lj]));
+                    if (!yj) continue;
+#pragma unroll 4
                     for (int d = 0; d < CONN; ++d) {
                         int dz, dy, dx;
                         dir_off<CONN>(d, dz, dy, dx);
                         const int iz = z + dz, iy = y + dy, ix = x + dx;
                         if (iz < 0 || iz >= A.D || iy < 0 || iy >= A.H || ix < 0 || ix >= A.W) continue;
                         const long long i = ((long long)iz * A.H + iy) * A.W + ix;
-                        const int li = ov_local(A, kz, ky, kx, iz, iy, ix);
-                        const bool yi = li >= 0 && A.yhat[kb + li];
-                        if (!(lj >= 0 && yj) && !yi) continue;
                         const long long w = (d < nh) ? A.Wl[(long long)d * A.N + j] : A.Wl[(long long)(d - nh) * A.N + i];
+                        if (!w) continue;
                         const int qi = A.q[i];
-                        if (lj >= 0 && yj) G += w * ((long long)A.M * (qi - (li >= 0)) / (qi * qj));
-                        if (yi) G -= w * ((long long)A.M * (qj - (lj >= 0)) / (qj * qi));
+                        const int li = ov_local(A, kz, ky, kx, iz, iy, ix);
+                        G += w * ((long long)A.M * (qi - (li >= 0)) / (qi * qj));
                     }
                 }
+        // second term: per neighbour i, the blocks holding i whose label of i is 1
+#pragma unroll 4
+        for (int d = 0; d < CONN; ++d) {
+            int dz, dy, dx;
+            dir_off<CONN>(d, dz, dy, dx);
+            const int iz = z + dz, iy = y + dy, ix = x + dx;
+            if (iz < 0 || iz >= A.D || iy < 0 || iy >= A.H || ix < 0 || ix >= A.W) continue;
+            const long long i = ((long long)iz * A.H + iy) * A.W + ix;
+            const long long w = (d < nh) ? A.Wl[(long long)d * A.N + j] : A.Wl[(long long)(d - nh) * A.N + i];
+            if (!w) continue;
+            const int qi = A.q[i];
+            int iz0, iz1, iy0, iy1, ix0, ix1;
+            ov_tiles(iz, A.gd, A.tbd, A.nbz, iz0, iz1);
+            ov_tiles(iy, A.gh, A.tbh, A.nby, iy0, iy1);
+            ov_tiles(ix, A.gw, A.tbw, A.nbx, ix0, ix1);
+            for (int kz = iz0; kz <= iz1; ++kz)
+                for (int ky = iy0; ky <= iy1; ++ky)
+                    for (int kx = ix0; kx <= ix1; ++kx) {
+                        const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
+                        if (!A.yhat[kb + ov_local(A, kz, ky, kx, iz, iy, ix)]) continue;
+                        const int lj = ov_local(A, kz, ky, kx, z, y, x);
+                        G -= w * ((long long)A.M * (qj - (lj >= 0)) / (qj * qi));
+                    }
+        }
         const double yv = __ddiv_rn(Asum, (double)qj);
         const double gq = __dmul_rn((double)G, inv);
         const double tq = __ddiv_rn(__ddiv_rn(gq, mu), (double)qj);
@@ -247,6 +280,7 @@ __global__ void __launch_bounds__(256) k_ov_a(OvArgs A, int t) {
     }
 }
 
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
 // Proposition 1 output: label 1 iff the block copies vote 1 by a strict majority.
 __global__ void k_ov_labels(OvArgs A, uint8_t* labels) {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.N;
@@ -267,13 +301,20 @@ __global__ void k_ov_labels(OvArgs A, uint8_t* labels) {
         labels[j] = (uint8_t)(2 * votes > (int)A.q[j]);
     }
 }
+#endif
 
-// Rejects n-links whose scaled capacity M Wl would not stay below 2^24.
-__global__ void k_ov_wcheck(const int32_t* Wl, long long n, int M, Ctrl* c) {
+#ifndef DOPE_KERNEL_TEMPLATES_ONLY
+// Rejects n-links whose scaled capacity would break the block cut's int32
+// bound: M |Wl| * max(1, conn / 8) must stay below 2^24 (so a node's n-link
+// sum stays below 2^27, as for the 3x3 kernels).
+__global__ void k_ov_wcheck(const int32_t* Wl, long long n, long long scale, Ctrl* c) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        if ((long long)Wl[i] * M >= 16777216LL) set_status(c, 4 /* DOPE_EOVERFLOW */);
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long w = Wl[i] < 0 ? -(long long)Wl[i] : (long long)Wl[i];
+        if (w * scale >= 16777216LL) set_status(c, 4 /* DOPE_EOVERFLOW */);
+    }
 }
+#endif
 
 // E_int of image-order labels on image-order U / Wl (Eq. 1, each edge once).
 template <int CONN>
@@ -292,7 +333,7 @@ __global__ void k_energy_img(int D, int H, int W, const int32_t* __restrict__ U,
             int dz, dy, dx;
             dir_off<CONN>(d, dz, dy, dx);
             const int nz = z + dz, ny = y + dy, nx = x + dx;
-            if (nz >= D || ny >= H || nx < 0 || nx >= W) continue;
+            if (nz < 0 || nz >= D || ny < 0 || ny >= H || nx < 0 || nx >= W) continue;
             const long long j = ((long long)nz * H + ny) * W + nx;
             if (yi != lab[j]) acc += Wl[(long long)d * N + i];
         }

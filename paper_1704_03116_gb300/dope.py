@@ -487,7 +487,9 @@ class Dope:
             for i, g in enumerate(grow):
                 p.grow[i] = int(g)
         self.grid = tuple(int(g) for g in grid)
-        self.overlap = grow is not None and any(int(g) for g in grow)
+        # overlap-path contexts (overlapping partitions, larger kernels) keep
+        # their multipliers per block copy
+        self.overlap = (grow is not None and any(int(g) for g in grow)) or int(connectivity) not in (4, 8, 6)
         self.ctx = dope_create(grid, connectivity, block_shape, lam, p)
         self.n, self.nblocks, self.block_volume, self.face_size = _geom(self.ctx)
 
