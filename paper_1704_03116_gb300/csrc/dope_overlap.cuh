@@ -66,6 +66,12 @@ __device__ __forceinline__ int ov_local(const OvArgs& A, int kz, int ky, int kx,
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// num * M / (qa * qb) for the powers of two q in {1, 2, 4, 8} and M = qmax^2
+// (qa * qb divides M, so the shift is exact).
+__device__ __forceinline__ int ov_frac(int num, int M, int qa, int qb) {
+    return (num * M) >> ((__ffs(qa) - 1) + (__ffs(qb) - 1));
+}
+
 // Step a4 + a5 for one block of the overlapping partition: box graph in shared
 // memory (same layout as solve_block), then the exact canonical cut.
 template <int CONN>
@@ -120,7 +126,7 @@ __global__ void __launch_bounds__(512) k_ov_solve(OvArgs A, double mu, int t, in
             const long long j = ((long long)nz * A.H + ny) * A.W + nx;
             const int w = (d < nh) ? A.Wl[(long long)d * A.N + i] : A.Wl[(long long)(d - nh) * A.N + j];
             const int qj = A.q[j];
-            if (d < nh && in_box) res[d * B + v] = w * (A.M / (qi * qj));
+            if (d < nh && in_box) res[d * B + v] = w * ov_frac(1, A.M, qi, qj);
             double phi = 1.0;
             if (in_box) {
                 if (qj == 1) continue;
@@ -211,7 +217,7 @@ __global__ void k_ov_y(OvArgs A, double mu) {
                         if (!w) continue;
                         const int qi = A.q[i];
                         const int li = ov_local(A, kz, ky, kx, iz, iy, ix);
-                        G += w * ((long long)A.M * (qi - (li >= 0)) / (qi * qj));
+                        G += w * ov_frac(qi - (li >= 0), A.M, qi, qj);
                     }
                 }
         // second term: per neighbour i, the blocks holding i whose label of i is 1
@@ -235,7 +241,7 @@ __global__ void k_ov_y(OvArgs A, double mu) {
                         const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
                         if (!A.yhat[kb + ov_local(A, kz, ky, kx, iz, iy, ix)]) continue;
                         const int lj = ov_local(A, kz, ky, kx, z, y, x);
-                        G -= w * ((long long)A.M * (qj - (lj >= 0)) / (qj * qi));
+                        G -= w * ov_frac(qj - (lj >= 0), A.M, qj, qi);
                     }
         }
         const double yv = __ddiv_rn(Asum, (double)qj);
