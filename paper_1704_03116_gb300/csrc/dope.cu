@@ -62,6 +62,7 @@ struct dope_ctx {
     int ov_threads = 0, ov_smem = 0;
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
+    Ctrl* hctrl = nullptr;      // pinned host copy of the whole control block (dope_solve's single read)
     // staging (lazily allocated)
     void* stage = nullptr;
     size_t stage_bytes = 0;
@@ -258,8 +259,9 @@ int ov_run(dope_ctx* c, int n, cudaStream_t st);
 int ov_reset_async(dope_ctx* c, cudaStream_t st);
 int ov_finish(dope_ctx* c, uint8_t* labels_dev, int64_t* energy, cudaStream_t st);
 
-// Up to n iterations in one cooperative launch of k_admm_persistent.
-int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
+// Issue up to n iterations as one cooperative launch (k_admm_resident when
+// every block has its own co-resident CTA, else k_admm_persistent).
+int persistent_issue(dope_ctx* c, int n, cudaStream_t st) {
     const int t0 = c->t;
     PersistArgs P;
     P.s = solve_args(c);
@@ -294,12 +296,15 @@ int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
     if (e != cudaSuccess) return DOPE_ECUDA;
     c->launches++;
     if (c->profiling) CK(cudaEventRecord(c->ev[1], st));
-    Ctrl h{};
-    int rc = read_ctrl(c, &h, st);
-    if (rc) return rc;
+    return DOPE_OK;
+}
+
+// Fold a finished persistent launch (control header h, and the per-iteration
+// r2 trace when the caller copied it) into the context state and statistics.
+int persistent_collect(dope_ctx* c, int t0, const Ctrl& h, const unsigned long long* r2trace, cudaStream_t st) {
     if (h.status) return h.status;
     const int done = h.iters_done - t0;
-    int converged = h.conv_t != 0;
+    const int converged = h.conv_t != 0;
     if (c->profiling) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
@@ -319,11 +324,26 @@ int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
     c->stats.window_iterations = h.window_iters;
     c->stats.solver_kernel = c->resident ? 2 : 1;
     double r2 = 0.0;
-    rc = read_r2max(c, c->t, &r2, st);
-    if (rc) return rc;
+    if (r2trace) {
+        memcpy(&r2, &r2trace[c->t], sizeof(r2));
+    } else {
+        int rc = read_r2max(c, c->t, &r2, st);
+        if (rc) return rc;
+    }
     c->stats.rmax_last = std::sqrt(r2);
     c->stats.kernel_launches = c->launches;
     return DOPE_OK;
+}
+
+// Up to n iterations in one cooperative launch of k_admm_persistent.
+int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
+    const int t0 = c->t;
+    int rc = persistent_issue(c, n, st);
+    if (rc) return rc;
+    Ctrl h{};
+    rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    return persistent_collect(c, t0, h, nullptr, st);
 }
 
 // Up to n iterations of Algorithm 1 from the current state.
@@ -1111,6 +1131,7 @@ void dope_destroy(dope_ctx* c) {
     dfree(al, c->oa.a);
     dfree(al, c->oa.yhat);
     if (c->own_tab) dope_tables_destroy(c->own_tab);
+    if (c->hctrl) cudaFreeHost(c->hctrl);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
 }
@@ -1226,6 +1247,47 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
     const int threads = 256;
     k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads, 0, st>>>(c->g, c->yF, c->aF);
     CK(cudaGetLastError());
+    if (!c->nsm && c->p.launch_mode != 1 && c->persist_grid > 0 && c->p.max_iter > 0) {
+        // one persistent launch, then the energy, the labels and one read of the
+        // whole control block: a single synchronisation for the solve
+        if (!c->hctrl && cudaMallocHost(&c->hctrl, c->ctrl_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->hctrl = nullptr;
+            return DOPE_ENOMEM;
+        }
+        const int n = c->p.max_iter;
+        memset(&c->stats, 0, sizeof(c->stats));
+        int rc = clear_status(c, st);
+        if (rc) return rc;
+        CK(cudaMemsetAsync(&c->ctrl->r2max[1], 0, sizeof(unsigned long long) * (size_t)n, st));
+        rc = persistent_issue(c, n, st);
+        if (rc) return rc;
+        if (energy_int) {
+            c->launches++;
+            const int eb = grid_for(c->g.N, threads);
+            if (c->conn == 4) k_energy<4><<<eb, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
+            else if (c->conn == 8) k_energy<8><<<eb, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
+            else k_energy<6><<<eb, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
+        }
+        uint8_t* dst = labels;
+        if (where == DOPE_HOST) {
+            rc = ensure_stage(c, (size_t)c->g.Nu, 1);
+            if (rc) return rc;
+            dst = (uint8_t*)c->stage2;
+        }
+        k_unpermute_u8<<<grid_for(c->g.Nu, threads), threads, 0, st>>>(c->g, c->yhat, dst);
+        c->launches++;
+        CK(cudaGetLastError());
+        if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(c->hctrl, c->ctrl, c->ctrl_bytes, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        rc = persistent_collect(c, 0, *c->hctrl, c->hctrl->r2max, st);
+        if (rc) return rc;
+        if (energy_int) *energy_int = (int64_t)c->hctrl->energy;
+        c->stats.kernel_launches = c->launches;
+        if (iterations) *iterations = c->t;
+        return c->stats.converged ? DOPE_OK : DOPE_ENOTCONV;
+    }
     int rc = run_iterations(c, c->p.max_iter, st);
     if (rc) return rc;
     if (energy_int) {
