@@ -261,9 +261,11 @@ int ov_finish(dope_ctx* c, uint8_t* labels_dev, int64_t* energy, cudaStream_t st
 
 // Issue up to n iterations as one cooperative launch (k_admm_resident when
 // every block has its own co-resident CTA, else k_admm_persistent).
-int persistent_issue(dope_ctx* c, int n, cudaStream_t st) {
+int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = nullptr, int out_energy = 0) {
     const int t0 = c->t;
     PersistArgs P;
+    P.out_labels = out_labels;
+    P.out_energy = out_energy;
     P.s = solve_args(c);
     P.u = update_args(c);
     P.t0 = t0;
@@ -1245,11 +1247,10 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
     c->mu = c->p.mu0;
     c->launches = 1;
     const int threads = 256;
-    k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads, 0, st>>>(c->g, c->yF, c->aF);
-    CK(cudaGetLastError());
     if (!c->nsm && c->p.launch_mode != 1 && c->persist_grid > 0 && c->p.max_iter > 0) {
-        // one persistent launch, then the energy, the labels and one read of the
-        // whole control block: a single synchronisation for the solve
+        // one persistent launch that also starts from y = 1/2, a = 0 and
+        // finishes with the labels and their energy, then one read of the whole
+        // control block: a single launch and a single synchronisation per solve
         if (!c->hctrl && cudaMallocHost(&c->hctrl, c->ctrl_bytes) != cudaSuccess) {
             cudaGetLastError();
             c->hctrl = nullptr;
@@ -1260,24 +1261,15 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
         int rc = clear_status(c, st);
         if (rc) return rc;
         CK(cudaMemsetAsync(&c->ctrl->r2max[1], 0, sizeof(unsigned long long) * (size_t)n, st));
-        rc = persistent_issue(c, n, st);
-        if (rc) return rc;
-        if (energy_int) {
-            c->launches++;
-            const int eb = grid_for(c->g.N, threads);
-            if (c->conn == 4) k_energy<4><<<eb, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
-            else if (c->conn == 8) k_energy<8><<<eb, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
-            else k_energy<6><<<eb, threads, 0, st>>>(c->g, c->U, c->Wl, c->yhat, c->ctrl);
-        }
         uint8_t* dst = labels;
         if (where == DOPE_HOST) {
             rc = ensure_stage(c, (size_t)c->g.Nu, 1);
             if (rc) return rc;
             dst = (uint8_t*)c->stage2;
         }
-        k_unpermute_u8<<<grid_for(c->g.Nu, threads), threads, 0, st>>>(c->g, c->yhat, dst);
-        c->launches++;
-        CK(cudaGetLastError());
+        c->launches = 0;
+        rc = persistent_issue(c, n, st, dst, energy_int ? 1 : 0);
+        if (rc) return rc;
         if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(c->hctrl, c->ctrl, c->ctrl_bytes, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1288,6 +1280,8 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
         if (iterations) *iterations = c->t;
         return c->stats.converged ? DOPE_OK : DOPE_ENOTCONV;
     }
+    k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads, 0, st>>>(c->g, c->yF, c->aF);
+    CK(cudaGetLastError());
     int rc = run_iterations(c, c->p.max_iter, st);
     if (rc) return rc;
     if (energy_int) {

@@ -865,7 +865,7 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k) 
             for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
             const long long s = (long long)k * g.F + f;
             const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
-            const double aa = __ldcg(&A.aF[s]);
+            const double aa = t == 1 ? 0.0 : __ldcg(&A.aF[s]);   // a = 0 before iteration 1
             // G = 0: (G/1024)/mu = +0 and x - (+0) = x exactly, so the division is skipped
             const double ya = __dadd_rn((double)yh, aa);
             const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
@@ -1136,7 +1136,61 @@ struct PersistArgs {
     int NH;                 // halo pixels of a block (distinct cross-block neighbours)
     const int16_t* hslot;   // [CONN][F] halo pixel of (direction, face slot), -1 if none
     const int* hinfo;       // [NH] halo_entry of each halo pixel
+    uint8_t* out_labels;    // finish (a8) in the launch: labels in the caller's image order (or null)
+    int out_energy;         // finish (a8) in the launch: E_int of the labels into ctrl->energy
 };
+
+// Step a8 for block k at the end of a persistent launch (after a grid
+// barrier, so every block's final labels are in yhat): the block's labels in
+// the caller's image order, and the block's share of E_int (its unaries and
+// the edges leaving its pixels forward, each undirected edge once) added to
+// ctrl->energy.  Every thread of the CTA calls it.
+template <int CONN>
+__device__ void finish_block(const PersistArgs& P, int k, long long* red) {
+    const Geo& g = P.s.g;
+    constexpr int nh = CONN / 2;
+    const int B = g.B;
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    long long acc = 0;
+    for (int v = threadIdx.x; v < B; v += blockDim.x) {
+        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+        const long long gi = (long long)k * B + v;
+        const int yi = __ldcg(&P.s.yhat[gi]);
+        if (P.out_labels) {
+            const int z = kz * g.bd + lz, y = ky * g.bh + ly, x = kx * g.bw + lx;
+            if (z < g.Du && y < g.Hu && x < g.Wu) P.out_labels[((long long)z * g.Hu + y) * g.Wu + x] = (uint8_t)yi;
+        }
+        if (P.out_energy) {
+            acc += (long long)P.s.U[gi] * yi;
+#pragma unroll
+            for (int d = 0; d < nh; ++d) {
+                int dz, dy, dx;
+                dir_off<CONN>(d, dz, dy, dx);
+                const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+                long long gj;
+                if (nlz < g.bd && nly < g.bh && nlx >= 0 && nlx < g.bw) {
+                    gj = gi + (dz * g.bh + dy) * g.bw + dx;
+                } else {
+                    int kn, ln;
+                    if (!cross_nbr<CONN>(g, kz, ky, kx, lz, ly, lx, d, kn, ln)) continue;
+                    gj = (long long)kn * B + ln;
+                }
+                if (yi != __ldcg(&P.s.yhat[gj])) acc += P.s.Wl[(long long)d * g.N + gi];
+            }
+        }
+    }
+    if (!P.out_energy) return;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        if (t) atomicAdd(&P.s.ctrl->energy, (unsigned long long)t);
+    }
+    __syncthreads();
+}
 
 // Next block for this CTA: static stride, or the phase's atomic counter.
 __device__ __forceinline__ int next_block(int dynamic, unsigned* counter, int k_prev, int* s_k) {
@@ -1226,10 +1280,12 @@ template <int CONN, int NT>
 __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persistent(PersistArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_k;
+    __shared__ long long s_red[32];
     Ctrl* c = P.s.ctrl;
     const int K = P.s.g.K;
     double mu = P.mu_start;
     int t = P.t0, conv = 0;
+    bool failed = false;
     unsigned nbar = 0;
     for (int j = 0; j < P.n; ++j) {
         t = P.t0 + j + 1;
@@ -1242,14 +1298,14 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
              k = next_block(P.dynamic, &c->work[0], k, &s_k))
             solve_block<CONN>(P.s, it, k, smem);
         const long long c1 = clock64();
-        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
         const long long c2 = clock64();
         if (blockIdx.x == 0 && threadIdx.x == 0) c->work[0] = 0u;
         for (int k = next_block(P.dynamic, &c->work[1], -1, &s_k); k < K;
              k = next_block(P.dynamic, &c->work[1], k, &s_k))
             update_block<CONN>(P.u, mu, t, k);
         const long long c3 = clock64();
-        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) break;
+        if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
         if (threadIdx.x == 0) {
             const long long c4 = clock64();
             atomicAdd(&c->pcyc[0], (unsigned long long)(c1 - c0));
@@ -1265,6 +1321,10 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
         c->iters_done = t;
         c->conv_t = conv ? t : 0;
     }
+    // every exit above follows the last iteration's second barrier, and its
+    // labels were written before the first: the finish can read them all
+    if (!failed && (P.out_labels || P.out_energy))
+        for (int k = blockIdx.x; k < K; k += gridDim.x) finish_block<CONN>(P, k, s_red);
 }
 
 // ---------------------------------------------------------------------------
@@ -1488,8 +1548,9 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         lab[v] = P.t0 == 0 ? 0 : __ldcg(&P.s.yhat[gi]);
     }
     for (int f = tid; f < F; f += NT) {
-        yS[f] = __ldcg(&P.s.yF[(long long)k * F + f]);
-        aS[f] = __ldcg(&P.s.aF[(long long)k * F + f]);
+        // Algorithm 1 starts from y = 1/2, a = 0
+        yS[f] = P.t0 == 0 ? 0.5 : __ldcg(&P.s.yF[(long long)k * F + f]);
+        aS[f] = P.t0 == 0 ? 0.0 : __ldcg(&P.s.aF[(long long)k * F + f]);
         fl[f] = P.s.faceLocal[f];
     }
     if (P.window) {
@@ -1949,6 +2010,10 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->iters_done = t;
         c->conv_t = conv ? t : 0;
+    }
+    if (!failed && (P.out_labels || P.out_energy)) {
+        __shared__ long long s_red[32];
+        if (grid_sync(c, gridDim.x, nbar, P.spin_limit)) finish_block<CONN>(P, k, s_red);
     }
 }
 
