@@ -131,15 +131,18 @@ def contrast_weights(image, dims, conn, sigma=None, inv_dist=False):
 
 def sigma_fp32_path(image, dims, conn):
     """The default sigma as the FP32 path forms it: per pair
-    d2 = (((x0-y0)^2 + (x1-y1)^2) + ...) in FP32 and sqrt(d2) in FP32, summed
-    in FP64 and divided by the number of pairs; floored at 1e-6."""
+    d2 = (((x0-y0)^2 + (x1-y1)^2) + ...) in FP32 and sqrt(d2) in FP32; per
+    pixel the sum of its pairs' roots in FP32, in offset order; the pixels'
+    sums added in FP64 and divided by the number of pairs; floored at 1e-6."""
     vol = _as_volume(np.asarray(image, np.float32), dims)
-    tot, cnt = 0.0, 0
+    per_pixel = np.zeros(vol.shape[:3], np.float32)
+    cnt = 0
     for off in _OFFS[conn]:
         valid, nb = _pairs(vol, off)
-        d2 = _d2_fp32(vol, nb)
-        tot += float(np.sqrt(d2)[valid].astype(np.float64).sum())
+        r = np.where(valid, np.sqrt(_d2_fp32(vol, nb)), np.float32(0.0)).astype(np.float32)
+        per_pixel = (per_pixel + r).astype(np.float32)
         cnt += int(valid.sum())
+    tot = float(per_pixel.astype(np.float64).sum())
     return max(tot / cnt, 1e-6) if cnt else 1e-6
 
 

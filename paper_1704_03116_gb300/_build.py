@@ -1,9 +1,10 @@
 """Build of the CUDA library libdope.so (sm_103a), in-tree.
 
-Three translation units, compiled in parallel by nvcc for sm_103a only and
+Four translation units, compiled in parallel by nvcc for sm_103a only and
 linked into one shared library: csrc/dope.cu (kernels in csrc/*.cuh, the
-solver C-ABI), csrc/dope_big.cu (the larger-kernel instantiations) and
-csrc/dope_server.cu (the request server, host code).  It links the CUDA runtime statically and has no PyTorch
+solver C-ABI), csrc/dope_big.cu (the larger-kernel instantiations),
+csrc/dope_server.cu (the request server, host code) and
+csrc/dope_potentials.cu (the whole-image potentials).  It links the CUDA runtime statically and has no PyTorch
 dependency (the C-ABI takes plain pointers).
 """
 import os
@@ -13,9 +14,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "dope.cu"), os.path.join(HERE, "csrc", "dope_big.cu"),
-       os.path.join(HERE, "csrc", "dope_server.cu")]
+       os.path.join(HERE, "csrc", "dope_server.cu"), os.path.join(HERE, "csrc", "dope_potentials.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("dope_kernels.cuh", "dope_internal.h", "dope_overlap.cuh",
-                                                       "dope_nsm.cuh", "dope_big.h")] + [os.path.join(ROOT, "include", "dope.h")]
+                                                       "dope_nsm.cuh", "dope_big.h")] + \
+    [os.path.join(ROOT, "include", h) for h in ("dope.h", "dope_potentials.h")]
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdope.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

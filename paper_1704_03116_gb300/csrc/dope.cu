@@ -1150,6 +1150,14 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
     return DOPE_OK;
 }
 
+// Quantise device unaries (user order) into the context (stream-ordered).
+int issue_set_unaries(dope_ctx* c, const float* src, cudaStream_t st) {
+    const int threads = 256;
+    k_set_unaries<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, src, c->U, c->ctrl);
+    CK(cudaGetLastError());
+    return DOPE_OK;
+}
+
 int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* stream) {
     if (!c || !u || n != c->g.Nu || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
@@ -1162,14 +1170,32 @@ int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* st
     }
     int rc = clear_status(c, st);
     if (rc) return rc;
-    const int threads = 256;
-    k_set_unaries<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, src, c->U, c->ctrl);
-    CK(cudaGetLastError());
+    rc = issue_set_unaries(c, src, st);
+    if (rc) return rc;
     Ctrl h{};
     rc = read_ctrl(c, &h, st);
     if (rc) return rc;
     c->have_u = (h.status == 0);
     return h.status;
+}
+
+// Quantise device weights (user order, [conn/2][Nu]) into the context.
+int issue_set_weights(dope_ctx* c, const int32_t* src, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = grid_for(c->g.N, threads);
+    if (c->ov) {
+        const int nh = c->conn / 2;
+        if (!ov_dispatch(c->conn, [&](auto cc) {
+                k_set_weights<decltype(cc)::value><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, 0);
+            }))
+            big_set_weights(c->conn, c->g, src, c->Wl, c->lambda, c->ctrl, blocks, threads, st);
+        const long long scale = (long long)c->oa.M * (c->conn > 8 ? c->conn / 8 : 1);
+        k_ov_wcheck<<<grid_for(c->g.N * nh, threads), threads, 0, st>>>(c->Wl, c->g.N * nh, scale, c->ctrl);
+    } else if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
+    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
+    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
+    CK(cudaGetLastError());
+    return DOPE_OK;
 }
 
 int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void* stream) {
@@ -1185,23 +1211,53 @@ int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void*
     }
     int rc = clear_status(c, st);
     if (rc) return rc;
-    const int threads = 256;
-    const int blocks = grid_for(c->g.N, threads);
-    if (c->ov) {
-        if (!ov_dispatch(c->conn, [&](auto cc) {
-                k_set_weights<decltype(cc)::value><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, 0);
-            }))
-            big_set_weights(c->conn, c->g, src, c->Wl, c->lambda, c->ctrl, blocks, threads, st);
-        const long long scale = (long long)c->oa.M * (c->conn > 8 ? c->conn / 8 : 1);
-        k_ov_wcheck<<<grid_for(c->g.N * nh, threads), threads, 0, st>>>(c->Wl, c->g.N * nh, scale, c->ctrl);
-    } else if (c->conn == 4) k_set_weights<4><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
-    else if (c->conn == 8) k_set_weights<8><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
-    else k_set_weights<6><<<blocks, threads, 0, st>>>(c->g, src, c->Wl, c->lambda, c->ctrl, c->nsm);
-    CK(cudaGetLastError());
+    rc = issue_set_weights(c, src, st);
+    if (rc) return rc;
     Ctrl h{};
     rc = read_ctrl(c, &h, st);
     if (rc) return rc;
     c->have_w = (h.status == 0);
+    return h.status;
+}
+
+int dope_set_image(dope_ctx* c, const float* image, int channels, const dope_gmm* fg, const dope_gmm* bg,
+                   double clip, double sigma, int inv_dist, int where, double* sigma_used, void* stream) {
+    if (!c || !image || channels < 1 || channels > DOPE_GMM_MAX_CH || (where != DOPE_HOST && where != DOPE_DEVICE))
+        return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    const size_t n = (size_t)c->g.Nu;
+    const int nh = c->conn / 2;
+    // scratch: [sigma workspace 64 B][u: n floats][wq: nh * n int32][image if on the host]
+    const size_t off_u = 64, off_w = off_u + ((sizeof(float) * n + 255) & ~(size_t)255);
+    const size_t off_i = off_w + ((sizeof(int32_t) * n * nh + 255) & ~(size_t)255);
+    const size_t bytes = off_i + (where == DOPE_HOST ? sizeof(float) * n * channels : 0);
+    int rc = ensure_stage(c, bytes, 0);
+    if (rc) return rc;
+    char* base = (char*)c->stage;
+    double* ws = (double*)base;
+    float* u = (float*)(base + off_u);
+    int32_t* wq = (int32_t*)(base + off_w);
+    const float* img = image;
+    if (where == DOPE_HOST) {
+        CK(cudaMemcpyAsync(base + off_i, image, sizeof(float) * n * channels, cudaMemcpyHostToDevice, st));
+        img = (const float*)(base + off_i);
+    }
+    rc = pot_unaries_issue(img, (long long)n, channels, fg, bg, clip, u, st);
+    if (rc) return rc;
+    const int64_t dims[3] = {c->g.Du, c->g.Hu, c->g.Wu};
+    rc = pot_weights_issue(img, dims, c->ndim, channels, c->conn, sigma, inv_dist, wq, ws, st);
+    if (rc) return rc;
+    rc = clear_status(c, st);
+    if (!rc) rc = issue_set_unaries(c, u, st);
+    if (!rc) rc = issue_set_weights(c, wq, st);
+    if (rc) return rc;
+    double sig = sigma;
+    if (!(sigma > 0.0)) CK(cudaMemcpyAsync(&sig, ws + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    Ctrl h{};
+    rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    if (sigma_used) *sigma_used = sig;
+    c->have_u = c->have_w = (h.status == 0);
     return h.status;
 }
 

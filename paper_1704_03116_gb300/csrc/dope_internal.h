@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "dope.h"
+#include "dope_potentials.h"
 
 // Source of device memory for a context.  alloc returns 256-byte aligned
 // device memory or null; release gives it back.  A null alloc means
@@ -89,3 +90,14 @@ int dope_batch_collect(dope_ctx* const* cs, int n, dope_batch_ws* w, int* t, int
 // The single-problem path (what dope_solve runs) from the context's current
 // state to its stop test or max_iter; synchronises `st`.
 int dope_run_single(dope_ctx* c, cudaStream_t st, int* t, int* conv);
+
+// Whole-image potentials (dope_potentials.cu), stream-ordered, no
+// synchronisation.  pot_unaries_issue: u[i] of n pixels of a [n][C] image.
+// pot_weights_issue: wq [conn/2][N] of a (D, H, W) grid (D = 1 for ndim 2);
+// ws = 2 doubles of device scratch (sum of contrasts, sigma used), needed
+// only when sigma <= 0.  Both validate their arguments (DOPE_EINVAL) before
+// any GPU work.
+int pot_unaries_issue(const float* img, long long n, int C, const dope_gmm* fg, const dope_gmm* bg, double clip,
+                      float* u, cudaStream_t st);
+int pot_weights_issue(const float* img, const int64_t dims[3], int ndim, int C, int conn, double sigma,
+                      int inv_dist, int32_t* wq, double* ws, cudaStream_t st);

@@ -21,6 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdope.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "dope.h")
+HEADERS = [HEADER, os.path.join(os.path.dirname(_HERE), "include", "dope_potentials.h")]
 
 DOPE_OK, DOPE_EINVAL, DOPE_EUNSUPPORTED, DOPE_ENOMEM = 0, 1, 2, 3
 DOPE_EOVERFLOW, DOPE_ENOTCONV, DOPE_ETIMEOUT, DOPE_ECUDA = 4, 5, 6, 7
@@ -93,6 +94,15 @@ class dope_tune_result(ctypes.Structure):
 
 DOPE_BATCH_MAX = 256
 DOPE_TUNE_BLOCK = 1
+DOPE_GMM_MAX_COMP, DOPE_GMM_MAX_CH = 8, 4
+DOPE_CONTRAST_WS_BYTES = 64
+
+
+class dope_gmm(ctypes.Structure):
+    _fields_ = [("n_comp", ctypes.c_int), ("channels", ctypes.c_int),
+                ("weight", ctypes.c_double * DOPE_GMM_MAX_COMP),
+                ("mean", (ctypes.c_double * DOPE_GMM_MAX_CH) * DOPE_GMM_MAX_COMP),
+                ("cov", ((ctypes.c_double * DOPE_GMM_MAX_CH) * DOPE_GMM_MAX_CH) * DOPE_GMM_MAX_COMP)]
 
 
 def _load():
@@ -133,6 +143,10 @@ def _load():
         "dope_autotune": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params), vp, vp, i32,
                                 i32, i32, P(dope_tune_result), i32, P(ctypes.c_int), P(dope_tune_result), vp]),
         "dope_get_block_state": (i32, [vp, vp, vp, i64, P(ctypes.c_int64), vp]),
+        "dope_gmm_unaries": (i32, [vp, i64, i32, P(dope_gmm), P(dope_gmm), dbl, vp, vp]),
+        "dope_contrast_weights": (i32, [vp, P(ctypes.c_int64), i32, i32, i32, dbl, i32, vp, vp,
+                                        P(ctypes.c_double), vp]),
+        "dope_set_image": (i32, [vp, vp, i32, P(dope_gmm), P(dope_gmm), dbl, dbl, i32, i32, P(ctypes.c_double), vp]),
         "dope_destroy": (None, [vp]),
         "dope_strerror": (ctypes.c_char_p, [i32]),
     }
@@ -148,10 +162,13 @@ except OSError as e:  # pragma: no cover - a broken build must fail loudly
     raise ImportError(f"cannot load {LIB_PATH}: {e}") from e
 
 
-def declared_symbols(header=HEADER):
-    """Function names declared in include/dope.h."""
-    txt = open(header).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dope_[a-z_0-9]+)\s*\(", txt, re.M)))
+def declared_symbols(headers=None):
+    """Function names declared in include/dope.h and include/dope_potentials.h."""
+    names = set()
+    for h in headers or HEADERS:
+        txt = open(h).read()
+        names |= set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(dope_[a-z_0-9]+)\s*\(", txt, re.M))
+    return sorted(names)
 
 
 def _check(rc, where):
@@ -471,6 +488,89 @@ def dope_strerror(status):
 # Convenience object over the same calls
 # --------------------------------------------------------------------------
 
+# --------------------------------------------------------------------------
+# Whole-image potentials (include/dope_potentials.h)
+# --------------------------------------------------------------------------
+
+def gmm(weights, means, covs):
+    """A dope_gmm from (weights [K], means [K, C], covs [K, C, C])."""
+    w = np.asarray(weights, np.float64).reshape(-1)
+    m = np.asarray(means, np.float64).reshape(len(w), -1)
+    S = np.asarray(covs, np.float64).reshape(len(w), m.shape[1], m.shape[1])
+    if not 1 <= len(w) <= DOPE_GMM_MAX_COMP or not 1 <= m.shape[1] <= DOPE_GMM_MAX_CH:
+        raise ValueError("1..8 components of 1..4 channels")
+    g = dope_gmm()
+    g.n_comp, g.channels = len(w), m.shape[1]
+    for j in range(len(w)):
+        g.weight[j] = float(w[j])
+        for r in range(m.shape[1]):
+            g.mean[j][r] = float(m[j, r])
+            for c in range(m.shape[1]):
+                g.cov[j][r][c] = float(S[j, r, c])
+    return g
+
+
+def _as_gmm(g):
+    return g if isinstance(g, dope_gmm) else gmm(*g)
+
+
+def _dev_tensor(x, what):
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise TypeError(f"{what} must be a contiguous float32 CUDA tensor")
+    return x
+
+
+def dope_gmm_unaries(image, fg, bg, clip=1.0e5, channels=None, out=None, stream=None):
+    """u = clip(log p_bg(x) - log p_fg(x)) per pixel of a CUDA image [..., C]
+    (pixel-major, channels interleaved); fg / bg: dope_gmm or (weights,
+    means, covs).  Returns the float32 CUDA tensor u [N]."""
+    import torch
+    image = _dev_tensor(image, "image")
+    fg, bg = _as_gmm(fg), _as_gmm(bg)
+    C = fg.channels if channels is None else int(channels)
+    n = image.numel() // C
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=image.device)
+    _dev_tensor(out, "out")
+    _check(_lib.dope_gmm_unaries(ctypes.c_void_p(image.data_ptr()), n, C, ctypes.byref(fg), ctypes.byref(bg),
+                                 float(clip), ctypes.c_void_p(out.data_ptr()), _stream(stream)), "dope_gmm_unaries")
+    return out
+
+
+def dope_contrast_weights(image, grid, connectivity, channels=1, sigma=0.0, inv_dist=False, out=None,
+                          stream=None):
+    """wq [conn/2, N] int32 CUDA tensor of a CUDA image on `grid` ((H, W) or
+    (D, H, W)) and the sigma used (sigma <= 0: the mean contrast)."""
+    import torch
+    image = _dev_tensor(image, "image")
+    grid = tuple(int(g) for g in grid)
+    n = int(np.prod(grid))
+    nh = int(connectivity) // 2
+    if out is None:
+        out = torch.empty((nh, n), dtype=torch.int32, device=image.device)
+    ws = torch.empty(DOPE_CONTRAST_WS_BYTES // 8, dtype=torch.float64, device=image.device)
+    g = (ctypes.c_int64 * len(grid))(*grid)
+    sig = ctypes.c_double(0.0)
+    _check(_lib.dope_contrast_weights(ctypes.c_void_p(image.data_ptr()), g, len(grid), int(channels),
+                                      int(connectivity), float(sigma), int(bool(inv_dist)),
+                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                      ctypes.byref(sig), _stream(stream)), "dope_contrast_weights")
+    return out, sig.value
+
+
+def dope_set_image(ctx, image, fg, bg, clip=1.0e5, sigma=0.0, inv_dist=False, channels=None, stream=None):
+    """Both potentials of an image (CUDA tensor or host array, [..., C])
+    straight into a context; returns the sigma used."""
+    fg, bg = _as_gmm(fg), _as_gmm(bg)
+    C = fg.channels if channels is None else int(channels)
+    p, where, keep = _ptr(image, _t(np.float32))
+    sig = ctypes.c_double(0.0)
+    _check(_lib.dope_set_image(ctx, p, C, ctypes.byref(fg), ctypes.byref(bg), float(clip), float(sigma),
+                               int(bool(inv_dist)), where, ctypes.byref(sig), _stream(stream)), "dope_set_image")
+    return sig.value
+
+
 class Dope:
     """One DOPE context: grid, connectivity, block shape, lambda (Algorithm 1 inputs)."""
 
@@ -506,6 +606,10 @@ class Dope:
 
     def set_weights(self, wq, stream=None):
         dope_set_weights(self.ctx, wq, stream)
+
+    def set_image(self, image, fg, bg, clip=1.0e5, sigma=0.0, inv_dist=False, stream=None):
+        """Unaries and weights computed on the GPU from the image; returns sigma."""
+        return dope_set_image(self.ctx, image, fg, bg, clip, sigma, inv_dist, stream=stream)
 
     def solve(self, labels=None, stream=None, allow_notconv=False):
         """(labels, E = E_int / 1024, iterations)."""

@@ -2,6 +2,8 @@
 and its host-side argument checks work without a GPU."""
 import ctypes
 
+import numpy as np
+
 import pytest
 
 
@@ -82,14 +84,36 @@ def test_no_gpu_server_and_batch(lib):
     assert rc == lib.DOPE_EINVAL
 
 
+def test_potentials_argument_checks(lib):
+    """The potentials calls validate the models and the grid on the host,
+    before any GPU work (n = 0 / null pointers never reach a device)."""
+    L = lib._lib
+    ok = lib.gmm([1.0], [[0.5, 0.5, 0.5]], [np.eye(3) * 0.01])
+    assert L.dope_gmm_unaries(None, 0, 3, ctypes.byref(ok), ctypes.byref(ok), 1e5, None, None) == lib.DOPE_OK
+    bad = lib.gmm([1.0], [[0.5, 0.5, 0.5]], [np.diag([0.01, -0.01, 0.01])])      # not positive definite
+    assert L.dope_gmm_unaries(None, 0, 3, ctypes.byref(ok), ctypes.byref(bad), 1e5, None, None) == lib.DOPE_EINVAL
+    zero_w = lib.gmm([0.0], [[0.5, 0.5, 0.5]], [np.eye(3) * 0.01])
+    assert L.dope_gmm_unaries(None, 0, 3, ctypes.byref(zero_w), ctypes.byref(ok), 1e5, None, None) == lib.DOPE_EINVAL
+    assert L.dope_gmm_unaries(None, 0, 2, ctypes.byref(ok), ctypes.byref(ok), 1e5, None, None) == lib.DOPE_EINVAL
+    assert L.dope_gmm_unaries(None, 0, 3, ctypes.byref(ok), ctypes.byref(ok), 0.0, None, None) == lib.DOPE_EINVAL
+    assert L.dope_gmm_unaries(None, 5, 3, ctypes.byref(ok), ctypes.byref(ok), 1e5, None, None) == lib.DOPE_EINVAL
+    g = (ctypes.c_int64 * 3)(4, 8, 8)
+    for ndim, conn in ((2, 6), (2, 32), (3, 4), (3, 24), (2, 10)):
+        assert L.dope_contrast_weights(None, g, ndim, 3, conn, 1.0, 0, None, None, None, None) == lib.DOPE_EINVAL
+    assert L.dope_contrast_weights(None, g, 2, 5, 4, 1.0, 0, None, None, None, None) == lib.DOPE_EINVAL
+    assert L.dope_set_image(None, None, 3, ctypes.byref(ok), ctypes.byref(ok), 1e5, 0.0, 0, 0, None,
+                            None) == lib.DOPE_EINVAL
+
+
 def test_struct_layouts_match_header(lib):
     """ctypes mirrors of the C structs have the C sizes (compiled probe)."""
     import os
     import subprocess
     import tempfile
-    src = ('#include <stdio.h>\n#include "dope.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+    src = ('#include <stdio.h>\n#include "dope_potentials.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
            'sizeof(dope_params),sizeof(dope_stats),sizeof(dope_profile),sizeof(dope_server_params),'
-           'sizeof(dope_request),sizeof(dope_result),sizeof(dope_server_stats),sizeof(dope_tune_result));'
+           'sizeof(dope_request),sizeof(dope_result),sizeof(dope_server_stats),sizeof(dope_tune_result),'
+           'sizeof(dope_gmm));'
            'return 0;}\n')
     inc = os.path.dirname(lib.HEADER)
     with tempfile.TemporaryDirectory() as td:
@@ -100,5 +124,5 @@ def test_struct_layouts_match_header(lib):
         got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(t) for t in (lib.dope_params, lib.dope_stats, lib.dope_profile, lib.dope_server_params,
                                        lib.dope_request, lib.dope_result, lib.dope_server_stats,
-                                       lib.dope_tune_result)]
+                                       lib.dope_tune_result, lib.dope_gmm)]
     assert got == want
