@@ -314,6 +314,64 @@ def _summ(res, st, t0, reqs, arrivals):
             "failed": sum(1 for i in res if res[i]["status"] != 0), "completed": len(res)}
 
 
+_BASES = {}
+
+
+def _serving_base(b):
+    from paper_1704_03116_gb300 import inputs
+    if b not in _BASES:
+        _BASES[b] = inputs.serving_base(b)
+    return _BASES[b]
+
+
+def potentials_summary(reps=10):
+    """Algorithm 1's first step on the GPU for a 2048 x 2048 RGB image (the
+    serving stream's base image, 3 + 3 component mixtures, 8-connected
+    contrast weights divided by the distance, sigma = mean contrast): device
+    time of the data-term kernel and of the two contrast passes, L2 flushed
+    before each repetition.  Algorithmic bytes per pixel: data term 12 read +
+    4 written; contrast sum 12 read; contrast weights 12 read + 4 per offset
+    written (neighbours' features come from cache)."""
+    import torch
+    from paper_1704_03116_gb300 import dope
+    b = _serving_base(0)
+    H, W = b["image"].shape[:2]
+    n = H * W
+    img = torch.from_numpy(np.ascontiguousarray(b["image"].reshape(-1, 3))).cuda()
+    u = torch.empty(n, dtype=torch.float32, device="cuda")
+    wq = torch.empty((4, n), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        dope.dope_gmm_unaries(img, b["gmm_fg"], b["gmm_bg"], out=u)
+        dope.dope_contrast_weights(img, (H, W), 8, channels=3, inv_dist=True, out=wq)
+    tu, tw = [], []
+    fg, bg = dope.gmm(*b["gmm_fg"]), dope.gmm(*b["gmm_bg"])
+    for r in range(reps):
+        flush.fill_(r & 0xFF)
+        # keep the GPU busy while the host queues the timed launches, so the
+        # events see device time only (no host marshalling in between)
+        torch.cuda._sleep(2_000_000)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        dope.dope_gmm_unaries(img, fg, bg, out=u)
+        e[1].record(stream)
+        dope.dope_contrast_weights(img, (H, W), 8, channels=3, inv_dist=True, out=wq, read_sigma=False)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        tu.append(e[0].elapsed_time(e[1]))
+        tw.append(e[1].elapsed_time(e[2]))
+    hbm, kind = peaks()
+    bu, bw = 16 * n, (12 + 12 + 16) * n
+    mu, mw = statistics.median(tu), statistics.median(tw)
+    return {"workload": f"{H}x{W} RGB, 3+3 component mixtures, 8-conn contrast / distance, sigma = mean contrast",
+            "unaries_us": 1e3 * mu, "weights_us": 1e3 * mw,
+            "unaries_gbs": bu / (mu / 1e3) / 1e9, "weights_gbs": bw / (mw / 1e3) / 1e9,
+            "frac": (bu + bw) / ((mu + mw) / 1e3) / 1e9 / hbm, "peak": hbm, "peak_kind": f"{kind} hbm_gbs",
+            "pixels_per_s": n / ((mu + mw) / 1e3), "bytes_per_pixel": 56, "reps": reps,
+            "l2": "flushed before every repetition (256 MiB write)"}
+
+
 def serving_summary(requests, rate, saturated=True):
     """Serving stream: requests (RGB contrast-Potts crops, side U[128,2048],
     4/8-conn 50/50, lambda U[1,16]) arrive as a Poisson process at `rate`;
@@ -326,7 +384,7 @@ def serving_summary(requests, rate, saturated=True):
     n = requests
     reqs = inputs.serving_requests(n, rate=rate)
     arrivals = [r["arrival"] for r in reqs]
-    bases = [inputs.serving_base(b) for b in range(2)]
+    bases = [_serving_base(b) for b in range(2)]
     dbase = [(torch.from_numpy(b["u"]).cuda(), torch.from_numpy(b["wq"]).cuda()) for b in bases]
     dev_in = []
     for r in reqs:
@@ -555,6 +613,33 @@ def main():
     h2d = sum(d["u"].nbytes + d["wq"].nbytes for d in insts)
     d2h = sum(g.n for g in ctxs) + 8 * len(ctxs)
 
+    # ---- end to end from the image: potentials on the GPU (Algorithm 1's
+    # first step), then the solve; pinned image in, labels out --------------
+    e2e_img = None
+    if all("image" in d and "gmm_fg" in d and "inv_dist" in d for d in insts) and not overlap:
+        hi = [torch.from_numpy(np.ascontiguousarray(d["image"], np.float32)).pin_memory() for d in insts]
+        img_ms = []
+        barrier()
+        for s in range(args.steps):
+            flush.fill_((s + 7) & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for g, d, im, lab in zip(ctxs, insts, hi, hl):
+                g.set_image(im.numpy(), d["gmm_fg"], d["gmm_bg"], inv_dist=d["inv_dist"])
+                g.solve(lab.numpy(), allow_notconv="grow" in insts[0])
+            torch.cuda.synchronize()
+            img_ms.append(1e3 * (time.perf_counter() - t0))
+        barrier()
+        t_img = sum(img_ms) / 1e3
+        if world > 1:
+            tt = torch.tensor([t_img], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_img = float(tt.item())
+        e2e_img = {"value": world * n_px * args.steps / t_img, "unit": "pixels/s",
+                   "h2d_bytes_per_step": sum(im.numel() * 4 for im in hi), "d2h_bytes_per_step": d2h,
+                   "ms_per_step": statistics.mean(img_ms),
+                   "note": "image in; mixture data term and contrast weights computed on the GPU"}
+
     metric = METRIC if "grow" not in insts[0] else "pixels/sec of 3 ADMM iterations (overlapping partition, Figure 2 protocol)"
     line = {"metric": metric, "value": value, "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
@@ -569,12 +654,19 @@ def main():
             "e2e": {"value": world * n_px * args.steps / e2e_t, "unit": "pixels/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)}}
+    if e2e_img:
+        line["e2e_from_image"] = e2e_img
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, gaps, res = cpu_baseline(insts, cfg)
         line["cpu_baseline"] = cb
         line["energy_gap_vs_serial_lsa_tr" if insts[0].get("lsa_steps") else "energy_gap_vs_global_mincut"] = gaps
         line["oracle_match"] = all(abs(E * 1024 - r["energy"]) <= 1e-4 * abs(r["energy"])
                                    for E, r in zip(energies[-len(insts):], res))
+    if rank == 0 and world == 1 and args.workload == "ellipses512":
+        try:
+            line["potentials"] = potentials_summary()
+        except Exception as e:  # the main line stands on its own
+            line["potentials"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and args.workload == "ellipses512" and not args.no_serving:
         # the serving target: batched vs one-at-a-time on the request stream
         try:

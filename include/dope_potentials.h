@@ -26,9 +26,11 @@
  * radius-2 ball in 3-D) every offset (dz, dy, dx) of the kernel whose first
  * non-zero coordinate is positive, in increasing (dz, dy, dx) order.
  *
- * Precision: FP32 arithmetic on the device (one FP32 exp per pair), with the
- * mixture constants (Cholesky factors, log-determinants, log-weights) formed
- * on the host in FP64.  The quantised weight of a pair whose 1024 w lies
+ * Precision: FP32 arithmetic on the device, with the mixture constants
+ * (Cholesky factors, log-determinants, log-weights) formed on the host in
+ * FP64; the data term combines its components with the hardware base-2
+ * exponential and logarithm (errors near 2^-22), and the weights use one
+ * FP32 exp per pair.  The quantised weight of a pair whose 1024 w lies
  * within a few FP32 ulp of a rounding tie can differ by one from the FP64
  * definition; every other weight is the FP64 definition's rne(1024 w).
  *

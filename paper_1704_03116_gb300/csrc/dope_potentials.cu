@@ -6,11 +6,13 @@
 //   u_i   = clip(log p_bg(x_i) - log p_fg(x_i)),  p = sum_j pi_j N(m_j, S_j)
 //   wq_ij = rne(1024 exp(-|x_i - x_j|^2 / (2 sigma^2)) [/ |p_i - p_j|])
 //
-// Both are elementwise over the image and bound by HBM traffic (12 B read per
-// RGB pixel; 4 B written for u, 4 B per forward offset for wq).  The mixture
-// constants are formed once on the host in FP64 (Cholesky factor L of each
-// S_j, its inverse, log-determinant and log-weight) and passed by value; the
-// device evaluates each component as c_j - |L_j^-1 (x - m_j)|^2 / 2 in FP32.
+// Both are elementwise over the image: 12 B read per RGB pixel, 4 B written
+// for u and 4 B per forward offset for wq; at these sizes the kernels are
+// bound by instruction issue as much as by HBM.  The mixture constants are
+// formed once on the host in FP64 (Cholesky factor L of each S_j, its
+// inverse, log-determinant and log-weight, all in log2 units) and passed by
+// value; the device evaluates each component as c_j - |L'_j (x - m_j)|^2 in
+// FP32 and combines them with the hardware base-2 exponential and logarithm.
 // The weights take their rounding decision in FP32 with one correctly
 // rounded operation at a time (no contraction), in the order the header
 // lists, so that only the exponential differs from an FP32 restatement.
@@ -36,8 +38,10 @@ constexpr int MAXC = DOPE_GMM_MAX_COMP;
 constexpr int MAXF = DOPE_GMM_MAX_CH;
 constexpr int MAXOFF = 40;   // forward offsets of the 9x9 square
 
-// One mixture, ready for the device: component j's log-density is
-//   c[j] - 0.5 * sum_r ( sum_{c <= r} Li[j][r(r+1)/2 + c] (x_c - mean[j][c]) )^2
+// One mixture, ready for the device: component j's log2-density is
+//   c[j] - sum_r ( sum_{c <= r} Li[j][r(r+1)/2 + c] (x_c - mean[j][c]) )^2
+// (the inverse Cholesky factor scaled by sqrt(log2(e) / 2), the constant in
+// log2 units).
 struct GmmDev {
     int K;
     float mean[MAXC][MAXF];
@@ -54,6 +58,7 @@ int gmm_prepare(const dope_gmm* g, int C, GmmDev* out) {
     if (!g || g->n_comp < 1 || g->n_comp > MAXC || g->channels != C) return DOPE_EINVAL;
     memset(out, 0, sizeof(*out));
     out->K = g->n_comp;
+    for (int j = g->n_comp; j < MAXC; ++j) out->c[j] = -INFINITY;   // padding: exp(-inf) = 0
     for (int j = 0; j < g->n_comp; ++j) {
         const double w = g->weight[j];
         if (!(w > 0.0) || !isfinite(w)) return DOPE_EINVAL;
@@ -81,43 +86,64 @@ int gmm_prepare(const dope_gmm* g, int C, GmmDev* out) {
                 Li[r][c] = -s / L[r][r];
             }
         }
+        // log2 units: log2 N_j(x) = c[j] - |Li'_j (x - m_j)|^2 with
+        // Li' = Li sqrt(log2(e) / 2) and c[j] = log2(e) (log w_j - log det L_j - C/2 log 2 pi)
+        const double log2e = 1.4426950408889634, sc = sqrt(0.5 * log2e);
         double half_logdet = 0.0;
         for (int r = 0; r < C; ++r) half_logdet += log(L[r][r]);
-        out->c[j] = (float)(log(w) - half_logdet - 0.5 * C * log(2.0 * M_PI));
+        out->c[j] = (float)(log2e * (log(w) - half_logdet - 0.5 * C * log(2.0 * M_PI)));
         for (int r = 0; r < C; ++r) {
             const double m = g->mean[j][r];
             if (!isfinite(m)) return DOPE_EINVAL;
             out->mean[j][r] = (float)m;
-            for (int c = 0; c <= r; ++c) out->Li[j][r * (r + 1) / 2 + c] = (float)Li[r][c];
+            for (int c = 0; c <= r; ++c) out->Li[j][r * (r + 1) / 2 + c] = (float)(Li[r][c] * sc);
         }
     }
     return DOPE_OK;
 }
 
-template <int C>
-__device__ __forceinline__ float mixture_ll(const GmmDev& g, const float* x) {
-    float l[MAXC];
-    float top = -INFINITY;
+// Hardware base-2 exponential and logarithm (MUFU; relative error of
+// ex2 and absolute error of lg2 near 2^-22 on the ranges used here).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// log2 sum_j 2^(l_j) over K components (l_j the log2-densities): the largest
+// term as the shift, then one ex2 per component.  K is a template constant
+// (the larger of the two models' counts; the smaller model's extra
+// components have c = -inf and add exactly 0), so every constant is an
+// immediate operand of the parameter bank.
+template <int C, int K>
+__device__ __forceinline__ float mixture_ll2(const GmmDev& g, const float* x) {
+    float nl[K];   // -l_j
+    float lo = INFINITY;
 #pragma unroll
-    for (int j = 0; j < MAXC; ++j) {
-        if (j < g.K) {
-            float q = 0.f;
+    for (int j = 0; j < K; ++j) {
+        float d[C];
 #pragma unroll
-            for (int r = 0; r < C; ++r) {
-                float z = 0.f;
+        for (int c = 0; c < C; ++c) d[c] = x[c] - g.mean[j][c];
+        float q = -g.c[j];
 #pragma unroll
-                for (int c = 0; c <= r; ++c) z = fmaf(g.Li[j][r * (r + 1) / 2 + c], x[c] - g.mean[j][c], z);
-                q = fmaf(z, z, q);
-            }
-            l[j] = fmaf(-0.5f, q, g.c[j]);
-            top = fmaxf(top, l[j]);
+        for (int r = 0; r < C; ++r) {
+            float z = 0.f;
+#pragma unroll
+            for (int c = 0; c <= r; ++c) z = fmaf(g.Li[j][r * (r + 1) / 2 + c], d[c], z);
+            q = fmaf(z, z, q);
         }
+        nl[j] = q;
+        lo = fminf(lo, q);
     }
     float s = 0.f;
 #pragma unroll
-    for (int j = 0; j < MAXC; ++j)
-        if (j < g.K) s += expf(l[j] - top);
-    return top + logf(s);
+    for (int j = 0; j < K; ++j) s += ex2_approx(lo - nl[j]);
+    return lg2_approx(s) - lo;
 }
 
 constexpr int GMM_TILE = 256;   // pixels per CTA tile (one per thread)
@@ -126,9 +152,9 @@ constexpr int GMM_TILE = 256;   // pixels per CTA tile (one per thread)
 // through shared memory with coalesced loads, then evaluates one pixel per
 // thread; grid-stride over tiles.  Plain (L2-allocating) loads and stores:
 // the image is read again by the contrast kernels and u by the quantiser.
-template <int C>
-__global__ void __launch_bounds__(GMM_TILE) k_gmm_unaries(const float* __restrict__ img, long long n,
-                                                           GmmPair P, float clip, float* __restrict__ u) {
+template <int C, int K>
+__global__ void __launch_bounds__(GMM_TILE) k_gmm_unaries(const float* __restrict__ img, long long n, GmmPair P,
+                                                           float clip, float* __restrict__ u) {
     __shared__ float tile[GMM_TILE * C];
     const long long ntiles = (n + GMM_TILE - 1) / GMM_TILE;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -141,10 +167,30 @@ __global__ void __launch_bounds__(GMM_TILE) k_gmm_unaries(const float* __restric
             float x[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) x[c] = tile[threadIdx.x * C + c];
-            float v = mixture_ll<C>(P.bg, x) - mixture_ll<C>(P.fg, x);
+            float v = 0.6931471805599453f * (mixture_ll2<C, K>(P.bg, x) - mixture_ll2<C, K>(P.fg, x));
             v = v < -clip ? -clip : (v > clip ? clip : v);   // NaN stays NaN
             u[p0 + threadIdx.x] = v;
         }
+    }
+}
+
+template <int C, int K>
+void launch_gmm(int blocks, const float* img, long long n, const GmmPair& P, float clip, float* u, cudaStream_t st) {
+    k_gmm_unaries<C, K><<<blocks, GMM_TILE, 0, st>>>(img, n, P, clip, u);
+}
+
+template <int C>
+void launch_gmm_k(int K, int blocks, const float* img, long long n, const GmmPair& P, float clip, float* u,
+                  cudaStream_t st) {
+    switch (K) {
+        case 1: launch_gmm<C, 1>(blocks, img, n, P, clip, u, st); break;
+        case 2: launch_gmm<C, 2>(blocks, img, n, P, clip, u, st); break;
+        case 3: launch_gmm<C, 3>(blocks, img, n, P, clip, u, st); break;
+        case 4: launch_gmm<C, 4>(blocks, img, n, P, clip, u, st); break;
+        case 5: launch_gmm<C, 5>(blocks, img, n, P, clip, u, st); break;
+        case 6: launch_gmm<C, 6>(blocks, img, n, P, clip, u, st); break;
+        case 7: launch_gmm<C, 7>(blocks, img, n, P, clip, u, st); break;
+        default: launch_gmm<C, 8>(blocks, img, n, P, clip, u, st); break;
     }
 }
 
@@ -196,40 +242,111 @@ __device__ __forceinline__ float contrast_d2(const float* xi, const float* __res
     return s;
 }
 
+// Pixel traversal of the contrast kernels: a CTA of (bx, by) threads covers
+// bx consecutive pixels of by consecutive rows; blockIdx.x picks the column
+// segment and blockIdx.y strides over the D * ceil(H / by) row groups, so no
+// per-pixel division is needed and the grid stays a few CTAs per SM.
+template <typename Fn>
+__device__ __forceinline__ void for_each_pixel(const ContrastGeo& G, int hb, Fn&& fn) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long groups = (long long)G.D * hb;
+    for (long long r = blockIdx.y; r < groups; r += gridDim.y) {
+        const int z = (int)(r / hb), y = (int)(r % hb) * blockDim.y + threadIdx.y;
+        if (x < G.W && y < G.H) fn(z, y, x, ((long long)z * G.H + y) * G.W + x);
+    }
+}
+
+// Offsets of the contrast kernels: compile-time for connectivity 4, 8 and 6
+// (the weight layout's order), from the geometry's table otherwise (CONN 0).
+template <int CONN>
+__device__ __forceinline__ void pair_off(const ContrastGeo& G, int d, int& dz, int& dy, int& dx) {
+    if constexpr (CONN == 4) {
+        dz = 0; dy = d; dx = 1 - d;
+    } else if constexpr (CONN == 8) {
+        dz = 0; dy = d >= 1; dx = d == 0 ? 1 : (d == 1 ? 0 : (d == 2 ? 1 : -1));
+    } else if constexpr (CONN == 6) {
+        dz = d == 2; dy = d == 1; dx = d == 0;
+    } else {
+        dz = G.off[d][0]; dy = G.off[d][1]; dx = G.off[d][2];
+    }
+}
+
+template <int CONN>
+__host__ __device__ constexpr int pair_count() { return CONN == 4 ? 2 : (CONN == 8 ? 4 : (CONN == 6 ? 3 : 0)); }
+
+// Visit every forward pair (d, neighbour features) of pixel (z, y, x) in
+// offset order; fn(d, xj) gets xj = nullptr where the partner is outside the
+// grid.  For the radius-1 neighbourhoods an interior pixel skips the bounds
+// checks and finds its partners at fixed index offsets.
+template <int C, int CONN, typename Fn>
+__device__ __forceinline__ void for_each_pair(const ContrastGeo& G, const float* __restrict__ img, int z, int y,
+                                              int x, long long i, Fn&& fn) {
+    if constexpr (CONN != 0) {
+        constexpr int NH = pair_count<CONN>();
+        const bool interior = x >= 1 && x + 1 < G.W && y + 1 < G.H && (CONN != 6 || z + 1 < G.D);
+        if (interior) {
+#pragma unroll
+            for (int d = 0; d < NH; ++d) {
+                int dz, dy, dx;
+                pair_off<CONN>(G, d, dz, dy, dx);
+                const long long o = ((long long)dz * G.H + dy) * G.W + dx;
+                fn(d, img + (i + o) * C);
+            }
+            return;
+        }
+#pragma unroll
+        for (int d = 0; d < NH; ++d) {
+            int dz, dy, dx;
+            pair_off<CONN>(G, d, dz, dy, dx);
+            const int zz = z + dz, yy = y + dy, xx = x + dx;
+            const bool in = zz < G.D && yy < G.H && xx >= 0 && xx < G.W;
+            fn(d, in ? img + (((long long)zz * G.H + yy) * G.W + xx) * C : nullptr);
+        }
+    } else {
+        for (int d = 0; d < G.nh; ++d) {
+            int dz, dy, dx;
+            pair_off<0>(G, d, dz, dy, dx);
+            const int zz = z + dz, yy = y + dy, xx = x + dx;
+            const bool in = zz < G.D && yy >= 0 && yy < G.H && xx >= 0 && xx < G.W;
+            fn(d, in ? img + (((long long)zz * G.H + yy) * G.W + xx) * C : nullptr);
+        }
+    }
+}
+
 // Sum over every neighbour pair of |x_i - x_j|: per pixel in FP32 (offset
-// order), over pixels in FP64; one double atomic per warp into acc.
-template <int C>
-__global__ void __launch_bounds__(256) k_contrast_sum(const float* __restrict__ img, ContrastGeo G,
-                                                      double* __restrict__ acc) {
+// order), over pixels in FP64; one double atomic per CTA into acc.
+template <int C, int CONN>
+__global__ void __launch_bounds__(256) k_contrast_sum(const float* __restrict__ img, const __grid_constant__ ContrastGeo G,
+                                                      int hb, double* __restrict__ acc) {
+    __shared__ double red[8];
     double part = 0.0;
-    const unsigned HW = (unsigned)G.H * (unsigned)G.W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < G.N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned ii = (unsigned)i;   // N < 2^31
-        const int x = (int)(ii % (unsigned)G.W), y = (int)((ii / (unsigned)G.W) % (unsigned)G.H),
-                  z = (int)(ii / (unsigned)HW);
+    for_each_pixel(G, hb, [&](int z, int y, int x, long long i) {
         float xi[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) xi[c] = __ldg(&img[i * C + c]);
         float s = 0.f;
-        for (int d = 0; d < G.nh; ++d) {
-            const int zz = z + G.off[d][0], yy = y + G.off[d][1], xx = x + G.off[d][2];
-            if (zz >= G.D || yy < 0 || yy >= G.H || xx < 0 || xx >= G.W) continue;
-            const long long j = ((long long)zz * G.H + yy) * G.W + xx;
-            s = __fadd_rn(s, __fsqrt_rn(contrast_d2<C>(xi, &img[j * C])));
-        }
+        for_each_pair<C, CONN>(G, img, z, y, x, i, [&](int, const float* xj) {
+            if (xj) s = __fadd_rn(s, __fsqrt_rn(contrast_d2<C>(xi, xj)));
+        });
         part += (double)s;
-    }
+    });
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(acc, part);
+    const int t = threadIdx.y * blockDim.x + threadIdx.x, nw = (blockDim.x * blockDim.y) >> 5;
+    if ((t & 31) == 0) red[t >> 5] = part;
+    __syncthreads();
+    if (t == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w) tot += red[w];
+        if (tot != 0.0) atomicAdd(acc, tot);
+    }
 }
 
 // wq[d][i] for every pixel and forward offset.  sigma_given > 0 is used as
 // is; otherwise sigma = max(acc[0] / pairs, 1e-6).  Thread 0 of CTA 0 stores
 // the sigma used in acc[1].
-template <int C>
-__global__ void __launch_bounds__(256) k_contrast_weights(const float* __restrict__ img, ContrastGeo G,
-                                                          double sigma_given, double pairs,
+template <int C, int CONN>
+__global__ void __launch_bounds__(256) k_contrast_weights(const float* __restrict__ img, const __grid_constant__ ContrastGeo G,
+                                                          int hb, double sigma_given, double pairs,
                                                           double* __restrict__ acc, int32_t* __restrict__ wq) {
     double sigma = sigma_given;
     if (!(sigma > 0.0)) {
@@ -237,28 +354,47 @@ __global__ void __launch_bounds__(256) k_contrast_weights(const float* __restric
         if (!(sigma >= 1e-6)) sigma = 1e-6;
     }
     const float k = __double2float_rn(__ddiv_rn(1.0, __dmul_rn(__dmul_rn(2.0, sigma), sigma)));
-    if (blockIdx.x == 0 && threadIdx.x == 0 && acc) acc[1] = sigma;
-    const unsigned HW = (unsigned)G.H * (unsigned)G.W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < G.N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned ii = (unsigned)i;   // N < 2^31
-        const int x = (int)(ii % (unsigned)G.W), y = (int)((ii / (unsigned)G.W) % (unsigned)G.H),
-                  z = (int)(ii / (unsigned)HW);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0 && acc) acc[1] = sigma;
+    for_each_pixel(G, hb, [&](int z, int y, int x, long long i) {
         float xi[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) xi[c] = __ldg(&img[i * C + c]);
-        for (int d = 0; d < G.nh; ++d) {
-            const int zz = z + G.off[d][0], yy = y + G.off[d][1], xx = x + G.off[d][2];
+        for_each_pair<C, CONN>(G, img, z, y, x, i, [&](int d, const float* xj) {
             int32_t q = 0;
-            if (zz < G.D && yy >= 0 && yy < G.H && xx >= 0 && xx < G.W) {
-                const long long j = ((long long)zz * G.H + yy) * G.W + xx;
-                const float a = __fmul_rn(contrast_d2<C>(xi, &img[j * C]), k);
+            if (xj) {
+                const float a = __fmul_rn(contrast_d2<C>(xi, xj), k);
                 float e = expf(-a);
                 e = __fmul_rn(e, G.invdist[d]);
                 q = __float2int_rn(__fmul_rn(1024.f, e));
             }
             wq[(long long)d * G.N + i] = q;
-        }
+        });
+    });
+}
+
+template <int C, int CONN>
+void launch_contrast(bool sum, dim3 grid, dim3 block, const float* img, const ContrastGeo& G, int hb, double sigma,
+                     double pairs, double* ws, int32_t* wq, cudaStream_t st) {
+    if (sum) k_contrast_sum<C, CONN><<<grid, block, 0, st>>>(img, G, hb, ws);
+    else k_contrast_weights<C, CONN><<<grid, block, 0, st>>>(img, G, hb, sigma, pairs, ws, wq);
+}
+
+template <int C>
+void launch_contrast_c(int conn, bool sum, dim3 grid, dim3 block, const float* img, const ContrastGeo& G, int hb,
+                       double sigma, double pairs, double* ws, int32_t* wq, cudaStream_t st) {
+    if (conn == 4) launch_contrast<C, 4>(sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st);
+    else if (conn == 8) launch_contrast<C, 8>(sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st);
+    else if (conn == 6) launch_contrast<C, 6>(sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st);
+    else launch_contrast<C, 0>(sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st);
+}
+
+void launch_contrast_any(int C, int conn, bool sum, dim3 grid, dim3 block, const float* img, const ContrastGeo& G,
+                         int hb, double sigma, double pairs, double* ws, int32_t* wq, cudaStream_t st) {
+    switch (C) {
+        case 1: launch_contrast_c<1>(conn, sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st); break;
+        case 2: launch_contrast_c<2>(conn, sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st); break;
+        case 3: launch_contrast_c<3>(conn, sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st); break;
+        default: launch_contrast_c<4>(conn, sum, grid, block, img, G, hb, sigma, pairs, ws, wq, st); break;
     }
 }
 
@@ -294,11 +430,12 @@ int pot_unaries_issue(const float* img, long long n, int C, const dope_gmm* fg, 
     if (n == 0) return DOPE_OK;
     const float cl = clip > 3.0e38 ? 3.0e38f : (float)clip;
     const int blocks = blocks_for(n, GMM_TILE);
+    const int K = P.fg.K > P.bg.K ? P.fg.K : P.bg.K;
     switch (C) {
-        case 1: k_gmm_unaries<1><<<blocks, GMM_TILE, 0, st>>>(img, n, P, cl, u); break;
-        case 2: k_gmm_unaries<2><<<blocks, GMM_TILE, 0, st>>>(img, n, P, cl, u); break;
-        case 3: k_gmm_unaries<3><<<blocks, GMM_TILE, 0, st>>>(img, n, P, cl, u); break;
-        default: k_gmm_unaries<4><<<blocks, GMM_TILE, 0, st>>>(img, n, P, cl, u); break;
+        case 1: launch_gmm_k<1>(K, blocks, img, n, P, cl, u, st); break;
+        case 2: launch_gmm_k<2>(K, blocks, img, n, P, cl, u, st); break;
+        case 3: launch_gmm_k<3>(K, blocks, img, n, P, cl, u, st); break;
+        default: launch_gmm_k<4>(K, blocks, img, n, P, cl, u, st); break;
     }
     PCK(cudaGetLastError());
     return DOPE_OK;
@@ -329,23 +466,23 @@ int pot_weights_issue(const float* img, const int64_t dims[3], int ndim, int C, 
         const long long ez = G.D - (dz < 0 ? -dz : dz), ey = G.H - (dy < 0 ? -dy : dy), ex = G.W - (dx < 0 ? -dx : dx);
         if (ez > 0 && ey > 0 && ex > 0) pairs += (double)(ez * ey * ex);
     }
-    const int blocks = blocks_for(N, 256);
+    // CTA shape: bx = the power of two in [32, 256] that covers a row (or
+    // 256), by = 256 / bx rows; grid.x column segments, grid.y row groups
+    int bx = 32;
+    while (bx < 256 && bx < G.W) bx <<= 1;
+    const int by = 256 / bx;
+    const int hb = (G.H + by - 1) / by;
+    const long long gx = (G.W + bx - 1) / bx, groups = (long long)G.D * hb;
+    if (gx > 0x7fffffffLL) return DOPE_EINVAL;
+    const long long want = grid_cap() / gx > 0 ? grid_cap() / gx : 1;
+    const dim3 grid((unsigned)gx, (unsigned)(groups < want ? groups : (want < 65535 ? want : 65535)));
+    const dim3 block(bx, by);
+    if (!(sigma > 0.0)) PCK(cudaMemsetAsync(ws, 0, 2 * sizeof(double), st));
     if (!(sigma > 0.0)) {
-        PCK(cudaMemsetAsync(ws, 0, 2 * sizeof(double), st));
-        switch (C) {
-            case 1: k_contrast_sum<1><<<blocks, 256, 0, st>>>(img, G, ws); break;
-            case 2: k_contrast_sum<2><<<blocks, 256, 0, st>>>(img, G, ws); break;
-            case 3: k_contrast_sum<3><<<blocks, 256, 0, st>>>(img, G, ws); break;
-            default: k_contrast_sum<4><<<blocks, 256, 0, st>>>(img, G, ws); break;
-        }
+        launch_contrast_any(C, conn, true, grid, block, img, G, hb, sigma, pairs, ws, wq, st);
         PCK(cudaGetLastError());
     }
-    switch (C) {
-        case 1: k_contrast_weights<1><<<blocks, 256, 0, st>>>(img, G, sigma, pairs, ws, wq); break;
-        case 2: k_contrast_weights<2><<<blocks, 256, 0, st>>>(img, G, sigma, pairs, ws, wq); break;
-        case 3: k_contrast_weights<3><<<blocks, 256, 0, st>>>(img, G, sigma, pairs, ws, wq); break;
-        default: k_contrast_weights<4><<<blocks, 256, 0, st>>>(img, G, sigma, pairs, ws, wq); break;
-    }
+    launch_contrast_any(C, conn, false, grid, block, img, G, hb, sigma, pairs, ws, wq, st);
     PCK(cudaGetLastError());
     return DOPE_OK;
 }

@@ -539,9 +539,11 @@ def dope_gmm_unaries(image, fg, bg, clip=1.0e5, channels=None, out=None, stream=
 
 
 def dope_contrast_weights(image, grid, connectivity, channels=1, sigma=0.0, inv_dist=False, out=None,
-                          stream=None):
+                          stream=None, read_sigma=True):
     """wq [conn/2, N] int32 CUDA tensor of a CUDA image on `grid` ((H, W) or
-    (D, H, W)) and the sigma used (sigma <= 0: the mean contrast)."""
+    (D, H, W)) and the sigma used (sigma <= 0: the mean contrast).  With
+    read_sigma=False the call stays asynchronous and the sigma returned is
+    None."""
     import torch
     image = _dev_tensor(image, "image")
     grid = tuple(int(g) for g in grid)
@@ -555,8 +557,9 @@ def dope_contrast_weights(image, grid, connectivity, channels=1, sigma=0.0, inv_
     _check(_lib.dope_contrast_weights(ctypes.c_void_p(image.data_ptr()), g, len(grid), int(channels),
                                       int(connectivity), float(sigma), int(bool(inv_dist)),
                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
-                                      ctypes.byref(sig), _stream(stream)), "dope_contrast_weights")
-    return out, sig.value
+                                      ctypes.byref(sig) if read_sigma else None, _stream(stream)),
+           "dope_contrast_weights")
+    return out, (sig.value if read_sigma else None)
 
 
 def dope_set_image(ctx, image, fg, bg, clip=1.0e5, sigma=0.0, inv_dist=False, channels=None, stream=None):

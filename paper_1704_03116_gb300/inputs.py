@@ -238,7 +238,7 @@ def ellipses_rgb(seed=0, size=512, lam=4.0, block=(32, 32), conn=8, n_ellipses=1
     w, sig = contrast_weights(img32.astype(np.float64)[None], conn, inv_dist=True)
     return {"name": f"ellipses{size}", "grid": (H, W), "conn": conn, "block": tuple(block),
             "lam": float(lam), "mu0": 100.0, "u": u, "wq": quantise_weights(w),
-            "sigma": sig, "image": img32, "gmm_fg": g_fg, "gmm_bg": g_bg}
+            "sigma": sig, "image": img32, "gmm_fg": g_fg, "gmm_bg": g_bg, "inv_dist": True}
 
 
 # --------------------------------------------------------------------------
@@ -283,7 +283,7 @@ def ellipsoids3d(seed=0, shape=(128, 256, 256), lam=3.0, block=(8, 16, 16), nois
     return {"name": "ellipsoids%dx%dx%d" % (W, H, D), "grid": tuple(shape), "conn": 6,
             "block": tuple(block), "lam": float(lam), "mu0": 500.0, "u": u.reshape(-1),
             "wq": quantise_weights(w), "sigma": sig, "truth": fg.reshape(-1).astype(np.uint8),
-            "image": vol.reshape(-1),
+            "image": vol.reshape(-1), "inv_dist": False,
             # the two classes' Gaussians as one-component, one-channel mixtures
             "gmm_fg": (np.array([1.0]), np.array([[m1]]), np.array([[[s1 * s1]]])),
             "gmm_bg": (np.array([1.0]), np.array([[m0]]), np.array([[[s0 * s0]]]))}
