@@ -268,12 +268,17 @@ def run_reference(args):
     return 0
 
 
-def _serve(dope, torch, reqs, dev_in, labels, mode, arrivals, warm):
+def _serve(dope, torch, reqs, dev_in, labels, mode, arrivals, warm, submit=None):
     """Run the request stream through a server; arrivals = None submits all
-    at once (saturated).  Returns per-request results and server stats."""
+    at once (saturated).  submit(srv, r, inputs, labels, tag) queues one
+    request (default: unaries and weights).  Returns per-request results and
+    server stats."""
+    if submit is None:
+        def submit(srv, r, x, lab, tag):
+            srv.submit(r["grid"], r["conn"], r["block"], r["lam"], x[0], x[1], lab, tag=tag)
     srv = dope.Server(mode=mode)
-    for (u, w, lab, r) in warm:                       # first launches, tables
-        srv.submit(r["grid"], r["conn"], r["block"], r["lam"], u, w, lab)
+    for (x, lab, r) in warm:                          # first launches, tables
+        submit(srv, r, x, lab, 0)
     got = 0
     while got < len(warm):
         got += len(srv.poll(timeout=1.0))
@@ -288,8 +293,7 @@ def _serve(dope, torch, reqs, dev_in, labels, mode, arrivals, warm):
                 if dt <= 0:
                     break
                 time.sleep(min(dt, 0.001) if dt > 0.0002 else 0)
-        u, w = dev_in[i]
-        srv.submit(r["grid"], r["conn"], r["block"], r["lam"], u, w, labels[i], tag=i)
+        submit(srv, r, dev_in[i], labels[i], i)
     deadline = time.time() + 600
     while len(res) < len(reqs) and time.time() < deadline:
         for x in srv.poll(timeout=0.5):
@@ -405,7 +409,7 @@ def serving_summary(requests, rate, saturated=True):
     warm = []
     for k in range(3):
         r = dict(reqs[k], lam=2.0)
-        warm.append((dev_in[k][0], dev_in[k][1], torch.zeros_like(labels[k]), r))
+        warm.append((dev_in[k], torch.zeros_like(labels[k]), r))
     torch.cuda.synchronize()
     out = {}
     res_b, st_b, t0b = _serve(dope, torch, reqs, dev_in, labels, 0, arrivals, warm)
@@ -422,6 +426,25 @@ def serving_summary(requests, rate, saturated=True):
         out["batched_saturated"] = _summ(res_bs, st_bs, t0bs, reqs, None)
         res_1s, st_1s, t01s = _serve(dope, torch, reqs, dev_in, labels, 1, None, warm)
         out["one_at_a_time_saturated"] = _summ(res_1s, st_1s, t01s, reqs, None)
+        # the same stream given as RGB crops: the server computes the
+        # potentials on the GPU (the bases' mixtures; sigma fixed to the base
+        # image's, so a crop's weights mean what they mean in the full image)
+        imgs = [torch.from_numpy(np.ascontiguousarray(b["image"])).cuda() for b in bases]
+        gm = [(dope.gmm(*b["gmm_fg"]), dope.gmm(*b["gmm_bg"]), float(b["sigma"])) for b in bases]
+        img_in = [imgs[r["base"]][r["y0"]:r["y0"] + r["side"], r["x0"]:r["x0"] + r["side"]].contiguous()
+                  for r in reqs]
+        del dev_in
+
+        def submit_img(srv, r, x, lab, tag):
+            fg, bg, sig = gm[r["base"]]
+            srv.submit_image(r["grid"], r["conn"], r["block"], r["lam"], x, fg, bg, lab, sigma=sig,
+                             inv_dist=True, tag=tag)
+        warm_i = [(img_in[k], w[1], w[2]) for k, w in enumerate(warm)]
+        torch.cuda.synchronize()
+        res_bi, st_bi, t0bi = _serve(dope, torch, reqs, img_in, labels, 0, None, warm_i, submit_img)
+        out["batched_saturated_from_image"] = dict(_summ(res_bi, st_bi, t0bi, reqs, None),
+                                                   inputs="device-resident RGB crops, 12 B/px; "
+                                                          "potentials computed by the server")
     out["results_identical_batched_vs_one_at_a_time"] = bool(same)
     out["iterations_mean"] = round(sum(res_b[i]["iterations"] for i in range(n)) / n, 1)
     out["config"] = {"workload": "serving stream: RGB contrast-Potts crops of two seeded 2048x2048 ellipse "

@@ -389,6 +389,11 @@ typedef struct {
     int where_labels;         /* DOPE_HOST or DOPE_DEVICE */
     int reserved;
     uint64_t tag;             /* returned in the result */
+    const void *image_request;  /* NULL: unaries / weights as above.  Otherwise a
+                                   const dope_image_request* (dope_potentials.h):
+                                   the server computes the potentials on the GPU
+                                   from the image, and unaries / weights are
+                                   ignored (may be NULL). */
 } dope_request;
 
 typedef struct {

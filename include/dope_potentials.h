@@ -99,6 +99,22 @@ int dope_set_image(dope_ctx* ctx, const float* image, int channels, const dope_g
                    const dope_gmm* bg, double clip, double sigma, int inv_dist, int where,
                    double* sigma_used, void* stream);
 
+/* A request's inputs given as an image, for dope_server_submit
+ * (dope_request.image_request): the server computes the potentials on the
+ * GPU in the request's set-up, as dope_set_image does, into memory it charges
+ * to its arena.  The struct is copied at submit; the image (host or device,
+ * dope_request.where_inputs) must stay valid and unchanged until the result
+ * has been polled.  A model that is not valid fails the request with
+ * DOPE_EINVAL. */
+typedef struct {
+    const float *image;       /* [N][channels], image order */
+    int channels;             /* 1..4, the models' channel count */
+    int inv_dist;             /* divide the weights by the pixel distance */
+    double clip;              /* > 0 */
+    double sigma;             /* > 0: given; <= 0: the mean contrast */
+    dope_gmm fg, bg;
+} dope_image_request;
+
 #ifdef __cplusplus
 }
 #endif

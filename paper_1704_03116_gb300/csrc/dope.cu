@@ -1151,7 +1151,7 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
 }
 
 // Quantise device unaries (user order) into the context (stream-ordered).
-int issue_set_unaries(dope_ctx* c, const float* src, cudaStream_t st) {
+static int issue_set_unaries(dope_ctx* c, const float* src, cudaStream_t st) {
     const int threads = 256;
     k_set_unaries<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, src, c->U, c->ctrl);
     CK(cudaGetLastError());
@@ -1180,7 +1180,7 @@ int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* st
 }
 
 // Quantise device weights (user order, [conn/2][Nu]) into the context.
-int issue_set_weights(dope_ctx* c, const int32_t* src, cudaStream_t st) {
+static int issue_set_weights(dope_ctx* c, const int32_t* src, cudaStream_t st) {
     const int threads = 256;
     const int blocks = grid_for(c->g.N, threads);
     if (c->ov) {
@@ -1220,11 +1220,13 @@ int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void*
     return h.status;
 }
 
-int dope_set_image(dope_ctx* c, const float* image, int channels, const dope_gmm* fg, const dope_gmm* bg,
-                   double clip, double sigma, int inv_dist, int where, double* sigma_used, void* stream) {
+// Potentials of an image into the context's staging memory, then the
+// quantisers (stream-ordered, no synchronisation).  *ws_out: the device
+// scratch whose second double holds the sigma used.
+static int image_issue(dope_ctx* c, const float* image, int channels, const dope_gmm* fg, const dope_gmm* bg, double clip,
+                double sigma, int inv_dist, int where, cudaStream_t st, cudaEvent_t after_copies, double** ws_out) {
     if (!c || !image || channels < 1 || channels > DOPE_GMM_MAX_CH || (where != DOPE_HOST && where != DOPE_DEVICE))
         return DOPE_EINVAL;
-    cudaStream_t st = S(stream);
     const size_t n = (size_t)c->g.Nu;
     const int nh = c->conn / 2;
     // scratch: [sigma workspace 64 B][u: n floats][wq: nh * n int32][image if on the host]
@@ -1242,6 +1244,7 @@ int dope_set_image(dope_ctx* c, const float* image, int channels, const dope_gmm
         CK(cudaMemcpyAsync(base + off_i, image, sizeof(float) * n * channels, cudaMemcpyHostToDevice, st));
         img = (const float*)(base + off_i);
     }
+    if (after_copies) CK(cudaEventRecord(after_copies, st));
     rc = pot_unaries_issue(img, (long long)n, channels, fg, bg, clip, u, st);
     if (rc) return rc;
     const int64_t dims[3] = {c->g.Du, c->g.Hu, c->g.Wu};
@@ -1250,6 +1253,15 @@ int dope_set_image(dope_ctx* c, const float* image, int channels, const dope_gmm
     rc = clear_status(c, st);
     if (!rc) rc = issue_set_unaries(c, u, st);
     if (!rc) rc = issue_set_weights(c, wq, st);
+    if (ws_out) *ws_out = ws;
+    return rc;
+}
+
+int dope_set_image(dope_ctx* c, const float* image, int channels, const dope_gmm* fg, const dope_gmm* bg,
+                   double clip, double sigma, int inv_dist, int where, double* sigma_used, void* stream) {
+    cudaStream_t st = S(stream);
+    double* ws = nullptr;
+    int rc = image_issue(c, image, channels, fg, bg, clip, sigma, inv_dist, where, st, nullptr, &ws);
     if (rc) return rc;
     double sig = sigma;
     if (!(sigma > 0.0)) CK(cudaMemcpyAsync(&sig, ws + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1260,6 +1272,7 @@ int dope_set_image(dope_ctx* c, const float* image, int channels, const dope_gmm
     c->have_u = c->have_w = (h.status == 0);
     return h.status;
 }
+
 
 int dope_reset(dope_ctx* c) {
     if (!c) return DOPE_EINVAL;
@@ -1562,6 +1575,16 @@ int dope_get_geometry(dope_ctx* c, int64_t* n_pixels, int64_t* n_blocks, int* bl
 }
 
 }  // extern "C"
+
+int dope_image_upload_async(dope_ctx* c, const dope_image_request* q, int where, cudaStream_t st,
+                            cudaEvent_t after_copies) {
+    if (!c || !q) return DOPE_EINVAL;
+    int rc = image_issue(c, q->image, q->channels, &q->fg, &q->bg, q->clip, q->sigma, q->inv_dist, where, st,
+                         after_copies, nullptr);
+    if (rc) return rc;
+    c->have_u = c->have_w = 1;   // provisional until dope_ctx_status has read the status word
+    return DOPE_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free solve (dope_solve_noalloc).

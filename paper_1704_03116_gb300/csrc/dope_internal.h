@@ -91,6 +91,14 @@ int dope_batch_collect(dope_ctx* const* cs, int n, dope_batch_ws* w, int* t, int
 // state to its stop test or max_iter; synchronises `st`.
 int dope_run_single(dope_ctx* c, cudaStream_t st, int* t, int* conv);
 
+// dope_upload_async for a request given as an image: the image (host copy
+// staged first; after_copies, if not null, is recorded once the caller's
+// image is no longer read) goes through the potentials kernels into the
+// context's staging memory and then through the quantisers.  Stream-ordered;
+// the status word is read later (dope_ctx_status / dope_status_async).
+int dope_image_upload_async(dope_ctx* c, const dope_image_request* q, int where, cudaStream_t st,
+                            cudaEvent_t after_copies);
+
 // Whole-image potentials (dope_potentials.cu), stream-ordered, no
 // synchronisation.  pot_unaries_issue: u[i] of n pixels of a [n][C] image.
 // pot_weights_issue: wq [conn/2][N] of a (D, H, W) grid (D = 1 for ndim 2);

@@ -119,6 +119,7 @@ struct Slot {              // pinned, one per admitted request
 struct Job {
     uint64_t id = 0;
     dope_request r{};
+    dope_image_request img{};   // the request's image source, when r.image_request is set
     double t_submit = 0, t_admit = 0;
     JobState state = J_QUEUED;
     dope_ctx* ctx = nullptr;
@@ -202,7 +203,15 @@ bool request_ok(const dope_request* r) {
     if (!r || (r->ndim != 2 && r->ndim != 3)) return false;
     if (r->ndim == 2 && r->connectivity != 4 && r->connectivity != 8) return false;
     if (r->ndim == 3 && r->connectivity != 6) return false;
-    if (!r->unaries || !r->weights || !r->labels) return false;
+    if (!r->labels) return false;
+    if (r->image_request) {
+        const dope_image_request* q = static_cast<const dope_image_request*>(r->image_request);
+        if (!q->image || q->channels < 1 || q->channels > DOPE_GMM_MAX_CH || !(q->clip > 0.0) ||
+            !std::isfinite(q->sigma))
+            return false;
+    } else if (!r->unaries || !r->weights) {
+        return false;
+    }
     if ((r->where_inputs != DOPE_HOST && r->where_inputs != DOPE_DEVICE) ||
         (r->where_labels != DOPE_HOST && r->where_labels != DOPE_DEVICE))
         return false;
@@ -300,7 +309,9 @@ void admit(dope_server* s) {
         if (!nomem) {
             j->ev_copied = s->get_event();
             j->ev_setup = s->get_event();
-            rc = dope_upload_async(ctx, r.unaries, r.weights, r.where_inputs, s->s_setup, j->ev_copied);
+            rc = r.image_request
+                     ? dope_image_upload_async(ctx, &j->img, r.where_inputs, s->s_setup, j->ev_copied)
+                     : dope_upload_async(ctx, r.unaries, r.weights, r.where_inputs, s->s_setup, j->ev_copied);
             if (rc == DOPE_ENOMEM) nomem = true;
             else if (rc) {
                 s->queue.pop_front();
@@ -606,6 +617,10 @@ int dope_server_submit(dope_server* s, const dope_request* r, uint64_t* id) {
     Job* j = new (std::nothrow) Job();
     if (!j) return DOPE_ENOMEM;
     j->r = *r;
+    if (r->image_request) {
+        j->img = *static_cast<const dope_image_request*>(r->image_request);
+        j->r.image_request = &j->img;
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) { delete j; return DOPE_EINVAL; }

@@ -69,7 +69,7 @@ class dope_request(ctypes.Structure):
                 ("block_shape", ctypes.c_int32 * 3), ("lambda_", ctypes.c_double), ("params", dope_params),
                 ("use_params", ctypes.c_int), ("where_inputs", ctypes.c_int), ("unaries", ctypes.c_void_p),
                 ("weights", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("where_labels", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("tag", ctypes.c_uint64)]
+                ("reserved", ctypes.c_int), ("tag", ctypes.c_uint64), ("image_request", ctypes.c_void_p)]
 
 
 class dope_result(ctypes.Structure):
@@ -492,6 +492,11 @@ def dope_strerror(status):
 # Whole-image potentials (include/dope_potentials.h)
 # --------------------------------------------------------------------------
 
+class dope_image_request(ctypes.Structure):
+    _fields_ = [("image", ctypes.c_void_p), ("channels", ctypes.c_int), ("inv_dist", ctypes.c_int),
+                ("clip", ctypes.c_double), ("sigma", ctypes.c_double), ("fg", dope_gmm), ("bg", dope_gmm)]
+
+
 def gmm(weights, means, covs):
     """A dope_gmm from (weights [K], means [K, C], covs [K, C, C])."""
     w = np.asarray(weights, np.float64).reshape(-1)
@@ -723,6 +728,45 @@ class Server:
         r.tag = int(tag)
         rid = dope_server_submit(self.srv, r)
         self._keep[rid] = (ku, kw, kl)
+        return rid
+
+    def submit_image(self, grid, connectivity, block_shape, lam, image, fg, bg, labels, clip=1.0e5, sigma=0.0,
+                     inv_dist=False, params=None, tag=0):
+        """Queue a solve whose potentials the server computes on the GPU from
+        `image` ([..., C] float32, host array or CUDA tensor; fg / bg:
+        dope_gmm or (weights, means, covs))."""
+        grid = [int(g) for g in grid]
+        block = [int(b) for b in block_shape]
+        if len(grid) != len(block) or len(grid) not in (2, 3):
+            raise ValueError("grid and block_shape must both have rank 2 or 3")
+        fg, bg = _as_gmm(fg), _as_gmm(bg)
+        pi, wi, ki = _ptr(image, _t(np.float32))
+        if isinstance(labels, np.ndarray):
+            if labels.dtype != np.uint8 or not labels.flags.c_contiguous:
+                raise TypeError("labels must be a contiguous uint8 array")
+            pl, wl, kl = ctypes.c_void_p(labels.ctypes.data), DOPE_HOST, labels
+        else:
+            pl, wl, kl = _ptr(labels, _t(np.uint8))
+        q = dope_image_request()
+        q.image, q.channels, q.inv_dist = pi, fg.channels, int(bool(inv_dist))
+        q.clip, q.sigma, q.fg, q.bg = float(clip), float(sigma), fg, bg
+        r = dope_request()
+        r.ndim = len(grid)
+        r.connectivity = int(connectivity)
+        for i in range(len(grid)):
+            r.grid[i] = grid[i]
+            r.block_shape[i] = block[i]
+        r.lambda_ = float(lam)
+        if params is not None:
+            r.params = params
+            r.use_params = 1
+        r.where_inputs = wi
+        r.labels = pl
+        r.where_labels = wl
+        r.tag = int(tag)
+        r.image_request = ctypes.cast(ctypes.pointer(q), ctypes.c_void_p)
+        rid = dope_server_submit(self.srv, r)      # the server copies q
+        self._keep[rid] = (ki, kl)
         return rid
 
     def poll(self, timeout=0.0, cap=256):

@@ -113,7 +113,7 @@ def test_struct_layouts_match_header(lib):
     src = ('#include <stdio.h>\n#include "dope_potentials.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
            'sizeof(dope_params),sizeof(dope_stats),sizeof(dope_profile),sizeof(dope_server_params),'
            'sizeof(dope_request),sizeof(dope_result),sizeof(dope_server_stats),sizeof(dope_tune_result),'
-           'sizeof(dope_gmm));'
+           'sizeof(dope_gmm));printf("%zu\\n",sizeof(dope_image_request));'
            'return 0;}\n')
     inc = os.path.dirname(lib.HEADER)
     with tempfile.TemporaryDirectory() as td:
@@ -124,5 +124,5 @@ def test_struct_layouts_match_header(lib):
         got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(t) for t in (lib.dope_params, lib.dope_stats, lib.dope_profile, lib.dope_server_params,
                                        lib.dope_request, lib.dope_result, lib.dope_server_stats,
-                                       lib.dope_tune_result, lib.dope_gmm)]
+                                       lib.dope_tune_result, lib.dope_gmm, lib.dope_image_request)]
     assert got == want

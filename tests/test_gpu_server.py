@@ -159,3 +159,82 @@ def test_server_rejects_bad_requests(dp):
     with pytest.raises(dp.DopeError):
         srv.submit(d["grid"], 4, d["block"], -1.0, d["u"], d["wq"], np.zeros(4096, np.uint8))
     srv.close()
+
+
+def _mixture(rng, K, scale):
+    w = rng.uniform(0.2, 1.0, K)
+    A = rng.normal(0, scale, (K, 3, 3))
+    cov = A @ A.transpose(0, 2, 1) + scale * scale * np.eye(3)
+    return w / w.sum(), rng.uniform(0, 1, (K, 3)), cov
+
+
+def _image_requests(n, seed):
+    """Ragged RGB requests (regions plus noise) with their colour models."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        H, W = (int(v) for v in rng.integers(30, 150, 2))
+        img = (np.round(rng.uniform(0, 1, (H * W, 3)) * 3) / 3 + rng.normal(0, 0.05, (H * W, 3))).astype(np.float32)
+        out.append({"grid": (H, W), "conn": 4 if rng.random() < 0.5 else 8,
+                    "block": (16, 16) if rng.random() < 0.5 else (32, 32), "lam": float(rng.uniform(1, 8)),
+                    "image": img, "fg": _mixture(rng, 3, 0.1), "bg": _mixture(rng, 2, 0.1)})
+    return out
+
+
+def _collect(srv, n):
+    got, t0 = {}, time.time()
+    while len(got) < n:
+        for r in srv.poll(timeout=1.0):
+            got[r["tag"]] = r
+        assert time.time() - t0 < 300, "server did not finish"
+    return got
+
+
+def test_server_image_requests(dp):
+    """Requests given as images (potentials computed by the server on the GPU)
+    equal the same requests given as the potentials the standalone calls
+    compute: batched and one at a time, host and device images."""
+    torch = pytest.importorskip("torch")
+    reqs = _image_requests(10, 5)
+    for d in reqs:
+        img = torch.from_numpy(d["image"]).cuda()
+        d["u"] = dp.dope_gmm_unaries(img, d["fg"], d["bg"], clip=50.0).cpu().numpy()
+        d["wq"] = dp.dope_contrast_weights(img, d["grid"], d["conn"], channels=3, inv_dist=True)[0].cpu().numpy()
+    ref_lab, ref_res, _ = _run(dp, reqs, mode=0)
+    for mode, on_dev in ((0, False), (1, False), (0, True)):
+        srv = dp.Server(mode=mode)
+        labs = []
+        for i, d in enumerate(reqs):
+            n = int(np.prod(d["grid"]))
+            if on_dev:
+                lab = torch.zeros(n, dtype=torch.uint8, device="cuda")
+                im = torch.from_numpy(d["image"]).cuda()
+                torch.cuda.synchronize()
+            else:
+                lab, im = np.zeros(n, np.uint8), d["image"]
+            srv.submit_image(d["grid"], d["conn"], d["block"], d["lam"], im, d["fg"], d["bg"], lab, clip=50.0,
+                             inv_dist=True, tag=i)
+            labs.append(lab)
+        got = _collect(srv, len(reqs))
+        srv.close()
+        for i in range(len(reqs)):
+            got_lab = labs[i].cpu().numpy() if on_dev else labs[i]
+            assert got[i]["status"] == ref_res[i]["status"] == 0
+            assert got[i]["energy_int"] == ref_res[i]["energy_int"]
+            assert got[i]["iterations"] == ref_res[i]["iterations"]
+            assert np.array_equal(got_lab, ref_lab[i]), (mode, on_dev, i)
+
+
+def test_server_image_request_bad_model(dp):
+    """A covariance that is not positive definite fails that request alone."""
+    reqs = _image_requests(3, 9)
+    srv = dp.Server(mode=0)
+    bad = (np.array([1.0]), np.array([[0.5, 0.5, 0.5]]), np.array([np.diag([0.01, -0.01, 0.01])]))
+    labs = [np.zeros(int(np.prod(d["grid"])), np.uint8) for d in reqs]
+    for i, d in enumerate(reqs):
+        srv.submit_image(d["grid"], d["conn"], d["block"], d["lam"], d["image"], bad if i == 1 else d["fg"], d["bg"],
+                         labs[i], clip=50.0, inv_dist=True, tag=i)
+    got = _collect(srv, 3)
+    srv.close()
+    assert got[1]["status"] == dp.DOPE_EINVAL
+    assert got[0]["status"] == 0 and got[2]["status"] == 0
