@@ -698,7 +698,8 @@ void ov_launch_iteration(dope_ctx* c, int t, double mu, int check_prev, cudaStre
     const OvArgs& A = c->oa;
     k_ov_solve<CONN><<<A.g.K, c->ov_threads, c->ov_smem, st>>>(A, mu, t, check_prev);
     if (mid) cudaEventRecord(mid, st);
-    k_ov_y<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
+    if ((A.gd | A.gh | A.gw) == 0) k_ov_y_q1<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
+    else k_ov_y<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
     k_ov_a<CONN><<<A.g.K, 256, 0, st>>>(A, t);
     c->launches += 3;
 }

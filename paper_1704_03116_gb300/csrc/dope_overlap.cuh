@@ -97,6 +97,9 @@ __global__ void __launch_bounds__(512) k_ov_solve(OvArgs A, double mu, int t, in
     const int bw = g.bw, pl = g.bh * g.bw;
     const double m1024 = __dmul_rn(1024.0, mu);
     const long long c_start = clock64();
+    // zero growth: every q is 1 and M is 1 (Q = I), so in-box neighbours only
+    // give their forward n-link and need neither q nor the backward weight
+    const bool q1 = (A.gd | A.gh | A.gw) == 0;
     // forward n-links and unaries
 #pragma unroll 1
     for (int v = tid; v < B; v += NT) {
@@ -124,6 +127,10 @@ __global__ void __launch_bounds__(512) k_ov_solve(OvArgs A, double mu, int t, in
             if (d < nh) res[d * B + v] = 0;
             if (!in_grid) continue;
             const long long j = ((long long)nz * A.H + ny) * A.W + nx;
+            if (q1 && in_box) {
+                if (d < nh) res[d * B + v] = A.Wl[(long long)d * A.N + i];
+                continue;
+            }
             const int w = (d < nh) ? A.Wl[(long long)d * A.N + i] : A.Wl[(long long)(d - nh) * A.N + j];
             const int qj = A.q[j];
             if (d < nh && in_box) res[d * B + v] = w * ov_frac(1, A.M, qi, qj);
@@ -247,6 +254,56 @@ __global__ void k_ov_y(OvArgs A, double mu) {
         const double yv = __ddiv_rn(Asum, (double)qj);
         const double gq = __dmul_rn((double)G, inv);
         const double tq = __ddiv_rn(__ddiv_rn(gq, mu), (double)qj);
+        A.y[j] = __dsub_rn(yv, tq);
+    }
+}
+
+// Eq. 10 at zero growth (Q = I, M = 1): G_j = sum over the neighbours i of j
+// in other blocks of Wl_ij (yhat_j - yhat_i), the same integer the general
+// form gives, and y_j = (yhat_j + a_j) - (G_j / 1024) / mu with the general
+// form's operations.  Pixels farther than the kernel radius from their
+// block's faces have no such neighbour and skip the neighbourhood.
+template <int CONN>
+__global__ void k_ov_y_q1(OvArgs A, double mu) {
+    if (*(volatile int*)&A.ctrl->conv_t) return;
+    constexpr int nh = CONN / 2;
+    constexpr int R = kernel_radius<CONN>();
+    constexpr bool three_d = CONN == 6 || CONN == 32;
+    const double inv = 1.0 / 1024.0;
+    const int bd = A.g.bd, bh = A.g.bh, bw = A.g.bw;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.N;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(j % A.W);
+        const int y = (int)((j / A.W) % A.H);
+        const int z = (int)(j / ((long long)A.W * A.H));
+        const int kz = z / bd, ky = y / bh, kx = x / bw;
+        const int lz = z - kz * bd, ly = y - ky * bh, lx = x - kx * bw;
+        const long long kl = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B + (lz * bh + ly) * bw + lx;
+        const int yj = A.yhat[kl];
+        const double Asum = __dadd_rn(0.0, __dadd_rn((double)yj, A.a[kl]));
+        long long G = 0;
+        const bool edge = lx < R || lx >= bw - R || ly < R || ly >= bh - R || (three_d && (lz < R || lz >= bd - R));
+        if (edge) {
+#pragma unroll 4
+            for (int d = 0; d < CONN; ++d) {
+                int dz, dy, dx;
+                dir_off<CONN>(d, dz, dy, dx);
+                const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+                if (nlz >= 0 && nlz < bd && nly >= 0 && nly < bh && nlx >= 0 && nlx < bw) continue;   // same block
+                const int iz = z + dz, iy = y + dy, ix = x + dx;
+                if (iz < 0 || iz >= A.D || iy < 0 || iy >= A.H || ix < 0 || ix >= A.W) continue;
+                const long long i = ((long long)iz * A.H + iy) * A.W + ix;
+                const long long w = (d < nh) ? A.Wl[(long long)d * A.N + j] : A.Wl[(long long)(d - nh) * A.N + i];
+                if (!w) continue;
+                const int kzi = iz / bd, kyi = iy / bh, kxi = ix / bw;
+                const long long ki = (long long)((kzi * A.nby + kyi) * A.nbx + kxi) * A.g.B +
+                                     ((iz - kzi * bd) * bh + (iy - kyi * bh)) * bw + (ix - kxi * bw);
+                G += w * (long long)(yj - (int)A.yhat[ki]);
+            }
+        }
+        const double yv = __ddiv_rn(Asum, 1.0);
+        const double gq = __dmul_rn((double)G, inv);
+        const double tq = __ddiv_rn(__ddiv_rn(gq, mu), 1.0);
         A.y[j] = __dsub_rn(yv, tq);
     }
 }
