@@ -398,17 +398,17 @@ void launch_contrast_any(int C, int conn, bool sum, dim3 grid, dim3 block, const
     }
 }
 
+// A few CTAs per SM for the grid-stride kernels (the SM count of the device
+// current at the first call; initialised once, thread-safe).
 int grid_cap() {
-    static int sms = 0;
-    if (!sms) {
+    static const int sms = []() {
         int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            sms = v;
-        else {
-            cudaGetLastError();
-            sms = 152;
-        }
-    }
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            return v;
+        cudaGetLastError();
+        return 152;
+    }();
     return sms * 8;
 }
 
@@ -448,11 +448,13 @@ int pot_weights_issue(const float* img, const int64_t dims[3], int ndim, int C, 
     memset(&G, 0, sizeof(G));
     G.nh = fwd_offsets(ndim, conn, G.off);
     if (!G.nh) return DOPE_EINVAL;
-    for (int a = 0; a < 3; ++a)
+    long long N = 1;
+    for (int a = 0; a < 3; ++a) {
         if (dims[a] < 1 || dims[a] > (1 << 30)) return DOPE_EINVAL;
+        N *= dims[a];                       // < 2^31 * 2^30 at every step
+        if (N >= (1LL << 31)) return DOPE_EINVAL;
+    }
     if (ndim == 2 && dims[0] != 1) return DOPE_EINVAL;
-    const long long N = dims[0] * dims[1] * dims[2];
-    if (N >= (1LL << 31)) return DOPE_EINVAL;
     if (!img || !wq || (!(sigma > 0.0) && !ws) || !isfinite(sigma)) return DOPE_EINVAL;
     G.D = (int)dims[0];
     G.H = (int)dims[1];
@@ -477,8 +479,8 @@ int pot_weights_issue(const float* img, const int64_t dims[3], int ndim, int C, 
     const long long want = grid_cap() / gx > 0 ? grid_cap() / gx : 1;
     const dim3 grid((unsigned)gx, (unsigned)(groups < want ? groups : (want < 65535 ? want : 65535)));
     const dim3 block(bx, by);
-    if (!(sigma > 0.0)) PCK(cudaMemsetAsync(ws, 0, 2 * sizeof(double), st));
     if (!(sigma > 0.0)) {
+        PCK(cudaMemsetAsync(ws, 0, 2 * sizeof(double), st));
         launch_contrast_any(C, conn, true, grid, block, img, G, hb, sigma, pairs, ws, wq, st);
         PCK(cudaGetLastError());
     }

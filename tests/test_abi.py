@@ -101,6 +101,8 @@ def test_potentials_argument_checks(lib):
     for ndim, conn in ((2, 6), (2, 32), (3, 4), (3, 24), (2, 10)):
         assert L.dope_contrast_weights(None, g, ndim, 3, conn, 1.0, 0, None, None, None, None) == lib.DOPE_EINVAL
     assert L.dope_contrast_weights(None, g, 2, 5, 4, 1.0, 0, None, None, None, None) == lib.DOPE_EINVAL
+    huge = (ctypes.c_int64 * 3)(1 << 30, 1 << 30, 1 << 30)             # N far beyond 2^31
+    assert L.dope_contrast_weights(None, huge, 3, 1, 6, 1.0, 0, None, None, None, None) == lib.DOPE_EINVAL
     assert L.dope_set_image(None, None, 3, ctypes.byref(ok), ctypes.byref(ok), 1e5, 0.0, 0, 0, None,
                             None) == lib.DOPE_EINVAL
 
