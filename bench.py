@@ -622,8 +622,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for g, u, w, lab in zip(ctxs, hu, hw, hl):
-            g.set_unaries(u.numpy())
-            g.set_weights(w.numpy())
+            g.set_inputs(u.numpy(), w.numpy())
             g.solve(lab.numpy(), allow_notconv="grow" in insts[0])
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
@@ -648,7 +647,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for g, d, im, lab in zip(ctxs, insts, hi, hl):
-                g.set_image(im.numpy(), d["gmm_fg"], d["gmm_bg"], inv_dist=d["inv_dist"])
+                g.set_image(im.numpy(), d["gmm_fg"], d["gmm_bg"], inv_dist=d["inv_dist"], read_sigma=False)
                 g.solve(lab.numpy(), allow_notconv="grow" in insts[0])
             torch.cuda.synchronize()
             img_ms.append(1e3 * (time.perf_counter() - t0))

@@ -171,6 +171,16 @@ int dope_set_unaries(dope_ctx *ctx, const float *u, int64_t n, int where, void *
  * non-zero, DOPE_EOVERFLOW if some Wl >= 2^24.  Synchronises `stream`. */
 int dope_set_weights(dope_ctx *ctx, const int32_t *wq, int64_t n, int where, void *stream);
 
+/* Unaries and weights together, asynchronously: the same copies and
+ * quantisation as dope_set_unaries + dope_set_weights, with no
+ * synchronisation.  The quantisers' status (DOPE_EOVERFLOW,
+ * DOPE_EUNSUPPORTED, DOPE_EINVAL for the inputs) is reported by the next call
+ * on the context that synchronises (dope_solve reads it with its results, in
+ * its one synchronisation); after such an error both inputs count as unset.
+ * Host inputs are copied on `stream`: they must stay valid and unchanged
+ * until the next synchronising call on the context. */
+int dope_set_inputs(dope_ctx *ctx, const float *u, const int32_t *wq, int64_t n, int where, void *stream);
+
 /* Algorithm 1 from its initial state (y = 1/2, a = 0, mu = mu0) until every
  * block has ||yhat_k - S_k y||_2 <= eps (tested after each iteration, so at
  * least one runs) or max_iter iterations.  Writes labels[N] (image order;

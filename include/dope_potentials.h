@@ -92,9 +92,12 @@ int dope_contrast_weights(const float* image_dev, const int64_t* grid, int ndim,
  * connectivity; the unaries then quantised as by dope_set_unaries, the
  * weights as by dope_set_weights): the image (host or device, `where`) goes
  * through the two calls above into the context's own scratch memory, then
- * into its solver state, with one synchronisation at the end.  The status is
- * dope_set_unaries' or dope_set_weights' (DOPE_EOVERFLOW when a quantised
- * unary or weight leaves its range).  sigma_used may be NULL. */
+ * into its solver state.  With sigma_used != NULL the call synchronises once
+ * at the end and returns the status of dope_set_unaries / dope_set_weights
+ * (DOPE_EOVERFLOW when a quantised unary or weight leaves its range); with
+ * sigma_used == NULL it does not synchronise, and that status is reported by
+ * the next synchronising call on the context, as for dope_set_inputs
+ * (dope.h). */
 int dope_set_image(dope_ctx* ctx, const float* image, int channels, const dope_gmm* fg,
                    const dope_gmm* bg, double clip, double sigma, int inv_dist, int where,
                    double* sigma_used, void* stream);

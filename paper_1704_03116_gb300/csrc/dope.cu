@@ -70,6 +70,7 @@ struct dope_ctx {
     size_t stage2_bytes = 0;
     // host state
     int have_u = 0, have_w = 0;
+    bool pending = false;     // an asynchronous upload's status word not read yet
     int t = 0;          // iterations done since reset
     double mu = 0.0;    // mu the next iteration uses
     dope_stats stats{};
@@ -156,6 +157,22 @@ int read_ctrl(dope_ctx* c, Ctrl* h, cudaStream_t st) {
 
 int clear_status(dope_ctx* c, cudaStream_t st) {
     CK(cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl) - sizeof(unsigned long long), st));
+    return DOPE_OK;
+}
+
+// Settle an asynchronous upload (dope_set_inputs, dope_set_image without
+// sigma_used): read the status word its quantisers wrote (one
+// synchronisation).  An input error invalidates both inputs and is returned.
+int settle_inputs(dope_ctx* c, cudaStream_t st) {
+    if (!c->pending) return DOPE_OK;
+    c->pending = false;
+    Ctrl h{};
+    int rc = read_ctrl(c, &h, st);
+    if (rc) return rc;
+    if (h.status) {
+        c->have_u = c->have_w = 0;
+        return h.status;
+    }
     return DOPE_OK;
 }
 
@@ -350,6 +367,10 @@ int run_persistent(dope_ctx* c, int n, cudaStream_t st) {
 
 // Up to n iterations of Algorithm 1 from the current state.
 int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
+    {
+        const int rc = settle_inputs(c, st);
+        if (rc) return rc;
+    }
     if (!c->have_u || !c->have_w) return DOPE_EINVAL;
     const int t0 = c->t;
     if (n > c->p.max_iter - t0) n = c->p.max_iter - t0;
@@ -1162,6 +1183,7 @@ static int issue_set_unaries(dope_ctx* c, const float* src, cudaStream_t st) {
 int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* stream) {
     if (!c || !u || n != c->g.Nu || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    settle_inputs(c, st);   // an earlier asynchronous upload's error leaves both inputs unset
     const float* src = u;
     if (where == DOPE_HOST) {
         int rc = ensure_stage(c, sizeof(float) * (size_t)n, 0);
@@ -1202,6 +1224,7 @@ static int issue_set_weights(dope_ctx* c, const int32_t* src, cudaStream_t st) {
 int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void* stream) {
     if (!c || !wq || n != c->g.Nu || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    settle_inputs(c, st);   // an earlier asynchronous upload's error leaves both inputs unset
     const int nh = c->conn / 2;
     const int32_t* src = wq;
     if (where == DOPE_HOST) {
@@ -1219,6 +1242,32 @@ int dope_set_weights(dope_ctx* c, const int32_t* wq, int64_t n, int where, void*
     if (rc) return rc;
     c->have_w = (h.status == 0);
     return h.status;
+}
+
+int dope_set_inputs(dope_ctx* c, const float* u, const int32_t* wq, int64_t n, int where, void* stream) {
+    if (!c || !u || !wq || n != c->g.Nu || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    c->pending = false;   // both inputs are replaced
+    const size_t nu = (size_t)n, nh = (size_t)(c->conn / 2);
+    const float* su = u;
+    const int32_t* sw = wq;
+    if (where == DOPE_HOST) {
+        const size_t off_w = (sizeof(float) * nu + 255) & ~(size_t)255;
+        int rc = ensure_stage(c, off_w + sizeof(int32_t) * nu * nh, 0);
+        if (rc) return rc;
+        char* base = (char*)c->stage;
+        CK(cudaMemcpyAsync(base, u, sizeof(float) * nu, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(base + off_w, wq, sizeof(int32_t) * nu * nh, cudaMemcpyHostToDevice, st));
+        su = (const float*)base;
+        sw = (const int32_t*)(base + off_w);
+    }
+    int rc = clear_status(c, st);
+    if (!rc) rc = issue_set_unaries(c, su, st);
+    if (!rc) rc = issue_set_weights(c, sw, st);
+    if (rc) return rc;
+    c->have_u = c->have_w = 1;   // provisional: the status is read by the next synchronising call
+    c->pending = true;
+    return DOPE_OK;
 }
 
 // Potentials of an image into the context's staging memory, then the
@@ -1262,8 +1311,15 @@ int dope_set_image(dope_ctx* c, const float* image, int channels, const dope_gmm
                    double clip, double sigma, int inv_dist, int where, double* sigma_used, void* stream) {
     cudaStream_t st = S(stream);
     double* ws = nullptr;
+    if (c) c->pending = false;   // both inputs are replaced
     int rc = image_issue(c, image, channels, fg, bg, clip, sigma, inv_dist, where, st, nullptr, &ws);
     if (rc) return rc;
+    if (!sigma_used) {
+        // asynchronous: the status is read by the next synchronising call
+        c->have_u = c->have_w = 1;
+        c->pending = true;
+        return DOPE_OK;
+    }
     double sig = sigma;
     if (!(sigma > 0.0)) CK(cudaMemcpyAsync(&sig, ws + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     Ctrl h{};
@@ -1328,8 +1384,20 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
         }
         const int n = c->p.max_iter;
         memset(&c->stats, 0, sizeof(c->stats));
-        int rc = clear_status(c, st);
-        if (rc) return rc;
+        // an asynchronous upload's status word stays (it is read with the
+        // rest of the control block at the end); everything else is cleared
+        const bool pend = c->pending;
+        c->pending = false;
+        if (pend) {
+            static_assert(offsetof(Ctrl, status) == sizeof(int), "status follows conv_t");
+            CK(cudaMemsetAsync(c->ctrl, 0, sizeof(int), st));
+            CK(cudaMemsetAsync((char*)c->ctrl + 2 * sizeof(int), 0,
+                               sizeof(Ctrl) - sizeof(unsigned long long) - 2 * sizeof(int), st));
+        } else {
+            const int rc0 = clear_status(c, st);
+            if (rc0) return rc0;
+        }
+        int rc = DOPE_OK;
         CK(cudaMemsetAsync(&c->ctrl->r2max[1], 0, sizeof(unsigned long long) * (size_t)n, st));
         uint8_t* dst = labels;
         if (where == DOPE_HOST) {
@@ -1344,7 +1412,11 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
         CK(cudaMemcpyAsync(c->hctrl, c->ctrl, c->ctrl_bytes, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         rc = persistent_collect(c, 0, *c->hctrl, c->hctrl->r2max, st);
-        if (rc) return rc;
+        if (rc) {
+            if (pend && (rc == DOPE_EINVAL || rc == DOPE_EUNSUPPORTED || rc == DOPE_EOVERFLOW))
+                c->have_u = c->have_w = 0;   // the upload's error: its inputs are not usable
+            return rc;
+        }
         if (energy_int) *energy_int = (int64_t)c->hctrl->energy;
         c->stats.kernel_launches = c->launches;
         if (iterations) *iterations = c->t;
@@ -1409,6 +1481,7 @@ int dope_set_state(dope_ctx* c, const double* y, const double* a, const uint8_t*
     if (!c || !y || !a || !yhat || t < 0 || t > c->p.max_iter || !(mu > 0.0)) return DOPE_EINVAL;
     if (c->ov) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    settle_inputs(c, st);
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 17, 1);
     if (rc) return rc;
@@ -1440,6 +1513,10 @@ int dope_shifted_caps(dope_ctx* c, int64_t* C, void* stream) {
     if (!c || !C || !c->have_u || !c->have_w) return DOPE_EINVAL;
     if (c->ov) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    {
+        const int rs = settle_inputs(c, st);
+        if (rs) return rs;
+    }
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 8, 1);
     if (rc) return rc;
@@ -1463,6 +1540,10 @@ int dope_block_cuts(dope_ctx* c, const int64_t* C, uint8_t* yhat, void* stream) 
     if (!c || !C || !yhat || !c->have_w) return DOPE_EINVAL;
     if (c->ov || c->nsm) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    {
+        const int rs = settle_inputs(c, st);
+        if (rs) return rs;
+    }
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, N * 17, 1);
     if (rc) return rc;
@@ -1498,6 +1579,10 @@ int dope_block_cuts(dope_ctx* c, const int64_t* C, uint8_t* yhat, void* stream) 
 int dope_energy(dope_ctx* c, const uint8_t* labels, int where, int64_t* energy_int, void* stream) {
     if (!c || !labels || !energy_int || !c->have_u || !c->have_w) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
+    {
+        const int rs = settle_inputs(c, st);
+        if (rs) return rs;
+    }
     const size_t N = (size_t)c->g.N;
     int rc = ensure_stage(c, 2 * N, 1);
     if (rc) return rc;
@@ -2199,8 +2284,12 @@ extern "C" int dope_iterate_batch(dope_ctx* const* ctxs, int n, int n_iter, int*
     }
     dope_batch_ws* w = g_batch_ws[dev];
     cudaStream_t st = S(stream);
-    for (int i = 0; i < n; ++i)
-        if (ctxs[i]) ctxs[i]->launches = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) continue;
+        const int rs = settle_inputs(ctxs[i], st);
+        if (rs) return rs;
+        ctxs[i]->launches = 0;
+    }
     int rc = dope_batch_launch(ctxs, n, n_iter, 0, 1, nullptr, w, st);
     if (rc) return rc;
     CK(cudaStreamSynchronize(st));
@@ -2216,9 +2305,10 @@ extern "C" int dope_iterate_batch(dope_ctx* const* ctxs, int n, int n_iter, int*
 
 extern "C" int dope_labels(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, void* stream) {
     if (!c || !labels || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
-    if (!c->have_u || !c->have_w) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
-    int rc;
+    int rc = settle_inputs(c, st);
+    if (rc) return rc;
+    if (!c->have_u || !c->have_w) return DOPE_EINVAL;
     if (c->ov) {
         uint8_t* dst = labels;
         if (where == DOPE_HOST) {

@@ -117,6 +117,7 @@ def _load():
         "dope_create": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params), P(vp)]),
         "dope_set_unaries": (i32, [vp, vp, i64, i32, vp]),
         "dope_set_weights": (i32, [vp, vp, i64, i32, vp]),
+        "dope_set_inputs": (i32, [vp, vp, vp, i64, i32, vp]),
         "dope_solve": (i32, [vp, vp, i32, P(ctypes.c_int64), P(ctypes.c_int), vp]),
         "dope_reset": (i32, [vp]),
         "dope_iterate": (i32, [vp, i32, P(ctypes.c_int), P(ctypes.c_int), vp]),
@@ -243,6 +244,19 @@ def dope_set_weights(ctx, wq, stream=None):
     if n is None:
         raise ValueError("wq must be [conn/2, N]")
     _check(_lib.dope_set_weights(ctx, p, n, where, _stream(stream)), "dope_set_weights")
+
+
+def dope_set_inputs(ctx, u, wq, stream=None):
+    """Unaries and weights together, asynchronously (the status is reported
+    by the next synchronising call, e.g. dope_solve)."""
+    pu, wu, ku = _ptr(u, _t(np.float32))
+    pw, ww, kw = _ptr(wq, _t(np.int32))
+    if wu != ww:
+        raise TypeError("unaries and weights must both be host or both device arrays")
+    if len(kw.shape) != 2:
+        raise ValueError("wq must be [conn/2, N]")
+    _check(_lib.dope_set_inputs(ctx, pu, pw, int(np.prod(ku.shape)), wu, _stream(stream)), "dope_set_inputs")
+    return ku, kw
 
 
 def dope_solve(ctx, labels, stream=None, allow_notconv=False):
@@ -567,16 +581,20 @@ def dope_contrast_weights(image, grid, connectivity, channels=1, sigma=0.0, inv_
     return out, (sig.value if read_sigma else None)
 
 
-def dope_set_image(ctx, image, fg, bg, clip=1.0e5, sigma=0.0, inv_dist=False, channels=None, stream=None):
+def dope_set_image(ctx, image, fg, bg, clip=1.0e5, sigma=0.0, inv_dist=False, channels=None, stream=None,
+                   read_sigma=True):
     """Both potentials of an image (CUDA tensor or host array, [..., C])
-    straight into a context; returns the sigma used."""
+    straight into a context; returns the sigma used.  read_sigma=False: no
+    synchronisation (returns None; the status is reported by the next
+    synchronising call)."""
     fg, bg = _as_gmm(fg), _as_gmm(bg)
     C = fg.channels if channels is None else int(channels)
     p, where, keep = _ptr(image, _t(np.float32))
     sig = ctypes.c_double(0.0)
     _check(_lib.dope_set_image(ctx, p, C, ctypes.byref(fg), ctypes.byref(bg), float(clip), float(sigma),
-                               int(bool(inv_dist)), where, ctypes.byref(sig), _stream(stream)), "dope_set_image")
-    return sig.value
+                               int(bool(inv_dist)), where, ctypes.byref(sig) if read_sigma else None,
+                               _stream(stream)), "dope_set_image")
+    return sig.value if read_sigma else None
 
 
 class Dope:
@@ -615,9 +633,15 @@ class Dope:
     def set_weights(self, wq, stream=None):
         dope_set_weights(self.ctx, wq, stream)
 
-    def set_image(self, image, fg, bg, clip=1.0e5, sigma=0.0, inv_dist=False, stream=None):
-        """Unaries and weights computed on the GPU from the image; returns sigma."""
-        return dope_set_image(self.ctx, image, fg, bg, clip, sigma, inv_dist, stream=stream)
+    def set_image(self, image, fg, bg, clip=1.0e5, sigma=0.0, inv_dist=False, stream=None, read_sigma=True):
+        """Unaries and weights computed on the GPU from the image; returns sigma
+        (None with read_sigma=False, which does not synchronise)."""
+        return dope_set_image(self.ctx, image, fg, bg, clip, sigma, inv_dist, stream=stream, read_sigma=read_sigma)
+
+    def set_inputs(self, u, wq, stream=None):
+        """Unaries and weights together, without synchronising (errors are
+        reported by the next solve)."""
+        self._inputs = dope_set_inputs(self.ctx, u, wq, stream)
 
     def solve(self, labels=None, stream=None, allow_notconv=False):
         """(labels, E = E_int / 1024, iterations)."""
