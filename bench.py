@@ -621,9 +621,12 @@ def main():
         flush.fill_((s + 1) & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        # every solve of the step queued, then one wait per solve
         for g, u, w, lab in zip(ctxs, hu, hw, hl):
             g.set_inputs(u.numpy(), w.numpy())
-            g.solve(lab.numpy(), allow_notconv="grow" in insts[0])
+            g.solve_begin(lab.numpy())
+        for g in ctxs:
+            g.solve_end(allow_notconv="grow" in insts[0])
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
@@ -648,7 +651,9 @@ def main():
             t0 = time.perf_counter()
             for g, d, im, lab in zip(ctxs, insts, hi, hl):
                 g.set_image(im.numpy(), d["gmm_fg"], d["gmm_bg"], inv_dist=d["inv_dist"], read_sigma=False)
-                g.solve(lab.numpy(), allow_notconv="grow" in insts[0])
+                g.solve_begin(lab.numpy())
+            for g in ctxs:
+                g.solve_end(allow_notconv="grow" in insts[0])
             torch.cuda.synchronize()
             img_ms.append(1e3 * (time.perf_counter() - t0))
         barrier()

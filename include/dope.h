@@ -190,6 +190,19 @@ int dope_set_inputs(dope_ctx *ctx, const float *u, const int32_t *wq, int64_t n,
 int dope_solve(dope_ctx *ctx, uint8_t *labels, int where, int64_t *energy_int,
                int *iterations, void *stream);
 
+/* dope_solve in two halves, so that several solves (on one or more contexts)
+ * can be queued before the host waits.  dope_solve_begin issues the solve on
+ * `stream` and returns without synchronising when the solve is one launch
+ * (the default launch mode on a partition without overlap, submodular
+ * weights); other contexts solve inside it.  dope_solve_end synchronises
+ * `stream` and returns what dope_solve returns (status, E_int, iterations);
+ * the labels are in `labels` once it has returned.  Between the two calls the
+ * context takes no other call; host labels and inputs must stay valid until
+ * dope_solve_end.  DOPE_EINVAL: a second begin without an end, or an end
+ * without a begin. */
+int dope_solve_begin(dope_ctx *ctx, uint8_t *labels, int where, void *stream);
+int dope_solve_end(dope_ctx *ctx, int64_t *energy_int, int *iterations, void *stream);
+
 /* Reset the ADMM state to y = 1/2, a = 0, mu = mu0, t = 0 (Algorithm 1,
  * Initialization). */
 int dope_reset(dope_ctx *ctx);

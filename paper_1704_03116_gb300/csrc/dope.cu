@@ -71,6 +71,10 @@ struct dope_ctx {
     // host state
     int have_u = 0, have_w = 0;
     bool pending = false;     // an asynchronous upload's status word not read yet
+    int begun = 0;            // dope_solve_begin: 1 launch issued, 2 solved synchronously
+    bool begun_pend = false;  // the issued launch carries an upload's status word
+    int sync_rc = 0, sync_iters = 0;
+    int64_t sync_energy = 0;
     int t = 0;          // iterations done since reset
     double mu = 0.0;    // mu the next iteration uses
     dope_stats stats{};
@@ -1337,7 +1341,7 @@ int dope_reset(dope_ctx* c) {
 }
 
 int dope_iterate(dope_ctx* c, int n_iter, int* iterations_done, int* converged, void* stream) {
-    if (!c || n_iter < 0) return DOPE_EINVAL;
+    if (!c || n_iter < 0 || c->begun) return DOPE_EINVAL;
     c->launches = 0;
     int rc = run_iterations(c, n_iter, S(stream));
     if (rc) return rc;
@@ -1346,9 +1350,73 @@ int dope_iterate(dope_ctx* c, int n_iter, int* iterations_done, int* converged, 
     return DOPE_OK;
 }
 
+// A solve of this context is one persistent launch (the resident or the
+// persistent kernel runs Algorithm 1 from its initial state to the labels).
+static bool single_launch(const dope_ctx* c) {
+    return !c->ov && !c->nsm && c->p.launch_mode != 1 && c->persist_grid > 0 && c->p.max_iter > 0;
+}
+
+// First half of a single-launch solve: clear the control block (keeping an
+// asynchronous upload's status word), the launch, the labels copied out and
+// the control block copied to pinned host memory.  No synchronisation.
+static int solve_issue(dope_ctx* c, uint8_t* labels, int where, int want_energy, cudaStream_t st) {
+    if (!c->hctrl && cudaMallocHost(&c->hctrl, c->ctrl_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->hctrl = nullptr;
+        return DOPE_ENOMEM;
+    }
+    c->t = 0;
+    c->mu = c->p.mu0;
+    const int n = c->p.max_iter;
+    memset(&c->stats, 0, sizeof(c->stats));
+    const bool pend = c->pending;
+    c->pending = false;
+    c->begun_pend = pend;
+    if (pend) {
+        static_assert(offsetof(Ctrl, status) == sizeof(int), "status follows conv_t");
+        CK(cudaMemsetAsync(c->ctrl, 0, sizeof(int), st));
+        CK(cudaMemsetAsync((char*)c->ctrl + 2 * sizeof(int), 0,
+                           sizeof(Ctrl) - sizeof(unsigned long long) - 2 * sizeof(int), st));
+    } else {
+        const int rc0 = clear_status(c, st);
+        if (rc0) return rc0;
+    }
+    CK(cudaMemsetAsync(&c->ctrl->r2max[1], 0, sizeof(unsigned long long) * (size_t)n, st));
+    uint8_t* dst = labels;
+    if (where == DOPE_HOST) {
+        const int rc = ensure_stage(c, (size_t)c->g.Nu, 1);
+        if (rc) return rc;
+        dst = (uint8_t*)c->stage2;
+    }
+    c->launches = 0;
+    const int rc = persistent_issue(c, n, st, dst, want_energy);
+    if (rc) return rc;
+    if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->hctrl, c->ctrl, c->ctrl_bytes, cudaMemcpyDeviceToHost, st));
+    return DOPE_OK;
+}
+
+// Second half, once the stream has passed the copies: the results from the
+// pinned control block.
+static int solve_collect(dope_ctx* c, int64_t* energy_int, int* iterations, cudaStream_t st) {
+    const bool pend = c->begun_pend;
+    c->begun_pend = false;
+    const int rc = persistent_collect(c, 0, *c->hctrl, c->hctrl->r2max, st);
+    if (rc) {
+        if (pend && (rc == DOPE_EINVAL || rc == DOPE_EUNSUPPORTED || rc == DOPE_EOVERFLOW))
+            c->have_u = c->have_w = 0;   // the upload's error: its inputs are not usable
+        return rc;
+    }
+    if (energy_int) *energy_int = (int64_t)c->hctrl->energy;
+    c->stats.kernel_launches = c->launches;
+    if (iterations) *iterations = c->t;
+    return c->stats.converged ? DOPE_OK : DOPE_ENOTCONV;
+}
+
 int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int* iterations,
                void* stream) {
     if (!c || !labels || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    if (c->begun) return DOPE_EINVAL;   // a dope_solve_begin awaits its dope_solve_end
     if (!c->have_u || !c->have_w) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
     if (c->ov) {
@@ -1373,54 +1441,14 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
     c->mu = c->p.mu0;
     c->launches = 1;
     const int threads = 256;
-    if (!c->nsm && c->p.launch_mode != 1 && c->persist_grid > 0 && c->p.max_iter > 0) {
+    if (single_launch(c)) {
         // one persistent launch that also starts from y = 1/2, a = 0 and
         // finishes with the labels and their energy, then one read of the whole
         // control block: a single launch and a single synchronisation per solve
-        if (!c->hctrl && cudaMallocHost(&c->hctrl, c->ctrl_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            c->hctrl = nullptr;
-            return DOPE_ENOMEM;
-        }
-        const int n = c->p.max_iter;
-        memset(&c->stats, 0, sizeof(c->stats));
-        // an asynchronous upload's status word stays (it is read with the
-        // rest of the control block at the end); everything else is cleared
-        const bool pend = c->pending;
-        c->pending = false;
-        if (pend) {
-            static_assert(offsetof(Ctrl, status) == sizeof(int), "status follows conv_t");
-            CK(cudaMemsetAsync(c->ctrl, 0, sizeof(int), st));
-            CK(cudaMemsetAsync((char*)c->ctrl + 2 * sizeof(int), 0,
-                               sizeof(Ctrl) - sizeof(unsigned long long) - 2 * sizeof(int), st));
-        } else {
-            const int rc0 = clear_status(c, st);
-            if (rc0) return rc0;
-        }
-        int rc = DOPE_OK;
-        CK(cudaMemsetAsync(&c->ctrl->r2max[1], 0, sizeof(unsigned long long) * (size_t)n, st));
-        uint8_t* dst = labels;
-        if (where == DOPE_HOST) {
-            rc = ensure_stage(c, (size_t)c->g.Nu, 1);
-            if (rc) return rc;
-            dst = (uint8_t*)c->stage2;
-        }
-        c->launches = 0;
-        rc = persistent_issue(c, n, st, dst, energy_int ? 1 : 0);
+        int rc = solve_issue(c, labels, where, energy_int ? 1 : 0, st);
         if (rc) return rc;
-        if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(c->hctrl, c->ctrl, c->ctrl_bytes, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        rc = persistent_collect(c, 0, *c->hctrl, c->hctrl->r2max, st);
-        if (rc) {
-            if (pend && (rc == DOPE_EINVAL || rc == DOPE_EUNSUPPORTED || rc == DOPE_EOVERFLOW))
-                c->have_u = c->have_w = 0;   // the upload's error: its inputs are not usable
-            return rc;
-        }
-        if (energy_int) *energy_int = (int64_t)c->hctrl->energy;
-        c->stats.kernel_launches = c->launches;
-        if (iterations) *iterations = c->t;
-        return c->stats.converged ? DOPE_OK : DOPE_ENOTCONV;
+        return solve_collect(c, energy_int, iterations, st);
     }
     k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads, 0, st>>>(c->g, c->yF, c->aF);
     CK(cudaGetLastError());
@@ -1444,6 +1472,41 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
     c->stats.kernel_launches = c->launches;
     if (iterations) *iterations = c->t;
     return c->stats.converged ? DOPE_OK : DOPE_ENOTCONV;
+}
+
+int dope_solve_begin(dope_ctx* c, uint8_t* labels, int where, void* stream) {
+    if (!c || !labels || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
+    if (c->begun) return DOPE_EINVAL;
+    if (!c->have_u || !c->have_w) return DOPE_EINVAL;
+    cudaStream_t st = S(stream);
+    if (single_launch(c)) {
+        const int rc = solve_issue(c, labels, where, 1, st);
+        if (rc) return rc;
+        c->begun = 1;
+        return DOPE_OK;
+    }
+    // other contexts solve here; dope_solve_end returns the outcome
+    int64_t e = 0;
+    int it = 0;
+    c->sync_rc = dope_solve(c, labels, where, &e, &it, stream);
+    c->sync_energy = e;
+    c->sync_iters = it;
+    c->begun = 2;
+    return DOPE_OK;
+}
+
+int dope_solve_end(dope_ctx* c, int64_t* energy_int, int* iterations, void* stream) {
+    if (!c || !c->begun) return DOPE_EINVAL;
+    const int how = c->begun;
+    c->begun = 0;
+    if (how == 2) {
+        if (energy_int) *energy_int = c->sync_energy;
+        if (iterations) *iterations = c->sync_iters;
+        return c->sync_rc;
+    }
+    cudaStream_t st = S(stream);
+    CK(cudaStreamSynchronize(st));
+    return solve_collect(c, energy_int, iterations, st);
 }
 
 int dope_get_state(dope_ctx* c, double* y, double* a, uint8_t* yhat, double* mu, int* t, void* stream) {

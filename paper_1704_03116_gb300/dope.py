@@ -119,6 +119,8 @@ def _load():
         "dope_set_weights": (i32, [vp, vp, i64, i32, vp]),
         "dope_set_inputs": (i32, [vp, vp, vp, i64, i32, vp]),
         "dope_solve": (i32, [vp, vp, i32, P(ctypes.c_int64), P(ctypes.c_int), vp]),
+        "dope_solve_begin": (i32, [vp, vp, i32, vp]),
+        "dope_solve_end": (i32, [vp, P(ctypes.c_int64), P(ctypes.c_int), vp]),
         "dope_reset": (i32, [vp]),
         "dope_iterate": (i32, [vp, i32, P(ctypes.c_int), P(ctypes.c_int), vp]),
         "dope_get_state": (i32, [vp, vp, vp, vp, P(ctypes.c_double), P(ctypes.c_int), vp]),
@@ -649,6 +651,31 @@ class Dope:
             labels = np.empty(self.n, np.uint8)
         e, it, _ = dope_solve(self.ctx, labels, stream, allow_notconv)
         return labels, e / 1024.0, it
+
+    def solve_begin(self, labels=None, stream=None):
+        """Issue a solve without waiting (see solve_end); returns the labels
+        buffer, valid once solve_end has returned."""
+        if labels is None:
+            labels = np.empty(self.n, np.uint8)
+        if isinstance(labels, np.ndarray):
+            if labels.dtype != np.uint8 or not labels.flags.c_contiguous:
+                raise TypeError("labels must be a contiguous uint8 array")
+            p, where, keep = ctypes.c_void_p(labels.ctypes.data), DOPE_HOST, labels
+        else:
+            p, where, keep = _ptr(labels, _t(np.uint8))
+        _check(_lib.dope_solve_begin(self.ctx, p, where, _stream(stream)), "dope_solve_begin")
+        self._begun = keep
+        return labels
+
+    def solve_end(self, stream=None, allow_notconv=False):
+        """Wait for the solve solve_begin issued: (labels, E = E_int / 1024, iterations)."""
+        e = ctypes.c_int64(0)
+        it = ctypes.c_int(0)
+        rc = _lib.dope_solve_end(self.ctx, ctypes.byref(e), ctypes.byref(it), _stream(stream))
+        labels, self._begun = getattr(self, "_begun", None), None
+        if not (rc == DOPE_ENOTCONV and allow_notconv):
+            _check(rc, "dope_solve_end")
+        return labels, e.value / 1024.0, it.value
 
     def iterate(self, n, stream=None):
         return dope_iterate(self.ctx, n, stream)

@@ -123,3 +123,71 @@ def test_set_image_async_equals_sync(dp):
     assert sig > 0 and ia == ib and ea == eb and np.array_equal(la, lb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("name,grid,conn,block,kw", CASES, ids=[c[0] for c in CASES])
+def test_solve_begin_end_equals_solve(dp, name, grid, conn, block, kw):
+    u, wq = _instance(name, grid, conn, block)
+    notconv = "grow" in kw or "lsa_steps" in kw
+    a = dp.Dope(grid, conn, block, 2.0, **kw)
+    a.set_inputs(u, wq)
+    la, ea, ia = a.solve(allow_notconv=notconv)
+    a.set_inputs(u, wq)
+    lab = a.solve_begin()
+    lb, eb, ib = a.solve_end(allow_notconv=notconv)
+    assert lb is lab and ia == ib and ea == eb and np.array_equal(la, lb)
+    a.close()
+
+
+def test_solves_queued_on_several_contexts(dp):
+    """Several contexts begun on one stream, then ended (in reverse order):
+    each result equals its own dope_solve."""
+    torch = pytest.importorskip("torch")
+    ds = [inputs.random_instance((96, 128), 8, (32, 32), lam=float(l), seed=l) for l in (1, 3, 9)]
+    ref = []
+    for d in ds:
+        g = dp.Dope(d["grid"], 8, d["block"], d["lam"])
+        g.set_inputs(d["u"], d["wq"])
+        ref.append(g.solve())
+        g.close()
+    gs = [dp.Dope(d["grid"], 8, d["block"], d["lam"]) for d in ds]
+    labs = [torch.zeros(96 * 128, dtype=torch.uint8).pin_memory() for _ in ds]
+    for g, d, lab in zip(gs, ds, labs):
+        g.set_inputs(d["u"], d["wq"])
+        g.solve_begin(lab.numpy())
+    out = {}
+    for i in (2, 0, 1):
+        out[i] = gs[i].solve_end()
+    for i, (l0, e0, i0) in enumerate(ref):
+        l1, e1, i1 = out[i]
+        assert i0 == i1 and e0 == e1 and np.array_equal(l0, l1) and np.array_equal(labs[i].numpy(), l0)
+    for g in gs:
+        g.close()
+
+
+def test_solve_begin_end_misuse_and_deferred_error(dp):
+    d = inputs.random_instance((64, 64), 8, (32, 32), lam=1.0, seed=5)
+    g = dp.Dope((64, 64), 8, (32, 32), 1.0)
+    with pytest.raises(dp.DopeError) as ei:                # end without begin
+        g.solve_end()
+    assert ei.value.status == dp.DOPE_EINVAL
+    g.set_inputs(d["u"], d["wq"])
+    g.solve_begin()
+    with pytest.raises(dp.DopeError) as ei:                # a second begin
+        g.solve_begin()
+    assert ei.value.status == dp.DOPE_EINVAL
+    with pytest.raises(dp.DopeError) as ei:                # dope_solve while begun
+        g.solve()
+    assert ei.value.status == dp.DOPE_EINVAL
+    g.solve_end()
+    bad = d["wq"].copy()
+    bad[2, 7] = 1 << 24
+    g.set_inputs(d["u"], bad)
+    g.solve_begin()                                        # issued: the error is not known yet
+    with pytest.raises(dp.DopeError) as ei:
+        g.solve_end()
+    assert ei.value.status == dp.DOPE_EOVERFLOW
+    with pytest.raises(dp.DopeError) as ei:                # inputs now unset
+        g.solve_begin()
+    assert ei.value.status == dp.DOPE_EINVAL
+    g.close()
