@@ -612,6 +612,7 @@ def main():
             "time_share": share}
 
     # ---- end to end through the C-ABI with pinned host buffers ---------
+    up = torch.cuda.Stream()
     hu = [torch.from_numpy(d["u"]).pin_memory() for d in insts]
     hw = [torch.from_numpy(np.ascontiguousarray(d["wq"])).pin_memory() for d in insts]
     hl = [torch.empty(g.n, dtype=torch.uint8).pin_memory() for g in ctxs]
@@ -621,12 +622,16 @@ def main():
         flush.fill_((s + 1) & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        # every solve of the step queued, then one wait per solve
+        # every solve of the step queued, then one wait per solve; inputs go
+        # up on their own stream, each solve ordered after its upload
         for g, u, w, lab in zip(ctxs, hu, hw, hl):
-            g.set_inputs(u.numpy(), w.numpy())
-            g.solve_begin(lab.numpy())
+            g.set_inputs(u.numpy(), w.numpy(), stream=up.cuda_stream)
+            ev_up = torch.cuda.Event()
+            ev_up.record(up)
+            stream.wait_event(ev_up)
+            g.solve_begin(lab.numpy(), stream=stream.cuda_stream)
         for g in ctxs:
-            g.solve_end(allow_notconv="grow" in insts[0])
+            g.solve_end(stream=stream.cuda_stream, allow_notconv="grow" in insts[0])
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
@@ -650,10 +655,14 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for g, d, im, lab in zip(ctxs, insts, hi, hl):
-                g.set_image(im.numpy(), d["gmm_fg"], d["gmm_bg"], inv_dist=d["inv_dist"], read_sigma=False)
-                g.solve_begin(lab.numpy())
+                g.set_image(im.numpy(), d["gmm_fg"], d["gmm_bg"], inv_dist=d["inv_dist"], read_sigma=False,
+                            stream=up.cuda_stream)
+                ev_up = torch.cuda.Event()
+                ev_up.record(up)
+                stream.wait_event(ev_up)
+                g.solve_begin(lab.numpy(), stream=stream.cuda_stream)
             for g in ctxs:
-                g.solve_end(allow_notconv="grow" in insts[0])
+                g.solve_end(stream=stream.cuda_stream, allow_notconv="grow" in insts[0])
             torch.cuda.synchronize()
             img_ms.append(1e3 * (time.perf_counter() - t0))
         barrier()
