@@ -35,6 +35,24 @@ PROFILES = os.path.join(ROOT, "profiles")
 KERNEL_SRC = os.path.join(ROOT, "paper_1704_03116_gb300", "csrc", "dope_kernels.cuh")
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """The largest value over the ranks (a job's time is its slowest rank's);
+    the value itself for one process."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank in at most `seconds` (the slowest rank's time)."""
+    return world * units_per_rank / seconds
+
+
 def workload(name):
     from paper_1704_03116_gb300 import inputs
     if name == "ellipses512":
@@ -567,12 +585,8 @@ def main():
     lat = [a.elapsed_time(b) for a, b in ev]
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     t_local = sum(step_ms) / 1e3
-    t_max = t_local
-    if world > 1:
-        tt = torch.tensor([t_local], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * n_px * args.steps / t_max
+    t_max = max_over_ranks(t_local, world)
+    value = job_rate(n_px * args.steps, world, t_max)
     profs = [g.profile() for g in ctxs]
     for g in ctxs:
         g.set_profiling(False)
@@ -644,11 +658,7 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
-    e2e_t = sum(e2e_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([e2e_t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
+    e2e_t = max_over_ranks(sum(e2e_ms) / 1e3, world)
     h2d = sum(d["u"].nbytes + d["wq"].nbytes for d in insts)
     d2h = sum(g.n for g in ctxs) + 8 * len(ctxs)
 
@@ -675,12 +685,8 @@ def main():
             torch.cuda.synchronize()
             img_ms.append(1e3 * (time.perf_counter() - t0))
         barrier()
-        t_img = sum(img_ms) / 1e3
-        if world > 1:
-            tt = torch.tensor([t_img], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_img = float(tt.item())
-        e2e_img = {"value": world * n_px * args.steps / t_img, "unit": "pixels/s",
+        t_img = max_over_ranks(sum(img_ms) / 1e3, world)
+        e2e_img = {"value": job_rate(n_px * args.steps, world, t_img), "unit": "pixels/s",
                    "h2d_bytes_per_step": sum(im.numel() * 4 for im in hi), "d2h_bytes_per_step": d2h,
                    "ms_per_step": statistics.mean(img_ms),
                    "note": "image in; mixture data term and contrast weights computed on the GPU"}
@@ -696,7 +702,7 @@ def main():
             "iterations": sorted(set(iters)), "energies": sorted(set(energies)),
             "converged": [bool(g.stats()["converged"]) for g in ctxs],
             "wall_s": wall, "gpu_launches": launches, "roofline": roof, "clocks": clk,
-            "e2e": {"value": world * n_px * args.steps / e2e_t, "unit": "pixels/s",
+            "e2e": {"value": job_rate(n_px * args.steps, world, e2e_t), "unit": "pixels/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)}}
     if e2e_img:

@@ -99,6 +99,9 @@ typedef struct {
                             local submodular approximation, each step an exact block cut) with at
                             most lsa_steps steps per block and iteration.  Such contexts run two
                             launches per iteration, Q = I only. */
+    int barrier_timeout_us;  /* longest wait at a grid barrier of the one-launch solve before the
+                            launch gives up: every CTA leaves, the call returns DOPE_ETIMEOUT and
+                            the context stays usable.  0 (default): about 2 s. */
 } dope_params;
 
 /* Statistics of the last dope_solve / dope_iterate call. */

@@ -71,6 +71,7 @@ struct dope_ctx {
     // host state
     int have_u = 0, have_w = 0;
     bool pending = false;     // an asynchronous upload's status word not read yet
+    long long spin_limit = 4000000000LL;   // grid-barrier wait bound in SM cycles (about 2 s)
     int begun = 0;            // dope_solve_begin: 1 launch issued, 2 solved synchronously
     bool begun_pend = false;  // the issued launch carries an upload's status word
     int sync_rc = 0, sync_iters = 0;
@@ -293,7 +294,7 @@ int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = 
     P.n = n;
     P.mu_start = c->mu;
     P.mu_fact = c->p.mu_fact;
-    P.spin_limit = 4000000000LL;   // about 2 s at the GB300 clock
+    P.spin_limit = c->spin_limit;
     P.dynamic = c->persist_grid < c->g.K;
     P.window = c->window_ok && c->p.launch_mode == 0;
     P.NH = c->NH;
@@ -1008,6 +1009,16 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
     if (c->p.relabel_period <= 0) c->p.relabel_period = 8;
     if (c->p.max_pulses <= 0) c->p.max_pulses = (int)(64 * B + 4096);
     if (c->p.fold_rounds <= 0) c->p.fold_rounds = MAX_FOLD_ROUNDS;
+    if (c->p.barrier_timeout_us > 0) {
+        // SM cycles from the device's clock rate (kHz)
+        int dev = 0, khz = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess ||
+            khz <= 0) {
+            cudaGetLastError();
+            khz = 2070000;
+        }
+        c->spin_limit = (long long)c->p.barrier_timeout_us * (long long)khz / 1000LL + 1;
+    }
     {
         int grow3[3] = {0, 0, 0};
         bool any = false;

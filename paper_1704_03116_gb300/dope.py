@@ -38,7 +38,8 @@ class dope_params(ctypes.Structure):
     _fields_ = [("mu0", ctypes.c_double), ("mu_fact", ctypes.c_double), ("eps", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("relabel_period", ctypes.c_int),
                 ("threads", ctypes.c_int), ("max_pulses", ctypes.c_int), ("fold_rounds", ctypes.c_int),
-                ("launch_mode", ctypes.c_int), ("grow", ctypes.c_int * 3), ("lsa_steps", ctypes.c_int)]
+                ("launch_mode", ctypes.c_int), ("grow", ctypes.c_int * 3), ("lsa_steps", ctypes.c_int),
+                ("barrier_timeout_us", ctypes.c_int)]
 
 
 class dope_stats(ctypes.Structure):
@@ -604,11 +605,12 @@ class Dope:
 
     def __init__(self, grid, connectivity, block_shape, lam, mu0=None, mu_fact=None, eps=None,
                  max_iter=None, relabel_period=None, threads=None, max_pulses=None, fold_rounds=None,
-                 launch_mode=None, grow=None, lsa_steps=None):
+                 launch_mode=None, grow=None, lsa_steps=None, barrier_timeout_us=None):
         p = dope_default_params()
         for k, v in dict(mu0=mu0, mu_fact=mu_fact, eps=eps, max_iter=max_iter,
                          relabel_period=relabel_period, threads=threads, max_pulses=max_pulses,
-                         fold_rounds=fold_rounds, launch_mode=launch_mode, lsa_steps=lsa_steps).items():
+                         fold_rounds=fold_rounds, launch_mode=launch_mode, lsa_steps=lsa_steps,
+                         barrier_timeout_us=barrier_timeout_us).items():
             if v is not None:
                 setattr(p, k, v)
         if grow is not None:
