@@ -57,8 +57,9 @@ extern "C" {
 #define DOPE_ENOMEM        3   /* device or host allocation failed */
 #define DOPE_EOVERFLOW     4   /* |U_i| >= 2^30 or Wl_ij >= 2^24, non-finite u */
 #define DOPE_ENOTCONV      5   /* max_iter reached before the stop test held; outputs valid */
-#define DOPE_ETIMEOUT      6   /* a block solver hit its pulse bound; outputs not valid */
+#define DOPE_ETIMEOUT      6   /* a bounded device loop or wait ran out; outputs not valid */
 #define DOPE_ECUDA         7   /* a CUDA runtime call failed */
+#define DOPE_ECANCELED     8   /* the request was cancelled (dope_server_cancel) */
 
 #define DOPE_HOST   0
 #define DOPE_DEVICE 1
@@ -451,6 +452,16 @@ int dope_server_submit(dope_server *srv, const dope_request *req, uint64_t *id);
 /* Completed results, oldest first: waits up to timeout_s seconds for at
  * least one, then returns up to cap of them (*count may be 0 on timeout). */
 int dope_server_poll(dope_server *srv, dope_result *out, int cap, int *count, double timeout_s);
+
+/* Cancel a submitted request.  A queued or admitted request is dropped and
+ * its result published with status DOPE_ECANCELED.  One inside a running
+ * batched launch makes the launch end at its next iteration boundary (the
+ * other requests continue in the next launch, unchanged).  In mode 1 the
+ * request being solved finishes first.  A request that has already finished
+ * keeps its result.  Its memory returns to the arena; its buffers are no
+ * longer written once the result is polled.  DOPE_EINVAL for an id never
+ * issued. */
+int dope_server_cancel(dope_server *srv, uint64_t id);
 
 /* Seconds since the server was created (the clock of dope_result). */
 double dope_server_clock(const dope_server *srv);

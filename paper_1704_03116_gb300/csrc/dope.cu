@@ -1147,8 +1147,9 @@ const char* dope_strerror(int s) {
         case DOPE_ENOMEM: return "out of memory";
         case DOPE_EOVERFLOW: return "capacity out of range";
         case DOPE_ENOTCONV: return "max_iter reached before convergence";
-        case DOPE_ETIMEOUT: return "block solver hit its pulse bound";
+        case DOPE_ETIMEOUT: return "a bounded device loop or wait ran out";
         case DOPE_ECUDA: return "CUDA runtime error";
+        case DOPE_ECANCELED: return "request cancelled";
         default: return "unknown status";
     }
 }

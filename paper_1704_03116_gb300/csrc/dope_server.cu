@@ -122,6 +122,7 @@ struct Job {
     dope_image_request img{};   // the request's image source, when r.image_request is set
     double t_submit = 0, t_admit = 0;
     JobState state = J_QUEUED;
+    bool cancel = false;        // dope_server_cancel: drop at the next safe point
     dope_ctx* ctx = nullptr;
     uint8_t* lab_dev = nullptr;
     bool own_lab = false;
@@ -154,6 +155,7 @@ struct dope_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Job*> submitted;
     std::deque<dope_result> results;
+    std::vector<uint64_t> cancels;   // ids to cancel, taken by the worker
     bool stop = false;
     uint64_t next_id = 1;
     std::atomic<int64_t> n_submitted{0}, n_admitted{0}, n_completed{0}, n_launches{0}, n_yields{0};
@@ -368,6 +370,7 @@ void promote(dope_server* s, bool wait) {
         if (!done) { keep.push_back(j); continue; }
         dope_release_staging(j->ctx);
         const int st = s->slots[j->slot].status;
+        if (j->cancel) { fail_job(s, j, DOPE_ECANCELED); continue; }
         if (st) { fail_job(s, j, st); continue; }
         j->state = J_READY;
         s->ready.push_back(j);
@@ -456,6 +459,7 @@ void end_launch(dope_server* s) {
         j->iters = t[(size_t)i];
         j->conv = conv[(size_t)i];
         j->status = rc ? rc : st[(size_t)i];
+        if (j->cancel && !j->status && !j->conv && j->iters < dope_ctx_max_iter(j->ctx)) j->status = DOPE_ECANCELED;
         if (j->status || j->conv || j->iters >= dope_ctx_max_iter(j->ctx)) finish(s, j);
         else keep.push_back(j);
     }
@@ -484,6 +488,53 @@ void run_one(dope_server* s) {
     finish(s, j);
 }
 
+// Requests cancelled since the last pass: queued and ready ones go at once,
+// set-ups once their work has drained (promote), running ones at the end of
+// the launch, which is asked to yield (end_launch); finishing ones keep their
+// result.
+void apply_cancels(dope_server* s, const std::vector<uint64_t>& ids) {
+    for (uint64_t id : ids) {
+        bool found = false;
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+            if ((*it)->id == id) {
+                Job* j = *it;
+                s->queue.erase(it);
+                fail_job(s, j, DOPE_ECANCELED);
+                found = true;
+                break;
+            }
+        if (found) continue;
+        for (auto it = s->ready.begin(); it != s->ready.end(); ++it)
+            if ((*it)->id == id) {
+                Job* j = *it;
+                s->ready.erase(it);
+                fail_job(s, j, DOPE_ECANCELED);
+                found = true;
+                break;
+            }
+        if (found) continue;
+        for (Job* j : s->setup)
+            if (j->id == id) { j->cancel = true; found = true; }
+        if (found) continue;
+        for (auto it = s->running.begin(); it != s->running.end(); ++it)
+            if ((*it)->id == id) {
+                Job* j = *it;
+                j->cancel = true;
+                if (s->in_launch) {
+                    if (!*(volatile int*)s->yield_h) {
+                        *(volatile int*)s->yield_h = 1;
+                        s->n_yields++;
+                    }
+                } else {            // between launches: finish it now
+                    s->running.erase(it);
+                    j->status = DOPE_ECANCELED;
+                    finish(s, j);
+                }
+                break;
+            }
+    }
+}
+
 void worker_main(dope_server* s) {
     cudaSetDevice(s->dev);
     for (;;) {
@@ -495,6 +546,12 @@ void worker_main(dope_server* s) {
                 s->submitted.pop_front();
             }
         }
+        std::vector<uint64_t> cancel_now;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            cancel_now.swap(s->cancels);
+        }
+        if (!cancel_now.empty()) apply_cancels(s, cancel_now);
         admit(s);
         promote(s, false);
         retire(s);
@@ -631,6 +688,17 @@ int dope_server_submit(dope_server* s, const dope_request* r, uint64_t* id) {
     s->n_submitted++;
     s->cv_work.notify_one();
     if (id) *id = j->id;
+    return DOPE_OK;
+}
+
+int dope_server_cancel(dope_server* s, uint64_t id) {
+    if (!s) return DOPE_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (id == 0 || id >= s->next_id) return DOPE_EINVAL;
+        s->cancels.push_back(id);
+    }
+    s->cv_work.notify_one();
     return DOPE_OK;
 }
 

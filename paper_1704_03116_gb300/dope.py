@@ -25,6 +25,7 @@ HEADERS = [HEADER, os.path.join(os.path.dirname(_HERE), "include", "dope_potenti
 
 DOPE_OK, DOPE_EINVAL, DOPE_EUNSUPPORTED, DOPE_ENOMEM = 0, 1, 2, 3
 DOPE_EOVERFLOW, DOPE_ENOTCONV, DOPE_ETIMEOUT, DOPE_ECUDA = 4, 5, 6, 7
+DOPE_ECANCELED = 8
 DOPE_HOST, DOPE_DEVICE = 0, 1
 
 
@@ -142,6 +143,7 @@ def _load():
         "dope_server_submit": (i32, [vp, P(dope_request), P(ctypes.c_uint64)]),
         "dope_server_poll": (i32, [vp, P(dope_result), i32, P(ctypes.c_int), dbl]),
         "dope_server_clock": (dbl, [vp]),
+        "dope_server_cancel": (i32, [vp, ctypes.c_uint64]),
         "dope_server_get_stats": (i32, [vp, P(dope_server_stats)]),
         "dope_server_destroy": (None, [vp]),
         "dope_autotune": (i32, [P(ctypes.c_int64), i32, i32, P(ctypes.c_int32), dbl, P(dope_params), vp, vp, i32,
@@ -830,6 +832,11 @@ class Server:
                         "converged": bool(r.converged), "energy_int": r.energy_int,
                         "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done})
         return out
+
+    def cancel(self, rid):
+        """Cancel a submitted request (its result then has status DOPE_ECANCELED,
+        unless it had already finished)."""
+        _check(_lib.dope_server_cancel(self.srv, ctypes.c_uint64(int(rid))), "dope_server_cancel")
 
     def clock(self):
         return dope_server_clock(self.srv)

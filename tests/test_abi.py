@@ -76,6 +76,8 @@ def test_no_gpu_server_and_batch(lib):
     out = ctypes.c_void_p()
     assert lib._lib.dope_server_create(ctypes.byref(p), ctypes.byref(out)) == lib.DOPE_EINVAL
     assert lib._lib.dope_server_submit(None, None, None) == lib.DOPE_EINVAL
+    assert lib._lib.dope_server_cancel(None, 1) == lib.DOPE_EINVAL
+    assert lib.dope_strerror(lib.DOPE_ECANCELED) == "request cancelled"
     with pytest.raises(lib.DopeError) as ei:
         lib.dope_iterate_batch([], 10)
     assert ei.value.status == lib.DOPE_EINVAL
