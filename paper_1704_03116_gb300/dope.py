@@ -718,6 +718,27 @@ class Dope:
         """(a, yhat) per block copy, box-major (overlapping partitions)."""
         return dope_get_block_state(self.ctx)
 
+    def energy_trace(self, max_iter=1000, stream=None):
+        """Algorithm 1 from its initial state one iteration at a time (the same
+        iterates as a solve), recording after each iteration t the energy
+        E_int(yhat_t) (computed on the device), the number of labels that
+        differ from iteration t - 1 (from all-background at t = 1), and the
+        largest block residual.  Returns a dict of lists; the energy evolution
+        Section 4 plots per ADMM iteration."""
+        self.reset()
+        energies, flips = [], []
+        prev = np.zeros(self.n, np.uint8)
+        lab = np.empty(self.n, np.uint8)
+        for _ in range(int(max_iter)):
+            _, conv = dope_iterate(self.ctx, 1, stream)
+            energies.append(dope_labels(self.ctx, lab, stream))
+            flips.append(int(np.count_nonzero(lab != prev)))
+            prev[...] = lab
+            if conv:
+                break
+        return {"energy_int": energies, "flips": flips, "rmax": self.trace().tolist(),
+                "labels": prev.copy()}
+
     def labels(self, labels=None, stream=None):
         """(labels, E_int) of the last iteration run."""
         if labels is None:

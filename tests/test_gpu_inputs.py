@@ -191,3 +191,29 @@ def test_solve_begin_end_misuse_and_deferred_error(dp):
         g.solve_begin()
     assert ei.value.status == dp.DOPE_EINVAL
     g.close()
+
+
+def test_energy_trace_matches_oracle_steps(dp):
+    """The per-iteration trace (energy of yhat_t, label flips, residual)
+    against the oracle stepping Algorithm 1 itself; its last labels and
+    energy are the solve's."""
+    import oracle
+    d = inputs.random_instance((64, 96), 8, (16, 16), lam=3.0, seed=21)
+    g = dp.Dope(d["grid"], 8, d["block"], d["lam"])
+    g.set_inputs(d["u"], d["wq"])
+    tr = g.energy_trace()
+    lab, E, it = g.solve()
+    g.close()
+    inst = oracle.quantise(d["grid"], 8, d["block"], d["u"], d["wq"], d["lam"])
+    n = inst.n
+    y, a, mu = np.full(n, 0.5), np.zeros(n), 100.0
+    prev = np.zeros(n, np.uint8)
+    for t, (e_gpu, f_gpu, r_gpu) in enumerate(zip(tr["energy_int"], tr["flips"], tr["rmax"]), start=1):
+        yhat, y, a, r2 = oracle.admm_step(inst, mu, y, a)
+        mu *= 1.05
+        assert e_gpu == oracle.energy(inst, yhat), t
+        assert f_gpu == int(np.count_nonzero(yhat != prev)), t
+        assert r_gpu == pytest.approx(float(np.sqrt(r2.max())), rel=1e-9, abs=1e-12), t
+        prev = yhat
+    assert len(tr["energy_int"]) == it
+    assert tr["energy_int"][-1] == E * 1024 and np.array_equal(tr["labels"], lab)
