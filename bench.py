@@ -444,6 +444,13 @@ def serving_summary(requests, rate, saturated=True):
         out["batched_saturated"] = _summ(res_bs, st_bs, t0bs, reqs, None)
         res_1s, st_1s, t01s = _serve(dope, torch, reqs, dev_in, labels, 1, None, warm)
         out["one_at_a_time_saturated"] = _summ(res_1s, st_1s, t01s, reqs, None)
+        # batching only as wide as the backlog (server mode 2), both ways
+        res_a, st_a, t0a = _serve(dope, torch, reqs, dev_in, labels, 2, arrivals, warm)
+        out["adaptive"] = _summ(res_a, st_a, t0a, reqs, arrivals)
+        res_as, st_as, t0as = _serve(dope, torch, reqs, dev_in, labels, 2, None, warm)
+        out["adaptive_saturated"] = _summ(res_as, st_as, t0as, reqs, None)
+        same = same and all(res_a[i]["energy_int"] == res_1[i]["energy_int"] and
+                            res_a[i]["iterations"] == res_1[i]["iterations"] for i in range(n))
         # the same stream given as RGB crops: the server computes the
         # potentials on the GPU (the bases' mixtures; sigma fixed to the base
         # image's, so a crop's weights mean what they mean in the full image)
@@ -463,7 +470,7 @@ def serving_summary(requests, rate, saturated=True):
         out["batched_saturated_from_image"] = dict(_summ(res_bi, st_bi, t0bi, reqs, None),
                                                    inputs="device-resident RGB crops, 12 B/px; "
                                                           "potentials computed by the server")
-    out["results_identical_batched_vs_one_at_a_time"] = bool(same)
+    out["results_identical_across_modes"] = bool(same)
     out["iterations_mean"] = round(sum(res_b[i]["iterations"] for i in range(n)) / n, 1)
     out["config"] = {"workload": "serving stream: RGB contrast-Potts crops of two seeded 2048x2048 ellipse "
                                  "images, side U[128,2048], 4/8-conn 50/50, lambda U[1,16], blocks 32x32",

@@ -396,7 +396,9 @@ typedef struct dope_server dope_server;
 typedef struct {
     uint64_t hbm_bytes;   /* arena size (0: 3/4 of the device's free memory at creation) */
     int max_batch;        /* most admitted requests (0: DOPE_BATCH_MAX) */
-    int mode;             /* 0: continuous batching, 1: one request at a time */
+    int mode;             /* 0: continuous batching (up to max_batch requests at once),
+                             1: one request at a time, 2: continuous batching only as wide
+                             as the backlog (at least 2, at most max_batch) */
     int launch_iters;     /* most iterations of one batched launch (0: no bound) */
     int reserved;
 } dope_server_params;

@@ -280,7 +280,11 @@ dope_tables* tables_for(dope_server* s, int conn, const int32_t blk[3], int* rc)
 
 // Admit queued requests (first come, first served) while memory and slots last.
 void admit(dope_server* s) {
-    while (!s->queue.empty() && s->admitted_count() < s->p.max_batch && !s->free_slots.empty()) {
+    // mode 2: batch only as wide as the backlog (at least 2): near first come,
+    // first served while the server keeps up, full batching when it does not
+    int limit = s->p.max_batch;
+    if (s->p.mode == 2) limit = std::min(limit, std::max(2, (int)s->queue.size()));
+    while (!s->queue.empty() && s->admitted_count() < limit && !s->free_slots.empty()) {
         Job* j = s->queue.front();
         const dope_request& r = j->r;
         int32_t blk3[3] = {1, 1, 1};
@@ -573,7 +577,7 @@ void worker_main(dope_server* s) {
         }
         bool busy = s->in_launch;
         if (!s->in_launch) {
-            if (s->p.mode == 0 && (!s->running.empty() || !s->ready.empty())) {
+            if (s->p.mode != 1 && (!s->running.empty() || !s->ready.empty())) {
                 start_launch(s);
                 busy = true;
             } else if (s->p.mode == 1 && !s->ready.empty()) {
@@ -624,7 +628,7 @@ int dope_server_create(const dope_server_params* p, dope_server** out) {
     dope_server_params prm{};
     if (p) prm = *p;
     if (prm.max_batch <= 0 || prm.max_batch > DOPE_BATCH_MAX) prm.max_batch = DOPE_BATCH_MAX;
-    if (prm.mode != 0 && prm.mode != 1) return DOPE_EINVAL;
+    if (prm.mode < 0 || prm.mode > 2) return DOPE_EINVAL;
     if (prm.launch_iters < 0) return DOPE_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {

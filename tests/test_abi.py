@@ -72,7 +72,7 @@ def test_no_gpu_server_and_batch(lib):
     with pytest.raises(lib.DopeError) as ei:
         lib.dope_server_create()
     assert ei.value.status == lib.DOPE_ECUDA
-    p = lib.dope_server_params(0, 0, 7, 0, 0)            # unknown mode
+    p = lib.dope_server_params(0, 0, 7, 0, 0)            # unknown mode (0, 1, 2 exist)
     out = ctypes.c_void_p()
     assert lib._lib.dope_server_create(ctypes.byref(p), ctypes.byref(out)) == lib.DOPE_EINVAL
     assert lib._lib.dope_server_submit(None, None, None) == lib.DOPE_EINVAL

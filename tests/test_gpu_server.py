@@ -72,9 +72,10 @@ def alone(dp, mix):
     return labels, res
 
 
-def test_server_mix_equals_alone(dp, mix, alone):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_server_mix_equals_alone(dp, mix, alone, mode):
     lab1, res1 = alone
-    labels, res, st = _run(dp, mix, mode=0)
+    labels, res, st = _run(dp, mix, mode=mode)
     for i in range(len(mix)):
         assert res[i]["status"] == 0 and res1[i]["status"] == 0
         assert res[i]["iterations"] == res1[i]["iterations"], i
