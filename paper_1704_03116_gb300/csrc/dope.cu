@@ -1382,29 +1382,41 @@ static int solve_issue(dope_ctx* c, uint8_t* labels, int where, int want_energy,
     const int n = c->p.max_iter;
     memset(&c->stats, 0, sizeof(c->stats));
     const bool pend = c->pending;
-    c->pending = false;
     c->begun_pend = pend;
+    // on any failure below, a pending upload's status stays pending
+    auto fail = [&](int rc) { c->pending = pend; c->begun_pend = false; return rc; };
     if (pend) {
         static_assert(offsetof(Ctrl, status) == sizeof(int), "status follows conv_t");
-        CK(cudaMemsetAsync(c->ctrl, 0, sizeof(int), st));
-        CK(cudaMemsetAsync((char*)c->ctrl + 2 * sizeof(int), 0,
-                           sizeof(Ctrl) - sizeof(unsigned long long) - 2 * sizeof(int), st));
+        if (cudaMemsetAsync(c->ctrl, 0, sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync((char*)c->ctrl + 2 * sizeof(int), 0,
+                            sizeof(Ctrl) - sizeof(unsigned long long) - 2 * sizeof(int), st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DOPE_ECUDA);
+        }
     } else {
         const int rc0 = clear_status(c, st);
-        if (rc0) return rc0;
+        if (rc0) return fail(rc0);
     }
-    CK(cudaMemsetAsync(&c->ctrl->r2max[1], 0, sizeof(unsigned long long) * (size_t)n, st));
+    if (cudaMemsetAsync(&c->ctrl->r2max[1], 0, sizeof(unsigned long long) * (size_t)n, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DOPE_ECUDA);
+    }
     uint8_t* dst = labels;
     if (where == DOPE_HOST) {
         const int rc = ensure_stage(c, (size_t)c->g.Nu, 1);
-        if (rc) return rc;
+        if (rc) return fail(rc);
         dst = (uint8_t*)c->stage2;
     }
     c->launches = 0;
     const int rc = persistent_issue(c, n, st, dst, want_energy);
-    if (rc) return rc;
-    if (where == DOPE_HOST) CK(cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(c->hctrl, c->ctrl, c->ctrl_bytes, cudaMemcpyDeviceToHost, st));
+    if (rc) return fail(rc);
+    if ((where == DOPE_HOST &&
+         cudaMemcpyAsync(labels, dst, (size_t)c->g.Nu, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+        cudaMemcpyAsync(c->hctrl, c->ctrl, c->ctrl_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DOPE_ECUDA);
+    }
+    c->pending = false;   // its status word is now read with the control block
     return DOPE_OK;
 }
 

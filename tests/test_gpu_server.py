@@ -245,7 +245,7 @@ def test_server_cancel_queued_and_running(dp):
     """A queued request and one inside a running launch are both cancelled
     (status DOPE_ECANCELED); the request beside them finishes with the
     result it has alone; afterwards the arena holds only the cached tables."""
-    big = inputs.random_instance((1024, 1024), 8, (32, 32), lam=6.0, seed=11)
+    big = inputs.random_instance((1536, 1536), 8, (32, 32), lam=6.0, seed=11)
     small = inputs.random_instance((256, 320), 4, (16, 16), lam=3.0, seed=12)
     # alone (one at a time)
     lab_small_alone = np.zeros(256 * 320, np.uint8)
@@ -255,7 +255,7 @@ def test_server_cancel_queued_and_running(dp):
     srv.close()
     # one batched iteration per launch, so the big request runs for many launches
     srv = dp.Server(mode=0, launch_iters=1)
-    labs = [np.zeros(1024 * 1024, np.uint8), np.zeros(256 * 320, np.uint8), np.zeros(1024 * 1024, np.uint8)]
+    labs = [np.zeros(1536 * 1536, np.uint8), np.zeros(256 * 320, np.uint8), np.zeros(1536 * 1536, np.uint8)]
     id_big = srv.submit(big["grid"], 8, big["block"], big["lam"], big["u"], big["wq"], labs[0], tag=0)
     srv.submit(small["grid"], 4, small["block"], small["lam"], small["u"], small["wq"], labs[1], tag=1)
     t0 = time.time()
@@ -272,7 +272,7 @@ def test_server_cancel_queued_and_running(dp):
     assert st["bytes_in_use"] < (1 << 20)                # only the shared face / halo tables stay
     srv.close()
     # queued: an arena that holds one big request at a time
-    srv = dp.Server(mode=0, hbm_bytes=64 << 20, launch_iters=1)         # ~46 MB per request in set-up
+    srv = dp.Server(mode=0, hbm_bytes=128 << 20, launch_iters=1)        # ~105 MB per request in set-up
     ids = [srv.submit(big["grid"], 8, big["block"], big["lam"], big["u"], big["wq"], labs[i % 2 * 2], tag=i)
            for i in range(2)]
     srv.cancel(ids[1])                                   # still waiting for memory
