@@ -80,7 +80,8 @@ typedef struct {
     double eps;
     int max_iter;
     int relabel_period;  /* push-relabel pulses between global relabels */
-    int threads;         /* threads per block-solver CTA (multiple of 32) */
+    int threads;         /* threads per block-solver CTA (multiple of 32; 0: one per node up
+                            to 512, a quarter of the nodes for non-submodular blocks) */
     int max_pulses;      /* bound on push-relabel pulses per block and iteration */
     int fold_rounds;     /* bound on exact-folding rounds per block and iteration */
     int launch_mode;     /* 0: one persistent cooperative launch per solve / iterate call,

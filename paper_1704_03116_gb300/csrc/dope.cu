@@ -1107,6 +1107,15 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
         c->nsm = 1;
         c->persist_grid = 0;
         c->resident = 0;
+        if (c->p.threads <= 0) {
+            // narrower CTAs: a block's LSA-TR steps are barrier-bound, so more
+            // blocks in flight per SM pay more than more threads per block
+            // (16x16 blocks: 64 threads solve 1.6x faster than 256)
+            int t = (int)(((B + 3) / 4 + 31) / 32 * 32);
+            if (t > 512) t = 512;
+            if (t < 32) t = 32;
+            if ((long long)t * NPTMAX >= B) c->threads = t;
+        }
         c->nsm_smem = (int)(((solver_smem_bytes(connectivity, (int)B) + 15) & ~(size_t)15) + nsm_extra_bytes((int)B));
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
