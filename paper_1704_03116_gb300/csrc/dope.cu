@@ -716,6 +716,53 @@ int create_overlap(dope_ctx* c, const int64_t dims[3], const int32_t blk[3], con
         cudaGetLastError();
         return DOPE_ECUDA;
     }
+    if (A.gd | A.gh | A.gw) {
+        // Eq. 10's two pixel lists: "inner" pixels are held, with every pixel
+        // within the kernel radius, by one block only; along each axis the
+        // holding range [lo, hi] is monotone in the coordinate, so that is
+        // lo(c - R) == hi(c + R) per axis
+        const int R = c->conn == 24 || c->conn == 32 ? 2 : (c->conn == 48 ? 3 : (c->conn == 80 ? 4 : 1));
+        const bool three_d = c->conn == 6 || c->conn == 32;
+        auto axis = [&](long long n, int b, int gr, int nb, int r) {
+            std::vector<uint8_t> v((size_t)n);
+            auto fdiv = [](long long a, long long d) { return a >= 0 ? a / d : -((-a + d - 1) / d); };
+            for (long long x = 0; x < n; ++x) {
+                long long lo = fdiv(x - r - gr, b), hi = fdiv(x + r + gr, b);
+                if (lo < 0) lo = 0;
+                if (hi > nb - 1) hi = nb - 1;
+                v[(size_t)x] = lo == hi;
+            }
+            return v;
+        };
+        const auto iz = axis(dims[0], blk[0], A.gd, A.nbz, three_d ? R : 0);
+        const auto iy = axis(dims[1], blk[1], A.gh, A.nby, R);
+        const auto ix = axis(dims[2], blk[2], A.gw, A.nbx, R);
+        std::vector<int> inner, band;
+        inner.reserve((size_t)N);
+        for (long long z = 0; z < dims[0]; ++z)
+            for (long long y = 0; y < dims[1]; ++y)
+                for (long long x = 0; x < dims[2]; ++x) {
+                    const int j = (int)((z * dims[1] + y) * dims[2] + x);
+                    if (iz[(size_t)z] && iy[(size_t)y] && ix[(size_t)x]) inner.push_back(j);
+                    else band.push_back(j);
+                }
+        int* di = (int*)dalloc(c->al, sizeof(int) * (inner.size() + 1));
+        int* db = (int*)dalloc(c->al, sizeof(int) * (band.size() + 1));
+        if (!di || !db) {
+            dfree(c->al, di);
+            dfree(c->al, db);
+            return DOPE_ENOMEM;
+        }
+        A.inner = di;
+        A.band = db;
+        A.n_inner = (long long)inner.size();
+        A.n_band = (long long)band.size();
+        if ((!inner.empty() && cudaMemcpy(di, inner.data(), sizeof(int) * inner.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+            (!band.empty() && cudaMemcpy(db, band.data(), sizeof(int) * band.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+            cudaGetLastError();
+            return DOPE_ECUDA;
+        }
+    }
     return ov_reset_async(c, st);
 }
 
@@ -724,8 +771,15 @@ void ov_launch_iteration(dope_ctx* c, int t, double mu, int check_prev, cudaStre
     const OvArgs& A = c->oa;
     k_ov_solve<CONN><<<A.g.K, c->ov_threads, c->ov_smem, st>>>(A, mu, t, check_prev);
     if (mid) cudaEventRecord(mid, st);
-    if ((A.gd | A.gh | A.gw) == 0) k_ov_y_q1<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
-    else k_ov_y<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
+    if ((A.gd | A.gh | A.gw) == 0) {
+        k_ov_y_q1<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
+    } else if (A.inner) {
+        k_ov_y_inner<CONN><<<grid_for(A.n_inner, 256), 256, 0, st>>>(A, mu);
+        k_ov_y_band<CONN><<<grid_for(A.n_band, 256), 256, 0, st>>>(A, mu);
+        c->launches++;
+    } else {
+        k_ov_y<CONN><<<grid_for(A.N, 256), 256, 0, st>>>(A, mu);
+    }
     k_ov_a<CONN><<<A.g.K, 256, 0, st>>>(A, t);
     c->launches += 3;
 }
@@ -1176,6 +1230,8 @@ void dope_destroy(dope_ctx* c) {
     dfree(al, c->stage);
     dfree(al, c->stage2);
     dfree(al, const_cast<uint8_t*>(c->oa.q));
+    dfree(al, const_cast<int*>(c->oa.inner));
+    dfree(al, const_cast<int*>(c->oa.band));
     dfree(al, c->oa.y);
     dfree(al, c->oa.a);
     dfree(al, c->oa.yhat);

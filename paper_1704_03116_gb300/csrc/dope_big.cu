@@ -65,8 +65,14 @@ void big_ov_iteration(int conn, const OvArgs& A, int threads, int smem, double m
         constexpr int C = decltype(cc)::value;
         k_ov_solve<C><<<A.g.K, threads, smem, st>>>(A, mu, t, check_prev);
         if (mid) cudaEventRecord(mid, st);
-        if ((A.gd | A.gh | A.gw) == 0) k_ov_y_q1<C><<<grid_for_n(A.N, 256), 256, 0, st>>>(A, mu);
-        else k_ov_y<C><<<grid_for_n(A.N, 256), 256, 0, st>>>(A, mu);
+        if ((A.gd | A.gh | A.gw) == 0) {
+            k_ov_y_q1<C><<<grid_for_n(A.N, 256), 256, 0, st>>>(A, mu);
+        } else if (A.inner) {
+            k_ov_y_inner<C><<<grid_for_n(A.n_inner, 256), 256, 0, st>>>(A, mu);
+            k_ov_y_band<C><<<grid_for_n(A.n_band, 256), 256, 0, st>>>(A, mu);
+        } else {
+            k_ov_y<C><<<grid_for_n(A.N, 256), 256, 0, st>>>(A, mu);
+        }
         k_ov_a<C><<<A.g.K, 256, 0, st>>>(A, t);
     });
 }

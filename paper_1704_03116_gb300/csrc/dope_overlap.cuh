@@ -42,6 +42,11 @@ struct OvArgs {
     double* a;                 // [K][B] Eq. 11 multipliers, box-major
     uint8_t* yhat;             // [K][B] block labels, box-major
     double* r2blk;             // [K]
+    // with growth: the pixels held, together with every neighbour, by one
+    // block only (their Eq. 10 cross term is 0) and all the others
+    const int* inner;          // [n_inner] image indices, or null
+    const int* band;           // [n_band]
+    long long n_inner, n_band;
     Ctrl* ctrl;
     double eps;
     int relabel_period, max_pulses, fold_rounds;
@@ -184,75 +189,120 @@ __device__ __forceinline__ void ov_tiles(int c, int gr, int tb, int nb, int& lo,
     hi = min(nb - 1, floordiv(c + gr, tb));
 }
 
-// Eq. 10 for every pixel (one thread per pixel).  A_j runs over the blocks
-// holding j in increasing block order; the integer G_j over the blocks holding
-// j (first term) and, per neighbour i, over the blocks holding i (second term).
+// Eq. 10 for pixel j.  A_j runs over the blocks holding j in increasing
+// block order; the integer G_j over the blocks holding j (first term) and,
+// per neighbour i, over the blocks holding i (second term).
+template <int CONN>
+__device__ __forceinline__ void ov_y_pixel(const OvArgs& A, double mu, long long j, double inv) {
+    constexpr int nh = CONN / 2;
+    const int x = (int)(j % A.W);
+    const int y = (int)((j / A.W) % A.H);
+    const int z = (int)(j / ((long long)A.W * A.H));
+    const int qj = A.q[j];
+    int kz0, kz1, ky0, ky1, kx0, kx1;
+    ov_tiles(z, A.gd, A.tbd, A.nbz, kz0, kz1);
+    ov_tiles(y, A.gh, A.tbh, A.nby, ky0, ky1);
+    ov_tiles(x, A.gw, A.tbw, A.nbx, kx0, kx1);
+    double Asum = 0.0;
+    long long G = 0;
+    // blocks holding j: A_j and the first term
+    for (int kz = kz0; kz <= kz1; ++kz)
+        for (int ky = ky0; ky <= ky1; ++ky)
+            for (int kx = kx0; kx <= kx1; ++kx) {
+                const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
+                const int lj = ov_local(A, kz, ky, kx, z, y, x);
+                const int yj = A.yhat[kb + lj];
+                Asum = __dadd_rn(Asum, __dadd_rn((double)yj, A.a[kb + lj]));
+                if (!yj) continue;
+#pragma unroll 4
+                for (int d = 0; d < CONN; ++d) {
+                    int dz, dy, dx;
+                    dir_off<CONN>(d, dz, dy, dx);
+                    const int iz = z + dz, iy = y + dy, ix = x + dx;
+                    if (iz < 0 || iz >= A.D || iy < 0 || iy >= A.H || ix < 0 || ix >= A.W) continue;
+                    const long long i = ((long long)iz * A.H + iy) * A.W + ix;
+                    const long long w = (d < nh) ? A.Wl[(long long)d * A.N + j] : A.Wl[(long long)(d - nh) * A.N + i];
+                    if (!w) continue;
+                    const int qi = A.q[i];
+                    const int li = ov_local(A, kz, ky, kx, iz, iy, ix);
+                    G += w * ov_frac(qi - (li >= 0), A.M, qi, qj);
+                }
+            }
+    // second term: per neighbour i, the blocks holding i whose label of i is 1
+#pragma unroll 4
+    for (int d = 0; d < CONN; ++d) {
+        int dz, dy, dx;
+        dir_off<CONN>(d, dz, dy, dx);
+        const int iz = z + dz, iy = y + dy, ix = x + dx;
+        if (iz < 0 || iz >= A.D || iy < 0 || iy >= A.H || ix < 0 || ix >= A.W) continue;
+        const long long i = ((long long)iz * A.H + iy) * A.W + ix;
+        const long long w = (d < nh) ? A.Wl[(long long)d * A.N + j] : A.Wl[(long long)(d - nh) * A.N + i];
+        if (!w) continue;
+        const int qi = A.q[i];
+        int iz0, iz1, iy0, iy1, ix0, ix1;
+        ov_tiles(iz, A.gd, A.tbd, A.nbz, iz0, iz1);
+        ov_tiles(iy, A.gh, A.tbh, A.nby, iy0, iy1);
+        ov_tiles(ix, A.gw, A.tbw, A.nbx, ix0, ix1);
+        for (int kz = iz0; kz <= iz1; ++kz)
+            for (int ky = iy0; ky <= iy1; ++ky)
+                for (int kx = ix0; kx <= ix1; ++kx) {
+                    const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
+                    if (!A.yhat[kb + ov_local(A, kz, ky, kx, iz, iy, ix)]) continue;
+                    const int lj = ov_local(A, kz, ky, kx, z, y, x);
+                    G -= w * ov_frac(qj - (lj >= 0), A.M, qj, qi);
+                }
+    }
+    const double yv = __ddiv_rn(Asum, (double)qj);
+    const double gq = __dmul_rn((double)G, inv);
+    const double tq = __ddiv_rn(__ddiv_rn(gq, mu), (double)qj);
+    A.y[j] = __dsub_rn(yv, tq);
+}
+
+// Eq. 10 for every pixel (one thread per pixel).
 template <int CONN>
 __global__ void k_ov_y(OvArgs A, double mu) {
     if (*(volatile int*)&A.ctrl->conv_t) return;
-    constexpr int nh = CONN / 2;
     const double inv = 1.0 / (1024.0 * (double)A.M);   // exact: a power of two
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.N;
-         j += (long long)gridDim.x * blockDim.x) {
+         j += (long long)gridDim.x * blockDim.x)
+        ov_y_pixel<CONN>(A, mu, j, inv);
+}
+
+// Eq. 10 for the pixels of A.band (the general form, warps of band pixels only).
+template <int CONN>
+__global__ void k_ov_y_band(OvArgs A, double mu) {
+    if (*(volatile int*)&A.ctrl->conv_t) return;
+    const double inv = 1.0 / (1024.0 * (double)A.M);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < A.n_band;
+         t += (long long)gridDim.x * blockDim.x)
+        ov_y_pixel<CONN>(A, mu, (long long)A.band[t], inv);
+}
+
+// Eq. 10 for the pixels of A.inner: held, with every neighbour, by one block
+// k only, so phi_ki = 0 in the first term and [j in Omega_k] = 1 in the
+// second, G_j = 0, and y_j = (yhat_kj + a_kj) / q_j - ((0 / (1024 M)) / mu) / q_j
+// with the general form's operations.  (A template only so that each
+// translation unit that launches it has its own instance.)
+template <int CONN>
+__global__ void k_ov_y_inner(OvArgs A, double mu) {
+    if (*(volatile int*)&A.ctrl->conv_t) return;
+    const double inv = 1.0 / (1024.0 * (double)A.M);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < A.n_inner;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long j = A.inner[t];
         const int x = (int)(j % A.W);
         const int y = (int)((j / A.W) % A.H);
         const int z = (int)(j / ((long long)A.W * A.H));
+        int kz, ky, kx, hi;
+        ov_tiles(z, A.gd, A.tbd, A.nbz, kz, hi);
+        ov_tiles(y, A.gh, A.tbh, A.nby, ky, hi);
+        ov_tiles(x, A.gw, A.tbw, A.nbx, kx, hi);
+        const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
+        const int lj = ov_local(A, kz, ky, kx, z, y, x);
         const int qj = A.q[j];
-        int kz0, kz1, ky0, ky1, kx0, kx1;
-        ov_tiles(z, A.gd, A.tbd, A.nbz, kz0, kz1);
-        ov_tiles(y, A.gh, A.tbh, A.nby, ky0, ky1);
-        ov_tiles(x, A.gw, A.tbw, A.nbx, kx0, kx1);
-        double Asum = 0.0;
-        long long G = 0;
-        // blocks holding j: A_j and the first term
-        for (int kz = kz0; kz <= kz1; ++kz)
-            for (int ky = ky0; ky <= ky1; ++ky)
-                for (int kx = kx0; kx <= kx1; ++kx) {
-                    const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
-                    const int lj = ov_local(A, kz, ky, kx, z, y, x);
-                    const int yj = A.yhat[kb + lj];
-                    Asum = __dadd_rn(Asum, __dadd_rn((double)yj, A.a[kb + lj]));
-                    if (!yj) continue;
-#pragma unroll 4
-                    for (int d = 0; d < CONN; ++d) {
-                        int dz, dy, dx;
-                        dir_off<CONN>(d, dz, dy, dx);
-                        const int iz = z + dz, iy = y + dy, ix = x + dx;
-                        if (iz < 0 || iz >= A.D || iy < 0 || iy >= A.H || ix < 0 || ix >= A.W) continue;
-                        const long long i = ((long long)iz * A.H + iy) * A.W + ix;
-                        const long long w = (d < nh) ? A.Wl[(long long)d * A.N + j] : A.Wl[(long long)(d - nh) * A.N + i];
-                        if (!w) continue;
-                        const int qi = A.q[i];
-                        const int li = ov_local(A, kz, ky, kx, iz, iy, ix);
-                        G += w * ov_frac(qi - (li >= 0), A.M, qi, qj);
-                    }
-                }
-        // second term: per neighbour i, the blocks holding i whose label of i is 1
-#pragma unroll 4
-        for (int d = 0; d < CONN; ++d) {
-            int dz, dy, dx;
-            dir_off<CONN>(d, dz, dy, dx);
-            const int iz = z + dz, iy = y + dy, ix = x + dx;
-            if (iz < 0 || iz >= A.D || iy < 0 || iy >= A.H || ix < 0 || ix >= A.W) continue;
-            const long long i = ((long long)iz * A.H + iy) * A.W + ix;
-            const long long w = (d < nh) ? A.Wl[(long long)d * A.N + j] : A.Wl[(long long)(d - nh) * A.N + i];
-            if (!w) continue;
-            const int qi = A.q[i];
-            int iz0, iz1, iy0, iy1, ix0, ix1;
-            ov_tiles(iz, A.gd, A.tbd, A.nbz, iz0, iz1);
-            ov_tiles(iy, A.gh, A.tbh, A.nby, iy0, iy1);
-            ov_tiles(ix, A.gw, A.tbw, A.nbx, ix0, ix1);
-            for (int kz = iz0; kz <= iz1; ++kz)
-                for (int ky = iy0; ky <= iy1; ++ky)
-                    for (int kx = ix0; kx <= ix1; ++kx) {
-                        const long long kb = (long long)((kz * A.nby + ky) * A.nbx + kx) * A.g.B;
-                        if (!A.yhat[kb + ov_local(A, kz, ky, kx, iz, iy, ix)]) continue;
-                        const int lj = ov_local(A, kz, ky, kx, z, y, x);
-                        G -= w * ov_frac(qj - (lj >= 0), A.M, qj, qi);
-                    }
-        }
-        const double yv = __ddiv_rn(Asum, (double)qj);
-        const double gq = __dmul_rn((double)G, inv);
+        const double As = __dadd_rn(0.0, __dadd_rn((double)A.yhat[kb + lj], A.a[kb + lj]));
+        const double yv = __ddiv_rn(As, (double)qj);
+        const double gq = __dmul_rn(0.0, inv);
         const double tq = __ddiv_rn(__ddiv_rn(gq, mu), (double)qj);
         A.y[j] = __dsub_rn(yv, tq);
     }
