@@ -109,6 +109,19 @@ def test_potentials_argument_checks(lib):
                             None) == lib.DOPE_EINVAL
 
 
+def test_async_and_two_phase_calls_reject_bad_arguments(lib):
+    """The asynchronous upload and the two-phase solve validate on the host."""
+    L = lib._lib
+    assert L.dope_set_inputs(None, None, None, 0, 0, None) == lib.DOPE_EINVAL
+    assert L.dope_solve_begin(None, None, 0, None) == lib.DOPE_EINVAL
+    assert L.dope_solve_end(None, None, None, None) == lib.DOPE_EINVAL
+    ok = lib.gmm([1.0], [[0.5, 0.5, 0.5]], [np.eye(3) * 0.01])
+    assert L.dope_set_image(None, None, 3, ctypes.byref(ok), ctypes.byref(ok), 1e5, 0.0, 0, 0, None,
+                            None) == lib.DOPE_EINVAL
+    p = lib.dope_default_params()
+    assert p.barrier_timeout_us == 0 and p.threads == 0
+
+
 def test_struct_layouts_match_header(lib):
     """ctypes mirrors of the C structs have the C sizes (compiled probe)."""
     import os
