@@ -176,8 +176,9 @@ int dope_set_unaries(dope_ctx *ctx, const float *u, int64_t n, int where, void *
  * non-zero, DOPE_EOVERFLOW if some Wl >= 2^24.  Synchronises `stream`. */
 int dope_set_weights(dope_ctx *ctx, const int32_t *wq, int64_t n, int where, void *stream);
 
-/* Unaries and weights together, asynchronously: the same copies and
- * quantisation as dope_set_unaries + dope_set_weights, with no
+/* Unaries (Eq. 2) and weights (Eq. 1) together, asynchronously: u [n] and
+ * wq [conn/2][n] in the layouts above, the same copies and quantisation as
+ * dope_set_unaries + dope_set_weights, with no
  * synchronisation.  The quantisers' status (DOPE_EOVERFLOW,
  * DOPE_EUNSUPPORTED, DOPE_EINVAL for the inputs) is reported by the next call
  * on the context that synchronises (dope_solve reads it with its results, in
@@ -195,8 +196,8 @@ int dope_set_inputs(dope_ctx *ctx, const float *u, const int32_t *wq, int64_t n,
 int dope_solve(dope_ctx *ctx, uint8_t *labels, int where, int64_t *energy_int,
                int *iterations, void *stream);
 
-/* dope_solve in two halves, so that several solves (on one or more contexts)
- * can be queued before the host waits.  dope_solve_begin issues the solve on
+/* dope_solve (Algorithm 1 to its stop test) in two halves, so that several
+ * solves (on one or more contexts) can be queued before the host waits.  dope_solve_begin issues the solve on
  * `stream` and returns without synchronising when the solve is one launch
  * (the default launch mode on a partition without overlap, submodular
  * weights); other contexts solve inside it.  dope_solve_end synchronises
