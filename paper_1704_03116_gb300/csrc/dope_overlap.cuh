@@ -71,6 +71,14 @@ __device__ __forceinline__ int ov_local(const OvArgs& A, int kz, int ky, int kx,
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// 1 / q for the block counts q in {1, 2, 4, 8} (Proposition 1's q_ii with
+// 2 g <= tile side), exactly: dividing by q and multiplying by this are the
+// same correctly rounded operation on the same exact value, so x * inv_q(q)
+// has the bits of x / q (and avoids the FP64 divide).
+__device__ __forceinline__ double inv_q(int q) {
+    return q == 1 ? 1.0 : (q == 2 ? 0.5 : (q == 4 ? 0.25 : (q == 8 ? 0.125 : __ddiv_rn(1.0, (double)q))));
+}
+
 // num * M / (qa * qb) for the powers of two q in {1, 2, 4, 8} and M = qmax^2
 // (qa * qb divides M, so the shift is exact).
 __device__ __forceinline__ int ov_frac(int num, int M, int qa, int qb) {
@@ -142,13 +150,13 @@ __global__ void __launch_bounds__(512) k_ov_solve(OvArgs A, double mu, int t, in
             double phi = 1.0;
             if (in_box) {
                 if (qj == 1) continue;
-                phi = __dsub_rn(1.0, __ddiv_rn(1.0, (double)qj));
+                phi = __dsub_rn(1.0, inv_q(qj));
             }
             const double wf = __dmul_rn((double)w, phi);
             const double t_ = __dmul_rn(wf, __dsub_rn(yi, A.y[j]));
             s = __dadd_rn(s, t_);
         }
-        s = __ddiv_rn(s, (double)qi);
+        s = __dmul_rn(s, inv_q(qi));
         const double vv = __dadd_rn(__dsub_rn(A.a[(long long)k * B + v], yi), 0.5);
         s = __dadd_rn(s, __dmul_rn(m1024, vv));
         double ms = __dmul_rn((double)A.M, s);
@@ -252,9 +260,9 @@ __device__ __forceinline__ void ov_y_pixel(const OvArgs& A, double mu, long long
                     G -= w * ov_frac(qj - (lj >= 0), A.M, qj, qi);
                 }
     }
-    const double yv = __ddiv_rn(Asum, (double)qj);
+    const double yv = __dmul_rn(Asum, inv_q(qj));
     const double gq = __dmul_rn((double)G, inv);
-    const double tq = __ddiv_rn(__ddiv_rn(gq, mu), (double)qj);
+    const double tq = __dmul_rn(__ddiv_rn(gq, mu), inv_q(qj));
     A.y[j] = __dsub_rn(yv, tq);
 }
 
@@ -301,9 +309,9 @@ __global__ void k_ov_y_inner(OvArgs A, double mu) {
         const int lj = ov_local(A, kz, ky, kx, z, y, x);
         const int qj = A.q[j];
         const double As = __dadd_rn(0.0, __dadd_rn((double)A.yhat[kb + lj], A.a[kb + lj]));
-        const double yv = __ddiv_rn(As, (double)qj);
+        const double yv = __dmul_rn(As, inv_q(qj));
         const double gq = __dmul_rn(0.0, inv);
-        const double tq = __ddiv_rn(__ddiv_rn(gq, mu), (double)qj);
+        const double tq = __dmul_rn(__ddiv_rn(gq, mu), inv_q(qj));
         A.y[j] = __dsub_rn(yv, tq);
     }
 }
@@ -351,9 +359,9 @@ __global__ void k_ov_y_q1(OvArgs A, double mu) {
                 G += w * (long long)(yj - (int)A.yhat[ki]);
             }
         }
-        const double yv = __ddiv_rn(Asum, 1.0);
+        const double yv = Asum;                                    // x / 1 = x
         const double gq = __dmul_rn((double)G, inv);
-        const double tq = __ddiv_rn(__ddiv_rn(gq, mu), 1.0);
+        const double tq = __ddiv_rn(gq, mu);
         A.y[j] = __dsub_rn(yv, tq);
     }
 }
