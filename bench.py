@@ -561,6 +561,7 @@ def main():
           for _ in range(args.steps * len(ctxs))]
     clocks = Clocks(local)
     launches, iters, energies = 0, [], []
+    work = {"pulses_total": 0, "free_nodes_total": 0, "bfs_levels_total": 0}
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -583,6 +584,8 @@ def main():
             _, E, it = g.solve_end(stream=stream.cuda_stream, allow_notconv="grow" in insts[0])
             st = g.stats()
             launches += st["kernel_launches"]
+            for key in work:
+                work[key] += int(st.get(key, 0))
             iters.append(it)
             energies.append(E)
     torch.cuda.synchronize()
@@ -709,6 +712,12 @@ def main():
             "iterations": sorted(set(iters)), "energies": sorted(set(energies)),
             "converged": [bool(g.stats()["converged"]) for g in ctxs],
             "wall_s": wall, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            # the block solver's work (its own counters): push-relabel pulses, nodes
+            # left for push-relabel after folding, BFS levels -- per solve and per second
+            "solver": {"pulses_per_solve": work["pulses_total"] / max(len(iters), 1),
+                       "free_nodes_per_solve": work["free_nodes_total"] / max(len(iters), 1),
+                       "bfs_levels_per_solve": work["bfs_levels_total"] / max(len(iters), 1),
+                       "pulses_per_s": work["pulses_total"] / max(t_local, 1e-12)},
             "e2e": {"value": job_rate(n_px * args.steps, world, e2e_t), "unit": "pixels/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)}}
