@@ -132,6 +132,10 @@ typedef struct {
                                    (two launches per iteration), 1 k_admm_persistent, 2 k_admm_resident,
                                    3 k_admm_batch (dope_iterate_batch) */
     int reserved;
+    int64_t blocks_solved;      /* k_admm_persistent with worklists: block solves run from the
+                                   worklists (after each launch's first iteration, which does
+                                   every block); 0 on the other kernels */
+    int64_t blocks_updated;     /* likewise, block updates (Eq. 10 / 11) run from the worklists */
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the

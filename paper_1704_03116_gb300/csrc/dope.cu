@@ -62,6 +62,8 @@ struct dope_ctx {
     int ov_threads = 0, ov_smem = 0;
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
+    unsigned char* sched = nullptr;   // block worklists of k_admm_persistent (sched_bytes)
+    unsigned sched_epoch = 0;         // persistent launches issued with them
     Ctrl* hctrl = nullptr;      // pinned host copy of the whole control block (dope_solve's single read)
     // staging (lazily allocated)
     void* stage = nullptr;
@@ -267,6 +269,8 @@ void fill_stats(dope_ctx* c, const Ctrl& h) {
     for (int i = 0; i < 4; ++i) c->stats.phase_cycles[i] = (double)h.cyc[i];
     for (int i = 0; i < 4; ++i) c->stats.loop_cycles[i] = (double)h.pcyc[i];
     for (int i = 0; i < 8; ++i) c->stats.window_cycles[i] = (double)h.wcyc[i];
+    c->stats.blocks_solved = (int64_t)h.sched_work[0];
+    c->stats.blocks_updated = (int64_t)h.sched_work[1];
 }
 
 int read_r2max(dope_ctx* c, int t, double* r2, cudaStream_t st) {
@@ -300,6 +304,13 @@ int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = 
     P.NH = c->NH;
     P.hslot = c->hslot;
     P.hinfo = c->hinfo;
+    if (c->sched && !c->resident && c->p.mu_fact >= 1.0) {
+        // worklists: valid while mu does not decrease (the forced test's bound
+        // only grows); each launch's marks carry a new epoch
+        ++c->sched_epoch;
+        P.s.sched = P.u.sched = c->sched;
+        P.s.epoch = P.u.epoch = c->sched_epoch;
+    }
     void* args[] = {&P};
     if (c->profiling) {
         if (c->ev.size() < 2) {
@@ -1176,6 +1187,17 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (c->nsm_smem > optin || pad) { dope_destroy(c); return DOPE_EINVAL; }
     }
+    if (!c->nsm && !c->resident && c->persist_grid > 0) {
+        // worklists of the persistent kernel; marks start below every launch's
+        const size_t sb = sched_bytes(g.K, g.F);
+        A((void**)&c->sched, sb);
+        if (rc) { dope_destroy(c); return rc; }
+        if (cudaMemsetAsync(c->sched, 0, sb, st) != cudaSuccess) {
+            cudaGetLastError();
+            dope_destroy(c);
+            return DOPE_ECUDA;
+        }
+    }
     rc = reset_state_async(c, st);
     if (rc) { dope_destroy(c); return rc; }
     *out = c;
@@ -1227,6 +1249,7 @@ void dope_destroy(dope_ctx* c) {
     dfree(al, c->aF);
     dfree(al, c->r2blk);
     dfree(al, c->ctrl);
+    dfree(al, c->sched);
     dfree(al, c->stage);
     dfree(al, c->stage2);
     dfree(al, const_cast<uint8_t*>(c->oa.q));
@@ -2175,7 +2198,7 @@ size_t dope_ctx_device_bytes(const dope_ctx* c) {
     if (!c) return 0;
     const size_t N = (size_t)c->g.N, KF = (size_t)c->g.K * c->g.F;
     return N * 4 + N * 4 * (size_t)(c->conn / 2) + N + 16 * KF + 8 * (size_t)c->g.K + c->ctrl_bytes +
-           c->stage_bytes + c->stage2_bytes;
+           (c->sched ? sched_bytes(c->g.K, c->g.F) : 0) + c->stage_bytes + c->stage2_bytes;
 }
 
 int64_t dope_ctx_pixels(const dope_ctx* c) { return c ? (int64_t)c->g.Nu : 0; }
@@ -2334,6 +2357,8 @@ int dope_batch_launch(dope_ctx* const* cs, int n, int n_iter, int exit_on_done, 
         d.max_pulses = c->p.max_pulses;
         d.fold_rounds = c->p.fold_rounds;
         d.conn = c->conn;
+        d.sched = nullptr;
+        d.epoch = 0;
         BatchProb& b = w->hprob[i];
         b.t0 = c->t;
         const int left = c->p.max_iter - c->t;

@@ -73,8 +73,89 @@ struct Ctrl {
                                     // wait at the closing barrier, rest of the resolution
     unsigned long long pcyc[4];     // persistent kernel, thread 0 of each CTA: solve phase,
                                     // first barrier wait, update phase, second barrier wait
+    unsigned sq_n[2];               // worklists of the persistent kernel, by parity of the
+    unsigned uq_n[2];               // iteration they serve: blocks to solve / to update
+    unsigned long long sched_work[2];   // blocks solved / updated from the worklists (statistics)
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
 };
+
+// ---------------------------------------------------------------------------
+// Block worklists (persistent kernels).  A block is *quiet* for iteration t+1
+// when its Eq. 8 problem provably keeps its labels and its Eq. 10 / 11 update
+// provably changes nothing:
+//   * every face pixel i of the block has a_i = +0 and y_i = yhat_i, and every
+//     cross-block neighbour j has y_j = y_i and yhat_j = yhat_i; so every cross
+//     term of Eq. 8 is exactly zero and the pixel's unary is that of an
+//     interior pixel, U_i +- 512 mu;
+//   * every pixel passes the integer forced test (|U_i +- H| beyond its n-link
+//     sum, H = floor(512 mu)), so every minimiser of Eq. 8 keeps its label.
+// With the labels fixed, G_i = 0 for every face pixel, Eq. 10 gives y = yhat
+// and Eq. 11 a = +0: the state does not move.  Because mu only grows (H is
+// monotone), a quiet block stays quiet until its own state or a cross
+// neighbour's state (y, a or label) changes.  The kernel therefore solves, in
+// iteration t+1, only the blocks on a solve list: the non-quiet blocks and
+// the blocks next to a face pixel whose state changed in iteration t; and it
+// updates, in iteration t, only the blocks on an update list: the non-quiet
+// blocks and the blocks next to a face pixel whose label changed.  Everything
+// else is skipped, exactly: the skipped work would have reproduced the state
+// bit for bit.  The first iteration of every launch solves and updates every
+// block and evaluates nothing (so a state set from outside is never trusted).
+//
+// Per-context buffer (sched_bytes), K blocks, F face slots per block:
+//   smark, umark u64 [K]   last (epoch << 32 | t) a block was put on the
+//                          solve / update list (one entry per list)
+//   sq, uq      int32 [2][K]  the lists, by parity of their iteration
+//   qs          uint8 [K]     1: the block was found quiet at its last solve
+//   yhF         uint8 [K][F]  label of each face slot as of its block's last update
+// ---------------------------------------------------------------------------
+struct SchedView {
+    unsigned long long* smark;
+    unsigned long long* umark;
+    int* sq;
+    int* uq;
+    uint8_t* qs;
+    uint8_t* yhF;
+};
+
+__host__ __device__ inline size_t sched_bytes(int K, int F) {
+    return 16 * (size_t)K + 16 * (size_t)K + (size_t)K + (size_t)K * F;
+}
+
+__device__ __forceinline__ SchedView sched_view(unsigned char* base, int K) {
+    SchedView s;
+    s.smark = reinterpret_cast<unsigned long long*>(base);
+    s.umark = s.smark + K;
+    s.sq = reinterpret_cast<int*>(s.umark + K);
+    s.uq = s.sq + 2 * (size_t)K;
+    s.qs = reinterpret_cast<uint8_t*>(s.uq + 2 * (size_t)K);
+    s.yhF = s.qs + K;
+    return s;
+}
+
+// Put block kn on a list for the iteration whose mark is m, unless it is on
+// it already.
+__device__ __forceinline__ void wl_push(unsigned long long* mark, int* list, unsigned* count, int kn,
+                                        unsigned long long m) {
+    if (atomicMax(&mark[kn], m) < m) list[atomicAdd(count, 1u)] = kn;
+}
+
+// Threads 0..26 of the CTA: put every block of the 3x3(x3) neighbourhood of
+// block k whose offset code ((dkz+1)*9 + (dky+1)*3 + dkx+1, 13 = k itself) is
+// set in `mask` on the list.
+template <class GEO>
+__device__ __forceinline__ void wl_push_mask(const GEO& g, int k, unsigned mask, unsigned long long* mark,
+                                             int* list, unsigned* count, unsigned long long m) {
+    const int j = threadIdx.x;
+    if (j >= 27 || !((mask >> j) & 1u)) return;
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    const int nkz = kz + j / 9 - 1, nky = ky + (j / 3) % 3 - 1, nkx = kx + j % 3 - 1;
+    if (nkz < 0 || nkz >= g.nbz || nky < 0 || nky >= g.nby || nkx < 0 || nkx >= g.nbx) return;
+    wl_push(mark, list, count, (nkz * g.nby + nky) * g.nbx + nkx, m);
+}
+
+__device__ __forceinline__ unsigned long long wl_mark(unsigned epoch, int t) {
+    return ((unsigned long long)epoch << 32) | (unsigned)t;
+}
 
 struct SolveArgs {
     Geo g;
@@ -94,6 +175,8 @@ struct SolveArgs {
     int fold_rounds;                // bound on exact-folding rounds
     int int_test;                   // interior forced test in integers (needs 512 mu < 2^52)
     long long H;                    // floor(512 mu)
+    unsigned char* sched = nullptr; // block worklists (persistent kernel), or null
+    unsigned epoch = 0;             // launch number for the worklists' marks
 };
 
 struct UpdArgs {
@@ -109,6 +192,8 @@ struct UpdArgs {
     Ctrl* ctrl;
     double mu;
     int t;
+    unsigned char* sched = nullptr; // block worklists (persistent kernel), or null
+    unsigned epoch = 0;
 };
 
 // Values of one iteration t that the block solver and the face update need:
@@ -118,6 +203,7 @@ struct IterArgs {
     double mu;
     long long H;
     int t, first, int_test;
+    int qeval;      // evaluate quiet blocks and fill the worklists (needs A.sched)
 };
 
 __device__ __forceinline__ IterArgs iter_args(int t, double mu) {
@@ -128,6 +214,7 @@ __device__ __forceinline__ IterArgs iter_args(int t, double mu) {
     const double h = __dmul_rn(__dmul_rn(1024.0, mu), 0.5);
     it.int_test = h < 4503599627370496.0 ? 1 : 0;   // 2^52
     it.H = it.int_test ? (long long)floor(h) : 0;
+    it.qeval = 0;
     return it;
 }
 
@@ -139,6 +226,7 @@ __device__ __forceinline__ IterArgs iter_of(const SolveArgs& A) {
     it.t = A.t;
     it.first = A.first;
     it.int_test = A.int_test;
+    it.qeval = 0;
     return it;
 }
 
@@ -310,6 +398,18 @@ __device__ __forceinline__ long long shifted_cap(const Geo& g, const int32_t* __
 // shifted_cap in the same order, with the neighbours found through the halo
 // table and every load issued before the FP64 chain.
 template <int CONN>
+__device__ __forceinline__ long long face_cap_from(long long Ui, double yv, double av, const double* yj,
+                                                   const int* wj, unsigned ok, double m1024) {
+    double s = (double)Ui;
+#pragma unroll
+    for (int d = 0; d < CONN; ++d)
+        if ((ok >> d) & 1) s = __dadd_rn(s, __dmul_rn((double)wj[d], __dsub_rn(yv, yj[d])));
+    s = __dadd_rn(s, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
+    s = fmin(fmax(s, -CLAMP62), CLAMP62);
+    return __double2ll_rn(s);
+}
+
+template <int CONN>
 __device__ __forceinline__ long long face_cap_core(const Geo& g, long long Ui, double yv, double av,
                                                    const int32_t* __restrict__ Wl,
                                                    const double* __restrict__ yF,
@@ -332,13 +432,7 @@ __device__ __forceinline__ long long face_cap_core(const Geo& g, long long Ui, d
                              : Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
         }
     }
-    double s = (double)Ui;
-#pragma unroll
-    for (int d = 0; d < CONN; ++d)
-        if ((ok >> d) & 1) s = __dadd_rn(s, __dmul_rn((double)wj[d], __dsub_rn(yv, yj[d])));
-    s = __dadd_rn(s, __dmul_rn(m1024, __dadd_rn(__dsub_rn(av, yv), 0.5)));
-    s = fmin(fmax(s, -CLAMP62), CLAMP62);
-    return __double2ll_rn(s);
+    return face_cap_from<CONN>(Ui, yv, av, yj, wj, ok, m1024);
 }
 
 template <int CONN>
@@ -491,17 +585,17 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
     const int tid = threadIdx.x, NT = blockDim.x;
     int* res = reinterpret_cast<int*>(smem);
     long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
-    int* e = reinterpret_cast<int*>(C64);
-    int* ein = e + B;
     int* capsum = reinterpret_cast<int*>(C64 + B);
-    int16_t* hA = reinterpret_cast<int16_t*>(capsum);
-    int16_t* hB = hA + B;
     uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
     const int bw = g.bw, pl = g.bh * g.bw;
     constexpr int nh = CONN / 2;
     const double m1024 = __dmul_rn(1024.0, it.mu);
     unsigned long long imask = 0;        // 8 bits per own node: intra-block directions
+    unsigned oldlab = 0;                 // bit q: label of own node tid + q NT before this solve
+    int allf = 1;                        // every own node forced by the integer test
+    int qok = 1;                         // ... and the block quiet (see sched_view)
+    __shared__ unsigned s_pm;            // neighbour blocks to put on the update list
     const long long c_start = clock64();
 
     // 1a. capacity build: forward intra-block n-links from HBM, U and yhat
@@ -546,29 +640,127 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
         }
         capsum[v] = cs;
         const int yh = st[v];
-        st[v] = FREE;
+        oldlab |= (unsigned)yh << q;
         if (need_caps && A.faceIndex[v] < 0) {
+            st[v] = FREE;
             // interior pixel: y = yhat, a = 0 (see the note above face_cap)
             const long long Ui = C64[v];
             const long long T = yh ? Ui - it.H : Ui + it.H;
             if (it.int_test && (yh ? (T < -(long long)cs) : (T >= (long long)cs))) {
                 C64[v] = T;
             } else {
+                allf = 0;
                 const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
                 C64[v] = shifted_cap<CONN>(g, A.U, A.Wl, A.yhat, A.yF, A.aF, A.faceIndex, k, kz, ky,
                                            kx, v, lz, ly, lx, 0, m1024);
             }
+        } else if (!need_caps) {
+            st[v] = FREE;
         }
     }
-    // 1c. face pixels, one face slot per thread: exact FP64 Eq. 8 unary
+    // 1c. face pixels, one face slot per thread (after the n-link sums are in):
+    // a face pixel in the trivial state (a = +0, y = yhat) whose cross
+    // neighbours all have y_j = y_i gets exactly the interior unary (every
+    // cross term of Eq. 8 is +-0 and adds nothing) and the integer forced
+    // test; every other face pixel the exact FP64 Eq. 8 unary.
     if (need_caps) {
+        __syncthreads();
+        const SchedView sv = sched_view(A.sched, g.K);
         for (int f = tid; f < g.F; f += NT) {
             const int v = A.faceLocal[f];
-            C64[v] = face_cap<CONN>(g, A.U, A.Wl, A.yF, A.aF, A.halo, k, kz, ky, kx, v, f, m1024);
+            const long long gi = (long long)k * B + v;
+            const int yh = st[v];
+            const long long sidx = (long long)k * g.F + f;
+            const double yv = __ldcg(&A.yF[sidx]);
+            const double av = __ldcg(&A.aF[sidx]);
+            double yj[CONN];
+            int wj[CONN];
+            unsigned ok = 0;
+            bool lab_same = true;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int kn, ln, fn;
+                yj[d] = 0.0;
+                wj[d] = 0;
+                if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+                    ok |= 1u << d;
+                    yj[d] = __ldcg(&A.yF[(long long)kn * g.F + fn]);
+                    wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi]
+                                     : A.Wl[(long long)(d - nh) * g.N + (long long)kn * B + ln];
+                    if (it.qeval) lab_same = lab_same && (int)__ldcg(&sv.yhF[(long long)kn * g.F + fn]) == yh;
+                }
+            }
+            bool uni = __double_as_longlong(av) == 0 && yv == (double)yh;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d)
+                if ((ok >> d) & 1) uni = uni && yj[d] == yv;
+            const long long Ui = C64[v];
+            bool forced = false;
+            if (uni) {
+                const long long T = yh ? Ui - it.H : Ui + it.H;
+                const long long cs = capsum[v];
+                if (it.int_test && (yh ? (T < -cs) : (T >= cs))) {
+                    C64[v] = T;
+                    forced = true;
+                } else {
+                    C64[v] = interior_cap(Ui, yh, m1024);
+                }
+            } else {
+                C64[v] = face_cap_from<CONN>(Ui, yv, av, yj, wj, ok, m1024);
+            }
+            st[v] = FREE;
+            allf &= forced ? 1 : 0;
+            qok &= (forced && lab_same) ? 1 : 0;
         }
     }
-    __syncthreads();
+    // Every pixel forced to its own label: the labels stand (the cut would
+    // reproduce them), so the cut is skipped.
+    allf = need_caps ? __syncthreads_and(allf) : (__syncthreads(), 0);
+    if (it.qeval) {
+        const int quiet = __syncthreads_and(qok & allf);
+        if (tid == 0) {
+            const SchedView sv = sched_view(A.sched, g.K);
+            sv.qs[k] = (uint8_t)quiet;
+            s_pm = quiet ? 0u : (1u << 13);      // a block that is not quiet is updated
+        }
+    }
+    if (allf) {
+        if (it.qeval) {
+            __syncthreads();
+            const SchedView sv = sched_view(A.sched, g.K);
+            wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &A.ctrl->uq_n[it.t & 1],
+                         wl_mark(A.epoch, it.t));
+            __syncthreads();
+        }
+        return;
+    }
     cut_block<CONN, SA>(A, k, smem, bw, pl, imask, c_start, nullptr);
+    if (it.qeval) {
+        // blocks next to a face pixel whose label changed get updated too
+        unsigned pm = 0;
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            const int v = tid + q * NT;
+            if (v >= B) continue;
+            const int nl = __ldcg(&A.yhat[(long long)k * B + v]);
+            const int f = A.faceIndex[v];
+            if (nl != (int)((oldlab >> q) & 1u) && f >= 0) {
+#pragma unroll
+                for (int d = 0; d < CONN; ++d) {
+                    int kn, ln, fn;
+                    const int e = A.halo[d * g.F + f];
+                    if (halo_decode(g, e, kz, ky, kx, kn, ln, fn)) pm |= 1u << (e >> 24);
+                }
+            }
+        }
+        pm = __reduce_or_sync(0xffffffffu, pm);
+        if ((tid & 31) == 0 && pm) atomicOr(&s_pm, pm);
+        __syncthreads();
+        const SchedView sv = sched_view(A.sched, g.K);
+        wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &A.ctrl->uq_n[it.t & 1],
+                         wl_mark(A.epoch, it.t));
+        __syncthreads();
+    }
 }
 
 // Steps a5-a6 on the graph the build left in shared memory (res, C64, capsum,
@@ -832,31 +1024,38 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
 //   a_i = a_i + (yhat_i - y_i)                             (Eq. 11)
 // ---------------------------------------------------------------------------
 template <int CONN, class UA>
-__device__ void update_block(const UA& __restrict__ A, double mu, int t, int k) {
+__device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, int selfpush = 0) {
     const Geo& g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     constexpr int nh = CONN / 2;
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    const bool wl = A.sched != nullptr;
+    const SchedView sv = sched_view(A.sched, g.K);
     // r_k^2 is summed in a fixed order, whatever the CTA shape: face slots in
     // chunks of 32, each chunk by the same butterfly, chunks in increasing order
     __shared__ double part[128];
+    __shared__ unsigned pmask[128];
     const int nchunks = (g.F + 31) >> 5;
     for (int ch = wid; ch < nchunks; ch += nw) {
         const int f = ch * 32 + lane;
         double d2 = 0.0;
+        unsigned pm = 0;
         if (f < g.F) {
             const int v = A.faceLocal[f];
             const long long gi = (long long)k * g.B + v;
             int wj[CONN], yj[CONN];
+            unsigned cm = 0;      // offset codes of the blocks holding this pixel's cross neighbours
 #pragma unroll
             for (int d = 0; d < CONN; ++d) {
                 int kn, ln, fn;
                 wj[d] = 0;
                 yj[d] = 0;
-                if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+                const int e = A.halo[d * g.F + f];
+                if (halo_decode(g, e, kz, ky, kx, kn, ln, fn)) {
                     const long long gj = (long long)kn * g.B + ln;
                     wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
                     yj[d] = __ldcg(&A.yhat[gj]);
+                    cm |= 1u << (e >> 24);
                 }
             }
             const int yh = __ldcg(&A.yhat[gi]);
@@ -864,28 +1063,67 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k) 
 #pragma unroll
             for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
             const long long s = (long long)k * g.F + f;
-            const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
-            const double aa = t == 1 ? 0.0 : __ldcg(&A.aF[s]);   // a = 0 before iteration 1
-            // G = 0: (G/1024)/mu = +0 and x - (+0) = x exactly, so the division is skipped
-            const double ya = __dadd_rn((double)yh, aa);
-            const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
-            const double an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
-            A.yF[s] = yn;
-            A.aF[s] = an;
-            const double dd = __dsub_rn((double)yh, yn);
-            d2 = __dmul_rn(dd, dd);
+            const double yo = __ldcg(&A.yF[s]);
+            const double ao = __ldcg(&A.aF[s]);
+            const double aa = t == 1 ? 0.0 : ao;   // a = 0 before iteration 1
+            double yn, an;
+            if (G == 0 && __double_as_longlong(aa) == 0) {
+                // the operations below with G = 0 and a = +0: y = yhat + (+0) = yhat,
+                // a = +0 + (yhat - y) = +0, (yhat - y)^2 = +0
+                yn = (double)yh;
+                an = 0.0;
+            } else {
+                const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
+                // G = 0: (G/1024)/mu = +0 and x - (+0) = x exactly, so the division is skipped
+                const double ya = __dadd_rn((double)yh, aa);
+                yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
+                an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
+                const double dd = __dsub_rn((double)yh, yn);
+                d2 = __dmul_rn(dd, dd);
+            }
+            // only what changed is written back
+            bool changed = __double_as_longlong(yn) != __double_as_longlong(yo) ||
+                           __double_as_longlong(an) != __double_as_longlong(ao);
+            if (changed) {
+                A.yF[s] = yn;
+                A.aF[s] = an;
+            }
+            if (wl) {
+                if ((int)__ldcg(&sv.yhF[s]) != yh) {
+                    sv.yhF[s] = (uint8_t)yh;
+                    changed = true;
+                }
+                if (changed) pm = cm | (1u << 13);
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-        if (lane == 0) part[ch] = d2;
+        if (__any_sync(0xffffffffu, d2 != 0.0))
+            for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        if (wl) pm = __reduce_or_sync(0xffffffffu, pm);
+        if (lane == 0) {
+            part[ch] = d2;
+            pmask[ch] = pm;
+        }
     }
     __syncthreads();
     if (tid == 0) {
         double r2 = 0.0;
         for (int ch = 0; ch < nchunks; ++ch) r2 = __dadd_rn(r2, part[ch]);
         A.r2blk[k] = r2;
-        atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
+        if (r2 != 0.0) atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
+        if (wl) {
+            // the blocks next to a face pixel whose state changed (and this
+            // block, if it changed or is not quiet) are solved next iteration
+            unsigned m = (selfpush || !__ldcg(&sv.qs[k])) ? (1u << 13) : 0u;
+            for (int ch = 0; ch < nchunks; ++ch) m |= pmask[ch];
+            pmask[0] = m;
+        }
     }
-    __syncthreads();   // part is reused by the next block
+    __syncthreads();
+    if (wl) {
+        wl_push_mask(g, k, pmask[0], sv.smark, sv.sq + (size_t)((t + 1) & 1) * g.K, &A.ctrl->sq_n[(t + 1) & 1],
+                     wl_mark(A.epoch, t + 1));
+        __syncthreads();
+    }
 }
 
 // One launch = one iteration's Eq. 10 / Eq. 11 update, one CTA per block.
@@ -1287,23 +1525,41 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
     int t = P.t0, conv = 0;
     bool failed = false;
     unsigned nbar = 0;
+    const bool wl = P.s.sched != nullptr;
+    const SchedView sv = sched_view(P.s.sched, K);
     for (int j = 0; j < P.n; ++j) {
         t = P.t0 + j + 1;
-        const IterArgs it = iter_args(t, mu);
+        IterArgs it = iter_args(t, mu);
+        // with worklists, the launch's first iteration does every block;
+        // later ones the blocks on the lists (see sched_view)
+        const bool full = !wl || j == 0;
+        it.qeval = !full;
         // the update counter is idle during the solve phase and vice versa,
-        // so each is reset in the other phase
+        // so each is reset in the other phase; likewise the list counts
         const long long c0 = clock64();
-        if (blockIdx.x == 0 && threadIdx.x == 0) c->work[1] = 0u;
-        for (int k = next_block(P.dynamic, &c->work[0], -1, &s_k); k < K;
-             k = next_block(P.dynamic, &c->work[0], k, &s_k))
-            solve_block<CONN>(P.s, it, k, smem);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->work[1] = 0u;
+            if (wl) c->sq_n[(t + 1) & 1] = 0u;
+        }
+        const int ns = full ? K : (int)__ldcg(&c->sq_n[t & 1]);
+        for (int i = next_block(P.dynamic, &c->work[0], -1, &s_k); i < ns;
+             i = next_block(P.dynamic, &c->work[0], i, &s_k))
+            solve_block<CONN>(P.s, it, full ? i : __ldcg(&sv.sq[(t & 1) * (size_t)K + i]), smem);
         const long long c1 = clock64();
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
         const long long c2 = clock64();
-        if (blockIdx.x == 0 && threadIdx.x == 0) c->work[0] = 0u;
-        for (int k = next_block(P.dynamic, &c->work[1], -1, &s_k); k < K;
-             k = next_block(P.dynamic, &c->work[1], k, &s_k))
-            update_block<CONN>(P.u, mu, t, k);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->work[0] = 0u;
+            if (wl) c->uq_n[(t + 1) & 1] = 0u;
+        }
+        const int nu = full ? K : (int)__ldcg(&c->uq_n[t & 1]);
+        for (int i = next_block(P.dynamic, &c->work[1], -1, &s_k); i < nu;
+             i = next_block(P.dynamic, &c->work[1], i, &s_k))
+            update_block<CONN>(P.u, mu, t, full ? i : __ldcg(&sv.uq[(t & 1) * (size_t)K + i]), full ? 1 : 0);
+        if (wl && !full && blockIdx.x == 0 && threadIdx.x == 0) {
+            atomicAdd(&c->sched_work[0], (unsigned long long)ns);
+            atomicAdd(&c->sched_work[1], (unsigned long long)nu);
+        }
         const long long c3 = clock64();
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
         if (threadIdx.x == 0) {
@@ -2053,6 +2309,8 @@ struct BatchDesc {
     Ctrl* ctrl;
     double eps;
     int relabel_period, max_pulses, fold_rounds, conn;
+    unsigned char* sched;           // always null here (no worklists in the batched launch)
+    unsigned epoch;
 };
 
 __constant__ BatchDesc c_batch[BATCH_MAX];

@@ -52,7 +52,8 @@ class dope_stats(ctypes.Structure):
                 ("phase_cycles", ctypes.c_double * 4), ("loop_cycles", ctypes.c_double * 4),
                 ("windows", ctypes.c_int), ("window_iterations", ctypes.c_int),
                 ("window_cycles", ctypes.c_double * 8), ("solver_kernel", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("reserved", ctypes.c_int), ("blocks_solved", ctypes.c_int64),
+                ("blocks_updated", ctypes.c_int64)]
 
 
 class dope_profile(ctypes.Structure):
