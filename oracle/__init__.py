@@ -109,6 +109,10 @@ def _load():
                                        ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int), _F64P,
                                        _F64P, _F64P, _F64P]
     lib.orc_nsm_admm.restype = ctypes.c_int
+    lib.orc_lsa_tr_block_trace.argtypes = geo[:3] + [_I64P, ctypes.c_int64, _I64P, _U8P, ctypes.c_int,
+                                                      ctypes.c_int, _U8P, _U8P, _I64P, _I64P, _I64P, _I64P,
+                                                      _I64P, _I64P, ctypes.POINTER(ctypes.c_int)]
+    lib.orc_lsa_tr_block_trace.restype = ctypes.c_int
     lib.orc_lsa_tr_global.argtypes = [_I64P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, _U8P]
     lib.orc_lsa_tr_global.restype = ctypes.c_int64
     lib.orc_num_threads.argtypes = []
@@ -469,6 +473,36 @@ def nsm_admm(inst: Instance, mu0, mu_fact=1.05, eps=1e-3, max_iter=1000, steps=L
     t = iters.value
     return {"labels": labels, "iterations": t, "converged": rc == 0, "rmax": rmax[:t].copy(), "y": y,
             "a": a, "mu": float(mu[0]), "energy": energy(inst, labels)}
+
+
+def lsa_tr_block_trace(inst: Instance, k, Cb, x0, steps=LSA_STEPS):
+    """LSA-TR on block k alone from labels x0 (block-local order) with block
+    unaries Cb, recording every step: a list of dicts with the expansion point
+    x_in, the approximation's unaries `un` and constant `cst`, the trust-region
+    weight `lam`, the minimiser x_out, E(x_in) `ecur`, the approximation at the
+    minimiser `ap`, E(minimiser) `enew`, and `accepted`; plus the final labels."""
+    B = int(np.prod(inst.block))
+    Cb = _c(Cb, np.int64).reshape(-1)
+    x = np.array(x0, dtype=np.uint8).reshape(-1)
+    assert Cb.shape == (B,) and x.shape == (B,)
+    cap = int(steps)
+    xin = np.zeros((cap, B), np.uint8)
+    xout = np.zeros((cap, B), np.uint8)
+    un = np.zeros((cap, B), np.int64)
+    v = {nm: np.zeros(cap, np.int64) for nm in ("cst", "lam", "ecur", "ap", "enew")}
+    acc = np.zeros(cap, np.int32)
+    geo = inst._geo()[:3]
+    done = _load().orc_lsa_tr_block_trace(*geo, _p(inst.Wl, _I64P), int(k), _p(Cb, _I64P), _p(x, _U8P),
+                                          int(steps), cap, _p(xin, _U8P), _p(xout, _U8P), _p(un, _I64P),
+                                          _p(v["cst"], _I64P), _p(v["lam"], _I64P), _p(v["ecur"], _I64P),
+                                          _p(v["ap"], _I64P), _p(v["enew"], _I64P),
+                                          acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if done < 0:
+        raise RuntimeError("orc_lsa_tr_block_trace failed")
+    recs = [{"x_in": xin[s].copy(), "x_out": xout[s].copy(), "un": un[s].copy(), "cst": int(v["cst"][s]),
+             "lam": int(v["lam"][s]), "ecur": int(v["ecur"][s]), "ap": int(v["ap"][s]),
+             "enew": int(v["enew"][s]), "accepted": bool(acc[s])} for s in range(min(done, cap))]
+    return recs, x
 
 
 def lsa_tr_global(inst: Instance, steps=200):

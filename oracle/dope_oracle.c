@@ -1200,9 +1200,32 @@ static int64_t lsa_energy(const grid_t *g, int64_t k, int B, const int64_t *Cb, 
     return e;
 }
 
+/* Per-step record of one LSA-TR run (test infrastructure: the CPU tests pin
+ * every step against its definition).  Arrays have room for `cap` steps of B
+ * nodes each; step s fills: xin[s*B..] the expansion point x^s, un[s*B..] the
+ * approximation's unaries, cst[s] its constant, lam[s] the trust-region
+ * weight, xout[s*B..] the step's minimiser, ecur[s] = E(x^s), ap[s] = the
+ * approximation at the minimiser, enew[s] = E(minimiser) (ap, enew = 0 when
+ * the minimiser is x^s), acc[s] = 1 if the minimiser was kept. */
+typedef struct {
+    int cap;
+    uint8_t *xin, *xout;
+    int64_t *un, *cst, *lam, *ecur, *ap, *enew;
+    int *acc;
+} lsa_trace_t;
+
 /* LSA-TR on block k from x (in place); Cb = block unaries (local order). */
+static int lsa_tr_block_traced(const grid_t *g, int64_t k, const int64_t *Cb, const int64_t *Wl, uint8_t *x,
+                               int steps, int *steps_done, lsa_trace_t *tr);
+
 static int lsa_tr_block(const grid_t *g, int64_t k, const int64_t *Cb, const int64_t *Wl, uint8_t *x,
                         int steps, int *steps_done)
+{
+    return lsa_tr_block_traced(g, k, Cb, Wl, x, steps, steps_done, NULL);
+}
+
+static int lsa_tr_block_traced(const grid_t *g, int64_t k, const int64_t *Cb, const int64_t *Wl, uint8_t *x,
+                               int steps, int *steps_done, lsa_trace_t *tr)
 {
     int B = g->bd * g->bh * g->bw;
     int64_t *un = malloc(sizeof(int64_t) * (size_t)B);
@@ -1240,6 +1263,18 @@ static int lsa_tr_block(const grid_t *g, int64_t k, const int64_t *Cb, const int
         bk_free(&b);
         int same = 1;
         for (int l = 0; l < B; l++) same &= (xs[l] == x[l]);
+        int rec = tr && s < tr->cap;
+        if (rec) {
+            memcpy(tr->xin + (size_t)s * B, x, (size_t)B);
+            memcpy(tr->xout + (size_t)s * B, xs, (size_t)B);
+            memcpy(tr->un + (size_t)s * B, un, sizeof(int64_t) * (size_t)B);
+            tr->cst[s] = cst;
+            tr->lam[s] = lam;
+            tr->ecur[s] = e_cur;
+            tr->ap[s] = 0;
+            tr->enew[s] = 0;
+            tr->acc[s] = 0;
+        }
         if (same) {
             if (lam == 0) { s++; break; }
             lam /= 4;
@@ -1261,6 +1296,11 @@ static int lsa_tr_block(const grid_t *g, int64_t k, const int64_t *Cb, const int
         }
         int64_t e_new = lsa_energy(g, k, B, Cb, Wl, xs);
         int64_t R = e_cur - e_new, P = e_cur - ap;
+        if (rec) {
+            tr->ap[s] = ap;
+            tr->enew[s] = e_new;
+            tr->acc[s] = R > 0;
+        }
         if (R > 0) {
             memcpy(x, xs, (size_t)B);
             e_cur = e_new;
@@ -1340,6 +1380,23 @@ int orc_nsm_admm(const int64_t *dims, int conn, const int *block, const int64_t 
     if (mu_out) *mu_out = mu;
     free(y); free(a); free(r2); free(C);
     return rc;
+}
+
+/* Test hook: LSA-TR on block k of the grid from labels x (block-local order,
+ * updated in place) with the block unaries Cb (local order), recording every
+ * step (lsa_trace_t).  Returns the number of steps run, or < 0 on error. */
+int orc_lsa_tr_block_trace(const int64_t *dims, int conn, const int *block, const int64_t *Wl, int64_t k,
+                           const int64_t *Cb, uint8_t *x, int steps, int cap, uint8_t *xin, uint8_t *xout,
+                           int64_t *un, int64_t *cst, int64_t *lam, int64_t *ecur, int64_t *ap, int64_t *enew,
+                           int *acc)
+{
+    grid_t g;
+    if (grid_init(&g, dims, conn, block)) return -1;
+    if (k < 0 || k >= g_nblocks(&g)) return -1;
+    lsa_trace_t tr = {cap, xin, xout, un, cst, lam, ecur, ap, enew, acc};
+    int done = 0;
+    if (lsa_tr_block_traced(&g, k, Cb, Wl, x, steps, &done, &tr)) return -4;
+    return done;
 }
 
 /* Serial LSA-TR on the whole grid (one block = the grid) from x = 0: the
