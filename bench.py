@@ -1,17 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: pixels/s of DOPE ADMM to convergence on one GB300 (per rank).
 
-Workload (default "ellipses512"): the 512x512 RGB ellipse image, 8-connected
-contrast-sensitive Potts, 32x32 sub-regions (K = 256), solved for the three
-lambdas 1, 4 and 16; one step = the three solves to convergence
-(Algorithm 1, mu0 = 100, mu_fact = 1.05, eps = 1e-3).  Inputs are synthetic
-(seeded), resident in HBM for `value`; `e2e` goes through the C-ABI with
-pinned host buffers, host<->device copies inside the timed region.  The L2
-is flushed (a 256 MiB write) before every timed step, outside the step's
-events.
+Workload (default "ellipsoids256"): the 256x256x128 volume (D x H x W =
+128 x 256 x 256, three nested ellipsoids, bias field, Rician-like noise),
+6-connected contrast-sensitive Potts, 8x16x16 sub-regions (K = 4096),
+lambda 3; one step = one solve to convergence (Algorithm 1, mu0 = 500,
+mu_fact = 1.05, eps = 1e-3).  Inputs are synthetic (seeded), resident in HBM
+for `value`; `e2e` goes through the C-ABI with pinned host buffers,
+host<->device copies inside the timed region.  The L2 is flushed (a 256 MiB
+write) before every timed step, outside the step's events.  The line also
+carries the energy gap and the Dice coefficient against the global min-cut
+(whole-volume BK), the oracle's own solve (cpu_baseline, oracle_match), and,
+as sub-objects, the 512x512 RGB image line (lambda 1, 4, 16), the GPU
+potentials and the serving comparison.
 
 --impl reference times the oracle (the plain CPU implementation of the
-method: BK per block + FP64 ADMM, OpenMP over blocks) on the same workload.
+method: BK per block + FP64 ADMM, OpenMP over blocks) on a bounded sample of
+the same workload (reference_sample).
 """
 import argparse
 import hashlib
@@ -160,10 +165,11 @@ def overlap_bytes(d):
     return nb * (22 + 4 * nh), n * (9 + 4 * nh) + nb * (9 + 25)
 
 
-def kernel_traffic(kname):
+def kernel_traffic(kname, wname):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
-    summary, or None when there is none or the kernel source changed since."""
-    path = os.path.join(PROFILES, f"{kname}_ellipses512.md")
+    summary of that kernel on that workload, or None when there is none or the
+    kernel source changed since."""
+    path = os.path.join(PROFILES, f"{kname}_{wname}.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -233,9 +239,12 @@ def _oracle_solve(oracle, q, d):
     return oracle.admm(q, d["mu0"], max_iter=mi)
 
 
-def cpu_baseline(insts, cfg):
-    """The oracle (as it stands) on one full step of the workload: every lambda's
-    Algorithm 1 run, OpenMP over blocks on all host cores."""
+def cpu_baseline(insts, gpu_labels=None):
+    """The oracle (as it stands) on one full step of the workload: every
+    instance's Algorithm 1 run, OpenMP over blocks on all host cores.  Also the
+    gap of each oracle solve to the global minimum (whole-grid BK, the paper's
+    sGC; serial LSA-TR on the whole grid for non-submodular blocks) and the
+    Dice coefficient of the GPU's labels (else the oracle's) against it."""
     import oracle
     qs = [oracle.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"], signed=bool(d.get("lsa_steps")))
           for d in insts]
@@ -243,17 +252,35 @@ def cpu_baseline(insts, cfg):
     res = [_oracle_solve(oracle, q, d) for q, d in zip(qs, insts)]
     dt = time.perf_counter() - t0
     px = sum(q.n for q in qs)
-    gaps = []
-    for q, r, d in zip(qs, res, insts):
+    gaps, dscs = [], []
+    for j, (q, r, d) in enumerate(zip(qs, res, insts)):
         if d.get("lsa_steps"):
             # non-submodular: against the serial LSA-TR on the whole grid (the paper's Table 3)
-            _, egc = oracle.lsa_tr_global(q, steps=64)
+            lgc, egc = oracle.lsa_tr_global(q, steps=64)
         else:
-            _, egc = oracle.global_mincut(q)
+            lgc, egc = oracle.global_mincut(q)
         gaps.append((r["energy"] - egc) / abs(egc))
+        lab = gpu_labels[j] if gpu_labels is not None else r["labels"]
+        dscs.append(dice(lab, lgc))
     return {"value": px / dt, "unit": "pixels/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"one full step ({len(qs)} solves, {px} pixels) in {dt:.2f} s",
-            "oracle_iterations": [r["iterations"] for r in res]}, gaps, res
+            "oracle_iterations": [r["iterations"] for r in res]}, gaps, res, dscs
+
+
+def reference_sample(name):
+    """The bounded sample one step of the reference arm solves: the workload
+    itself, or for the 256x256x128 volume (about 20-30 s of oracle time per
+    solve) its middle slab of 16 x 256 x 256 voxels, two block layers (same
+    blocks, lambda, mu0; n-links leaving the slab dropped): 1/8 of the volume,
+    crossing all three ellipsoids, 15 iterations against the volume's 18."""
+    from paper_1704_03116_gb300 import inputs
+    insts, cfg = workload(name)
+    if name == "ellipsoids256":
+        d = insts[0]
+        D = d["grid"][0]
+        return [inputs.crop_instance(d, (D // 2 - 8, 0, 0), (16,) + tuple(d["grid"][1:]))], \
+            "middle 16x256x256 slab of the volume (1/8), one oracle solve per step"
+    return insts, "each step one solve of the workload, cycling over its lambdas"
 
 
 def run_reference(args):
@@ -261,12 +288,13 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    insts, cfg = workload(args.workload)
+    _, cfg = workload(args.workload)
+    insts, sample = reference_sample(args.workload)
     qs = [oracle.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"], signed=bool(d.get("lsa_steps")))
           for d in insts]
     times, px = [], []
     for s in range(args.warmup + args.steps):
-        j = s % len(qs)           # each step: one of the workload's solves (bounded sample)
+        j = s % len(qs)           # each step: one of the sample's solves
         t0 = time.perf_counter()
         _oracle_solve(oracle, qs[j], insts[j])
         dt = time.perf_counter() - t0
@@ -279,8 +307,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": val, "unit": "pixels/s", "cores": oracle.num_threads(),
-                             "kind": "oracle",
-                             "sample": "each step one solve of the workload, cycling over its lambdas"},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -498,42 +525,19 @@ def run_serving(args):
     print(json.dumps(line))
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="dope", choices=["dope", "reference"])
-    ap.add_argument("--workload", default="ellipses512")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--requests", type=int, default=1000, help="serving workload: requests")
-    ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per second")
-    ap.add_argument("--no-saturated", action="store_true", help="serving workload: skip the capacity runs")
-    ap.add_argument("--no-serving", action="store_true",
-                    help="default workload: skip the serving comparison added to its line")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "serving":
-        return run_serving(args)
-
+def measure(name, args, world, local, with_e2e=True):
+    """Time one workload on this rank: `value` (device-resident inputs), the
+    per-solve latencies, the dominant kernel's roofline, the block solver's
+    counters and (with_e2e) the end-to-end figures through the C-ABI.
+    Returns (line fields, the workload's instances, the last labels per
+    instance on the host)."""
     import torch
-    import torch.distributed as dist
-    from paper_1704_03116_gb300 import _build
-    if int(os.environ.get("LOCAL_RANK", "0")) == 0:
-        _build.build()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        dist.barrier()
     from paper_1704_03116_gb300 import dope
 
-    insts, cfg = workload(args.workload)
+    insts, cfg = workload(name)
     ctxs = []
     overlap = "grow" in insts[0] or insts[0]["conn"] not in (4, 8, 6)
+    notconv = "grow" in insts[0]
     for d in insts:
         g = dope.Dope(d["grid"], d["conn"], d["block"], d["lam"], mu0=d["mu0"], grow=d.get("grow"),
                       max_iter=d.get("max_iter"), lsa_steps=d.get("lsa_steps"))
@@ -547,11 +551,12 @@ def main():
 
     def barrier():
         if world > 1:
+            import torch.distributed as dist
             dist.barrier()
 
     for _ in range(args.warmup):
         for g, lab in zip(ctxs, labels):
-            g.solve(lab, allow_notconv="grow" in insts[0])
+            g.solve(lab, allow_notconv=notconv)
     torch.cuda.synchronize()
 
     # ---- device-resident timed region -----------------------------------
@@ -561,7 +566,8 @@ def main():
           for _ in range(args.steps * len(ctxs))]
     clocks = Clocks(local)
     launches, iters, energies = 0, [], []
-    work = {"pulses_total": 0, "free_nodes_total": 0, "bfs_levels_total": 0}
+    work = {"pulses_total": 0, "free_nodes_total": 0, "bfs_levels_total": 0, "blocks_solved": 0,
+            "blocks_updated": 0}
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -581,7 +587,7 @@ def main():
             b.record(stream)
         step_ev[s][1].record(stream)
         for g in ctxs:
-            _, E, it = g.solve_end(stream=stream.cuda_stream, allow_notconv="grow" in insts[0])
+            _, E, it = g.solve_end(stream=stream.cuda_stream, allow_notconv=notconv)
             st = g.stats()
             launches += st["kernel_launches"]
             for key in work:
@@ -598,8 +604,10 @@ def main():
     t_max = max_over_ranks(t_local, world)
     value = job_rate(n_px * args.steps, world, t_max)
     profs = [g.profile() for g in ctxs]
+    kinds = [g.stats()["solver_kernel"] for g in ctxs]
     for g in ctxs:
         g.set_profiling(False)
+    host_labels = [lab.cpu().numpy() for lab in labels]
 
     # ---- roofline of the dominant kernel --------------------------------
     hbm, peak_kind = peaks()
@@ -613,6 +621,7 @@ def main():
     upd_ms = sum(p["ms"][1] for p in profs)
     upd_n = sum(p["launches"][1] for p in profs)
     iters_n = sum(p["iterations"] for p in profs)
+    model = "every pixel's bytes once per iteration"
     if overlap:
         sb, ub = overlap_bytes(insts[0])
         if solve_ms >= upd_ms:
@@ -623,9 +632,17 @@ def main():
     elif upd_n == 0:
         # persistent mode: one launch runs every iteration of a solve (the
         # resident kernel when every block fits on the GPU at once)
-        kname = "k_admm_resident" if ctxs[0].stats()["solver_kernel"] == 2 else "k_admm_persistent"
+        kname = "k_admm_resident" if kinds[0] == 2 else "k_admm_persistent"
         kms, kn = solve_ms, solve_n
-        kbytes = first_n * sf + (iters_n - first_n) * sl + iters_n * up
+        if kname == "k_admm_persistent" and work["blocks_solved"]:
+            # worklists: the launch's first iteration does every block, later
+            # ones the blocks on the lists; the bytes of the blocks processed
+            sfb, slb, upb = sf / k1, sl / k1, up / k1
+            kbytes = kn * k1 * (sfb + upb) + work["blocks_solved"] * slb + work["blocks_updated"] * upb
+            model = ("bytes of the blocks processed: iteration 1 every block, later iterations the "
+                     "blocks on the worklists (per block solve %.0f B, update %.0f B)" % (slb, upb))
+        else:
+            kbytes = first_n * sf + (iters_n - first_n) * sl + iters_n * up
         share = {kname: 1.0}
     elif solve_ms >= upd_ms:
         kname = "k_nsm_solve" if insts[0].get("lsa_steps") else "k_block_solve"
@@ -639,13 +656,38 @@ def main():
     achieved = kbytes / (kms / 1e3) / 1e9
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "peak_kind": f"{peak_kind} hbm_gbs",
-            "traffic": kernel_traffic(kname),
-            "algorithmic_bytes_per_launch": kbytes / max(kn, 1),
+            "traffic": kernel_traffic(kname, name),
+            "algorithmic_bytes_per_launch": kbytes / max(kn, 1), "bytes_model": model,
             "avg_launch_us": 1e3 * kms / max(kn, 1), "launches": kn, "iterations_covered": iters_n,
             "time_share": share}
 
+    out = {"metric": METRIC if "grow" not in insts[0] else
+           "pixels/sec of 3 ADMM iterations (overlapping partition, Figure 2 protocol)",
+           "value": value, "unit": "pixels/s", "ms_per_step": statistics.mean(step_ms),
+           "config": dict(cfg, l2="flushed before every step (256 MiB write)",
+                          parallelism="replicas" if world > 1 else "single"),
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "solves": len(lat)},
+           "iterations": sorted(set(iters)), "energies": sorted(set(energies)),
+           "converged": [bool(g.stats()["converged"]) for g in ctxs],
+           "pixel_iterations_per_s": sum(g.n * it for g, it in zip(ctxs * args.steps, iters)) / max(t_local, 1e-12),
+           "wall_s": wall, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+           # the block solver's work (its own counters): push-relabel pulses, nodes
+           # left for push-relabel after folding, BFS levels -- per solve and per
+           # second; block solves / updates run from the persistent kernel's worklists
+           "solver": {"pulses_per_solve": work["pulses_total"] / max(len(iters), 1),
+                      "free_nodes_per_solve": work["free_nodes_total"] / max(len(iters), 1),
+                      "bfs_levels_per_solve": work["bfs_levels_total"] / max(len(iters), 1),
+                      "pulses_per_s": work["pulses_total"] / max(t_local, 1e-12),
+                      "worklist_block_solves_per_solve": work["blocks_solved"] / max(len(iters), 1),
+                      "worklist_block_updates_per_solve": work["blocks_updated"] / max(len(iters), 1),
+                      "blocks": k1}}
+    last_E = energies[-len(ctxs):]
+    if not with_e2e:
+        return out, insts, host_labels, last_E
+
     # ---- end to end through the C-ABI with pinned host buffers ---------
-    up = torch.cuda.Stream()
+    up_s = torch.cuda.Stream()
     hu = [torch.from_numpy(d["u"]).pin_memory() for d in insts]
     hw = [torch.from_numpy(np.ascontiguousarray(d["wq"])).pin_memory() for d in insts]
     hl = [torch.empty(g.n, dtype=torch.uint8).pin_memory() for g in ctxs]
@@ -658,23 +700,24 @@ def main():
         # every solve of the step queued, then one wait per solve; inputs go
         # up on their own stream, each solve ordered after its upload
         for g, u, w, lab in zip(ctxs, hu, hw, hl):
-            g.set_inputs(u.numpy(), w.numpy(), stream=up.cuda_stream)
+            g.set_inputs(u.numpy(), w.numpy(), stream=up_s.cuda_stream)
             ev_up = torch.cuda.Event()
-            ev_up.record(up)
+            ev_up.record(up_s)
             stream.wait_event(ev_up)
             g.solve_begin(lab.numpy(), stream=stream.cuda_stream)
         for g in ctxs:
-            g.solve_end(stream=stream.cuda_stream, allow_notconv="grow" in insts[0])
+            g.solve_end(stream=stream.cuda_stream, allow_notconv=notconv)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     barrier()
     e2e_t = max_over_ranks(sum(e2e_ms) / 1e3, world)
     h2d = sum(d["u"].nbytes + d["wq"].nbytes for d in insts)
     d2h = sum(g.n for g in ctxs) + 8 * len(ctxs)
+    out["e2e"] = {"value": job_rate(n_px * args.steps, world, e2e_t), "unit": "pixels/s",
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)}
 
     # ---- end to end from the image: potentials on the GPU (Algorithm 1's
     # first step), then the solve; pinned image in, labels out --------------
-    e2e_img = None
     if all("image" in d and "gmm_fg" in d and "inv_dist" in d for d in insts) and not overlap:
         hi = [torch.from_numpy(np.ascontiguousarray(d["image"], np.float32)).pin_memory() for d in insts]
         img_ms = []
@@ -685,56 +728,111 @@ def main():
             t0 = time.perf_counter()
             for g, d, im, lab in zip(ctxs, insts, hi, hl):
                 g.set_image(im.numpy(), d["gmm_fg"], d["gmm_bg"], inv_dist=d["inv_dist"], read_sigma=False,
-                            stream=up.cuda_stream)
+                            stream=up_s.cuda_stream)
                 ev_up = torch.cuda.Event()
-                ev_up.record(up)
+                ev_up.record(up_s)
                 stream.wait_event(ev_up)
                 g.solve_begin(lab.numpy(), stream=stream.cuda_stream)
             for g in ctxs:
-                g.solve_end(stream=stream.cuda_stream, allow_notconv="grow" in insts[0])
+                g.solve_end(stream=stream.cuda_stream, allow_notconv=notconv)
             torch.cuda.synchronize()
             img_ms.append(1e3 * (time.perf_counter() - t0))
         barrier()
         t_img = max_over_ranks(sum(img_ms) / 1e3, world)
-        e2e_img = {"value": job_rate(n_px * args.steps, world, t_img), "unit": "pixels/s",
-                   "h2d_bytes_per_step": sum(im.numel() * 4 for im in hi), "d2h_bytes_per_step": d2h,
-                   "ms_per_step": statistics.mean(img_ms),
-                   "note": "image in; mixture data term and contrast weights computed on the GPU"}
+        out["e2e_from_image"] = {"value": job_rate(n_px * args.steps, world, t_img), "unit": "pixels/s",
+                                 "h2d_bytes_per_step": sum(im.numel() * 4 for im in hi),
+                                 "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(img_ms),
+                                 "note": "image in; mixture data term and contrast weights computed on the GPU"}
+    return out, insts, host_labels, last_E
 
-    metric = METRIC if "grow" not in insts[0] else "pixels/sec of 3 ADMM iterations (overlapping partition, Figure 2 protocol)"
-    line = {"metric": metric, "value": value, "unit": "pixels/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64", "data": "synthetic",
-            "config": dict(cfg, l2="flushed before every step (256 MiB write)",
-                           parallelism="replicas" if world > 1 else "single"),
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "solves": len(lat)},
-            "iterations": sorted(set(iters)), "energies": sorted(set(energies)),
-            "converged": [bool(g.stats()["converged"]) for g in ctxs],
-            "wall_s": wall, "gpu_launches": launches, "roofline": roof, "clocks": clk,
-            # the block solver's work (its own counters): push-relabel pulses, nodes
-            # left for push-relabel after folding, BFS levels -- per solve and per second
-            "solver": {"pulses_per_solve": work["pulses_total"] / max(len(iters), 1),
-                       "free_nodes_per_solve": work["free_nodes_total"] / max(len(iters), 1),
-                       "bfs_levels_per_solve": work["bfs_levels_total"] / max(len(iters), 1),
-                       "pulses_per_s": work["pulses_total"] / max(t_local, 1e-12)},
-            "e2e": {"value": job_rate(n_px * args.steps, world, e2e_t), "unit": "pixels/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": statistics.mean(e2e_ms)}}
-    if e2e_img:
-        line["e2e_from_image"] = e2e_img
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, gaps, res = cpu_baseline(insts, cfg)
-        line["cpu_baseline"] = cb
-        line["energy_gap_vs_serial_lsa_tr" if insts[0].get("lsa_steps") else "energy_gap_vs_global_mincut"] = gaps
-        line["oracle_match"] = all(abs(E * 1024 - r["energy"]) <= 1e-4 * abs(r["energy"])
-                                   for E, r in zip(energies[-len(insts):], res))
-    if rank == 0 and world == 1 and args.workload == "ellipses512":
+
+def dice(a, b):
+    """Dice similarity coefficient of the foreground (label 1) of two labellings."""
+    a = np.asarray(a, bool)
+    b = np.asarray(b, bool)
+    s = int(a.sum()) + int(b.sum())
+    return 1.0 if s == 0 else 2.0 * int((a & b).sum()) / s
+
+
+def oracle_checks(out, insts, host_labels, last_E, with_cpu=True):
+    """CPU side of a line: the oracle's Algorithm 1 on one full step (timed:
+    cpu_baseline), the gap of every solve's energy to the global minimum (or
+    to serial LSA-TR for non-submodular blocks), the Dice coefficient of the
+    labels against the global minimiser (the paper's DSC against sGC), and
+    whether the GPU energies match the oracle's."""
+    cb, gaps, res, dscs = cpu_baseline(insts, host_labels)
+    if with_cpu:
+        out["cpu_baseline"] = cb
+    key = "lsa_tr" if insts[0].get("lsa_steps") else "global_mincut"
+    out["energy_gap_vs_serial_lsa_tr" if key == "lsa_tr" else "energy_gap_vs_global_mincut"] = gaps
+    out["gap_target"] = 1e-3
+    out["gap_within_target"] = [bool(x <= 1e-3) for x in gaps]
+    out["dsc_vs_serial_lsa_tr" if key == "lsa_tr" else "dsc_vs_global_mincut"] = dscs
+    out["oracle_match"] = all(abs(E * 1024 - r["energy"]) <= 1e-4 * abs(r["energy"])
+                              for E, r in zip(last_E, res))
+    out["oracle_labels_match"] = all(np.array_equal(l, r["labels"]) for l, r in zip(host_labels, res))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dope", choices=["dope", "reference"])
+    ap.add_argument("--workload", default="ellipsoids256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=1000, help="serving workload: requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per second")
+    ap.add_argument("--no-saturated", action="store_true", help="serving workload: skip the capacity runs")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default workload: skip the serving comparison added to its line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: only the headline (no 2-D line, potentials or serving)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1704_03116_gb300 import _build
+    if int(os.environ.get("LOCAL_RANK", "0")) == 0:
+        _build.build()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+
+    out, insts, host_labels, last_E = measure(args.workload, args, world, local)
+    line = {"metric": out.pop("metric"), "value": out.pop("value"), "unit": out.pop("unit"), "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32+f64",
+            "data": "synthetic", "config": out.pop("config")}
+    line.update(out)
+    single = rank == 0 and world == 1
+    if single and not args.no_cpu_baseline:
+        oracle_checks(line, insts, host_labels, last_E)
+    default = args.workload == "ellipsoids256" and not args.no_extras
+    if single and default:
+        # the 2-D colour-image workload (512 x 512 RGB, lambda 1, 4, 16) as its own object
+        try:
+            sub, si, sl, sE = measure("ellipses512", args, world, local, with_e2e=True)
+            if not args.no_cpu_baseline:
+                oracle_checks(sub, si, sl, sE)
+            line["ellipses512"] = sub
+        except Exception as e:  # the main line stands on its own
+            line["ellipses512"] = {"error": f"{type(e).__name__}: {e}"}
+    if single and (default or args.workload == "ellipses512"):
         try:
             line["potentials"] = potentials_summary()
         except Exception as e:  # the main line stands on its own
             line["potentials"] = {"error": f"{type(e).__name__}: {e}"}
-    if rank == 0 and world == 1 and args.workload == "ellipses512" and not args.no_serving:
+    if single and (default or args.workload == "ellipses512") and not args.no_serving:
         # the serving target: batched vs one-at-a-time on the request stream
         try:
             srv, _ = serving_summary(args.requests, args.rate, not args.no_saturated)

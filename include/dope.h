@@ -296,16 +296,27 @@ int dope_get_geometry(dope_ctx *ctx, int64_t *n_pixels, int64_t *n_blocks, int *
  * It runs the same Algorithm 1 solve as dope_create + dope_set_unaries +
  * dope_set_weights + dope_solve (same kernels, same results), without a
  * context.  Arguments are those of dope_create plus: u[N] (float32, image
- * order) and wq[conn/2][N] (int32, image order) as DEVICE pointers, labels[N]
- * a DEVICE pointer receiving the labels (image order), *energy_int and
- * *iterations (host, may be NULL).  Calls no cudaMalloc / cudaFree and no
- * allocating library routine: all device state lives in one static device
- * array of DOPE_NOALLOC_SCRATCH_BYTES that every GPU loading this library
- * holds until the process exits.  Problems whose state does not fit
- * (roughly N <= 262144 pixels for 8-connected 32x32 blocks) are rejected with
- * DOPE_EINVAL before any GPU work.  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call
+ * order) and wq[conn/2][N] (int32, image order) as DEVICE pointers on the
+ * current device, labels[N] a DEVICE pointer on the current device receiving
+ * the labels (image order), *energy_int and *iterations (host, may be NULL).
+ * N is the product of grid[]; the function takes no lengths, so the caller
+ * must supply buffers of at least these element counts (the Python binding
+ * checks them).  Calls no cudaMalloc / cudaFree and no allocating library
+ * routine: all device state lives in one static device array of
+ * DOPE_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.  The state takes about (5 + 4 conn/2) N + 16 K F bytes
+ * (K blocks of F face pixels) plus 8 bytes per iteration of max_iter, each
+ * part rounded up to 256 bytes: 8-connected 32x32 blocks cost about 23 bytes
+ * per pixel (832 x 832 fits, 864 x 864 does not), 4-connected 16x16 blocks
+ * about 16.  Problems that do not fit, and max_iter above
+ * DOPE_NOALLOC_SCRATCH_BYTES / 8, are rejected with DOPE_EINVAL before any
+ * GPU work.  The array's memory is taken when this library's device code is
+ * first loaded on a device (the first call of an entry point that runs device
+ * code there); a caller whose allocator reserves the device's memory should
+ * make one call first.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, and only a
+ * successful lookup is kept (a failed one returns DOPE_ECUDA and is retried
+ * by the next call); make that first call before any stream capture.  Every call
  * shares the array and it keeps the last call's contents (each call clears
  * what must start at zero itself): calls that overlap on the GPU -- on two
  * streams, or from two host threads -- race and corrupt each other; issue

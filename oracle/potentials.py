@@ -20,12 +20,14 @@ takes a large part of the paper's run times.  The potentials follow Section 2:
     is given or, by default, the mean of |x_i - x_j| over all neighbour pairs
     (floored at 1e-6); entries whose partner lies outside the grid are 0.
 
-Two forms of the pairwise weights live here:
-  * ``contrast_weights`` -- the definition in FP64;
-  * ``contrast_weights_q`` -- the quantised weights rne(1024 w) with the
-    floating-point decision taken in FP32, the precision of the GPU kernel,
-    one correctly rounded operation at a time in the order the docstring
-    lists (only exp differs between implementations, by a few ulp).
+The oracle of the pairwise weights is ``contrast_weights``, the definition in
+FP64 (with ``mean_contrast`` for the default sigma); parity tests compare the
+GPU's quantised weights with rne(1024 w) of it outside a band around rounding
+ties that the FP32 error bound fixes.  ``contrast_weights_q`` and
+``sigma_fp32_path`` restate the same quantities with the decision taken in
+FP32, one correctly rounded operation at a time; they only illustrate (in the
+CPU tests) why FP32 and FP64 decisions differ near ties, and no parity test
+uses them as the reference.
 The data term is a float output (its quantisation happens later, in FP64, when
 it is loaded into a solver), so ``gmm_unaries`` is FP64 throughout.
 

@@ -705,7 +705,7 @@ int create_overlap(dope_ctx* c, const int64_t dims[3], const int32_t blk[3], con
     Al((void**)&A.a, sizeof(double) * KB);
     Al((void**)&A.yhat, KB);
     Al((void**)&c->r2blk, sizeof(double) * (size_t)b.K);
-    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
+    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * ((size_t)c->p.max_iter + 2);
     Al((void**)&c->ctrl, c->ctrl_bytes);
     if (rc) return rc;
     A.U = c->U;
@@ -1151,7 +1151,7 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
     A((void**)&c->yF, sizeof(double) * (size_t)g.K * g.F);
     A((void**)&c->aF, sizeof(double) * (size_t)g.K * g.F);
     A((void**)&c->r2blk, sizeof(double) * (size_t)g.K);
-    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(c->p.max_iter + 2);
+    c->ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * ((size_t)c->p.max_iter + 2);
     A((void**)&c->ctrl, c->ctrl_bytes);
     if (rc) { dope_destroy(c); return rc; }
     if (cudaMemsetAsync(c->ctrl, 0, c->ctrl_bytes, st) != cudaSuccess) {
@@ -1865,9 +1865,8 @@ static __device__ __align__(256) unsigned char dope_noalloc_scratch[DOPE_NOALLOC
 namespace {
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
-void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
-int g_noalloc_rc[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];     // device address of the array, once looked up
 
 // Face slots of a block: pixels with a neighbour outside the block, numbered
 // in increasing local index (same tables as dope_create builds on the host).
@@ -1937,23 +1936,43 @@ __global__ void k_face_tables(int bd, int bh, int bw, int16_t* faceIndex, int16_
     }
 }
 
-// Per-device set-up: device address of the scratch array.
+// Per-device set-up: device address of the scratch array, with the device
+// current.  Only a successful lookup is kept; a failed one (the module could
+// not be loaded, e.g. no memory left for the array) clears the error state
+// and is retried by the next call.
 int noalloc_setup(int* dev_out, void** ptr_out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return DOPE_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DOPE_ECUDA;
+    }
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return DOPE_EINVAL;
-    std::call_once(g_noalloc_once[dev], [dev]() {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
         void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, dope_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, dope_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return DOPE_ECUDA;
+        }
         g_noalloc_ptr[dev] = ptr;
-        g_noalloc_rc[dev] = (e == cudaSuccess && ptr) ? DOPE_OK : DOPE_ECUDA;
-    });
+    }
     *dev_out = dev;
     *ptr_out = g_noalloc_ptr[dev];
-    return g_noalloc_rc[dev];
+    return DOPE_OK;
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// off += align256(bytes), false if that passes `limit` (every term is checked
+// against the space left, so the sum cannot wrap)
+inline bool take(size_t& off, size_t bytes, size_t limit) {
+    if (off > limit || bytes > limit - off) return false;
+    const size_t a = align256(bytes);
+    if (a > limit - off) return false;
+    off += a;
+    return true;
+}
 
 }  // namespace
 
@@ -2012,20 +2031,22 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
     }
     const int nh = connectivity / 2;
 
-    // scratch layout
-    const size_t ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * (size_t)(prm.max_iter + 2);
+    // scratch layout (every term checked against the space left)
+    const size_t LIM = (size_t)DOPE_NOALLOC_SCRATCH_BYTES;
+    if ((size_t)prm.max_iter > LIM / sizeof(unsigned long long)) return DOPE_EINVAL;
+    const size_t ctrl_bytes = sizeof(Ctrl) + sizeof(unsigned long long) * ((size_t)prm.max_iter + 2);
     size_t off = 0;
-    const size_t o_ctrl = off;  off += align256(ctrl_bytes);
-    const size_t o_U = off;     off += align256(sizeof(int32_t) * (size_t)N);
-    const size_t o_Wl = off;    off += align256(sizeof(int32_t) * (size_t)N * nh);
-    const size_t o_yhat = off;  off += align256((size_t)N);
-    const size_t o_yF = off;    off += align256(sizeof(double) * (size_t)g.K * g.F);
-    const size_t o_aF = off;    off += align256(sizeof(double) * (size_t)g.K * g.F);
-    const size_t o_r2 = off;    off += align256(sizeof(double) * (size_t)g.K);
-    const size_t o_fi = off;    off += align256(sizeof(int16_t) * (size_t)B);
-    const size_t o_fl = off;    off += align256(sizeof(int16_t) * (size_t)(g.F ? g.F : 1));
-    const size_t o_halo = off;  off += align256(sizeof(int) * (size_t)connectivity * (g.F ? g.F : 1));
-    if (off > (size_t)DOPE_NOALLOC_SCRATCH_BYTES) return DOPE_EINVAL;
+    const size_t o_ctrl = off;  if (!take(off, ctrl_bytes, LIM)) return DOPE_EINVAL;
+    const size_t o_U = off;     if (!take(off, sizeof(int32_t) * (size_t)N, LIM)) return DOPE_EINVAL;
+    const size_t o_Wl = off;    if (!take(off, sizeof(int32_t) * (size_t)N * nh, LIM)) return DOPE_EINVAL;
+    const size_t o_yhat = off;  if (!take(off, (size_t)N, LIM)) return DOPE_EINVAL;
+    const size_t o_yF = off;    if (!take(off, sizeof(double) * (size_t)g.K * g.F, LIM)) return DOPE_EINVAL;
+    const size_t o_aF = off;    if (!take(off, sizeof(double) * (size_t)g.K * g.F, LIM)) return DOPE_EINVAL;
+    const size_t o_r2 = off;    if (!take(off, sizeof(double) * (size_t)g.K, LIM)) return DOPE_EINVAL;
+    const size_t o_fi = off;    if (!take(off, sizeof(int16_t) * (size_t)B, LIM)) return DOPE_EINVAL;
+    const size_t o_fl = off;    if (!take(off, sizeof(int16_t) * (size_t)(g.F ? g.F : 1), LIM)) return DOPE_EINVAL;
+    const size_t o_halo = off;
+    if (!take(off, sizeof(int) * (size_t)connectivity * (g.F ? g.F : 1), LIM)) return DOPE_EINVAL;
 
     int dev = 0;
     void* base = nullptr;

@@ -380,9 +380,29 @@ def dope_get_profile(ctx):
 def dope_solve_noalloc(grid, connectivity, block_shape, lam, u, wq, labels, params=None, stream=None,
                        allow_notconv=False):
     """Allocation-free solve (no context, no device allocation): u, wq and
-    labels must be CUDA tensors.  Returns (E_int, iterations, status)."""
+    labels must be CUDA tensors on the current device with u of N elements,
+    wq of shape (conn/2, N) (or conn/2 * N elements) and labels of at least N
+    elements, N = prod(grid); the C function takes no lengths, so they are
+    checked here before anything runs.  Returns (E_int, iterations, status)."""
     grid = [int(x) for x in grid]
     block = [int(x) for x in block_shape]
+    n = int(np.prod(grid)) if grid else 0
+    nh = int(connectivity) // 2
+    for name, x in (("u", u), ("wq", wq), ("labels", labels)):
+        if not (hasattr(x, "is_cuda") and x.is_cuda):
+            raise TypeError(f"dope_solve_noalloc takes device tensors ({name})")
+    import torch
+    cur = torch.cuda.current_device()
+    for name, x in (("u", u), ("wq", wq), ("labels", labels)):
+        if x.device.index != cur:
+            raise ValueError(f"dope_solve_noalloc: {name} is on cuda:{x.device.index}, the current device is "
+                             f"cuda:{cur}")
+    if u.numel() != n:
+        raise ValueError(f"dope_solve_noalloc: u has {u.numel()} elements, the grid {n}")
+    if wq.numel() != nh * n or (wq.dim() == 2 and tuple(wq.shape) != (nh, n)):
+        raise ValueError(f"dope_solve_noalloc: wq must be ({nh}, {n}), got {tuple(wq.shape)}")
+    if labels.numel() < n:
+        raise ValueError(f"dope_solve_noalloc: labels has {labels.numel()} elements, needs {n}")
     pu, wu, ku = _ptr(u, _t(np.float32))
     pw, ww, kw = _ptr(wq, _t(np.int32))
     pl, wl, kl = _ptr(labels, _t(np.uint8))

@@ -289,6 +289,40 @@ def ellipsoids3d(seed=0, shape=(128, 256, 256), lam=3.0, block=(8, 16, 16), nois
             "gmm_bg": (np.array([1.0]), np.array([[m0]]), np.array([[[s0 * s0]]]))}
 
 
+def crop_instance(d, lo, shape):
+    """The sub-grid of instance d starting at `lo` with extent `shape` (same
+    connectivity, block shape, lambda, mu0): unaries cropped, weights cropped
+    with every n-link that leaves the crop set to 0."""
+    grid = tuple(d["grid"])
+    nd = len(grid)
+    assert nd == len(lo) == len(shape)
+    sl = tuple(slice(a, a + n) for a, n in zip(lo, shape))
+    u = np.ascontiguousarray(d["u"].reshape(grid)[sl]).reshape(-1)
+    nh = d["conn"] // 2
+    w = np.array(d["wq"].reshape((nh,) + grid)[(slice(None),) + sl])
+    offs = FWD_OFFSETS[d["conn"]]
+    sh3 = (1,) * (3 - nd) + tuple(shape)
+    w3 = w.reshape((nh,) + sh3)
+    zz, yy, xx = np.meshgrid(*[np.arange(n) for n in sh3], indexing="ij")
+    for k, (dz, dy, dx) in enumerate(offs):
+        z2, y2, x2 = zz + dz, yy + dy, xx + dx
+        out = (z2 < 0) | (z2 >= sh3[0]) | (y2 < 0) | (y2 >= sh3[1]) | (x2 < 0) | (x2 >= sh3[2])
+        w3[k][out] = 0
+    r = dict(d, grid=tuple(shape), u=u, wq=np.ascontiguousarray(w3.reshape(nh, -1)))
+    n = int(np.prod(grid))
+    for key in ("image", "truth"):
+        if key in d:
+            a = np.asarray(d[key])
+            extra = a.size // n
+            b = a.reshape(grid + ((extra,) if extra > 1 else ()))[sl]
+            if a.ndim == 1:
+                b = b.reshape(-1)
+            elif a.ndim == 2:
+                b = b.reshape(-1, extra)
+            r[key] = np.ascontiguousarray(b)
+    return r
+
+
 # --------------------------------------------------------------------------
 # Small random instances for tests
 # --------------------------------------------------------------------------

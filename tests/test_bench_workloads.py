@@ -33,3 +33,29 @@ def test_replica_helpers_single_process():
     import bench
     assert bench.job_rate(100, 1, 4.0) == 25.0
     assert bench.max_over_ranks(1.25, 1) == 1.25
+
+
+def test_reference_sample_is_a_slab_of_the_volume():
+    """The reference arm's bounded sample of the 256x256x128 volume is its
+    middle 16-slice slab: same unaries, weights inside the slab unchanged,
+    n-links leaving it zero, whole blocks."""
+    import bench
+    from paper_1704_03116_gb300 import inputs
+    full = inputs.ellipsoids3d()
+    insts, sample = bench.reference_sample("ellipsoids256")
+    d = insts[0]
+    assert d["grid"] == (16, 256, 256) and "slab" in sample
+    assert all(g % b == 0 for g, b in zip(d["grid"], d["block"]))
+    u = full["u"].reshape(128, 256, 256)[56:72]
+    assert np.array_equal(d["u"].reshape(16, 256, 256), u)
+    w = full["wq"].reshape(3, 128, 256, 256)[:, 56:72]
+    dw = d["wq"].reshape(3, 16, 256, 256)
+    assert np.array_equal(dw[:, :-1], w[:, :-1]) and (dw[2, -1] == 0).all()
+    assert np.array_equal(dw[:2, -1], w[:2, -1])
+
+
+def test_dice():
+    import bench
+    a = np.array([1, 1, 0, 0], np.uint8)
+    b = np.array([1, 0, 1, 0], np.uint8)
+    assert bench.dice(a, a) == 1.0 and bench.dice(a, b) == 0.5 and bench.dice(a * 0, b * 0) == 1.0

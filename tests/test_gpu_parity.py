@@ -106,11 +106,20 @@ def _solve_both(orc, dp, d, **kw):
     return inst, ref, g, lab, E, it
 
 
-def _assert_solve_parity(ref, lab, E, it, trace):
+def _assert_solve_parity(ref, lab, E, it, trace, orc=None, dp=None, d=None, inst=None):
     if it != ref["iterations"]:
         t = min(it, ref["iterations"])
         # only allowed when the deciding residual sits on eps within rounding
         assert abs(ref["rmax"][t - 1] - 1e-3) <= 1e-9 * 1e-3, (it, ref["iterations"])
+        # labels and energy still agree at the common iteration: both sides
+        # rerun with max_iter = t
+        if orc is not None:
+            ref_t = orc.admm(inst, d["mu0"], 1.05, 1e-3, t)
+            g_t = dp.Dope.from_instance(d, max_iter=t)
+            lab_t, E_t, it_t = g_t.solve(allow_notconv=True)
+            assert it_t == ref_t["iterations"] == t
+            assert np.array_equal(lab_t, ref_t["labels"]) and E_t * 1024 == ref_t["energy"]
+            np.testing.assert_allclose(g_t.trace(), ref_t["rmax"], rtol=1e-9, atol=1e-15)
         return
     assert np.array_equal(lab, ref["labels"])
     assert E * 1024 == ref["energy"]
@@ -122,14 +131,14 @@ def _assert_solve_parity(ref, lab, E, it, trace):
 def test_solve_parity_small(orc, dp, grid, conn, block, lam):
     d = inputs.random_instance(grid, conn, block, lam=lam, seed=11)
     inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
-    _assert_solve_parity(ref, lab, E, it, g.trace())
+    _assert_solve_parity(ref, lab, E, it, g.trace(), orc, dp, d, inst)
 
 
 def test_solve_parity_disk64(orc, dp):
     """64x64 disk, 4-conn, lambda 2, 16x16 sub-regions; gap to sGC reported."""
     d = inputs.disk64()
     inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
-    _assert_solve_parity(ref, lab, E, it, g.trace())
+    _assert_solve_parity(ref, lab, E, it, g.trace(), orc, dp, d, inst)
     _, egc = orc.global_mincut(inst)
     gap = (E * 1024 - egc) / abs(egc)
     print(f"disk64: iterations {it}, E {E}, E_gc {egc / 1024}, gap {gap:.3e}")
@@ -141,7 +150,7 @@ def test_solve_parity_ellipses512(orc, dp, lam):
     """512x512 RGB ellipses, 8-conn contrast Potts, 32x32 sub-regions (full size)."""
     d = inputs.ellipses_rgb(lam=lam)
     inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
-    _assert_solve_parity(ref, lab, E, it, g.trace())
+    _assert_solve_parity(ref, lab, E, it, g.trace(), orc, dp, d, inst)
     _, egc = orc.global_mincut(inst)
     print(f"ellipses512 lam={lam}: iterations {it}, gap {(E * 1024 - egc) / abs(egc):.3e}, "
           f"stats {g.stats()}")
@@ -151,7 +160,7 @@ def test_solve_parity_ellipsoids_full(orc, dp):
     """256x256x128 volume, 6-conn, 16x16x8 sub-regions, lambda 3 (full size)."""
     d = inputs.ellipsoids3d()
     inst, ref, g, lab, E, it = _solve_both(orc, dp, d)
-    _assert_solve_parity(ref, lab, E, it, g.trace())
+    _assert_solve_parity(ref, lab, E, it, g.trace(), orc, dp, d, inst)
     print(f"ellipsoids: iterations {it}, E {E}, stats {g.stats()}")
 
 

@@ -7,9 +7,18 @@ the oracle (oracle/potentials.py).
     the FP32 unit roundoff (6e-8) times the magnitude of the terms, which the
     two log-likelihoods bound; 4e-6 (|ll_fg| + |ll_bg| + 1) leaves a margin of
     about 60 roundoffs.
-  * weights: the quantised decision in FP32 on both sides; equal except where
-    1024 w lies within 1e-3 of a rounding tie (the two exps may differ by a
-    few ulp there), and within one of the FP64 definition everywhere.
+  * weights: against the FP64 definition, w = exp(-|x_i - x_j|^2 / (2 s^2))
+    (divided by the pixel distance where asked) at the kernel's sigma s,
+    quantised rne(1024 w).  The kernel decides in FP32: |x_i - x_j|^2 carries
+    at most (C + 2) roundings, k = 1 / (2 s^2) one, their product one, exp a
+    few ulp, so the argument a = d2 k is off by at most (C + 4) 2^-24 a and
+    1024 w by at most 1024 (a e^-a (C + 4) + 4) 2^-24 <= 1024 (0.37 (C + 4) + 4)
+    6e-8 < 5e-4 (C <= 4).  So the quantised weights equal the definition's
+    wherever 1024 w lies farther than 1e-3 from a rounding tie, and are within
+    one of it everywhere.
+  * sigma (the mean contrast): each pair's root in FP32 (at most C + 3
+    roundings) and each pixel's sum of up to conn/2 roots in FP32, then FP64:
+    relative error below (C + 3 + conn/2) 2^-24 <= 1e-5 of the FP64 definition.
 """
 import numpy as np
 import pytest
@@ -93,14 +102,21 @@ def test_unaries_clip_and_empty(dp, P):
 
 
 def _check_w(P, img, dims, conn, got, sig_got, sigma=None, inv_dist=False):
+    """The kernel's quantised weights against the FP64 definition (see the
+    module docstring for the tie band and the sigma bound)."""
     img = np.asarray(img, np.float32)
-    wq, sig, margin = P.contrast_weights_q(img, dims, conn, sigma=sigma, inv_dist=inv_dist)
-    assert sig_got == pytest.approx(sig, rel=1e-12)
-    diff = np.abs(got.astype(np.int64) - wq)
+    if sigma is None:
+        sig64 = max(P.mean_contrast(img, dims, conn), 1e-6)
+        assert abs(sig_got - sig64) <= 1e-5 * sig64, (sig_got, sig64)
+    else:
+        assert sig_got == sigma
+    w64, _ = P.contrast_weights(img, dims, conn, sigma=sig_got, inv_dist=inv_dist)
+    v = 1024.0 * w64
+    ref = np.rint(v).astype(np.int64)
+    margin = np.abs(np.abs(v - np.floor(v)) - 0.5)
+    diff = np.abs(got.astype(np.int64) - ref)
     assert diff.max() <= 1
     assert (diff[margin > 1e-3] == 0).all(), int((diff[margin > 1e-3] != 0).sum())
-    w64, _ = P.contrast_weights(img, dims, conn, sigma=sig, inv_dist=inv_dist)
-    assert np.abs(got.astype(np.int64) - np.rint(1024.0 * w64)).max() <= 1
     return int((diff != 0).sum())
 
 

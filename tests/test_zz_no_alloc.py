@@ -60,3 +60,46 @@ def test_noalloc_rejects_oversize(dp):
     with pytest.raises(dp.DopeError) as ei:
         dp.dope_solve_noalloc((2048, 2048), 8, (32, 32), 1.0, u, w, lab)
     assert ei.value.status == dp.DOPE_EINVAL
+
+
+def test_noalloc_size_boundary(dp):
+    """8-connected 32x32 blocks cost about 23 bytes per pixel of the 16 MiB
+    array: 832 x 832 fits (and equals the regular solve), 864 x 864 does not."""
+    d = inputs.random_instance((832, 832), 8, (32, 32), lam=2.0, seed=6)
+    ref = _regular(dp, d)
+    got = _noalloc(dp, d)
+    assert np.array_equal(got[0], ref[0]) and got[1] == ref[1] and got[2] == ref[2]
+    import torch
+    n = 864 * 864
+    u = torch.zeros(n, dtype=torch.float32, device="cuda")
+    w = torch.zeros((4, n), dtype=torch.int32, device="cuda")
+    lab = torch.empty(n, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dp.DopeError) as ei:
+        dp.dope_solve_noalloc((864, 864), 8, (32, 32), 1.0, u, w, lab)
+    assert ei.value.status == dp.DOPE_EINVAL
+    p = dp.dope_default_params()
+    p.max_iter = 1 << 30                     # its trace alone would not fit
+    with pytest.raises(dp.DopeError) as ei:
+        dp.dope_solve_noalloc((64, 64), 8, (32, 32), 1.0, u[:4096], w[:, :4096].contiguous(), lab, params=p)
+    assert ei.value.status == dp.DOPE_EINVAL
+
+
+def test_noalloc_rejects_short_or_foreign_buffers(dp):
+    """Buffers shorter than the grid, a weight array of the wrong shape, and
+    host tensors are refused by the binding before anything runs."""
+    import torch
+    n = 64 * 64
+    u = torch.zeros(n, dtype=torch.float32, device="cuda")
+    w = torch.zeros((4, n), dtype=torch.int32, device="cuda")
+    lab = torch.empty(n, dtype=torch.uint8, device="cuda")
+    args = ((64, 64), 8, (32, 32), 1.0)
+    with pytest.raises(ValueError):
+        dp.dope_solve_noalloc(*args, u[: n - 1], w, lab)
+    with pytest.raises(ValueError):
+        dp.dope_solve_noalloc(*args, u, w[:2].contiguous(), lab)
+    with pytest.raises(ValueError):
+        dp.dope_solve_noalloc(*args, u, w.reshape(2, 2 * n), lab)
+    with pytest.raises(ValueError):
+        dp.dope_solve_noalloc(*args, u, w, lab[: n - 1])
+    with pytest.raises(TypeError):
+        dp.dope_solve_noalloc(*args, u.cpu(), w, lab)
