@@ -62,8 +62,10 @@ struct dope_ctx {
     int ov_threads = 0, ov_smem = 0;
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
-    unsigned char* sched = nullptr;   // block worklists of k_admm_persistent (sched_bytes)
-    unsigned sched_epoch = 0;         // persistent launches issued with them
+    unsigned char* sched = nullptr;   // block worklists of the persistent / batched kernels (sched_bytes)
+    unsigned sched_epoch = 0;         // launches issued with them
+    int sched_t = -1;                 // the lists are valid for iteration sched_t + 1 (-1: not valid)
+    bool sched_launch = false;        // the launch in flight uses the lists
     Ctrl* hctrl = nullptr;      // pinned host copy of the whole control block (dope_solve's single read)
     // staging (lazily allocated)
     void* stage = nullptr;
@@ -304,13 +306,20 @@ int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = 
     P.NH = c->NH;
     P.hslot = c->hslot;
     P.hinfo = c->hinfo;
+    P.wl_cont = 0;
+    c->sched_launch = false;
     if (c->sched && !c->resident && c->p.mu_fact >= 1.0) {
         // worklists: valid while mu does not decrease (the forced test's bound
-        // only grows); each launch's marks carry a new epoch
+        // only grows); each launch's marks carry a new epoch.  A launch that
+        // continues the previous list launch of this context from the state it
+        // left (nothing changed since) starts from its lists.
         ++c->sched_epoch;
         P.s.sched = P.u.sched = c->sched;
         P.s.epoch = P.u.epoch = c->sched_epoch;
+        P.wl_cont = (c->t > 0 && c->sched_t == c->t) ? 1 : 0;
+        c->sched_launch = true;
     }
+    c->sched_t = -1;
     void* args[] = {&P};
     if (c->profiling) {
         if (c->ev.size() < 2) {
@@ -339,6 +348,7 @@ int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = 
 int persistent_collect(dope_ctx* c, int t0, const Ctrl& h, const unsigned long long* r2trace, cudaStream_t st) {
     if (h.status) return h.status;
     const int done = h.iters_done - t0;
+    c->sched_t = c->sched_launch ? t0 + done : -1;
     const int converged = h.conv_t != 0;
     if (c->profiling) {
         float ms = 0.f;
@@ -467,6 +477,7 @@ int run_iterations(dope_ctx* c, int n, cudaStream_t st) {
     }
     c->t = t0 + done;
     c->mu = mus[done];
+    c->sched_t = -1;
     c->stats.iterations = c->t;
     c->stats.converged = converged;
     fill_stats(c, h);
@@ -525,6 +536,7 @@ void raise_smem_limits() {
 int reset_state_async(dope_ctx* c, cudaStream_t st) {
     c->t = 0;
     c->mu = c->p.mu0;
+    c->sched_t = -1;
     const int threads = 256;
     k_init_state<<<grid_for((long long)c->g.K * c->g.F, threads), threads, 0, st>>>(c->g, c->yF, c->aF);
     CK(cudaGetLastError());
@@ -627,6 +639,7 @@ void ov_raise_smem() {
 int ov_reset_async(dope_ctx* c, cudaStream_t st) {
     c->t = 0;
     c->mu = c->p.mu0;
+    c->sched_t = -1;
     const OvArgs& A = c->oa;
     const int threads = 256;
     // y = 1/2 (Algorithm 1 initialisation), a = 0, yhat = 0
@@ -861,6 +874,7 @@ int ov_run(dope_ctx* c, int n, cudaStream_t st) {
     }
     c->t = t0 + done;
     c->mu = mus[done];
+    c->sched_t = -1;
     c->stats.iterations = c->t;
     c->stats.converged = converged;
     fill_stats(c, h);
@@ -1187,8 +1201,9 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (c->nsm_smem > optin || pad) { dope_destroy(c); return DOPE_EINVAL; }
     }
-    if (!c->nsm && !c->resident && c->persist_grid > 0) {
-        // worklists of the persistent kernel; marks start below every launch's
+    if (!c->nsm) {
+        // worklists of the persistent and batched kernels; marks start below
+        // every launch's
         const size_t sb = sched_bytes(g.K, g.F);
         A((void**)&c->sched, sb);
         if (rc) { dope_destroy(c); return rc; }
@@ -1278,6 +1293,7 @@ int dope_create(const int64_t* grid, int ndim, int connectivity, const int32_t* 
 
 // Quantise device unaries (user order) into the context (stream-ordered).
 static int issue_set_unaries(dope_ctx* c, const float* src, cudaStream_t st) {
+    if (c) c->sched_t = -1;   // inputs or labels change: the worklists no longer hold
     const int threads = 256;
     k_set_unaries<<<grid_for(c->g.N, threads), threads, 0, st>>>(c->g, src, c->U, c->ctrl);
     CK(cudaGetLastError());
@@ -1308,6 +1324,7 @@ int dope_set_unaries(dope_ctx* c, const float* u, int64_t n, int where, void* st
 
 // Quantise device weights (user order, [conn/2][Nu]) into the context.
 static int issue_set_weights(dope_ctx* c, const int32_t* src, cudaStream_t st) {
+    if (c) c->sched_t = -1;   // inputs or labels change: the worklists no longer hold
     const int threads = 256;
     const int blocks = grid_for(c->g.N, threads);
     if (c->ov) {
@@ -1379,6 +1396,7 @@ int dope_set_inputs(dope_ctx* c, const float* u, const int32_t* wq, int64_t n, i
 // scratch whose second double holds the sigma used.
 static int image_issue(dope_ctx* c, const float* image, int channels, const dope_gmm* fg, const dope_gmm* bg, double clip,
                 double sigma, int inv_dist, int where, cudaStream_t st, cudaEvent_t after_copies, double** ws_out) {
+    if (c) c->sched_t = -1;   // inputs change: the worklists no longer hold
     if (!c || !image || channels < 1 || channels > DOPE_GMM_MAX_CH || (where != DOPE_HOST && where != DOPE_DEVICE))
         return DOPE_EINVAL;
     const size_t n = (size_t)c->g.Nu;
@@ -1467,6 +1485,7 @@ static int solve_issue(dope_ctx* c, uint8_t* labels, int where, int want_energy,
     }
     c->t = 0;
     c->mu = c->p.mu0;
+    c->sched_t = -1;
     const int n = c->p.max_iter;
     memset(&c->stats, 0, sizeof(c->stats));
     const bool pend = c->pending;
@@ -1551,6 +1570,7 @@ int dope_solve(dope_ctx* c, uint8_t* labels, int where, int64_t* energy_int, int
     // Algorithm 1 initialisation: y = 1/2, a = 0, mu = mu0 (stream-ordered)
     c->t = 0;
     c->mu = c->p.mu0;
+    c->sched_t = -1;
     c->launches = 1;
     const int threads = 256;
     if (single_launch(c)) {
@@ -1681,6 +1701,7 @@ int dope_set_state(dope_ctx* c, const double* y, const double* a, const uint8_t*
     }
     c->t = t;
     c->mu = mu;
+    c->sched_t = -1;
     return DOPE_OK;
 }
 
@@ -1712,6 +1733,7 @@ int dope_shifted_caps(dope_ctx* c, int64_t* C, void* stream) {
 }
 
 int dope_block_cuts(dope_ctx* c, const int64_t* C, uint8_t* yhat, void* stream) {
+    if (c) c->sched_t = -1;   // inputs or labels change: the worklists no longer hold
     if (!c || !C || !yhat || !c->have_w) return DOPE_EINVAL;
     if (c->ov || c->nsm) return DOPE_EINVAL;
     cudaStream_t st = S(stream);
@@ -1839,6 +1861,7 @@ int dope_get_geometry(dope_ctx* c, int64_t* n_pixels, int64_t* n_blocks, int* bl
 
 int dope_image_upload_async(dope_ctx* c, const dope_image_request* q, int where, cudaStream_t st,
                             cudaEvent_t after_copies) {
+    if (c) c->sched_t = -1;   // inputs change: the worklists no longer hold
     if (!c || !q) return DOPE_EINVAL;
     int rc = image_issue(c, q->image, q->channels, &q->fg, &q->bg, q->clip, q->sigma, q->inv_dist, where, st,
                          after_copies, nullptr);
@@ -2161,6 +2184,7 @@ extern "C" int dope_solve_noalloc(const int64_t* grid, int ndim, int connectivit
 // ---------------------------------------------------------------------------
 int dope_upload_async(dope_ctx* c, const float* u, const int32_t* wq, int where, cudaStream_t st,
                       cudaEvent_t after_copies) {
+    if (c) c->sched_t = -1;   // inputs or labels change: the worklists no longer hold
     if (!c || !u || !wq || (where != DOPE_HOST && where != DOPE_DEVICE)) return DOPE_EINVAL;
     const size_t n = (size_t)c->g.Nu;
     const int nh = c->conn / 2;
@@ -2381,12 +2405,23 @@ int dope_batch_launch(dope_ctx* const* cs, int n, int n_iter, int exit_on_done, 
         d.sched = nullptr;
         d.epoch = 0;
         BatchProb& b = w->hprob[i];
+        b.cont = 0;
+        c->sched_launch = false;
+        if (c->sched && c->p.mu_fact >= 1.0) {
+            // worklists (see k_admm_batch); each launch's marks carry a new
+            // epoch, and a launch that continues this context's previous list
+            // launch from the state it left starts from its lists
+            d.sched = c->sched;
+            d.epoch = ++c->sched_epoch;
+            b.cont = (c->t > 0 && c->sched_t == c->t) ? 1 : 0;
+            c->sched_launch = true;
+        }
+        c->sched_t = -1;
         b.t0 = c->t;
         const int left = c->p.max_iter - c->t;
         b.n = n_iter < left ? n_iter : left;
         if (b.n < 0) b.n = 0;
         b.K = c->g.K;
-        b.pad = 0;
         b.mu = c->mu;
         b.mu_fact = c->p.mu_fact;
     }
@@ -2446,17 +2481,21 @@ int dope_batch_collect(dope_ctx* const* cs, int n, dope_batch_ws* w, int* t, int
         w->holds_table = false;
         table_release();
     }
+    const int launch_status = *w->hstatus;
     for (int i = 0; i < n; ++i) {
         dope_ctx* c = cs[i];
         const BatchOut& o = w->hout[i];
         c->t = o.t;
         c->mu = o.mu;
+        c->sched_t = (c->sched_launch && o.status == 0 && launch_status == 0) ? o.t : -1;
         memset(&c->stats, 0, sizeof(c->stats));
         c->stats.iterations = o.t;
         c->stats.converged = o.conv;
         c->stats.rmax_last = std::sqrt(o.r2);
         c->stats.kernel_launches = c->launches;
         c->stats.solver_kernel = 3;
+        c->stats.blocks_solved = (int64_t)o.work[0];
+        c->stats.blocks_updated = (int64_t)o.work[1];
         if (t) t[i] = o.t;
         if (conv) conv[i] = o.conv;
         if (status) status[i] = o.status;

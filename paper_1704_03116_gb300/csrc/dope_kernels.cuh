@@ -73,8 +73,6 @@ struct Ctrl {
                                     // wait at the closing barrier, rest of the resolution
     unsigned long long pcyc[4];     // persistent kernel, thread 0 of each CTA: solve phase,
                                     // first barrier wait, update phase, second barrier wait
-    unsigned sq_n[2];               // worklists of the persistent kernel, by parity of the
-    unsigned uq_n[2];               // iteration they serve: blocks to solve / to update
     unsigned long long sched_work[2];   // blocks solved / updated from the worklists (statistics)
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
 };
@@ -102,6 +100,8 @@ struct Ctrl {
 // block and evaluates nothing (so a state set from outside is never trusted).
 //
 // Per-context buffer (sched_bytes), K blocks, F face slots per block:
+//   sq_n, uq_n  u32 [2]    lengths of the lists below (kept here, not in the
+//                          control block, so they outlive its clearing)
 //   smark, umark u64 [K]   last (epoch << 32 | t) a block was put on the
 //                          solve / update list (one entry per list)
 //   sq, uq      int32 [2][K]  the lists, by parity of their iteration
@@ -109,6 +109,8 @@ struct Ctrl {
 //   yhF         uint8 [K][F]  label of each face slot as of its block's last update
 // ---------------------------------------------------------------------------
 struct SchedView {
+    unsigned* sq_n;
+    unsigned* uq_n;
     unsigned long long* smark;
     unsigned long long* umark;
     int* sq;
@@ -118,12 +120,14 @@ struct SchedView {
 };
 
 __host__ __device__ inline size_t sched_bytes(int K, int F) {
-    return 16 * (size_t)K + 16 * (size_t)K + (size_t)K + (size_t)K * F;
+    return 16 + 16 * (size_t)K + 16 * (size_t)K + (size_t)K + (size_t)K * F;
 }
 
 __device__ __forceinline__ SchedView sched_view(unsigned char* base, int K) {
     SchedView s;
-    s.smark = reinterpret_cast<unsigned long long*>(base);
+    s.sq_n = reinterpret_cast<unsigned*>(base);
+    s.uq_n = s.sq_n + 2;
+    s.smark = reinterpret_cast<unsigned long long*>(base + 16);
     s.umark = s.smark + K;
     s.sq = reinterpret_cast<int*>(s.umark + K);
     s.uq = s.sq + 2 * (size_t)K;
@@ -728,7 +732,7 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
         if (it.qeval) {
             __syncthreads();
             const SchedView sv = sched_view(A.sched, g.K);
-            wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &A.ctrl->uq_n[it.t & 1],
+            wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &sv.uq_n[it.t & 1],
                          wl_mark(A.epoch, it.t));
             __syncthreads();
         }
@@ -757,7 +761,7 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
         if ((tid & 31) == 0 && pm) atomicOr(&s_pm, pm);
         __syncthreads();
         const SchedView sv = sched_view(A.sched, g.K);
-        wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &A.ctrl->uq_n[it.t & 1],
+        wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &sv.uq_n[it.t & 1],
                          wl_mark(A.epoch, it.t));
         __syncthreads();
     }
@@ -1120,7 +1124,7 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
     }
     __syncthreads();
     if (wl) {
-        wl_push_mask(g, k, pmask[0], sv.smark, sv.sq + (size_t)((t + 1) & 1) * g.K, &A.ctrl->sq_n[(t + 1) & 1],
+        wl_push_mask(g, k, pmask[0], sv.smark, sv.sq + (size_t)((t + 1) & 1) * g.K, &sv.sq_n[(t + 1) & 1],
                      wl_mark(A.epoch, t + 1));
         __syncthreads();
     }
@@ -1374,6 +1378,7 @@ struct PersistArgs {
     int NH;                 // halo pixels of a block (distinct cross-block neighbours)
     const int16_t* hslot;   // [CONN][F] halo pixel of (direction, face slot), -1 if none
     const int* hinfo;       // [NH] halo_entry of each halo pixel
+    int wl_cont;            // 1: the worklists left by the previous launch hold (first iteration uses them)
     uint8_t* out_labels;    // finish (a8) in the launch: labels in the caller's image order (or null)
     int out_energy;         // finish (a8) in the launch: E_int of the labels into ctrl->energy
 };
@@ -1532,16 +1537,16 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
         IterArgs it = iter_args(t, mu);
         // with worklists, the launch's first iteration does every block;
         // later ones the blocks on the lists (see sched_view)
-        const bool full = !wl || j == 0;
+        const bool full = !wl || (j == 0 && !P.wl_cont);
         it.qeval = !full;
         // the update counter is idle during the solve phase and vice versa,
         // so each is reset in the other phase; likewise the list counts
         const long long c0 = clock64();
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->work[1] = 0u;
-            if (wl) c->sq_n[(t + 1) & 1] = 0u;
+            if (wl) sv.sq_n[(t + 1) & 1] = 0u;
         }
-        const int ns = full ? K : (int)__ldcg(&c->sq_n[t & 1]);
+        const int ns = full ? K : (int)__ldcg(&sv.sq_n[t & 1]);
         for (int i = next_block(P.dynamic, &c->work[0], -1, &s_k); i < ns;
              i = next_block(P.dynamic, &c->work[0], i, &s_k))
             solve_block<CONN>(P.s, it, full ? i : __ldcg(&sv.sq[(t & 1) * (size_t)K + i]), smem);
@@ -1550,9 +1555,9 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
         const long long c2 = clock64();
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->work[0] = 0u;
-            if (wl) c->uq_n[(t + 1) & 1] = 0u;
+            if (wl) sv.uq_n[(t + 1) & 1] = 0u;
         }
-        const int nu = full ? K : (int)__ldcg(&c->uq_n[t & 1]);
+        const int nu = full ? K : (int)__ldcg(&sv.uq_n[t & 1]);
         for (int i = next_block(P.dynamic, &c->work[1], -1, &s_k); i < nu;
              i = next_block(P.dynamic, &c->work[1], i, &s_k))
             update_block<CONN>(P.u, mu, t, full ? i : __ldcg(&sv.uq[(t & 1) * (size_t)K + i]), full ? 1 : 0);
@@ -2320,7 +2325,7 @@ struct BatchProb {
     int t0;                 // iterations done before the launch
     int n;                  // iterations allowed in this launch
     int K;                  // blocks
-    int pad;
+    int cont;               // 1: the worklists left by this problem's previous launch hold
     double mu;              // mu of iteration t0 + 1
     double mu_fact;
 };
@@ -2333,6 +2338,7 @@ struct BatchOut {
     int pad;
     double mu;              // mu of iteration t + 1
     double r2;              // max_k r2_k of iteration t (0 if t = 0)
+    unsigned long long work[2];   // the problem's block solves / updates run from its worklists so far
 };
 
 struct BatchArgs {
@@ -2356,6 +2362,25 @@ __device__ __forceinline__ int batch_owner(const int* lbase, int nlive, int gk) 
     return lo;
 }
 
+// Warp 0: exclusive prefix sums of s_cnt[0 .. nlive) into s_lbase, the total
+// into *s_total (ballot-free shuffle scan in chunks of 32).
+__device__ __forceinline__ void batch_scan(const int* s_cnt, int* s_lbase, int nlive, int* s_total) {
+    const int lane = threadIdx.x & 31;
+    int run = 0;
+    for (int c0 = 0; c0 < nlive; c0 += 32) {
+        const int q = c0 + lane;
+        const int kp = q < nlive ? s_cnt[q] : 0;
+        int v = kp;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (q < nlive) s_lbase[q] = run + v - kp;
+        run += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) *s_total = run;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(BatchArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -2363,9 +2388,11 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
     __shared__ int s_t[BATCH_MAX];
     __shared__ int s_K[BATCH_MAX];
     __shared__ int s_list[BATCH_MAX];     // live problems, in problem order
-    __shared__ int s_lbase[BATCH_MAX];    // their first list entries
+    __shared__ int s_lbase[BATCH_MAX];    // their first entries in the phase's list
+    __shared__ int s_cnt[BATCH_MAX];      // their entries in the phase's list
     __shared__ unsigned char s_alive[BATCH_MAX];
     __shared__ unsigned char s_conv[BATCH_MAX];
+    __shared__ unsigned char s_full[BATCH_MAX];   // 1: this iteration does every block of the problem
     __shared__ int s_nlive, s_total, s_k, s_any, s_done;
     const int np = P.nprob;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -2381,37 +2408,43 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
     __syncthreads();
     unsigned nbar = 0;
     for (;;) {
-        // live list and its block bases (warp 0, ballot + shuffle scan)
+        // live list (warp 0, ballot compaction)
         if (wid == 0) {
-            int run = 0, cnt = 0;
+            int cnt = 0;
             for (int c0 = 0; c0 < np; c0 += 32) {
                 const int p = c0 + lane;
                 const bool al = p < np && s_alive[p];
-                const int kp = al ? s_K[p] : 0;
-                int v = kp;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int u = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += u;
-                }
                 const unsigned m = __ballot_sync(0xffffffffu, al);
-                const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-                if (al) {
-                    s_list[pos] = p;
-                    s_lbase[pos] = run + v - kp;
-                }
-                run += __shfl_sync(0xffffffffu, v, 31);
+                if (al) s_list[cnt + __popc(m & ((1u << lane) - 1u))] = p;
                 cnt += __popc(m);
             }
-            if (lane == 0) {
-                s_nlive = cnt;
-                s_total = run;
-            }
+            if (lane == 0) s_nlive = cnt;
         }
         __syncthreads();
-        const int nlive = s_nlive, total = s_total;
+        const int nlive = s_nlive;
         if (nlive == 0) break;
-        // solve phase (the update counter is idle now and is reset here)
-        if (blockIdx.x == 0 && tid == 0) bc->work[1] = 0u;
+        // with worklists, a problem's first iteration in the launch does every
+        // block, later ones the blocks on its lists (see sched_view)
+        for (int q = tid; q < nlive; q += blockDim.x) {
+            const int p = s_list[q];
+            const int t = s_t[p] + 1;
+            const bool full = c_batch[p].sched == nullptr || (s_t[p] == P.probs[p].t0 && !P.probs[p].cont);
+            s_full[p] = full ? 1 : 0;
+            s_cnt[q] = full ? s_K[p] : (int)__ldcg(&sched_view(c_batch[p].sched, s_K[p]).sq_n[t & 1]);
+        }
+        __syncthreads();
+        if (wid == 0) batch_scan(s_cnt, s_lbase, nlive, &s_total);
+        __syncthreads();
+        int total = s_total;
+        // solve phase (the update counter is idle now and is reset here, as are
+        // the next iteration's solve-list counts)
+        if (blockIdx.x == 0) {
+            if (tid == 0) bc->work[1] = 0u;
+            for (int q = tid; q < nlive; q += blockDim.x) {
+                const int p = s_list[q];
+                if (c_batch[p].sched) sched_view(c_batch[p].sched, s_K[p]).sq_n[(s_t[p] + 2) & 1] = 0u;
+            }
+        }
         for (;;) {
             __syncthreads();
             if (tid == 0) s_k = (int)atomicAdd(&bc->work[0], 1u);
@@ -2420,8 +2453,12 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
             if (gk >= total) break;
             const int q = batch_owner(s_lbase, nlive, gk);
             const int p = s_list[q];
-            const int k = gk - s_lbase[q];
-            const IterArgs it = iter_args(s_t[p] + 1, s_mu[p]);
+            const int i = gk - s_lbase[q];
+            const int t = s_t[p] + 1;
+            IterArgs it = iter_args(t, s_mu[p]);
+            it.qeval = !s_full[p];
+            const int k = s_full[p] ? i
+                                    : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).sq[(size_t)(t & 1) * s_K[p] + i]);
             const int conn = c_batch[p].conn;
             if (conn == 4) solve_block<4>(c_batch[p], it, k, smem);
             else if (conn == 8) solve_block<8>(c_batch[p], it, k, smem);
@@ -2429,7 +2466,28 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
         }
         if (!grid_sync(bc, gridDim.x, nbar, P.spin_limit)) break;
         // update phase
-        if (blockIdx.x == 0 && tid == 0) bc->work[0] = 0u;
+        for (int q = tid; q < nlive; q += blockDim.x) {
+            const int p = s_list[q];
+            const int t = s_t[p] + 1;
+            if (!s_full[p] && blockIdx.x == 0) {
+                atomicAdd(&c_batch[p].ctrl->sched_work[0], (unsigned long long)s_cnt[q]);
+            }
+            s_cnt[q] = s_full[p] ? s_K[p] : (int)__ldcg(&sched_view(c_batch[p].sched, s_K[p]).uq_n[t & 1]);
+        }
+        __syncthreads();
+        if (wid == 0) batch_scan(s_cnt, s_lbase, nlive, &s_total);
+        __syncthreads();
+        total = s_total;
+        if (blockIdx.x == 0) {
+            if (tid == 0) bc->work[0] = 0u;
+            for (int q = tid; q < nlive; q += blockDim.x) {
+                const int p = s_list[q];
+                if (c_batch[p].sched) {
+                    sched_view(c_batch[p].sched, s_K[p]).uq_n[(s_t[p] + 2) & 1] = 0u;
+                    if (!s_full[p]) atomicAdd(&c_batch[p].ctrl->sched_work[1], (unsigned long long)s_cnt[q]);
+                }
+            }
+        }
         for (;;) {
             __syncthreads();
             if (tid == 0) s_k = (int)atomicAdd(&bc->work[1], 1u);
@@ -2438,11 +2496,14 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
             if (gk >= total) break;
             const int q = batch_owner(s_lbase, nlive, gk);
             const int p = s_list[q];
-            const int k = gk - s_lbase[q];
+            const int i = gk - s_lbase[q];
+            const int t = s_t[p] + 1;
+            const int k = s_full[p] ? i
+                                    : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).uq[(size_t)(t & 1) * s_K[p] + i]);
             const int conn = c_batch[p].conn;
-            if (conn == 4) update_block<4>(c_batch[p], s_mu[p], s_t[p] + 1, k);
-            else if (conn == 8) update_block<8>(c_batch[p], s_mu[p], s_t[p] + 1, k);
-            else update_block<6>(c_batch[p], s_mu[p], s_t[p] + 1, k);
+            if (conn == 4) update_block<4>(c_batch[p], s_mu[p], t, k, s_full[p]);
+            else if (conn == 8) update_block<8>(c_batch[p], s_mu[p], t, k, s_full[p]);
+            else update_block<6>(c_batch[p], s_mu[p], t, k, s_full[p]);
         }
         if (blockIdx.x == 0 && tid == 0) {
             unsigned y = 0;
@@ -2485,6 +2546,8 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
             o.pad = 0;
             o.mu = s_mu[p];
             o.r2 = o.t > 0 ? __longlong_as_double((long long)__ldcg(&c->r2max[o.t])) : 0.0;
+            o.work[0] = __ldcg(&c->sched_work[0]);
+            o.work[1] = __ldcg(&c->sched_work[1]);
             P.out[p] = o;
         }
     }

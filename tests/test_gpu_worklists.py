@@ -130,3 +130,69 @@ def test_worklists_after_set_state(orc, dp):
     yh, y, a, mu = ref[12]
     assert done == 12 and np.array_equal(st["yhat"], yh)
     assert np.array_equal(st["y"], y) and np.array_equal(st["a"], a)
+
+
+def test_batched_worklists_equal_oracle(orc, dp):
+    """The batched launch keeps per-problem worklists too: problems of several
+    shapes with small mu0 (labels move for many iterations), advanced in
+    launches of 1, 4 and 7 iterations, equal the oracle's states after the same
+    iterations, and skip blocks after their first iteration in a launch."""
+    cases = [inputs.random_instance(gr, cn, bl, lam=lam, seed=s) for (gr, cn, bl, lam, s) in (
+        ((96, 128), 4, (16, 16), 2.0, 1), ((64, 96), 8, (16, 32), 4.0, 2), ((24, 48, 40), 6, (8, 8, 8), 2.5, 3),
+        ((128, 128), 8, (32, 32), 8.0, 4))]
+    mu0s = [0.5, 1.0, 2.0, 3.0]
+    refs = []
+    for d, mu0 in zip(cases, mu0s):
+        refs.append(_oracle_states(orc, _inst(orc, d), mu0, 12))
+    gs = [dp.Dope.from_instance(d, mu0=mu0) for d, mu0 in zip(cases, mu0s)]
+    for g in gs:
+        g.reset()
+    t = 0
+    for n in (1, 4, 7):
+        res = dp.iterate_batch(gs, n)
+        t += n
+        for g, ref, (it, conv, st) in zip(gs, refs, res):
+            assert st == 0 and it == t and not conv
+            s = g.get_state()
+            yh, y, a, mu = ref[t]
+            assert np.array_equal(s["yhat"], yh), t
+            assert np.array_equal(s["y"], y) and np.array_equal(s["a"], a), t
+
+
+def test_batched_worklists_skip_and_match_oracle(orc, dp):
+    """At the paper's mu0 labels freeze after a few iterations: a batch solved to
+    convergence in one launch matches the oracle's solves and, after each
+    problem's first iteration, solves fewer blocks than it has."""
+    cases = [inputs.ellipses_rgb(size=256, lam=lam) for lam in (1.0, 8.0)] + \
+        [inputs.ellipsoids3d(shape=(32, 96, 96)), inputs.random_instance((192, 160), 4, (16, 16), lam=2.0, seed=9)]
+    gs = [dp.Dope.from_instance(d) for d in cases]
+    res = dp.iterate_batch(gs, 1000)
+    for j, (d, g, (it, conv, st)) in enumerate(zip(cases, gs, res)):
+        ref = orc.admm(_inst(orc, d), d["mu0"], 1.05, 1e-3, 1000)
+        assert st == 0 and conv and it == ref["iterations"]
+        lab, e = g.labels()
+        assert np.array_equal(lab, ref["labels"]) and e == ref["energy"]
+        s = g.stats()
+        assert s["solver_kernel"] == 3 and s["blocks_solved"] > 0
+        if j < 3:       # the noisy random field keeps label boundaries on most block faces
+            assert s["blocks_solved"] < g.nblocks * (it - 1), (s, g.nblocks, it)
+
+
+def test_worklists_dropped_when_inputs_change(orc, dp):
+    """Lists left by a launch are reused by the next launch only while nothing
+    changed: new unaries between two launches must be seen by every block."""
+    d = inputs.random_instance((96, 96), 8, (16, 16), lam=2.0, seed=12)
+    d2 = dict(d, u=np.ascontiguousarray(d["u"][::-1]))      # other unaries, same weights
+    i1, i2 = _inst(orc, d), _inst(orc, d2)
+    g = dp.Dope.from_instance(d, mu0=100.0, threads=256)
+    g.reset()
+    done, conv = g.iterate(6)
+    assert done == 6 and not conv
+    g.set_unaries(d2["u"])
+    done, conv = g.iterate(5)
+    st = g.get_state()
+    y, a, mu = np.full(i1.n, 0.5), np.zeros(i1.n), 100.0
+    for t in range(done):
+        yh, y, a, r2 = orc.admm_step(i1 if t < 6 else i2, mu, y, a)
+        mu *= 1.05
+    assert np.array_equal(st["yhat"], yh) and np.array_equal(st["y"], y) and np.array_equal(st["a"], a)
