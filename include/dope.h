@@ -13,7 +13,11 @@
  * satisfies ||yhat_k - S_k y||_2 <= eps.  This library runs that loop on one
  * GPU: one CTA per block with the block's residual graph in shared memory
  * (push-relabel + BFS, canonical minimal cut), and a fused elementwise kernel
- * for the y / a updates.  Partitions are non-overlapping (Q = I).
+ * for the y / a updates.  Partitions are non-overlapping (Q = I, the paper's
+ * Size00) unless dope_params.grow asks for the overlapping ones of Section 3
+ * (Size10 / Size25); connectivities 24 / 48 / 80 / 32 select Section 3's
+ * larger kernels, and dope_params.lsa_steps > 0 admits non-submodular
+ * weights (blocks solved by LSA-TR, Section 3.4).
  *
  * Conventions
  *  - Grids: 2-D (H, W) or 3-D (D, H, W), row-major, pixel index

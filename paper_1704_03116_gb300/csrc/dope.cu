@@ -8,6 +8,7 @@
 // convergence return at once and the host synchronises once per batch.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -90,6 +91,26 @@ struct dope_ctx {
     dope_profile prof{};
 };
 
+int dope_sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < 64) {
+        const int v = cache[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < 64) cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 namespace {
 
 #define CK(x)                                  \
@@ -100,9 +121,12 @@ namespace {
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// CTAs for n elements: one per element group, at most 32 per SM (the
+// kernels stride over the rest).
 int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
-    if (b > 152LL * 32) b = 152LL * 32;
+    const long long cap = 32LL * dope_sm_count();
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
 }

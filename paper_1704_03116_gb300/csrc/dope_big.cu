@@ -13,6 +13,8 @@
 #include "dope_overlap.cuh"
 #include "dope_big.h"
 
+int dope_sm_count();   // dope.cu: SM count of the current device (cached)
+
 namespace dope {
 
 namespace {
@@ -40,9 +42,12 @@ void raise_limit(const void* fn) {
     cudaGetLastError();
 }
 
+// CTAs for n elements: one per element group, at most 32 per SM of the
+// current device (the kernels stride over the rest).
 int grid_for_n(long long n, int threads) {
+    const int sms = dope_sm_count();
     long long b = (n + threads - 1) / threads;
-    if (b > 152LL * 32) b = 152LL * 32;
+    if (b > 32LL * sms) b = 32LL * sms;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -9,6 +9,10 @@
 #include "dope.h"
 #include "dope_potentials.h"
 
+// SM count of the current device (queried once per device and cached;
+// 1 if the query fails).  Grid-stride kernels size their grids from it.
+int dope_sm_count();
+
 // Source of device memory for a context.  alloc returns 256-byte aligned
 // device memory or null; release gives it back.  A null alloc means
 // cudaMalloc / cudaFree.

@@ -398,19 +398,10 @@ void launch_contrast_any(int C, int conn, bool sum, dim3 grid, dim3 block, const
     }
 }
 
-// A few CTAs per SM for the grid-stride kernels (the SM count of the device
-// current at the first call; initialised once, thread-safe).
-int grid_cap() {
-    static const int sms = []() {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            return v;
-        cudaGetLastError();
-        return 152;
-    }();
-    return sms * 8;
-}
+// A few CTAs per SM for the grid-stride kernels: the SM count of the device
+// current at the call (the kernels stride, so any grid is correct; a failed
+// query only makes the grid small).
+int grid_cap() { return dope_sm_count() * 8; }
 
 int blocks_for(long long n, int per_block) {
     const long long b = (n + per_block - 1) / per_block;
