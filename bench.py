@@ -283,6 +283,53 @@ def reference_sample(name):
     return insts, "each step one solve of the workload, cycling over its lambdas"
 
 
+def run_cpu_set(args):
+    """The CPU timing set of the measurement plan, on this machine's host cores:
+    for the 64x64 disk, the 512x512 RGB image (lambda 1, 4, 16), the 256x256x128
+    volume and the 1024x1024 non-submodular grid, the wall time of one full
+    step (every instance of the workload, inputs already in memory) of
+      * the oracle (BK per block + FP64 ADMM) with OpenMP over blocks on all
+        cores,
+      * the same oracle on one thread,
+      * the serial whole-grid solve the paper compares against (BK min-cut,
+        its sGC; serial LSA-TR for the non-submodular grid), one thread;
+    each the median of `--cpu-reps` runs.  Prints one JSON line."""
+    import oracle
+    out = {"nproc": os.cpu_count(), "threads_all": oracle.num_threads(), "reps": args.cpu_reps, "workloads": {}}
+    all_threads = oracle.num_threads()
+    for name in ("disk64", "ellipses512", "ellipsoids256", "nonsubmodular1024"):
+        insts, cfg = workload(name)
+        qs = [oracle.quantise(d["grid"], d["conn"], d["block"], d["u"], d["wq"], d["lam"],
+                              signed=bool(d.get("lsa_steps"))) for d in insts]
+        px = sum(q.n for q in qs)
+        rec = {"workload": cfg["workload"], "pixels_per_step": px}
+
+        def timed(fn):
+            ts = []
+            for _ in range(args.cpu_reps):
+                t0 = time.perf_counter()
+                fn()
+                ts.append(time.perf_counter() - t0)
+            return statistics.median(ts)
+
+        for label, nthr in (("oracle_all_cores", all_threads), ("oracle_1_thread", 1)):
+            oracle.set_threads(nthr)
+            t = timed(lambda: [_oracle_solve(oracle, q, d) for q, d in zip(qs, insts)])
+            rec[label] = {"s": t, "pixels_per_s": px / t, "threads": nthr}
+        oracle.set_threads(1)
+        if insts[0].get("lsa_steps"):
+            t = timed(lambda: [oracle.lsa_tr_global(q, steps=64) for q in qs])
+            rec["serial_lsa_tr_1_thread"] = {"s": t, "pixels_per_s": px / t}
+        else:
+            t = timed(lambda: [oracle.global_mincut(q) for q in qs])
+            rec["serial_bk_1_thread"] = {"s": t, "pixels_per_s": px / t}
+        oracle.set_threads(all_threads)
+        out["workloads"][name] = rec
+        print(json.dumps({name: rec}), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -789,7 +836,12 @@ def main():
                     help="default workload: skip the serving comparison added to its line")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: only the headline (no 2-D line, potentials or serving)")
+    ap.add_argument("--cpu-set", action="store_true",
+                    help="time the oracle (all cores, one thread) and the serial whole-grid solve on the host")
+    ap.add_argument("--cpu-reps", type=int, default=5, help="--cpu-set: runs per timing (median)")
     args = ap.parse_args()
+    if args.cpu_set:
+        return run_cpu_set(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
