@@ -668,7 +668,8 @@ def measure(name, args, world, local, with_e2e=True):
     upd_ms = sum(p["ms"][1] for p in profs)
     upd_n = sum(p["launches"][1] for p in profs)
     iters_n = sum(p["iterations"] for p in profs)
-    model = "every pixel's bytes once per iteration"
+    model = "per pixel-iteration figure x pixel-iterations (every pixel's bytes once per iteration)"
+    processed = None
     if overlap:
         sb, ub = overlap_bytes(insts[0])
         if solve_ms >= upd_ms:
@@ -681,15 +682,16 @@ def measure(name, args, world, local, with_e2e=True):
         # resident kernel when every block fits on the GPU at once)
         kname = "k_admm_resident" if kinds[0] == 2 else "k_admm_persistent"
         kms, kn = solve_ms, solve_n
+        kbytes = first_n * sf + (iters_n - first_n) * sl + iters_n * up
         if kname == "k_admm_persistent" and work["blocks_solved"]:
             # worklists: the launch's first iteration does every block, later
-            # ones the blocks on the lists; the bytes of the blocks processed
+            # ones the blocks on the lists; the bytes of the blocks it processed
             sfb, slb, upb = sf / k1, sl / k1, up / k1
-            kbytes = kn * k1 * (sfb + upb) + work["blocks_solved"] * slb + work["blocks_updated"] * upb
-            model = ("bytes of the blocks processed: iteration 1 every block, later iterations the "
-                     "blocks on the worklists (per block solve %.0f B, update %.0f B)" % (slb, upb))
-        else:
-            kbytes = first_n * sf + (iters_n - first_n) * sl + iters_n * up
+            pbytes = kn * k1 * (sfb + upb) + work["blocks_solved"] * slb + work["blocks_updated"] * upb
+            processed = {"bytes_per_launch": pbytes / max(kn, 1),
+                         "achieved_gbs": pbytes / (kms / 1e3) / 1e9,
+                         "model": "iteration 1 every block, later iterations the blocks on the worklists "
+                                  "(per block: solve %.0f B, update %.0f B)" % (slb, upb)}
         share = {kname: 1.0}
     elif solve_ms >= upd_ms:
         kname = "k_nsm_solve" if insts[0].get("lsa_steps") else "k_block_solve"
@@ -707,6 +709,8 @@ def measure(name, args, world, local, with_e2e=True):
             "algorithmic_bytes_per_launch": kbytes / max(kn, 1), "bytes_model": model,
             "avg_launch_us": 1e3 * kms / max(kn, 1), "launches": kn, "iterations_covered": iters_n,
             "time_share": share}
+    if processed:
+        roof["blocks_processed"] = processed
 
     out = {"metric": METRIC if "grow" not in insts[0] else
            "pixels/sec of 3 ADMM iterations (overlapping partition, Figure 2 protocol)",

@@ -287,6 +287,19 @@ int dope_get_profile(dope_ctx *ctx, dope_profile *out);
 int dope_get_geometry(dope_ctx *ctx, int64_t *n_pixels, int64_t *n_blocks, int *block_volume,
                       int *face_size);
 
+/* Checked build (libdope_checked.so, compiled with DOPE_CHECKED; a test tool,
+ * the paper has no counterpart).  Every shared-memory index
+ * of the block solver and of the resident kernel is tested against its array
+ * before the access; an index outside it is recorded (the first one since the
+ * last clear) and the access goes to a scratch cell, so the kernel neither
+ * faults nor writes outside the array, and the solve's results are then not
+ * valid.  *first_bad (host) receives 0 if no index was outside, else
+ * ((array length << 32) | index) + 1; clear != 0 resets the record
+ * afterwards.  Synchronises the current device.  Returns DOPE_EUNSUPPORTED on
+ * the ordinary library (which has no checks), DOPE_ECUDA if the record
+ * cannot be read. */
+int dope_check_status(uint64_t *first_bad, int clear);
+
 /* Size of the device scratch array behind dope_solve_noalloc. */
 #define DOPE_NOALLOC_SCRATCH_BYTES (16u << 20)
 

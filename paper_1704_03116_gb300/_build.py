@@ -20,6 +20,7 @@ DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("dope_kernels.cuh", "dope_
     [os.path.join(ROOT, "include", h) for h in ("dope.h", "dope_potentials.h")]
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libdope.so")
+LIB_CHECKED = os.path.join(HERE, "libdope_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,19 +31,26 @@ def nvcc():
     return "nvcc"
 
 
-def build(force=False, verbose=False):
-    """Compile libdope.so if it is missing or older than its sources."""
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in DEPS)):
-        return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force=False, verbose=False, checked=False):
+    """Compile libdope.so if it is missing or older than its sources.  With
+    checked=True, libdope_checked.so instead: the same library with
+    DOPE_CHECKED, every shared-memory index of the block solver and the
+    resident kernel tested against its array (dope_check_status)."""
+    lib = LIB_CHECKED if checked else LIB
+    objdir = os.path.join(OBJDIR, "checked") if checked else OBJDIR
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= max(os.path.getmtime(d) for d in DEPS)):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     common = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-I" + os.path.join(ROOT, "include")]
+    if checked:
+        common.append("-DDOPE_CHECKED")
     if verbose:
         common.insert(1, "-Xptxas=-v")
     objs, procs = [], []
     for src in SRC:
-        obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
         objs.append(obj)
         procs.append(subprocess.Popen([*common, "-c", "-o", obj, src], stdout=subprocess.PIPE,
                                       stderr=subprocess.PIPE, text=True))
@@ -56,14 +64,13 @@ def build(force=False, verbose=False):
             sys.stderr.write(err)
     if failed:
         raise RuntimeError("nvcc failed building libdope.so")
-    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs], capture_output=True, text=True)
+    r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs], capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
-        raise RuntimeError("nvcc failed linking libdope.so")
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+        raise RuntimeError("nvcc failed linking " + os.path.basename(lib))
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -1278,6 +1278,36 @@ const char* dope_strerror(int s) {
     }
 }
 
+int dope_check_status(uint64_t* first_bad, int clear) {
+    if (!first_bad) return DOPE_EINVAL;
+    *first_bad = 0;
+#ifdef DOPE_CHECKED
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return DOPE_ECUDA;
+    }
+    unsigned long long w = 0, wb = 0;
+    if (cudaMemcpyFromSymbol(&w, dope::dope_check_word, sizeof(w)) != cudaSuccess) {
+        cudaGetLastError();
+        return DOPE_ECUDA;
+    }
+    if (clear) {
+        const unsigned long long z = 0;
+        if (cudaMemcpyToSymbol(dope::dope_check_word, &z, sizeof(z)) != cudaSuccess) {
+            cudaGetLastError();
+            return DOPE_ECUDA;
+        }
+    }
+    const int rc = dope_big_check_word(&wb, clear);
+    if (rc) return rc;
+    *first_bad = (uint64_t)(w ? w : wb);
+    return DOPE_OK;
+#else
+    (void)clear;
+    return DOPE_EUNSUPPORTED;
+#endif
+}
+
 void dope_destroy(dope_ctx* c) {
     if (!c) return;
     const dope_allocator al = c->al;

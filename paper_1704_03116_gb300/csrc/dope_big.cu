@@ -97,3 +97,26 @@ void big_energy_img(int conn, int D, int H, int W, const int32_t* U, const int32
 }
 
 }  // namespace dope
+
+// The checked build's index record of this translation unit (the larger-kernel
+// instantiations): read, and cleared if asked.  0 on the ordinary build.
+int dope_big_check_word(unsigned long long* w, int clear) {
+#ifdef DOPE_CHECKED
+    if (cudaMemcpyFromSymbol(w, dope::dope_check_word, sizeof(*w)) != cudaSuccess) {
+        cudaGetLastError();
+        return DOPE_ECUDA;
+    }
+    if (clear) {
+        const unsigned long long z = 0;
+        if (cudaMemcpyToSymbol(dope::dope_check_word, &z, sizeof(z)) != cudaSuccess) {
+            cudaGetLastError();
+            return DOPE_ECUDA;
+        }
+    }
+#else
+    (void)clear;
+    *w = 0;
+#endif
+    return DOPE_OK;
+}
+

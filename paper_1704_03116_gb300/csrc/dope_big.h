@@ -19,3 +19,7 @@ void big_energy_img(int conn, int D, int H, int W, const int32_t* U, const int32
                     Ctrl* ctrl, int blocks, int threads, cudaStream_t st);
 
 }  // namespace dope
+
+// The checked build's shared-memory index record of dope_big.cu (0 on the
+// ordinary build); clear != 0 resets it.
+int dope_big_check_word(unsigned long long* w, int clear);

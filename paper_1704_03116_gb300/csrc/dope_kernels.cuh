@@ -20,6 +20,51 @@
 
 namespace dope {
 
+// ---------------------------------------------------------------------------
+// Shared-memory arrays of the block solver and the resident kernel are used
+// through SArr, a pointer with the array's length.  In the ordinary build it
+// is the pointer alone.  In the checked build (DOPE_CHECKED, libdope_checked)
+// every index is tested against the length first: an index outside the array
+// is recorded in dope_check_word (the first one wins: (length << 32 | index) + 1)
+// and the access goes to a scratch cell instead, so a wrong index neither
+// faults nor writes outside the array; the host reads the word with
+// dope_check_status.  Each translation unit has its own word.
+// ---------------------------------------------------------------------------
+#ifdef DOPE_CHECKED
+static __device__ unsigned long long dope_check_word;
+static __device__ __align__(16) unsigned char dope_check_cell[16];
+#endif
+
+template <class T>
+struct SArr {
+    T* p;
+#ifdef DOPE_CHECKED
+    long long n;
+    __device__ __forceinline__ SArr(T* ptr, long long len) : p(ptr), n(len) {}
+    __device__ __forceinline__ T& operator[](long long i) const {
+        if (i < 0 || i >= n) {
+            atomicCAS(&dope_check_word, 0ull,
+                      ((unsigned long long)(n & 0xffffffffLL) << 32 | (unsigned long long)(i & 0xffffffffLL)) + 1ull);
+            return *reinterpret_cast<T*>(dope_check_cell);
+        }
+        return p[i];
+    }
+    __device__ __forceinline__ SArr sub(long long off, long long len) const {
+        if (off < 0 || off + len > n) {
+            atomicCAS(&dope_check_word, 0ull,
+                      ((unsigned long long)(n & 0xffffffffLL) << 32 | (unsigned long long)(off & 0xffffffffLL)) + 1ull);
+            return SArr(reinterpret_cast<T*>(dope_check_cell), 0);
+        }
+        return SArr(p + off, len);
+    }
+#else
+    __device__ __forceinline__ SArr(T* ptr, long long) : p(ptr) {}
+    __device__ __forceinline__ T& operator[](long long i) const { return p[i]; }
+    __device__ __forceinline__ SArr sub(long long off, long long len) const { return SArr(p + off, len); }
+#endif
+    __device__ __forceinline__ explicit operator bool() const { return p != nullptr; }
+};
+
 constexpr int NPTMAX = 8;          // nodes per thread in the block solver
 constexpr int FREE = 0, FIX0 = 1, FIX1 = 2;
 constexpr int MAX_FOLD_ROUNDS = 3;    // default bound on exact-folding rounds
@@ -495,13 +540,13 @@ __device__ __forceinline__ long long interior_cap(long long Ui, int yh, double m
 // instead of a block barrier.  Returns whether a free node with excess can
 // still reach t.
 template <int CONN>
-__device__ __forceinline__ int bfs_bits(const int* __restrict__ res, const int* __restrict__ e, int16_t* h,
-                                        const uint8_t* st, uint32_t* bits, int bw, int pl, int B,
+__device__ __forceinline__ int bfs_bits(const SArr<int> res, const SArr<int> e, const SArr<int16_t> h,
+                                        const SArr<uint8_t> st, const SArr<uint32_t> bits, int bw, int pl, int B,
                                         int HMAX, int tid, int NT, int& levels) {
     const int W = (B + 31) >> 5;
-    uint32_t* E = bits;                  // [CONN][W]
-    uint32_t* Fa = bits + CONN * W;      // frontier, two buffers
-    uint32_t* Fb = Fa + W;
+    const SArr<uint32_t> E = bits.sub(0, (long long)CONN * W);          // [CONN][W]
+    const SArr<uint32_t> Fa = bits.sub((long long)CONN * W, W);         // frontier, two buffers
+    const SArr<uint32_t> Fb = bits.sub((long long)(CONN + 1) * W, W);
     const int lane = tid & 31;
     for (int base = 0; base < B; base += NT) {
         const int v = base + tid;
@@ -527,8 +572,8 @@ __device__ __forceinline__ int bfs_bits(const int* __restrict__ res, const int* 
             const int i = lane + 32 * s2;
             vis[s2] = i < W ? Fa[i] : 0u;
         }
-        uint32_t* F = Fa;
-        uint32_t* Nf = Fb;
+        SArr<uint32_t> F = Fa;
+        SArr<uint32_t> Nf = Fb;
         while (lv < HMAX - 1) {
             unsigned any = 0;
 #pragma unroll
@@ -560,7 +605,7 @@ __device__ __forceinline__ int bfs_bits(const int* __restrict__ res, const int* 
             if (!__any_sync(0xffffffffu, any != 0)) break;
             ++lv;
             __syncwarp();
-            uint32_t* tmp = F; F = Nf; Nf = tmp;
+            const SArr<uint32_t> tmp = F; F = Nf; Nf = tmp;
         }
     }
     levels += lv;
@@ -587,10 +632,13 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
     const Geo& g = A.g;
     const int B = g.B;
     const int tid = threadIdx.x, NT = blockDim.x;
-    int* res = reinterpret_cast<int*>(smem);
-    long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
-    int* capsum = reinterpret_cast<int*>(C64 + B);
-    uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
+    int* res_p = reinterpret_cast<int*>(smem);
+    long long* C64_p = reinterpret_cast<long long*>(res_p + CONN * B);
+    int* capsum_p = reinterpret_cast<int*>(C64_p + B);
+    const SArr<int> res(res_p, (long long)CONN * B);
+    const SArr<long long> C64(C64_p, B);
+    const SArr<int> capsum(capsum_p, B);
+    const SArr<uint8_t> st(reinterpret_cast<uint8_t*>(capsum_p + B), B);
     const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
     const int bw = g.bw, pl = g.bh * g.bw;
     constexpr int nh = CONN / 2;
@@ -777,15 +825,19 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
     const Geo& g = A.g;
     const int B = g.B;
     const int tid = threadIdx.x, NT = blockDim.x;
-    int* res = reinterpret_cast<int*>(smem);
-    long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
-    int* e = reinterpret_cast<int*>(C64);
-    int* ein = e + B;
-    int* capsum = reinterpret_cast<int*>(C64 + B);
-    int16_t* hA = reinterpret_cast<int16_t*>(capsum);
-    int16_t* hB = hA + B;
-    uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
-    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + solver_bits_offset(CONN, B));
+    int* res_p = reinterpret_cast<int*>(smem);
+    long long* C64_p = reinterpret_cast<long long*>(res_p + CONN * B);
+    int* capsum_p = reinterpret_cast<int*>(C64_p + B);
+    const SArr<int> res(res_p, (long long)CONN * B);
+    const SArr<long long> C64(C64_p, B);
+    const SArr<int> e(reinterpret_cast<int*>(C64_p), B);
+    const SArr<int> ein(reinterpret_cast<int*>(C64_p) + B, B);
+    const SArr<int> capsum(capsum_p, B);
+    const SArr<int16_t> hA(reinterpret_cast<int16_t*>(capsum_p), B);
+    const SArr<int16_t> hB(reinterpret_cast<int16_t*>(capsum_p) + B, B);
+    const SArr<uint8_t> st(reinterpret_cast<uint8_t*>(capsum_p + B), B);
+    const SArr<uint32_t> bits(reinterpret_cast<uint32_t*>(smem + solver_bits_offset(CONN, B)),
+                              (long long)(CONN + 3) * ((B + 31) / 32));
     const long long c_built = clock64();
     long long c_bfs = 0;
     int levels = 0, bfs_max = 0;
@@ -864,8 +916,8 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
     const long long c_folded = clock64();
     const int HMAX = B + 1;
     int pulses = 0;
-    int16_t* hc = hA;
-    int16_t* hn = hB;
+    SArr<int16_t> hc = hA;
+    SArr<int16_t> hn = hB;
     if (__syncthreads_or(nfree)) {
         // 3. push-relabel (phase 1: maximum preflow)
         long long cb = clock64();
@@ -936,7 +988,7 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
                 hn[v] = (int16_t)hv;
             }
             active = __syncthreads_or(act);
-            int16_t* tmp = hc; hc = hn; hn = tmp;
+            const SArr<int16_t> tmp = hc; hc = hn; hn = tmp;
             ++pulses;
             if (active && period > 0 && (pulses % period) == 0) {
                 cb = clock64();
@@ -1656,7 +1708,8 @@ __host__ __device__ inline size_t resident_smem_bytes(int conn, int B, int F) {
 
 template <int CONN>
 __device__ __forceinline__ void update_block_resident(const UpdArgs& A, int k, int t, double mu,
-                                                      const uint8_t* lab, double* yS, double* aS) {
+                                                      const SArr<uint8_t> lab, const SArr<double> yS,
+                                                      const SArr<double> aS) {
     const Geo& g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     constexpr int nh = CONN / 2;
@@ -1749,36 +1802,39 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     const int k = blockIdx.x;                  // gridDim.x == K
     constexpr int nh = CONN / 2;
     Ctrl* c = P.s.ctrl;
-    int* res = reinterpret_cast<int*>(smem);
-    long long* C64 = reinterpret_cast<long long*>(res + CONN * B);
-    int* capsum = reinterpret_cast<int*>(C64 + B);
-    uint8_t* st = reinterpret_cast<uint8_t*>(capsum + B);
+    int* res_p = reinterpret_cast<int*>(smem);
+    long long* C64_p = reinterpret_cast<long long*>(res_p + CONN * B);
+    int* capsum_p = reinterpret_cast<int*>(C64_p + B);
+    const SArr<int> res(res_p, (long long)CONN * B);
+    const SArr<long long> C64(C64_p, B);
+    const SArr<int> capsum(capsum_p, B);
+    const SArr<uint8_t> st(reinterpret_cast<uint8_t*>(capsum_p + B), B);
     const ResidentLayout L = resident_layout(CONN, B, F, NH);
-    double* yS = reinterpret_cast<double*>(smem + L.yS);
-    double* aS = reinterpret_cast<double*>(smem + L.aS);
-    int* resW = reinterpret_cast<int*>(smem + L.resW);
-    int* cs0 = reinterpret_cast<int*>(smem + L.cs0);
-    int* Us = reinterpret_cast<int*>(smem + L.Us);
-    int16_t* fl = reinterpret_cast<int16_t*>(smem + L.fl);   // face slot -> local pixel
-    uint8_t* lab = smem + L.lab;
+    const SArr<double> yS(reinterpret_cast<double*>(smem + L.yS), F);
+    const SArr<double> aS(reinterpret_cast<double*>(smem + L.aS), F);
+    const SArr<int> resW(reinterpret_cast<int*>(smem + L.resW), (long long)nh * B);
+    const SArr<int> cs0(reinterpret_cast<int*>(smem + L.cs0), B);
+    const SArr<int> Us(reinterpret_cast<int*>(smem + L.Us), B);
+    const SArr<int16_t> fl(reinterpret_cast<int16_t*>(smem + L.fl), F);   // face slot -> local pixel
+    const SArr<uint8_t> lab(smem + L.lab, B);
     // run-ahead window arrays: allocated (and touched) only when P.window
-    double* yS0 = reinterpret_cast<double*>(smem + L.yS0);
-    double* aS0 = reinterpret_cast<double*>(smem + L.aS0);
-    double* hy = reinterpret_cast<double*>(smem + L.hy);
-    double* ha = reinterpret_cast<double*>(smem + L.ha);
-    double* rloc = reinterpret_cast<double*>(smem + L.rloc);
-    int* Gf = reinterpret_cast<int*>(smem + L.Gf);
-    int* hG = reinterpret_cast<int*>(smem + L.hG);
-    int* hw = reinterpret_cast<int*>(smem + L.hw);
-    int16_t* hs = reinterpret_cast<int16_t*>(smem + L.hs);
-    uint8_t* hl = smem + L.hl;
-    uint8_t* labw = smem + L.labw;
-    long long* cI = reinterpret_cast<long long*>(smem + L.cI);   // certificate: exact integer part
-    float* cB = reinterpret_cast<float*>(smem + L.cB);            // bound on |a|, |y - yhat|
-    float* cW = reinterpret_cast<float*>(smem + L.cW);            // sum_j w_j (B_i + B_j)
-    float* cE = reinterpret_cast<float*>(smem + L.cE);            // rounding allowance
-    float* hB = reinterpret_cast<float*>(smem + L.hB);            // bound for halo pixels
-    double* ring = reinterpret_cast<double*>(smem + L.ring);      // [RING][2][F] own y, a
+    const SArr<double> yS0(reinterpret_cast<double*>(smem + L.yS0), F);
+    const SArr<double> aS0(reinterpret_cast<double*>(smem + L.aS0), F);
+    const SArr<double> hy(reinterpret_cast<double*>(smem + L.hy), NH);
+    const SArr<double> ha(reinterpret_cast<double*>(smem + L.ha), NH);
+    const SArr<double> rloc(reinterpret_cast<double*>(smem + L.rloc), WMAX);
+    const SArr<int> Gf(reinterpret_cast<int*>(smem + L.Gf), F);
+    const SArr<int> hG(reinterpret_cast<int*>(smem + L.hG), NH);
+    const SArr<int> hw(reinterpret_cast<int*>(smem + L.hw), (long long)CONN * F);
+    const SArr<int16_t> hs(reinterpret_cast<int16_t*>(smem + L.hs), (long long)CONN * F);
+    const SArr<uint8_t> hl(smem + L.hl, NH);
+    const SArr<uint8_t> labw(smem + L.labw, B);
+    const SArr<long long> cI(reinterpret_cast<long long*>(smem + L.cI), F);   // certificate: exact integer part
+    const SArr<float> cB(reinterpret_cast<float*>(smem + L.cB), F);            // bound on |a|, |y - yhat|
+    const SArr<float> cW(reinterpret_cast<float*>(smem + L.cW), F);            // sum_j w_j (B_i + B_j)
+    const SArr<float> cE(reinterpret_cast<float*>(smem + L.cE), F);            // rounding allowance
+    const SArr<float> hB(reinterpret_cast<float*>(smem + L.hB), NH);            // bound for halo pixels
+    const SArr<double> ring(reinterpret_cast<double*>(smem + L.ring), (long long)RING * 2 * F);      // [RING][2][F] own y, a
     __shared__ long long s_tau;                                   // max interior |U| + n-link sum
     __shared__ double part[128];
 
@@ -1933,7 +1989,7 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
     // sum: label 0; C < minus it: label 1) the labels are those cut_block
     // returns, without the max-flow; out receives them.  false: some node is
     // free and cut_block must run.
-    auto fast_forced = [&](uint8_t* out) -> bool {
+    auto fast_forced = [&](const SArr<uint8_t> out) -> bool {
         int fr = 0;
 #pragma unroll 1
         for (int q = 0; q < NPTMAX; ++q) {
@@ -1996,7 +2052,7 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
                 }
             } else {
                 copy_res();
-                cut_block<CONN>(P.s, k, smem, bw, pl, imask, c0, lab);
+                cut_block<CONN>(P.s, k, smem, bw, pl, imask, c0, lab.p);
             }
             const long long c1 = clock64();
             if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
@@ -2168,7 +2224,7 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
                 tb = clock64();
                 if (!fast_forced(labw)) {
                     copy_res();
-                    cut_block<CONN>(P.s, k, smem, bw, pl, imask, clock64(), labw, false);
+                    cut_block<CONN>(P.s, k, smem, bw, pl, imask, clock64(), labw.p, false);
                 }
                 tc = clock64();
                 int moved = 0;
@@ -2185,7 +2241,7 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
             });
             if (tid == 0) rloc[sidx - 1] = r2;
             {
-                double* rs = ring + (size_t)(sidx % RING) * 2 * F;
+                const SArr<double> rs = ring.sub((long long)(sidx % RING) * 2 * F, 2LL * F);
                 for (int f = tid; f < F; f += NT) { rs[f] = yS[f]; rs[F + f] = aS[f]; }
             }
             long long te = clock64();
@@ -2236,7 +2292,7 @@ __global__ void __launch_bounds__(256, 2) k_admm_resident(PersistArgs P) {
         const int sdone = thaw_s - 1;                  // iterations this CTA advanced
         const int back = (tw + sdone) - tend;          // iterations to undo
         if (back > 0 && back < RING && tend > tw) {
-            const double* rs = ring + (size_t)((tend - tw) % RING) * 2 * F;
+            const SArr<double> rs = ring.sub((long long)((tend - tw) % RING) * 2 * F, 2LL * F);
             for (int f = tid; f < F; f += NT) { yS[f] = rs[f]; aS[f] = rs[F + f]; }
         } else if (back > 0) {
             for (int f = tid; f < F; f += NT) {

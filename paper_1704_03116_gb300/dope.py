@@ -19,7 +19,11 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdope.so")
+# DOPE_LIBRARY=checked selects the checked build (shared-memory index checks
+# that record a bad index instead of touching memory; built by
+# _build.build(checked=True)); anything else the ordinary library.
+LIB_PATH = os.path.join(_HERE, "libdope_checked.so" if os.environ.get("DOPE_LIBRARY") == "checked"
+                        else "libdope.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "dope.h")
 HEADERS = [HEADER, os.path.join(os.path.dirname(_HERE), "include", "dope_potentials.h")]
 
@@ -156,6 +160,7 @@ def _load():
         "dope_set_image": (i32, [vp, vp, i32, P(dope_gmm), P(dope_gmm), dbl, dbl, i32, i32, P(ctypes.c_double), vp]),
         "dope_destroy": (None, [vp]),
         "dope_strerror": (ctypes.c_char_p, [i32]),
+        "dope_check_status": (i32, [P(ctypes.c_uint64), i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +223,18 @@ def _t(np_dtype):
 # --------------------------------------------------------------------------
 # C-ABI functions (same names)
 # --------------------------------------------------------------------------
+
+def dope_check_status(clear=False):
+    """Checked build only: (length, index) of the first shared-memory index a
+    kernel found outside its array since the last clear, or None.  Raises
+    DopeError(DOPE_EUNSUPPORTED) on the ordinary build."""
+    w = ctypes.c_uint64(0)
+    _check(_lib.dope_check_status(ctypes.byref(w), int(bool(clear))), "dope_check_status")
+    if not w.value:
+        return None
+    v = w.value - 1
+    return (v >> 32, v & 0xffffffff)
+
 
 def dope_default_params():
     p = dope_params()
