@@ -140,6 +140,9 @@ typedef struct {
                                    worklists (after each launch's first iteration, which does
                                    every block); 0 on the other kernels */
     int64_t blocks_updated;     /* likewise, block updates (Eq. 10 / 11) run from the worklists */
+    int64_t blocks_solved_partial;  /* of blocks_solved, those whose nodes were all still forced, so
+                                   that only their active and changed chunks of face pixels were
+                                   evaluated (no capacity build, no cut) */
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the

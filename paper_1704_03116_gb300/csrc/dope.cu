@@ -297,6 +297,7 @@ void fill_stats(dope_ctx* c, const Ctrl& h) {
     for (int i = 0; i < 8; ++i) c->stats.window_cycles[i] = (double)h.wcyc[i];
     c->stats.blocks_solved = (int64_t)h.sched_work[0];
     c->stats.blocks_updated = (int64_t)h.sched_work[1];
+    c->stats.blocks_solved_partial = (int64_t)h.sched_part;
 }
 
 int read_r2max(dope_ctx* c, int t, double* r2, cudaStream_t st) {

@@ -72,12 +72,18 @@ constexpr double CLAMP62 = 4611686018427387904.0;   // 2^62
 
 // Block-solver shared memory: res int32 [conn][B], R1 8 B [B], R2 4 B [B],
 // st uint8 [B], then (aligned to 4 B) the bit-parallel BFS words: per-direction
-// residual masks [conn][W], seeds / frontier buffers [3][W], W = ceil(B / 32).
+// residual masks [conn][W], seeds / frontier buffers [3][W], W = ceil(B / 32),
+// then the free-node list int16 [B].
 __host__ __device__ inline size_t solver_bits_offset(int conn, int B) {
     return ((size_t)(conn + 3) * 4 * B + B + 3) & ~(size_t)3;
 }
-__host__ __device__ inline size_t solver_smem_bytes(int conn, int B) {
+// After the bit words: the list of nodes left free by the first folding round
+// (int16 [B]), so later rounds and the push-relabel pulses visit only those.
+__host__ __device__ inline size_t solver_list_offset(int conn, int B) {
     return solver_bits_offset(conn, B) + 4 * (size_t)(conn + 3) * ((B + 31) / 32);
+}
+__host__ __device__ inline size_t solver_smem_bytes(int conn, int B) {
+    return solver_list_offset(conn, B) + 2 * (size_t)B;
 }
 
 struct Geo {
@@ -119,6 +125,7 @@ struct Ctrl {
     unsigned long long pcyc[4];     // persistent kernel, thread 0 of each CTA: solve phase,
                                     // first barrier wait, update phase, second barrier wait
     unsigned long long sched_work[2];   // blocks solved / updated from the worklists (statistics)
+    unsigned long long sched_part;      // of those solves, the ones that evaluated only some chunks
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
 };
 
@@ -160,12 +167,18 @@ struct SchedView {
     unsigned long long* umark;
     int* sq;
     int* uq;
-    uint8_t* qs;
+    unsigned* act;      // [K][4] chunks (32 face slots each) holding a slot that is not trivial
+    unsigned* dsc;      // [K][4] chunks whose slots' Eq. 8 inputs changed since the block's last solve
+    unsigned* duc;      // [K][4] chunks whose slots' cross-neighbour labels changed in this solve phase
+    uint8_t* qs;        // [K] 0 not forced, 1 quiet, 2 forced with active chunks
     uint8_t* yhF;
 };
 
+// Chunk masks hold up to 128 chunks of 32 face slots (F <= B <= 4096).
+constexpr int CHUNK_WORDS = 4;
+
 __host__ __device__ inline size_t sched_bytes(int K, int F) {
-    return 16 + 16 * (size_t)K + 16 * (size_t)K + (size_t)K + (size_t)K * F;
+    return 16 + 16 * (size_t)K + 16 * (size_t)K + 48 * (size_t)K + (size_t)K + (size_t)K * F;
 }
 
 __device__ __forceinline__ SchedView sched_view(unsigned char* base, int K) {
@@ -176,9 +189,18 @@ __device__ __forceinline__ SchedView sched_view(unsigned char* base, int K) {
     s.umark = s.smark + K;
     s.sq = reinterpret_cast<int*>(s.umark + K);
     s.uq = s.sq + 2 * (size_t)K;
-    s.qs = reinterpret_cast<uint8_t*>(s.uq + 2 * (size_t)K);
+    s.act = reinterpret_cast<unsigned*>(s.uq + 2 * (size_t)K);
+    s.dsc = s.act + CHUNK_WORDS * (size_t)K;
+    s.duc = s.dsc + CHUNK_WORDS * (size_t)K;
+    s.qs = reinterpret_cast<uint8_t*>(s.duc + CHUNK_WORDS * (size_t)K);
     s.yhF = s.qs + K;
     return s;
+}
+
+// Mark face slot fn of block kn in a chunk mask.
+__device__ __forceinline__ void chunk_mark(unsigned* masks, int kn, int fn) {
+    const int ch = fn >> 5;
+    atomicOr(&masks[(size_t)kn * CHUNK_WORDS + (ch >> 5)], 1u << (ch & 31));
 }
 
 // Put block kn on a list for the iteration whose mark is m, unless it is on
@@ -627,11 +649,163 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
                                        unsigned long long imask, long long c_start, uint8_t* lab_smem,
                                        bool to_global = true);
 
+// Two floats bracketing a double, from its bits alone (no FP64 operation):
+// lo <= x <= hi.  The double's mantissa is cut to 23 bits (toward zero) and,
+// if anything was cut, the other bound is the next float away from zero.
+// Magnitudes below 2^-126 get [-2^-126, 2^-126] (0 stays exact), magnitudes
+// of 2^128 and above an infinite bound.
+__device__ __forceinline__ void dbl_bounds(double x, float& lo, float& hi) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (b >> 63) != 0;
+    const int e = (int)((b >> 52) & 0x7ff);
+    float tlo, thi;                      // bounds of |x|
+    if ((b << 1) == 0) {
+        tlo = thi = 0.f;
+    } else if (e < 1023 - 126) {
+        tlo = 0.f;
+        thi = 1.1754943508222875e-38f;   // 2^-126
+    } else if (e > 1023 + 127) {
+        tlo = 3.4028234663852886e38f;    // largest float
+        thi = __int_as_float(0x7f800000);
+    } else {
+        const unsigned fb = ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+        tlo = __uint_as_float(fb);
+        thi = (b & 0x1fffffffull) ? __uint_as_float(fb + 1u) : tlo;   // fb + 1: next float up (inf at the top)
+    }
+    lo = neg ? -thi : tlo;
+    hi = neg ? -tlo : thi;
+}
+
+// Certificate for the Eq. 8 unary of a face pixel without FP64 work: an
+// interval [s_lo, s_hi] holding the exact real value of
+//   s = U + sum_d w_d (y - y_d) + m1024 ((a - y) + 1/2)
+// from FP32 interval arithmetic with directed rounding on the bounds of each
+// double, widened by 2^-48 M for the roundings of the FP64 evaluation the
+// exact path does: at most 3 CONN + 4 <= 28 round-to-nearest steps, each of
+// which moves the result by at most 2^-53 M, where M = |U| + sum_d w_d (|y| +
+// |y_d|) + m1024 (|a| + |y| + 1/2) bounds every intermediate value (an error
+// in y - y_d or a - y enters multiplied by w_d or m1024, still within M).
+// Returns 0 if s provably rounds to C >= cs (label 0 in
+// every minimiser), 1 if to C < -cs (label 1), -1 if the interval decides
+// nothing (the exact value must be computed).  w_d >= 0 (submodular).
+template <int CONN>
+__device__ __forceinline__ int face_cert(long long Ui, double yv, double av, const double* yj, const int* wj,
+                                         unsigned ok, double m1024, long long cs) {
+    float ylo, yhi, alo, ahi, mlo, mhi;
+    dbl_bounds(yv, ylo, yhi);
+    dbl_bounds(av, alo, ahi);
+    dbl_bounds(m1024, mlo, mhi);
+    float slo = __ll2float_rd(Ui), shi = __ll2float_ru(Ui);
+    float M = fabsf(shi) > fabsf(slo) ? fabsf(shi) : fabsf(slo);
+    const float ymag = fmaxf(fabsf(ylo), fabsf(yhi));
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        if (!((ok >> d) & 1)) continue;
+        float jlo, jhi;
+        dbl_bounds(yj[d], jlo, jhi);
+        const float w = (float)wj[d];                 // exact: n-links are below 2^24
+        slo = __fadd_rd(slo, __fmul_rd(w, __fsub_rd(ylo, jhi)));
+        shi = __fadd_ru(shi, __fmul_ru(w, __fsub_ru(yhi, jlo)));
+        M = __fadd_ru(M, __fmul_ru(w, __fadd_ru(ymag, fmaxf(fabsf(jlo), fabsf(jhi)))));
+    }
+    const float qlo = __fadd_rd(__fsub_rd(alo, yhi), 0.5f);
+    const float qhi = __fadd_ru(__fsub_ru(ahi, ylo), 0.5f);
+    slo = __fadd_rd(slo, qlo >= 0.f ? __fmul_rd(mlo, qlo) : __fmul_rd(mhi, qlo));
+    shi = __fadd_ru(shi, qhi >= 0.f ? __fmul_ru(mhi, qhi) : __fmul_ru(mlo, qhi));
+    M = __fadd_ru(M, __fmul_ru(mhi, __fadd_ru(__fadd_ru(fmaxf(fabsf(alo), fabsf(ahi)), ymag), 0.5f)));
+    static_assert(CONN <= 8, "the rounding count above assumes at most 8 neighbours");
+    const float dl = __fmul_ru(M, 3.552713678800501e-15f);      // 2^-48 M
+    if (__fsub_rd(slo, dl) >= __ll2float_ru(cs)) return 0;      // s >= cs: C >= cs
+    if (__fadd_ru(shi, dl) <= __ll2float_rd(-cs - 1)) return 1; // s <= -cs - 1: C < -cs
+    return -1;
+}
+
+// Eq. 8 unary of face slot f (local pixel v, label yh, unary Ui, intra-block
+// n-link sum cs) of block k.  A slot in the trivial state (a = +0, y = yhat)
+// whose cross neighbours all have y_j = y_i gets the interior unary (every
+// cross term is +-0) and the integer forced test; every other slot the exact
+// FP64 value.  Returns C (the exact value, or U +- H where the integer test
+// holds); `uni`: trivial with equal cross neighbours, labels included (the
+// neighbours' labels as of their blocks' last update); `forced`: forced to
+// its own label yh (C >= cs for 0, C < -cs for 1) in every minimiser.
+template <int CONN, class SA>
+__device__ __forceinline__ long long face_slot_cap(const SA& __restrict__ A, const IterArgs& it, const SchedView& sv,
+                                                   int k, int kz, int ky, int kx, int f, int v, long long Ui,
+                                                   int yh, long long cs, double m1024, bool& uni, bool& forced) {
+    const Geo& g = A.g;
+    constexpr int nh = CONN / 2;
+    const long long gi = (long long)k * g.B + v;
+    const long long sidx = (long long)k * g.F + f;
+    const double yv = __ldcg(&A.yF[sidx]);
+    const double av = __ldcg(&A.aF[sidx]);
+    double yj[CONN];
+    int wj[CONN];
+    unsigned ok = 0;
+    bool lab_same = true;
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        int kn, ln, fn;
+        yj[d] = 0.0;
+        wj[d] = 0;
+        if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+            ok |= 1u << d;
+            yj[d] = __ldcg(&A.yF[(long long)kn * g.F + fn]);
+            wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi]
+                             : A.Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
+            if (it.qeval) lab_same = lab_same && (int)__ldcg(&sv.yhF[(long long)kn * g.F + fn]) == yh;
+        }
+    }
+    // equality tests on the bits (no FP64 work): y = +0 or 1.0 exactly, and a
+    // neighbour's y with the same bits as this pixel's
+    const long long yb = __double_as_longlong(yv);
+    bool u = __double_as_longlong(av) == 0 && yb == (yh ? 0x3ff0000000000000LL : 0LL);
+#pragma unroll
+    for (int d = 0; d < CONN; ++d)
+        if ((ok >> d) & 1) u = u && __double_as_longlong(yj[d]) == yb;
+    long long C;
+    if (u) {
+        const long long T = yh ? Ui - it.H : Ui + it.H;
+        if (it.int_test && (yh ? (T < -cs) : (T >= cs))) C = T;
+        else C = interior_cap(Ui, yh, m1024);
+    } else {
+        // a certified label needs no exact value: any C beyond the n-link
+        // sum on that side gives the same minimisers (the folding fixes the
+        // node either way)
+        const int lab = face_cert<CONN>(Ui, yv, av, yj, wj, ok, m1024, cs);
+        if (lab == 0) C = cs;
+        else if (lab == 1) C = -cs - 1;
+        else C = face_cap_from<CONN>(Ui, yv, av, yj, wj, ok, m1024);
+    }
+    uni = u && lab_same;
+    forced = yh ? (C < -cs) : (C >= cs);
+    return C;
+}
+
+// Intra-block n-link sum of local pixel v (the value the capacity build puts
+// in capsum), read from the forward weight planes.
+template <int CONN>
+__device__ __forceinline__ long long nlink_sum(const Geo& g, const int32_t* __restrict__ Wl, int k, int v) {
+    constexpr int nh = CONN / 2;
+    const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+    const long long gi = (long long)k * g.B + v;
+    long long cs = 0;
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        int dz, dy, dx;
+        dir_off<CONN>(d, dz, dy, dx);
+        const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+        if (nlz < 0 || nlz >= g.bd || nly < 0 || nly >= g.bh || nlx < 0 || nlx >= g.bw) continue;
+        cs += (d < nh) ? Wl[(long long)d * g.N + gi]
+                       : Wl[(long long)(d - nh) * g.N + gi + (dz * g.bh + dy) * g.bw + dx];
+    }
+    return cs;
+}
+
 template <int CONN, class SA>
 __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, unsigned char* smem) {
     const Geo& g = A.g;
     const int B = g.B;
-    const int tid = threadIdx.x, NT = blockDim.x;
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
     int* res_p = reinterpret_cast<int*>(smem);
     long long* C64_p = reinterpret_cast<long long*>(res_p + CONN * B);
     int* capsum_p = reinterpret_cast<int*>(C64_p + B);
@@ -643,12 +817,79 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
     const int bw = g.bw, pl = g.bh * g.bw;
     constexpr int nh = CONN / 2;
     const double m1024 = __dmul_rn(1024.0, it.mu);
+    const SchedView sv = sched_view(A.sched, g.K);
+    const int nchunks = (g.F + 31) >> 5;
     unsigned long long imask = 0;        // 8 bits per own node: intra-block directions
     unsigned oldlab = 0;                 // bit q: label of own node tid + q NT before this solve
-    int allf = 1;                        // every own node forced by the integer test
-    int qok = 1;                         // ... and the block quiet (see sched_view)
+    int allf = 1;                        // every own node forced to its own label
+    int allu = 1;                        // every face slot trivial with equal cross neighbours
     __shared__ unsigned s_pm;            // neighbour blocks to put on the update list
+    __shared__ unsigned s_act[CHUNK_WORDS];
+    __shared__ unsigned s_ev[CHUNK_WORDS];
+    __shared__ int s_ok;
     const long long c_start = clock64();
+
+    if (it.qeval && __ldcg(&sv.qs[k]) != 0) {
+        // Every node of the block was forced to its label at its last solve.
+        // Nodes in chunks that are neither active nor marked dirty still are
+        // (their inputs did not change, and the integer test's bound only
+        // grows), so only those chunks are evaluated again; if all their slots
+        // are still forced to their labels, the labels stand.
+        if (tid < CHUNK_WORDS) {
+            const unsigned a = __ldcg(&sv.act[(size_t)k * CHUNK_WORDS + tid]);
+            const unsigned d = __ldcg(&sv.dsc[(size_t)k * CHUNK_WORDS + tid]);
+            s_ev[tid] = a | d;       // every active chunk is among them
+            s_act[tid] = 0u;
+        }
+        if (tid == 0) s_ok = 1;
+        __syncthreads();
+        int ok = 1;
+        // the evaluated chunks in increasing order, one per warp
+        int seen = 0;
+        for (int w = 0; w < CHUNK_WORDS; ++w) {
+            unsigned m = s_ev[w];
+            while (m) {
+                const int ch = w * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                if ((seen++ % nw) != wid) continue;
+                const int f = ch * 32 + lane;
+                bool uni = true, forced = true;
+                if (f < g.F) {
+                    const int v = A.faceLocal[f];
+                    const long long gi = (long long)k * B + v;
+                    const int yh = __ldcg(&A.yhat[gi]);
+                    const long long cs = nlink_sum<CONN>(g, A.Wl, k, v);
+                    face_slot_cap<CONN>(A, it, sv, k, kz, ky, kx, f, v, (long long)A.U[gi], yh, cs, m1024, uni,
+                                        forced);
+                }
+                ok &= __all_sync(0xffffffffu, forced) ? 1 : 0;
+                if (!__all_sync(0xffffffffu, uni) && lane == 0) atomicOr(&s_act[w], 1u << (ch & 31));
+            }
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) s_ok = 0;
+        }
+        __syncthreads();
+        if (s_ok) {
+            // labels stand; the block stays forced (quiet if no chunk is active)
+            int any = 0;
+#pragma unroll
+            for (int w = 0; w < CHUNK_WORDS; ++w) any |= s_act[w] != 0;
+            if (tid < CHUNK_WORDS) {
+                sv.act[(size_t)k * CHUNK_WORDS + tid] = s_act[tid];
+                sv.dsc[(size_t)k * CHUNK_WORDS + tid] = 0u;
+            }
+            if (tid == 0) {
+                sv.qs[k] = any ? 2 : 1;
+                atomicAdd(&A.ctrl->sched_part, 1ull);
+            }
+            wl_push_mask(g, k, any ? (1u << 13) : 0u, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K,
+                         &sv.uq_n[it.t & 1], wl_mark(A.epoch, it.t));
+            __syncthreads();
+            return;
+        }
+        // a slot is no longer forced to its label: the full solve below
+    }
 
     // 1a. capacity build: forward intra-block n-links from HBM, U and yhat
 #pragma unroll 1
@@ -671,6 +912,7 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
         C64[v] = A.Cgiven ? A.Cgiven[gi] : (long long)A.U[gi];
         st[v] = it.first ? 0 : __ldcg(&A.yhat[gi]);
     }
+    if (tid < CHUNK_WORDS) s_act[tid] = 0u;
     __syncthreads();
     // 1b. backward n-links from shared memory, n-link sums, interior unaries
     const bool need_caps = !A.Cgiven && !it.first;
@@ -701,85 +943,53 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
             if (it.int_test && (yh ? (T < -(long long)cs) : (T >= (long long)cs))) {
                 C64[v] = T;
             } else {
-                allf = 0;
                 const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
-                C64[v] = shifted_cap<CONN>(g, A.U, A.Wl, A.yhat, A.yF, A.aF, A.faceIndex, k, kz, ky,
-                                           kx, v, lz, ly, lx, 0, m1024);
+                const long long C = shifted_cap<CONN>(g, A.U, A.Wl, A.yhat, A.yF, A.aF, A.faceIndex, k, kz, ky,
+                                                      kx, v, lz, ly, lx, 0, m1024);
+                C64[v] = C;
+                if (!(yh ? (C < -(long long)cs) : (C >= (long long)cs))) allf = 0;
             }
         } else if (!need_caps) {
             st[v] = FREE;
         }
     }
-    // 1c. face pixels, one face slot per thread (after the n-link sums are in):
-    // a face pixel in the trivial state (a = +0, y = yhat) whose cross
-    // neighbours all have y_j = y_i gets exactly the interior unary (every
-    // cross term of Eq. 8 is +-0 and adds nothing) and the integer forced
-    // test; every other face pixel the exact FP64 Eq. 8 unary.
+    // 1c. face pixels, in chunks of 32 slots per warp (after the n-link sums are in)
     if (need_caps) {
         __syncthreads();
-        const SchedView sv = sched_view(A.sched, g.K);
-        for (int f = tid; f < g.F; f += NT) {
-            const int v = A.faceLocal[f];
-            const long long gi = (long long)k * B + v;
-            const int yh = st[v];
-            const long long sidx = (long long)k * g.F + f;
-            const double yv = __ldcg(&A.yF[sidx]);
-            const double av = __ldcg(&A.aF[sidx]);
-            double yj[CONN];
-            int wj[CONN];
-            unsigned ok = 0;
-            bool lab_same = true;
-#pragma unroll
-            for (int d = 0; d < CONN; ++d) {
-                int kn, ln, fn;
-                yj[d] = 0.0;
-                wj[d] = 0;
-                if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
-                    ok |= 1u << d;
-                    yj[d] = __ldcg(&A.yF[(long long)kn * g.F + fn]);
-                    wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi]
-                                     : A.Wl[(long long)(d - nh) * g.N + (long long)kn * B + ln];
-                    if (it.qeval) lab_same = lab_same && (int)__ldcg(&sv.yhF[(long long)kn * g.F + fn]) == yh;
-                }
+        for (int ch = wid; ch < nchunks; ch += nw) {
+            const int f = ch * 32 + lane;
+            bool uni = true, forced = true;
+            if (f < g.F) {
+                const int v = A.faceLocal[f];
+                C64[v] = face_slot_cap<CONN>(A, it, sv, k, kz, ky, kx, f, v, C64[v], st[v], capsum[v], m1024, uni,
+                                             forced);
+                st[v] = FREE;
             }
-            bool uni = __double_as_longlong(av) == 0 && yv == (double)yh;
-#pragma unroll
-            for (int d = 0; d < CONN; ++d)
-                if ((ok >> d) & 1) uni = uni && yj[d] == yv;
-            const long long Ui = C64[v];
-            bool forced = false;
-            if (uni) {
-                const long long T = yh ? Ui - it.H : Ui + it.H;
-                const long long cs = capsum[v];
-                if (it.int_test && (yh ? (T < -cs) : (T >= cs))) {
-                    C64[v] = T;
-                    forced = true;
-                } else {
-                    C64[v] = interior_cap(Ui, yh, m1024);
-                }
-            } else {
-                C64[v] = face_cap_from<CONN>(Ui, yv, av, yj, wj, ok, m1024);
-            }
-            st[v] = FREE;
             allf &= forced ? 1 : 0;
-            qok &= (forced && lab_same) ? 1 : 0;
+            allu &= uni ? 1 : 0;
+            if (it.qeval && !__all_sync(0xffffffffu, uni) && lane == 0) atomicOr(&s_act[ch >> 5], 1u << (ch & 31));
         }
     }
-    // Every pixel forced to its own label: the labels stand (the cut would
+    // Every node forced to its own label: the labels stand (the cut would
     // reproduce them), so the cut is skipped.
     allf = need_caps ? __syncthreads_and(allf) : (__syncthreads(), 0);
-    if (it.qeval) {
-        const int quiet = __syncthreads_and(qok & allf);
+    if (A.sched) {
+        const int quiet = __syncthreads_and(allu) && allf;
         if (tid == 0) {
-            const SchedView sv = sched_view(A.sched, g.K);
-            sv.qs[k] = (uint8_t)quiet;
+            // 0: not forced; 1: quiet; 2: forced with active chunks.  The
+            // first iteration of a launch (no evaluation) leaves 0.
+            sv.qs[k] = (uint8_t)(!it.qeval ? 0 : (quiet ? 1 : (allf ? 2 : 0)));
             s_pm = quiet ? 0u : (1u << 13);      // a block that is not quiet is updated
+        }
+        if (tid < CHUNK_WORDS) {
+            sv.act[(size_t)k * CHUNK_WORDS + tid] = s_act[tid];
+            sv.dsc[(size_t)k * CHUNK_WORDS + tid] = 0u;
+            if (!it.qeval) sv.duc[(size_t)k * CHUNK_WORDS + tid] = 0u;
         }
     }
     if (allf) {
         if (it.qeval) {
             __syncthreads();
-            const SchedView sv = sched_view(A.sched, g.K);
             wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &sv.uq_n[it.t & 1],
                          wl_mark(A.epoch, it.t));
             __syncthreads();
@@ -788,7 +998,8 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
     }
     cut_block<CONN, SA>(A, k, smem, bw, pl, imask, c_start, nullptr);
     if (it.qeval) {
-        // blocks next to a face pixel whose label changed get updated too
+        // blocks next to a face pixel whose label changed get updated too, and
+        // the chunks of those neighbours are marked for their update
         unsigned pm = 0;
 #pragma unroll 1
         for (int q = 0; q < NPTMAX; ++q) {
@@ -801,16 +1012,18 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
                 for (int d = 0; d < CONN; ++d) {
                     int kn, ln, fn;
                     const int e = A.halo[d * g.F + f];
-                    if (halo_decode(g, e, kz, ky, kx, kn, ln, fn)) pm |= 1u << (e >> 24);
+                    if (halo_decode(g, e, kz, ky, kx, kn, ln, fn)) {
+                        pm |= 1u << (e >> 24);
+                        chunk_mark(sv.duc, kn, fn);
+                    }
                 }
             }
         }
         pm = __reduce_or_sync(0xffffffffu, pm);
         if ((tid & 31) == 0 && pm) atomicOr(&s_pm, pm);
         __syncthreads();
-        const SchedView sv = sched_view(A.sched, g.K);
         wl_push_mask(g, k, s_pm, sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &sv.uq_n[it.t & 1],
-                         wl_mark(A.epoch, it.t));
+                     wl_mark(A.epoch, it.t));
         __syncthreads();
     }
 }
@@ -838,18 +1051,55 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
     const SArr<uint8_t> st(reinterpret_cast<uint8_t*>(capsum_p + B), B);
     const SArr<uint32_t> bits(reinterpret_cast<uint32_t*>(smem + solver_bits_offset(CONN, B)),
                               (long long)(CONN + 3) * ((B + 31) / 32));
+    const SArr<int16_t> flist(reinterpret_cast<int16_t*>(smem + solver_list_offset(CONN, B)), B);
+    __shared__ int s_nf;
     const long long c_built = clock64();
     long long c_bfs = 0;
     int levels = 0, bfs_max = 0;
 
-    // 2. exact folding of forced nodes
+    // 2. exact folding of forced nodes.  The first round scans every node and
+    // lists the nodes it leaves free (flist, s_nf of them, in no particular
+    // order: every pass below decides each node from values fixed for the
+    // pass, so the order does not matter); later rounds, the unary
+    // conversion and the push-relabel pulses visit only the list.  Nodes fixed
+    // by later rounds stay in the list and are skipped by their state.
+    if (tid == 0) s_nf = 0;
+    __syncthreads();             // the count starts at 0 before any warp appends
     int round = 0;
-    for (; round < A.fold_rounds; ++round) {
+    const int rounds = A.fold_rounds > 0 ? A.fold_rounds : 1;   // the first round builds the list
+    for (; round < rounds; ++round) {
         int changed = 0;
+        if (round == 0) {
 #pragma unroll 1
-        for (int q = 0; q < NPTMAX; ++q) {
-            int v = tid + q * NT;
-            if (v < B && st[v] == FREE) {
+            for (int q = 0; q < NPTMAX; ++q) {
+                int v = tid + q * NT;
+                bool fr = false;
+                if (v < B && st[v] == FREE) {
+                    const long long c = C64[v];
+                    const long long cs = capsum[v];
+                    int ns = (c >= cs) ? FIX0 : (c < -cs ? FIX1 : FREE);
+                    if (ns != FREE) {
+                        st[v] = (uint8_t)ns;
+#pragma unroll
+                        for (int d = 0; d < CONN; ++d) res[d * B + v] = 0;
+                        changed = 1;
+                    } else {
+                        fr = true;
+                    }
+                }
+                // warp-aggregated append to the free-node list
+                const unsigned m = __ballot_sync(0xffffffffu, fr);
+                int base = 0;
+                if ((tid & 31) == 0 && m) base = atomicAdd(&s_nf, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (fr) flist[base + __popc(m & ((1u << (tid & 31)) - 1u))] = (int16_t)v;
+            }
+        } else {
+            const int nf0 = s_nf;
+#pragma unroll 1
+            for (int i = tid; i < nf0; i += NT) {
+                const int v = flist[i];
+                if (st[v] != FREE) continue;
                 const long long c = C64[v];
                 const long long cs = capsum[v];
                 int ns = (c >= cs) ? FIX0 : (c < -cs ? FIX1 : FREE);
@@ -862,18 +1112,17 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
             }
         }
         // stop when nothing changed, or when no node is left free
+        __syncthreads();
+        const int nfl = s_nf;
         int left = 0;
 #pragma unroll 1
-        for (int q = 0; q < NPTMAX; ++q) {
-            int v = tid + q * NT;
-            left |= (v < B && st[v] == FREE);
-        }
+        for (int i = tid; i < nfl; i += NT) left |= st[flist[i]] == FREE;
         const int any_changed = __syncthreads_or(changed);
         if (!any_changed || !__syncthreads_or(left)) { round += any_changed; break; }
 #pragma unroll 1
-        for (int q = 0; q < NPTMAX; ++q) {
-            int v = tid + q * NT;
-            if (v < B && st[v] == FREE) {
+        for (int i = tid; i < nfl; i += NT) {
+            const int v = flist[i];
+            if (st[v] == FREE) {
                 long long c = C64[v];
                 int cs = capsum[v];
 #pragma unroll
@@ -894,24 +1143,25 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
         }
         __syncthreads();
     }
+    __syncthreads();
+    const int nlist = s_nf;
 
     // unaries of free nodes (|C| < 2^28) -> R2 as int32, then R1 becomes e / ein
-    // and R2 the heights
+    // and R2 the heights (only the free nodes' entries are used from here on)
     int nfree = 0;
 #pragma unroll 1
-    for (int q = 0; q < NPTMAX; ++q) {
-        int v = tid + q * NT;
-        if (v < B) {
-            const bool fr = st[v] == FREE;
-            capsum[v] = fr ? (int)C64[v] : 0;
-            nfree += fr;
-        }
+    for (int i = tid; i < nlist; i += NT) {
+        const int v = flist[i];
+        const bool fr = st[v] == FREE;
+        capsum[v] = fr ? (int)C64[v] : 0;
+        nfree += fr;
     }
     __syncthreads();
 #pragma unroll 1
-    for (int q = 0; q < NPTMAX; ++q) {
-        int v = tid + q * NT;
-        if (v < B) { e[v] = capsum[v]; ein[v] = 0; }
+    for (int i = tid; i < nlist; i += NT) {
+        const int v = flist[i];
+        e[v] = capsum[v];
+        ein[v] = 0;
     }
     const long long c_folded = clock64();
     const int HMAX = B + 1;
@@ -931,11 +1181,12 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
                 if (tid == 0) set_status(A.ctrl, 6 /* DOPE_ETIMEOUT */);
                 break;
             }
-            // push: heights hc fixed for the whole phase
+            // push: heights hc fixed for the whole phase (free nodes only: a
+            // free node's residual edges all lead to free nodes)
 #pragma unroll 1
-            for (int q = 0; q < NPTMAX; ++q) {
-                int v = tid + q * NT;
-                if (v < B && st[v] == FREE) {
+            for (int i = tid; i < nlist; i += NT) {
+                const int v = flist[i];
+                if (st[v] == FREE) {
                     int ev = e[v];
                     const int hv = hc[v];
                     if (ev > 0 && hv < HMAX) {
@@ -959,12 +1210,12 @@ __device__ __forceinline__ void cut_block(const SA& __restrict__ A, int k, unsig
                 }
             }
             __syncthreads();
-            // merge incoming flow, relabel into hn
+            // merge incoming flow, relabel into hn (a fixed node's height is
+            // never read: no residual edge leads to it)
             int act = 0;
 #pragma unroll 1
-            for (int q = 0; q < NPTMAX; ++q) {
-                int v = tid + q * NT;
-                if (v >= B) continue;
+            for (int i = tid; i < nlist; i += NT) {
+                const int v = flist[i];
                 int hv = hc[v];
                 if (st[v] == FREE) {
                     const int ev = e[v] + ein[v];
@@ -1091,11 +1342,38 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
     // chunks of 32, each chunk by the same butterfly, chunks in increasing order
     __shared__ double part[128];
     __shared__ unsigned pmask[128];
+    __shared__ unsigned s_do[CHUNK_WORDS];   // chunks updated here
+    __shared__ int s_qs;
     const int nchunks = (g.F + 31) >> 5;
-    for (int ch = wid; ch < nchunks; ch += nw) {
+    // A forced block (quiet, or with active chunks) updates only its active
+    // chunks and those holding a slot whose cross neighbour's label changed:
+    // every other slot is trivial with G = 0, so its update is the identity
+    // and adds +0 to r_k^2.  Other blocks update every chunk.
+    if (tid < CHUNK_WORDS) {
+        unsigned m = 0xffffffffu;
+        if (wl) {
+            const int q = __ldcg(&sv.qs[k]);
+            const unsigned du = __ldcg(&sv.duc[(size_t)k * CHUNK_WORDS + tid]);
+            if (!selfpush && q != 0) m = __ldcg(&sv.act[(size_t)k * CHUNK_WORDS + tid]) | du;
+            if (du) sv.duc[(size_t)k * CHUNK_WORDS + tid] = 0u;
+            if (tid == 0) s_qs = q;
+        }
+        s_do[tid] = m;
+    }
+    __syncthreads();
+    int seen = 0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        if (!((s_do[ch >> 5] >> (ch & 31)) & 1u)) continue;
+        if ((seen++ % nw) != wid) continue;
         const int f = ch * 32 + lane;
         double d2 = 0.0;
         unsigned pm = 0;
+        int fj[CONN], kj[CONN];   // face slot and block of each cross neighbour (block -1: none)
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            kj[d] = -1;
+            fj[d] = 0;
+        }
         if (f < g.F) {
             const int v = A.faceLocal[f];
             const long long gi = (long long)k * g.B + v;
@@ -1112,6 +1390,8 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
                     wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
                     yj[d] = __ldcg(&A.yhat[gj]);
                     cm |= 1u << (e >> 24);
+                    kj[d] = kn;
+                    fj[d] = fn;
                 }
             }
             const int yh = __ldcg(&A.yhat[gi]);
@@ -1152,6 +1432,22 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
                 if (changed) pm = cm | (1u << 13);
             }
         }
+        if (wl && !selfpush) {
+            // this slot's and its cross neighbours' Eq. 8 inputs changed: their
+            // blocks are solved next iteration and these chunks evaluated (one
+            // atomic per distinct chunk of the warp; the first iteration of a
+            // launch needs none, every block's next solve is a full one)
+            const bool ch_me = pm != 0;
+            const unsigned lanes = __ballot_sync(0xffffffffu, ch_me);
+            if (ch_me && lane == __ffs(lanes) - 1) chunk_mark(sv.dsc, k, f);
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                const bool mk = ch_me && kj[d] >= 0;
+                const unsigned key = mk ? (unsigned)kj[d] * 128u + (unsigned)(fj[d] >> 5) : 0xffffffffu;
+                const unsigned grp = __match_any_sync(0xffffffffu, key);
+                if (mk && lane == __ffs(grp) - 1) chunk_mark(sv.dsc, kj[d], fj[d]);
+            }
+        }
         if (__any_sync(0xffffffffu, d2 != 0.0))
             for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
         if (wl) pm = __reduce_or_sync(0xffffffffu, pm);
@@ -1163,14 +1459,18 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
     __syncthreads();
     if (tid == 0) {
         double r2 = 0.0;
-        for (int ch = 0; ch < nchunks; ++ch) r2 = __dadd_rn(r2, part[ch]);
+        unsigned m = 0;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            if (!((s_do[ch >> 5] >> (ch & 31)) & 1u)) continue;   // +0: adds nothing
+            r2 = __dadd_rn(r2, part[ch]);
+            m |= pmask[ch];
+        }
         A.r2blk[k] = r2;
         if (r2 != 0.0) atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
         if (wl) {
             // the blocks next to a face pixel whose state changed (and this
             // block, if it changed or is not quiet) are solved next iteration
-            unsigned m = (selfpush || !__ldcg(&sv.qs[k])) ? (1u << 13) : 0u;
-            for (int ch = 0; ch < nchunks; ++ch) m |= pmask[ch];
+            if (selfpush || s_qs != 1) m |= 1u << 13;
             pmask[0] = m;
         }
     }

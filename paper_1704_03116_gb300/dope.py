@@ -57,7 +57,7 @@ class dope_stats(ctypes.Structure):
                 ("windows", ctypes.c_int), ("window_iterations", ctypes.c_int),
                 ("window_cycles", ctypes.c_double * 8), ("solver_kernel", ctypes.c_int),
                 ("reserved", ctypes.c_int), ("blocks_solved", ctypes.c_int64),
-                ("blocks_updated", ctypes.c_int64)]
+                ("blocks_updated", ctypes.c_int64), ("blocks_solved_partial", ctypes.c_int64)]
 
 
 class dope_profile(ctypes.Structure):
