@@ -386,6 +386,50 @@ __device__ __forceinline__ int opp_dir(int k) {
     return k < nh ? k + nh : k - nh;
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies global -> shared (cp.async.bulk, the 1-D form of
+// the tensor memory accelerator), completed on an mbarrier in shared memory.
+// Source and destination 16-byte aligned, sizes multiples of 16.  The CTA is
+// its own cluster, so its shared::cluster addresses are its own.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Order this thread's earlier generic-proxy accesses of shared memory before
+// later asynchronous-proxy writes to it (the bulk copies).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void set_status(Ctrl* c, int code) {
     atomicCAS(&c->status, 0, code);
 }
@@ -891,26 +935,91 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
         // a slot is no longer forced to its label: the full solve below
     }
 
-    // 1a. capacity build: forward intra-block n-links from HBM, U and yhat
-#pragma unroll 1
-    for (int q = 0; q < NPTMAX; ++q) {
-        int v = tid + q * NT;
-        if (v >= B) continue;
-        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
-        const long long gi = (long long)k * B + v;
-        uint8_t m = 0;
+    // 1a. capacity build: forward intra-block n-links, U and yhat.  The block's
+    // slabs are contiguous (block-major layout), so when the block volume is a
+    // multiple of 16 one thread stages them into shared memory with bulk
+    // asynchronous copies (the forward weight planes straight into res, U
+    // into the capsum array, the labels into st), completed on an mbarrier;
+    // the nodes then zero the out-of-block n-links and widen U in place.
+    const bool bulk = !A.Cgiven && (B & 15) == 0;
+    if (bulk) {
+        __shared__ unsigned long long s_bar;
+        if (tid == 0) mbar_init(&s_bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            fence_proxy_async_smem();     // earlier generic accesses of this smem come first
+            const unsigned plane = 4u * (unsigned)B;
+            const unsigned bytes = (unsigned)nh * plane + plane + (it.first ? 0u : (unsigned)B);
+            mbar_expect_tx(&s_bar, bytes);
+            const long long base = (long long)k * B;
 #pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            int dz, dy, dx;
-            dir_off<CONN>(d, dz, dy, dx);
-            const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
-            const bool in = nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw;
-            if (in) m |= (uint8_t)(1u << d);
-            if (d < nh) res[d * B + v] = in ? A.Wl[(long long)d * g.N + gi] : 0;
+            for (int d = 0; d < nh; ++d) bulk_g2s(res_p + (size_t)d * B, A.Wl + (long long)d * g.N + base, plane, &s_bar);
+            bulk_g2s(capsum_p, A.U + base, plane, &s_bar);
+            if (!it.first) bulk_g2s(&st[0], A.yhat + base, (unsigned)B, &s_bar);
         }
-        imask |= (unsigned long long)m << (8 * q);
-        C64[v] = A.Cgiven ? A.Cgiven[gi] : (long long)A.U[gi];
-        st[v] = it.first ? 0 : __ldcg(&A.yhat[gi]);
+        {
+            // every thread waits for the copies (bounded, about 2 s: they come
+            // from this GPU's memory); a wait that runs out sets the status,
+            // then waits as long again for the copies still in flight
+            const long long t0 = clock64();
+            bool late = false;
+            while (!mbar_try_wait(&s_bar, 0)) {
+                if (!late && clock64() - t0 > 4000000000LL) {
+                    if (tid == 0) set_status(A.ctrl, 6 /* DOPE_ETIMEOUT */);
+                    late = true;
+                }
+                if (clock64() - t0 > 8000000000LL) break;
+            }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v >= B) continue;
+            const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+            uint8_t m = 0;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int dz, dy, dx;
+                dir_off<CONN>(d, dz, dy, dx);
+                const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+                const bool in = nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw;
+                if (in) m |= (uint8_t)(1u << d);
+                else if (d < nh) res[d * B + v] = 0;
+            }
+            imask |= (unsigned long long)m << (8 * q);
+            if (it.first) st[v] = 0;
+        }
+        // U: int32 in capsum -> int64 in C64 (different arrays; capsum is
+        // rewritten only in step 1b, after the barrier below)
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v < B) C64[v] = (long long)capsum[v];
+        }
+        __syncthreads();
+        if (tid == 0) mbar_inval(&s_bar);
+    } else {
+#pragma unroll 1
+        for (int q = 0; q < NPTMAX; ++q) {
+            int v = tid + q * NT;
+            if (v >= B) continue;
+            const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+            const long long gi = (long long)k * B + v;
+            uint8_t m = 0;
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int dz, dy, dx;
+                dir_off<CONN>(d, dz, dy, dx);
+                const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+                const bool in = nlz >= 0 && nlz < g.bd && nly >= 0 && nly < g.bh && nlx >= 0 && nlx < g.bw;
+                if (in) m |= (uint8_t)(1u << d);
+                if (d < nh) res[d * B + v] = in ? A.Wl[(long long)d * g.N + gi] : 0;
+            }
+            imask |= (unsigned long long)m << (8 * q);
+            C64[v] = A.Cgiven ? A.Cgiven[gi] : (long long)A.U[gi];
+            st[v] = it.first ? 0 : __ldcg(&A.yhat[gi]);
+        }
     }
     if (tid < CHUNK_WORDS) s_act[tid] = 0u;
     __syncthreads();
