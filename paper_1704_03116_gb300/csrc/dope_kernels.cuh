@@ -845,8 +845,117 @@ __device__ __forceinline__ long long nlink_sum(const Geo& g, const int32_t* __re
     return cs;
 }
 
+// One warp: re-evaluate chunk ch of forced block k (a partial solve).  Returns
+// through the warp: forced (every slot still forced to its label) and uni
+// (every slot trivial with equal neighbours).
 template <int CONN, class SA>
-__device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, unsigned char* smem) {
+__device__ __forceinline__ void eval_chunk(const SA& __restrict__ A, const IterArgs& it, const SchedView& sv, int k,
+                                           int ch, double m1024, bool& all_forced, bool& all_uni) {
+    const Geo& g = A.g;
+    const int lane = threadIdx.x & 31;
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    const int f = ch * 32 + lane;
+    bool uni = true, forced = true;
+    if (f < g.F) {
+        const int v = A.faceLocal[f];
+        const long long gi = (long long)k * g.B + v;
+        const int yh = __ldcg(&A.yhat[gi]);
+        const long long cs = nlink_sum<CONN>(g, A.Wl, k, v);
+        face_slot_cap<CONN>(A, it, sv, k, kz, ky, kx, f, v, (long long)A.U[gi], yh, cs, m1024, uni, forced);
+    }
+    all_forced = __all_sync(0xffffffffu, forced);
+    all_uni = __all_sync(0xffffffffu, uni);
+}
+
+// Partial solves of up to MB forced blocks at once (their nodes were all
+// forced to their labels at their last solve; see solve_block): the chunks
+// to evaluate of all of them are spread over the CTA's warps, so their load
+// latencies overlap.  ok[j] = 1 if block j's labels stand (its masks and
+// state are updated and it is put on the update list if still active); 0 if
+// a slot is no longer forced, and then nothing was written for it.
+constexpr int MB = 4;
+
+template <int CONN, class SA>
+__device__ void partial_solve_multi(const SA& __restrict__ A, const IterArgs it, const int* kk, int nb, int* ok) {
+    const Geo& g = A.g;
+    const int tid = threadIdx.x, wid = tid >> 5, nw = blockDim.x >> 5;
+    const SchedView sv = sched_view(A.sched, g.K);
+    const double m1024 = __dmul_rn(1024.0, it.mu);
+    __shared__ unsigned s_ev[MB][CHUNK_WORDS];
+    __shared__ unsigned s_act[MB][CHUNK_WORDS];
+    __shared__ int s_okb[MB];
+    __shared__ int s_tot;
+    if (tid < nb * CHUNK_WORDS) {
+        const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
+        const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
+        s_ev[j][w] = __ldcg(&sv.act[o]) | __ldcg(&sv.dsc[o]);     // every active chunk is among them
+        s_act[j][w] = 0u;
+    }
+    if (tid < MB) s_okb[tid] = 1;
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int j = 0; j < nb; ++j)
+            for (int w = 0; w < CHUNK_WORDS; ++w) tot += __popc(s_ev[j][w]);
+        s_tot = tot;
+    }
+    __syncthreads();
+    const int tot = s_tot;
+    // task t -> (block j, chunk ch): the t-th set bit over the blocks' masks
+    for (int t = wid; t < tot; t += nw) {
+        int r = t, j = 0, w = 0;
+        for (;;) {
+            const int c = __popc(s_ev[j][w]);
+            if (r < c) break;
+            r -= c;
+            if (++w == CHUNK_WORDS) { w = 0; ++j; }
+        }
+        unsigned m = s_ev[j][w];
+        for (int i = 0; i < r; ++i) m &= m - 1;
+        const int ch = w * 32 + __ffs(m) - 1;
+        bool fo, un;
+        eval_chunk<CONN>(A, it, sv, kk[j], ch, m1024, fo, un);
+        if ((threadIdx.x & 31) == 0) {
+            if (!fo) s_okb[j] = 0;
+            if (!un) atomicOr(&s_act[j][ch >> 5], 1u << (ch & 31));
+        }
+    }
+    __syncthreads();
+    // blocks whose labels stand: masks, state, and the update list (threads
+    // 32 j .. 32 j + 26 push block j)
+    if (tid < nb * CHUNK_WORDS) {
+        const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
+        if (s_okb[j]) {
+            const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
+            sv.act[o] = s_act[j][w];
+            sv.dsc[o] = 0u;
+        }
+    }
+    {
+        const int j = tid >> 5;
+        if (j < nb && s_okb[j]) {
+            int any = 0;
+#pragma unroll
+            for (int w = 0; w < CHUNK_WORDS; ++w) any |= s_act[j][w] != 0;
+            if ((tid & 31) == 0) {
+                sv.qs[kk[j]] = any ? 2 : 1;
+                atomicAdd(&A.ctrl->sched_part, 1ull);
+            }
+            const int lane = tid & 31;
+            if (any && lane == 13) {
+                // this block itself (offset code 13) on the update list
+                wl_push(sv.umark, sv.uq + (size_t)(it.t & 1) * g.K, &sv.uq_n[it.t & 1], kk[j],
+                        wl_mark(A.epoch, it.t));
+            }
+        }
+    }
+    if (tid < nb) ok[tid] = s_okb[tid];
+    __syncthreads();
+}
+
+template <int CONN, class SA>
+__device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, unsigned char* smem,
+                            bool try_partial = true) {
     const Geo& g = A.g;
     const int B = g.B;
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
@@ -873,7 +982,7 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
     __shared__ int s_ok;
     const long long c_start = clock64();
 
-    if (it.qeval && __ldcg(&sv.qs[k]) != 0) {
+    if (try_partial && it.qeval && __ldcg(&sv.qs[k]) != 0) {
         // Every node of the block was forced to its label at its last solve.
         // Nodes in chunks that are neither active nor marked dirty still are
         // (their inputs did not change, and the integer test's bound only
@@ -1439,12 +1548,111 @@ __global__ void __launch_bounds__(512, 2) k_block_solve(SolveArgs A) {
 //   y_i = (yhat_i + a_i) - (G_i / 1024) / mu               (Eq. 10)
 //   a_i = a_i + (yhat_i - y_i)                             (Eq. 11)
 // ---------------------------------------------------------------------------
+// One warp: Eq. 10 / Eq. 11 on chunk ch (32 face slots) of block k.  Returns
+// the chunk's sum of (yhat - y)^2 (every lane: the butterfly's result) and the
+// offset codes of the blocks to solve next iteration (OR over the warp).
+template <int CONN, class UA>
+__device__ __forceinline__ void update_chunk(const UA& __restrict__ A, double mu, int t, int k, int ch, int selfpush,
+                                             const SchedView& sv, double& d2_out, unsigned& pm_out) {
+    const Geo& g = A.g;
+    const int lane = threadIdx.x & 31;
+    constexpr int nh = CONN / 2;
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    const bool wl = A.sched != nullptr;
+    const int f = ch * 32 + lane;
+    double d2 = 0.0;
+    unsigned pm = 0;
+    int fj[CONN], kj[CONN];   // face slot and block of each cross neighbour (block -1: none)
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        kj[d] = -1;
+        fj[d] = 0;
+    }
+    if (f < g.F) {
+        const int v = A.faceLocal[f];
+        const long long gi = (long long)k * g.B + v;
+        int wj[CONN], yj[CONN];
+        unsigned cm = 0;      // offset codes of the blocks holding this pixel's cross neighbours
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int kn, ln, fn;
+            wj[d] = 0;
+            yj[d] = 0;
+            const int e = A.halo[d * g.F + f];
+            if (halo_decode(g, e, kz, ky, kx, kn, ln, fn)) {
+                const long long gj = (long long)kn * g.B + ln;
+                wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
+                yj[d] = __ldcg(&A.yhat[gj]);
+                cm |= 1u << (e >> 24);
+                kj[d] = kn;
+                fj[d] = fn;
+            }
+        }
+        const int yh = __ldcg(&A.yhat[gi]);
+        int G = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
+        const long long s = (long long)k * g.F + f;
+        const double yo = __ldcg(&A.yF[s]);
+        const double ao = __ldcg(&A.aF[s]);
+        const double aa = t == 1 ? 0.0 : ao;   // a = 0 before iteration 1
+        double yn, an;
+        if (G == 0 && __double_as_longlong(aa) == 0) {
+            // the operations below with G = 0 and a = +0: y = yhat + (+0) = yhat,
+            // a = +0 + (yhat - y) = +0, (yhat - y)^2 = +0
+            yn = (double)yh;
+            an = 0.0;
+        } else {
+            const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
+            // G = 0: (G/1024)/mu = +0 and x - (+0) = x exactly, so the division is skipped
+            const double ya = __dadd_rn((double)yh, aa);
+            yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
+            an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
+            const double dd = __dsub_rn((double)yh, yn);
+            d2 = __dmul_rn(dd, dd);
+        }
+        // only what changed is written back
+        bool changed = __double_as_longlong(yn) != __double_as_longlong(yo) ||
+                       __double_as_longlong(an) != __double_as_longlong(ao);
+        if (changed) {
+            A.yF[s] = yn;
+            A.aF[s] = an;
+        }
+        if (wl) {
+            if ((int)__ldcg(&sv.yhF[s]) != yh) {
+                sv.yhF[s] = (uint8_t)yh;
+                changed = true;
+            }
+            if (changed) pm = cm | (1u << 13);
+        }
+    }
+    if (wl && !selfpush) {
+        // this slot's and its cross neighbours' Eq. 8 inputs changed: their
+        // blocks are solved next iteration and these chunks evaluated (one
+        // atomic per distinct chunk of the warp; the first iteration of a
+        // launch needs none, every block's next solve is a full one)
+        const bool ch_me = pm != 0;
+        const unsigned lanes = __ballot_sync(0xffffffffu, ch_me);
+        if (ch_me && lane == __ffs(lanes) - 1) chunk_mark(sv.dsc, k, f);
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const bool mk = ch_me && kj[d] >= 0;
+            const unsigned key = mk ? (unsigned)kj[d] * 128u + (unsigned)(fj[d] >> 5) : 0xffffffffu;
+            const unsigned grp = __match_any_sync(0xffffffffu, key);
+            if (mk && lane == __ffs(grp) - 1) chunk_mark(sv.dsc, kj[d], fj[d]);
+        }
+    }
+    if (__any_sync(0xffffffffu, d2 != 0.0))
+        for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    if (wl) pm = __reduce_or_sync(0xffffffffu, pm);
+    d2_out = d2;
+    pm_out = pm;
+}
+
 template <int CONN, class UA>
 __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, int selfpush = 0) {
     const Geo& g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-    constexpr int nh = CONN / 2;
-    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
     const bool wl = A.sched != nullptr;
     const SchedView sv = sched_view(A.sched, g.K);
     // r_k^2 is summed in a fixed order, whatever the CTA shape: face slots in
@@ -1474,92 +1682,9 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
     for (int ch = 0; ch < nchunks; ++ch) {
         if (!((s_do[ch >> 5] >> (ch & 31)) & 1u)) continue;
         if ((seen++ % nw) != wid) continue;
-        const int f = ch * 32 + lane;
-        double d2 = 0.0;
-        unsigned pm = 0;
-        int fj[CONN], kj[CONN];   // face slot and block of each cross neighbour (block -1: none)
-#pragma unroll
-        for (int d = 0; d < CONN; ++d) {
-            kj[d] = -1;
-            fj[d] = 0;
-        }
-        if (f < g.F) {
-            const int v = A.faceLocal[f];
-            const long long gi = (long long)k * g.B + v;
-            int wj[CONN], yj[CONN];
-            unsigned cm = 0;      // offset codes of the blocks holding this pixel's cross neighbours
-#pragma unroll
-            for (int d = 0; d < CONN; ++d) {
-                int kn, ln, fn;
-                wj[d] = 0;
-                yj[d] = 0;
-                const int e = A.halo[d * g.F + f];
-                if (halo_decode(g, e, kz, ky, kx, kn, ln, fn)) {
-                    const long long gj = (long long)kn * g.B + ln;
-                    wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
-                    yj[d] = __ldcg(&A.yhat[gj]);
-                    cm |= 1u << (e >> 24);
-                    kj[d] = kn;
-                    fj[d] = fn;
-                }
-            }
-            const int yh = __ldcg(&A.yhat[gi]);
-            int G = 0;
-#pragma unroll
-            for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
-            const long long s = (long long)k * g.F + f;
-            const double yo = __ldcg(&A.yF[s]);
-            const double ao = __ldcg(&A.aF[s]);
-            const double aa = t == 1 ? 0.0 : ao;   // a = 0 before iteration 1
-            double yn, an;
-            if (G == 0 && __double_as_longlong(aa) == 0) {
-                // the operations below with G = 0 and a = +0: y = yhat + (+0) = yhat,
-                // a = +0 + (yhat - y) = +0, (yhat - y)^2 = +0
-                yn = (double)yh;
-                an = 0.0;
-            } else {
-                const double gq = __dmul_rn((double)G, 0.0009765625);   // G / 1024, exact
-                // G = 0: (G/1024)/mu = +0 and x - (+0) = x exactly, so the division is skipped
-                const double ya = __dadd_rn((double)yh, aa);
-                yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
-                an = __dadd_rn(aa, __dsub_rn((double)yh, yn));
-                const double dd = __dsub_rn((double)yh, yn);
-                d2 = __dmul_rn(dd, dd);
-            }
-            // only what changed is written back
-            bool changed = __double_as_longlong(yn) != __double_as_longlong(yo) ||
-                           __double_as_longlong(an) != __double_as_longlong(ao);
-            if (changed) {
-                A.yF[s] = yn;
-                A.aF[s] = an;
-            }
-            if (wl) {
-                if ((int)__ldcg(&sv.yhF[s]) != yh) {
-                    sv.yhF[s] = (uint8_t)yh;
-                    changed = true;
-                }
-                if (changed) pm = cm | (1u << 13);
-            }
-        }
-        if (wl && !selfpush) {
-            // this slot's and its cross neighbours' Eq. 8 inputs changed: their
-            // blocks are solved next iteration and these chunks evaluated (one
-            // atomic per distinct chunk of the warp; the first iteration of a
-            // launch needs none, every block's next solve is a full one)
-            const bool ch_me = pm != 0;
-            const unsigned lanes = __ballot_sync(0xffffffffu, ch_me);
-            if (ch_me && lane == __ffs(lanes) - 1) chunk_mark(sv.dsc, k, f);
-#pragma unroll
-            for (int d = 0; d < CONN; ++d) {
-                const bool mk = ch_me && kj[d] >= 0;
-                const unsigned key = mk ? (unsigned)kj[d] * 128u + (unsigned)(fj[d] >> 5) : 0xffffffffu;
-                const unsigned grp = __match_any_sync(0xffffffffu, key);
-                if (mk && lane == __ffs(grp) - 1) chunk_mark(sv.dsc, kj[d], fj[d]);
-            }
-        }
-        if (__any_sync(0xffffffffu, d2 != 0.0))
-            for (int o = 16; o > 0; o >>= 1) d2 = __dadd_rn(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-        if (wl) pm = __reduce_or_sync(0xffffffffu, pm);
+        double d2;
+        unsigned pm;
+        update_chunk<CONN>(A, mu, t, k, ch, selfpush, sv, d2, pm);
         if (lane == 0) {
             part[ch] = d2;
             pmask[ch] = pm;
@@ -1589,6 +1714,86 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
                      wl_mark(A.epoch, t + 1));
         __syncthreads();
     }
+}
+
+// Updates of up to MB forced blocks at once (none in the first iteration of a
+// launch): the chunks of all of them (active, or next to a changed label) are
+// spread over the CTA's warps; each block's r_k^2 is then summed in its fixed
+// chunk order and its pushes made by its own group of threads.
+template <int CONN, class UA>
+__device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, const int* kk, int nb) {
+    const Geo& g = A.g;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const SchedView sv = sched_view(A.sched, g.K);
+    __shared__ double partm[MB][128];
+    __shared__ unsigned pmm[MB][128];
+    __shared__ unsigned s_dom[MB][CHUNK_WORDS];
+    __shared__ unsigned s_mm[MB];
+    __shared__ int s_totm;
+    const int nchunks = (g.F + 31) >> 5;
+    if (tid < nb * CHUNK_WORDS) {
+        const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
+        const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
+        const unsigned du = __ldcg(&sv.duc[o]);
+        s_dom[j][w] = __ldcg(&sv.act[o]) | du;
+        if (du) sv.duc[o] = 0u;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int j = 0; j < nb; ++j)
+            for (int w = 0; w < CHUNK_WORDS; ++w) tot += __popc(s_dom[j][w]);
+        s_totm = tot;
+    }
+    __syncthreads();
+    const int tot = s_totm;
+    for (int tk = wid; tk < tot; tk += nw) {
+        int r = tk, j = 0, w = 0;
+        for (;;) {
+            const int c = __popc(s_dom[j][w]);
+            if (r < c) break;
+            r -= c;
+            if (++w == CHUNK_WORDS) { w = 0; ++j; }
+        }
+        unsigned m = s_dom[j][w];
+        for (int i = 0; i < r; ++i) m &= m - 1;
+        const int ch = w * 32 + __ffs(m) - 1;
+        double d2;
+        unsigned pm;
+        update_chunk<CONN>(A, mu, t, kk[j], ch, 0, sv, d2, pm);
+        if (lane == 0) {
+            partm[j][ch] = d2;
+            pmm[j][ch] = pm;
+        }
+    }
+    __syncthreads();
+    if (wid < nb && lane == 0) {
+        const int j = wid, k = kk[j];
+        double r2 = 0.0;
+        unsigned m = 0;
+        for (int ch = 0; ch < nchunks; ++ch) {
+            if (!((s_dom[j][ch >> 5] >> (ch & 31)) & 1u)) continue;   // +0: adds nothing
+            r2 = __dadd_rn(r2, partm[j][ch]);
+            m |= pmm[j][ch];
+        }
+        A.r2blk[k] = r2;
+        if (r2 != 0.0) atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
+        if (__ldcg(&sv.qs[k]) != 1) m |= 1u << 13;
+        s_mm[j] = m;
+    }
+    __syncthreads();
+    if (wid < nb && lane < 27) {
+        const int j = wid, k = kk[j];
+        const unsigned m = s_mm[j];
+        if ((m >> lane) & 1u) {
+            const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+            const int nkz = kz + lane / 9 - 1, nky = ky + (lane / 3) % 3 - 1, nkx = kx + lane % 3 - 1;
+            if (nkz >= 0 && nkz < g.nbz && nky >= 0 && nky < g.nby && nkx >= 0 && nkx < g.nbx)
+                wl_push(sv.smark, sv.sq + (size_t)((t + 1) & 1) * g.K, &sv.sq_n[(t + 1) & 1],
+                        (nkz * g.nby + nky) * g.nbx + nkx, wl_mark(A.epoch, t + 1));
+        }
+    }
+    __syncthreads();
 }
 
 // One launch = one iteration's Eq. 10 / Eq. 11 update, one CTA per block.
@@ -1984,6 +2189,7 @@ template <int CONN, int NT>
 __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persistent(PersistArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_k;
+    __shared__ int s_kk[MB], s_qq[MB], s_pk[MB], s_pok[MB], s_np;   // a grab of list entries
     __shared__ long long s_red[32];
     Ctrl* c = P.s.ctrl;
     const int K = P.s.g.K;
@@ -2008,9 +2214,45 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
             if (wl) sv.sq_n[(t + 1) & 1] = 0u;
         }
         const int ns = full ? K : (int)__ldcg(&sv.sq_n[t & 1]);
-        for (int i = next_block(P.dynamic, &c->work[0], -1, &s_k); i < ns;
-             i = next_block(P.dynamic, &c->work[0], i, &s_k))
-            solve_block<CONN>(P.s, it, full ? i : __ldcg(&sv.sq[(t & 1) * (size_t)K + i]), smem);
+        if (full || !P.dynamic) {
+            for (int i = next_block(P.dynamic, &c->work[0], -1, &s_k); i < ns;
+                 i = next_block(P.dynamic, &c->work[0], i, &s_k))
+                solve_block<CONN>(P.s, it, full ? i : __ldcg(&sv.sq[(t & 1) * (size_t)K + i]), smem);
+        } else {
+            // from the list, a few entries per grab: the forced blocks among them
+            // are re-evaluated together (partial_solve_multi), the others (and
+            // any whose partial solve fails) solved one by one
+            int grab = ns / (int)gridDim.x;
+            grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
+            for (;;) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_k = (int)atomicAdd(&c->work[0], (unsigned)grab);
+                __syncthreads();
+                const int i0 = s_k;
+                if (i0 >= ns) break;
+                const int nb = ns - i0 < grab ? ns - i0 : grab;
+                if (threadIdx.x < nb) {
+                    const int kb = __ldcg(&sv.sq[(t & 1) * (size_t)K + i0 + threadIdx.x]);
+                    s_kk[threadIdx.x] = kb;
+                    s_qq[threadIdx.x] = __ldcg(&sv.qs[kb]);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int np = 0;
+                    for (int j = 0; j < nb; ++j)
+                        if (s_qq[j]) s_pk[np++] = s_kk[j];
+                    s_np = np;
+                }
+                __syncthreads();
+                const int np = s_np;
+                if (np) partial_solve_multi<CONN>(P.s, it, s_pk, np, s_pok);
+                for (int j = 0, jp = 0; j < nb; ++j) {
+                    bool done = false;
+                    if (s_qq[j]) done = s_pok[jp++] != 0;
+                    if (!done) solve_block<CONN>(P.s, it, s_kk[j], smem, false);
+                }
+            }
+        }
         const long long c1 = clock64();
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
         const long long c2 = clock64();
@@ -2019,9 +2261,40 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
             if (wl) sv.uq_n[(t + 1) & 1] = 0u;
         }
         const int nu = full ? K : (int)__ldcg(&sv.uq_n[t & 1]);
-        for (int i = next_block(P.dynamic, &c->work[1], -1, &s_k); i < nu;
-             i = next_block(P.dynamic, &c->work[1], i, &s_k))
-            update_block<CONN>(P.u, mu, t, full ? i : __ldcg(&sv.uq[(t & 1) * (size_t)K + i]), full ? 1 : 0);
+        if (full || !P.dynamic) {
+            for (int i = next_block(P.dynamic, &c->work[1], -1, &s_k); i < nu;
+                 i = next_block(P.dynamic, &c->work[1], i, &s_k))
+                update_block<CONN>(P.u, mu, t, full ? i : __ldcg(&sv.uq[(t & 1) * (size_t)K + i]), full ? 1 : 0);
+        } else {
+            // from the list, a few entries per grab: forced blocks updated together
+            int grab = nu / (int)gridDim.x;
+            grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
+            for (;;) {
+                __syncthreads();
+                if (threadIdx.x == 0) s_k = (int)atomicAdd(&c->work[1], (unsigned)grab);
+                __syncthreads();
+                const int i0 = s_k;
+                if (i0 >= nu) break;
+                const int nb = nu - i0 < grab ? nu - i0 : grab;
+                if (threadIdx.x < nb) {
+                    const int kb = __ldcg(&sv.uq[(t & 1) * (size_t)K + i0 + threadIdx.x]);
+                    s_kk[threadIdx.x] = kb;
+                    s_qq[threadIdx.x] = __ldcg(&sv.qs[kb]);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int np = 0;
+                    for (int j = 0; j < nb; ++j)
+                        if (s_qq[j]) s_pk[np++] = s_kk[j];
+                    s_np = np;
+                }
+                __syncthreads();
+                const int np = s_np;
+                if (np) update_blocks_multi<CONN>(P.u, mu, t, s_pk, np);
+                for (int j = 0; j < nb; ++j)
+                    if (!s_qq[j]) update_block<CONN>(P.u, mu, t, s_kk[j], 0);
+            }
+        }
         if (wl && !full && blockIdx.x == 0 && threadIdx.x == 0) {
             atomicAdd(&c->sched_work[0], (unsigned long long)ns);
             atomicAdd(&c->sched_work[1], (unsigned long long)nu);
