@@ -1721,7 +1721,8 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
 // spread over the CTA's warps; each block's r_k^2 is then summed in its fixed
 // chunk order and its pushes made by its own group of threads.
 template <int CONN, class UA>
-__device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, const int* kk, int nb) {
+__device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, const int* kk, int nb,
+                                    int full = 0) {
     const Geo& g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const SchedView sv = sched_view(A.sched, g.K);
@@ -1733,10 +1734,16 @@ __device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, 
     const int nchunks = (g.F + 31) >> 5;
     if (tid < nb * CHUNK_WORDS) {
         const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
-        const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
-        const unsigned du = __ldcg(&sv.duc[o]);
-        s_dom[j][w] = __ldcg(&sv.act[o]) | du;
-        if (du) sv.duc[o] = 0u;
+        if (full) {
+            // the first iteration of a launch: every chunk (and no list state is read)
+            const int hi = nchunks - w * 32;
+            s_dom[j][w] = hi <= 0 ? 0u : (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u));
+        } else {
+            const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
+            const unsigned du = __ldcg(&sv.duc[o]);
+            s_dom[j][w] = __ldcg(&sv.act[o]) | du;
+            if (du) sv.duc[o] = 0u;
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -1760,7 +1767,7 @@ __device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, 
         const int ch = w * 32 + __ffs(m) - 1;
         double d2;
         unsigned pm;
-        update_chunk<CONN>(A, mu, t, kk[j], ch, 0, sv, d2, pm);
+        update_chunk<CONN>(A, mu, t, kk[j], ch, full, sv, d2, pm);
         if (lane == 0) {
             partm[j][ch] = d2;
             pmm[j][ch] = pm;
@@ -1778,7 +1785,7 @@ __device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, 
         }
         A.r2blk[k] = r2;
         if (r2 != 0.0) atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
-        if (__ldcg(&sv.qs[k]) != 1) m |= 1u << 13;
+        if (full || __ldcg(&sv.qs[k]) != 1) m |= 1u << 13;
         s_mm[j] = m;
     }
     __syncthreads();
@@ -2261,7 +2268,7 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
             if (wl) sv.uq_n[(t + 1) & 1] = 0u;
         }
         const int nu = full ? K : (int)__ldcg(&sv.uq_n[t & 1]);
-        if (full || !P.dynamic) {
+        if (!wl || !P.dynamic) {
             for (int i = next_block(P.dynamic, &c->work[1], -1, &s_k); i < nu;
                  i = next_block(P.dynamic, &c->work[1], i, &s_k))
                 update_block<CONN>(P.u, mu, t, full ? i : __ldcg(&sv.uq[(t & 1) * (size_t)K + i]), full ? 1 : 0);
@@ -2277,9 +2284,10 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
                 if (i0 >= nu) break;
                 const int nb = nu - i0 < grab ? nu - i0 : grab;
                 if (threadIdx.x < nb) {
-                    const int kb = __ldcg(&sv.uq[(t & 1) * (size_t)K + i0 + threadIdx.x]);
+                    const int kb = full ? i0 + (int)threadIdx.x
+                                        : __ldcg(&sv.uq[(t & 1) * (size_t)K + i0 + threadIdx.x]);
                     s_kk[threadIdx.x] = kb;
-                    s_qq[threadIdx.x] = __ldcg(&sv.qs[kb]);
+                    s_qq[threadIdx.x] = full ? 1 : __ldcg(&sv.qs[kb]);
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {
@@ -2290,7 +2298,7 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
                 }
                 __syncthreads();
                 const int np = s_np;
-                if (np) update_blocks_multi<CONN>(P.u, mu, t, s_pk, np);
+                if (np) update_blocks_multi<CONN>(P.u, mu, t, s_pk, np, full ? 1 : 0);
                 for (int j = 0; j < nb; ++j)
                     if (!s_qq[j]) update_block<CONN>(P.u, mu, t, s_kk[j], 0);
             }
