@@ -875,16 +875,37 @@ __device__ __forceinline__ void eval_chunk(const SA& __restrict__ A, const IterA
 // a slot is no longer forced, and then nothing was written for it.
 constexpr int MB = 4;
 
+// Shared scratch of the update and partial-solve helpers.  They are templates
+// over the connectivity, and a batched launch instantiates each of them three
+// times; taking their arrays from one non-template accessor keeps a single
+// copy per kernel (static shared variables of a template exist once per
+// instantiation).  The helpers never run at the same time in a CTA.
+struct UpdSmem {
+    double part[MB][128];        // per block and chunk: sum of (yhat - y)^2
+    unsigned pm[MB][128];        // per block and chunk: offset codes to push
+    unsigned dom[MB][CHUNK_WORDS];   // chunks updated / evaluated
+    unsigned act[MB][CHUNK_WORDS];   // chunks found active
+    unsigned mm[MB];             // per block: push mask
+    int okb[MB];                 // per block: labels stand
+    int tot;
+    int qs;
+};
+__device__ __forceinline__ UpdSmem& upd_smem() {
+    __shared__ UpdSmem u;
+    return u;
+}
+
 template <int CONN, class SA>
 __device__ void partial_solve_multi(const SA& __restrict__ A, const IterArgs it, const int* kk, int nb, int* ok) {
     const Geo& g = A.g;
     const int tid = threadIdx.x, wid = tid >> 5, nw = blockDim.x >> 5;
     const SchedView sv = sched_view(A.sched, g.K);
     const double m1024 = __dmul_rn(1024.0, it.mu);
-    __shared__ unsigned s_ev[MB][CHUNK_WORDS];
-    __shared__ unsigned s_act[MB][CHUNK_WORDS];
-    __shared__ int s_okb[MB];
-    __shared__ int s_tot;
+    UpdSmem& us = upd_smem();
+    unsigned (&s_ev)[MB][CHUNK_WORDS] = us.dom;
+    unsigned (&s_act)[MB][CHUNK_WORDS] = us.act;
+    int (&s_okb)[MB] = us.okb;
+    int& s_tot = us.tot;
     if (tid < nb * CHUNK_WORDS) {
         const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
         const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
@@ -1657,10 +1678,11 @@ __device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, 
     const SchedView sv = sched_view(A.sched, g.K);
     // r_k^2 is summed in a fixed order, whatever the CTA shape: face slots in
     // chunks of 32, each chunk by the same butterfly, chunks in increasing order
-    __shared__ double part[128];
-    __shared__ unsigned pmask[128];
-    __shared__ unsigned s_do[CHUNK_WORDS];   // chunks updated here
-    __shared__ int s_qs;
+    UpdSmem& us = upd_smem();
+    double (&part)[128] = us.part[0];
+    unsigned (&pmask)[128] = us.pm[0];
+    unsigned (&s_do)[CHUNK_WORDS] = us.dom[0];   // chunks updated here
+    int& s_qs = us.qs;
     const int nchunks = (g.F + 31) >> 5;
     // A forced block (quiet, or with active chunks) updates only its active
     // chunks and those holding a slot whose cross neighbour's label changed:
@@ -1726,11 +1748,12 @@ __device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, 
     const Geo& g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const SchedView sv = sched_view(A.sched, g.K);
-    __shared__ double partm[MB][128];
-    __shared__ unsigned pmm[MB][128];
-    __shared__ unsigned s_dom[MB][CHUNK_WORDS];
-    __shared__ unsigned s_mm[MB];
-    __shared__ int s_totm;
+    UpdSmem& us = upd_smem();
+    double (&partm)[MB][128] = us.part;
+    unsigned (&pmm)[MB][128] = us.pm;
+    unsigned (&s_dom)[MB][CHUNK_WORDS] = us.dom;
+    unsigned (&s_mm)[MB] = us.mm;
+    int& s_totm = us.tot;
     const int nchunks = (g.F + 31) >> 5;
     if (tid < nb * CHUNK_WORDS) {
         const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
@@ -3140,6 +3163,7 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
     __shared__ unsigned char s_conv[BATCH_MAX];
     __shared__ unsigned char s_full[BATCH_MAX];   // 1: this iteration does every block of the problem
     __shared__ int s_nlive, s_total, s_k, s_any, s_done;
+    __shared__ int s_gp[MB], s_gk[MB], s_gq[MB], s_gpk[MB], s_gok[MB], s_gnp;   // a grab of list entries
     const int np = P.nprob;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     Ctrl* bc = P.bc;
@@ -3191,24 +3215,60 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
                 if (c_batch[p].sched) sched_view(c_batch[p].sched, s_K[p]).sq_n[(s_t[p] + 2) & 1] = 0u;
             }
         }
+        // a few entries per grab; the forced blocks of one problem among them are
+        // re-evaluated together (partial_solve_multi), the others one by one
+        int grab = total / (int)gridDim.x;
+        grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
         for (;;) {
             __syncthreads();
-            if (tid == 0) s_k = (int)atomicAdd(&bc->work[0], 1u);
+            if (tid == 0) s_k = (int)atomicAdd(&bc->work[0], (unsigned)grab);
             __syncthreads();
-            const int gk = s_k;
-            if (gk >= total) break;
-            const int q = batch_owner(s_lbase, nlive, gk);
-            const int p = s_list[q];
-            const int i = gk - s_lbase[q];
-            const int t = s_t[p] + 1;
-            IterArgs it = iter_args(t, s_mu[p]);
-            it.qeval = !s_full[p];
-            const int k = s_full[p] ? i
-                                    : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).sq[(size_t)(t & 1) * s_K[p] + i]);
-            const int conn = c_batch[p].conn;
-            if (conn == 4) solve_block<4>(c_batch[p], it, k, smem);
-            else if (conn == 8) solve_block<8>(c_batch[p], it, k, smem);
-            else solve_block<6>(c_batch[p], it, k, smem);
+            const int g0 = s_k;
+            if (g0 >= total) break;
+            const int nb = total - g0 < grab ? total - g0 : grab;
+            if (tid < nb) {
+                const int q = batch_owner(s_lbase, nlive, g0 + tid);
+                const int p = s_list[q];
+                const int i = g0 + tid - s_lbase[q];
+                const int t = s_t[p] + 1;
+                const int kb = s_full[p] ? i
+                                         : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).sq[(size_t)(t & 1) * s_K[p] + i]);
+                s_gp[tid] = p;
+                s_gk[tid] = kb;
+                s_gq[tid] = s_full[p] ? 0 : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).qs[kb]);
+            }
+            __syncthreads();
+            for (int j0 = 0; j0 < nb;) {
+                const int p = s_gp[j0];
+                int j1 = j0 + 1;
+                while (j1 < nb && s_gp[j1] == p) ++j1;
+                const int t = s_t[p] + 1;
+                IterArgs it = iter_args(t, s_mu[p]);
+                it.qeval = !s_full[p];
+                const int conn = c_batch[p].conn;
+                if (tid == 0) {
+                    int np = 0;
+                    for (int j = j0; j < j1; ++j)
+                        if (s_gq[j]) s_gpk[np++] = s_gk[j];
+                    s_gnp = np;
+                }
+                __syncthreads();
+                if (s_gnp) {
+                    if (conn == 4) partial_solve_multi<4>(c_batch[p], it, s_gpk, s_gnp, s_gok);
+                    else if (conn == 8) partial_solve_multi<8>(c_batch[p], it, s_gpk, s_gnp, s_gok);
+                    else partial_solve_multi<6>(c_batch[p], it, s_gpk, s_gnp, s_gok);
+                }
+                for (int j = j0, jp = 0; j < j1; ++j) {
+                    bool done = false;
+                    if (s_gq[j]) done = s_gok[jp++] != 0;
+                    if (done) continue;
+                    if (conn == 4) solve_block<4>(c_batch[p], it, s_gk[j], smem, false);
+                    else if (conn == 8) solve_block<8>(c_batch[p], it, s_gk[j], smem, false);
+                    else solve_block<6>(c_batch[p], it, s_gk[j], smem, false);
+                }
+                __syncthreads();
+                j0 = j1;
+            }
         }
         if (!grid_sync(bc, gridDim.x, nbar, P.spin_limit)) break;
         // update phase
@@ -3234,22 +3294,58 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
                 }
             }
         }
+        // a few entries per grab; with worklists the blocks of one problem among
+        // them are updated together when forced (or in its first iteration)
+        grab = total / (int)gridDim.x;
+        grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
         for (;;) {
             __syncthreads();
-            if (tid == 0) s_k = (int)atomicAdd(&bc->work[1], 1u);
+            if (tid == 0) s_k = (int)atomicAdd(&bc->work[1], (unsigned)grab);
             __syncthreads();
-            const int gk = s_k;
-            if (gk >= total) break;
-            const int q = batch_owner(s_lbase, nlive, gk);
-            const int p = s_list[q];
-            const int i = gk - s_lbase[q];
-            const int t = s_t[p] + 1;
-            const int k = s_full[p] ? i
-                                    : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).uq[(size_t)(t & 1) * s_K[p] + i]);
-            const int conn = c_batch[p].conn;
-            if (conn == 4) update_block<4>(c_batch[p], s_mu[p], t, k, s_full[p]);
-            else if (conn == 8) update_block<8>(c_batch[p], s_mu[p], t, k, s_full[p]);
-            else update_block<6>(c_batch[p], s_mu[p], t, k, s_full[p]);
+            const int g0 = s_k;
+            if (g0 >= total) break;
+            const int nb = total - g0 < grab ? total - g0 : grab;
+            if (tid < nb) {
+                const int q = batch_owner(s_lbase, nlive, g0 + tid);
+                const int p = s_list[q];
+                const int i = g0 + tid - s_lbase[q];
+                const int t = s_t[p] + 1;
+                const int kb = s_full[p] ? i
+                                         : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).uq[(size_t)(t & 1) * s_K[p] + i]);
+                s_gp[tid] = p;
+                s_gk[tid] = kb;
+                // together: problems with worklists, in their first iteration or forced blocks
+                s_gq[tid] = c_batch[p].sched == nullptr ? 0
+                            : (s_full[p] ? 1 : (__ldcg(&sched_view(c_batch[p].sched, s_K[p]).qs[kb]) != 0));
+            }
+            __syncthreads();
+            for (int j0 = 0; j0 < nb;) {
+                const int p = s_gp[j0];
+                int j1 = j0 + 1;
+                while (j1 < nb && s_gp[j1] == p) ++j1;
+                const int t = s_t[p] + 1;
+                const int conn = c_batch[p].conn;
+                if (tid == 0) {
+                    int np = 0;
+                    for (int j = j0; j < j1; ++j)
+                        if (s_gq[j]) s_gpk[np++] = s_gk[j];
+                    s_gnp = np;
+                }
+                __syncthreads();
+                if (s_gnp) {
+                    if (conn == 4) update_blocks_multi<4>(c_batch[p], s_mu[p], t, s_gpk, s_gnp, s_full[p]);
+                    else if (conn == 8) update_blocks_multi<8>(c_batch[p], s_mu[p], t, s_gpk, s_gnp, s_full[p]);
+                    else update_blocks_multi<6>(c_batch[p], s_mu[p], t, s_gpk, s_gnp, s_full[p]);
+                }
+                for (int j = j0; j < j1; ++j) {
+                    if (s_gq[j]) continue;
+                    if (conn == 4) update_block<4>(c_batch[p], s_mu[p], t, s_gk[j], s_full[p]);
+                    else if (conn == 8) update_block<8>(c_batch[p], s_mu[p], t, s_gk[j], s_full[p]);
+                    else update_block<6>(c_batch[p], s_mu[p], t, s_gk[j], s_full[p]);
+                }
+                __syncthreads();
+                j0 = j1;
+            }
         }
         if (blockIdx.x == 0 && tid == 0) {
             unsigned y = 0;
