@@ -2131,6 +2131,61 @@ __device__ void finish_block(const PersistArgs& P, int k, long long* red) {
     __syncthreads();
 }
 
+// Step a8 over the whole grid at the end of a persistent launch, as a flat
+// grid-stride loop over the block-major pixel index (coalesced reads of the
+// labels, unaries and weight planes; no per-block barriers): labels in the
+// caller's image order and E_int (unaries of the labelled pixels plus every
+// cut forward edge, each undirected edge once) into ctrl->energy.  The sum is
+// in int64 and so exact in any order.  Every thread of every CTA calls it.
+template <int CONN>
+__device__ void finish_flat(const PersistArgs& P, long long* red) {
+    const Geo& g = P.s.g;
+    constexpr int nh = CONN / 2;
+    const int B = g.B;
+    long long acc = 0;
+    // N < 2^31 (the context checks it), so the index arithmetic stays in 32 bits
+    const unsigned stride = gridDim.x * blockDim.x, n = (unsigned)g.N, ub = (unsigned)B;
+    for (unsigned gu = blockIdx.x * blockDim.x + threadIdx.x; gu < n; gu += stride) {
+        const long long gi = gu;
+        const int k = (int)(gu / ub), v = (int)(gu - (unsigned)k * ub);
+        const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+        const int lx = v % g.bw, ly = (v / g.bw) % g.bh, lz = v / (g.bw * g.bh);
+        const int yi = __ldcg(&P.s.yhat[gi]);
+        if (P.out_labels) {
+            const int z = kz * g.bd + lz, y = ky * g.bh + ly, x = kx * g.bw + lx;
+            if (z < g.Du && y < g.Hu && x < g.Wu) P.out_labels[((long long)z * g.Hu + y) * g.Wu + x] = (uint8_t)yi;
+        }
+        if (P.out_energy) {
+            acc += (long long)P.s.U[gi] * yi;
+#pragma unroll
+            for (int d = 0; d < nh; ++d) {
+                int dz, dy, dx;
+                dir_off<CONN>(d, dz, dy, dx);
+                const int nlz = lz + dz, nly = ly + dy, nlx = lx + dx;
+                long long gj;
+                if (nlz < g.bd && nly < g.bh && nlx >= 0 && nlx < g.bw) {
+                    gj = gi + (dz * g.bh + dy) * g.bw + dx;
+                } else {
+                    int kn, ln;
+                    if (!cross_nbr<CONN>(g, kz, ky, kx, lz, ly, lx, d, kn, ln)) continue;
+                    gj = (long long)kn * B + ln;
+                }
+                if (yi != __ldcg(&P.s.yhat[gj])) acc += P.s.Wl[(long long)d * g.N + gi];
+            }
+        }
+    }
+    if (!P.out_energy) return;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        if (t) atomicAdd(&P.s.ctrl->energy, (unsigned long long)t);
+    }
+}
+
 // Next block for this CTA: static stride, or the phase's atomic counter.
 __device__ __forceinline__ int next_block(int dynamic, unsigned* counter, int k_prev, int* s_k) {
     if (!dynamic) return k_prev < 0 ? (int)blockIdx.x : k_prev + (int)gridDim.x;
@@ -2350,7 +2405,7 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
     // every exit above follows the last iteration's second barrier, and its
     // labels were written before the first: the finish can read them all
     if (!failed && (P.out_labels || P.out_energy))
-        for (int k = blockIdx.x; k < K; k += gridDim.x) finish_block<CONN>(P, k, s_red);
+        finish_flat<CONN>(P, s_red);
 }
 
 // ---------------------------------------------------------------------------
