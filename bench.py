@@ -35,6 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 LAMBDAS = (1.0, 4.0, 16.0)
+ARENA_BYTES = 0        # serving: the server's device arena (0: its default, 3/4 of the free memory)
 METRIC = "pixels/sec to ADMM convergence"
 PROFILES = os.path.join(ROOT, "profiles")
 KERNEL_SRC = os.path.join(ROOT, "paper_1704_03116_gb300", "csrc", "dope_kernels.cuh")
@@ -368,7 +369,7 @@ def _serve(dope, torch, reqs, dev_in, labels, mode, arrivals, warm, submit=None)
     if submit is None:
         def submit(srv, r, x, lab, tag):
             srv.submit(r["grid"], r["conn"], r["block"], r["lam"], x[0], x[1], lab, tag=tag)
-    srv = dope.Server(mode=mode)
+    srv = dope.Server(mode=mode, hbm_bytes=ARENA_BYTES)
     for (x, lab, r) in warm:                          # first launches, tables
         submit(srv, r, x, lab, 0)
     got = 0
@@ -836,6 +837,8 @@ def main():
     ap.add_argument("--requests", type=int, default=1000, help="serving workload: requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving workload: arrivals per second")
     ap.add_argument("--no-saturated", action="store_true", help="serving workload: skip the capacity runs")
+    ap.add_argument("--arena-gb", type=float, default=0.0,
+                    help="serving: bound the server's device arena (GB; 0 = 3/4 of the free memory)")
     ap.add_argument("--no-serving", action="store_true",
                     help="default workload: skip the serving comparison added to its line")
     ap.add_argument("--no-extras", action="store_true",
@@ -844,6 +847,8 @@ def main():
                     help="time the oracle (all cores, one thread) and the serial whole-grid solve on the host")
     ap.add_argument("--cpu-reps", type=int, default=5, help="--cpu-set: runs per timing (median)")
     args = ap.parse_args()
+    global ARENA_BYTES
+    ARENA_BYTES = int(args.arena_gb * (1 << 30))
     if args.cpu_set:
         return run_cpu_set(args)
     if args.impl == "reference":
