@@ -887,8 +887,8 @@ struct UpdSmem {
     unsigned act[MB][CHUNK_WORDS];   // chunks found active
     unsigned mm[MB];             // per block: push mask
     int okb[MB];                 // per block: labels stand
+    int qb[MB];                  // per block: list state (0 not forced, 1 quiet, 2 forced and active)
     int tot;
-    int qs;
 };
 __device__ __forceinline__ UpdSmem& upd_smem() {
     __shared__ UpdSmem u;
@@ -1670,113 +1670,52 @@ __device__ __forceinline__ void update_chunk(const UA& __restrict__ A, double mu
     pm_out = pm;
 }
 
+// Eq. 10 / Eq. 11 on up to MB blocks kk[0..nb) of one problem.  Each block's
+// chunks to update are chosen first: every chunk in a full iteration (full !=
+// 0: the first of a launch, or no worklists) or of a block that is not
+// forced; a forced block's active chunks and those holding a slot whose cross
+// neighbour's label changed otherwise (every other slot is trivial with G =
+// 0: its update is the identity and adds +0 to r_k^2).  The chunks of all the
+// blocks are spread over the CTA's warps, so their load latencies overlap;
+// each block's r_k^2 is then summed in a fixed order, whatever the CTA shape
+// (slots in chunks of 32, each chunk by the same butterfly, chunks in
+// increasing order), and its pushes made by its own warp.
 template <int CONN, class UA>
-__device__ void update_block(const UA& __restrict__ A, double mu, int t, int k, int selfpush = 0) {
+__device__ void update_blocks(const UA& __restrict__ A, double mu, int t, const int* kk, int nb, int full) {
     const Geo& g = A.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const bool wl = A.sched != nullptr;
-    const SchedView sv = sched_view(A.sched, g.K);
-    // r_k^2 is summed in a fixed order, whatever the CTA shape: face slots in
-    // chunks of 32, each chunk by the same butterfly, chunks in increasing order
-    UpdSmem& us = upd_smem();
-    double (&part)[128] = us.part[0];
-    unsigned (&pmask)[128] = us.pm[0];
-    unsigned (&s_do)[CHUNK_WORDS] = us.dom[0];   // chunks updated here
-    int& s_qs = us.qs;
-    const int nchunks = (g.F + 31) >> 5;
-    // A forced block (quiet, or with active chunks) updates only its active
-    // chunks and those holding a slot whose cross neighbour's label changed:
-    // every other slot is trivial with G = 0, so its update is the identity
-    // and adds +0 to r_k^2.  Other blocks update every chunk.
-    if (tid < CHUNK_WORDS) {
-        unsigned m = 0xffffffffu;
-        if (wl) {
-            const int q = __ldcg(&sv.qs[k]);
-            const unsigned du = __ldcg(&sv.duc[(size_t)k * CHUNK_WORDS + tid]);
-            if (!selfpush && q != 0) m = __ldcg(&sv.act[(size_t)k * CHUNK_WORDS + tid]) | du;
-            if (du) sv.duc[(size_t)k * CHUNK_WORDS + tid] = 0u;
-            if (tid == 0) s_qs = q;
-        }
-        s_do[tid] = m;
-    }
-    __syncthreads();
-    int seen = 0;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        if (!((s_do[ch >> 5] >> (ch & 31)) & 1u)) continue;
-        if ((seen++ % nw) != wid) continue;
-        double d2;
-        unsigned pm;
-        update_chunk<CONN>(A, mu, t, k, ch, selfpush, sv, d2, pm);
-        if (lane == 0) {
-            part[ch] = d2;
-            pmask[ch] = pm;
-        }
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double r2 = 0.0;
-        unsigned m = 0;
-        for (int ch = 0; ch < nchunks; ++ch) {
-            if (!((s_do[ch >> 5] >> (ch & 31)) & 1u)) continue;   // +0: adds nothing
-            r2 = __dadd_rn(r2, part[ch]);
-            m |= pmask[ch];
-        }
-        A.r2blk[k] = r2;
-        if (r2 != 0.0) atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
-        if (wl) {
-            // the blocks next to a face pixel whose state changed (and this
-            // block, if it changed or is not quiet) are solved next iteration
-            if (selfpush || s_qs != 1) m |= 1u << 13;
-            pmask[0] = m;
-        }
-    }
-    __syncthreads();
-    if (wl) {
-        wl_push_mask(g, k, pmask[0], sv.smark, sv.sq + (size_t)((t + 1) & 1) * g.K, &sv.sq_n[(t + 1) & 1],
-                     wl_mark(A.epoch, t + 1));
-        __syncthreads();
-    }
-}
-
-// Updates of up to MB forced blocks at once (none in the first iteration of a
-// launch): the chunks of all of them (active, or next to a changed label) are
-// spread over the CTA's warps; each block's r_k^2 is then summed in its fixed
-// chunk order and its pushes made by its own group of threads.
-template <int CONN, class UA>
-__device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, const int* kk, int nb,
-                                    int full = 0) {
-    const Geo& g = A.g;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const SchedView sv = sched_view(A.sched, g.K);
     UpdSmem& us = upd_smem();
     double (&partm)[MB][128] = us.part;
     unsigned (&pmm)[MB][128] = us.pm;
     unsigned (&s_dom)[MB][CHUNK_WORDS] = us.dom;
-    unsigned (&s_mm)[MB] = us.mm;
-    int& s_totm = us.tot;
     const int nchunks = (g.F + 31) >> 5;
     if (tid < nb * CHUNK_WORDS) {
         const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
-        if (full) {
-            // the first iteration of a launch: every chunk (and no list state is read)
-            const int hi = nchunks - w * 32;
-            s_dom[j][w] = hi <= 0 ? 0u : (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u));
-        } else {
+        const int hi = nchunks - w * 32;
+        const unsigned all = hi <= 0 ? 0u : (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u));
+        unsigned m = all;
+        int q = 0;
+        if (wl && !full) {   // (a full iteration reads no list state)
             const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
+            q = __ldcg(&sv.qs[kk[j]]);
             const unsigned du = __ldcg(&sv.duc[o]);
-            s_dom[j][w] = __ldcg(&sv.act[o]) | du;
+            if (q != 0) m = (__ldcg(&sv.act[o]) | du) & all;
             if (du) sv.duc[o] = 0u;
         }
+        s_dom[j][w] = m;
+        if (w == 0) us.qb[j] = q;
     }
     __syncthreads();
     if (tid == 0) {
         int tot = 0;
         for (int j = 0; j < nb; ++j)
             for (int w = 0; w < CHUNK_WORDS; ++w) tot += __popc(s_dom[j][w]);
-        s_totm = tot;
+        us.tot = tot;
     }
     __syncthreads();
-    const int tot = s_totm;
+    const int tot = us.tot;
     for (int tk = wid; tk < tot; tk += nw) {
         int r = tk, j = 0, w = 0;
         for (;;) {
@@ -1808,13 +1747,15 @@ __device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, 
         }
         A.r2blk[k] = r2;
         if (r2 != 0.0) atomicMax(&A.ctrl->r2max[t], (unsigned long long)__double_as_longlong(r2));
-        if (full || __ldcg(&sv.qs[k]) != 1) m |= 1u << 13;
-        s_mm[j] = m;
+        // the blocks next to a face pixel whose state changed (and this block,
+        // if it changed or is not quiet) are solved next iteration
+        if (full || us.qb[j] != 1) m |= 1u << 13;
+        us.mm[j] = m;
     }
     __syncthreads();
-    if (wid < nb && lane < 27) {
+    if (wl && wid < nb && lane < 27) {
         const int j = wid, k = kk[j];
-        const unsigned m = s_mm[j];
+        const unsigned m = us.mm[j];
         if ((m >> lane) & 1u) {
             const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
             const int nkz = kz + lane / 9 - 1, nky = ky + (lane / 3) % 3 - 1, nkx = kx + lane % 3 - 1;
@@ -1826,11 +1767,18 @@ __device__ void update_blocks_multi(const UA& __restrict__ A, double mu, int t, 
     __syncthreads();
 }
 
+// One block's update (see update_blocks).
+template <int CONN, class UA>
+__device__ __forceinline__ void update_block(const UA& __restrict__ A, double mu, int t, int k, int full) {
+    const int kk[1] = {k};
+    update_blocks<CONN>(A, mu, t, kk, 1, full);
+}
+
 // One launch = one iteration's Eq. 10 / Eq. 11 update, one CTA per block.
 template <int CONN>
 __global__ void __launch_bounds__(256) k_face_update(UpdArgs A) {
     if (*(volatile int*)&A.ctrl->conv_t) return;
-    update_block<CONN>(A, A.mu, A.t, blockIdx.x);
+    update_block<CONN>(A, A.mu, A.t, blockIdx.x, 0);
 }
 
 // Threads of a k_face_update CTA (one CTA per block) for F face slots.
@@ -2195,6 +2143,30 @@ __device__ __forceinline__ int next_block(int dynamic, unsigned* counter, int k_
     return *s_k;
 }
 
+// Hands out entries [0, n) of a list to the CTAs in pieces of at most MB:
+// when n <= MB x grid, one even piece per CTA (n / grid or one more; no
+// atomics, so no CTA takes a second piece while others idle); otherwise
+// pieces of MB grabbed from *counter (zeroed beforehand) until none is left.
+// f(i0, nb) runs with the whole CTA; pieces are separated by __syncthreads.
+template <class Fn>
+__device__ __forceinline__ void list_pieces(int n, unsigned* counter, int* s_i, Fn&& f) {
+    const int G = (int)gridDim.x;
+    if (n <= MB * G) {
+        const int i0 = (int)((long long)blockIdx.x * n / G);
+        const int i1 = (int)((long long)(blockIdx.x + 1) * n / G);
+        if (i1 > i0) f(i0, i1 - i0);
+        return;
+    }
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) *s_i = (int)atomicAdd(counter, (unsigned)MB);
+        __syncthreads();
+        const int i0 = *s_i;
+        if (i0 >= n) break;
+        f(i0, n - i0 < MB ? n - i0 : MB);
+    }
+}
+
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
 // arrival counter only grows: barrier number b of the launch completes when
 // it reaches b * nblocks.  Thread 0 arrives with a release RMW (the CTA's
@@ -2304,18 +2276,10 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
                  i = next_block(P.dynamic, &c->work[0], i, &s_k))
                 solve_block<CONN>(P.s, it, full ? i : __ldcg(&sv.sq[(t & 1) * (size_t)K + i]), smem);
         } else {
-            // from the list, a few entries per grab: the forced blocks among them
-            // are re-evaluated together (partial_solve_multi), the others (and
-            // any whose partial solve fails) solved one by one
-            int grab = ns / (int)gridDim.x;
-            grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
-            for (;;) {
-                __syncthreads();
-                if (threadIdx.x == 0) s_k = (int)atomicAdd(&c->work[0], (unsigned)grab);
-                __syncthreads();
-                const int i0 = s_k;
-                if (i0 >= ns) break;
-                const int nb = ns - i0 < grab ? ns - i0 : grab;
+            // from the list, a few entries at a time: the forced blocks among
+            // them are re-evaluated together (partial_solve_multi), the others
+            // (and any whose partial solve fails) solved one by one
+            auto piece = [&](int i0, int nb) {
                 if (threadIdx.x < nb) {
                     const int kb = __ldcg(&sv.sq[(t & 1) * (size_t)K + i0 + threadIdx.x]);
                     s_kk[threadIdx.x] = kb;
@@ -2336,7 +2300,9 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
                     if (s_qq[j]) done = s_pok[jp++] != 0;
                     if (!done) solve_block<CONN>(P.s, it, s_kk[j], smem, false);
                 }
-            }
+                __syncthreads();
+            };
+            list_pieces(ns, &c->work[0], &s_k, piece);
         }
         const long long c1 = clock64();
         if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { failed = true; break; }
@@ -2351,35 +2317,16 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
                  i = next_block(P.dynamic, &c->work[1], i, &s_k))
                 update_block<CONN>(P.u, mu, t, full ? i : __ldcg(&sv.uq[(t & 1) * (size_t)K + i]), full ? 1 : 0);
         } else {
-            // from the list, a few entries per grab: forced blocks updated together
-            int grab = nu / (int)gridDim.x;
-            grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
-            for (;;) {
+            // from the list (or every block, in a full iteration), a few
+            // entries at a time, updated together
+            auto piece = [&](int i0, int nb) {
+                if (threadIdx.x < nb)
+                    s_kk[threadIdx.x] = full ? i0 + (int)threadIdx.x
+                                             : __ldcg(&sv.uq[(t & 1) * (size_t)K + i0 + threadIdx.x]);
                 __syncthreads();
-                if (threadIdx.x == 0) s_k = (int)atomicAdd(&c->work[1], (unsigned)grab);
-                __syncthreads();
-                const int i0 = s_k;
-                if (i0 >= nu) break;
-                const int nb = nu - i0 < grab ? nu - i0 : grab;
-                if (threadIdx.x < nb) {
-                    const int kb = full ? i0 + (int)threadIdx.x
-                                        : __ldcg(&sv.uq[(t & 1) * (size_t)K + i0 + threadIdx.x]);
-                    s_kk[threadIdx.x] = kb;
-                    s_qq[threadIdx.x] = full ? 1 : __ldcg(&sv.qs[kb]);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    int np = 0;
-                    for (int j = 0; j < nb; ++j)
-                        if (s_qq[j]) s_pk[np++] = s_kk[j];
-                    s_np = np;
-                }
-                __syncthreads();
-                const int np = s_np;
-                if (np) update_blocks_multi<CONN>(P.u, mu, t, s_pk, np, full ? 1 : 0);
-                for (int j = 0; j < nb; ++j)
-                    if (!s_qq[j]) update_block<CONN>(P.u, mu, t, s_kk[j], 0);
-            }
+                update_blocks<CONN>(P.u, mu, t, s_kk, nb, full ? 1 : 0);
+            };
+            list_pieces(nu, &c->work[1], &s_k, piece);
         }
         if (wl && !full && blockIdx.x == 0 && threadIdx.x == 0) {
             atomicAdd(&c->sched_work[0], (unsigned long long)ns);
@@ -3218,7 +3165,7 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
     __shared__ unsigned char s_conv[BATCH_MAX];
     __shared__ unsigned char s_full[BATCH_MAX];   // 1: this iteration does every block of the problem
     __shared__ int s_nlive, s_total, s_k, s_any, s_done;
-    __shared__ int s_gp[MB], s_gk[MB], s_gq[MB], s_gpk[MB], s_gok[MB], s_gnp;   // a grab of list entries
+    __shared__ int s_gp[MB], s_gk[MB], s_gq[MB], s_gpk[MB], s_gok[MB], s_gnp;   // a piece of list entries
     const int np = P.nprob;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     Ctrl* bc = P.bc;
@@ -3270,17 +3217,9 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
                 if (c_batch[p].sched) sched_view(c_batch[p].sched, s_K[p]).sq_n[(s_t[p] + 2) & 1] = 0u;
             }
         }
-        // a few entries per grab; the forced blocks of one problem among them are
-        // re-evaluated together (partial_solve_multi), the others one by one
-        int grab = total / (int)gridDim.x;
-        grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
-        for (;;) {
-            __syncthreads();
-            if (tid == 0) s_k = (int)atomicAdd(&bc->work[0], (unsigned)grab);
-            __syncthreads();
-            const int g0 = s_k;
-            if (g0 >= total) break;
-            const int nb = total - g0 < grab ? total - g0 : grab;
+        // a few entries at a time; the forced blocks of one problem among them
+        // are re-evaluated together (partial_solve_multi), the others one by one
+        auto solve_piece = [&](int g0, int nb) {
             if (tid < nb) {
                 const int q = batch_owner(s_lbase, nlive, g0 + tid);
                 const int p = s_list[q];
@@ -3324,7 +3263,8 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
                 __syncthreads();
                 j0 = j1;
             }
-        }
+        };
+        list_pieces(total, &bc->work[0], &s_k, solve_piece);
         if (!grid_sync(bc, gridDim.x, nbar, P.spin_limit)) break;
         // update phase
         for (int q = tid; q < nlive; q += blockDim.x) {
@@ -3349,17 +3289,9 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
                 }
             }
         }
-        // a few entries per grab; with worklists the blocks of one problem among
-        // them are updated together when forced (or in its first iteration)
-        grab = total / (int)gridDim.x;
-        grab = grab < 1 ? 1 : (grab > MB ? MB : grab);
-        for (;;) {
-            __syncthreads();
-            if (tid == 0) s_k = (int)atomicAdd(&bc->work[1], (unsigned)grab);
-            __syncthreads();
-            const int g0 = s_k;
-            if (g0 >= total) break;
-            const int nb = total - g0 < grab ? total - g0 : grab;
+        // a few entries at a time; the blocks of one problem among them are
+        // updated together
+        auto update_piece = [&](int g0, int nb) {
             if (tid < nb) {
                 const int q = batch_owner(s_lbase, nlive, g0 + tid);
                 const int p = s_list[q];
@@ -3369,9 +3301,6 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
                                          : __ldcg(&sched_view(c_batch[p].sched, s_K[p]).uq[(size_t)(t & 1) * s_K[p] + i]);
                 s_gp[tid] = p;
                 s_gk[tid] = kb;
-                // together: problems with worklists, in their first iteration or forced blocks
-                s_gq[tid] = c_batch[p].sched == nullptr ? 0
-                            : (s_full[p] ? 1 : (__ldcg(&sched_view(c_batch[p].sched, s_K[p]).qs[kb]) != 0));
             }
             __syncthreads();
             for (int j0 = 0; j0 < nb;) {
@@ -3380,28 +3309,13 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_batch(Ba
                 while (j1 < nb && s_gp[j1] == p) ++j1;
                 const int t = s_t[p] + 1;
                 const int conn = c_batch[p].conn;
-                if (tid == 0) {
-                    int np = 0;
-                    for (int j = j0; j < j1; ++j)
-                        if (s_gq[j]) s_gpk[np++] = s_gk[j];
-                    s_gnp = np;
-                }
-                __syncthreads();
-                if (s_gnp) {
-                    if (conn == 4) update_blocks_multi<4>(c_batch[p], s_mu[p], t, s_gpk, s_gnp, s_full[p]);
-                    else if (conn == 8) update_blocks_multi<8>(c_batch[p], s_mu[p], t, s_gpk, s_gnp, s_full[p]);
-                    else update_blocks_multi<6>(c_batch[p], s_mu[p], t, s_gpk, s_gnp, s_full[p]);
-                }
-                for (int j = j0; j < j1; ++j) {
-                    if (s_gq[j]) continue;
-                    if (conn == 4) update_block<4>(c_batch[p], s_mu[p], t, s_gk[j], s_full[p]);
-                    else if (conn == 8) update_block<8>(c_batch[p], s_mu[p], t, s_gk[j], s_full[p]);
-                    else update_block<6>(c_batch[p], s_mu[p], t, s_gk[j], s_full[p]);
-                }
-                __syncthreads();
+                if (conn == 4) update_blocks<4>(c_batch[p], s_mu[p], t, s_gk + j0, j1 - j0, s_full[p]);
+                else if (conn == 8) update_blocks<8>(c_batch[p], s_mu[p], t, s_gk + j0, j1 - j0, s_full[p]);
+                else update_blocks<6>(c_batch[p], s_mu[p], t, s_gk + j0, j1 - j0, s_full[p]);
                 j0 = j1;
             }
-        }
+        };
+        list_pieces(total, &bc->work[1], &s_k, update_piece);
         if (blockIdx.x == 0 && tid == 0) {
             unsigned y = 0;
             if (P.yield_flag) {
