@@ -64,6 +64,10 @@ struct dope_ctx {
     Ctrl* ctrl = nullptr;
     size_t ctrl_bytes = 0;
     unsigned char* sched = nullptr;   // block worklists of the persistent / batched kernels (sched_bytes)
+    unsigned long long* wslot = nullptr;   // run-ahead windows of the persistent kernel: [K][F] entry slots,
+    unsigned long long* wtag = nullptr;    // [K] block tags,
+    unsigned* wmask = nullptr;             // [K][CHUNK_WORDS] entry chunks,
+    double* wst = nullptr;                 // [K][F][4] states after a window's last two iterations
     unsigned sched_epoch = 0;         // launches issued with them
     int sched_t = -1;                 // the lists are valid for iteration sched_t + 1 (-1: not valid)
     bool sched_launch = false;        // the launch in flight uses the lists
@@ -332,6 +336,12 @@ int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = 
     P.hslot = c->hslot;
     P.hinfo = c->hinfo;
     P.wl_cont = 0;
+    P.lwin = 0;
+    P.lwcap = 0;
+    P.wslot = c->wslot;
+    P.wtag = c->wtag;
+    P.wmask = c->wmask;
+    P.wst = c->wst;
     c->sched_launch = false;
     if (c->sched && !c->resident && c->p.mu_fact >= 1.0) {
         // worklists: valid while mu does not decrease (the forced test's bound
@@ -343,6 +353,16 @@ int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = 
         P.s.epoch = P.u.epoch = c->sched_epoch;
         P.wl_cont = (c->t > 0 && c->sched_t == c->t) ? 1 : 0;
         c->sched_launch = true;
+        // run-ahead windows over the lists (launch_mode 0): per-chunk partial
+        // sums of a piece of up to MB blocks, LWMAX iterations at most
+        if (c->wslot && P.dynamic && c->p.launch_mode == 0) {
+            // chunk sums of a piece (MB blocks) in at most half of it, the list
+            // of moving slots in the rest
+            const long long per_it = (long long)MB * ((c->g.F + 31) / 32) * 8;
+            const long long cap = ((long long)c->smem / 2 - (long long)MB * ((c->g.F + 31) / 32) * 8) / per_it;
+            P.lwcap = (int)(cap < LWMAX ? cap : LWMAX);
+            P.lwin = P.lwcap >= 2 ? 1 : 0;
+        }
     }
     c->sched_t = -1;
     void* args[] = {&P};
@@ -1237,6 +1257,20 @@ int dope_create_ex(const int64_t* grid, int ndim, int connectivity, const int32_
             dope_destroy(c);
             return DOPE_ECUDA;
         }
+        // run-ahead windows of the persistent kernel (list launches that are
+        // not resident); tags start below every launch's
+        if (!c->resident && c->persist_grid > 0 && c->persist_grid < g.K) {
+            A((void**)&c->wslot, sizeof(unsigned long long) * (size_t)g.K * g.F);
+            A((void**)&c->wtag, sizeof(unsigned long long) * (size_t)g.K);
+            A((void**)&c->wmask, sizeof(unsigned) * CHUNK_WORDS * (size_t)g.K);
+            A((void**)&c->wst, 4 * sizeof(double) * (size_t)g.K * g.F);
+            if (rc) { dope_destroy(c); return rc; }
+            if (cudaMemsetAsync(c->wtag, 0, sizeof(unsigned long long) * (size_t)g.K, st) != cudaSuccess) {
+                cudaGetLastError();
+                dope_destroy(c);
+                return DOPE_ECUDA;
+            }
+        }
     }
     rc = reset_state_async(c, st);
     if (rc) { dope_destroy(c); return rc; }
@@ -1320,6 +1354,10 @@ void dope_destroy(dope_ctx* c) {
     dfree(al, c->r2blk);
     dfree(al, c->ctrl);
     dfree(al, c->sched);
+    dfree(al, c->wslot);
+    dfree(al, c->wtag);
+    dfree(al, c->wmask);
+    dfree(al, c->wst);
     dfree(al, c->stage);
     dfree(al, c->stage2);
     dfree(al, const_cast<uint8_t*>(c->oa.q));
@@ -2298,7 +2336,8 @@ size_t dope_ctx_device_bytes(const dope_ctx* c) {
     if (!c) return 0;
     const size_t N = (size_t)c->g.N, KF = (size_t)c->g.K * c->g.F;
     return N * 4 + N * 4 * (size_t)(c->conn / 2) + N + 16 * KF + 8 * (size_t)c->g.K + c->ctrl_bytes +
-           (c->sched ? sched_bytes(c->g.K, c->g.F) : 0) + c->stage_bytes + c->stage2_bytes;
+           (c->sched ? sched_bytes(c->g.K, c->g.F) : 0) + c->stage_bytes + c->stage2_bytes +
+           (c->wslot ? (40 * KF + 8 * (size_t)c->g.K + 4 * CHUNK_WORDS * (size_t)c->g.K) : 0);
 }
 
 int64_t dope_ctx_pixels(const dope_ctx* c) { return c ? (int64_t)c->g.Nu : 0; }

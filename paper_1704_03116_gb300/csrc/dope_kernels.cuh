@@ -99,6 +99,8 @@ struct Geo {
     long long Nu;
 };
 
+constexpr int LWMAX = 64;   // most iterations per run-ahead window of the persistent kernel
+
 struct Ctrl {
     int conv_t;             // iteration whose stop test held (0 = not yet)
     int status;             // first DOPE_* error raised by a kernel
@@ -126,6 +128,10 @@ struct Ctrl {
                                     // first barrier wait, update phase, second barrier wait
     unsigned long long sched_work[2];   // blocks solved / updated from the worklists (statistics)
     unsigned long long sched_part;      // of those solves, the ones that evaluated only some chunks
+    unsigned cuts[2];               // persistent kernel: blocks solved by a cut, by iteration parity
+    unsigned wwork[3];              // persistent kernel's windows: piece counters of the three phases
+    int lthaw[2];                   // persistent kernel's windows: earliest iteration not proven, by window parity
+    unsigned long long r2w[2][LWMAX];   // persistent kernel's windows: bits of max_k r2_k, by window parity
     unsigned long long r2max[1];    // [max_iter + 2]: bits of max_k r2_k per iteration
 };
 
@@ -889,6 +895,8 @@ struct UpdSmem {
     int okb[MB];                 // per block: labels stand
     int qb[MB];                  // per block: list state (0 not forced, 1 quiet, 2 forced and active)
     int tot;
+    int ecnt;                    // run-ahead window: moving slots listed
+    int ovf;                     // run-ahead window: the list did not fit
 };
 __device__ __forceinline__ UpdSmem& upd_smem() {
     __shared__ UpdSmem u;
@@ -1236,6 +1244,7 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
         return;
     }
     cut_block<CONN, SA>(A, k, smem, bw, pl, imask, c_start, nullptr);
+    if (A.sched && tid == 0) atomicAdd(&A.ctrl->cuts[it.t & 1], 1u);
     if (it.qeval) {
         // blocks next to a face pixel whose label changed get updated too, and
         // the chunks of those neighbours are marked for their update
@@ -2025,6 +2034,12 @@ struct PersistArgs {
     int wl_cont;            // 1: the worklists left by the previous launch hold (first iteration uses them)
     uint8_t* out_labels;    // finish (a8) in the launch: labels in the caller's image order (or null)
     int out_energy;         // finish (a8) in the launch: E_int of the labels into ctrl->energy
+    int lwin;               // persistent kernel: run-ahead windows over the worklists
+    int lwcap;              // their longest window the dynamic shared memory holds
+    unsigned long long* wslot;   // [K][F] window entry slots: G (low 32 bits), bound (high, float)
+    unsigned long long* wtag;    // [K] tag of the last window that had the block on its list
+    unsigned* wmask;             // [K][4] that window's entry chunks of the block
+    double* wst;                 // [K][F][4] states (y, a) after a window's last two iterations
 };
 
 // Step a8 for block k at the end of a persistent launch (after a grid
@@ -2236,6 +2251,692 @@ __device__ __forceinline__ bool grid_sync(Ctrl* c, unsigned nblocks, unsigned& n
     return s_ok != 0;
 }
 
+// One Eq. 10 / Eq. 11 step of a face pixel with fixed label yh and cross sum G
+// (the operations of update_block, in the same order).
+__device__ __forceinline__ double face_step(int yh, int G, double mu, double& y, double& a) {
+    const double gq = __dmul_rn((double)G, 0.0009765625);
+    const double ya = __dadd_rn((double)yh, a);
+    const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
+    a = __dadd_rn(a, __dsub_rn((double)yh, yn));
+    y = yn;
+    const double dd = __dsub_rn((double)yh, yn);
+    return __dmul_rn(dd, dd);
+}
+
+// Bytes of dynamic shared memory of the running launch.
+__device__ __forceinline__ int dyn_smem_bytes() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return (int)r;
+}
+
+// ---------------------------------------------------------------------------
+// Run-ahead windows of the persistent kernel.  Once an iteration solves no
+// block by a cut (every block on the list kept its labels by the forced
+// tests), the labels are expected to stay frozen, and then each face slot's
+// y and a follow Eq. 10 / Eq. 11 with a constant cross sum G, independently of
+// every other slot.  A window advances Wn iterations at once over the blocks
+// S on the current solve list, in three phases separated by grid barriers:
+//
+//  1. traj: for each chunk of S holding a slot that is not trivial or whose
+//     Eq. 8 inputs changed (act | dsc, the entry chunks), G and the state at
+//     the window start; the slot's (G, bound B) go to wslot, where B bounds
+//     |a| and |y - yhat| for every state of the window (with labels frozen,
+//     a_t = g / mu_t and y_t - yhat = a_{t-1} - g / mu_t in exact arithmetic,
+//     g = G / 1024, each computed step adding a few ulps and no accumulation,
+//     so B = |a_tw| + |y_tw - yhat| + 2 |g| / mu_{tw+1} + 2^-40).  The slot's
+//     states are stepped through the window with the update's operations and
+//     each block's r2 summed per iteration in the update's fixed order, its
+//     maximum over S kept per iteration.
+//  2. cert: for each face slot of S whose state or a cross neighbour's state
+//     may move (an entry slot, or next to one), the Eq. 8 forced test of
+//     every window iteration from an interval certificate built on the
+//     bounds (the exact unary, from states replayed from the window start,
+//     where the certificate is too weak).  Every other pixel of a block of S
+//     is forced by the integer test or its exact interior unary at the
+//     block's last solve, and stays so while mu grows.  The first iteration
+//     with a slot not proven forced (or a block of S not forced at its last
+//     solve) ends the valid run.
+//  3. commit: the first valid iteration whose stop test holds, else the last
+//     valid one, is the end of the window: every entry slot's state there is
+//     replayed from the window start and written, the r2 maxima of the
+//     committed iterations copied to the trace, and the worklists left as the
+//     iteration after the end expects (the list S, its chunks marked dirty).
+//
+// Every committed state, residual and stop decision is the one the ordinary
+// iterations compute, bit for bit: the labels of the window's iterations are
+// those the ordinary solves would keep (every node proven forced), and the
+// states are computed by the same operations in the same order.
+// ---------------------------------------------------------------------------
+struct LWin {
+    int tw;                    // last iteration before the window
+    int Wn;                    // window iterations tw+1 .. tw+Wn
+    double mu;                 // mu of iteration tw+1
+    unsigned long long tag;    // tag of this window's blocks (wtag)
+    unsigned long long* r2w;   // [LWMAX] bits of max over S of r2_k, by window iteration
+    int* thaw;                 // earliest iteration not proven (atomicMin)
+};
+
+// One window step of the state (y, a) of a slot with label yh and cross sum G
+// from the window start, n steps with mu = mu0, mu0 * f, ... (the states the
+// ordinary iterations compute).
+__device__ __forceinline__ void lwin_replay(int yh, int G, double mu0, double fct, int n, double& y, double& a) {
+    double m = mu0;
+    for (int i = 0; i < n; ++i) {
+        face_step(yh, G, m, y, a);
+        m = __dmul_rn(m, fct);
+    }
+}
+
+// Sum of 32 values in the order of the warp butterfly used for a chunk's
+// (yhat - y)^2 (levels pairing lanes i and i ^ 16, then ^ 8, ^ 4, ^ 2, ^ 1),
+// by one thread: m marks the lanes whose value is not +0, v[r * stride] is
+// the value of the r-th marked lane.  Adding +0 to a value x >= +0 gives x
+// exactly, so only the pairs of two marked values are added, and the result
+// is the butterfly's, bit for bit.
+__device__ __forceinline__ double bfly_sum(unsigned m, const double* v, int stride) {
+    if (m == 0u) return 0.0;
+    if ((m & (m - 1u)) == 0u) return v[0];
+    double w[16];
+    unsigned p = 0u;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const bool lo = (m >> i) & 1u, hi = (m >> (i + 16)) & 1u;
+        const int rl = __popc(m & ((1u << i) - 1u));
+        const int rh = __popc(m & ((1u << (i + 16)) - 1u));
+        double x = 0.0;
+        if (lo && hi) x = __dadd_rn(v[rl * stride], v[rh * stride]);
+        else if (lo) x = v[rl * stride];
+        else if (hi) x = v[rh * stride];
+        w[i] = x;
+        if (lo || hi) p |= 1u << i;
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const bool a = (p >> i) & 1u, b = (p >> (i + o)) & 1u;
+            if (a && b) w[i] = __dadd_rn(w[i], w[i + o]);
+            else if (b) w[i] = w[i + o];
+        }
+        p = (p | (p >> o)) & ((1u << o) - 1u);
+    }
+    return w[0];
+}
+
+// Window iterations whose chunk sums one pass of phase 1 keeps in shared
+// memory, and entries (slots that move) a thread carries through the window.
+constexpr int LW_WB = 8;
+constexpr int LW_RMAX = 4;
+
+// Phase 1 for a piece kk[0..nb) of S.  scr / scr_bytes: dynamic shared memory.
+template <int CONN>
+__device__ __noinline__ void lwin_traj(const PersistArgs& P, const LWin& W, const int* kk, int nb,
+                                       unsigned char* scr, int scr_bytes) {
+    const UpdArgs& A = P.u;
+    const Geo& g = A.g;
+    constexpr int nh = CONN / 2;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5, NT = blockDim.x;
+    const SchedView sv = sched_view(A.sched, g.K);
+    UpdSmem& us = upd_smem();
+    unsigned (&s_dom)[MB][CHUNK_WORDS] = us.dom;
+    double* mus = us.part[0];            // mu of each window iteration
+    const int Wn = W.Wn;
+    if (tid < nb * CHUNK_WORDS) {
+        const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
+        const int k = kk[j];
+        const size_t o = (size_t)k * CHUNK_WORDS + w;
+        const unsigned m = __ldcg(&sv.act[o]) | __ldcg(&sv.dsc[o]);
+        s_dom[j][w] = m;
+        P.wmask[o] = m;
+        if (w == 0) {
+            P.wtag[k] = W.tag;
+            if (__ldcg(&sv.qs[k]) == 0) atomicMin(W.thaw, W.tw + 1);   // not forced: its next solve cuts
+        }
+    }
+    if (tid == 0) {
+        double m = W.mu;
+        for (int i = 0; i < Wn; ++i) {
+            mus[i] = m;
+            m = __dmul_rn(m, P.mu_fact);
+        }
+        us.ecnt = 0;
+        us.ovf = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int j = 0; j < nb; ++j) {
+            us.okb[j] = tot;
+            for (int w = 0; w < CHUNK_WORDS; ++w) tot += __popc(s_dom[j][w]);
+        }
+        us.tot = tot;
+    }
+    __syncthreads();
+    const int tot = us.tot;
+    // scratch: chunk sums part[tot][Wn], per chunk its moving lanes and their
+    // first entry, per entry its slot (x2, + label) and G, and the entries'
+    // (yhat - y)^2 for LW_WB iterations at a time
+    double* part = reinterpret_cast<double*>(scr);
+    unsigned* t_mask = reinterpret_cast<unsigned*>(part + (size_t)tot * Wn);
+    int* t_base = reinterpret_cast<int*>(t_mask + tot);
+    const size_t head = ((size_t)tot * Wn * 8 + (size_t)tot * 8 + 15) & ~(size_t)15;
+    const int ecap = scr_bytes > (long long)head ? (int)(((size_t)scr_bytes - head) / (8 + 4 + 8 * LW_WB)) : 0;
+    long long* e_s = reinterpret_cast<long long*>(scr + head);
+    double* e_d = reinterpret_cast<double*>(e_s + ecap);
+    int* e_G = reinterpret_cast<int*>(e_d + (size_t)ecap * LW_WB);
+    // pass A, a warp per chunk: G, the bound and the entry list
+    for (int tk = wid; tk < tot; tk += nw) {
+        int r = tk, j = 0, w = 0;
+        for (;;) {
+            const int c = __popc(s_dom[j][w]);
+            if (r < c) break;
+            r -= c;
+            if (++w == CHUNK_WORDS) { w = 0; ++j; }
+        }
+        unsigned mm = s_dom[j][w];
+        for (int i = 0; i < r; ++i) mm &= mm - 1;
+        const int ch = w * 32 + __ffs(mm) - 1;
+        const int k = kk[j];
+        const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+        const int f = ch * 32 + lane;
+        bool mv = false;
+        int G = 0, yh = 0;
+        long long s = 0;
+        if (f < g.F) {
+            const int v = A.faceLocal[f];
+            const long long gi = (long long)k * g.B + v;
+            int wj[CONN], yj[CONN];
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) {
+                int kn, ln, fn;
+                wj[d] = 0;
+                yj[d] = 0;
+                if (halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn)) {
+                    const long long gj = (long long)kn * g.B + ln;
+                    wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + gj];
+                    yj[d] = __ldcg(&A.yhat[gj]);
+                }
+            }
+            yh = __ldcg(&A.yhat[gi]);
+#pragma unroll
+            for (int d = 0; d < CONN; ++d) G += wj[d] * (yh - yj[d]);
+            s = (long long)k * g.F + f;
+            const double y = __ldcg(&A.yF[s]), a = __ldcg(&A.aF[s]);
+            // a slot with G = 0, a = +0 and y = yhat keeps its state and adds +0
+            mv = !(G == 0 && __double_as_longlong(a) == 0 &&
+                   __double_as_longlong(y) == __double_as_longlong((double)yh));
+            float bf = 9.094947017729282e-13f;   // 2^-40
+            if (mv) {
+                bf = __double2float_ru(fabs(a) + fabs(y - (double)yh) +
+                                       2.0 * fabs((double)G) * 0.0009765625 * (1.0 / W.mu) * (1.0 + 1e-12) +
+                                       9.094947017729282e-13);
+                // above 2^-40 for every moving slot (2^-40 with G = 0 marks a still one)
+                if (__float_as_uint(bf) <= 0x2b800000u) bf = __uint_as_float(0x2b800001u);
+            }
+            P.wslot[s] = ((unsigned long long)__float_as_uint(bf) << 32) | (unsigned)G;
+        }
+        const unsigned ntm = __ballot_sync(0xffffffffu, mv);
+        int base = 0;
+        if (ntm) {
+            if (lane == 0) base = atomicAdd(&us.ecnt, __popc(ntm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+        }
+        if (base + __popc(ntm) > ecap) {
+            if (lane == 0) us.ovf = 1;
+        } else if (mv) {
+            const int e = base + __popc(ntm & ((1u << lane) - 1u));
+            e_s[e] = (s << 1) | yh;
+            e_G[e] = G;
+        }
+        if (lane == 0) {
+            t_mask[tk] = ntm;
+            t_base[tk] = base;
+        }
+    }
+    __syncthreads();
+    const int ne = us.ecnt;
+    if (us.ovf || ne > LW_RMAX * NT) {
+        // more moving slots than the scratch holds: no window this time
+        if (tid == 0) atomicMin(W.thaw, W.tw + 1);
+        __syncthreads();
+        return;
+    }
+    // the entries a thread carries: e = tid + r NT
+    double ey[LW_RMAX], ea[LW_RMAX];
+#pragma unroll
+    for (int r = 0; r < LW_RMAX; ++r) {
+        const int e = tid + r * NT;
+        ey[r] = 0.0;
+        ea[r] = 0.0;
+        if (e < ne) {
+            const long long s = e_s[e] >> 1;
+            ey[r] = __ldcg(&A.yF[s]);
+            ea[r] = __ldcg(&A.aF[s]);
+        }
+    }
+    for (int i0 = 0; i0 < Wn; i0 += LW_WB) {
+        const int nb8 = Wn - i0 < LW_WB ? Wn - i0 : LW_WB;
+#pragma unroll
+        for (int r = 0; r < LW_RMAX; ++r) {
+            const int e = tid + r * NT;
+            if (e >= ne) continue;
+            const int yh = (int)(e_s[e] & 1), G = e_G[e];
+            for (int ii = 0; ii < nb8; ++ii) {
+                e_d[(size_t)e * LW_WB + ii] = face_step(yh, G, mus[i0 + ii], ey[r], ea[r]);
+                if (i0 + ii == Wn - 2 || i0 + ii == Wn - 1) {
+                    // the states after the window's last two iterations
+                    const long long s = e_s[e] >> 1;
+                    const int q = i0 + ii == Wn - 1 ? 1 : 0;
+                    P.wst[(size_t)s * 4 + 2 * q] = ey[r];
+                    P.wst[(size_t)s * 4 + 2 * q + 1] = ea[r];
+                }
+            }
+        }
+        __syncthreads();
+        // chunk sums, the lanes of a warp on the same chunk where they can
+        for (int q = tid; q < tot * nb8; q += NT) {
+            const int tk = q / nb8, ii = q - tk * nb8;
+            part[(size_t)tk * Wn + i0 + ii] = bfly_sum(t_mask[tk], e_d + (size_t)t_base[tk] * LW_WB + ii, LW_WB);
+        }
+        __syncthreads();
+    }
+    // each block's r2 per iteration: its chunks' sums in increasing chunk order
+    // (the other chunks' slots are trivial and add +0)
+    for (int q = tid; q < nb * Wn; q += NT) {
+        const int j = q / Wn, i = q % Wn;
+        const int t0 = us.okb[j], t1 = j + 1 < nb ? us.okb[j + 1] : tot;
+        double r2 = 0.0;
+        for (int tk = t0; tk < t1; ++tk) r2 = __dadd_rn(r2, part[(size_t)tk * Wn + i]);
+        if (r2 != 0.0) atomicMax(&W.r2w[i], (unsigned long long)__double_as_longlong(r2));
+    }
+    __syncthreads();
+}
+
+// The exact Eq. 8 forced test of face slot f of block k at window iteration
+// i (the unary of iteration tw+i from the states after iteration tw+i-1,
+// replayed from the window start where they move; mv: some state around the
+// slot moves, eo / em: the slot / its cross neighbours are entry slots).
+template <int CONN>
+__device__ __noinline__ bool lwin_exact(const PersistArgs& P, const LWin& W, int k, int f, int i, bool mv, bool eo,
+                                        unsigned em, double m1024, long long Ui, int lab, long long cs) {
+    const SolveArgs& A = P.s;
+    const Geo& g = A.g;
+    constexpr int nh = CONN / 2;
+    const int F = g.F;
+    const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+    const long long gi = (long long)k * g.B + A.faceLocal[f];
+    const long long s = (long long)k * F + f;
+    double yv = __ldcg(&A.yF[s]), av = __ldcg(&A.aF[s]);
+    if (eo && mv) lwin_replay(lab, (int)(unsigned)__ldcg(&P.wslot[s]), W.mu, P.mu_fact, i - 1, yv, av);
+    double yjv[CONN];
+    int wj[CONN];
+    unsigned okm = 0;
+#pragma unroll
+    for (int d = 0; d < CONN; ++d) {
+        yjv[d] = 0.0;
+        wj[d] = 0;
+        int kn, ln, fn;
+        if (!halo_decode(g, A.halo[d * F + f], kz, ky, kx, kn, ln, fn)) continue;
+        okm |= 1u << d;
+        wj[d] = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
+        const long long sj = (long long)kn * F + fn;
+        yjv[d] = __ldcg(&A.yF[sj]);
+        if (mv && ((em >> d) & 1u)) {
+            double aj = __ldcg(&A.aF[sj]);
+            const int lj = __ldcg(&A.yhat[(long long)kn * g.B + ln]);
+            lwin_replay(lj, (int)(unsigned)__ldcg(&P.wslot[sj]), W.mu, P.mu_fact, i - 1, yjv[d], aj);
+        }
+    }
+    const long long C = face_cap_from<CONN>(Ui, yv, av, yjv, wj, okm, m1024);
+    return lab ? (C < -cs) : (C >= cs);
+}
+
+// Phase 2 for a piece kk[0..nb) of S.
+template <int CONN>
+__device__ __noinline__ void lwin_cert(const PersistArgs& P, const LWin& W, const int* kk, int nb) {
+    const SolveArgs& A = P.s;
+    const Geo& g = A.g;
+    constexpr int nh = CONN / 2;
+    const int F = g.F;
+    const int tid = threadIdx.x;
+    // entry chunks of the 27 blocks around each block of the piece (0 outside
+    // the grid or S), and the window iterations' constants
+    __shared__ unsigned s_nm[MB][27][CHUNK_WORDS];
+    __shared__ double s_mu[LWMAX], s_m1024[LWMAX];
+    __shared__ long long s_H[LWMAX];
+    __shared__ float s_mf[LWMAX], s_e2h[LWMAX];
+    __shared__ int s_it[LWMAX];
+    for (int q = tid; q < nb * 27; q += blockDim.x) {
+        const int j = q / 27, code = q % 27, k = kk[j];
+        const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+        const int nz = kz + code / 9 - 1, ny = ky + (code / 3) % 3 - 1, nx = kx + code % 3 - 1;
+        bool in = nz >= 0 && nz < g.nbz && ny >= 0 && ny < g.nby && nx >= 0 && nx < g.nbx;
+        const int kn = in ? (nz * g.nby + ny) * g.nbx + nx : 0;
+        in = in && __ldcg(&P.wtag[kn]) == W.tag;
+        for (int w = 0; w < CHUNK_WORDS; ++w)
+            s_nm[j][code][w] = in ? __ldcg(&P.wmask[(size_t)kn * CHUNK_WORDS + w]) : 0u;
+    }
+    if (tid == 0) {
+        double m = W.mu;
+        for (int i = 0; i < W.Wn; ++i) {
+            s_mu[i] = m;
+            m = __dmul_rn(m, P.mu_fact);
+        }
+    }
+    __syncthreads();
+    if (tid < W.Wn) {
+        // iteration tw+1+tid: m1024 and H as iter_args computes them
+        const double m1024 = __dmul_rn(1024.0, s_mu[tid]);
+        const double h = __dmul_rn(m1024, 0.5);
+        s_m1024[tid] = m1024;
+        s_it[tid] = h < 4503599627370496.0 ? 1 : 0;   // 2^52
+        s_H[tid] = s_it[tid] ? (long long)floor(h) : 0;
+        s_mf[tid] = __double2float_ru(m1024);
+        s_e2h[tid] = __fmul_ru(1.8189894035458565e-12f, __double2float_ru(h));   // 2^-40 * 2h
+    }
+    __syncthreads();
+    int fail = 0x7fffffff;   // earliest window iteration (1-based) found not forced
+    unsigned ncert = 0, nexact = 0;
+    // an entry slot that does not move has G = 0 and the bound 2^-40
+    constexpr unsigned long long STILL = 0x2b80000000000000ull;
+    for (int q = tid; q < nb * F; q += blockDim.x) {
+        const int j = q / F, f = q - j * F, k = kk[j];
+        const bool eo = (s_nm[j][13][f >> 10] >> ((f >> 5) & 31)) & 1u;
+        unsigned em = 0;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            const int he = A.halo[d * F + f];
+            if (he >= 0) {
+                const int code = he >> 24, fn = he & 0xfff;
+                if ((s_nm[j][code][fn >> 10] >> ((fn >> 5) & 31)) & 1u) em |= 1u << d;
+            }
+        }
+        // neither the slot nor a cross neighbour can move: its unary keeps the
+        // interior form of its last solve, forced while mu grows
+        if (!eo && em == 0) continue;
+        ++ncert;
+        const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+        const int v = A.faceLocal[f];
+        const long long gi = (long long)k * g.B + v;
+        const long long s = (long long)k * F + f;
+        const int lab = __ldcg(&A.yhat[gi]);
+        const long long Ui = A.U[gi];
+        const long long cs = nlink_sum<CONN>(g, A.Wl, k, v);
+        float bo = 0.f;
+        bool mv = false;   // the slot's or a cross neighbour's state moves in the window
+        if (eo) {
+            const unsigned long long e = __ldcg(&P.wslot[s]);
+            bo = __uint_as_float((unsigned)(e >> 32));
+            mv = e != STILL;
+        }
+        // the certificate's integer part and bounds, one direction at a time
+        long long I = Ui, wtot = 0;
+        float wsum = 0.f;
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int kn, ln, fn;
+            if (!halo_decode(g, A.halo[d * F + f], kz, ky, kx, kn, ln, fn)) continue;
+            const int w = (d < nh) ? A.Wl[(long long)d * g.N + gi] : A.Wl[(long long)(d - nh) * g.N + (long long)kn * g.B + ln];
+            const int lj = __ldcg(&A.yhat[(long long)kn * g.B + ln]);
+            const long long sj = (long long)kn * F + fn;
+            float bj;
+            if ((em >> d) & 1u) {
+                const unsigned long long e = __ldcg(&P.wslot[sj]);
+                bj = __uint_as_float((unsigned)(e >> 32));
+                mv = mv || e != STILL;
+            } else {
+                bj = __double2float_ru(fabs(__ldcg(&A.yF[sj]) - (double)lj));   // constant in the window
+            }
+            I += (long long)w * (lab - lj);
+            wsum = __fadd_ru(wsum, __fmul_ru((float)w, __fadd_ru(bo, bj)));
+            wtot += w;
+        }
+        // allowance for the computed value vs the exact one: 2^-40 (|I| + 3 sum w),
+        // plus 2^-40 * 2h per iteration below
+        const float cE = __double2float_ru(9.094947017729282e-13 * ((double)llabs(I) + 3.0 * (double)wtot) *
+                                           (1.0 + 1e-12));
+        const float base = __fadd_ru(wsum, cE);
+        const float bo2 = __fmul_ru(2.f, bo);
+        // With no state around the slot moving, its unary is U + (a constant)
+        // + m1024 (1/2 - yhat), which only moves away from the cut as mu
+        // grows: the first window iteration decides for all.
+        const int imax = mv ? W.Wn : 1;
+        for (int i = 1; i <= imax && i < fail; ++i) {
+            if (!s_it[i - 1]) { fail = i; break; }   // no integer bound
+            const long long H = s_H[i - 1];
+            const float dl = __fadd_ru(__fadd_ru(base, __fmul_ru(s_mf[i - 1], bo2)), s_e2h[i - 1]);
+            bool ok = false;
+            if (dl < 4.0e18f) {
+                const long long D = (dl < 2.0e9f ? (long long)(int)ceilf(dl) : (long long)ceilf(dl)) + 1;
+                ok = lab ? (I - H + D + 1 <= -cs) : (I + H - D - 1 >= cs);
+            }
+            if (!ok) {
+                ++nexact;
+                ok = lwin_exact<CONN>(P, W, k, f, i, mv, eo, em, s_m1024[i - 1], Ui, lab, cs);
+            }
+            if (!ok) { fail = i; break; }
+        }
+    }
+    if (fail != 0x7fffffff) atomicMin(W.thaw, W.tw + fail);
+    // statistics: slots certified, exact unaries evaluated
+    ncert = __reduce_add_sync(0xffffffffu, ncert);
+    nexact = __reduce_add_sync(0xffffffffu, nexact);
+    if ((tid & 31) == 0) {
+        if (ncert) atomicAdd(&A.ctrl->wcyc[6], (unsigned long long)ncert);
+        if (nexact) atomicAdd(&A.ctrl->wcyc[7], (unsigned long long)nexact);
+    }
+    __syncthreads();
+}
+
+// Phase 3 for a piece kk[0..nb) (entries i0.. of the list S): the state after
+// n window iterations for every moving slot (kept by phase 1 for the last two
+// iterations, else replayed), the chunk marks the ordinary updates would have
+// made, and (list_to != null) the piece's entries copied to the list of the
+// iteration after the window.
+template <int CONN>
+__device__ __noinline__ void lwin_commit(const PersistArgs& P, const LWin& W, const int* kk, int nb, int n,
+                                         int* list_to, int i0) {
+    const UpdArgs& A = P.u;
+    const Geo& g = A.g;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const SchedView sv = sched_view(A.sched, g.K);
+    UpdSmem& us = upd_smem();
+    unsigned (&s_dom)[MB][CHUNK_WORDS] = us.dom;
+    if (list_to && tid < nb) list_to[i0 + tid] = kk[tid];
+    if (tid < nb * CHUNK_WORDS) {
+        const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
+        const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
+        const unsigned m = __ldcg(&P.wmask[o]);
+        s_dom[j][w] = m;
+        // the entry chunks are evaluated at the next solve
+        if (n > 0 && m) atomicOr(&sv.dsc[o], m);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int j = 0; j < nb; ++j)
+            for (int w = 0; w < CHUNK_WORDS; ++w) tot += __popc(s_dom[j][w]);
+        us.tot = tot;
+    }
+    __syncthreads();
+    const int tot = n > 0 ? us.tot : 0;
+    const int q = n == W.Wn ? 1 : (n == W.Wn - 1 ? 0 : -1);   // kept state, or replay
+    for (int tk = wid; tk < tot; tk += nw) {
+        int r = tk, j = 0, w = 0;
+        for (;;) {
+            const int c = __popc(s_dom[j][w]);
+            if (r < c) break;
+            r -= c;
+            if (++w == CHUNK_WORDS) { w = 0; ++j; }
+        }
+        unsigned mm = s_dom[j][w];
+        for (int i = 0; i < r; ++i) mm &= mm - 1;
+        const int ch = w * 32 + __ffs(mm) - 1;
+        const int k = kk[j];
+        const int kz = k / (g.nby * g.nbx), ky = (k / g.nbx) % g.nby, kx = k % g.nbx;
+        const int f = ch * 32 + lane;
+        bool changed = false;
+        if (f < g.F) {
+            const long long s = (long long)k * g.F + f;
+            const int yh = __ldcg(&A.yhat[(long long)k * g.B + A.faceLocal[f]]);
+            const int G = (int)(unsigned)__ldcg(&P.wslot[s]);
+            const double y0 = __ldcg(&A.yF[s]), a0 = __ldcg(&A.aF[s]);
+            const bool mv = !(G == 0 && __double_as_longlong(a0) == 0 &&
+                              __double_as_longlong(y0) == __double_as_longlong((double)yh));
+            if (mv) {
+                double y = y0, a = a0;
+                if (q >= 0) {
+                    y = __ldcg(&P.wst[(size_t)s * 4 + 2 * q]);
+                    a = __ldcg(&P.wst[(size_t)s * 4 + 2 * q + 1]);
+                } else {
+                    lwin_replay(yh, G, W.mu, P.mu_fact, n, y, a);
+                }
+                if (__double_as_longlong(y) != __double_as_longlong(y0) ||
+                    __double_as_longlong(a) != __double_as_longlong(a0)) {
+                    A.yF[s] = y;
+                    A.aF[s] = a;
+                    changed = true;
+                }
+            }
+        }
+        // a changed slot's cross neighbours' chunks are evaluated at the next
+        // solve (its own chunk is an entry chunk, marked above)
+#pragma unroll
+        for (int d = 0; d < CONN; ++d) {
+            int kn = -1, ln, fn = 0;
+            bool mk = false;
+            if (changed) mk = halo_decode(g, A.halo[d * g.F + f], kz, ky, kx, kn, ln, fn);
+            const unsigned key = mk ? (unsigned)kn * 128u + (unsigned)(fn >> 5) : 0xffffffffu;
+            const unsigned grp = __match_any_sync(0xffffffffu, key);
+            if (mk && lane == __ffs(grp) - 1) chunk_mark(sv.dsc, kn, fn);
+        }
+    }
+    __syncthreads();
+}
+
+// Length of a window from iteration tw (launch ends after tlimit).  Once
+// labels are frozen every block residual shrinks by 1/mu_fact per iteration,
+// so the stop test is expected about ln(r/eps)/ln(mu_fact) iterations on; the
+// window is cut there (plus one).  This only sizes the window; what is
+// committed is decided by the exact stop test.
+static __device__ __noinline__ int lwin_size(const PersistArgs& P, int tw, int tlimit) {
+    const Ctrl* c = P.s.ctrl;
+    int Wn = min(min(LWMAX, P.lwcap), tlimit - tw);
+    const double r_tw = __dsqrt_rn(__longlong_as_double((long long)__ldcg(&c->r2max[tw])));
+    const double r_pr = tw >= 2 ? __dsqrt_rn(__longlong_as_double((long long)__ldcg(&c->r2max[tw - 1]))) : 0.0;
+    const bool geometric = r_pr > 0.0 && fabs(r_tw * P.mu_fact / r_pr - 1.0) < 1e-3;
+    if (r_tw > P.s.eps && P.mu_fact > 1.0) {
+        const double n_pred = ceil(log(r_tw / P.s.eps) / log(P.mu_fact));
+        if (n_pred + 1.0 < (double)Wn) Wn = max(1, (int)n_pred + 1);
+    }
+    if (!geometric) Wn = min(Wn, 16);
+    return Wn;
+}
+
+struct LWRes {
+    int tend;        // last iteration committed
+    int stop;        // its stop test held
+    int ran_out;     // every window iteration was proven (labels still frozen)
+    int failed;      // a grid barrier gave up
+    unsigned nbar;   // barriers passed so far in the launch
+};
+
+// One window from iteration tw with mu of iteration tw+1 (every CTA, uniform
+// arguments): the three phases and their barriers (see LWin).
+template <int CONN>
+__device__ __noinline__ LWRes lwin_run(const PersistArgs& P, int tw, double mu, int Wn, int nwin, unsigned nbar,
+                                       unsigned char* smem, int* s_kk, int* s_k) {
+    Ctrl* c = P.s.ctrl;
+    const int K = P.s.g.K;
+    const SchedView sv = sched_view(P.s.sched, K);
+    __shared__ int s_tend, s_stop;
+    LWRes R;
+    R.failed = 0;
+    LWin W;
+    W.tw = tw;
+    W.Wn = Wn;
+    W.mu = mu;
+    W.tag = ((unsigned long long)P.s.epoch << 32) | (unsigned)(nwin + 1);
+    W.r2w = c->r2w[nwin & 1];
+    W.thaw = &c->lthaw[nwin & 1];
+    const int ns = (int)__ldcg(&sv.sq_n[(tw + 1) & 1]);
+    const int* Sl = sv.sq + (size_t)((tw + 1) & 1) * K;
+    const long long w0 = clock64();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->wwork[1] = 0u;
+        c->wwork[2] = 0u;
+    }
+    auto load_piece = [&](int i0, int nb) {
+        if (threadIdx.x < nb) s_kk[threadIdx.x] = __ldcg(&Sl[i0 + threadIdx.x]);
+        __syncthreads();
+    };
+    const int scr_bytes = dyn_smem_bytes();
+    auto p1 = [&](int i0, int nb) { load_piece(i0, nb); lwin_traj<CONN>(P, W, s_kk, nb, smem, scr_bytes); };
+    list_pieces(ns, &c->wwork[0], s_k, p1);
+    const long long w1 = clock64();
+    if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { R.failed = 1; R.nbar = nbar; return R; }
+    const long long w2 = clock64();
+    auto p2 = [&](int i0, int nb) { load_piece(i0, nb); lwin_cert<CONN>(P, W, s_kk, nb); };
+    list_pieces(ns, &c->wwork[1], s_k, p2);
+    const long long w3 = clock64();
+    if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { R.failed = 1; R.nbar = nbar; return R; }
+    const long long w4 = clock64();
+    // resolution (the same in every CTA): the valid run ends before the
+    // earliest iteration not proven; the window ends at the first valid
+    // iteration whose stop test holds, else at the valid end
+    const int tstar = __ldcg(W.thaw);
+    const int tvalid = min(tstar - 1, tw + Wn);
+    if (threadIdx.x == 0) {
+        int tend = tvalid, stop = 0;
+        for (int tt = tw + 1; tt <= tvalid; ++tt) {
+            const double r2 = __longlong_as_double((long long)__ldcg(&W.r2w[tt - tw - 1]));
+            if (!(__dsqrt_rn(r2) > P.s.eps)) { tend = tt; stop = 1; break; }
+        }
+        s_tend = tend;
+        s_stop = stop;
+    }
+    __syncthreads();
+    const int tend = s_tend, stop = s_stop;
+    const int n = tend - tw;
+    int* list_to = (((tend + 1) ^ (tw + 1)) & 1) ? sv.sq + (size_t)((tend + 1) & 1) * K : nullptr;
+    auto p3 = [&](int i0, int nb) {
+        load_piece(i0, nb);
+        lwin_commit<CONN>(P, W, s_kk, nb, n, list_to, i0);
+    };
+    list_pieces(ns, &c->wwork[2], s_k, p3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int tt = tw + 1; tt <= tend; ++tt) c->r2max[tt] = __ldcg(&W.r2w[tt - tw - 1]);
+        if (list_to) {
+            sv.sq_n[(tend + 1) & 1] = (unsigned)ns;
+            sv.uq_n[(tend + 1) & 1] = 0u;
+        }
+        c->windows += 1;
+        c->window_iters += n;
+        c->cuts[(tend + 1) & 1] = 0u;
+        // the next window's phase-1 counter, residuals and thaw
+        c->wwork[0] = 0u;
+        for (int i = 0; i < LWMAX; ++i) c->r2w[(nwin + 1) & 1][i] = 0ull;
+        c->lthaw[(nwin + 1) & 1] = 0x7fffffff;
+    }
+    const long long w5 = clock64();
+    if (!grid_sync(c, gridDim.x, nbar, P.spin_limit)) { R.failed = 1; R.nbar = nbar; return R; }
+    if (threadIdx.x == 0) {
+        const long long w6 = clock64();
+        atomicAdd(&c->wcyc[0], (unsigned long long)(w1 - w0));
+        atomicAdd(&c->wcyc[1], (unsigned long long)(w2 - w1));
+        atomicAdd(&c->wcyc[2], (unsigned long long)(w3 - w2));
+        atomicAdd(&c->wcyc[3], (unsigned long long)(w4 - w3));
+        atomicAdd(&c->wcyc[4], (unsigned long long)(w5 - w4));
+        atomicAdd(&c->wcyc[5], (unsigned long long)(w6 - w5));
+    }
+    R.tend = tend;
+    R.stop = stop;
+    R.ran_out = tstar > tw + Wn;
+    R.nbar = nbar;
+    return R;
+}
+
 // Occupancy of the block-solver kernels by CTA width: 256 threads (up to
 // 2048 nodes, 4 per thread for 32x32 blocks) run 3 CTAs per SM with 80
 // registers; 512 threads (blocks up to 4096 nodes) run 2 CTAs per SM with 64.
@@ -2243,7 +2944,7 @@ template <int NT>
 struct SolverOcc { static constexpr int min_blocks = NT <= 256 ? 3 : 2; };
 
 template <int CONN, int NT>
-__global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persistent(PersistArgs P) {
+__global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persistent(const __grid_constant__ PersistArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_k;
     __shared__ int s_kk[MB], s_qq[MB], s_pk[MB], s_pok[MB], s_np;   // a grab of list entries
@@ -2256,12 +2957,53 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
     unsigned nbar = 0;
     const bool wl = P.s.sched != nullptr;
     const SchedView sv = sched_view(P.s.sched, K);
-    for (int j = 0; j < P.n; ++j) {
-        t = P.t0 + j + 1;
+    // Window state, the same in every thread of the CTA, kept in shared memory
+    // (thread 0 writes it after the last barrier of an iteration or window,
+    // every thread reads it after the loop's __syncthreads): the last
+    // iteration solved no block by a cut, iterations to wait before the next
+    // try, the current wait after failed tries, windows run.  The window code
+    // reads the launch arguments from a shared copy.
+    __shared__ int s_ws[4];
+    __shared__ __align__(16) unsigned char s_Pbuf[sizeof(PersistArgs)];
+    if (threadIdx.x < 4) s_ws[threadIdx.x] = 0;
+    if (P.lwin)
+        for (int i = threadIdx.x; i < (int)(sizeof(PersistArgs) / 4); i += blockDim.x)
+            reinterpret_cast<int*>(s_Pbuf)[i] = reinterpret_cast<const int*>(&P)[i];
+    const PersistArgs& SP = *reinterpret_cast<const PersistArgs*>(s_Pbuf);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->lthaw[0] = c->lthaw[1] = 0x7fffffff;
+    while (t < P.t0 + P.n) {
+        __syncthreads();
+        if (P.lwin && s_ws[0] && s_ws[1] == 0 && P.t0 + P.n - t >= 2) {
+            const int Wn = lwin_size(SP, t, P.t0 + P.n);
+            if (Wn >= 2) {
+                const LWRes R = lwin_run<CONN>(SP, t, mu, Wn, s_ws[3], nbar, smem, s_kk, &s_k);
+                nbar = R.nbar;
+                if (R.failed) { failed = true; break; }
+                for (int i = t; i < R.tend; ++i) mu = __dmul_rn(mu, P.mu_fact);
+                const int n = R.tend - t;
+                t = R.tend;
+                if (R.stop) { conv = 1; break; }
+                if (threadIdx.x == 0) {
+                    // a window that ran to its end leaves the labels frozen; one
+                    // cut short waits for a frozen ordinary iteration, and one
+                    // that committed next to nothing backs off before the next try
+                    s_ws[3] += 1;
+                    s_ws[0] = R.ran_out;
+                    if (n < 2) {
+                        s_ws[2] = s_ws[2] ? min(2 * s_ws[2], 16) : 1;
+                        s_ws[1] = s_ws[2];
+                    } else {
+                        s_ws[2] = 0;
+                    }
+                }
+                continue;
+            }
+        }
+        ++t;
         IterArgs it = iter_args(t, mu);
         // with worklists, the launch's first iteration does every block;
         // later ones the blocks on the lists (see sched_view)
-        const bool full = !wl || (j == 0 && !P.wl_cont);
+        const bool full = !wl || (t == P.t0 + 1 && !P.wl_cont);
         it.qeval = !full;
         // the update counter is idle during the solve phase and vice versa,
         // so each is reset in the other phase; likewise the list counts
@@ -2309,6 +3051,8 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
         const long long c2 = clock64();
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->work[0] = 0u;
+            // (every CTA read the cut count of iteration t-1 before the barrier)
+            c->cuts[(t + 1) & 1] = 0u;
             if (wl) sv.uq_n[(t + 1) & 1] = 0u;
         }
         const int nu = full ? K : (int)__ldcg(&sv.uq_n[t & 1]);
@@ -2342,6 +3086,10 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
             atomicAdd(&c->pcyc[3], (unsigned long long)(c4 - c3));
         }
         mu = __dmul_rn(mu, P.mu_fact);
+        if (threadIdx.x == 0) {
+            s_ws[0] = wl && !full && __ldcg(&c->cuts[t & 1]) == 0u;
+            if (s_ws[1] > 0) --s_ws[1];
+        }
         const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[t]));
         if (!(__dsqrt_rn(r2) > P.s.eps)) { conv = 1; break; }
     }
@@ -2479,17 +3227,6 @@ __device__ __forceinline__ void update_block_resident(const UpdArgs& A, int k, i
     __syncthreads();
 }
 
-// One Eq. 10 / Eq. 11 step of a face pixel with fixed label yh and cross sum G
-// (the operations of update_block, in the same order).
-__device__ __forceinline__ double face_step(int yh, int G, double mu, double& y, double& a) {
-    const double gq = __dmul_rn((double)G, 0.0009765625);
-    const double ya = __dadd_rn((double)yh, a);
-    const double yn = G ? __dsub_rn(ya, __ddiv_rn(gq, mu)) : ya;
-    a = __dadd_rn(a, __dsub_rn((double)yh, yn));
-    y = yn;
-    const double dd = __dsub_rn((double)yh, yn);
-    return __dmul_rn(dd, dd);
-}
 
 __host__ __device__ inline size_t window_smem_bytes(int conn, int B, int F, int NH) {
     return resident_layout(conn, B, F, NH).window_end;
