@@ -124,14 +124,19 @@ typedef struct {
     int fold_rounds_max;        /* most folding rounds one block took */
     double phase_cycles[4];     /* SM cycles of the block solver, summed over CTAs:
                                    capacity build, folding, push-relabel pulses, BFS */
-    double loop_cycles[4];      /* persistent launch, summed over CTAs and iterations:
-                                   solve phase, first barrier wait, update phase,
-                                   run-ahead windows */
+    double loop_cycles[4];      /* persistent launch, summed over CTAs and ordinary iterations:
+                                   solve phase, first barrier wait, update phase, second
+                                   barrier wait (k_admm_resident: the last entry is its
+                                   run-ahead windows) */
     int windows;                /* run-ahead windows run (launch_mode 0) */
     int window_iterations;      /* iterations committed from run-ahead windows */
-    double window_cycles[8];    /* run-ahead windows, summed over CTAs: build, block solve,
-                                   label check, own update, halo update, window set-up,
-                                   wait at the closing barrier, rest of the resolution */
+    double window_cycles[8];    /* run-ahead windows, summed over CTAs.  k_admm_resident: build,
+                                   block solve, label check, own update, halo update, window
+                                   set-up, wait at the closing barrier, rest of the resolution.
+                                   k_admm_persistent: SM cycles of its three phases and the
+                                   barrier wait after each (state stepping, wait, certificates,
+                                   wait, commit, wait), then two counts: face slots certified
+                                   and exact unaries evaluated where a certificate was too weak */
     int solver_kernel;          /* kernel that ran the iterations: 0 k_block_solve + k_face_update
                                    (two launches per iteration), 1 k_admm_persistent, 2 k_admm_resident,
                                    3 k_admm_batch (dope_iterate_batch) */

@@ -160,12 +160,21 @@ int solver_width(int B, int threads) {
     return B <= 1024 ? 256 : threads;
 }
 
-const void* persistent_fn(int conn, int nt) {
+// The persistent kernel for a connectivity and CTA width; win: its form with
+// run-ahead windows (launched after the plain form, see k_admm_persistent).
+const void* persistent_fn(int conn, int nt, bool win = false) {
+    if (win) {
+        if (nt <= 256)
+            return conn == 4 ? (const void*)k_admm_persistent<4, 256, true>
+                 : conn == 8 ? (const void*)k_admm_persistent<8, 256, true> : (const void*)k_admm_persistent<6, 256, true>;
+        return conn == 4 ? (const void*)k_admm_persistent<4, 512, true>
+             : conn == 8 ? (const void*)k_admm_persistent<8, 512, true> : (const void*)k_admm_persistent<6, 512, true>;
+    }
     if (nt <= 256)
-        return conn == 4 ? (const void*)k_admm_persistent<4, 256>
-             : conn == 8 ? (const void*)k_admm_persistent<8, 256> : (const void*)k_admm_persistent<6, 256>;
-    return conn == 4 ? (const void*)k_admm_persistent<4, 512>
-         : conn == 8 ? (const void*)k_admm_persistent<8, 512> : (const void*)k_admm_persistent<6, 512>;
+        return conn == 4 ? (const void*)k_admm_persistent<4, 256, false>
+             : conn == 8 ? (const void*)k_admm_persistent<8, 256, false> : (const void*)k_admm_persistent<6, 256, false>;
+    return conn == 4 ? (const void*)k_admm_persistent<4, 512, false>
+         : conn == 8 ? (const void*)k_admm_persistent<8, 512, false> : (const void*)k_admm_persistent<6, 512, false>;
 }
 
 const void* batch_fn(int nt) {
@@ -381,6 +390,13 @@ int persistent_issue(dope_ctx* c, int n, cudaStream_t st, uint8_t* out_labels = 
     } else {
         e = cudaLaunchCooperativeKernel(persistent_fn(c->conn, c->pthreads), c->persist_grid, c->pthreads, args,
                                         c->smem, st);
+        if (e == cudaSuccess && P.lwin) {
+            // the windowed form continues where the plain one handed off (it
+            // returns at once when the plain one ended the launch)
+            c->launches++;
+            e = cudaLaunchCooperativeKernel(persistent_fn(c->conn, c->pthreads, true), c->persist_grid, c->pthreads,
+                                            args, c->smem, st);
+        }
     }
     if (e != cudaSuccess) return DOPE_ECUDA;
     c->launches++;
@@ -571,8 +587,10 @@ void raise_smem_limit(const void* fn) {
 template <int CONN>
 void raise_smem_limits() {
     raise_smem_limit((const void*)k_block_solve<CONN>);
-    raise_smem_limit((const void*)k_admm_persistent<CONN, 256>);
-    raise_smem_limit((const void*)k_admm_persistent<CONN, 512>);
+    raise_smem_limit((const void*)k_admm_persistent<CONN, 256, false>);
+    raise_smem_limit((const void*)k_admm_persistent<CONN, 512, false>);
+    raise_smem_limit((const void*)k_admm_persistent<CONN, 256, true>);
+    raise_smem_limit((const void*)k_admm_persistent<CONN, 512, true>);
     raise_smem_limit((const void*)k_admm_resident<CONN>);
     raise_smem_limit((const void*)k_nsm_solve<CONN>);
 }
@@ -606,18 +624,22 @@ void choose_launch(dope_ctx* c) {
     const long long B = g.B;
     c->pthreads = solver_width(g.B, c->p.threads > 0 ? c->p.threads : c->threads);
     if (c->p.threads > 0) c->pthreads = c->threads;
-    const void* fn = persistent_fn(connectivity, c->pthreads);
     int dev = 0, sms = 0, coop = 0, per_sm = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    {
+    // co-resident CTAs of both forms (plain and windowed): the grid fits either
+    per_sm = 1 << 30;
+    for (int win = 0; win < 2; ++win) {
+        const void* fn = persistent_fn(connectivity, c->pthreads, win != 0);
         cudaFuncAttributes fa0;
+        int n = 0;
         if (cudaFuncGetAttributes(&fa0, fn) != cudaSuccess ||
             (size_t)c->smem + fa0.sharedSizeBytes > (size_t)optin ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, c->pthreads, c->smem) != cudaSuccess)
-            per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, c->pthreads, c->smem) != cudaSuccess)
+            n = 0;
+        if (n < per_sm) per_sm = n;
     }
     cudaGetLastError();
     long long cap = (long long)per_sm * sms;

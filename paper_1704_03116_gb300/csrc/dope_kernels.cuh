@@ -129,6 +129,9 @@ struct Ctrl {
     unsigned long long sched_work[2];   // blocks solved / updated from the worklists (statistics)
     unsigned long long sched_part;      // of those solves, the ones that evaluated only some chunks
     unsigned cuts[2];               // persistent kernel: blocks solved by a cut, by iteration parity
+    int handoff;                    // persistent kernel: the plain launch stopped at a frozen iteration,
+    unsigned bar_handoff;           // ... the grid barriers it had passed (bar_count goes on from there)
+    double mu_next;                 // ... and mu of the iteration after it
     unsigned wwork[3];              // persistent kernel's windows: piece counters of the three phases
     int lthaw[2];                   // persistent kernel's windows: earliest iteration not proven, by window parity
     unsigned long long r2w[2][LWMAX];   // persistent kernel's windows: bits of max_k r2_k, by window parity
@@ -2943,7 +2946,16 @@ __device__ __noinline__ LWRes lwin_run(const PersistArgs& P, int tw, double mu, 
 template <int NT>
 struct SolverOcc { static constexpr int min_blocks = NT <= 256 ? 3 : 2; };
 
-template <int CONN, int NT>
+// WIN: the form with run-ahead windows.  A solve with windows (lwin) is two
+// launches back to back: the plain form runs the ordinary iterations and, at
+// the first one that solves no block by a cut, records its iteration and mu
+// in the control block and returns (handoff, no finish); the windowed form
+// then continues from there to the end of the launch's iterations and does
+// the finish, or returns at once if the plain form already ended.  The
+// ordinary iterations thus run in a kernel with no window code (the calls
+// into it cost the iteration path registers); the windowed form runs only
+// the frozen tail.
+template <int CONN, int NT, bool WIN>
 __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persistent(const __grid_constant__ PersistArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_k;
@@ -2956,7 +2968,6 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
     bool failed = false;
     unsigned nbar = 0;
     const bool wl = P.s.sched != nullptr;
-    const SchedView sv = sched_view(P.s.sched, K);
     // Window state, the same in every thread of the CTA, kept in shared memory
     // (thread 0 writes it after the last barrier of an iteration or window,
     // every thread reads it after the loop's __syncthreads): the last
@@ -2964,16 +2975,24 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
     // try, the current wait after failed tries, windows run.  The window code
     // reads the launch arguments from a shared copy.
     __shared__ int s_ws[4];
-    __shared__ __align__(16) unsigned char s_Pbuf[sizeof(PersistArgs)];
     if (threadIdx.x < 4) s_ws[threadIdx.x] = 0;
-    if (P.lwin)
+    if (WIN) {
+        // the plain form's launch ended the solve (or the launch): nothing to do
+        if (!__ldcg(&c->handoff)) return;
+        t = __ldcg(&c->iters_done);
+        mu = __ldcg(&c->mu_next);
+        // the barrier's arrival counter only grows: continue its numbering
+        nbar = __ldcg(&c->bar_handoff);
+        if (threadIdx.x == 0) s_ws[0] = 1;
+    }
+    __shared__ __align__(16) unsigned char s_Pbuf[WIN ? sizeof(PersistArgs) : 16];
+    if (WIN)
         for (int i = threadIdx.x; i < (int)(sizeof(PersistArgs) / 4); i += blockDim.x)
             reinterpret_cast<int*>(s_Pbuf)[i] = reinterpret_cast<const int*>(&P)[i];
     const PersistArgs& SP = *reinterpret_cast<const PersistArgs*>(s_Pbuf);
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->lthaw[0] = c->lthaw[1] = 0x7fffffff;
     while (t < P.t0 + P.n) {
         __syncthreads();
-        if (P.lwin && s_ws[0] && s_ws[1] == 0 && P.t0 + P.n - t >= 2) {
+        if (WIN && s_ws[0] && s_ws[1] == 0 && P.t0 + P.n - t >= 2) {
             const int Wn = lwin_size(SP, t, P.t0 + P.n);
             if (Wn >= 2) {
                 const LWRes R = lwin_run<CONN>(SP, t, mu, Wn, s_ws[3], nbar, smem, s_kk, &s_k);
@@ -3000,10 +3019,12 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
             }
         }
         ++t;
+        // (the list pointers are derived here, not kept across the window call)
+        const SchedView sv = sched_view(P.s.sched, K);
         IterArgs it = iter_args(t, mu);
         // with worklists, the launch's first iteration does every block;
         // later ones the blocks on the lists (see sched_view)
-        const bool full = !wl || (t == P.t0 + 1 && !P.wl_cont);
+        const bool full = !wl || (!WIN && t == P.t0 + 1 && !P.wl_cont);
         it.qeval = !full;
         // the update counter is idle during the solve phase and vice versa,
         // so each is reset in the other phase; likewise the list counts
@@ -3092,7 +3113,23 @@ __global__ void __launch_bounds__(NT, SolverOcc<NT>::min_blocks) k_admm_persiste
         }
         const double r2 = __longlong_as_double((long long)__ldcg(&c->r2max[t]));
         if (!(__dsqrt_rn(r2) > P.s.eps)) { conv = 1; break; }
+        if (!WIN && P.lwin) {
+            // labels frozen: the windowed form continues from here
+            __syncthreads();
+            if (s_ws[0] && P.t0 + P.n - t >= 2) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    c->iters_done = t;
+                    c->mu_next = mu;
+                    c->bar_handoff = nbar;
+                    c->lthaw[0] = c->lthaw[1] = 0x7fffffff;   // for the windows
+                    c->conv_t = 0;
+                    c->handoff = 1;
+                }
+                return;
+            }
+        }
     }
+    if (!WIN && blockIdx.x == 0 && threadIdx.x == 0) c->handoff = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->iters_done = t;
         c->conv_t = conv ? t : 0;
