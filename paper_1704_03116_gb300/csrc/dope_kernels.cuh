@@ -2294,8 +2294,8 @@ __device__ __forceinline__ int dyn_smem_bytes() {
 //  2. cert: for each face slot of S whose state or a cross neighbour's state
 //     may move (an entry slot, or next to one), the Eq. 8 forced test of
 //     every window iteration from an interval certificate built on the
-//     bounds (the exact unary, from states replayed from the window start,
-//     where the certificate is too weak).  Every other pixel of a block of S
+//     bounds (at the window's first iteration, the exact unary where the
+//     certificate is too weak).  Every other pixel of a block of S
 //     is forced by the integer test or its exact interior unary at the
 //     block's last solve, and stays so while mu grows.  The first iteration
 //     with a slot not proven forced (or a block of S not forced at its last
@@ -2560,6 +2560,8 @@ __device__ __noinline__ void lwin_traj(const PersistArgs& P, const LWin& W, cons
 // i (the unary of iteration tw+i from the states after iteration tw+i-1,
 // replayed from the window start where they move; mv: some state around the
 // slot moves, eo / em: the slot / its cross neighbours are entry slots).
+// Phase 2 calls it for the window's first iteration only, where nothing is
+// replayed.
 template <int CONN>
 __device__ __noinline__ bool lwin_exact(const PersistArgs& P, const LWin& W, int k, int f, int i, bool mv, bool eo,
                                         unsigned em, double m1024, long long Ui, int lab, long long cs) {
@@ -2714,7 +2716,12 @@ __device__ __noinline__ void lwin_cert(const PersistArgs& P, const LWin& W, cons
                 const long long D = (dl < 2.0e9f ? (long long)(int)ceilf(dl) : (long long)ceilf(dl)) + 1;
                 ok = lab ? (I - H + D + 1 <= -cs) : (I + H - D - 1 >= cs);
             }
-            if (!ok) {
+            if (!ok && i == 1) {
+                // no certificate at the window's first iteration: the exact unary
+                // from the states at the window start decides.  Later iterations
+                // have none (their states would have to be replayed, quadratic
+                // in the window's length where certificates are weak): the
+                // window ends there.
                 ++nexact;
                 ok = lwin_exact<CONN>(P, W, k, f, i, mv, eo, em, s_m1024[i - 1], Ui, lab, cs);
             }

@@ -3,8 +3,9 @@
 Once an iteration solves no block by a cut, the kernel advances several
 iterations at once over the blocks on its solve list: the moving face slots'
 states are stepped through the window, every window iteration's Eq. 8 forced
-tests are certified (interval certificates, the exact unary where those are too
-weak), and the first iteration whose stop test holds is committed.  These tests
+tests are certified (interval certificates; at the window's first iteration the
+exact unary where those are too weak), and the first iteration whose stop test
+holds is committed.  These tests
 check that a solve with windows equals, bit for bit, the same solve without
 them (launch_mode 2) and the oracle's Algorithm 1: labels, energy, iteration
 count, residual trace and the final state (y, a, labels), in one launch or in
@@ -110,8 +111,8 @@ def test_windows_across_launches(orc, dp, volume):
 
 def test_windows_with_weak_certificates(orc, dp):
     """At mu0 = 100 with strong n-links the interval certificates fail for some
-    slots and their exact unaries decide; the solve still equals the plain one
-    and the oracle's."""
+    slots: exact unaries decide at a window's first iteration, and windows end
+    early; the solve still equals the plain one and the oracle's."""
     d = inputs.random_instance((512, 384), 8, (16, 16), lam=6.0, seed=21)
     w, p = _solve_pair(dp, d, threads=256, mu0=100.0)
     _assert_same(w, p)
