@@ -89,7 +89,9 @@ typedef struct {
     int max_pulses;      /* bound on push-relabel pulses per block and iteration */
     int fold_rounds;     /* bound on exact-folding rounds per block and iteration */
     int launch_mode;     /* 0: one persistent cooperative launch per solve / iterate call,
-                               with run-ahead windows once labels stop moving;
+                               with run-ahead windows once labels stop moving (on grids
+                               with more blocks than co-resident CTAs the windows run in
+                               a second launch queued right behind the first);
                             1: two launches per iteration (solve, update);
                             2: persistent launch without run-ahead windows */
     int grow[3];         /* overlapping partition (Section 2: blocks "can overlap"; Section 3's
