@@ -691,8 +691,9 @@ def measure(name, args, world, local, with_e2e=True):
             pbytes = kn * k1 * (sfb + upb) + work["blocks_solved"] * slb + work["blocks_updated"] * upb
             processed = {"bytes_per_launch": pbytes / max(kn, 1),
                          "achieved_gbs": pbytes / (kms / 1e3) / 1e9,
-                         "model": "iteration 1 every block, later iterations the blocks on the worklists "
-                                  "(per block: solve %.0f B, update %.0f B)" % (slb, upb)}
+                         "model": "iteration 1 every block, later ordinary iterations the blocks on the "
+                                  "worklists (per block: solve %.0f B, update %.0f B); iterations inside "
+                                  "run-ahead windows not counted" % (slb, upb)}
         share = {kname: 1.0}
         if kname == "k_admm_persistent":
             # a solve that reaches frozen labels is two launches back to back
