@@ -149,7 +149,8 @@ typedef struct {
     int64_t blocks_updated;     /* likewise, block updates (Eq. 10 / 11) run from the worklists */
     int64_t blocks_solved_partial;  /* of blocks_solved, those whose nodes were all still forced, so
                                    that only their active and changed chunks of face pixels were
-                                   evaluated (no capacity build, no cut) */
+                                   evaluated (no capacity build, no cut); after a launch's first
+                                   iteration, blocks whose every pixel was found forced that way */
 } dope_stats;
 
 /* Device time of the hot-path kernels, measured with CUDA events on the

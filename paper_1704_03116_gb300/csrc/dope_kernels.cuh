@@ -179,7 +179,7 @@ struct SchedView {
     unsigned* act;      // [K][4] chunks (32 face slots each) holding a slot that is not trivial
     unsigned* dsc;      // [K][4] chunks whose slots' Eq. 8 inputs changed since the block's last solve
     unsigned* duc;      // [K][4] chunks whose slots' cross-neighbour labels changed in this solve phase
-    uint8_t* qs;        // [K] 0 not forced, 1 quiet, 2 forced with active chunks
+    uint8_t* qs;        // [K] 0 not forced, 1 quiet, 2 forced with active chunks, 3 not evaluated (a launch's first iteration)
     uint8_t* yhF;
 };
 
@@ -917,11 +917,21 @@ __device__ void partial_solve_multi(const SA& __restrict__ A, const IterArgs it,
     unsigned (&s_act)[MB][CHUNK_WORDS] = us.act;
     int (&s_okb)[MB] = us.okb;
     int& s_tot = us.tot;
+    const int nchunks = (g.F + 31) >> 5;
     if (tid < nb * CHUNK_WORDS) {
         const int j = tid / CHUNK_WORDS, w = tid % CHUNK_WORDS;
         const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
-        s_ev[j][w] = __ldcg(&sv.act[o]) | __ldcg(&sv.dsc[o]);     // every active chunk is among them
+        const int q = __ldcg(&sv.qs[kk[j]]);
+        if (q == 3) {
+            // not evaluated since the launch's first iteration: every chunk,
+            // and every interior pixel below
+            const int hi = nchunks - w * 32;
+            s_ev[j][w] = hi <= 0 ? 0u : (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u));
+        } else {
+            s_ev[j][w] = __ldcg(&sv.act[o]) | __ldcg(&sv.dsc[o]);     // every active chunk is among them
+        }
         s_act[j][w] = 0u;
+        if (w == 0) us.qb[j] = q;
     }
     if (tid < MB) s_okb[tid] = 1;
     __syncthreads();
@@ -951,6 +961,26 @@ __device__ void partial_solve_multi(const SA& __restrict__ A, const IterArgs it,
             if (!fo) s_okb[j] = 0;
             if (!un) atomicOr(&s_act[j][ch >> 5], 1u << (ch & 31));
         }
+    }
+    // interior pixels of the blocks not evaluated since the launch's first
+    // iteration: the forced test of the capacity build (the integer bound,
+    // else the exact interior unary) against the intra-block n-link sum
+    const int B = g.B;
+    for (int q = tid; q < nb * B; q += blockDim.x) {
+        const int j = q / B, v = q - j * B;
+        if (us.qb[j] != 3 || A.faceIndex[v] >= 0) continue;
+        const int k = kk[j];
+        const long long gi = (long long)k * B + v;
+        const int yh = __ldcg(&A.yhat[gi]);
+        const long long Ui = A.U[gi];
+        const long long cs = nlink_sum<CONN>(g, A.Wl, k, v);
+        const long long T = yh ? Ui - it.H : Ui + it.H;
+        bool forced = it.int_test && (yh ? (T < -cs) : (T >= cs));
+        if (!forced) {
+            const long long C = interior_cap(Ui, yh, m1024);
+            forced = yh ? (C < -cs) : (C >= cs);
+        }
+        if (!forced) s_okb[j] = 0;
     }
     __syncthreads();
     // blocks whose labels stand: masks, state, and the update list (threads
@@ -1014,7 +1044,7 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
     __shared__ int s_ok;
     const long long c_start = clock64();
 
-    if (try_partial && it.qeval && __ldcg(&sv.qs[k]) != 0) {
+    if (try_partial && it.qeval && (unsigned)(__ldcg(&sv.qs[k]) - 1) < 2u) {
         // Every node of the block was forced to its label at its last solve.
         // Nodes in chunks that are neither active nor marked dirty still are
         // (their inputs did not change, and the integer test's bound only
@@ -1227,8 +1257,8 @@ __device__ void solve_block(const SA& __restrict__ A, const IterArgs it, int k, 
         const int quiet = __syncthreads_and(allu) && allf;
         if (tid == 0) {
             // 0: not forced; 1: quiet; 2: forced with active chunks.  The
-            // first iteration of a launch (no evaluation) leaves 0.
-            sv.qs[k] = (uint8_t)(!it.qeval ? 0 : (quiet ? 1 : (allf ? 2 : 0)));
+            // first iteration of a launch (no evaluation) leaves 3.
+            sv.qs[k] = (uint8_t)(!it.qeval ? 3 : (quiet ? 1 : (allf ? 2 : 0)));
             s_pm = quiet ? 0u : (1u << 13);      // a block that is not quiet is updated
         }
         if (tid < CHUNK_WORDS) {
@@ -1713,7 +1743,7 @@ __device__ void update_blocks(const UA& __restrict__ A, double mu, int t, const 
             const size_t o = (size_t)kk[j] * CHUNK_WORDS + w;
             q = __ldcg(&sv.qs[kk[j]]);
             const unsigned du = __ldcg(&sv.duc[o]);
-            if (q != 0) m = (__ldcg(&sv.act[o]) | du) & all;
+            if (q == 1 || q == 2) m = (__ldcg(&sv.act[o]) | du) & all;
             if (du) sv.duc[o] = 0u;
         }
         s_dom[j][w] = m;
@@ -2394,7 +2424,8 @@ __device__ __noinline__ void lwin_traj(const PersistArgs& P, const LWin& W, cons
         P.wmask[o] = m;
         if (w == 0) {
             P.wtag[k] = W.tag;
-            if (__ldcg(&sv.qs[k]) == 0) atomicMin(W.thaw, W.tw + 1);   // not forced: its next solve cuts
+            const int q = __ldcg(&sv.qs[k]);
+            if (q == 0 || q == 3) atomicMin(W.thaw, W.tw + 1);   // not proven forced: its next solve may cut
         }
     }
     if (tid == 0) {
